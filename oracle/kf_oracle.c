@@ -1,0 +1,832 @@
+/*
+ * kf_oracle.c -- plain FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
+ *
+ * Restates the method of arXiv 1701.02324 step by step, in the paper's order:
+ * ball tree (Sec. II-A), interpolative decomposition skeletons (Eq. e:id,
+ * Algorithm 1), the N log N factorization (Eqs. e:hodlr, e:blocksmw,
+ * e:innerid, e:invtelescope, Algorithm 2), the direct solve (Algorithm 3),
+ * the O(N log^2 N) predecessor factorization for comparison, the
+ * hierarchical matvec with lambda*I + K~, its transpose solve and the
+ * gradient with respect to b, lambda and h.
+ *
+ * Compiled with -ffp-contract=off: every a*b+c below is two roundings unless
+ * written as fma().  No blocking, fusion or reordering beyond the formulas.
+ * OpenMP is used only to run independent tree nodes at the same time; each
+ * node's arithmetic is the same sequential loop either way.
+ *
+ * Readings of points the paper leaves open are marked READING.
+ */
+#include "kf_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+  int32_t s;      /* rank s_alpha */
+  int32_t c;      /* columns of the ID: |alpha| (leaf) or s_l + s_r */
+  int64_t* skel;  /* s tree positions, pivot order */
+  double* P;      /* s x c */
+  double* Pfull;  /* |alpha| x s, Eq. e:innerid */
+  /* factorization */
+  double* LU;     /* leaf: |alpha|^2 LU of lambda I + K_aa */
+  int64_t* piv;   /* leaf row pivots */
+  double* Phat;   /* |alpha| x s */
+  double* Vl;     /* internal: K_{l~ r}, s_l x |r| */
+  double* Vr;     /* internal: K_{r~ l}, s_r x |l| */
+  double* Z;      /* internal: Z before LU */
+  double* ZLU;    /* internal: LU of Z */
+  int64_t* Zpiv;
+} node_t;
+
+struct kfo {
+  int64_t N;
+  int32_t d, m, D;
+  int32_t nnodes; /* 2^(D+1) - 1 */
+  double* X;      /* N x d, tree order */
+  int64_t* perm;  /* tree position -> original index */
+  int64_t* lo;    /* indexed by heap id */
+  int64_t* hi;
+  double h, c_exp, lambda;
+  int32_t skeletonized, factorized, variant;
+  int32_t illcond;
+  node_t* nd;     /* indexed by heap id */
+};
+
+static int is_leaf(const kfo* o, int32_t a) { return a >= (1 << o->D); }
+static int64_t nsz(const kfo* o, int32_t a) { return o->hi[a] - o->lo[a]; }
+
+/* Gaussian kernel, Eq. (e:gaussian): exp(-||x-y||^2 / (2 h^2)).  The squared
+ * distance is a sequential sum over the coordinates; c_exp = -0.5/(h*h). */
+static double kern(const kfo* o, int64_t i, int64_t j) {
+  const double* x = o->X + i * o->d;
+  const double* y = o->X + j * o->d;
+  double d2 = 0.0;
+  for (int32_t k = 0; k < o->d; ++k) {
+    double t = x[k] - y[k];
+    d2 = d2 + t * t;
+  }
+  return exp(d2 * o->c_exp);
+}
+
+/* dK/dh of the Gaussian kernel: K * ||x-y||^2 / h^3. */
+static double dkern_dh(const kfo* o, int64_t i, int64_t j) {
+  const double* x = o->X + i * o->d;
+  const double* y = o->X + j * o->d;
+  double d2 = 0.0;
+  for (int32_t k = 0; k < o->d; ++k) {
+    double t = x[k] - y[k];
+    d2 = d2 + t * t;
+  }
+  double h3 = o->h * o->h * o->h;
+  return exp(d2 * o->c_exp) * (d2 / h3);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Small dense helpers (plain loops).                                        */
+
+/* C (n x k) = A (n x p) * B (p x k), all row-major. */
+static void matmul(const double* A, const double* B, double* C, int64_t n, int64_t p, int64_t k) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < k; ++j) {
+      double acc = 0.0;
+      for (int64_t t = 0; t < p; ++t) acc = acc + A[i * p + t] * B[t * k + j];
+      C[i * k + j] = acc;
+    }
+}
+
+/* LU with partial pivoting (LAPACK GETRF semantics; ties in |pivot| go to the
+ * lowest row).  Returns the smallest |u_kk| relative to max |a_ij|. */
+static double lu_factor(double* A, int64_t* piv, int64_t n) {
+  double amax = 0.0;
+  for (int64_t i = 0; i < n * n; ++i) if (fabs(A[i]) > amax) amax = fabs(A[i]);
+  double minpiv = INFINITY;
+  for (int64_t k = 0; k < n; ++k) {
+    int64_t p = k;
+    double best = fabs(A[k * n + k]);
+    for (int64_t i = k + 1; i < n; ++i)
+      if (fabs(A[i * n + k]) > best) { best = fabs(A[i * n + k]); p = i; }
+    piv[k] = p;
+    if (p != k)
+      for (int64_t j = 0; j < n; ++j) { double t = A[k * n + j]; A[k * n + j] = A[p * n + j]; A[p * n + j] = t; }
+    double ukk = A[k * n + k];
+    if (fabs(ukk) < minpiv) minpiv = fabs(ukk);
+    if (ukk == 0.0) continue;
+    for (int64_t i = k + 1; i < n; ++i) {
+      double l = A[i * n + k] / ukk;
+      A[i * n + k] = l;
+      for (int64_t j = k + 1; j < n; ++j) A[i * n + j] = A[i * n + j] - l * A[k * n + j];
+    }
+  }
+  return (n == 0 || amax == 0.0) ? 1.0 : minpiv / amax;
+}
+
+/* Solve A X = B (trans = 0) or A^T X = B (trans = 1) in place, B is n x k. */
+static void lu_solve(const double* LU, const int64_t* piv, int64_t n, double* B, int64_t k, int trans) {
+  if (!trans) {
+    for (int64_t i = 0; i < n; ++i)
+      if (piv[i] != i)
+        for (int64_t j = 0; j < k; ++j) { double t = B[i * k + j]; B[i * k + j] = B[piv[i] * k + j]; B[piv[i] * k + j] = t; }
+    for (int64_t i = 0; i < n; ++i)          /* L y = Pb, unit lower */
+      for (int64_t t = 0; t < i; ++t)
+        for (int64_t j = 0; j < k; ++j) B[i * k + j] = B[i * k + j] - LU[i * n + t] * B[t * k + j];
+    for (int64_t i = n - 1; i >= 0; --i) {   /* U x = y */
+      for (int64_t t = i + 1; t < n; ++t)
+        for (int64_t j = 0; j < k; ++j) B[i * k + j] = B[i * k + j] - LU[i * n + t] * B[t * k + j];
+      for (int64_t j = 0; j < k; ++j) B[i * k + j] = B[i * k + j] / LU[i * n + i];
+    }
+  } else {
+    for (int64_t i = 0; i < n; ++i) {        /* U^T y = b */
+      for (int64_t t = 0; t < i; ++t)
+        for (int64_t j = 0; j < k; ++j) B[i * k + j] = B[i * k + j] - LU[t * n + i] * B[t * k + j];
+      for (int64_t j = 0; j < k; ++j) B[i * k + j] = B[i * k + j] / LU[i * n + i];
+    }
+    for (int64_t i = n - 1; i >= 0; --i)     /* L^T z = y */
+      for (int64_t t = i + 1; t < n; ++t)
+        for (int64_t j = 0; j < k; ++j) B[i * k + j] = B[i * k + j] - LU[t * n + i] * B[t * k + j];
+    for (int64_t i = n - 1; i >= 0; --i)     /* x = P^T z */
+      if (piv[i] != i)
+        for (int64_t j = 0; j < k; ++j) { double t = B[i * k + j]; B[i * k + j] = B[piv[i] * k + j]; B[piv[i] * k + j] = t; }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ball tree, Sec. II-A "Partitioning the matrix".
+ * READING: the splitting hyperplane is not specified.  For the points of a
+ * node: a = the point with the smallest original index; p = the point
+ * farthest from a; q = the point farthest from p (ties: smallest original
+ * index); every point is projected on q - p, proj_i = sum_k (x_ik - x_pk) *
+ * (x_qk - x_pk); the points are ordered by (proj, original index) and the
+ * left child takes the first floor(n/2).  Depth D = ceil(log2(N/m)) so that
+ * the leaves sit at level D = log2(N/m) as the paper states. */
+
+typedef struct { double key; int64_t orig; int64_t pos; } sortrec;
+
+static int cmp_sortrec(const void* A, const void* B) {
+  const sortrec* a = (const sortrec*)A;
+  const sortrec* b = (const sortrec*)B;
+  if (a->key < b->key) return -1;
+  if (a->key > b->key) return 1;
+  return (a->orig < b->orig) ? -1 : (a->orig > b->orig);
+}
+
+static double sqdist_rows(const double* x, const double* y, int32_t d) {
+  double acc = 0.0;
+  for (int32_t k = 0; k < d; ++k) { double t = x[k] - y[k]; acc = acc + t * t; }
+  return acc;
+}
+
+static void split_node(kfo* o, int32_t a, int32_t level) {
+  int64_t lo = o->lo[a], hi = o->hi[a], n = hi - lo;
+  if (level == o->D) return;
+  int32_t d = o->d;
+  if (n >= 2) {
+    int64_t ia = lo;
+    for (int64_t i = lo + 1; i < hi; ++i) if (o->perm[i] < o->perm[ia]) ia = i;
+    int64_t ip = lo; double best = -1.0;
+    for (int64_t i = lo; i < hi; ++i) {
+      double dd = sqdist_rows(o->X + i * d, o->X + ia * d, d);
+      if (dd > best || (dd == best && o->perm[i] < o->perm[ip])) { best = dd; ip = i; }
+    }
+    int64_t iq = lo; best = -1.0;
+    for (int64_t i = lo; i < hi; ++i) {
+      double dd = sqdist_rows(o->X + i * d, o->X + ip * d, d);
+      if (dd > best || (dd == best && o->perm[i] < o->perm[iq])) { best = dd; iq = i; }
+    }
+    sortrec* r = (sortrec*)malloc(sizeof(sortrec) * n);
+    const double* xp = o->X + ip * d;
+    const double* xq = o->X + iq * d;
+    for (int64_t i = lo; i < hi; ++i) {
+      const double* xi = o->X + i * d;
+      double acc = 0.0;
+      for (int32_t k = 0; k < d; ++k) acc = acc + (xi[k] - xp[k]) * (xq[k] - xp[k]);
+      r[i - lo].key = acc; r[i - lo].orig = o->perm[i]; r[i - lo].pos = i;
+    }
+    qsort(r, n, sizeof(sortrec), cmp_sortrec);
+    double* xs = (double*)malloc(sizeof(double) * n * d);
+    for (int64_t i = 0; i < n; ++i) memcpy(xs + i * d, o->X + r[i].pos * d, sizeof(double) * d);
+    memcpy(o->X + lo * d, xs, sizeof(double) * n * d);
+    for (int64_t i = 0; i < n; ++i) o->perm[lo + i] = r[i].orig;
+    free(xs); free(r);
+  }
+  int64_t mid = lo + n / 2;
+  o->lo[2 * a] = lo; o->hi[2 * a] = mid;
+  o->lo[2 * a + 1] = mid; o->hi[2 * a + 1] = hi;
+  split_node(o, 2 * a, level + 1);
+  split_node(o, 2 * a + 1, level + 1);
+}
+
+kfo* kfo_create(const double* X, int64_t N, int32_t d, int32_t m) {
+  if (!X || N < 1 || d < 1 || m < 1) return NULL;
+  for (int64_t i = 0; i < N * d; ++i) if (!isfinite(X[i])) return NULL;
+  kfo* o = (kfo*)calloc(1, sizeof(kfo));
+  o->N = N; o->d = d; o->m = m;
+  int32_t D = 0;
+  while (((int64_t)m << D) < N) ++D;
+  o->D = D;
+  o->nnodes = (1 << (D + 1)) - 1;
+  o->X = (double*)malloc(sizeof(double) * N * d);
+  memcpy(o->X, X, sizeof(double) * N * d);
+  o->perm = (int64_t*)malloc(sizeof(int64_t) * N);
+  for (int64_t i = 0; i < N; ++i) o->perm[i] = i;
+  o->lo = (int64_t*)calloc(o->nnodes + 1, sizeof(int64_t));
+  o->hi = (int64_t*)calloc(o->nnodes + 1, sizeof(int64_t));
+  o->lo[1] = 0; o->hi[1] = N;
+  split_node(o, 1, 0);
+  o->nd = (node_t*)calloc(o->nnodes + 1, sizeof(node_t));
+  return o;
+}
+
+static void free_factor(kfo* o) {
+  for (int32_t a = 1; a <= o->nnodes; ++a) {
+    node_t* n = &o->nd[a];
+    free(n->LU); free(n->piv); free(n->Phat); free(n->Vl); free(n->Vr);
+    free(n->Z); free(n->ZLU); free(n->Zpiv);
+    n->LU = n->Phat = n->Vl = n->Vr = n->Z = n->ZLU = NULL; n->piv = n->Zpiv = NULL;
+  }
+  o->factorized = 0;
+}
+
+static void free_skel(kfo* o) {
+  for (int32_t a = 1; a <= o->nnodes; ++a) {
+    node_t* n = &o->nd[a];
+    free(n->skel); free(n->P); free(n->Pfull);
+    n->skel = NULL; n->P = n->Pfull = NULL; n->s = 0; n->c = 0;
+  }
+  o->skeletonized = 0;
+}
+
+void kfo_free(kfo* o) {
+  if (!o) return;
+  free_factor(o);
+  free_skel(o);
+  free(o->nd); free(o->X); free(o->perm); free(o->lo); free(o->hi);
+  free(o);
+}
+
+int32_t kfo_depth(const kfo* o) { return o->D; }
+void kfo_perm(const kfo* o, int64_t* perm) { memcpy(perm, o->perm, sizeof(int64_t) * o->N); }
+void kfo_node_range(const kfo* o, int32_t a, int64_t* lo, int64_t* hi) { *lo = o->lo[a]; *hi = o->hi[a]; }
+
+/* ------------------------------------------------------------------------ */
+/* Sampling of S' (Sec. II-A: "sampling a small subset S' of S").
+ * READING: the paper defers the sampler to ASKIT.  Here S' is n_s =
+ * min(N - |alpha|, n_samp) distinct positions drawn uniformly from the
+ * complement of alpha: draw j gives u = splitmix64(seed ^ (node << 32) ^ j),
+ * c = u mod (N - |alpha|); c is skipped if already drawn; c maps to the tree
+ * position c (c < lo) or c + |alpha| (c >= lo).  When n_s equals the
+ * complement size the whole complement is taken.  The result is ascending. */
+
+/* splitmix64 (Steele, Lea, Flood 2014): add the golden-ratio increment, then
+ * the xor-shift-multiply finalizer. */
+uint64_t kfo_splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+static int cmp_i64(const void* A, const void* B) {
+  int64_t a = *(const int64_t*)A, b = *(const int64_t*)B;
+  return (a > b) - (a < b);
+}
+
+int32_t kfo_sample(const kfo* o, int32_t a, int32_t n_samp, uint64_t seed, int64_t* out) {
+  int64_t lo = o->lo[a], sz = nsz(o, a), M = o->N - sz;
+  int64_t ns = M < n_samp ? M : n_samp;
+  if (ns == M) {
+    int64_t t = 0;
+    for (int64_t i = 0; i < o->N; ++i) if (i < lo || i >= lo + sz) out[t++] = i;
+    return (int32_t)ns;
+  }
+  int64_t got = 0;
+  for (uint64_t j = 0; got < ns; ++j) {
+    uint64_t u = kfo_splitmix64(seed ^ ((uint64_t)a << 32) ^ j);
+    int64_t c = (int64_t)(u % (uint64_t)M);
+    int dup = 0;
+    for (int64_t t = 0; t < got; ++t) if (out[t] == c) { dup = 1; break; }
+    if (!dup) out[got++] = c;
+  }
+  for (int64_t t = 0; t < ns; ++t) if (out[t] >= lo) out[t] += sz;
+  qsort(out, ns, sizeof(int64_t), cmp_i64);
+  return (int32_t)ns;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Interpolative decomposition, Eq. (e:id): K_{S' C} ~ K_{S' C~} P_{C~ C}.
+ * Pivoted Householder QR (Businger-Golub) of A = K_{S' C}: at step k the
+ * squared norms of the trailing columns (rows k..) are recomputed and the
+ * largest is the pivot (ties: lowest column).  Rank rule of Sec. II-A with the
+ * diagonal of R as the singular-value estimate: s = the smallest k >= 1 with
+ * |R_kk| < tau |R_00| (0-based), capped by min(s_max, n_s, c); s = 0 when
+ * |R_00| = 0.  C~ = the first s pivots; P = [I, R11^-1 R12] with the columns
+ * put back in their original order.
+ * READING: the paper writes P = K_{S C~}^+ K_{S C}; on the sampled rows this
+ * is R11^-1 R12 of the truncated QR, the standard ID form it cites. */
+static void id_node(kfo* o, int32_t a, const int64_t* cols, int32_t c, double tau, int32_t s_max,
+                    int32_t n_samp, uint64_t seed) {
+  node_t* nd = &o->nd[a];
+  nd->c = c;
+  int64_t* S = (int64_t*)malloc(sizeof(int64_t) * (n_samp > 0 ? n_samp : 1));
+  int32_t ns = kfo_sample(o, a, n_samp, seed, S);
+  int32_t kmax = s_max;
+  if (ns < kmax) kmax = ns;
+  if (c < kmax) kmax = c;
+  double* A = (double*)malloc(sizeof(double) * (size_t)(ns > 0 ? ns : 1) * (c > 0 ? c : 1));
+  for (int32_t i = 0; i < ns; ++i)
+    for (int32_t j = 0; j < c; ++j) A[(int64_t)i * c + j] = kern(o, S[i], cols[j]);
+  int32_t* pv = (int32_t*)malloc(sizeof(int32_t) * (c > 0 ? c : 1));
+  for (int32_t j = 0; j < c; ++j) pv[j] = j;
+  double* v = (double*)malloc(sizeof(double) * (ns > 0 ? ns : 1));
+  int32_t s = kmax;
+  double r00 = 0.0;
+  for (int32_t k = 0; k < kmax; ++k) {
+    int32_t p = k; double best = -1.0;
+    for (int32_t j = k; j < c; ++j) {
+      double nrm = 0.0;
+      for (int32_t i = k; i < ns; ++i) nrm = nrm + A[(int64_t)i * c + j] * A[(int64_t)i * c + j];
+      if (nrm > best) { best = nrm; p = j; }
+    }
+    double rkk = sqrt(best);
+    if (k == 0) {
+      r00 = rkk;
+      if (r00 == 0.0) { s = 0; break; }
+    } else if (rkk < tau * r00) { s = k; break; }
+    if (p != k) {
+      for (int32_t i = 0; i < ns; ++i) { double t = A[(int64_t)i * c + k]; A[(int64_t)i * c + k] = A[(int64_t)i * c + p]; A[(int64_t)i * c + p] = t; }
+      int32_t t = pv[k]; pv[k] = pv[p]; pv[p] = t;
+    }
+    /* Householder reflector H = I - beta v v^T with H x = alpha e_0. */
+    double x0 = A[(int64_t)k * c + k];
+    double alpha = (x0 >= 0.0) ? -rkk : rkk;
+    double vtv = 0.0;
+    for (int32_t i = k; i < ns; ++i) {
+      v[i] = A[(int64_t)i * c + k];
+      if (i == k) v[i] = x0 - alpha;
+      vtv = vtv + v[i] * v[i];
+    }
+    double beta = (vtv > 0.0) ? 2.0 / vtv : 0.0;
+    for (int32_t j = k + 1; j < c; ++j) {
+      double w = 0.0;
+      for (int32_t i = k; i < ns; ++i) w = w + v[i] * A[(int64_t)i * c + j];
+      w = beta * w;
+      for (int32_t i = k; i < ns; ++i) A[(int64_t)i * c + j] = A[(int64_t)i * c + j] - w * v[i];
+    }
+    A[(int64_t)k * c + k] = alpha;
+    for (int32_t i = k + 1; i < ns; ++i) A[(int64_t)i * c + k] = 0.0;
+  }
+  /* T = R11^-1 R12 by back substitution (s x (c - s)). */
+  int32_t nc = c - s;
+  double* T = (double*)malloc(sizeof(double) * (size_t)(s > 0 ? s : 1) * (nc > 0 ? nc : 1));
+  for (int32_t j = 0; j < nc; ++j)
+    for (int32_t i = s - 1; i >= 0; --i) {
+      double acc = A[(int64_t)i * c + s + j];
+      for (int32_t t = i + 1; t < s; ++t) acc = acc - A[(int64_t)i * c + t] * T[(int64_t)t * nc + j];
+      T[(int64_t)i * nc + j] = acc / A[(int64_t)i * c + i];
+    }
+  nd->s = s;
+  nd->skel = (int64_t*)malloc(sizeof(int64_t) * (s > 0 ? s : 1));
+  nd->P = (double*)calloc((size_t)(s > 0 ? s : 1) * (c > 0 ? c : 1), sizeof(double));
+  for (int32_t i = 0; i < s; ++i) nd->skel[i] = cols[pv[i]];
+  for (int32_t i = 0; i < s; ++i) {
+    nd->P[(int64_t)i * c + pv[i]] = 1.0;
+    for (int32_t j = 0; j < nc; ++j) nd->P[(int64_t)i * c + pv[s + j]] = T[(int64_t)i * nc + j];
+  }
+  free(T); free(v); free(pv); free(A); free(S);
+}
+
+/* Columns of a node's ID: its points (leaf) or [l~ r~] (internal). */
+static int32_t id_columns(const kfo* o, int32_t a, int64_t** cols) {
+  if (is_leaf(o, a)) {
+    int32_t c = (int32_t)nsz(o, a);
+    *cols = (int64_t*)malloc(sizeof(int64_t) * (c > 0 ? c : 1));
+    for (int32_t j = 0; j < c; ++j) (*cols)[j] = o->lo[a] + j;
+    return c;
+  }
+  const node_t* l = &o->nd[2 * a];
+  const node_t* r = &o->nd[2 * a + 1];
+  int32_t c = l->s + r->s;
+  *cols = (int64_t*)malloc(sizeof(int64_t) * (c > 0 ? c : 1));
+  for (int32_t j = 0; j < l->s; ++j) (*cols)[j] = l->skel[j];
+  for (int32_t j = 0; j < r->s; ++j) (*cols)[l->s + j] = r->skel[j];
+  return c;
+}
+
+/* P_{alpha alpha~} telescoped, Eq. (e:innerid):
+ * P_{alpha alpha~} = diag(P_{l l~}, P_{r r~}) P_{[l~ r~] alpha~}. */
+static void build_pfull(kfo* o, int32_t a) {
+  node_t* nd = &o->nd[a];
+  int64_t n = nsz(o, a);
+  int32_t s = nd->s;
+  free(nd->Pfull);
+  nd->Pfull = (double*)calloc((size_t)(n > 0 ? n : 1) * (s > 0 ? s : 1), sizeof(double));
+  if (is_leaf(o, a)) {
+    for (int64_t i = 0; i < n; ++i)
+      for (int32_t j = 0; j < s; ++j) nd->Pfull[i * s + j] = nd->P[(int64_t)j * nd->c + i];
+    return;
+  }
+  const node_t* l = &o->nd[2 * a];
+  const node_t* r = &o->nd[2 * a + 1];
+  int64_t nl = nsz(o, 2 * a), nr = nsz(o, 2 * a + 1);
+  for (int64_t i = 0; i < nl; ++i)
+    for (int32_t j = 0; j < s; ++j) {
+      double acc = 0.0;
+      for (int32_t t = 0; t < l->s; ++t) acc = acc + l->Pfull[i * l->s + t] * nd->P[(int64_t)j * nd->c + t];
+      nd->Pfull[i * s + j] = acc;
+    }
+  for (int64_t i = 0; i < nr; ++i)
+    for (int32_t j = 0; j < s; ++j) {
+      double acc = 0.0;
+      for (int32_t t = 0; t < r->s; ++t) acc = acc + r->Pfull[i * r->s + t] * nd->P[(int64_t)j * nd->c + l->s + t];
+      nd->Pfull[(nl + i) * s + j] = acc;
+    }
+}
+
+/* Algorithm 1, Skeletonize(alpha): children first, then the ID of the node. */
+static void skeletonize_rec(kfo* o, int32_t a, double tau, int32_t s_max, int32_t n_samp, uint64_t seed) {
+  if (!is_leaf(o, a)) {
+#pragma omp task if (nsz(o, a) > 4096)
+    skeletonize_rec(o, 2 * a, tau, s_max, n_samp, seed);
+#pragma omp task if (nsz(o, a) > 4096)
+    skeletonize_rec(o, 2 * a + 1, tau, s_max, n_samp, seed);
+#pragma omp taskwait
+  }
+  if (a == 1) return; /* the root is not skeletonized */
+  int64_t* cols;
+  int32_t c = id_columns(o, a, &cols);
+  id_node(o, a, cols, c, tau, s_max, n_samp, seed);
+  free(cols);
+  build_pfull(o, a);
+}
+
+int32_t kfo_skeletonize(kfo* o, double h, double tau, int32_t s_max, int32_t n_samp, uint64_t seed) {
+  if (!(h > 0.0) || !(tau >= 0.0) || s_max < 0 || n_samp < 0) return KFO_EINVAL;
+  free_factor(o);
+  free_skel(o);
+  o->h = h;
+  o->c_exp = -0.5 / (h * h);
+#pragma omp parallel
+#pragma omp single
+  skeletonize_rec(o, 1, tau, s_max, n_samp, seed);
+  o->skeletonized = 1;
+  return KFO_OK;
+}
+
+int32_t kfo_rank(const kfo* o, int32_t a) { return o->nd[a].s; }
+int32_t kfo_ncols(const kfo* o, int32_t a) { return o->nd[a].c; }
+void kfo_skel(const kfo* o, int32_t a, int64_t* out) { memcpy(out, o->nd[a].skel, sizeof(int64_t) * o->nd[a].s); }
+void kfo_P(const kfo* o, int32_t a, double* out) {
+  memcpy(out, o->nd[a].P, sizeof(double) * (size_t)o->nd[a].s * o->nd[a].c);
+}
+void kfo_P_full(const kfo* o, int32_t a, double* out) {
+  memcpy(out, o->nd[a].Pfull, sizeof(double) * (size_t)nsz(o, a) * o->nd[a].s);
+}
+
+int32_t kfo_set_id(kfo* o, int32_t a, int32_t s, const int64_t* skel, const double* P) {
+  if (a < 2 || a > o->nnodes) return KFO_EINVAL;
+  free_factor(o);
+  node_t* nd = &o->nd[a];
+  int32_t c = is_leaf(o, a) ? (int32_t)nsz(o, a) : o->nd[2 * a].s + o->nd[2 * a + 1].s;
+  if (s < 0 || s > c) return KFO_EINVAL;
+  free(nd->skel); free(nd->P);
+  nd->s = s; nd->c = c;
+  nd->skel = (int64_t*)malloc(sizeof(int64_t) * (s > 0 ? s : 1));
+  nd->P = (double*)malloc(sizeof(double) * (size_t)(s > 0 ? s : 1) * (c > 0 ? c : 1));
+  memcpy(nd->skel, skel, sizeof(int64_t) * s);
+  memcpy(nd->P, P, sizeof(double) * (size_t)s * c);
+  build_pfull(o, a);
+  /* ancestors' telescoped P depend on this node */
+  for (int32_t b = a / 2; b >= 2; b /= 2)
+    if (o->nd[b].c == o->nd[2 * b].s + o->nd[2 * b + 1].s && o->nd[b].P) build_pfull(o, b);
+  return KFO_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 3, Solve(alpha, u, do_recur), applied in place to the n x k block
+ * U (rows = the node's tree positions).  Internal node: after the (optional)
+ * recursion on the children, w = v - W Z^-1 V v with
+ * V v = [K_{l~ r} v_r ; K_{r~ l} v_l] and W = diag(P^_l, P^_r) (Eq. e:blocksmw).
+ * READING: the printed last line uses u where the recursively solved v must
+ * stand; with do_recur = false the two coincide. */
+static void solve_rec(const kfo* o, int32_t a, double* U, int64_t k, int do_recur) {
+  const node_t* nd = &o->nd[a];
+  int64_t n = nsz(o, a);
+  if (is_leaf(o, a)) {
+    lu_solve(nd->LU, nd->piv, n, U, k, 0);
+    return;
+  }
+  int32_t l = 2 * a, r = 2 * a + 1;
+  int64_t nl = nsz(o, l), nr = nsz(o, r);
+  double* Ul = U;
+  double* Ur = U + nl * k;
+  if (do_recur) {
+#pragma omp task if (n > 4096)
+    solve_rec(o, l, Ul, k, 1);
+#pragma omp task if (n > 4096)
+    solve_rec(o, r, Ur, k, 1);
+#pragma omp taskwait
+  }
+  int32_t sl = o->nd[l].s, sr = o->nd[r].s, z = sl + sr;
+  if (z == 0) return;
+  double* t = (double*)malloc(sizeof(double) * z * k);
+  matmul(nd->Vl, Ur, t, sl, nr, k);            /* K_{l~ r} v_r */
+  matmul(nd->Vr, Ul, t + (int64_t)sl * k, sr, nl, k); /* K_{r~ l} v_l */
+  lu_solve(nd->ZLU, nd->Zpiv, z, t, k, 0);     /* Z^-1 V v */
+  const double* Pl = o->nd[l].Phat;
+  const double* Pr = o->nd[r].Phat;
+  for (int64_t i = 0; i < nl; ++i)
+    for (int64_t j = 0; j < k; ++j) {
+      double acc = 0.0;
+      for (int32_t q = 0; q < sl; ++q) acc = acc + Pl[i * sl + q] * t[(int64_t)q * k + j];
+      Ul[i * k + j] = Ul[i * k + j] - acc;
+    }
+  for (int64_t i = 0; i < nr; ++i)
+    for (int64_t j = 0; j < k; ++j) {
+      double acc = 0.0;
+      for (int32_t q = 0; q < sr; ++q) acc = acc + Pr[i * sr + q] * t[(int64_t)(sl + q) * k + j];
+      Ur[i * k + j] = Ur[i * k + j] - acc;
+    }
+  free(t);
+}
+
+/* W P_c with P_c = P_{[l~ r~] alpha~} = (P_{alpha~ [l~ r~]})^T:
+ * rows of l get P^_l P_c[top], rows of r get P^_r P_c[bottom]. */
+static double* w_times_pc(const kfo* o, int32_t a) {
+  const node_t* nd = &o->nd[a];
+  int32_t l = 2 * a, r = 2 * a + 1, s = nd->s, sl = o->nd[l].s, sr = o->nd[r].s;
+  int64_t nl = nsz(o, l), nr = nsz(o, r);
+  double* u = (double*)calloc((size_t)(nl + nr) * (s > 0 ? s : 1), sizeof(double));
+  for (int64_t i = 0; i < nl; ++i)
+    for (int32_t j = 0; j < s; ++j) {
+      double acc = 0.0;
+      for (int32_t q = 0; q < sl; ++q) acc = acc + o->nd[l].Phat[i * sl + q] * nd->P[(int64_t)j * nd->c + q];
+      u[i * s + j] = acc;
+    }
+  for (int64_t i = 0; i < nr; ++i)
+    for (int32_t j = 0; j < s; ++j) {
+      double acc = 0.0;
+      for (int32_t q = 0; q < sr; ++q) acc = acc + o->nd[r].Phat[i * sr + q] * nd->P[(int64_t)j * nd->c + sl + q];
+      u[(nl + i) * s + j] = acc;
+    }
+  return u;
+}
+
+/* Algorithm 2, Factorize(alpha), postorder. */
+static void factorize_rec(kfo* o, int32_t a) {
+  node_t* nd = &o->nd[a];
+  int64_t n = nsz(o, a);
+  if (is_leaf(o, a)) {
+    /* LU of lambda I + K_aa (lambda enters only the leaf blocks). */
+    nd->LU = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n * n : 1));
+    nd->piv = (int64_t*)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = 0; j < n; ++j)
+        nd->LU[i * n + j] = kern(o, o->lo[a] + i, o->lo[a] + j) + (i == j ? o->lambda : 0.0);
+    double rel = lu_factor(nd->LU, nd->piv, n);
+    if (rel < 1e-14) {
+#pragma omp atomic write
+      o->illcond = 1;
+    }
+    /* base case: P^_alpha = (lambda I + K_aa)^-1 P_{alpha alpha~} */
+    if (a != 1) {
+      int32_t s = nd->s;
+      nd->Phat = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (s > 0 ? s : 1));
+      memcpy(nd->Phat, nd->Pfull, sizeof(double) * (size_t)n * s);
+      lu_solve(nd->LU, nd->piv, n, nd->Phat, s, 0);
+    }
+    return;
+  }
+  int32_t l = 2 * a, r = 2 * a + 1;
+#pragma omp task if (n > 4096)
+  factorize_rec(o, l);
+#pragma omp task if (n > 4096)
+  factorize_rec(o, r);
+#pragma omp taskwait
+  int32_t sl = o->nd[l].s, sr = o->nd[r].s, z = sl + sr;
+  int64_t nl = nsz(o, l), nr = nsz(o, r);
+  /* V_alpha blocks K_{l~ r} and K_{r~ l} (second form of Eq. e:uv). */
+  nd->Vl = (double*)malloc(sizeof(double) * (size_t)(sl > 0 ? sl : 1) * (nr > 0 ? nr : 1));
+  nd->Vr = (double*)malloc(sizeof(double) * (size_t)(sr > 0 ? sr : 1) * (nl > 0 ? nl : 1));
+  for (int32_t i = 0; i < sl; ++i)
+    for (int64_t j = 0; j < nr; ++j) nd->Vl[i * nr + j] = kern(o, o->nd[l].skel[i], o->lo[r] + j);
+  for (int32_t i = 0; i < sr; ++i)
+    for (int64_t j = 0; j < nl; ++j) nd->Vr[i * nl + j] = kern(o, o->nd[r].skel[i], o->lo[l] + j);
+  /* Reduced system of Eq. (e:blocksmw): Z = [[I, K_{l~r} P^_r], [K_{r~l} P^_l, I]]. */
+  size_t zz = (size_t)(z > 0 ? z : 1) * (z > 0 ? z : 1);
+  nd->Z = (double*)calloc(zz, sizeof(double));
+  for (int32_t i = 0; i < z; ++i) nd->Z[(int64_t)i * z + i] = 1.0;
+  double* tmp = (double*)malloc(sizeof(double) * zz);
+  matmul(nd->Vl, o->nd[r].Phat, tmp, sl, nr, sr);
+  for (int32_t i = 0; i < sl; ++i)
+    for (int32_t j = 0; j < sr; ++j) nd->Z[(int64_t)i * z + sl + j] = tmp[(int64_t)i * sr + j];
+  matmul(nd->Vr, o->nd[l].Phat, tmp, sr, nl, sl);
+  for (int32_t i = 0; i < sr; ++i)
+    for (int32_t j = 0; j < sl; ++j) nd->Z[(int64_t)(sl + i) * z + j] = tmp[(int64_t)i * sl + j];
+  free(tmp);
+  nd->ZLU = (double*)malloc(sizeof(double) * zz);
+  memcpy(nd->ZLU, nd->Z, sizeof(double) * zz);
+  nd->Zpiv = (int64_t*)malloc(sizeof(int64_t) * (z > 0 ? z : 1));
+  double rel = lu_factor(nd->ZLU, nd->Zpiv, z);
+  if (rel < 1e-14) {
+#pragma omp atomic write
+    o->illcond = 1;
+  }
+  if (a == 1) return;
+  int32_t s = nd->s;
+  if (o->variant == 0) {
+    /* Eq. (e:invtelescope): P^_alpha = Solve(alpha, W P_c, false). */
+    double* u = w_times_pc(o, a);
+    solve_rec(o, a, u, s, 0);
+    nd->Phat = u;
+  } else {
+    /* log^2 N predecessor: P^_alpha = K~_aa^-1 P_{alpha alpha~} by a full
+     * recursive solve with the telescoped P of Eq. (e:innerid). */
+    double* u = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (s > 0 ? s : 1));
+    memcpy(u, nd->Pfull, sizeof(double) * (size_t)n * s);
+    solve_rec(o, a, u, s, 1);
+    nd->Phat = u;
+  }
+}
+
+int32_t kfo_factorize(kfo* o, double lambda, int32_t variant) {
+  if (!o->skeletonized) return KFO_EINVAL;
+  if (!(lambda >= 0.0) || (variant != 0 && variant != 1)) return KFO_EINVAL;
+  free_factor(o);
+  o->lambda = lambda;
+  o->variant = variant;
+  o->illcond = 0;
+#pragma omp parallel
+#pragma omp single
+  factorize_rec(o, 1);
+  o->factorized = 1;
+  return o->illcond ? KFO_EILLCOND : KFO_OK;
+}
+
+void kfo_Phat(const kfo* o, int32_t a, double* out) {
+  memcpy(out, o->nd[a].Phat, sizeof(double) * (size_t)nsz(o, a) * o->nd[a].s);
+}
+
+void kfo_Z(const kfo* o, int32_t a, double* out) {
+  int32_t z = o->nd[2 * a].s + o->nd[2 * a + 1].s;
+  memcpy(out, o->nd[a].Z, sizeof(double) * (size_t)z * z);
+}
+
+int32_t kfo_Phat_forms(const kfo* o, int32_t a, double* literal, double* pushed) {
+  if (!o->factorized || is_leaf(o, a) || a == 1) return KFO_EINVAL;
+  const node_t* nd = &o->nd[a];
+  int32_t s = nd->s, l = 2 * a, r = 2 * a + 1, sl = o->nd[l].s, sr = o->nd[r].s, z = sl + sr;
+  int64_t n = nsz(o, a), nl = nsz(o, l);
+  double* u = w_times_pc(o, a);
+  memcpy(literal, u, sizeof(double) * (size_t)n * s);
+  solve_rec(o, a, literal, s, 0);
+  free(u);
+  /* W Z^-1 P_c */
+  double* T = (double*)malloc(sizeof(double) * (size_t)(z > 0 ? z : 1) * (s > 0 ? s : 1));
+  for (int32_t i = 0; i < z; ++i)
+    for (int32_t j = 0; j < s; ++j) T[(int64_t)i * s + j] = nd->P[(int64_t)j * nd->c + i];
+  lu_solve(nd->ZLU, nd->Zpiv, z, T, s, 0);
+  matmul(o->nd[l].Phat, T, pushed, nl, sl, s);
+  matmul(o->nd[r].Phat, T + (int64_t)sl * s, pushed + nl * s, n - nl, sr, s);
+  free(T);
+  return KFO_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Transpose solve: K~_aa^-1 = (I - W Z^-1 V) D^-1 (Eq. e:smw), so
+ * K~_aa^-T = D^-T (I - V^T Z^-T W^T): first t = Z^-T [P^_l^T u_l ; P^_r^T u_r],
+ * u_l -= K_{r~ l}^T t_r, u_r -= K_{l~ r}^T t_l, then recurse. */
+static void tsolve_rec(const kfo* o, int32_t a, double* u) {
+  const node_t* nd = &o->nd[a];
+  int64_t n = nsz(o, a);
+  if (is_leaf(o, a)) {
+    lu_solve(nd->LU, nd->piv, n, u, 1, 1);
+    return;
+  }
+  int32_t l = 2 * a, r = 2 * a + 1, sl = o->nd[l].s, sr = o->nd[r].s, z = sl + sr;
+  int64_t nl = nsz(o, l), nr = nsz(o, r);
+  double* ul = u;
+  double* ur = u + nl;
+  if (z > 0) {
+    double* t = (double*)calloc(z, sizeof(double));
+    for (int32_t q = 0; q < sl; ++q) {
+      double acc = 0.0;
+      for (int64_t i = 0; i < nl; ++i) acc = acc + o->nd[l].Phat[i * sl + q] * ul[i];
+      t[q] = acc;
+    }
+    for (int32_t q = 0; q < sr; ++q) {
+      double acc = 0.0;
+      for (int64_t i = 0; i < nr; ++i) acc = acc + o->nd[r].Phat[i * sr + q] * ur[i];
+      t[sl + q] = acc;
+    }
+    lu_solve(nd->ZLU, nd->Zpiv, z, t, 1, 1);
+    for (int64_t j = 0; j < nl; ++j) {
+      double acc = 0.0;
+      for (int32_t q = 0; q < sr; ++q) acc = acc + nd->Vr[(int64_t)q * nl + j] * t[sl + q];
+      ul[j] = ul[j] - acc;
+    }
+    for (int64_t j = 0; j < nr; ++j) {
+      double acc = 0.0;
+      for (int32_t q = 0; q < sl; ++q) acc = acc + nd->Vl[(int64_t)q * nr + j] * t[q];
+      ur[j] = ur[j] - acc;
+    }
+    free(t);
+  }
+#pragma omp task if (n > 4096)
+  tsolve_rec(o, l, ul);
+#pragma omp task if (n > 4096)
+  tsolve_rec(o, r, ur);
+#pragma omp taskwait
+}
+
+int32_t kfo_solve(const kfo* o, const double* b, double* x, int32_t transpose) {
+  if (!o->factorized) return KFO_EINVAL;
+  int64_t N = o->N;
+  double* u = (double*)malloc(sizeof(double) * N);
+  for (int64_t i = 0; i < N; ++i) u[i] = b[o->perm[i]];
+#pragma omp parallel
+#pragma omp single
+  {
+    if (transpose) tsolve_rec(o, 1, u);
+    else solve_rec(o, 1, u, 1, 1);
+  }
+  for (int64_t i = 0; i < N; ++i) x[o->perm[i]] = u[i];
+  free(u);
+  return KFO_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hierarchical matvec with the operator the factorization inverts:
+ * K~_aa = [[K~_ll, P_{l l~} K_{l~ r}], [P_{r r~} K_{r~ l}, K~_rr]]
+ * (second form of Eq. e:uv), lambda I + K_aa at the leaves.  The skeleton
+ * blocks are evaluated on the fly, independent of the factorization.  With
+ * deriv = 1 every kernel entry is replaced by dK/dh and lambda by 0 (the
+ * derivative of the operator with the skeletons and P held fixed). */
+static void matvec_rec(const kfo* o, int32_t a, const double* x, double* y, int deriv) {
+  int64_t n = nsz(o, a), lo = o->lo[a];
+  if (is_leaf(o, a)) {
+    for (int64_t i = 0; i < n; ++i) {
+      double acc = 0.0;
+      for (int64_t j = 0; j < n; ++j)
+        acc = acc + (deriv ? dkern_dh(o, lo + i, lo + j) : kern(o, lo + i, lo + j)) * x[j];
+      y[i] = (deriv ? 0.0 : o->lambda * x[i]) + acc;
+    }
+    return;
+  }
+  int32_t l = 2 * a, r = 2 * a + 1;
+  int64_t nl = nsz(o, l);
+#pragma omp task if (n > 4096)
+  matvec_rec(o, l, x, y, deriv);
+#pragma omp task if (n > 4096)
+  matvec_rec(o, r, x + nl, y + nl, deriv);
+#pragma omp taskwait
+  for (int side = 0; side < 2; ++side) {
+    int32_t c = side == 0 ? l : r, sib = side == 0 ? r : l;
+    const node_t* cn = &o->nd[c];
+    int64_t nc = nsz(o, c), nsib = nsz(o, sib);
+    const double* xs = x + (o->lo[sib] - lo);
+    double* yc = y + (o->lo[c] - lo);
+    double* zt = (double*)calloc(cn->s > 0 ? cn->s : 1, sizeof(double));
+    for (int32_t q = 0; q < cn->s; ++q) {   /* K_{c~ sib} x_sib */
+      double acc = 0.0;
+      for (int64_t j = 0; j < nsib; ++j)
+        acc = acc + (deriv ? dkern_dh(o, cn->skel[q], o->lo[sib] + j) : kern(o, cn->skel[q], o->lo[sib] + j)) * xs[j];
+      zt[q] = acc;
+    }
+    for (int64_t i = 0; i < nc; ++i) {      /* P_{c c~} (...) */
+      double acc = 0.0;
+      for (int32_t q = 0; q < cn->s; ++q) acc = acc + cn->Pfull[i * cn->s + q] * zt[q];
+      yc[i] = yc[i] + acc;
+    }
+    free(zt);
+  }
+}
+
+int32_t kfo_matvec(const kfo* o, const double* x, double* y, int32_t deriv) {
+  if (!o->skeletonized) return KFO_EINVAL;
+  int64_t N = o->N;
+  double* u = (double*)malloc(sizeof(double) * N);
+  double* v = (double*)malloc(sizeof(double) * N);
+  for (int64_t i = 0; i < N; ++i) u[i] = x[o->perm[i]];
+#pragma omp parallel
+#pragma omp single
+  matvec_rec(o, 1, u, v, deriv);
+  for (int64_t i = 0; i < N; ++i) y[o->perm[i]] = v[i];
+  free(u); free(v);
+  return KFO_OK;
+}
+
+/* Gradient through x = A^-1 b with A = lambda I + K~(h):
+ * a = A^-T g; dL/db = a; dL/dlambda = -a^T x; dL/dh = -a^T (dK~/dh) x. */
+int32_t kfo_grad(const kfo* o, const double* x, const double* g, double* dLdb, double* dLdlambda, double* dLdh) {
+  if (!o->factorized) return KFO_EINVAL;
+  int64_t N = o->N;
+  kfo_solve(o, g, dLdb, 1);
+  double* dx = (double*)malloc(sizeof(double) * N);
+  kfo_matvec(o, x, dx, 1);
+  double sl = 0.0, sh = 0.0;
+  for (int64_t i = 0; i < N; ++i) { sl = sl + dLdb[i] * x[i]; sh = sh + dLdb[i] * dx[i]; }
+  *dLdlambda = -sl;
+  *dLdh = -sh;
+  free(dx);
+  return KFO_OK;
+}
