@@ -1,0 +1,424 @@
+#!/usr/bin/env python3
+"""Headline benchmark: factorization seconds and solve RHS/s of lambda I + K~
+at N = 2^20 (the scale workload: d = 28 points on a 6-D linear manifold, h = 1,
+lambda = 1, m = 1024, s_max = 256, tau = 1e-4, one right-hand side), mixed
+precision against the plain FP64 GPU path.
+
+One step = the whole hot path on the mixed path: ball tree, skeletonization
+(sampling, FP64 ID), factorization (leaf Cholesky, V blocks, reduced systems,
+telescoping) and the solve of the right-hand side with its residual check.
+``value`` is the factorization time per step (tree + skeletons + Algorithm 2)
+in seconds, max over ranks; ``solve_rhs_per_s`` and the FP64 comparison are
+reported beside it.  Inputs (points, right-hand side) are resident in HBM when
+the timed region starts; the factors are several GB, far larger than L2.
+
+``--impl reference`` times the CPU oracle on a bounded sample of the same
+workload instead (see ``cpu_baseline``).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "factorize sec & solve RHS/s at N=1M, rel err≤1e-5; mixed vs FP64 GPU path"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_PEAK_TFLOPS = 1.25          # recipe's nominal FP64 rate (152 SMs, 2.07 GHz)
+ORACLE_SAMPLE_N = 8192           # points per oracle sample step
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "bf16_tflops": float(p["bf16_tflops"]), "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback"}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self):
+        self.rows, self.proc = [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self, gpu_index=0):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [r for r in self.rows if len(r) >= 9 and r[0] == str(gpu_index)]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- algorithmic work
+def qr_flops(ns, c, s):
+    """FP64 flops of the truncated pivoted Householder QR + P of one node:
+    initial column norms, per step the reflector application (dot + update)
+    and the norms of the trailing columns, then T = R11^-1 R12."""
+    f = 2.0 * ns * c
+    for k in range(s):
+        rows, cols = ns - k, c - k - 1
+        f += 4.0 * rows * cols + 2.0 * (rows - 1) * cols
+    f += float(s) * s * (c - s)
+    return f
+
+
+def level_qr_flops(sizes, ranks, N, D, n_samp, s_max, lo, hi):
+    """QR flops per tree level (dict level -> flops), from realized ranks."""
+    out = {}
+    for l in range(1, D + 1):
+        tot = 0.0
+        for a in range(1 << l, 1 << (l + 1)):
+            n = hi[a] - lo[a]
+            ns = min(n_samp, N - n)
+            c = n if l == D else ranks[2 * a] + ranks[2 * a + 1]
+            tot += qr_flops(ns, c, ranks[a])
+        out[l] = tot
+    return out
+
+
+def tree_ranges(N, m):
+    D = 0
+    while (m << D) < N:
+        D += 1
+    lo = [0] * (2 << D)
+    hi = [0] * (2 << D)
+    lo[1], hi[1] = 0, N
+    for a in range(1, 1 << D):
+        n = hi[a] - lo[a]
+        mid = lo[a] + n // 2
+        lo[2 * a], hi[2 * a], lo[2 * a + 1], hi[2 * a + 1] = lo[a], mid, mid, hi[a]
+    return D, lo, hi
+
+
+def solve_bytes(N, D, ranks, lo, hi, tsize):
+    """Algorithmic bytes of one solve sweep: the lower triangles of the leaf
+    factors (read by the forward and the backward substitution), the V rows
+    K(x_i, sib~) and the P^ rows of every level, and the FP64 LU of every Z."""
+    b = 0.0
+    for a in range(1 << D, 2 << D):
+        n = hi[a] - lo[a]
+        b += tsize * n * (n + 1)              # two triangular passes over n(n+1)/2 entries
+    for l in range(1, D + 1):
+        for a in range(1 << l, 1 << (l + 1)):
+            n = hi[a] - lo[a]
+            b += tsize * n * (ranks[a ^ 1] + ranks[a])
+    for a in range(1, 1 << D):
+        z = ranks[2 * a] + ranks[2 * a + 1]
+        b += 8.0 * z * z
+    return b
+
+
+# ---------------------------------------------------------------- oracle (CPU) leg
+def run_oracle_sample(n_points):
+    import oracle
+    from paper_1701_02324_gb300 import inputs
+    oracle.build()
+    X = inputs.linear_manifold(n_points, 28, 6, 0.01, 1701003)
+    b = np.random.default_rng(1701003 + 17).standard_normal(n_points)
+    t0 = time.perf_counter()
+    o = oracle.Oracle(X, 1024)
+    o.skeletonize(1.0, 1e-4, 256)
+    o.factorize(1.0)
+    tf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.solve(b)
+    ts = time.perf_counter() - t0
+    return tf, ts, o.D
+
+
+def oracle_scale(n_sample, N=1 << 20, m=1024):
+    """Work model of the method (Sec. III: T_f = O(s^2 N log N)): per level
+    the work is proportional to N, so time scales with N * (levels + 1)."""
+    Ds, _, _ = tree_ranges(n_sample, m)
+    Df, _, _ = tree_ranges(N, m)
+    return (N * (Df + 1)) / (n_sample * (Ds + 1))
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def reference_main(args, rank, world):
+    if rank != 0:
+        return
+    scale = oracle_scale(ORACLE_SAMPLE_N)
+    for _ in range(args.warmup):
+        run_oracle_sample(ORACLE_SAMPLE_N)
+    tfs, tss = [], []
+    for _ in range(args.steps):
+        tf, ts, _ = run_oracle_sample(ORACLE_SAMPLE_N)
+        tfs.append(tf)
+        tss.append(ts)
+    tf = statistics.mean(tfs) * scale
+    ts = statistics.mean(tss) * scale
+    cores = int(os.environ.get("OMP_NUM_THREADS", cpu_cores()))
+    sample = (f"oracle tree+skeletonize+factorize of N={ORACLE_SAMPLE_N} points of the same recipe "
+              f"(h=1, lambda=1, m=1024, s_max=256, tau=1e-4), scaled by N*(levels+1) x{scale:.1f} to N=2^20")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(tf, 4), "unit": "s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(tfs), 2),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "scale_N1048576_d28", "N": 1 << 20, "d": 28, "h": 1.0, "lambda": 1.0, "m": 1024,
+                   "s_max": 256, "tau": 1e-4, "nrhs": 1, "precision": "fp64-cpu-oracle"},
+        "solve_rhs_per_s": round(1.0 / ts, 4),
+        "cpu_baseline": {"value": round(tf, 4), "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(tf, 4), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU leg
+def gpu_main(args, rank, world):
+    import torch
+
+    import paper_1701_02324_gb300 as kf
+    from paper_1701_02324_gb300 import _abi, inputs
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    lib = _abi.load()
+    p = inputs.scale()
+    X_host = np.ascontiguousarray(p.X)
+    b_host = np.ascontiguousarray(p.B[:, 0])
+    X = torch.from_numpy(X_host).to(dev)
+    b = torch.from_numpy(b_host).to(dev)
+    torch.cuda.synchronize()
+    dist = world > 1
+
+    def barrier():
+        if dist:
+            torch.distributed.barrier()
+
+    def step(prec, want_x=False):
+        tree = kf.Tree(X, p.m)
+        F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=prec, refine_max_iter=-1, sync_errors=False)
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record()
+        x = F.solve(b)
+        return tree, F, ev, x
+
+    # warm-up (also loads and builds everything)
+    for _ in range(args.warmup):
+        tree, F, _, _ = step(kf.KF_PREC_MIXED)
+        del F, tree
+    torch.cuda.synchronize()
+
+    # ---- timed region: mixed path -------------------------------------------
+    clocks = ClockSampler()
+    clocks.start()
+    lib.kf_profile_enable(1)
+    nph = len(_abi.PHASES)
+    ms_ph = np.zeros(nph)
+    ln_ph = np.zeros(nph, dtype=np.int64)
+    lib.kf_profile_read(ms_ph.ctypes.data_as(ctypes_p()), ln_ph.ctypes.data_as(ctypes_p()), nph)
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = lib.kf_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    fact_ms, solve_ms = [], []
+    t_start.record()
+    x_mixed = None
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tree, F, e1, x = step(kf.KF_PREC_MIXED)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e2.record()
+        torch.cuda.synchronize()
+        fact_ms.append(e0.elapsed_time(e1))
+        solve_ms.append(e1.elapsed_time(e2))
+        x_mixed = x
+        ranks = F.ranks()
+        del F, tree
+    t_end.record()
+    torch.cuda.synchronize()
+    barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    launches = lib.kf_launch_count() - launches0
+    lib.kf_profile_read(ms_ph.ctypes.data_as(ctypes_p()), ln_ph.ctypes.data_as(ctypes_p()), nph)
+    lib.kf_profile_enable(0)
+    clk = clocks.stop(dev.index)
+
+    # max over ranks
+    fact_s = statistics.mean(fact_ms) / 1e3
+    solve_s = statistics.mean(solve_ms) / 1e3
+    ms_per_step = total_ms / args.steps
+    if dist:
+        t = torch.tensor([fact_s, solve_s, ms_per_step], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        fact_s, solve_s, ms_per_step = t.tolist()
+
+    # ---- FP64 comparison leg (same workload, same skeletons) ---------------------
+    fp64 = None
+    if not args.no_fp64:
+        tree, F, _, _ = step(kf.KF_PREC_FP64)  # warm
+        del F, tree
+        ff, fs = [], []
+        x64 = None
+        for _ in range(max(1, args.fp64_steps)):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            tree, F, e1, x64 = step(kf.KF_PREC_FP64)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e2.record()
+            torch.cuda.synchronize()
+            ff.append(e0.elapsed_time(e1))
+            fs.append(e1.elapsed_time(e2))
+            _, info = F.solve(b, info=True)
+            del F, tree
+        rel = float(torch.linalg.norm(x_mixed - x64) / torch.linalg.norm(x64))
+        fp64 = {"factorize_s": round(statistics.mean(ff) / 1e3, 4),
+                "solve_rhs_per_s": round(1e3 / statistics.mean(fs), 2),
+                "eps_r": info["eps_r"], "mixed_rel_err_vs_fp64": rel}
+
+    # ---- end to end through the C ABI with host buffers ----------------------------
+    e2e = None
+    if not args.no_e2e:
+        xh = np.empty_like(b_host)
+        lib_t = []
+        for _ in range(max(1, args.e2e_steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tree = kf.Tree(torch.from_numpy(X_host), p.m)                  # host X: H2D inside
+            F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=kf.KF_PREC_MIXED, refine_max_iter=-1,
+                          sync_errors=False)
+            xt = F.solve(torch.from_numpy(b_host))                         # host b -> host x
+            xh[:] = xt.numpy()
+            lib_t.append(time.perf_counter() - t0)
+            del F, tree
+        e2e = {"value": round(statistics.mean(lib_t), 4), "unit": "s",
+               "h2d_bytes_per_step": int(X_host.nbytes + b_host.nbytes), "d2h_bytes_per_step": int(xh.nbytes),
+               "note": "wall time of tree + factorize + solve with host X, b and x (copies inside)"}
+
+    # ---- roofline of the dominant kernel ----------------------------------------
+    peaks = load_peaks()
+    D, lo, hi = tree_ranges(p.N, p.m)
+    phase_ms = {n: float(ms_ph[i]) for i, n in enumerate(_abi.PHASES)}
+    phase_launches = {n: int(ln_ph[i]) for i, n in enumerate(_abi.PHASES)}
+    dominant = max(phase_ms, key=phase_ms.get)
+    roof = None
+    if dominant == "qr" and phase_launches["qr"] > 0:
+        flops = sum(level_qr_flops(None, ranks, p.N, D, 2 * p.s_max, p.s_max, lo, hi).values()) * args.steps
+        avg_ms = phase_ms["qr"] / phase_launches["qr"]
+        per_launch = flops / phase_launches["qr"]
+        achieved = per_launch / (avg_ms * 1e-3) / 1e12
+        roof = {"kernel": "k_pivoted_qr (FP64 ID)", "bound": "alu", "achieved": round(achieved, 4),
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                "traffic": None, "peak_src": "recipe nominal FP64 rate (1.25 TFLOP/s; 1.20 measured by an FMA loop)",
+                "work_per_launch": per_launch, "avg_launch_ms": avg_ms}
+    else:
+        sb = solve_bytes(p.N, D, ranks, lo, hi, 4) * args.steps
+        sweep_ms = sum(phase_ms[k] for k in ("solve_leaf", "solve_colsum", "solve_zsolve", "solve_rowupd"))
+        achieved = sb / (sweep_ms * 1e-3) / 1e9 if sweep_ms > 0 else 0.0
+        roof = {"kernel": f"dominant phase {dominant}", "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                "traffic": None}
+    roof["phase_ms_per_step"] = {k: round(v / args.steps, 3) for k, v in phase_ms.items() if v > 0}
+
+    # ---- CPU baseline (oracle, bounded sample) ------------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        tf_o, ts_o, _ = run_oracle_sample(ORACLE_SAMPLE_N)
+        sc = oracle_scale(ORACLE_SAMPLE_N)
+        cpu = {"value": round(tf_o * sc, 3), "unit": "s", "cores": int(os.environ.get("OMP_NUM_THREADS", cpu_cores())),
+               "kind": "oracle",
+               "sample": f"oracle tree+skeletonize+factorize of N={ORACLE_SAMPLE_N} points of the same recipe, "
+                         f"{tf_o:.2f} s, scaled by N*(levels+1) x{sc:.1f} to N=2^20; solve {ts_o * sc:.3f} s/RHS scaled",
+               "solve_rhs_per_s": round(1.0 / (ts_o * sc), 4)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(fact_s, 4), "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 2), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "scale_N1048576_d28", "N": p.N, "d": p.d, "h": p.h, "lambda": p.lam, "m": p.m,
+                       "s_max": p.s_max, "tau": p.tau, "n_samp": 2 * p.s_max, "nrhs": 1,
+                       "precision": "mixed (FP32 factors, FP64 ID/Z/T)", "parallelism": f"replicas x{world}",
+                       "l2": "inputs and factors larger than L2 (no flush needed)"},
+            "solve_rhs_per_s": round(1.0 / solve_s, 2),
+            "fp64_path": fp64,
+            "ranks": {"mean": float(np.mean(ranks[2:])), "max": int(np.max(ranks))},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "peaks_src": peaks["src"],
+        }
+        print(json.dumps(line), flush=True)
+
+
+def ctypes_p():
+    import ctypes
+    return ctypes.c_void_p
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="kf", choices=["kf", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        reference_main(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    gpu_main(args, rank, world)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

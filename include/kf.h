@@ -1,0 +1,196 @@
+/*
+ * kf.h -- C ABI of the GB300 hierarchical kernel-matrix solver.
+ *
+ * Method: Yu, March, Biros, "An N log N Parallel Fast Direct Solver for Kernel
+ * Matrices" (arXiv 1701.02324).  Given N points x_i in R^d, the Gaussian kernel
+ * K_ij = exp(-||x_i - x_j||^2 / (2 h^2)) (Eq. e:gaussian) and lambda >= 0, the
+ * library builds the ball tree and interpolative-decomposition skeletons of
+ * Sec. II-A (Algorithm 1), factorizes the hierarchical approximation
+ * lambda I + K~ level by level with the Sherman-Morrison-Woodbury formula
+ * (Eqs. e:smw, e:hodlr, e:blocksmw, e:invtelescope; Algorithm 2), and applies
+ * its inverse (Algorithm 3), its transpose, the operator itself and the
+ * gradient of a loss through the solve.
+ *
+ * Conventions shared by every entry point:
+ *  - Status: every function returns kf_status; nothing aborts.  A message for
+ *    the last failure of a context is available from kf_last_error().
+ *  - Pointers: "device or host" arguments may point to device memory or to
+ *    ordinary/pinned host memory; the library looks the pointer up with
+ *    cudaPointerGetAttributes and stages host data through device buffers.
+ *    The caller keeps ownership of everything it passes in.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Work is enqueued on that stream.  Calls whose outputs
+ *    land in host memory synchronize the stream before returning.
+ *  - Point order: X rows, right-hand sides and solutions are in the caller's
+ *    ORIGINAL point order; the tree permutation is internal.
+ *  - Matrices of right-hand sides are column-major: column j of B starts at
+ *    B + j*ld (elements), ld >= N.
+ *  - Sizes: N < 2^31, 1 <= d <= 1024, 1 <= m, 1 <= s_max <= 512.
+ *  - Handles own the device memory they allocate, drawn through the
+ *    allocator given to kf_create (cudaMalloc/cudaFree when NULL).  A factor
+ *    keeps a pointer to its tree: free factors before their tree.  *_free(NULL)
+ *    is a no-op.
+ *  - Device-side errors (ill-conditioned pivots, bounded waits that ran out)
+ *    are written to a device status word and returned by the next call that
+ *    synchronizes (kf_factor_status, kf_solve with info, *_free) or at once
+ *    when kf_opts.sync_errors is set.
+ */
+#ifndef KF_H
+#define KF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KF_OK = 0,
+  KF_EINVAL = 1,        /* bad argument (NaN/Inf input, h <= 0, lambda < 0, sizes) */
+  KF_ENOMEM = 2,        /* the allocator returned NULL */
+  KF_ECUDA = 3,         /* a CUDA runtime call failed */
+  KF_EILLCOND = 4,      /* a leaf block or reduced system Z is numerically singular
+                           (Sec. III "Stability": detectable instability) */
+  KF_ENOTCONV = 5,      /* refinement did not reach the requested residual */
+  KF_ETIMEOUT = 6,      /* a bounded device-side wait ran out */
+  KF_EUNSUPPORTED = 7   /* valid request this build does not support */
+} kf_status;
+
+typedef enum { KF_F32 = 0, KF_F64 = 1 } kf_dtype;
+
+typedef enum {
+  KF_PREC_FP64 = 0,     /* every step in FP64 */
+  KF_PREC_MIXED = 1     /* FP32 factors, tensor-core contractions, FP64 pivoted QR,
+                           FP64 reduced-system LU and FP64 refinement residual */
+} kf_precision;
+
+typedef enum {
+  KF_V_STORED = 0,      /* keep the skeleton rows K_{b~ a} of every level for the solve */
+  KF_V_RECOMPUTE = 1    /* evaluate them on the fly in the solve (matrix-free, Sec. II-D) */
+} kf_vstorage;
+
+/* Device memory allocator.  alloc returns a device pointer of at least `bytes`
+ * bytes usable on `stream` (or NULL on failure); free releases it. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* user);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+  void* user;
+} kf_alloc;
+
+/* Options of kf_factorize.  Zero-initialise, then set fields; n_samp = 0 means
+ * 2*s_max, seed = 0 means 0x1701. */
+typedef struct {
+  int32_t precision;      /* kf_precision */
+  int32_t n_samp;         /* |S'|: sampled rows per ID (Sec. II-A), capped by N - |node| */
+  uint64_t seed;          /* sampler seed */
+  int32_t v_storage;      /* kf_vstorage */
+  int32_t sync_errors;    /* nonzero: synchronize and report device status at once */
+  double refine_tol;      /* mixed path: target relative residual (0 = 1e-10) */
+  int32_t refine_max_iter;/* mixed path: max refinement steps (0 = 8; -1 = none) */
+  int32_t reserved[8];
+} kf_opts;
+
+/* Filled by kf_solve when non-NULL (synchronizes the stream). */
+typedef struct {
+  double eps_r;           /* ||b - (lambda I + K~) x|| / ||b|| (Eq. e:errors), max over RHS;
+                             -1 when not computed (FP64 path without refinement) */
+  int32_t iters;          /* refinement steps taken */
+  int32_t status;         /* device status at the end of the solve */
+} kf_solve_info;
+
+typedef struct kf_ctx kf_ctx;
+typedef struct kf_tree kf_tree;
+typedef struct kf_factor kf_factor;
+
+/* Context: allocator and error message.  alloc may be NULL. */
+kf_status kf_create(kf_ctx** out, const kf_alloc* alloc);
+kf_status kf_destroy(kf_ctx* ctx);
+const char* kf_status_string(kf_status s);
+const char* kf_last_error(const kf_ctx* ctx);
+
+/* Ball tree of Sec. II-A "Partitioning the matrix".  X: N x d row-major,
+ * original order, device or host, dtype KF_F32 or KF_F64.  Depth
+ * D = ceil(log2(N/m)); each node splits into floor(n/2) and ceil(n/2) points by
+ * the order of (projection on the farthest-pair direction, original index).
+ * The tree copies and permutes X; the caller keeps X.  Errors: KF_EINVAL for
+ * non-finite coordinates or bad sizes. */
+kf_status kf_tree_build(kf_ctx* ctx, const void* X, int32_t dtype, int64_t N, int32_t d, int32_t m,
+                        void* stream, kf_tree** out);
+/* perm[i] = original index of the point at tree position i (device or host, N int64). */
+kf_status kf_tree_perm(const kf_tree* t, int64_t* perm, void* stream);
+/* Sizes of the tree; any output pointer may be NULL. */
+kf_status kf_tree_info(const kf_tree* t, int64_t* N, int32_t* d, int32_t* m, int32_t* depth);
+kf_status kf_tree_free(kf_tree* t);
+
+/* Skeletonize (Algorithm 1, ID of Eq. e:id with sampled rows S') and factorize
+ * (Algorithm 2) lambda I + K~.  h > 0, lambda >= 0, tau >= 0 (rank rule
+ * sigma_{s+1}/sigma_1 < tau estimated by |R_kk|/|R_00| of a pivoted QR),
+ * 1 <= s_max <= 512.  opts may be NULL (FP64, |S'| = 2 s_max, seed 0x1701,
+ * stored V).  Errors: KF_EINVAL, KF_ENOMEM, KF_EILLCOND (also later, see the
+ * device status convention above). */
+kf_status kf_factorize(kf_tree* t, double h, double lambda, double tau, int32_t s_max,
+                       const kf_opts* opts, void* stream, kf_factor** out);
+/* Device status word of the factorization (synchronizes the stream). */
+kf_status kf_factor_status(kf_factor* f, void* stream);
+kf_status kf_factor_free(kf_factor* f);
+
+/* X = (lambda I + K~)^-1 B (transpose = 0, Algorithm 3) or
+ * X = (lambda I + K~)^-T B (transpose = 1).  B, X: N x nrhs column-major with
+ * leading dimension ld, device or host, dtype KF_F32 or KF_F64; B and X may
+ * alias.  On the mixed path the solve is refined against the hierarchical
+ * operator in FP64 until the relative residual is below opts.refine_tol. */
+kf_status kf_solve(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t ld, int32_t dtype,
+                   int32_t transpose, void* stream, kf_solve_info* info);
+/* Y = (lambda I + K~) X with the operator the factorization inverts
+ * (second form of Eq. e:uv): leaf blocks lambda I + K_aa, off-diagonal blocks
+ * P_{l l~} K_{l~ r} and P_{r r~} K_{r~ l}.  Layout as kf_solve. */
+kf_status kf_matvec(kf_factor* f, const void* X, void* Y, int64_t nrhs, int64_t ld, int32_t dtype, void* stream);
+/* Gradient of a loss L through x = (lambda I + K~)^-1 b given x and dL/dx:
+ * a = (lambda I + K~)^-T dL/dx; dL/db = a; dL/dlambda = -sum a.x;
+ * dL/dh = -sum a.(dK~/dh) x with skeletons and P held fixed.  x, dLdx, dLdb:
+ * N x nrhs (ld), device or host, FP64.  dLdlambda, dLdh: host, one value
+ * summed over the RHS columns. */
+kf_status kf_grad(kf_factor* f, const void* x, const void* dLdx, void* dLdb, double* dLdlambda,
+                  double* dLdh, int64_t nrhs, int64_t ld, void* stream);
+
+/* ---- inspection (host outputs; they synchronize the stream) -------------- */
+/* Heap-numbered nodes: root 1, children 2a and 2a+1, level l holds nodes
+ * 2^l .. 2^(l+1)-1.  Ranks of nodes 0..2^(D+1)-1 (entry 0 and the root are 0). */
+kf_status kf_factor_ranks(const kf_factor* f, int32_t* ranks, void* stream);
+/* Skeleton of a non-root node: s tree positions in pivot order. */
+kf_status kf_factor_skeleton(const kf_factor* f, int32_t node, int64_t* skel, void* stream);
+/* Interpolation matrix of a non-root node's ID, s x c row-major FP64, with
+ * c = |node| (leaf) or s_l + s_r (internal). */
+kf_status kf_factor_P(const kf_factor* f, int32_t node, double* P, void* stream);
+/* P^_node = K~_node^-1 P_{node node~}, |node| x s row-major FP64. */
+kf_status kf_factor_Phat(const kf_factor* f, int32_t node, double* Phat, void* stream);
+
+/* Test hook: factorize with skeletons and interpolation matrices supplied by
+ * the caller instead of computing them, so that the factorization can be
+ * compared with a reference that used the same IDs.  ranks: host int32
+ * [2^(D+1)]; skel: host int64, node a's list at skel + a*s_max; P: host FP64,
+ * node a's s x c matrix at P + a*s_max*cmax with cmax = max(max leaf size,
+ * 2*s_max).  Otherwise as kf_factorize. */
+kf_status kf_factorize_with_ids(kf_tree* t, double h, double lambda, int32_t s_max, const int32_t* ranks,
+                                const int64_t* skel, const double* P, const kf_opts* opts, void* stream,
+                                kf_factor** out);
+
+/* ---- diagnostics ------------------------------------------------------------- */
+/* Number of kernel launches this process has made through the library. */
+int64_t kf_launch_count(void);
+/* Per-phase timing: while on, every launch is bracketed by CUDA events on its
+ * stream (adds two event records per launch).  Process-wide. */
+kf_status kf_profile_enable(int32_t on);
+/* Totals since the last read: ms[i] and launches[i] for phase i, nphase >=
+ * KF_PHASE_COUNT.  Synchronizes the recorded events.  Phases, in order: tree,
+ * sample, eval_A, qr, leaf_assemble, leaf_cholesky, leaf_phat, eval_V, zoff,
+ * z_lu, z_solve_pc, telescope, solve_leaf, solve_colsum, solve_zsolve,
+ * solve_rowupd, matvec_leaf, matvec_push, misc. */
+#define KF_PHASE_COUNT 19
+kf_status kf_profile_read(double* ms, int64_t* launches, int32_t nphase);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KF_H */

@@ -1,1 +1,340 @@
-"""GB300-native hierarchical factorization and solve of lambda*I + K."""
+"""GB300-native hierarchical factorization and solve of lambda*I + K.
+
+Thin Python binding of the C ABI in ``include/kf.h`` (Yu, March, Biros,
+"An N log N Parallel Fast Direct Solver for Kernel Matrices", arXiv
+1701.02324).  Every step of the method runs in the CUDA library
+``libkf.so``; this module only passes pointers, sizes and the current CUDA
+stream, and routes device allocations of the library through PyTorch's
+caching allocator.  There is no CPU fallback: without the library or a GPU
+the calls raise.
+
+Same names as the C ABI: ``tree_build``, ``factorize``, ``solve``,
+``matvec``, ``grad``, ``factor_free``/``tree_free``; ``Tree`` and ``Factor``
+wrap the handles, ``KernelSolve`` is the autograd function of
+x = (lambda I + K~(h))^-1 b.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _abi
+from ._abi import (KF_F32, KF_F64, KF_PREC_FP64, KF_PREC_MIXED, KF_V_RECOMPUTE, KF_V_STORED, KFError,
+                   kf_opts, kf_solve_info)
+
+__all__ = [
+    "build", "Context", "Tree", "Factor", "tree_build", "factorize", "factorize_with_ids", "solve", "matvec",
+    "grad", "tree_free", "factor_free", "KernelSolve", "KF_PREC_FP64", "KF_PREC_MIXED", "KF_V_STORED",
+    "KF_V_RECOMPUTE", "KFError",
+]
+
+
+def build(force: bool = False) -> str:
+    """Compile libkf.so for sm_103a (in-tree) and return its path."""
+    from . import _build
+    return _build.build(force=force)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr():
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---- allocator: library allocations drawn from PyTorch's caching allocator --------
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+@_ALLOC_FN
+def _torch_alloc(nbytes, stream, user):
+    torch = _torch()
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), int(stream or 0))
+    except RuntimeError:
+        return None
+
+
+@_FREE_FN
+def _torch_free(ptr, nbytes, stream, user):
+    if ptr and _DELETE[0] is not None:
+        try:
+            _DELETE[0](int(ptr))
+        except Exception:  # interpreter shutdown: the process is releasing everything anyway
+            pass
+
+
+_DELETE = [None]
+
+
+class Context:
+    """A kf_ctx: error messages and the device allocator (torch's by default)."""
+
+    def __init__(self, use_torch_allocator: bool = True):
+        self.lib = _abi.load()
+        self._alloc = None
+        if use_torch_allocator:
+            _DELETE[0] = _torch().cuda.caching_allocator_delete
+            self._alloc = _abi.kf_alloc(ctypes.cast(_torch_alloc, ctypes.c_void_p).value,
+                                        ctypes.cast(_torch_free, ctypes.c_void_p).value, None)
+        h = ctypes.c_void_p()
+        _abi.check(self.lib.kf_create(ctypes.byref(h), ctypes.byref(self._alloc) if self._alloc else None))
+        self.h = h
+
+    def check(self, status, allow=()):
+        return _abi.check(status, self.h, allow)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.lib.kf_destroy(self.h)
+            self.h = None
+
+
+_default_ctx = None
+
+
+def default_context() -> Context:
+    global _default_ctx
+    if _default_ctx is None:
+        _default_ctx = Context()
+    return _default_ctx
+
+
+def _dtype_code(t):
+    torch = _torch()
+    if t.dtype == torch.float64:
+        return KF_F64
+    if t.dtype == torch.float32:
+        return KF_F32
+    raise TypeError("kf: tensors must be float32 or float64")
+
+
+class Tree:
+    """Ball tree of Sec. II-A over X (N x d, device or host tensor)."""
+
+    def __init__(self, X, m: int, ctx: Context | None = None):
+        torch = _torch()
+        self.ctx = ctx or default_context()
+        X = X.contiguous()
+        self.N, self.d = X.shape
+        self.m = int(m)
+        h = ctypes.c_void_p()
+        self.ctx.check(self.ctx.lib.kf_tree_build(self.ctx.h, _ptr(X), _dtype_code(X), self.N, self.d, self.m,
+                                                  _stream_ptr(), ctypes.byref(h)))
+        self.h = h
+        D = ctypes.c_int32()
+        self.ctx.lib.kf_tree_info(self.h, None, None, None, ctypes.byref(D))
+        self.D = D.value
+        self._X = X if X.is_cuda else None
+        del torch
+
+    @property
+    def nnodes(self) -> int:
+        return (1 << (self.D + 1)) - 1
+
+    def perm(self):
+        torch = _torch()
+        out = torch.empty(self.N, dtype=torch.int64, device="cuda")
+        self.ctx.check(self.ctx.lib.kf_tree_perm(self.h, _ptr(out), _stream_ptr()))
+        return out
+
+    def free(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.kf_tree_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.free()
+
+
+def _opts(precision=KF_PREC_FP64, n_samp=0, seed=0, v_storage=KF_V_STORED, sync_errors=0, refine_tol=0.0,
+          refine_max_iter=0):
+    o = kf_opts()
+    o.precision, o.n_samp, o.seed, o.v_storage = int(precision), int(n_samp), int(seed), int(v_storage)
+    o.sync_errors, o.refine_tol, o.refine_max_iter = int(sync_errors), float(refine_tol), int(refine_max_iter)
+    return o
+
+
+class Factor:
+    """Skeletonization (Algorithm 1) + factorization (Algorithm 2) of lambda I + K~."""
+
+    def __init__(self, tree: Tree, h: float, lam: float, tau: float, s_max: int, precision=KF_PREC_FP64,
+                 n_samp: int = 0, seed: int = 0, v_storage=KF_V_STORED, refine_tol: float = 0.0,
+                 refine_max_iter: int = 0, sync_errors: bool = True, _ids=None):
+        self.tree, self.ctx = tree, tree.ctx
+        self.h_, self.lam, self.tau, self.s_max, self.precision = float(h), float(lam), float(tau), int(s_max), precision
+        o = _opts(precision, n_samp, seed, v_storage, int(sync_errors), refine_tol, refine_max_iter)
+        h_out = ctypes.c_void_p()
+        if _ids is None:
+            st = self.ctx.lib.kf_factorize(tree.h, self.h_, self.lam, self.tau, self.s_max, ctypes.byref(o),
+                                           _stream_ptr(), ctypes.byref(h_out))
+        else:
+            ranks, skel, P = _ids
+            st = self.ctx.lib.kf_factorize_with_ids(tree.h, self.h_, self.lam, self.s_max,
+                                                    ranks.ctypes.data_as(ctypes.c_void_p),
+                                                    skel.ctypes.data_as(ctypes.c_void_p),
+                                                    P.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o),
+                                                    _stream_ptr(), ctypes.byref(h_out))
+        self.status = self.ctx.check(st, allow=(_abi.KF_EILLCOND,))
+        self.h = h_out
+
+    # -- operations ---------------------------------------------------------------
+    def solve(self, B, transpose: bool = False, info: bool = False):
+        """X = (lambda I + K~)^-1 B (or ^-T); B: N or N x k tensor (device or host)."""
+        torch = _torch()
+        vec = B.dim() == 1
+        Bm = B.reshape(B.shape[0], -1)
+        Bc = Bm.t().contiguous()            # column-major N x k
+        X = torch.empty_like(Bc)
+        inf = kf_solve_info() if info else None
+        self.ctx.check(self.ctx.lib.kf_solve(self.h, _ptr(Bc), _ptr(X), Bm.shape[1], self.tree.N, _dtype_code(Bc),
+                                             int(bool(transpose)), _stream_ptr(),
+                                             ctypes.byref(inf) if inf is not None else None))
+        out = X.t()
+        out = out.reshape(B.shape) if vec else out
+        if info:
+            return out, {"eps_r": inf.eps_r, "iters": inf.iters, "status": inf.status}
+        return out
+
+    def matvec(self, Xv):
+        torch = _torch()
+        vec = Xv.dim() == 1
+        Xm = Xv.reshape(Xv.shape[0], -1)
+        Xc = Xm.t().contiguous()
+        Y = torch.empty_like(Xc)
+        self.ctx.check(self.ctx.lib.kf_matvec(self.h, _ptr(Xc), _ptr(Y), Xm.shape[1], self.tree.N, _dtype_code(Xc),
+                                              _stream_ptr()))
+        out = Y.t()
+        return out.reshape(Xv.shape) if vec else out
+
+    def grad(self, x, dLdx):
+        """(dL/db, dL/dlambda, dL/dh) for x = (lambda I + K~)^-1 b, FP64 tensors."""
+        torch = _torch()
+        vec = x.dim() == 1
+        xm = x.reshape(x.shape[0], -1).t().contiguous().to(torch.float64)
+        gm = dLdx.reshape(dLdx.shape[0], -1).t().contiguous().to(torch.float64)
+        db = torch.empty_like(gm)
+        dl, dh = ctypes.c_double(), ctypes.c_double()
+        self.ctx.check(self.ctx.lib.kf_grad(self.h, _ptr(xm), _ptr(gm), _ptr(db), ctypes.byref(dl), ctypes.byref(dh),
+                                            xm.shape[0], self.tree.N, _stream_ptr()))
+        db = db.t()
+        return (db.reshape(x.shape) if vec else db), dl.value, dh.value
+
+    # -- inspection -----------------------------------------------------------------
+    def ranks(self):
+        import numpy as np
+        r = np.zeros(self.tree.nnodes + 1, dtype=np.int32)
+        self.ctx.check(self.ctx.lib.kf_factor_ranks(self.h, r.ctypes.data_as(ctypes.c_void_p), _stream_ptr()))
+        return r
+
+    def skeleton(self, node: int):
+        import numpy as np
+        s = int(self.ranks()[node])
+        out = np.zeros(max(s, 1), dtype=np.int64)
+        self.ctx.check(self.ctx.lib.kf_factor_skeleton(self.h, node, out.ctypes.data_as(ctypes.c_void_p),
+                                                       _stream_ptr()))
+        return out[:s]
+
+    def P(self, node: int, ncols: int):
+        import numpy as np
+        s = int(self.ranks()[node])
+        out = np.zeros(max(s * ncols, 1))
+        self.ctx.check(self.ctx.lib.kf_factor_P(self.h, node, out.ctypes.data_as(ctypes.c_void_p), _stream_ptr()))
+        return out[: s * ncols].reshape(s, ncols)
+
+    def Phat(self, node: int, nrows: int):
+        import numpy as np
+        s = int(self.ranks()[node])
+        out = np.zeros(max(s * nrows, 1))
+        self.ctx.check(self.ctx.lib.kf_factor_Phat(self.h, node, out.ctypes.data_as(ctypes.c_void_p), _stream_ptr()))
+        return out[: s * nrows].reshape(nrows, s)
+
+    def device_status(self):
+        return self.ctx.lib.kf_factor_status(self.h, _stream_ptr())
+
+    def free(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.kf_factor_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.free()
+
+
+# ---- function-style names of the C ABI ------------------------------------------------
+def tree_build(X, m: int, ctx: Context | None = None) -> Tree:
+    return Tree(X, m, ctx)
+
+
+def factorize(tree: Tree, h: float, lam: float, tau: float, s_max: int, **kw) -> Factor:
+    return Factor(tree, h, lam, tau, s_max, **kw)
+
+
+def factorize_with_ids(tree: Tree, h: float, lam: float, s_max: int, ranks, skel, P, **kw) -> Factor:
+    return Factor(tree, h, lam, 0.0, s_max, _ids=(ranks, skel, P), **kw)
+
+
+def solve(factor: Factor, B, transpose: bool = False):
+    return factor.solve(B, transpose)
+
+
+def matvec(factor: Factor, X):
+    return factor.matvec(X)
+
+
+def grad(factor: Factor, x, dLdx):
+    return factor.grad(x, dLdx)
+
+
+def tree_free(tree: Tree):
+    tree.free()
+
+
+def factor_free(factor: Factor):
+    factor.free()
+
+
+def _autograd():
+    torch = _torch()
+
+    class KernelSolve(torch.autograd.Function):
+        """x = (lambda I + K~(h))^-1 b with gradients for b, lambda and h.
+
+        The backward pass is the library's adjoint: one transpose solve for
+        dL/db, and the sums -a.x and -a.(dK~/dh)x for lambda and h (skeletons
+        and P held fixed)."""
+
+        @staticmethod
+        def forward(ctx, b, lam, h, factor):
+            x = factor.solve(b)
+            ctx.factor = factor
+            ctx.save_for_backward(x)
+            return x
+
+        @staticmethod
+        def backward(ctx, gx):
+            (x,) = ctx.saved_tensors
+            db, dl, dh = ctx.factor.grad(x.to(torch.float64), gx.to(torch.float64))
+            dev = gx.device
+            return db.to(gx.dtype), torch.tensor(dl, device=dev), torch.tensor(dh, device=dev), None
+
+    return KernelSolve
+
+
+class _LazyAutograd:
+    _cls = None
+
+    def __getattr__(self, item):
+        if _LazyAutograd._cls is None:
+            _LazyAutograd._cls = _autograd()
+        return getattr(_LazyAutograd._cls, item)
+
+
+KernelSolve = _LazyAutograd()

@@ -1,0 +1,733 @@
+// kf_api.cu -- the C ABI declared in include/kf.h: argument checks, device
+// memory, staging of host or device buffers, the permutation into tree order
+// and the mixed-precision refinement loop around the solve.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kf_internal.cuh"
+#include "prof.cuh"
+
+kf_status kf_to_f64_launch(const float* in, double* out, int64_t n, cudaStream_t s);
+kf_status kf_to_f32_launch(const double* in, float* out, int64_t n, cudaStream_t s);
+kf_status kf_check_finite_launch(const double* x, int64_t n, int32_t* bad, cudaStream_t s);
+
+static thread_local std::string g_err;
+
+kf_status kf_set_err(kf_ctx* c, kf_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  g_err = buf;
+  return s;
+}
+
+void* kf_ctx::dalloc(size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  if (has_alloc) return alloc.alloc(bytes, (void*)s, alloc.user);
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void kf_ctx::dfree(void* p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  if (bytes == 0) bytes = 16;
+  if (has_alloc) alloc.free(p, bytes, (void*)s, alloc.user);
+  else cudaFreeAsync(p, s);
+}
+
+namespace {
+
+inline int grid_for(int64_t n, int threads, int cap = 152 * 16) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  return (int)(g < cap ? g : cap);
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// B (original order, column-major, ld, F32/F64) -> W (tree order, N x k row-major, FP64)
+__global__ void k_gather_in(const void* __restrict__ B, int dtype, int64_t ld, const int64_t* __restrict__ perm,
+                            int64_t N, int64_t k, double* __restrict__ W) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * k; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / k, r = e % k;
+    int64_t src = perm[i] + r * ld;
+    W[e] = dtype == KF_F64 ? ((const double*)B)[src] : (double)((const float*)B)[src];
+  }
+}
+__global__ void k_scatter_out(const double* __restrict__ W, const int64_t* __restrict__ perm, int64_t N, int64_t k,
+                              void* __restrict__ X, int dtype, int64_t ld) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * k; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / k, r = e % k;
+    int64_t dst = perm[i] + r * ld;
+    if (dtype == KF_F64) ((double*)X)[dst] = W[e];
+    else ((float*)X)[dst] = (float)W[e];
+  }
+}
+// per-column squared norms (atomic FP64)
+__global__ void k_colnorm2(const double* __restrict__ W, int64_t N, int64_t k, double* __restrict__ out) {
+  __shared__ double sh[8];
+  for (int64_t r = 0; r < k; ++r) {
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+      acc += W[i * k + r] * W[i * k + r];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+      atomicAdd(out + r, t);
+    }
+    __syncthreads();
+  }
+}
+__global__ void k_dot_all(const double* __restrict__ a, const double* __restrict__ b, int64_t n, double* __restrict__ out) {
+  __shared__ double sh[8];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += a[i] * b[i];
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    atomicAdd(out, t);
+  }
+}
+// r = b - y
+__global__ void k_sub(const double* __restrict__ b, const double* __restrict__ y, double* __restrict__ r, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = b[i] - y[i];
+}
+__global__ void k_add(double* __restrict__ x, const double* __restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += d[i];
+}
+
+struct Staged {
+  kf_ctx* c;
+  void* dev = nullptr;
+  size_t bytes = 0;
+  bool owned = false;
+  cudaStream_t s;
+  ~Staged() {
+    if (owned) c->dfree(dev, bytes, s);
+  }
+};
+
+// Make a device view of a caller buffer of `bytes` bytes (copy in if host).
+kf_status stage_in(kf_ctx* c, const void* p, size_t bytes, cudaStream_t s, Staged& out) {
+  out.c = c;
+  out.s = s;
+  out.bytes = bytes;
+  if (is_device_ptr(p)) {
+    out.dev = const_cast<void*>(p);
+    return KF_OK;
+  }
+  out.dev = c->dalloc(bytes, s);
+  if (!out.dev) return kf_set_err(c, KF_ENOMEM, "staging: allocation of %zu bytes failed", bytes);
+  out.owned = true;
+  KF_CUDA(c, cudaMemcpyAsync(out.dev, p, bytes, cudaMemcpyHostToDevice, s));
+  return KF_OK;
+}
+
+template <typename T>
+T* falloc(kf_factor* f, size_t n, cudaStream_t s) {
+  size_t b = sizeof(T) * n;
+  void* p = f->ctx->dalloc(b, s);
+  if (p) {
+    f->allocs.push_back({p, b});
+    cudaMemsetAsync(p, 0, b, s);
+  }
+  return (T*)p;
+}
+
+kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t s_max, const kf_opts* opts,
+                       cudaStream_t s, kf_factor** out) {
+  kf_ctx* c = t->ctx;
+  if (!(h > 0.0) || !isfinite(h)) return kf_set_err(c, KF_EINVAL, "h must be > 0 (got %g)", h);
+  if (!(lambda >= 0.0) || !isfinite(lambda)) return kf_set_err(c, KF_EINVAL, "lambda must be >= 0 (got %g)", lambda);
+  if (!(tau >= 0.0) || !isfinite(tau)) return kf_set_err(c, KF_EINVAL, "tau must be >= 0 (got %g)", tau);
+  if (s_max < 1 || s_max > KF_MAX_SMAX) return kf_set_err(c, KF_EINVAL, "s_max must be in [1, %d]", KF_MAX_SMAX);
+  kf_factor* f = new kf_factor();
+  f->t = t;
+  f->ctx = c;
+  f->h = h;
+  f->lambda = lambda;
+  f->tau = tau;
+  f->c_exp = -0.5 / (h * h);
+  f->s_max = s_max;
+  f->n_samp = 2 * s_max;
+  if (opts) {
+    f->prec = opts->precision;
+    if (opts->n_samp > 0) f->n_samp = opts->n_samp;
+    if (opts->seed) f->seed = opts->seed;
+    f->vstore = opts->v_storage;
+    f->sync_errors = opts->sync_errors;
+    if (opts->refine_tol > 0) f->refine_tol = opts->refine_tol;
+    if (opts->refine_max_iter > 0) f->refine_max_iter = opts->refine_max_iter;
+    if (opts->refine_max_iter < 0) f->refine_max_iter = 0;
+  }
+  if (f->prec != KF_PREC_FP64 && f->prec != KF_PREC_MIXED) {
+    delete f;
+    return kf_set_err(c, KF_EINVAL, "unknown precision %d", opts ? opts->precision : -1);
+  }
+  if (f->vstore != KF_V_STORED && f->vstore != KF_V_RECOMPUTE) {
+    delete f;
+    return kf_set_err(c, KF_EINVAL, "unknown v_storage");
+  }
+  if (f->n_samp > 1024) {
+    delete f;
+    return kf_set_err(c, KF_EINVAL, "n_samp must be <= 1024");
+  }
+  const int64_t N = t->N;
+  const int D = t->D;
+  f->cmax = std::max(t->leaf_max, 2 * s_max);
+  const size_t nn = (size_t)t->nnodes + 1;
+  const size_t ts = f->tsize();
+  f->rank = falloc<int32_t>(f, nn, s);
+  f->skel = falloc<int32_t>(f, nn * s_max, s);
+  f->status = falloc<int32_t>(f, 1, s);
+  f->Pleaf = falloc<double>(f, (size_t)N * s_max, s);
+  if (D > 0) {
+    f->Pc = falloc<double>(f, (size_t)(1 << D) * 2 * s_max * s_max, s);
+    f->ZLU = falloc<double>(f, (size_t)(1 << D) * 4 * s_max * s_max, s);
+    f->Zpiv = falloc<int32_t>(f, (size_t)(1 << D) * 2 * s_max, s);
+    f->Phat = falloc<char>(f, (size_t)D * N * s_max * ts, s);
+    f->VT = falloc<char>(f, (size_t)D * N * s_max * ts, s);
+  }
+  f->L = falloc<char>(f, (size_t)(1 << D) * t->leaf_max * t->leaf_max * ts, s);
+  bool ok = f->rank && f->skel && f->status && f->Pleaf && f->L &&
+            (D == 0 || (f->Pc && f->ZLU && f->Zpiv && f->Phat && f->VT));
+  if (!ok) {
+    kf_factor_free(f);
+    return kf_set_err(c, KF_ENOMEM, "factorize: device allocation failed");
+  }
+  *out = f;
+  return KF_OK;
+}
+
+kf_status read_status(kf_factor* f, cudaStream_t s) {
+  int32_t st = 0;
+  KF_CUDA(f->ctx, cudaMemcpyAsync(&st, f->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  KF_CUDA(f->ctx, cudaStreamSynchronize(s));
+  if (st & KF_DEV_TIMEOUT) return kf_set_err(f->ctx, KF_ETIMEOUT, "a bounded device wait ran out");
+  if (st & KF_DEV_ILLCOND)
+    return kf_set_err(f->ctx, KF_EILLCOND, "ill-conditioned leaf block or reduced system (small pivot)");
+  return KF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* kf_status_string(kf_status s) {
+  switch (s) {
+    case KF_OK: return "KF_OK";
+    case KF_EINVAL: return "KF_EINVAL";
+    case KF_ENOMEM: return "KF_ENOMEM";
+    case KF_ECUDA: return "KF_ECUDA";
+    case KF_EILLCOND: return "KF_EILLCOND";
+    case KF_ENOTCONV: return "KF_ENOTCONV";
+    case KF_ETIMEOUT: return "KF_ETIMEOUT";
+    case KF_EUNSUPPORTED: return "KF_EUNSUPPORTED";
+  }
+  return "KF_UNKNOWN";
+}
+
+kf_status kf_create(kf_ctx** out, const kf_alloc* alloc) {
+  if (!out) return KF_EINVAL;
+  kf_ctx* c = new kf_ctx();
+  if (alloc) {
+    if (!alloc->alloc || !alloc->free) {
+      delete c;
+      return kf_set_err(nullptr, KF_EINVAL, "allocator needs alloc and free");
+    }
+    c->alloc = *alloc;
+    c->has_alloc = 1;
+  }
+  *out = c;
+  return KF_OK;
+}
+
+kf_status kf_destroy(kf_ctx* c) {
+  delete c;
+  return KF_OK;
+}
+
+const char* kf_last_error(const kf_ctx* c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+kf_status kf_tree_build(kf_ctx* c, const void* X, int32_t dtype, int64_t N, int32_t d, int32_t m, void* stream,
+                        kf_tree** out) {
+  if (!c || !out) return KF_EINVAL;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!X) return kf_set_err(c, KF_EINVAL, "X is NULL");
+  if (N < 1 || N >= (int64_t)INT32_MAX) return kf_set_err(c, KF_EINVAL, "N must be in [1, 2^31)");
+  if (d < 1 || d > KF_MAX_D) return kf_set_err(c, KF_EINVAL, "d must be in [1, %d]", KF_MAX_D);
+  if (m < 1) return kf_set_err(c, KF_EINVAL, "m must be >= 1");
+  if (dtype != KF_F32 && dtype != KF_F64) return kf_set_err(c, KF_EINVAL, "dtype must be KF_F32 or KF_F64");
+  kf_tree* t = new kf_tree();
+  t->ctx = c;
+  t->N = N;
+  t->d = d;
+  t->m = m;
+  int D = 0;
+  while (((int64_t)m << D) < N) ++D;
+  if (D > 24) {
+    delete t;
+    return kf_set_err(c, KF_EINVAL, "tree deeper than 24 levels (N/m too large)");
+  }
+  t->D = D;
+  t->nnodes = (1 << (D + 1)) - 1;
+  t->lo.assign(t->nnodes + 1, 0);
+  t->hi.assign(t->nnodes + 1, 0);
+  t->lo[1] = 0;
+  t->hi[1] = (int32_t)N;
+  for (int a = 1; a < (1 << D); ++a) {
+    int32_t n = t->hi[a] - t->lo[a], mid = t->lo[a] + n / 2;
+    t->lo[2 * a] = t->lo[a];
+    t->hi[2 * a] = mid;
+    t->lo[2 * a + 1] = mid;
+    t->hi[2 * a + 1] = t->hi[a];
+  }
+  t->leaf_max = 0;
+  for (int a = 1 << D; a < (2 << D); ++a) t->leaf_max = std::max(t->leaf_max, t->hi[a] - t->lo[a]);
+  if (t->leaf_max < 1) t->leaf_max = 1;
+  auto talloc = [&](size_t b) {
+    void* p = c->dalloc(b, s);
+    if (p) t->allocs.push_back({p, b});
+    return p;
+  };
+  t->X64 = (double*)talloc(sizeof(double) * N * d);
+  t->X32 = (float*)talloc(sizeof(float) * N * d);
+  t->perm = (int64_t*)talloc(sizeof(int64_t) * N);
+  t->d_lo = (int32_t*)talloc(sizeof(int32_t) * (t->nnodes + 1));
+  t->d_hi = (int32_t*)talloc(sizeof(int32_t) * (t->nnodes + 1));
+  int32_t* bad = (int32_t*)talloc(sizeof(int32_t));
+  if (!t->X64 || !t->X32 || !t->perm || !t->d_lo || !t->d_hi || !bad) {
+    kf_tree_free(t);
+    return kf_set_err(c, KF_ENOMEM, "tree: device allocation failed");
+  }
+  kf_status st = KF_OK;
+  {
+    Staged xs;
+    size_t xb = (dtype == KF_F64 ? 8 : 4) * (size_t)N * d;
+    st = stage_in(c, X, xb, s, xs);
+    if (st == KF_OK) {
+      if (dtype == KF_F64) cudaMemcpyAsync(t->X64, xs.dev, xb, cudaMemcpyDeviceToDevice, s);
+      else kf_to_f64_launch((const float*)xs.dev, t->X64, N * d, s);
+      cudaMemcpyAsync(t->d_lo, t->lo.data(), sizeof(int32_t) * (t->nnodes + 1), cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(t->d_hi, t->hi.data(), sizeof(int32_t) * (t->nnodes + 1), cudaMemcpyHostToDevice, s);
+      cudaMemsetAsync(bad, 0, sizeof(int32_t), s);
+      kf_check_finite_launch(t->X64, N * d, bad, s);
+      int32_t hb = 0;
+      cudaMemcpyAsync(&hb, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) st = kf_set_err(c, KF_ECUDA, "tree: %s", cudaGetErrorString(e));
+      else if (hb) st = kf_set_err(c, KF_EINVAL, "X has non-finite coordinates");
+    }
+  }
+  if (st == KF_OK) st = kf_tree_build_device(t, s);
+  if (st == KF_OK) st = kf_to_f32_launch(t->X64, t->X32, N * d, s);
+  if (st != KF_OK) {
+    kf_tree_free(t);
+    return st;
+  }
+  *out = t;
+  return KF_OK;
+}
+
+kf_status kf_tree_perm(const kf_tree* t, int64_t* perm, void* stream) {
+  if (!t || !perm) return KF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  KF_CUDA(t->ctx, cudaMemcpyAsync(perm, t->perm, sizeof(int64_t) * t->N, cudaMemcpyDefault, s));
+  if (!is_device_ptr(perm)) KF_CUDA(t->ctx, cudaStreamSynchronize(s));
+  return KF_OK;
+}
+
+kf_status kf_tree_info(const kf_tree* t, int64_t* N, int32_t* d, int32_t* m, int32_t* depth) {
+  if (!t) return KF_EINVAL;
+  if (N) *N = t->N;
+  if (d) *d = t->d;
+  if (m) *m = t->m;
+  if (depth) *depth = t->D;
+  return KF_OK;
+}
+
+kf_status kf_tree_free(kf_tree* t) {
+  if (!t) return KF_OK;
+  for (auto& a : t->allocs) t->ctx->dfree(a.first, a.second, 0);
+  cudaDeviceSynchronize();
+  delete t;
+  return KF_OK;
+}
+
+kf_status kf_factorize(kf_tree* t, double h, double lambda, double tau, int32_t s_max, const kf_opts* opts,
+                       void* stream, kf_factor** out) {
+  if (!t || !out) return KF_EINVAL;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  kf_factor* f = nullptr;
+  kf_status st = alloc_factor(t, h, lambda, tau, s_max, opts, s, &f);
+  if (st != KF_OK) return st;
+  st = kf_skeletonize_device(f, s);
+  if (st == KF_OK) st = kf_factorize_device(f, s);
+  if (st == KF_OK && f->sync_errors) st = read_status(f, s);
+  if (st != KF_OK && st != KF_EILLCOND) {
+    kf_factor_free(f);
+    return st;
+  }
+  *out = f;
+  return st;
+}
+
+kf_status kf_factorize_with_ids(kf_tree* t, double h, double lambda, int32_t s_max, const int32_t* ranks,
+                                const int64_t* skel, const double* P, const kf_opts* opts, void* stream,
+                                kf_factor** out) {
+  if (!t || !out || !ranks || !skel || !P) return KF_EINVAL;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  kf_factor* f = nullptr;
+  kf_status st = alloc_factor(t, h, lambda, 0.0, s_max, opts, s, &f);
+  if (st != KF_OK) return st;
+  const int D = t->D, nn = t->nnodes;
+  const int cmax = f->cmax;
+  std::vector<int32_t> hr(nn + 1, 0), hs((size_t)(nn + 1) * s_max, -1);
+  std::vector<double> hpl((size_t)t->N * s_max, 0.0), hpc(D > 0 ? (size_t)(1 << D) * 2 * s_max * s_max : 1, 0.0);
+  // ranks first (children before parents: a node's column count is the sum
+  // of its children's ranks)
+  for (int a = nn; a >= 2 && st == KF_OK; --a) {
+    const bool leaf = a >= (1 << D);
+    const int sa = ranks[a];
+    const int c = leaf ? t->hi[a] - t->lo[a] : hr[2 * a] + hr[2 * a + 1];
+    if (sa < 0 || sa > s_max || sa > c) st = kf_set_err(t->ctx, KF_EINVAL, "import: bad rank %d at node %d", sa, a);
+    hr[a] = sa;
+  }
+  // children must be set before parents: ranks of children define c
+  for (int a = nn; a >= 2 && st == KF_OK; --a) {
+    bool leaf = a >= (1 << D);
+    int sa = hr[a];
+    int c = leaf ? t->hi[a] - t->lo[a] : hr[2 * a] + hr[2 * a + 1];
+    const double* Pa = P + (size_t)a * s_max * cmax;
+    for (int q = 0; q < sa; ++q) {
+      int64_t sk = skel[(size_t)a * s_max + q];
+      if (sk < t->lo[a] || sk >= t->hi[a]) {
+        st = kf_set_err(t->ctx, KF_EINVAL, "import: skeleton point outside node %d", a);
+        break;
+      }
+      hs[(size_t)a * s_max + q] = (int32_t)sk;
+      for (int j = 0; j < c; ++j) {
+        double v = Pa[(size_t)q * c + j];
+        if (leaf) hpl[(size_t)(t->lo[a] + j) * s_max + q] = v;
+        else hpc[((size_t)a * 2 * s_max + j) * s_max + q] = v;
+      }
+    }
+  }
+  if (st == KF_OK) {
+    cudaMemcpyAsync(f->rank, hr.data(), sizeof(int32_t) * (nn + 1), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(f->skel, hs.data(), sizeof(int32_t) * hs.size(), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(f->Pleaf, hpl.data(), sizeof(double) * hpl.size(), cudaMemcpyHostToDevice, s);
+    if (D > 0) cudaMemcpyAsync(f->Pc, hpc.data(), sizeof(double) * hpc.size(), cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaStreamSynchronize(s);  // host vectors go out of scope
+    if (e != cudaSuccess) st = kf_set_err(t->ctx, KF_ECUDA, "import: %s", cudaGetErrorString(e));
+  }
+  if (st == KF_OK) st = kf_factorize_device(f, s);
+  if (st == KF_OK && f->sync_errors) st = read_status(f, s);
+  if (st != KF_OK && st != KF_EILLCOND) {
+    kf_factor_free(f);
+    return st;
+  }
+  *out = f;
+  return st;
+}
+
+kf_status kf_factor_status(kf_factor* f, void* stream) {
+  if (!f) return KF_EINVAL;
+  return read_status(f, (cudaStream_t)stream);
+}
+
+kf_status kf_factor_free(kf_factor* f) {
+  if (!f) return KF_OK;
+  for (auto& a : f->allocs) f->ctx->dfree(a.first, a.second, 0);
+  cudaDeviceSynchronize();
+  delete f;
+  return KF_OK;
+}
+
+}  // extern "C"
+
+static kf_status check_rhs(kf_factor* f, const void* B, const void* X, int64_t nrhs, int64_t ld, int32_t dtype) {
+  if (!f) return KF_EINVAL;
+  if (!B || !X) return kf_set_err(f->ctx, KF_EINVAL, "NULL vector");
+  if (nrhs < 1) return kf_set_err(f->ctx, KF_EINVAL, "nrhs must be >= 1");
+  if (ld < f->t->N) return kf_set_err(f->ctx, KF_EINVAL, "ld must be >= N");
+  if (dtype != KF_F32 && dtype != KF_F64) return kf_set_err(f->ctx, KF_EINVAL, "dtype must be KF_F32 or KF_F64");
+  return KF_OK;
+}
+
+// Copy a caller matrix in, run fn on the tree-order FP64 block, copy out.
+template <typename Fn>
+static kf_status with_vectors(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t ld, int32_t dtype,
+                              cudaStream_t s, Fn fn) {
+  kf_ctx* c = f->ctx;
+  const int64_t N = f->t->N;
+  const size_t es = dtype == KF_F64 ? 8 : 4;
+  const size_t bb = es * (size_t)(ld * (nrhs - 1) + N);
+  Staged bs;
+  kf_status st = stage_in(c, B, bb, s, bs);
+  if (st != KF_OK) return st;
+  const bool xdev = is_device_ptr(X);
+  void* xd = X;
+  if (!xdev) {
+    xd = c->dalloc(bb, s);
+    if (!xd) return kf_set_err(c, KF_ENOMEM, "staging: allocation failed");
+    if (ld > N) cudaMemcpyAsync(xd, X, bb, cudaMemcpyHostToDevice, s);  // keep the gaps of X
+  }
+  double* W = (double*)c->dalloc(sizeof(double) * N * nrhs, s);
+  if (!W) {
+    if (!xdev) c->dfree(xd, bb, s);
+    return kf_set_err(c, KF_ENOMEM, "solve: allocation failed");
+  }
+  KF_PHASE(KF_PH_MISC, s, k_gather_in<<<grid_for(N * nrhs, 256), 256, 0, s>>>(bs.dev, dtype, ld, f->t->perm, N, nrhs, W));
+  st = fn(W);
+  if (st == KF_OK) {
+    KF_PHASE(KF_PH_MISC, s, k_scatter_out<<<grid_for(N * nrhs, 256), 256, 0, s>>>(W, f->t->perm, N, nrhs, xd, dtype, ld));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = kf_set_err(c, KF_ECUDA, "%s", cudaGetErrorString(e));
+  }
+  if (!xdev && st == KF_OK) {
+    cudaMemcpyAsync(X, xd, bb, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+  }
+  c->dfree(W, sizeof(double) * N * nrhs, s);
+  if (!xdev) c->dfree(xd, bb, s);
+  return st;
+}
+
+// max over columns of ||r_j|| / ||b_j||
+static kf_status rel_residual(kf_factor* f, const double* Bt, const double* Xt, int64_t k, double* R, double* Y,
+                              double* nrm, cudaStream_t s, double* out) {
+  kf_ctx* c = f->ctx;
+  const int64_t N = f->t->N;
+  kf_status st = kf_matvec_device(f, Xt, Y, k, 0, s);
+  if (st != KF_OK) return st;
+  KF_PHASE(KF_PH_MISC, s, k_sub<<<grid_for(N * k, 256), 256, 0, s>>>(Bt, Y, R, N * k));
+  KF_CUDA(c, cudaMemsetAsync(nrm, 0, sizeof(double) * 2 * k, s));
+  KF_PHASE(KF_PH_MISC, s, k_colnorm2<<<grid_for(N, 256, 304), 256, 0, s>>>(R, N, k, nrm));
+  KF_PHASE(KF_PH_MISC, s, k_colnorm2<<<grid_for(N, 256, 304), 256, 0, s>>>(Bt, N, k, nrm + k));
+  std::vector<double> h(2 * k);
+  KF_CUDA(c, cudaMemcpyAsync(h.data(), nrm, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
+  KF_CUDA(c, cudaStreamSynchronize(s));
+  double worst = 0.0;
+  for (int64_t j = 0; j < k; ++j) worst = std::max(worst, h[k + j] > 0 ? sqrt(h[j] / h[k + j]) : sqrt(h[j]));
+  *out = worst;
+  return KF_OK;
+}
+
+extern "C" {
+
+kf_status kf_solve(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t ld, int32_t dtype, int32_t transpose,
+                   void* stream, kf_solve_info* info) {
+  kf_status st = check_rhs(f, B, X, nrhs, ld, dtype);
+  if (st != KF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  kf_ctx* c = f->ctx;
+  const int64_t N = f->t->N;
+  const bool refine = (f->prec == KF_PREC_MIXED) && f->refine_max_iter > 0 && !transpose;
+  int iters = 0;
+  double eps = -1.0;
+  st = with_vectors(f, B, X, nrhs, ld, dtype, s, [&](double* W) -> kf_status {
+    if (!refine && !info) return kf_solve_device(f, W, nrhs, transpose, s);
+    const size_t vb = sizeof(double) * N * nrhs;
+    double* Bt = (double*)c->dalloc(vb, s);
+    double* R = (double*)c->dalloc(vb, s);
+    double* Y = (double*)c->dalloc(vb, s);
+    double* nrm = (double*)c->dalloc(sizeof(double) * 2 * nrhs, s);
+    kf_status r = (Bt && R && Y && nrm) ? KF_OK : kf_set_err(c, KF_ENOMEM, "refinement: allocation failed");
+    if (r == KF_OK) {
+      cudaMemcpyAsync(Bt, W, vb, cudaMemcpyDeviceToDevice, s);
+      r = kf_solve_device(f, W, nrhs, transpose, s);
+      if (r == KF_OK && !transpose) {
+        r = rel_residual(f, Bt, W, nrhs, R, Y, nrm, s, &eps);
+        while (r == KF_OK && refine && eps > f->refine_tol && iters < f->refine_max_iter) {
+          r = kf_solve_device(f, R, nrhs, 0, s);  // correction M^-1 r
+          if (r != KF_OK) break;
+          KF_PHASE(KF_PH_MISC, s, k_add<<<grid_for(N * nrhs, 256), 256, 0, s>>>(W, R, N * nrhs));
+          ++iters;
+          r = rel_residual(f, Bt, W, nrhs, R, Y, nrm, s, &eps);
+        }
+        if (r == KF_OK && refine && eps > f->refine_tol)
+          r = kf_set_err(c, KF_ENOTCONV, "refinement stopped at eps_r = %.3e after %d steps", eps, iters);
+      }
+    }
+    c->dfree(Bt, vb, s);
+    c->dfree(R, vb, s);
+    c->dfree(Y, vb, s);
+    c->dfree(nrm, sizeof(double) * 2 * nrhs, s);
+    return r;
+  });
+  if (info) {
+    info->eps_r = eps;
+    info->iters = iters;
+    int32_t dst = 0;
+    cudaMemcpyAsync(&dst, f->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    info->status = dst;
+  }
+  if (st == KF_OK && f->sync_errors) st = read_status(f, s);
+  return st;
+}
+
+kf_status kf_matvec(kf_factor* f, const void* Xin, void* Y, int64_t nrhs, int64_t ld, int32_t dtype, void* stream) {
+  kf_status st = check_rhs(f, Xin, Y, nrhs, ld, dtype);
+  if (st != KF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  kf_ctx* c = f->ctx;
+  const int64_t N = f->t->N;
+  return with_vectors(f, Xin, Y, nrhs, ld, dtype, s, [&](double* W) -> kf_status {
+    double* Yt = (double*)c->dalloc(sizeof(double) * N * nrhs, s);
+    if (!Yt) return kf_set_err(c, KF_ENOMEM, "matvec: allocation failed");
+    kf_status r = kf_matvec_device(f, W, Yt, nrhs, 0, s);
+    cudaMemcpyAsync(W, Yt, sizeof(double) * N * nrhs, cudaMemcpyDeviceToDevice, s);
+    c->dfree(Yt, sizeof(double) * N * nrhs, s);
+    return r;
+  });
+}
+
+kf_status kf_grad(kf_factor* f, const void* x, const void* dLdx, void* dLdb, double* dLdlambda, double* dLdh,
+                  int64_t nrhs, int64_t ld, void* stream) {
+  kf_status st = check_rhs(f, x, dLdx, nrhs, ld, KF_F64);
+  if (st != KF_OK) return st;
+  if (!dLdb || !dLdlambda || !dLdh) return kf_set_err(f->ctx, KF_EINVAL, "NULL gradient output");
+  cudaStream_t s = (cudaStream_t)stream;
+  kf_ctx* c = f->ctx;
+  const int64_t N = f->t->N;
+  const size_t vb = sizeof(double) * N * nrhs;
+  Staged xs;
+  st = stage_in(c, x, sizeof(double) * (size_t)(ld * (nrhs - 1) + N), s, xs);
+  if (st != KF_OK) return st;
+  double* Xt = (double*)c->dalloc(vb, s);
+  double* DX = (double*)c->dalloc(vb, s);
+  double* sums = (double*)c->dalloc(sizeof(double) * 2, s);
+  if (!Xt || !DX || !sums) {
+    c->dfree(Xt, vb, s);
+    c->dfree(DX, vb, s);
+    c->dfree(sums, 16, s);
+    return kf_set_err(c, KF_ENOMEM, "grad: allocation failed");
+  }
+  KF_PHASE(KF_PH_MISC, s, k_gather_in<<<grid_for(N * nrhs, 256), 256, 0, s>>>(xs.dev, KF_F64, ld, f->t->perm, N, nrhs, Xt));
+  kf_status r = kf_matvec_device(f, Xt, DX, nrhs, 1, s);  // (dK~/dh) x
+  double hs[2] = {0, 0};
+  if (r == KF_OK)
+    r = with_vectors(f, dLdx, dLdb, nrhs, ld, KF_F64, s, [&](double* A) -> kf_status {
+      kf_status q = kf_solve_device(f, A, nrhs, 1, s);  // a = (lambda I + K~)^-T dL/dx
+      if (q != KF_OK) return q;
+      cudaMemsetAsync(sums, 0, sizeof(double) * 2, s);
+      KF_PHASE(KF_PH_MISC, s, k_dot_all<<<grid_for(N * nrhs, 256, 304), 256, 0, s>>>(A, Xt, N * nrhs, sums));
+      KF_PHASE(KF_PH_MISC, s, k_dot_all<<<grid_for(N * nrhs, 256, 304), 256, 0, s>>>(A, DX, N * nrhs, sums + 1));
+      cudaMemcpyAsync(hs, sums, sizeof(double) * 2, cudaMemcpyDeviceToHost, s);
+      return KF_OK;
+    });
+  cudaStreamSynchronize(s);
+  *dLdlambda = -hs[0];
+  *dLdh = -hs[1];
+  c->dfree(Xt, vb, s);
+  c->dfree(DX, vb, s);
+  c->dfree(sums, 16, s);
+  return r;
+}
+
+kf_status kf_factor_ranks(const kf_factor* f, int32_t* ranks, void* stream) {
+  if (!f || !ranks) return KF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  KF_CUDA(f->ctx, cudaMemcpyAsync(ranks, f->rank, sizeof(int32_t) * (f->t->nnodes + 1), cudaMemcpyDeviceToHost, s));
+  KF_CUDA(f->ctx, cudaStreamSynchronize(s));
+  return KF_OK;
+}
+
+static kf_status node_ok(const kf_factor* f, int32_t node) {
+  if (node < 2 || node > f->t->nnodes) return kf_set_err(f->ctx, KF_EINVAL, "node %d is not a non-root node", node);
+  return KF_OK;
+}
+
+kf_status kf_factor_skeleton(const kf_factor* f, int32_t node, int64_t* skel, void* stream) {
+  if (!f || !skel) return KF_EINVAL;
+  kf_status st = node_ok(f, node);
+  if (st != KF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int32_t> r(f->t->nnodes + 1), sk(f->s_max);
+  KF_CUDA(f->ctx, cudaMemcpyAsync(r.data(), f->rank, sizeof(int32_t) * r.size(), cudaMemcpyDeviceToHost, s));
+  KF_CUDA(f->ctx, cudaMemcpyAsync(sk.data(), f->skel + (size_t)node * f->s_max, sizeof(int32_t) * f->s_max,
+                                  cudaMemcpyDeviceToHost, s));
+  KF_CUDA(f->ctx, cudaStreamSynchronize(s));
+  for (int q = 0; q < r[node]; ++q) skel[q] = sk[q];
+  return KF_OK;
+}
+
+kf_status kf_factor_P(const kf_factor* f, int32_t node, double* P, void* stream) {
+  if (!f || !P) return KF_EINVAL;
+  kf_status st = node_ok(f, node);
+  if (st != KF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const kf_tree* t = f->t;
+  const int s_max = f->s_max;
+  std::vector<int32_t> r(t->nnodes + 1);
+  KF_CUDA(f->ctx, cudaMemcpyAsync(r.data(), f->rank, sizeof(int32_t) * r.size(), cudaMemcpyDeviceToHost, s));
+  KF_CUDA(f->ctx, cudaStreamSynchronize(s));
+  const bool leaf = node >= (1 << t->D);
+  const int sa = r[node];
+  const int c = leaf ? t->hi[node] - t->lo[node] : r[2 * node] + r[2 * node + 1];
+  std::vector<double> buf((size_t)std::max(c, 1) * s_max);
+  const double* src = leaf ? f->Pleaf + (size_t)t->lo[node] * s_max : f->Pc + (size_t)node * 2 * s_max * s_max;
+  KF_CUDA(f->ctx, cudaMemcpyAsync(buf.data(), src, sizeof(double) * (size_t)c * s_max, cudaMemcpyDeviceToHost, s));
+  KF_CUDA(f->ctx, cudaStreamSynchronize(s));
+  for (int q = 0; q < sa; ++q)
+    for (int j = 0; j < c; ++j) P[(size_t)q * c + j] = buf[(size_t)j * s_max + q];
+  return KF_OK;
+}
+
+kf_status kf_factor_Phat(const kf_factor* f, int32_t node, double* Phat, void* stream) {
+  if (!f || !Phat) return KF_EINVAL;
+  kf_status st = node_ok(f, node);
+  if (st != KF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const kf_tree* t = f->t;
+  const int s_max = f->s_max, l = kf_level_of(node);
+  std::vector<int32_t> r(t->nnodes + 1);
+  KF_CUDA(f->ctx, cudaMemcpyAsync(r.data(), f->rank, sizeof(int32_t) * r.size(), cudaMemcpyDeviceToHost, s));
+  const int n = t->hi[node] - t->lo[node];
+  const size_t off = ((size_t)(l - 1) * t->N + t->lo[node]) * s_max;
+  std::vector<char> buf((size_t)std::max(n, 1) * s_max * f->tsize());
+  KF_CUDA(f->ctx, cudaMemcpyAsync(buf.data(), (const char*)f->Phat + off * f->tsize(), (size_t)n * s_max * f->tsize(),
+                                  cudaMemcpyDeviceToHost, s));
+  KF_CUDA(f->ctx, cudaStreamSynchronize(s));
+  const int sa = r[node];
+  for (int i = 0; i < n; ++i)
+    for (int q = 0; q < sa; ++q)
+      Phat[(size_t)i * sa + q] = f->prec == KF_PREC_FP64 ? ((const double*)buf.data())[(size_t)i * s_max + q]
+                                                         : (double)((const float*)buf.data())[(size_t)i * s_max + q];
+  return KF_OK;
+}
+
+}  // extern "C"

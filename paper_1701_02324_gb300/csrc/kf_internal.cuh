@@ -1,0 +1,140 @@
+// kf_internal.cuh -- internal types and device helpers of the CUDA library.
+//
+// Storage layout in HBM (all fixed-capacity, strides in elements):
+//   tree:   X64 N x d (tree order), X32 N x d, perm N, node ranges lo/hi per
+//           heap id (root 1, children 2a, 2a+1; level l = 2^l .. 2^(l+1)-1).
+//   skel:   rank[node], skel[node * s_max + q] (tree positions, pivot order).
+//   Pleaf:  N x s_max (FP64): row i holds P_{a a~}[i, :] of the leaf owning i.
+//   Pc:     internal node a: (2 s_max) x s_max FP64 at a * 2 s_max * s_max,
+//           P_c = P_{[l~ r~] a~} (rows: ID columns [l~ r~], cols: skeleton).
+//   Phat:   level l in [1, D]: N x s_max of type T at (l-1) * N * s_max; row i
+//           holds P^_{b b~}[i, :] of the level-l node b owning i (Eq. e:hodlr).
+//   VT:     level l in [1, D]: N x s_max of type T; row i holds
+//           K(x_i, x_{skel(sib)[q]}) where sib is the sibling of the level-l
+//           node owning i, so that K_{sib~ b} = VT[b rows, :s_sib]^T (Eq. e:uv).
+//   L:      leaf j: leaf_max x leaf_max of type T (Cholesky factor, row-major).
+//   ZLU:    internal node a: (2 s_max)^2 FP64 LU of Z_a, Zpiv (2 s_max) int32.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/kf.h"
+
+#define KF_MAX_SMAX 512
+#define KF_MAX_D 1024
+
+struct kf_ctx {
+  kf_alloc alloc;
+  int has_alloc = 0;
+  std::string err;
+  void* dalloc(size_t bytes, cudaStream_t s);
+  void dfree(void* p, size_t bytes, cudaStream_t s);
+};
+
+struct kf_tree {
+  kf_ctx* ctx = nullptr;
+  int64_t N = 0;
+  int32_t d = 0, m = 0, D = 0, nnodes = 0, leaf_max = 0;
+  std::vector<int32_t> lo, hi;  // host copy, heap indexed, size nnodes + 1
+  int32_t* d_lo = nullptr;
+  int32_t* d_hi = nullptr;
+  double* X64 = nullptr;
+  float* X32 = nullptr;
+  int64_t* perm = nullptr;
+  std::vector<std::pair<void*, size_t>> allocs;
+};
+
+struct kf_factor {
+  kf_tree* t = nullptr;
+  kf_ctx* ctx = nullptr;
+  double h = 1, lambda = 0, tau = 0, c_exp = 0;
+  int32_t s_max = 0, n_samp = 0, cmax = 0, prec = 0, vstore = 0, sync_errors = 0;
+  double refine_tol = 1e-10;
+  int32_t refine_max_iter = 8;
+  uint64_t seed = 0x1701;
+  int32_t* rank = nullptr;
+  int32_t* skel = nullptr;
+  double* Pleaf = nullptr;
+  double* Pc = nullptr;
+  void* Phat = nullptr;
+  void* VT = nullptr;
+  void* L = nullptr;
+  float* Pleaf32 = nullptr;
+  double* ZLU = nullptr;
+  int32_t* Zpiv = nullptr;
+  int32_t* status = nullptr;
+  std::vector<std::pair<void*, size_t>> allocs;
+  size_t tsize() const { return prec == KF_PREC_FP64 ? 8 : 4; }
+};
+
+// device status bits
+#define KF_DEV_ILLCOND 1
+#define KF_DEV_TIMEOUT 2
+#define KF_DEV_BADARG 4
+
+// ---- error helpers ----------------------------------------------------------
+kf_status kf_set_err(kf_ctx* c, kf_status s, const char* fmt, ...);
+#define KF_CUDA(ctx, call)                                                               \
+  do {                                                                                   \
+    cudaError_t _e = (call);                                                             \
+    if (_e != cudaSuccess) return kf_set_err((ctx), KF_ECUDA, "%s: %s (%s:%d)", #call,   \
+                                             cudaGetErrorString(_e), __FILE__, __LINE__); \
+  } while (0)
+#define KF_LAUNCH_CHECK(ctx) KF_CUDA(ctx, cudaGetLastError())
+
+// ---- device helpers ---------------------------------------------------------
+// Squared distance and Gaussian kernel in FP64 with two roundings per term
+// (no FMA contraction), the operation order of the definition in Eq. e:gaussian.
+__device__ __forceinline__ double kf_sqdist64(const double* __restrict__ x, const double* __restrict__ y, int d) {
+  double acc = 0.0;
+  for (int k = 0; k < d; ++k) {
+    double t = __dsub_rn(x[k], y[k]);
+    acc = __dadd_rn(acc, __dmul_rn(t, t));
+  }
+  return acc;
+}
+__device__ __forceinline__ double kf_kern64(const double* x, const double* y, int d, double c_exp) {
+  return exp(__dmul_rn(kf_sqdist64(x, y, d), c_exp));
+}
+__device__ __forceinline__ float kf_kern32(const float* __restrict__ x, const float* __restrict__ y, int d, float c_exp) {
+  float acc = 0.f;
+  for (int k = 0; k < d; ++k) {
+    float t = x[k] - y[k];
+    acc = fmaf(t, t, acc);
+  }
+  return __expf(acc * c_exp);
+}
+
+template <typename T> struct kf_kern;
+template <> struct kf_kern<double> {
+  static __device__ __forceinline__ double eval(const double* X64, const float*, int64_t i, int64_t j, int d, double c) {
+    return kf_kern64(X64 + i * d, X64 + j * d, d, c);
+  }
+};
+template <> struct kf_kern<float> {
+  static __device__ __forceinline__ float eval(const double*, const float* X32, int64_t i, int64_t j, int d, double c) {
+    return kf_kern32(X32 + i * d, X32 + j * d, d, (float)c);
+  }
+};
+
+__host__ __device__ inline int kf_level_of(int a) { return 31 - __builtin_clz((unsigned)a); }
+
+// splitmix64 (Steele, Lea, Flood 2014): golden-ratio increment then the
+// xor-shift-multiply finalizer; used as a counter-based generator.
+__host__ __device__ inline uint64_t kf_splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// ---- launchers implemented in the .cu files ------------------------------------
+kf_status kf_tree_build_device(kf_tree* t, cudaStream_t s);
+kf_status kf_skeletonize_device(kf_factor* f, cudaStream_t s);
+kf_status kf_factorize_device(kf_factor* f, cudaStream_t s);
+kf_status kf_solve_device(kf_factor* f, double* W, int64_t nrhs, int transpose, cudaStream_t s);
+kf_status kf_matvec_device(kf_factor* f, const double* Xin, double* Y, int64_t nrhs, int deriv, cudaStream_t s);

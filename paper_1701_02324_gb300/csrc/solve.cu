@@ -1,0 +1,455 @@
+// solve.cu -- Algorithm 3 (solve), its transpose, the hierarchical operator
+// lambda I + K~ (second form of Eq. e:uv) and dK~/dh, all level by level.
+//
+// Vectors live in tree order as N x k row-major blocks.  Per level l+1 the
+// sweeps are two streaming passes over N x s_max matrices:
+//   colsum:  u[b] = M[b rows, :cnt]^T w[b rows]      (segmented reduction)
+//   rowupd:  w[b rows] += sign * M[b rows, :cnt] v[b] (per-row dot products)
+// with M = VT (the V blocks K_{sib~ b}) or P^ (the W blocks), stored or
+// evaluated on the fly, and a small FP64 solve with Z per parent in between.
+//
+// Forward solve (Algorithm 3, bottom-up): w = L^-T L^-1 b at the leaves; for
+//   each level: g[l] = K_{l~ r} w_r, g[r] = K_{r~ l} w_l; t = Z^-1 [g_l; g_r];
+//   w_l -= P^_l t_top; w_r -= P^_r t_bot.
+// Transpose solve (top-down): t = Z^-T [P^_l^T w_l; P^_r^T w_r];
+//   w_l -= K_{r~ l}^T t_bot; w_r -= K_{l~ r}^T t_top; then the leaves.
+// Operator: leaves (lambda I + K_aa) x; g[c] = K_{c~ sib} x_sib for every
+//   non-root c; pushed down g[children] += P_c g[parent]; y += P_{leaf} g.
+#include <algorithm>
+
+#include "kf_internal.cuh"
+#include "prof.cuh"
+
+namespace {
+
+inline int grid_for(int64_t n, int threads, int cap = 152 * 16) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  return (int)(g < cap ? g : cap);
+}
+
+enum Src { SRC_STORED = 0, SRC_KERNEL = 1, SRC_DKERNEL = 2 };
+
+// Kernel entry (or its h-derivative) between tree positions i and j, FP32
+// evaluation for float matrices, FP64 for double.
+template <typename TM>
+__device__ __forceinline__ double eval_src(int src, const double* X64, const float* X32, int64_t i, int64_t j, int d,
+                                           double c_exp, double inv_h3) {
+  if (sizeof(TM) == 8) {
+    double d2 = kf_sqdist64(X64 + i * d, X64 + j * d, d);
+    double k = exp(d2 * c_exp);
+    return src == SRC_DKERNEL ? k * d2 * inv_h3 : k;
+  } else {
+    const float* x = X32 + i * d;
+    const float* y = X32 + j * d;
+    float acc = 0.f;
+    for (int t = 0; t < d; ++t) {
+      float u = x[t] - y[t];
+      acc = fmaf(u, u, acc);
+    }
+    float k = __expf(acc * (float)c_exp);
+    return src == SRC_DKERNEL ? (double)(k * acc * (float)inv_h3) : (double)k;
+  }
+}
+
+// ---- leaf triangular solves: Y <- L^-T L^-1 Y, Y rows = the leaf's points ----
+template <typename TM, typename TV>
+__global__ void __launch_bounds__(256) k_leaf_solve(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                    int leaf0, int ldL, const TM* __restrict__ Lall,
+                                                    TV* __restrict__ W, int k) {
+  constexpr int NB = 32;
+  __shared__ TM lb[NB][NB + 1];
+  const int lf = blockIdx.x, node = leaf0 + lf;
+  const int b = lo[node], n = hi[node] - b;
+  const TM* L = Lall + (int64_t)lf * ldL * ldL;
+  TV* Y = W + (int64_t)b * k;
+  for (int kb = 0; kb < n; kb += NB) {
+    const int nb = min(NB, n - kb);
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+      int i = e / NB, j = e % NB;
+      lb[i][j] = (i < nb && j <= i) ? L[(int64_t)(kb + i) * ldL + kb + j] : (TM)0;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < k; q += blockDim.x) {
+      TV x[NB];
+#pragma unroll
+      for (int i = 0; i < NB; ++i) x[i] = i < nb ? Y[(int64_t)(kb + i) * k + q] : (TV)0;
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+        if (i < nb) {
+          TV acc = x[i];
+          for (int t = 0; t < i; ++t) acc -= (TV)lb[i][t] * x[t];
+          x[i] = acc / (TV)lb[i][i];
+        }
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+        if (i < nb) Y[(int64_t)(kb + i) * k + q] = x[i];
+    }
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < (int64_t)(n - kb - nb) * k; e += blockDim.x) {
+      int i = kb + nb + (int)(e / k), q = (int)(e % k);
+      const TM* Li = L + (int64_t)i * ldL + kb;
+      TV acc = (TV)0;
+      for (int t = 0; t < nb; ++t) acc += (TV)Li[t] * Y[(int64_t)(kb + t) * k + q];
+      Y[(int64_t)i * k + q] -= acc;
+    }
+    __syncthreads();
+  }
+  for (int kb = ((n - 1) / NB) * NB; kb >= 0 && n > 0; kb -= NB) {
+    const int nb = min(NB, n - kb);
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+      int i = e / NB, j = e % NB;
+      lb[i][j] = (i < nb && j <= i) ? L[(int64_t)(kb + i) * ldL + kb + j] : (TM)0;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < k; q += blockDim.x) {
+      TV x[NB];
+#pragma unroll
+      for (int i = 0; i < NB; ++i) x[i] = i < nb ? Y[(int64_t)(kb + i) * k + q] : (TV)0;
+#pragma unroll
+      for (int i = NB - 1; i >= 0; --i)
+        if (i < nb) {
+          TV acc = x[i];
+          for (int t = i + 1; t < nb; ++t) acc -= (TV)lb[t][i] * x[t];
+          x[i] = acc / (TV)lb[i][i];
+        }
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+        if (i < nb) Y[(int64_t)(kb + i) * k + q] = x[i];
+    }
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < (int64_t)kb * k; e += blockDim.x) {
+      int i = (int)(e / k), q = (int)(e % k);
+      TV acc = (TV)0;
+      for (int t = 0; t < nb; ++t) acc += (TV)L[(int64_t)(kb + t) * ldL + i] * Y[(int64_t)(kb + t) * k + q];
+      Y[(int64_t)i * k + q] -= acc;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- segmented column sums -------------------------------------------------------
+// For every node b of a level (grid.y) and a chunk of its rows (grid.x):
+// u[dst(b)][q][r] += sum_i M[i][q] w[i][r], q < cnt(b).  Sibling mode: the
+// columns are the sibling's skeleton (cnt = rank[sib], dst = sib); own mode:
+// cnt = rank[b], dst = b.  u is FP64 [node][s_max][k].
+constexpr int kRowsPerChunk = 128;
+
+template <typename TM, typename TV, int kMaxK>
+__global__ void __launch_bounds__(256) k_colsum(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                const int32_t* __restrict__ rank, const int32_t* __restrict__ skel,
+                                                int node0, int s_max, int sibling_mode, int src,
+                                                const TM* __restrict__ M, const double* __restrict__ X64,
+                                                const float* __restrict__ X32, int d, double c_exp, double inv_h3,
+                                                const TV* __restrict__ W, int k, double* __restrict__ U) {
+  __shared__ TV ws[kRowsPerChunk][kMaxK];
+  const int nl = blockIdx.y, node = node0 + nl, sib = node ^ 1;
+  const int b = lo[node], n = hi[node] - b;
+  const int cnt = sibling_mode ? rank[sib] : rank[node];
+  const int dst = sibling_mode ? sib : node;
+  const int r0 = blockIdx.x * kRowsPerChunk;
+  if (r0 >= n || cnt == 0) return;
+  const int r1 = min(n, r0 + kRowsPerChunk);
+  const int32_t* sk = skel + (int64_t)sib * s_max;
+  for (int kb = 0; kb < k; kb += kMaxK) {
+    const int kk = min(kMaxK, k - kb);
+    __syncthreads();
+    for (int e = threadIdx.x; e < (r1 - r0) * kMaxK; e += blockDim.x) {
+      int i = e / kMaxK, r = e % kMaxK;
+      ws[i][r] = r < kk ? W[(int64_t)(b + r0 + i) * k + kb + r] : (TV)0;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+      TV acc[kMaxK];
+#pragma unroll
+      for (int r = 0; r < kMaxK; ++r) acc[r] = (TV)0;
+      for (int i = r0; i < r1; ++i) {
+        TV m;
+        if (src == SRC_STORED) m = (TV)M[(int64_t)(b + i) * s_max + q];
+        else m = (TV)eval_src<TM>(src, X64, X32, b + i, sk[q], d, c_exp, inv_h3);
+#pragma unroll
+        for (int r = 0; r < kMaxK; ++r) acc[r] += m * ws[i - r0][r];
+      }
+      double* out = U + ((int64_t)dst * s_max + q) * k + kb;
+      for (int r = 0; r < kk; ++r) atomicAdd(out + r, (double)acc[r]);
+    }
+  }
+}
+
+template <typename TM, typename TV>
+void launch_colsum(dim3 g, cudaStream_t s, const int32_t* lo, const int32_t* hi, const int32_t* rank,
+                   const int32_t* skel, int node0, int s_max, int sib, int src, const TM* M, const double* X64,
+                   const float* X32, int d, double c_exp, double inv_h3, const TV* W, int k, double* U) {
+  if (k == 1)
+    KF_PHASE(KF_PH_S_COLSUM, s, k_colsum<TM, TV, 1><<<g, 256, 0, s>>>(lo, hi, rank, skel, node0, s_max, sib, src, M, X64, X32, d, c_exp, inv_h3,
+                                          W, k, U));
+  else
+    KF_PHASE(KF_PH_S_COLSUM, s, k_colsum<TM, TV, 8><<<g, 256, 0, s>>>(lo, hi, rank, skel, node0, s_max, sib, src, M, X64, X32, d, c_exp, inv_h3,
+                                          W, k, U));
+}
+
+// ---- row updates: w[i][r] += sign * sum_q M[i][q] v[src(b)][q][r] ------------------
+template <typename TM, typename TV>
+__global__ void __launch_bounds__(256) k_rowupd(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                const int32_t* __restrict__ rank, const int32_t* __restrict__ skel,
+                                                int node0, int nnodes_level, int s_max, int sibling_mode, int src,
+                                                const TM* __restrict__ M, const double* __restrict__ X64,
+                                                const float* __restrict__ X32, int d, double c_exp, double inv_h3,
+                                                const double* __restrict__ V, double sign, TV* __restrict__ W, int k) {
+  // one warp per row
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nl = blockIdx.y, node = node0 + nl, sib = node ^ 1;
+  const int b = lo[node], n = hi[node] - b;
+  const int cnt = sibling_mode ? rank[sib] : rank[node];
+  const int from = sibling_mode ? sib : node;
+  if (cnt == 0) return;
+  const int32_t* sk = skel + (int64_t)sib * s_max;
+  const double* v = V + (int64_t)from * s_max * k;
+  for (int i = warp; i < n; i += (gridDim.x * blockDim.x) >> 5) {
+    for (int r = 0; r < k; ++r) {
+      double acc = 0.0;
+      for (int q = lane; q < cnt; q += 32) {
+        double m = (src == SRC_STORED) ? (double)M[(int64_t)(b + i) * s_max + q]
+                                       : eval_src<TM>(src, X64, X32, b + i, sk[q], d, c_exp, inv_h3);
+        acc += m * v[(int64_t)q * k + r];
+      }
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (lane == 0) W[(int64_t)(b + i) * k + r] += (TV)(sign * acc);
+    }
+  }
+}
+
+// ---- reduced systems: out[l], out[r] <- Z^-1 [in[l]; in[r]] (or Z^-T) ---------------
+__global__ void __launch_bounds__(256) k_zsolve(const int32_t* __restrict__ rank, int node0, int ldz, int s_max,
+                                                const double* __restrict__ ZLU, const int32_t* __restrict__ piv,
+                                                const double* __restrict__ in, double* __restrict__ out, int k,
+                                                int transpose) {
+  extern __shared__ double t[];  // ldz
+  const int nl = blockIdx.x, node = node0 + nl;
+  const int l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], z = sl + sr;
+  const double* A = ZLU + (int64_t)node * ldz * ldz;
+  const int32_t* pv = piv + (int64_t)node * ldz;
+  const int tid = threadIdx.x;
+  for (int c = 0; c < k; ++c) {
+    for (int i = tid; i < z; i += blockDim.x)
+      t[i] = i < sl ? in[((int64_t)l * s_max + i) * k + c] : in[((int64_t)r * s_max + (i - sl)) * k + c];
+    __syncthreads();
+    if (!transpose) {
+      if (tid == 0)
+        for (int i = 0; i < z; ++i)
+          if (pv[i] != i) { double a = t[i]; t[i] = t[pv[i]]; t[pv[i]] = a; }
+      __syncthreads();
+      // L (unit lower), column-oriented
+      for (int j = 0; j < z; ++j) {
+        double tj = t[j];
+        for (int i = j + 1 + tid; i < z; i += blockDim.x) t[i] -= A[(int64_t)i * ldz + j] * tj;
+        __syncthreads();
+      }
+      for (int j = z - 1; j >= 0; --j) {
+        if (tid == 0) t[j] /= A[(int64_t)j * ldz + j];
+        __syncthreads();
+        double tj = t[j];
+        for (int i = tid; i < j; i += blockDim.x) t[i] -= A[(int64_t)i * ldz + j] * tj;
+        __syncthreads();
+      }
+    } else {
+      // U^T y = b (forward), then L^T x = y (backward), then undo the pivots
+      for (int j = 0; j < z; ++j) {
+        if (tid == 0) t[j] /= A[(int64_t)j * ldz + j];
+        __syncthreads();
+        double tj = t[j];
+        for (int i = j + 1 + tid; i < z; i += blockDim.x) t[i] -= A[(int64_t)j * ldz + i] * tj;
+        __syncthreads();
+      }
+      for (int j = z - 1; j >= 0; --j) {
+        double tj = t[j];
+        for (int i = tid; i < j; i += blockDim.x) t[i] -= A[(int64_t)j * ldz + i] * tj;
+        __syncthreads();
+      }
+      if (tid == 0)
+        for (int i = z - 1; i >= 0; --i)
+          if (pv[i] != i) { double a = t[i]; t[i] = t[pv[i]]; t[pv[i]] = a; }
+      __syncthreads();
+    }
+    for (int i = tid; i < z; i += blockDim.x) {
+      if (i < sl) out[((int64_t)l * s_max + i) * k + c] = t[i];
+      else out[((int64_t)r * s_max + (i - sl)) * k + c] = t[i];
+    }
+    __syncthreads();
+  }
+}
+
+// ---- operator pieces ------------------------------------------------------------
+// Leaf blocks: y_i = lambda x_i + sum_j K(x_i, x_j) x_j (or dK/dh, no lambda).
+template <typename TM>
+__global__ void __launch_bounds__(128) k_leaf_mv(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                 int leaf0, const double* __restrict__ X64,
+                                                 const float* __restrict__ X32, int d, double c_exp, double inv_h3,
+                                                 int src, double lambda, const double* __restrict__ x,
+                                                 double* __restrict__ y, int k) {
+  const int lf = blockIdx.y, node = leaf0 + lf;
+  const int b = lo[node], n = hi[node] - b;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int r = 0; r < k; ++r) {
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j) acc += eval_src<TM>(src, X64, X32, b + i, b + j, d, c_exp, inv_h3) * x[(int64_t)(b + j) * k + r];
+    y[(int64_t)(b + i) * k + r] = (src == SRC_DKERNEL ? 0.0 : lambda * x[(int64_t)(b + i) * k + r]) + acc;
+  }
+}
+
+// Push skeleton coefficients down: g[l] += P_c[:s_l] g[a], g[r] += P_c[s_l:] g[a].
+__global__ void k_push_down(const int32_t* __restrict__ rank, int node0, int s_max, const double* __restrict__ Pc,
+                            double* __restrict__ G, int k) {
+  const int nl = blockIdx.x, node = node0 + nl;
+  const int l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], s = rank[node];
+  const double* P = Pc + (int64_t)node * 2 * s_max * s_max;
+  const double* ga = G + (int64_t)node * s_max * k;
+  for (int e = threadIdx.x; e < (sl + sr) * k; e += blockDim.x) {
+    int i = e / k, c = e % k;
+    double acc = 0.0;
+    for (int q = 0; q < s; ++q) acc += P[(int64_t)i * s_max + q] * ga[(int64_t)q * k + c];
+    double* dst = i < sl ? G + ((int64_t)l * s_max + i) * k + c : G + ((int64_t)r * s_max + (i - sl)) * k + c;
+    *dst += acc;
+  }
+}
+
+template <typename TV>
+__global__ void k_axpy_cast(const double* __restrict__ a, TV* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (TV)a[i];
+}
+template <typename TV>
+__global__ void k_cast_back(const TV* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+// ---- drivers -------------------------------------------------------------------------
+template <typename TM, typename TV>
+kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, double* Vb, cudaStream_t s) {
+  kf_tree* t = f->t;
+  kf_ctx* c = f->ctx;
+  const int D = t->D, s_max = f->s_max, ldz = 2 * s_max;
+  const int64_t N = t->N;
+  const TM* L = (const TM*)f->L;
+  const TM* Phat = (const TM*)f->Phat;
+  const TM* VT = (const TM*)f->VT;
+  auto lvl = [&](const TM* base, int l) { return base + (int64_t)(l - 1) * N * s_max; };
+  const int leaf0 = 1 << D;
+  const size_t ubytes = sizeof(double) * (size_t)(t->nnodes + 1) * s_max * k;
+  const double inv_h3 = 1.0 / (f->h * f->h * f->h);
+  const int vsrc = f->vstore == KF_V_STORED ? SRC_STORED : SRC_KERNEL;
+  if (!transpose) {
+    KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve<TM, TV><<<1 << D, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
+    for (int l = D - 1; l >= 0; --l) {
+      const int c0 = 1 << (l + 1), nc = 1 << (l + 1);
+      const int64_t rows = (N >> (l + 1)) + 1;
+      KF_CUDA(c, cudaMemsetAsync(U, 0, ubytes, s));
+      dim3 gc((unsigned)((rows + kRowsPerChunk - 1) / kRowsPerChunk), nc);
+      launch_colsum<TM, TV>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 1, vsrc, lvl(VT, l + 1), t->X64,
+                            t->X32, t->d, f->c_exp, inv_h3, W, (int)k, U);
+      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<1 << l, 256, sizeof(double) * ldz, s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv, U, Vb,
+                                                         (int)k, 0));
+      dim3 gr((unsigned)std::min<int64_t>((rows * 32 + 255) / 256, 1024), nc);
+      KF_PHASE(KF_PH_S_ROWUPD, s, k_rowupd<TM, TV><<<gr, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, c0, nc, s_max, 0, SRC_STORED,
+                                          lvl(Phat, l + 1), t->X64, t->X32, t->d, f->c_exp, inv_h3, Vb, -1.0, W,
+                                          (int)k));
+    }
+  } else {
+    for (int l = 0; l < D; ++l) {
+      const int c0 = 1 << (l + 1), nc = 1 << (l + 1);
+      const int64_t rows = (N >> (l + 1)) + 1;
+      KF_CUDA(c, cudaMemsetAsync(U, 0, ubytes, s));
+      dim3 gc((unsigned)((rows + kRowsPerChunk - 1) / kRowsPerChunk), nc);
+      launch_colsum<TM, TV>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 0, SRC_STORED, lvl(Phat, l + 1),
+                            t->X64, t->X32, t->d, f->c_exp, inv_h3, W, (int)k, U);
+      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<1 << l, 256, sizeof(double) * ldz, s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv, U, Vb,
+                                                         (int)k, 1));
+      dim3 gr((unsigned)std::min<int64_t>((rows * 32 + 255) / 256, 1024), nc);
+      KF_PHASE(KF_PH_S_ROWUPD, s, k_rowupd<TM, TV><<<gr, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, c0, nc, s_max, 1, vsrc,
+                                          lvl(VT, l + 1), t->X64, t->X32, t->d, f->c_exp, inv_h3, Vb, -1.0, W,
+                                          (int)k));
+    }
+    KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve<TM, TV><<<1 << D, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
+  }
+  KF_LAUNCH_CHECK(c);
+  return KF_OK;
+}
+
+template <typename TM>
+kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deriv, double* G, cudaStream_t s) {
+  kf_tree* t = f->t;
+  kf_ctx* c = f->ctx;
+  const int D = t->D, s_max = f->s_max;
+  const int64_t N = t->N;
+  const TM* VT = (const TM*)f->VT;
+  const int leaf0 = 1 << D;
+  const double inv_h3 = 1.0 / (f->h * f->h * f->h);
+  const int src = deriv ? SRC_DKERNEL : (f->vstore == KF_V_STORED ? SRC_STORED : SRC_KERNEL);
+  dim3 gl((t->leaf_max + 127) / 128, 1 << D);
+  KF_PHASE(KF_PH_MV_LEAF, s, k_leaf_mv<TM><<<gl, 128, 0, s>>>(t->d_lo, t->d_hi, leaf0, t->X64, t->X32, t->d, f->c_exp, inv_h3,
+                                   deriv ? SRC_DKERNEL : SRC_KERNEL, f->lambda, x, y, (int)k));
+  if (D == 0) { KF_LAUNCH_CHECK(c); return KF_OK; }
+  KF_CUDA(c, cudaMemsetAsync(G, 0, sizeof(double) * (size_t)(t->nnodes + 1) * s_max * k, s));
+  for (int l = 1; l <= D; ++l) {
+    const int64_t rows = (N >> l) + 1;
+    dim3 gc((unsigned)((rows + kRowsPerChunk - 1) / kRowsPerChunk), 1 << l);
+    launch_colsum<TM, double>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, s_max, 1, src,
+                              VT + (int64_t)(l - 1) * N * s_max, t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G);
+  }
+  for (int l = 1; l < D; ++l)
+    KF_PHASE(KF_PH_MV_PUSH, s, k_push_down<<<1 << l, 256, 0, s>>>(f->rank, 1 << l, s_max, f->Pc, G, (int)k));
+  const int64_t rows = (N >> D) + 1;
+  dim3 gr((unsigned)std::min<int64_t>((rows * 32 + 255) / 256, 1024), 1 << D);
+  KF_PHASE(KF_PH_S_ROWUPD, s, k_rowupd<double, double><<<gr, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, leaf0, 1 << D, s_max, 0,
+                                              SRC_STORED, f->Pleaf, t->X64, t->X32, t->d, f->c_exp, inv_h3, G, 1.0,
+                                              y, (int)k));
+  KF_LAUNCH_CHECK(c);
+  return KF_OK;
+}
+
+}  // namespace
+
+// W: N x k FP64 in tree order; solved in place.  The mixed path runs the sweep
+// on an FP32 copy.
+kf_status kf_solve_device(kf_factor* f, double* W, int64_t k, int transpose, cudaStream_t s) {
+  kf_ctx* c = f->ctx;
+  const int64_t N = f->t->N;
+  const size_t ub = sizeof(double) * (size_t)(f->t->nnodes + 1) * f->s_max * k;
+  double* U = (double*)c->dalloc(ub, s);
+  double* Vb = (double*)c->dalloc(ub, s);
+  if (!U || !Vb) {
+    c->dfree(U, ub, s);
+    c->dfree(Vb, ub, s);
+    return kf_set_err(c, KF_ENOMEM, "solve: allocation failed");
+  }
+  kf_status st;
+  if (f->prec == KF_PREC_FP64) {
+    st = solve_t<double, double>(f, W, k, transpose, U, Vb, s);
+  } else {
+    float* W32 = (float*)c->dalloc(sizeof(float) * N * k, s);
+    if (!W32) {
+      st = kf_set_err(c, KF_ENOMEM, "solve: allocation failed");
+    } else {
+      KF_PHASE(KF_PH_MISC, s, k_axpy_cast<float><<<grid_for(N * k, 256), 256, 0, s>>>(W, W32, N * k));
+      st = solve_t<float, float>(f, W32, k, transpose, U, Vb, s);
+      KF_PHASE(KF_PH_MISC, s, k_cast_back<float><<<grid_for(N * k, 256), 256, 0, s>>>(W32, W, N * k));
+      c->dfree(W32, sizeof(float) * N * k, s);
+    }
+  }
+  c->dfree(U, ub, s);
+  c->dfree(Vb, ub, s);
+  return st;
+}
+
+kf_status kf_matvec_device(kf_factor* f, const double* x, double* y, int64_t k, int deriv, cudaStream_t s) {
+  kf_ctx* c = f->ctx;
+  const size_t gb = sizeof(double) * (size_t)(f->t->nnodes + 1) * f->s_max * k;
+  double* G = (double*)c->dalloc(gb, s);
+  if (!G) return kf_set_err(c, KF_ENOMEM, "matvec: allocation failed");
+  kf_status st = f->prec == KF_PREC_FP64 ? matvec_t<double>(f, x, y, k, deriv, G, s)
+                                         : matvec_t<float>(f, x, y, k, deriv, G, s);
+  c->dfree(G, gb, s);
+  return st;
+}

@@ -1,0 +1,38 @@
+"""The C ABI library builds for sm_103a and exports every entry point that
+include/kf.h declares (no GPU needed)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1701_02324_gb300 import _abi, _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "kf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(kf_[A-Za-z_0-9]+)\s*\(", src)))
+
+
+def test_library_builds_and_exports_declared_symbols():
+    lib = _build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (kf_[A-Za-z_0-9]+)", out))
+    decl = declared_symbols()
+    assert decl, "no declarations found"
+    missing = [s for s in decl if s not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_ctypes_signatures_cover_header():
+    assert sorted(_abi.SIGNATURES) == declared_symbols()
+
+
+def test_library_loads_without_gpu():
+    lib = _abi.load()
+    assert lib.kf_status_string(4) == b"KF_EILLCOND"
+    assert lib.kf_status_string(0) == b"KF_OK"
+

@@ -1,0 +1,219 @@
+"""CUDA path vs the CPU oracle, through the C ABI (needs a GB300).
+
+Bars (stated per test): tree permutation bit-exact; skeleton lists exact
+where the pivoted QR takes the same pivots (reduction order may flip a near
+tie, so agreement is counted and the factorization is also checked with the
+oracle's skeletons imported); FP64 path within 1e-10 relative of the oracle;
+mixed path within 1e-5 relative after refinement.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # collected on CPU hosts, skipped there
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_1701_02324_gb300 as kf  # noqa: E402
+from paper_1701_02324_gb300 import inputs  # noqa: E402
+
+FP64, MIXED = kf.KF_PREC_FP64, kf.KF_PREC_MIXED
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def ids_from_oracle(o, smax):
+    nn = o.nnodes
+    leaf_max = max(o.node_range(a)[1] - o.node_range(a)[0] for a in range(1 << o.D, 1 << (o.D + 1)))
+    cmax = max(leaf_max, 2 * smax)
+    ranks = np.zeros(nn + 1, np.int32)
+    skel = np.zeros((nn + 1) * smax, np.int64)
+    P = np.zeros((nn + 1) * smax * cmax)
+    for a in range(2, nn + 1):
+        s = o.rank(a)
+        ranks[a] = s
+        skel[a * smax: a * smax + s] = o.skel(a)
+        Pa = o.P(a)
+        P[a * smax * cmax: a * smax * cmax + Pa.size] = Pa.ravel()
+    return ranks, skel, P
+
+
+def problem(N, d, seed=0):
+    rng = np.random.default_rng(seed)
+    return rng.random((N, d)), rng.standard_normal(N)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    p = inputs.plain_fp64()
+    o = oracle.Oracle(p.X, p.m)
+    o.skeletonize(p.h, p.tau, p.s_max)
+    o.factorize(p.lam)
+    tree = kf.Tree(torch.from_numpy(p.X).cuda(), p.m)
+    return p, o, tree
+
+
+# ---------------------------------------------------------------- tree
+@pytest.mark.parametrize("N,d,m", [(4096, 8, 256), (5000, 4, 300), (777, 1, 50), (3, 2, 1), (100, 3, 1000),
+                                   (65536, 8, 512), (70001, 28, 1024)])
+def test_tree_permutation_bit_exact(N, d, m):
+    X, _ = problem(N, d, seed=N)
+    tree = kf.Tree(torch.from_numpy(X).cuda(), m)
+    o = oracle.Oracle(X, m)
+    assert tree.D == o.D
+    assert np.array_equal(tree.perm().cpu().numpy(), o.perm())
+
+
+def test_tree_from_float32_host_input():
+    X, _ = problem(3000, 5, seed=1)
+    X32 = X.astype(np.float32)
+    tree = kf.Tree(torch.from_numpy(X32), 100)           # host tensor, FP32
+    o = oracle.Oracle(X32.astype(np.float64), 100)
+    assert np.array_equal(tree.perm().cpu().numpy(), o.perm())
+
+
+# ---------------------------------------------------------------- skeletons
+def test_skeletons_match_oracle(c1):
+    p, o, tree = c1
+    F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=FP64)
+    r = F.ranks()
+    nodes = range(2, o.nnodes + 1)
+    same_rank = sum(int(r[a]) == o.rank(a) for a in nodes)
+    same = sum(np.array_equal(F.skeleton(a), o.skel(a)) for a in nodes)
+    assert same_rank == len(nodes)
+    assert same == len(nodes)
+    for a in nodes:
+        np.testing.assert_allclose(F.P(a, o.ncols(a)), o.P(a), rtol=0, atol=1e-9 * max(1, np.abs(o.P(a)).max()))
+
+
+# ---------------------------------------------------------------- factorization and solve
+def test_fp64_solve_end_to_end(c1):
+    p, o, tree = c1
+    F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=FP64)
+    b = p.B[:, 0]
+    x, info = F.solve(torch.from_numpy(b).cuda(), info=True)
+    assert rel(x.cpu().numpy(), o.solve(b)) <= 1e-10
+    assert info["eps_r"] <= 1e-10
+
+
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-5)])
+def test_factorization_with_oracle_ids(c1, prec, tol):
+    p, o, tree = c1
+    ranks, skel, P = ids_from_oracle(o, p.s_max)
+    F = kf.factorize_with_ids(tree, p.h, p.lam, p.s_max, ranks, skel, P, precision=prec)
+    for a in range(2, o.nnodes + 1):
+        lo, hi = o.node_range(a)
+        Po = o.Phat(a)
+        ptol = 1e-10 if prec == FP64 else 1e-4
+        assert np.abs(F.Phat(a, hi - lo) - Po).max() <= ptol * max(1.0, np.abs(Po).max())
+    b = p.B[:, 0]
+    x = F.solve(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert rel(x, o.solve(b)) <= tol
+
+
+def test_matvec_transpose_and_grad_parity(c1):
+    p, o, tree = c1
+    ranks, skel, P = ids_from_oracle(o, p.s_max)
+    F = kf.factorize_with_ids(tree, p.h, p.lam, p.s_max, ranks, skel, P, precision=FP64)
+    b = p.B[:, 0]
+    bt = torch.from_numpy(b).cuda()
+    assert rel(F.matvec(bt).cpu().numpy(), o.matvec(b)) <= 1e-12
+    assert rel(F.solve(bt, transpose=True).cpu().numpy(), o.solve(b, transpose=True)) <= 1e-10
+    xo = o.solve(b)
+    y = np.random.default_rng(5).standard_normal(p.N)
+    g = 2 * (xo - y)
+    db, dl, dh = F.grad(torch.from_numpy(xo).cuda(), torch.from_numpy(g).cuda())
+    dbo, dlo, dho = o.grad(xo, g)
+    assert rel(db.cpu().numpy(), dbo) <= 1e-10
+    assert abs(dl - dlo) <= 1e-10 * abs(dlo)
+    assert abs(dh - dho) <= 1e-9 * abs(dho)
+
+
+def test_multiple_rhs_and_float32(c1):
+    p, o, tree = c1
+    F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=FP64)
+    B = np.random.default_rng(2).standard_normal((p.N, 5))
+    X = F.solve(torch.from_numpy(B).cuda()).cpu().numpy()
+    Xo = o.solve(B)
+    assert rel(X, Xo) <= 1e-10
+    X32 = F.solve(torch.from_numpy(B.astype(np.float32))).numpy()   # host FP32 in and out
+    assert rel(X32, Xo) <= 1e-6
+
+
+def test_mixed_path_refined(c1):
+    p, o, tree = c1
+    F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=MIXED, refine_tol=1e-10)
+    b = p.B[:, 0]
+    x, info = F.solve(torch.from_numpy(b).cuda(), info=True)
+    same = all(np.array_equal(F.skeleton(a), o.skel(a)) for a in range(2, o.nnodes + 1))
+    assert same
+    assert rel(x.cpu().numpy(), o.solve(b)) <= 1e-5
+    assert info["eps_r"] <= 1e-10
+
+
+# ---------------------------------------------------------------- edge cases
+def test_single_leaf_is_dense_solve():
+    X, b = problem(300, 2, seed=4)
+    tree = kf.Tree(torch.from_numpy(X).cuda(), 400)
+    assert tree.D == 0
+    F = kf.Factor(tree, 0.5, 1.0, 1e-6, 16)
+    o = oracle.Oracle(X, 400)
+    o.skeletonize(0.5, 1e-6, 16)
+    o.factorize(1.0)
+    assert rel(F.solve(torch.from_numpy(b).cuda()).cpu().numpy(), o.solve(b)) <= 1e-12
+
+
+def test_ragged_sizes():
+    X, b = problem(5000, 4, seed=6)
+    o = oracle.Oracle(X, 300)
+    o.skeletonize(0.4, 1e-5, 48)
+    o.factorize(0.5)
+    tree = kf.Tree(torch.from_numpy(X).cuda(), 300)
+    ranks, skel, P = ids_from_oracle(o, 48)
+    F = kf.factorize_with_ids(tree, 0.4, 0.5, 48, ranks, skel, P)
+    assert rel(F.solve(torch.from_numpy(b).cuda()).cpu().numpy(), o.solve(b)) <= 1e-10
+
+
+def test_small_h_limit_is_diagonal():
+    X, b = problem(2048, 3, seed=7)
+    tree = kf.Tree(torch.from_numpy(X).cuda(), 128)
+    F = kf.Factor(tree, 1e-4, 0.5, 1e-6, 32)
+    assert int(F.ranks().max()) == 0
+    np.testing.assert_allclose(F.solve(torch.from_numpy(b).cuda()).cpu().numpy(), b / 1.5, rtol=1e-15, atol=0)
+
+
+def test_large_h_limit_is_rank_one():
+    X, b = problem(2048, 3, seed=8)
+    tree = kf.Tree(torch.from_numpy(X).cuda(), 128)
+    lam = 2.0
+    F = kf.Factor(tree, 1e10, lam, 1e-8, 32)
+    r = F.ranks()
+    assert (r[2:] == 1).all()
+    xref = (b - b.sum() / (lam + 2048)) / lam
+    assert rel(F.solve(torch.from_numpy(b).cuda()).cpu().numpy(), xref) <= 1e-12
+
+
+def test_illconditioned_reported():
+    X, _ = problem(512, 3, seed=9)
+    X[1] = X[0]
+    tree = kf.Tree(torch.from_numpy(X).cuda(), 64)
+    F = kf.Factor(tree, 0.5, 0.0, 1e-6, 16)
+    assert F.status == kf._abi.KF_EILLCOND
+
+
+def test_invalid_arguments_rejected():
+    X, _ = problem(100, 2, seed=10)
+    Xbad = X.copy()
+    Xbad[3, 1] = np.nan
+    with pytest.raises(kf.KFError) as e:
+        kf.Tree(torch.from_numpy(Xbad).cuda(), 10)
+    assert e.value.status == kf._abi.KF_EINVAL
+    tree = kf.Tree(torch.from_numpy(X).cuda(), 10)
+    for h, lam, smax in [(0.0, 1.0, 8), (-1.0, 1.0, 8), (0.5, -1.0, 8), (0.5, 1.0, 0), (0.5, 1.0, 4096)]:
+        with pytest.raises(kf.KFError) as e:
+            kf.Factor(tree, h, lam, 1e-6, smax)
+        assert e.value.status == kf._abi.KF_EINVAL
