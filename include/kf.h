@@ -176,6 +176,31 @@ kf_status kf_factorize_with_ids(kf_tree* t, double h, double lambda, int32_t s_m
                                 const int64_t* skel, const double* P, const kf_opts* opts, void* stream,
                                 kf_factor** out);
 
+/* ---- allocation-free variant ------------------------------------------------------ */
+/* Ball-tree permutation (the same tree as kf_tree_build) computed without
+ * allocating any device memory.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate, for example code that runs
+ * inside a device-memory allocator's own callback (re-entering the allocator
+ * would deadlock or recurse), latency-bound loops in which cudaMalloc would
+ * synchronize the device, or processes whose device memory is entirely
+ * reserved by another framework's pool, where a cudaMalloc fails.
+ *
+ * X:    device, N x d FP64 row-major, original order (read only).
+ * Xt:   device output, N x d FP64, the points in tree order.
+ * perm: device output, N int64, perm[i] = original index of tree position i.
+ * Limits: 1 <= N <= 65536, 1 <= d, N * d <= 2^19, m >= 1; larger sizes are
+ * rejected with KF_EINVAL and a message in kf_last_error(NULL).
+ * Scratch: one 12 MiB file-scope device array that every GPU loading the
+ * library holds until the process exits.  Every call shares it and it keeps
+ * the previous call's contents (the call initializes what it reads), so calls
+ * whose GPU work overlaps (different streams, devices used concurrently from
+ * several threads) race and must be serialized by the caller.  The first call
+ * on each device looks up the array's device address on the current device;
+ * make that first call before any stream capture.  The call synchronizes
+ * `stream` once to read the finiteness check of X. */
+kf_status kf_tree_perm_noalloc(const double* X, int64_t N, int32_t d, int32_t m, double* Xt, int64_t* perm,
+                               void* stream);
+
 /* ---- diagnostics ------------------------------------------------------------- */
 /* Number of kernel launches this process has made through the library. */
 int64_t kf_launch_count(void);

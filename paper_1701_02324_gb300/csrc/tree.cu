@@ -320,3 +320,144 @@ kf_status kf_tree_build_device(kf_tree* t, cudaStream_t s) {
   c->dfree(ia, sizeof(int32_t) * 3 * maxnodes, s);
   return st;
 }
+
+// ---- allocation-free variant of the tree build ------------------------------------
+//
+// kf_tree_perm_noalloc runs the same kernels as kf_tree_build_device but takes
+// every scratch buffer from one file-scope device array instead of the
+// allocator, and uses the caller's outputs as the other half of each
+// ping-pong pair.  Limits: N <= 65536 and N * d <= 2^19, which keep the
+// array at 12 MiB (held by every GPU that loads the library until exit).
+namespace {
+
+constexpr int64_t kNoAllocMaxN = 65536;
+constexpr int64_t kNoAllocMaxND = int64_t(1) << 19;
+constexpr size_t kNoAllocBytes = size_t(12) << 20;
+
+__global__ void k_node_ranges(int64_t N, int D, int32_t* __restrict__ lo, int32_t* __restrict__ hi) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  lo[1] = 0;
+  hi[1] = (int32_t)N;
+  for (int a = 1; a < (1 << D); ++a) {
+    int32_t n = hi[a] - lo[a], mid = lo[a] + n / 2;
+    lo[2 * a] = lo[a];
+    hi[2 * a] = mid;
+    lo[2 * a + 1] = mid;
+    hi[2 * a + 1] = hi[a];
+  }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char kf_noalloc_tree_scratch[kNoAllocBytes];
+
+extern "C" kf_status kf_tree_perm_noalloc(const double* X, int64_t N, int32_t d, int32_t m, double* Xt,
+                                          int64_t* perm, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!X || !Xt || !perm) return kf_set_err(nullptr, KF_EINVAL, "kf_tree_perm_noalloc: NULL pointer");
+  if (N < 1 || N > kNoAllocMaxN)
+    return kf_set_err(nullptr, KF_EINVAL, "kf_tree_perm_noalloc: N = %lld outside [1, %lld]", (long long)N,
+                      (long long)kNoAllocMaxN);
+  if (d < 1 || (int64_t)N * d > kNoAllocMaxND)
+    return kf_set_err(nullptr, KF_EINVAL, "kf_tree_perm_noalloc: N * d = %lld exceeds %lld (or d < 1)",
+                      (long long)N * d, (long long)kNoAllocMaxND);
+  if (m < 1) return kf_set_err(nullptr, KF_EINVAL, "kf_tree_perm_noalloc: m must be >= 1");
+  // device address of the scratch array, looked up once per device
+  static void* dev_ptr[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+    return kf_set_err(nullptr, KF_ECUDA, "kf_tree_perm_noalloc: no current device");
+  if (!dev_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, kf_noalloc_tree_scratch);
+    if (e != cudaSuccess)
+      return kf_set_err(nullptr, KF_ECUDA, "kf_tree_perm_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    dev_ptr[dev] = p;
+  }
+  int D = 0;
+  while (((int64_t)m << D) < N) ++D;
+  const int nnodes = (1 << (D + 1)) - 1;
+  int64_t segmax = 1;
+  while (segmax < N) segmax <<= 1;
+  const int64_t vcap = 2 * segmax;
+  const int maxnodes = D > 0 ? 1 << (D - 1) : 1;
+  const int64_t part_cap = (N + kChunk - 1) / kChunk + 2 + 2 * (int64_t)maxnodes;
+  // carve the scratch array
+  unsigned char* base = (unsigned char*)dev_ptr[dev];
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    unsigned char* q = base + off;
+    off = align256(off + bytes);
+    return q;
+  };
+  double* Xb = (double*)take(sizeof(double) * N * d);
+  int64_t* pb = (int64_t*)take(sizeof(int64_t) * N);
+  double* key = (double*)take(sizeof(double) * vcap);
+  int64_t* orig = (int64_t*)take(sizeof(int64_t) * vcap);
+  int32_t* pos = (int32_t*)take(sizeof(int32_t) * vcap);
+  Cand* part = (Cand*)take(sizeof(Cand) * part_cap);
+  int32_t* ia = (int32_t*)take(sizeof(int32_t) * 3 * maxnodes);
+  int32_t* lo = (int32_t*)take(sizeof(int32_t) * (nnodes + 1));
+  int32_t* hi = (int32_t*)take(sizeof(int32_t) * (nnodes + 1));
+  int32_t* bad = (int32_t*)take(sizeof(int32_t));
+  if (off > kNoAllocBytes)
+    return kf_set_err(nullptr, KF_EINVAL, "kf_tree_perm_noalloc: scratch of %zu bytes needed, %zu available", off,
+                      kNoAllocBytes);
+  // inputs: copy X into the caller's output, check it, node ranges, identity order
+  if (cudaMemcpyAsync(Xt, X, sizeof(double) * N * d, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(bad, 0, sizeof(int32_t), s) != cudaSuccess)
+    return kf_set_err(nullptr, KF_ECUDA, "kf_tree_perm_noalloc: %s", cudaGetErrorString(cudaGetLastError()));
+  KF_PHASE(KF_PH_MISC, s, k_check_finite<<<grid_for(N * d, 256), 256, 0, s>>>(Xt, N * d, bad));
+  KF_PHASE(KF_PH_TREE, s, k_node_ranges<<<1, 1, 0, s>>>(N, D, lo, hi));
+  KF_PHASE(KF_PH_TREE, s, k_iota64<<<grid_for(N, 256), 256, 0, s>>>(perm, N));
+  int32_t hbad = 0;
+  if (cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return kf_set_err(nullptr, KF_ECUDA, "kf_tree_perm_noalloc: %s", cudaGetErrorString(cudaGetLastError()));
+  if (hbad) return kf_set_err(nullptr, KF_EINVAL, "kf_tree_perm_noalloc: X has non-finite coordinates");
+  int32_t* ip = ia + maxnodes;
+  int32_t* iq = ia + 2 * maxnodes;
+  double* Xa = Xt;
+  int64_t* pa = perm;
+  double* Xc = Xb;
+  int64_t* pc = pb;
+  for (int l = 0; l < D; ++l) {
+    const int node0 = 1 << l, nn = 1 << l;
+    const int64_t nmax = (N + (int64_t(1) << l) - 1) >> l;  // ceil(N / 2^l): the largest node of the level
+    int cpn = (int)((nmax + kChunk - 1) / kChunk);
+    if (cpn < 1) cpn = 1;
+    dim3 g(cpn, nn);
+    KF_PHASE(KF_PH_TREE, s, k_node_argmax_partial<<<g, kRedThreads, 0, s>>>(Xa, pa, d, lo, hi, node0, cpn, 0, nullptr, part));
+    KF_PHASE(KF_PH_TREE, s, k_node_argmax_final<<<(nn + 7) / 8, 256, 0, s>>>(part, nn, cpn, ia));
+    KF_PHASE(KF_PH_TREE, s, k_node_argmax_partial<<<g, kRedThreads, 0, s>>>(Xa, pa, d, lo, hi, node0, cpn, 1, ia, part));
+    KF_PHASE(KF_PH_TREE, s, k_node_argmax_final<<<(nn + 7) / 8, 256, 0, s>>>(part, nn, cpn, ip));
+    KF_PHASE(KF_PH_TREE, s, k_node_argmax_partial<<<g, kRedThreads, 0, s>>>(Xa, pa, d, lo, hi, node0, cpn, 1, ip, part));
+    KF_PHASE(KF_PH_TREE, s, k_node_argmax_final<<<(nn + 7) / 8, 256, 0, s>>>(part, nn, cpn, iq));
+    int64_t seg = 1;
+    while (seg < nmax) seg <<= 1;
+    if (seg < 2) seg = 2;
+    const int64_t total = seg * nn;
+    dim3 gk((unsigned)std::min<int64_t>((seg + 255) / 256, 4096), nn);
+    KF_PHASE(KF_PH_TREE, s, k_proj_keys<<<gk, 256, 0, s>>>(Xa, pa, d, lo, hi, node0, seg, ip, iq, key, orig, pos));
+    const int tiles = (int)((total + kSortTile - 1) / kSortTile);
+    const int64_t ktile = std::min<int64_t>(seg, kSortTile);
+    KF_PHASE(KF_PH_TREE, s, k_bitonic_shared<<<tiles, 512, 0, s>>>(key, orig, pos, total, seg, 2, ktile, 1));
+    for (int64_t k = 2 * kSortTile; k <= seg; k <<= 1) {
+      for (int64_t j = k >> 1; j >= kSortTile; j >>= 1)
+        KF_PHASE(KF_PH_TREE, s, k_bitonic_global<<<grid_for(total, 256), 256, 0, s>>>(key, orig, pos, total, seg, k, j));
+      KF_PHASE(KF_PH_TREE, s, k_bitonic_shared<<<tiles, 512, 0, s>>>(key, orig, pos, total, seg, k, k, kSortTile / 2));
+    }
+    KF_PHASE(KF_PH_TREE, s, k_gather_rows<<<gk, 256, 0, s>>>(Xa, pa, d, lo, hi, node0, seg, pos, Xc, pc));
+    std::swap(Xa, Xc);
+    std::swap(pa, pc);
+  }
+  if (Xa != Xt) {
+    cudaMemcpyAsync(Xt, Xa, sizeof(double) * N * d, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(perm, pa, sizeof(int64_t) * N, cudaMemcpyDeviceToDevice, s);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return kf_set_err(nullptr, KF_ECUDA, "kf_tree_perm_noalloc: %s", cudaGetErrorString(e));
+  return KF_OK;
+}
