@@ -389,6 +389,22 @@ def gpu_main(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def once(args):
+    """A single pass of the path at a chosen size, no timing: the command that
+    profiler captures run."""
+    import torch
+
+    import paper_1701_02324_gb300 as kf
+    from paper_1701_02324_gb300 import inputs
+    p = inputs.scale(args.n)
+    prec = kf.KF_PREC_MIXED if args.precision == "mixed" else kf.KF_PREC_FP64
+    tree = kf.Tree(torch.from_numpy(p.X).cuda(), p.m)
+    F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=prec, refine_max_iter=-1, fp64_operator=False)
+    x = F.solve(torch.from_numpy(p.B[:, 0]).cuda())
+    torch.cuda.synchronize()
+    print(f"once: N={p.N} precision={args.precision} |x|={float(torch.linalg.norm(x)):.6e}")
+
+
 def ctypes_p():
     import ctypes
     return ctypes.c_void_p
@@ -405,7 +421,14 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--once", action="store_true",
+                    help="one tree + factorize + solve of the scale recipe and exit (for profilers)")
+    ap.add_argument("--n", type=int, default=1 << 20, help="number of points of the scale recipe")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args()
+    if args.once:
+        once(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -86,9 +86,16 @@ typedef struct {
   uint64_t seed;          /* sampler seed */
   int32_t v_storage;      /* kf_vstorage */
   int32_t sync_errors;    /* nonzero: synchronize and report device status at once */
-  double refine_tol;      /* mixed path: target relative residual (0 = 1e-10) */
-  int32_t refine_max_iter;/* mixed path: max refinement steps (0 = 8; -1 = none) */
-  int32_t reserved[8];
+  double refine_tol;      /* target relative residual (0 = 1e-10) */
+  int32_t refine_max_iter;/* max refinement iterations (0 = 100, mixed path only; > 0 also turns
+                             refinement on for the FP64 path; -1 = no refinement) */
+  int32_t no_tensor_cores;/* mixed path: 1 = CUDA-core FP32 products instead of tcgen05 3xTF32 */
+  int32_t fp64_operator;  /* keep FP64 V blocks and leaf blocks so that the refinement residual and
+                             kf_matvec use an FP64-accurate operator: 0 = default (on for the mixed
+                             path), 1 = on, -1 = off */
+  int32_t gmres_restart;  /* refinement method: 0 = GMRES(20), m > 0 = GMRES(m) in FP64,
+                             right-preconditioned by the factorization; -1 = x += M^-1 r */
+  int32_t reserved[5];
 } kf_opts;
 
 /* Filled by kf_solve when non-NULL (synchronizes the stream). */
@@ -138,8 +145,12 @@ kf_status kf_factor_free(kf_factor* f);
 /* X = (lambda I + K~)^-1 B (transpose = 0, Algorithm 3) or
  * X = (lambda I + K~)^-T B (transpose = 1).  B, X: N x nrhs column-major with
  * leading dimension ld, device or host, dtype KF_F32 or KF_F64; B and X may
- * alias.  On the mixed path the solve is refined against the hierarchical
- * operator in FP64 until the relative residual is below opts.refine_tol. */
+ * alias.  When refinement is on (mixed path by default, refine_max_iter > 0)
+ * the solve is refined against the hierarchical operator, with FP64
+ * accumulation, until the relative residual (Eq. e:errors) is below
+ * opts.refine_tol: by x += M^-1 r or by GMRES(m) (opts.gmres_restart), M being
+ * the factorization.  The operator is FP64-accurate when opts.fp64_operator is
+ * set (or on the FP64 path); otherwise the mixed path evaluates it in FP32. */
 kf_status kf_solve(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t ld, int32_t dtype,
                    int32_t transpose, void* stream, kf_solve_info* info);
 /* Y = (lambda I + K~) X with the operator the factorization inverts
@@ -153,6 +164,25 @@ kf_status kf_matvec(kf_factor* f, const void* X, void* Y, int64_t nrhs, int64_t 
  * summed over the RHS columns. */
 kf_status kf_grad(kf_factor* f, const void* x, const void* dLdx, void* dLdb, double* dLdlambda,
                   double* dLdh, int64_t nrhs, int64_t ld, void* stream);
+
+/* ---- many independent problems ------------------------------------------------ */
+/* Skeletonize and factorize nprob independent problems (one tree each, uneven
+ * N and ranks) with ONE CUDA-graph launch: the factors are allocated first,
+ * then every problem's kernel sequence is captured into one graph whose
+ * branches run concurrently on up to 16 streams, and the graph is launched
+ * once on `stream` (the spec batched configuration; Algorithms 1-2 per
+ * problem).  h, lambda, tau: host arrays of nprob values; s_max and opts are
+ * shared.  out: host array of nprob factor handles (NULL on failure).
+ * Synchronizes `stream`; returns the worst per-problem status (KF_EILLCOND
+ * leaves the factors in place).  Scratch memory inside the graph comes from
+ * cudaMallocAsync even when the context has an allocator. */
+kf_status kf_factorize_batched(kf_tree* const* trees, int32_t nprob, const double* h, const double* lambda,
+                               const double* tau, int32_t s_max, const kf_opts* opts, void* stream, kf_factor** out);
+/* X_i = (lambda_i I + K~_i)^-1 B_i for nprob factors with one CUDA-graph launch
+ * (Algorithm 3 per problem, no refinement).  B, X: host arrays of DEVICE
+ * pointers; nrhs, ld: host arrays.  Synchronizes `stream`. */
+kf_status kf_solve_batched(kf_factor* const* f, int32_t nprob, const void* const* B, void* const* X,
+                           const int64_t* nrhs, const int64_t* ld, int32_t dtype, void* stream);
 
 /* ---- inspection (host outputs; they synchronize the stream) -------------- */
 /* Heap-numbered nodes: root 1, children 2a and 2a+1, level l holds nodes

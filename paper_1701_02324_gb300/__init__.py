@@ -24,7 +24,7 @@ from ._abi import (KF_F32, KF_F64, KF_PREC_FP64, KF_PREC_MIXED, KF_V_RECOMPUTE, 
 __all__ = [
     "build", "Context", "Tree", "Factor", "tree_build", "factorize", "factorize_with_ids", "solve", "matvec",
     "grad", "tree_free", "factor_free", "KernelSolve", "KF_PREC_FP64", "KF_PREC_MIXED", "KF_V_STORED",
-    "KF_V_RECOMPUTE", "KFError",
+    "KF_V_RECOMPUTE", "KFError", "factorize_batched", "solve_batched",
 ]
 
 
@@ -155,8 +155,12 @@ class Tree:
 
 
 def _opts(precision=KF_PREC_FP64, n_samp=0, seed=0, v_storage=KF_V_STORED, sync_errors=0, refine_tol=0.0,
-          refine_max_iter=0):
+          refine_max_iter=0, tensor_cores=True, fp64_operator=None, gmres_restart=0):
     o = kf_opts()
+    o.no_tensor_cores = 0 if tensor_cores else 1
+    o.fp64_operator = 0 if fp64_operator is None else (1 if fp64_operator is True else
+                                                       (-1 if fp64_operator is False else int(fp64_operator)))
+    o.gmres_restart = int(gmres_restart)
     o.precision, o.n_samp, o.seed, o.v_storage = int(precision), int(n_samp), int(seed), int(v_storage)
     o.sync_errors, o.refine_tol, o.refine_max_iter = int(sync_errors), float(refine_tol), int(refine_max_iter)
     return o
@@ -167,10 +171,12 @@ class Factor:
 
     def __init__(self, tree: Tree, h: float, lam: float, tau: float, s_max: int, precision=KF_PREC_FP64,
                  n_samp: int = 0, seed: int = 0, v_storage=KF_V_STORED, refine_tol: float = 0.0,
-                 refine_max_iter: int = 0, sync_errors: bool = True, _ids=None):
+                 refine_max_iter: int = 0, sync_errors: bool = True, tensor_cores: bool = True,
+                 fp64_operator=None, gmres_restart: int = 0, _ids=None):
         self.tree, self.ctx = tree, tree.ctx
         self.h_, self.lam, self.tau, self.s_max, self.precision = float(h), float(lam), float(tau), int(s_max), precision
-        o = _opts(precision, n_samp, seed, v_storage, int(sync_errors), refine_tol, refine_max_iter)
+        o = _opts(precision, n_samp, seed, v_storage, int(sync_errors), refine_tol, refine_max_iter, tensor_cores,
+                  fp64_operator, gmres_restart)
         h_out = ctypes.c_void_p()
         if _ids is None:
             st = self.ctx.lib.kf_factorize(tree.h, self.h_, self.lam, self.tau, self.s_max, ctypes.byref(o),
@@ -299,6 +305,54 @@ def tree_free(tree: Tree):
 
 def factor_free(factor: Factor):
     factor.free()
+
+
+def _ptr_array(vals):
+    arr = (ctypes.c_void_p * len(vals))(*vals)
+    return arr
+
+
+def factorize_batched(trees, hs, lams, taus, s_max: int, precision=KF_PREC_MIXED, n_samp: int = 0, seed: int = 0):
+    """Factorize many independent problems with one CUDA-graph launch
+    (kf_factorize_batched).  Returns a list of Factor objects."""
+    import numpy as np
+    n = len(trees)
+    ctx = trees[0].ctx
+    h = np.ascontiguousarray(hs, dtype=np.float64)
+    lam = np.ascontiguousarray(lams, dtype=np.float64)
+    tau = np.ascontiguousarray(taus, dtype=np.float64)
+    o = _opts(precision, n_samp, seed, KF_V_STORED, 0, 0.0, -1)
+    out = (ctypes.c_void_p * n)()
+    tarr = _ptr_array([t.h.value for t in trees])
+    st = ctx.lib.kf_factorize_batched(tarr, n, h.ctypes.data_as(ctypes.c_void_p), lam.ctypes.data_as(ctypes.c_void_p),
+                                      tau.ctypes.data_as(ctypes.c_void_p), int(s_max), ctypes.byref(o), _stream_ptr(),
+                                      out)
+    ctx.check(st, allow=(_abi.KF_EILLCOND,))
+    facs = []
+    for i in range(n):
+        F = Factor.__new__(Factor)
+        F.tree, F.ctx = trees[i], ctx
+        F.h_, F.lam, F.tau, F.s_max, F.precision = float(h[i]), float(lam[i]), float(tau[i]), int(s_max), precision
+        F.status = st
+        F.h = ctypes.c_void_p(out[i])
+        facs.append(F)
+    return facs
+
+
+def solve_batched(factors, Bs):
+    """X_i = (lambda_i I + K~_i)^-1 B_i for every problem with one CUDA-graph
+    launch (kf_solve_batched).  B_i: device tensors N_i x k_i (float32/64)."""
+    torch = _torch()
+    n = len(factors)
+    Bc = [B.reshape(B.shape[0], -1).t().contiguous() for B in Bs]
+    Xc = [torch.empty_like(b) for b in Bc]
+    nrhs = (ctypes.c_int64 * n)(*[b.shape[0] for b in Bc])
+    ld = (ctypes.c_int64 * n)(*[f.tree.N for f in factors])
+    ctx = factors[0].ctx
+    st = ctx.lib.kf_solve_batched(_ptr_array([f.h.value for f in factors]), n, _ptr_array([b.data_ptr() for b in Bc]),
+                                  _ptr_array([x.data_ptr() for x in Xc]), nrhs, ld, _dtype_code(Bc[0]), _stream_ptr())
+    ctx.check(st)
+    return [x.t().reshape(B.shape) for x, B in zip(Xc, Bs)]
 
 
 def _autograd():

@@ -29,7 +29,10 @@ class kf_opts(ctypes.Structure):
         ("sync_errors", ctypes.c_int32),
         ("refine_tol", ctypes.c_double),
         ("refine_max_iter", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 8),
+        ("no_tensor_cores", ctypes.c_int32),
+        ("fp64_operator", ctypes.c_int32),
+        ("gmres_restart", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
     ]
 
 
@@ -58,6 +61,8 @@ SIGNATURES = {
     "kf_factor_Phat": (_I32, [_P, _I32, _P, _P]),
     "kf_factorize_with_ids": (_I32, [_P, _D, _D, _I32, _P, _P, _P, _P, _P, ctypes.POINTER(_P)]),
     "kf_tree_perm_noalloc": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
+    "kf_factorize_batched": (_I32, [_P, _I32, _P, _P, _P, _I32, _P, _P, _P]),
+    "kf_solve_batched": (_I32, [_P, _I32, _P, _P, _P, _P, _I32, _P]),
     "kf_launch_count": (_I64, []),
     "kf_profile_enable": (_I32, [_I32]),
     "kf_profile_read": (_I32, [_P, _P, _I32]),

@@ -11,9 +11,17 @@
 // The last line is Solve(a, W P_c, false) of Algorithm 2 after the identity
 // u - W Z^-1 V u = W Z^-1 P_c for u = W P_c (since V W = Z - I).
 #include <algorithm>
+#include <vector>
 
 #include "kf_internal.cuh"
 #include "prof.cuh"
+
+kf_status kf_tc_zoff(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
+                     const float* VT, const float* Ph, int ldz, double* Z, int64_t rows_per_child, int32_t* status,
+                     cudaStream_t s);
+kf_status kf_tc_telescope(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
+                          const float* Pc_hat, const double* Tm, int ldz, float* Pa_hat, int64_t rows_per_child,
+                          int32_t* status, cudaStream_t s);
 
 namespace {
 
@@ -157,23 +165,53 @@ __global__ void __launch_bounds__(256) k_leaf_cholesky(const int32_t* __restrict
 }
 
 // P^ = L^-T L^-1 P for one leaf per CTA; rhs = Pleaf rows of the leaf (FP64,
-// N x s_max), out = Phat level D rows (type T).  Columns are independent: a
-// thread owns one column for blocks of 32 rows, the off-block update is a
-// small GEMM through shared memory.
+// N x s_max), out = Phat level D rows (type T).  Blocked by 32 rows: the
+// diagonal block is solved with one thread per column, the rest of the
+// matrix is updated with 64 x 64 register-tiled products.
+template <typename T>
+__device__ __forceinline__ void tile_update(T (*sa)[33], T (*sb)[65], int ty, int tx, int nb, T* Y, int ldy,
+                                            int ti, int tj, int rows, int cols) {
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+#pragma unroll 8
+  for (int t = 0; t < 32; ++t) {
+    T av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = sa[ty * 4 + a][t];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) bv[b] = sb[t][tx * 4 + b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int i = ti + ty * 4 + a, j = tj + tx * 4 + b;
+      if (i < rows && j < cols) Y[(int64_t)i * ldy + j] -= acc[a][b];
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_leaf_phat(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                    const int32_t* __restrict__ rank, int leaf0, int ldL,
                                                    const T* __restrict__ Lall, const double* __restrict__ Pleaf,
                                                    int s_max, T* __restrict__ Phat) {
-  constexpr int NB = 32;
-  __shared__ T lb[NB][NB + 1];
+  constexpr int NB = 32, TS = 64;
+  __shared__ T sa[TS][NB + 1];
+  __shared__ T sb[NB][TS + 1];
   const int lf = blockIdx.x, node = leaf0 + lf;
   const int b = lo[node], n = hi[node] - b, s = rank[node];
   const T* L = Lall + (int64_t)lf * ldL * ldL;
   T* Y = Phat + (int64_t)b * s_max;
   const double* P = Pleaf + (int64_t)b * s_max;
-  // copy rhs
-  for (int64_t e = threadIdx.x; e < (int64_t)n * s_max; e += blockDim.x) {
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  for (int64_t e = tid; e < (int64_t)n * s_max; e += blockDim.x) {
     int i = (int)(e / s_max), q = (int)(e % s_max);
     Y[(int64_t)i * s_max + q] = q < s ? (T)P[(int64_t)i * s_max + q] : (T)0;
   }
@@ -182,89 +220,136 @@ __global__ void __launch_bounds__(256) k_leaf_phat(const int32_t* __restrict__ l
   // forward: L y = p
   for (int kb = 0; kb < n; kb += NB) {
     const int nb = min(NB, n - kb);
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
       int i = e / NB, j = e % NB;
-      lb[i][j] = (i < nb && j <= i) ? L[(int64_t)(kb + i) * ldL + kb + j] : (T)0;
+      sa[i][j] = (i < nb && j <= i) ? L[(int64_t)(kb + i) * ldL + kb + j] : (T)0;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < s; q += blockDim.x) {
+    for (int q = tid; q < s; q += blockDim.x) {
       T x[NB];
 #pragma unroll
       for (int i = 0; i < NB; ++i) x[i] = i < nb ? Y[(int64_t)(kb + i) * s_max + q] : (T)0;
 #pragma unroll
-      for (int i = 0; i < NB; ++i) {
+      for (int i = 0; i < NB; ++i)
         if (i < nb) {
           T acc = x[i];
-          for (int t = 0; t < i; ++t) acc -= lb[i][t] * x[t];
-          x[i] = acc / lb[i][i];
+#pragma unroll
+          for (int t = 0; t < i; ++t) acc = fma(-sa[i][t], x[t], acc);
+          x[i] = acc / sa[i][i];
         }
-      }
 #pragma unroll
       for (int i = 0; i < NB; ++i)
         if (i < nb) Y[(int64_t)(kb + i) * s_max + q] = x[i];
     }
     __syncthreads();
-    // rows below: y_i -= L[i, kb:kb+nb] x_block
-    for (int64_t e = threadIdx.x; e < (int64_t)(n - kb - nb) * s; e += blockDim.x) {
-      int i = kb + nb + (int)(e / s), q = (int)(e % s);
-      const T* Li = L + (int64_t)i * ldL + kb;
-      T acc = (T)0;
-      for (int t = 0; t < nb; ++t) acc += Li[t] * Y[(int64_t)(kb + t) * s_max + q];
-      Y[(int64_t)i * s_max + q] -= acc;
-    }
-    __syncthreads();
+    for (int ti = kb + nb; ti < n; ti += TS)
+      for (int tj = 0; tj < s; tj += TS) {
+        for (int e = tid; e < TS * NB; e += blockDim.x) {
+          int r = e / NB, cc = e % NB;
+          sa[r][cc] = (ti + r < n && cc < nb) ? L[(int64_t)(ti + r) * ldL + kb + cc] : (T)0;
+          int rr = e / TS, c2 = e % TS;
+          sb[rr][c2] = (rr < nb && tj + c2 < s) ? Y[(int64_t)(kb + rr) * s_max + tj + c2] : (T)0;
+        }
+        __syncthreads();
+        tile_update<T>(sa, sb, ty, tx, nb, Y, s_max, ti, tj, n, s);
+        __syncthreads();
+      }
   }
   // backward: L^T x = y
   for (int kb = ((n - 1) / NB) * NB; kb >= 0; kb -= NB) {
     const int nb = min(NB, n - kb);
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
       int i = e / NB, j = e % NB;
-      lb[i][j] = (i < nb && j <= i) ? L[(int64_t)(kb + i) * ldL + kb + j] : (T)0;
+      sa[i][j] = (i < nb && j <= i) ? L[(int64_t)(kb + i) * ldL + kb + j] : (T)0;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < s; q += blockDim.x) {
+    for (int q = tid; q < s; q += blockDim.x) {
       T x[NB];
 #pragma unroll
       for (int i = 0; i < NB; ++i) x[i] = i < nb ? Y[(int64_t)(kb + i) * s_max + q] : (T)0;
 #pragma unroll
-      for (int i = NB - 1; i >= 0; --i) {
+      for (int i = NB - 1; i >= 0; --i)
         if (i < nb) {
           T acc = x[i];
-          for (int t = i + 1; t < nb; ++t) acc -= lb[t][i] * x[t];
-          x[i] = acc / lb[i][i];
+#pragma unroll
+          for (int t = i + 1; t < NB; ++t) acc = fma(-sa[t][i], x[t], acc);
+          x[i] = acc / sa[i][i];
         }
-      }
 #pragma unroll
       for (int i = 0; i < NB; ++i)
         if (i < nb) Y[(int64_t)(kb + i) * s_max + q] = x[i];
     }
     __syncthreads();
-    // rows above: y_i -= L[kb:kb+nb, i]^T x_block
-    for (int64_t e = threadIdx.x; e < (int64_t)kb * s; e += blockDim.x) {
-      int i = (int)(e / s), q = (int)(e % s);
-      T acc = (T)0;
-      for (int t = 0; t < nb; ++t) acc += L[(int64_t)(kb + t) * ldL + i] * Y[(int64_t)(kb + t) * s_max + q];
-      Y[(int64_t)i * s_max + q] -= acc;
-    }
-    __syncthreads();
+    // rows above: y[0:kb] -= L[kb:kb+nb, 0:kb]^T x_block
+    for (int ti = 0; ti < kb; ti += TS)
+      for (int tj = 0; tj < s; tj += TS) {
+        for (int e = tid; e < TS * NB; e += blockDim.x) {
+          int r = e % TS, cc = e / TS;   // coalesced over r (contiguous in a row of L)
+          sa[r][cc] = (ti + r < kb && cc < nb) ? L[(int64_t)(kb + cc) * ldL + ti + r] : (T)0;
+          int rr = e / TS, c2 = e % TS;
+          sb[rr][c2] = (rr < nb && tj + c2 < s) ? Y[(int64_t)(kb + rr) * s_max + tj + c2] : (T)0;
+        }
+        __syncthreads();
+        tile_update<T>(sa, sb, ty, tx, nb, Y, s_max, ti, tj, kb, s);
+        __syncthreads();
+      }
   }
 }
 
 // ---- V blocks: VT rows of every point of the level -------------------------------
+// VT[i][q] = K(x_i, x_{skel(sib)[q]}) for the points i of every node of the
+// level.  The sibling's skeleton coordinates are staged transposed in shared
+// memory (yT[k][q]); one warp per row, lanes over q, coalesced stores.
 template <typename T>
-__global__ void k_eval_vt(const double* __restrict__ X64, const float* __restrict__ X32, int d, double c_exp,
-                          const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
-                          const int32_t* __restrict__ rank, const int32_t* __restrict__ skel, int s_max, int node0,
-                          T* __restrict__ VT) {
+__global__ void __launch_bounds__(256) k_eval_vt(const double* __restrict__ X64, const float* __restrict__ X32, int d,
+                                                 double c_exp, const int32_t* __restrict__ lo,
+                                                 const int32_t* __restrict__ hi, const int32_t* __restrict__ rank,
+                                                 const int32_t* __restrict__ skel, int s_max, int node0, int rows_per_cta,
+                                                 int qchunk, T* __restrict__ VT, double* __restrict__ VT64) {
+  extern __shared__ unsigned char smraw[];
+  T* yT = (T*)smraw;                       // d x qchunk
+  T* xs = yT + (size_t)d * qchunk;         // 8 warps x d
   const int nl = blockIdx.y, node = node0 + nl, sib = node ^ 1;
   const int b = lo[node], n = hi[node] - b, ss = rank[sib];
+  const int r0 = blockIdx.x * rows_per_cta;
+  if (r0 >= n || ss == 0) return;
+  const int r1 = min(n, r0 + rows_per_cta);
   const int32_t* sk = skel + (int64_t)sib * s_max;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * s_max;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int i = (int)(e / s_max), q = (int)(e % s_max);
-    T v = (T)0;
-    if (q < ss) v = kf_kern<T>::eval(X64, X32, b + i, sk[q], d, c_exp);
-    VT[(int64_t)(b + i) * s_max + q] = v;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* xw = xs + warp * d;
+  const T c = (T)c_exp;
+  for (int q0 = 0; q0 < ss; q0 += qchunk) {
+    const int qn = min(qchunk, ss - q0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < d * qn; e += blockDim.x) {
+      int k = e / qn, q = e % qn;
+      int64_t src = (int64_t)sk[q0 + q] * d + k;
+      yT[(size_t)k * qn + q] = sizeof(T) == 8 ? (T)X64[src] : (T)X32[src];
+    }
+    __syncthreads();
+    for (int i = r0 + warp; i < r1; i += 8) {
+      for (int k = lane; k < d; k += 32)
+        xw[k] = sizeof(T) == 8 ? (T)X64[(int64_t)(b + i) * d + k] : (T)X32[(int64_t)(b + i) * d + k];
+      __syncwarp();
+      T* out = VT + (int64_t)(b + i) * s_max + q0;
+      for (int q = lane; q < qn; q += 32) {
+        T acc = (T)0;
+        for (int k = 0; k < d; ++k) {
+          T t = xw[k] - yT[(size_t)k * qn + q];
+          acc = fma(t, t, acc);
+        }
+        T kv = sizeof(T) == 8 ? (T)exp((double)(acc * c)) : (T)__expf((float)(acc * c));
+        if (VT64 != nullptr) {  // FP64 operator copy: recompute the entries that matter in FP64
+          const int64_t row = b + i;
+          double k64 = (double)kv;
+          if ((float)kv >= 5.9604645e-8f) k64 = kf_kern64(X64 + row * d, X64 + (int64_t)sk[q0 + q] * d, d, c_exp);
+          VT64[row * s_max + q0 + q] = k64;
+          kv = (T)k64;
+        }
+        out[q] = kv;
+      }
+      __syncwarp();
+    }
   }
 }
 
@@ -347,111 +432,287 @@ __global__ void __launch_bounds__(256) k_zoff(const int32_t* __restrict__ lo, co
     }
 }
 
-// LU with partial pivoting of Z (one CTA per node, FP64, in place); ties in
-// |pivot| go to the lowest row; pivots below 1e-14 max|Z| raise ILLCOND.
-__global__ void __launch_bounds__(512) k_z_lu(const int32_t* __restrict__ rank, int node0, int ldz,
-                                              double* __restrict__ Z, int32_t* __restrict__ piv,
-                                              int32_t* __restrict__ status) {
-  __shared__ double rv[32];
-  __shared__ int ri[32];
+// Blocked LU with partial pivoting of Z (FP64) followed, for non-root nodes,
+// by T = Z^-1 P_c, one CTA (256 threads) per node.
+//   panel:    32 columns at a time; per column an arg-max over the rows
+//             (ties: lowest row), a full-row swap, scaling, and the rank-1
+//             update restricted to the panel;
+//   U12:      L11^-1 A12 by the 32 x 32 unit-lower block;
+//   trailing: A22 -= L21 U12, 64 x 64 register-tiled FP64 tiles;
+// then X = P_c with the row swaps applied, L y = x and U t = y by 32-row
+// blocks (diagonal block per column thread, off-block updates tiled).
+__global__ void __launch_bounds__(256) k_z_factor(const int32_t* __restrict__ rank, int node0, int ldz, int s_max,
+                                                  double* __restrict__ Z, int32_t* __restrict__ piv,
+                                                  const double* __restrict__ Pc, double* __restrict__ T,
+                                                  int solve_pc, int32_t* __restrict__ status) {
+  constexpr int NB = 32, TS = 64;
+  __shared__ double sa[TS][NB + 1];
+  __shared__ double sb[NB][TS + 1];
+  __shared__ double rv[8];
+  __shared__ int ri[8];
   __shared__ int pk;
+  __shared__ double amax_sh;
   const int nl = blockIdx.x, node = node0 + nl;
   const int z = rank[2 * node] + rank[2 * node + 1];
   double* A = Z + (int64_t)node * ldz * ldz;
   int32_t* pv = piv + (int64_t)node * ldz;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  // max |Z|
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // max |Z| for the pivot test
   double mx = 0.0;
   for (int64_t e = tid; e < (int64_t)z * z; e += blockDim.x) mx = fmax(mx, fabs(A[(e / z) * ldz + e % z]));
   for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
   if (lane == 0) rv[warp] = mx;
   __syncthreads();
-  double amax = 0.0;
-  for (int w = 0; w < nw; ++w) amax = fmax(amax, rv[w]);
+  if (tid == 0) {
+    double m2 = 0.0;
+    for (int w = 0; w < 8; ++w) m2 = fmax(m2, rv[w]);
+    amax_sh = m2;
+  }
   __syncthreads();
+  const double amax = amax_sh;
   bool bad = false;
-  for (int k = 0; k < z; ++k) {
-    double bv = -1.0;
-    int bi = z;
-    for (int i = k + tid; i < z; i += blockDim.x) {
-      double v = fabs(A[(int64_t)i * ldz + k]);
-      if (v > bv) { bv = v; bi = i; }
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      double ov = __shfl_xor_sync(0xffffffffu, bv, off);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-    }
-    if (lane == 0) { rv[warp] = bv; ri[warp] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      double b2 = -1.0;
-      int i2 = z;
-      for (int w = 0; w < nw; ++w)
-        if (rv[w] > b2 || (rv[w] == b2 && ri[w] < i2)) { b2 = rv[w]; i2 = ri[w]; }
-      pk = i2;
-      pv[k] = i2;
-    }
-    __syncthreads();
-    const int p = pk;
-    if (p != k)
-      for (int j = tid; j < z; j += blockDim.x) {
-        double t = A[(int64_t)k * ldz + j];
-        A[(int64_t)k * ldz + j] = A[(int64_t)p * ldz + j];
-        A[(int64_t)p * ldz + j] = t;
+  for (int kb = 0; kb < z; kb += NB) {
+    const int nb = min(NB, z - kb);
+    for (int j = kb; j < kb + nb; ++j) {
+      double bv = -1.0;
+      int bi = z;
+      for (int i = j + tid; i < z; i += blockDim.x) {
+        double v = fabs(A[(int64_t)i * ldz + j]);
+        if (v > bv) { bv = v; bi = i; }
       }
-    __syncthreads();
-    double ukk = A[(int64_t)k * ldz + k];
-    if (!(fabs(ukk) > 1e-14 * amax)) bad = true;
-    if (ukk != 0.0) {
-      for (int i = k + 1 + tid; i < z; i += blockDim.x) A[(int64_t)i * ldz + k] /= ukk;
+      for (int off = 16; off > 0; off >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+      }
+      if (lane == 0) { rv[warp] = bv; ri[warp] = bi; }
       __syncthreads();
-      const int w = z - k - 1;
-      for (int64_t e = tid; e < (int64_t)w * w; e += blockDim.x) {
-        int i = k + 1 + (int)(e / w), j = k + 1 + (int)(e % w);
-        A[(int64_t)i * ldz + j] -= A[(int64_t)i * ldz + k] * A[(int64_t)k * ldz + j];
+      if (tid == 0) {
+        double b2 = -1.0;
+        int i2 = z;
+        for (int w = 0; w < 8; ++w)
+          if (rv[w] > b2 || (rv[w] == b2 && ri[w] < i2)) { b2 = rv[w]; i2 = ri[w]; }
+        pk = i2;
+        pv[j] = i2;
       }
+      __syncthreads();
+      const int p = pk;
+      if (p != j)
+        for (int c = tid; c < z; c += blockDim.x) {
+          double t = A[(int64_t)j * ldz + c];
+          A[(int64_t)j * ldz + c] = A[(int64_t)p * ldz + c];
+          A[(int64_t)p * ldz + c] = t;
+        }
+      __syncthreads();
+      const double ujj = A[(int64_t)j * ldz + j];
+      if (!(fabs(ujj) > 1e-14 * amax)) bad = true;
+      const double inv = ujj != 0.0 ? 1.0 / ujj : 0.0;
+      for (int i = j + 1 + tid; i < z; i += blockDim.x) {
+        double* Ai = A + (int64_t)i * ldz;
+        const double l = Ai[j] * inv;
+        Ai[j] = l;
+        for (int c = j + 1; c < kb + nb; ++c) Ai[c] = fma(-l, A[(int64_t)j * ldz + c], Ai[c]);
+      }
+      __syncthreads();
+    }
+    const int c0 = kb + nb;
+    if (c0 >= z) break;
+    // U12 = L11^-1 A12, thread per column
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+      int i = e / NB, j = e % NB;
+      sa[i][j] = (i < nb && j < i) ? A[(int64_t)(kb + i) * ldz + kb + j] : 0.0;
     }
     __syncthreads();
+    for (int c = c0 + tid; c < z; c += blockDim.x) {
+      double x[NB];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) x[r] = r < nb ? A[(int64_t)(kb + r) * ldz + c] : 0.0;
+#pragma unroll
+      for (int r = 1; r < NB; ++r) {
+        double acc = x[r];
+#pragma unroll
+        for (int t = 0; t < r; ++t) acc = fma(-sa[r][t], x[t], acc);
+        x[r] = acc;
+      }
+#pragma unroll
+      for (int r = 1; r < NB; ++r)
+        if (r < nb) A[(int64_t)(kb + r) * ldz + c] = x[r];
+    }
+    __syncthreads();
+    // A22 -= L21 U12
+    const int ty = tid / 16, tx = tid % 16;
+    for (int ti = c0; ti < z; ti += TS)
+      for (int tj = c0; tj < z; tj += TS) {
+        for (int e = tid; e < TS * NB; e += blockDim.x) {
+          int r = e / NB, cc = e % NB;
+          sa[r][cc] = (ti + r < z && cc < nb) ? A[(int64_t)(ti + r) * ldz + kb + cc] : 0.0;
+          int rr = e / TS, c2 = e % TS;
+          sb[rr][c2] = (rr < nb && tj + c2 < z) ? A[(int64_t)(kb + rr) * ldz + tj + c2] : 0.0;
+        }
+        __syncthreads();
+        double acc[4][4] = {};
+#pragma unroll 8
+        for (int t = 0; t < NB; ++t) {
+          double av[4], bv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) av[a] = sa[ty * 4 + a][t];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) bv[b] = sb[t][tx * 4 + b];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            int i = ti + ty * 4 + a, j = tj + tx * 4 + b;
+            if (i < z && j < z) A[(int64_t)i * ldz + j] -= acc[a][b];
+          }
+        __syncthreads();
+      }
   }
   if (bad && tid == 0) atomicOr(status, KF_DEV_ILLCOND);
-}
-
-// T = Z^-1 P_c for a non-root node; thread per column of P_c.
-__global__ void k_z_solve_pc(const int32_t* __restrict__ rank, int node0, int ldz, const double* __restrict__ ZLU,
-                             const int32_t* __restrict__ piv, const double* __restrict__ Pc, int s_max,
-                             double* __restrict__ T) {
-  const int nl = blockIdx.x, node = node0 + nl;
-  const int z = rank[2 * node] + rank[2 * node + 1], s = rank[node];
-  const double* A = ZLU + (int64_t)node * ldz * ldz;
-  const int32_t* pv = piv + (int64_t)node * ldz;
+  if (!solve_pc) return;
+  // ---- T = Z^-1 P_c --------------------------------------------------------------
+  const int s = rank[node];
   const double* B = Pc + (int64_t)node * ldz * s_max;
   double* X = T + (int64_t)nl * ldz * s_max;
-  for (int q = threadIdx.x; q < s_max; q += blockDim.x) {
-    if (q >= s) {
-      for (int i = 0; i < ldz; ++i) X[(int64_t)i * s_max + q] = 0.0;
-      continue;
-    }
-    for (int i = 0; i < z; ++i) X[(int64_t)i * s_max + q] = B[(int64_t)i * s_max + q];
-    for (int i = z; i < ldz; ++i) X[(int64_t)i * s_max + q] = 0.0;
-    for (int k = 0; k < z; ++k) {
-      int p = pv[k];
-      if (p != k) {
+  for (int64_t e = tid; e < (int64_t)ldz * s_max; e += blockDim.x) {
+    int i = (int)(e / s_max), q = (int)(e % s_max);
+    X[e] = (i < z && q < s) ? B[e] : 0.0;
+  }
+  __syncthreads();
+  if (s == 0 || z == 0) return;
+  for (int k = 0; k < z; ++k) {  // row swaps in factorization order
+    const int p = pv[k];
+    if (p != k)
+      for (int q = tid; q < s; q += blockDim.x) {
         double t = X[(int64_t)k * s_max + q];
         X[(int64_t)k * s_max + q] = X[(int64_t)p * s_max + q];
         X[(int64_t)p * s_max + q] = t;
       }
+    __syncthreads();
+  }
+  const int ty = tid / 16, tx = tid % 16;
+  // forward: L (unit lower)
+  for (int kb = 0; kb < z; kb += NB) {
+    const int nb = min(NB, z - kb);
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+      int i = e / NB, j = e % NB;
+      sa[i][j] = (i < nb && j < i) ? A[(int64_t)(kb + i) * ldz + kb + j] : 0.0;
     }
-    for (int i = 0; i < z; ++i) {
-      double acc = X[(int64_t)i * s_max + q];
-      for (int t = 0; t < i; ++t) acc -= A[(int64_t)i * ldz + t] * X[(int64_t)t * s_max + q];
-      X[(int64_t)i * s_max + q] = acc;
+    __syncthreads();
+    for (int q = tid; q < s; q += blockDim.x) {
+      double x[NB];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) x[r] = r < nb ? X[(int64_t)(kb + r) * s_max + q] : 0.0;
+#pragma unroll
+      for (int r = 1; r < NB; ++r) {
+        double acc = x[r];
+#pragma unroll
+        for (int t = 0; t < r; ++t) acc = fma(-sa[r][t], x[t], acc);
+        x[r] = acc;
+      }
+#pragma unroll
+      for (int r = 1; r < NB; ++r)
+        if (r < nb) X[(int64_t)(kb + r) * s_max + q] = x[r];
     }
-    for (int i = z - 1; i >= 0; --i) {
-      double acc = X[(int64_t)i * s_max + q];
-      for (int t = i + 1; t < z; ++t) acc -= A[(int64_t)i * ldz + t] * X[(int64_t)t * s_max + q];
-      X[(int64_t)i * s_max + q] = acc / A[(int64_t)i * ldz + i];
+    __syncthreads();
+    for (int ti = kb + nb; ti < z; ti += TS)
+      for (int tj = 0; tj < s; tj += TS) {
+        for (int e = tid; e < TS * NB; e += blockDim.x) {
+          int r = e / NB, cc = e % NB;
+          sa[r][cc] = (ti + r < z && cc < nb) ? A[(int64_t)(ti + r) * ldz + kb + cc] : 0.0;
+          int rr = e / TS, c2 = e % TS;
+          sb[rr][c2] = (rr < nb && tj + c2 < s) ? X[(int64_t)(kb + rr) * s_max + tj + c2] : 0.0;
+        }
+        __syncthreads();
+        double acc[4][4] = {};
+#pragma unroll 8
+        for (int t = 0; t < NB; ++t) {
+          double av[4], bv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) av[a] = sa[ty * 4 + a][t];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) bv[b] = sb[t][tx * 4 + b];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            int i = ti + ty * 4 + a, j = tj + tx * 4 + b;
+            if (i < z && j < s) X[(int64_t)i * s_max + j] -= acc[a][b];
+          }
+        __syncthreads();
+      }
+    // the diagonal-block loads of the next panel reuse sa: wait for this one
+    __syncthreads();
+  }
+  // backward: U
+  for (int kb = ((z - 1) / NB) * NB; kb >= 0; kb -= NB) {
+    const int nb = min(NB, z - kb);
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+      int i = e / NB, j = e % NB;
+      sa[i][j] = (i < nb && j < nb && j >= i) ? A[(int64_t)(kb + i) * ldz + kb + j] : 0.0;
     }
+    __syncthreads();
+    for (int q = tid; q < s; q += blockDim.x) {
+      double x[NB];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) x[r] = r < nb ? X[(int64_t)(kb + r) * s_max + q] : 0.0;
+#pragma unroll
+      for (int r = NB - 1; r >= 0; --r) {
+        if (r < nb) {
+          double acc = x[r];
+#pragma unroll
+          for (int t = r + 1; t < NB; ++t) acc = fma(-sa[r][t], x[t], acc);
+          x[r] = acc / sa[r][r];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        if (r < nb) X[(int64_t)(kb + r) * s_max + q] = x[r];
+    }
+    __syncthreads();
+    // rows above: X[0:kb] -= U[0:kb, kb:kb+nb] X[kb:kb+nb]
+    for (int ti = 0; ti < kb; ti += TS)
+      for (int tj = 0; tj < s; tj += TS) {
+        for (int e = tid; e < TS * NB; e += blockDim.x) {
+          int r = e / NB, cc = e % NB;
+          sa[r][cc] = (ti + r < kb && cc < nb) ? A[(int64_t)(ti + r) * ldz + kb + cc] : 0.0;
+          int rr = e / TS, c2 = e % TS;
+          sb[rr][c2] = (rr < nb && tj + c2 < s) ? X[(int64_t)(kb + rr) * s_max + tj + c2] : 0.0;
+        }
+        __syncthreads();
+        double acc[4][4] = {};
+#pragma unroll 8
+        for (int t = 0; t < NB; ++t) {
+          double av[4], bv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) av[a] = sa[ty * 4 + a][t];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) bv[b] = sb[t][tx * 4 + b];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            int i = ti + ty * 4 + a, j = tj + tx * 4 + b;
+            if (i < kb && j < s) X[(int64_t)i * s_max + j] -= acc[a][b];
+          }
+        __syncthreads();
+      }
+    __syncthreads();
   }
 }
 
@@ -514,62 +775,164 @@ __global__ void __launch_bounds__(256) k_telescope(const int32_t* __restrict__ l
     }
 }
 
+// FP64 copy of the leaf kernel blocks (no lambda), both triangles, for the
+// FP64-accurate operator.
+__global__ void k_leaf_k64(const double* __restrict__ X64, const float* __restrict__ X32, int d, double c_exp,
+                           const int32_t* __restrict__ lo, const int32_t* __restrict__ hi, int leaf0, int ldL,
+                           double* __restrict__ K64) {
+  const int lf = blockIdx.z, node = leaf0 + lf;
+  const int b = lo[node], n = hi[node] - b;
+  const int i = blockIdx.y;
+  if (i >= n) return;
+  double* Ki = K64 + ((int64_t)lf * ldL + i) * ldL;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    Ki[j] = kf_kern_hybrid(X64, X32, b + i, b + j, d, c_exp);
+}
+
 template <typename T>
-kf_status factorize_t(kf_factor* f, cudaStream_t s) {
+kf_status leaves_t(kf_factor* f, cudaStream_t s) {
   kf_tree* t = f->t;
   kf_ctx* c = f->ctx;
-  const int D = t->D, s_max = f->s_max, ldz = 2 * s_max;
+  const int D = t->D, s_max = f->s_max;
   const int64_t N = t->N;
   const int ldL = t->leaf_max;
   T* L = (T*)f->L;
   T* Phat = (T*)f->Phat;
-  T* VT = (T*)f->VT;
-  auto lvl = [&](T* base, int l) { return base + (int64_t)(l - 1) * N * s_max; };
   const int leaf0 = 1 << D, nleaf = 1 << D;
-  // leaves
-  {
-    dim3 g((ldL + 127) / 128, ldL, nleaf);
-    KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_assemble<T><<<g, 128, 0, s>>>(t->X64, t->X32, t->d, f->c_exp, f->lambda, t->d_lo, t->d_hi, leaf0, ldL, L));
-    KF_PHASE(KF_PH_LEAF_CHOL, s, k_leaf_cholesky<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, ldL, L, f->status));
-    if (D > 0)
-      KF_PHASE(KF_PH_LEAF_PHAT, s, k_leaf_phat<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, leaf0, ldL, L, f->Pleaf, s_max, lvl(Phat, D)));
-    KF_LAUNCH_CHECK(c);
-  }
-  if (D == 0) return KF_OK;
-  double* Tm = (double*)c->dalloc(sizeof(double) * (size_t)(1 << (D - 1)) * ldz * s_max, s);
-  if (!Tm) return kf_set_err(c, KF_ENOMEM, "factorize: allocation failed");
-  kf_status st = KF_OK;
-  for (int l = D - 1; l >= 0 && st == KF_OK; --l) {
-    const int node0 = 1 << l, nn = 1 << l;
-    const int child0 = 1 << (l + 1);
-    // V blocks of the children's level
-    dim3 gv(grid_for((int64_t)(N >> (l + 1)) * s_max + s_max, 256, 4096), 2 * nn);
-    KF_PHASE(KF_PH_EVAL_V, s, k_eval_vt<T><<<gv, 256, 0, s>>>(t->X64, t->X32, t->d, f->c_exp, t->d_lo, t->d_hi, f->rank, f->skel, s_max, child0,
-                                    lvl(VT, l + 1)));
-    // Z
-    KF_PHASE(KF_PH_ZOFF, s, k_z_init<<<dim3(grid_for((int64_t)ldz * ldz, 256, 64), nn), 256, 0, s>>>(f->rank, node0, ldz, f->ZLU));
-    const int tiles = ((s_max + 63) / 64) * ((s_max + 63) / 64);
-    const int64_t rows = N >> (l + 1);
-    int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(rows / 512, (152 * 8) / std::max(1, 2 * nn * tiles) + 1));
+  dim3 g((ldL + 127) / 128, ldL, nleaf);
+  KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_assemble<T><<<g, 128, 0, s>>>(t->X64, t->X32, t->d, f->c_exp, f->lambda, t->d_lo, t->d_hi, leaf0, ldL, L));
+  if (f->K64)
+    KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_k64<<<g, 128, 0, s>>>(t->X64, t->X32, t->d, f->c_exp, t->d_lo, t->d_hi, leaf0, ldL, f->K64));
+  KF_PHASE(KF_PH_LEAF_CHOL, s, k_leaf_cholesky<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, ldL, L, f->status));
+  if (D > 0)
+    KF_PHASE(KF_PH_LEAF_PHAT, s, k_leaf_phat<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, leaf0, ldL, L, f->Pleaf, s_max,
+                                                                  Phat + (int64_t)(D - 1) * N * s_max));
+  KF_LAUNCH_CHECK(c);
+  return KF_OK;
+}
+
+template <typename T>
+kf_status level_t(kf_factor* f, int l, double* Tm, cudaStream_t s) {
+  kf_tree* t = f->t;
+  kf_ctx* c = f->ctx;
+  const int s_max = f->s_max, ldz = 2 * s_max;
+  const int64_t N = t->N;
+  T* Phat = (T*)f->Phat;
+  T* VT = (T*)f->VT;
+  auto lvl = [&](T* base, int lv) { return base + (int64_t)(lv - 1) * N * s_max; };
+  const int node0 = 1 << l, nn = 1 << l;
+  const int child0 = 1 << (l + 1);
+  // V blocks of the children's level
+  const int vt_rows = 64;
+  dim3 gv((unsigned)(((N >> (l + 1)) + vt_rows) / vt_rows), 2 * nn);
+  // skeleton coordinates of up to qchunk columns per pass, at most 96 KiB of shared memory
+  const int qchunk = (int)std::max<int64_t>(1, std::min<int64_t>(s_max, (96 * 1024 / (int64_t)sizeof(T) - 8 * t->d) / t->d));
+  const size_t vt_smem = sizeof(T) * ((size_t)t->d * qchunk + 8 * t->d);
+  KF_CUDA(c, cudaFuncSetAttribute(k_eval_vt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vt_smem));
+  KF_PHASE(KF_PH_EVAL_V, s, k_eval_vt<T><<<gv, 256, vt_smem, s>>>(t->X64, t->X32, t->d, f->c_exp, t->d_lo, t->d_hi,
+                                                                 f->rank, f->skel, s_max, child0, vt_rows, qchunk,
+                                                                 lvl(VT, l + 1),
+                                                                 f->VT64 ? f->VT64 + (int64_t)l * N * s_max : nullptr));
+  // Z
+  KF_PHASE(KF_PH_ZOFF, s, k_z_init<<<dim3(grid_for((int64_t)ldz * ldz, 256, 64), nn), 256, 0, s>>>(f->rank, node0, ldz, f->ZLU));
+  const int tiles = ((s_max + 63) / 64) * ((s_max + 63) / 64);
+  const int64_t rows = N >> (l + 1);
+  int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(rows / 512, (152 * 8) / std::max(1, 2 * nn * tiles) + 1));
+  if (sizeof(T) == 4 && f->use_tc) {
+    kf_status r = kf_tc_zoff(t->d_lo, t->d_hi, f->rank, node0, nn, s_max, (const float*)lvl(VT, l + 1),
+                             (const float*)lvl(Phat, l + 1), ldz, f->ZLU, rows, f->status, s);
+    if (r != KF_OK) return kf_set_err(c, r, "tensor-core Z blocks failed at level %d", l);
+  } else {
     KF_PHASE(KF_PH_ZOFF, s, k_zoff<T><<<dim3(tiles, ksplit, 2 * nn), 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, node0, s_max, lvl(VT, l + 1),
                                                           lvl(Phat, l + 1), ldz, f->ZLU, ksplit));
-    KF_PHASE(KF_PH_ZLU, s, k_z_lu<<<nn, 512, 0, s>>>(f->rank, node0, ldz, f->ZLU, f->Zpiv, f->status));
-    if (l >= 1) {
-      KF_PHASE(KF_PH_ZSOLVE_PC, s, k_z_solve_pc<<<nn, 128, 0, s>>>(f->rank, node0, ldz, f->ZLU, f->Zpiv, f->Pc, s_max, Tm));
-      const int64_t cmax_rows = (N >> (l + 1)) + 1;
-      dim3 gt((unsigned)((cmax_rows + 63) / 64), (s_max + 63) / 64, 2 * nn);
+  }
+  KF_PHASE(KF_PH_ZLU, s, k_z_factor<<<nn, 256, 0, s>>>(f->rank, node0, ldz, s_max, f->ZLU, f->Zpiv, f->Pc, Tm,
+                                                       l >= 1 ? 1 : 0, f->status));
+  if (l >= 1) {
+    const int64_t cmax_rows = (N >> (l + 1)) + 1;
+    dim3 gt((unsigned)((cmax_rows + 63) / 64), (s_max + 63) / 64, 2 * nn);
+    if (sizeof(T) == 4 && f->use_tc) {
+      kf_status r = kf_tc_telescope(t->d_lo, t->d_hi, f->rank, node0, nn, s_max, (const float*)lvl(Phat, l + 1), Tm,
+                                    ldz, (float*)lvl(Phat, l), cmax_rows, f->status, s);
+      if (r != KF_OK) return kf_set_err(c, r, "tensor-core telescoping failed at level %d", l);
+    } else {
       KF_PHASE(KF_PH_TELESCOPE, s, k_telescope<T><<<gt, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, node0, s_max, lvl(Phat, l + 1), Tm, ldz,
                                         lvl(Phat, l)));
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) st = kf_set_err(c, KF_ECUDA, "factorize level %d: %s", l, cudaGetErrorString(e));
   }
-  c->dfree(Tm, sizeof(double) * (size_t)(1 << (D - 1)) * ldz * s_max, s);
-  return st;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return kf_set_err(c, KF_ECUDA, "factorize level %d: %s", l, cudaGetErrorString(e));
+  return KF_OK;
 }
 
 }  // namespace
 
+size_t kf_factor_tm_elems(const kf_factor* f) {
+  const int D = f->t->D;
+  return D > 0 ? (size_t)(1 << (D - 1)) * 2 * f->s_max * f->s_max : 1;
+}
+
+kf_status kf_factorize_leaves(kf_factor* f, cudaStream_t s) {
+  return f->prec == KF_PREC_FP64 ? leaves_t<double>(f, s) : leaves_t<float>(f, s);
+}
+
+kf_status kf_factorize_level(kf_factor* f, int l, double* Tm, cudaStream_t s) {
+  return f->prec == KF_PREC_FP64 ? level_t<double>(f, l, Tm, s) : level_t<float>(f, l, Tm, s);
+}
+
 kf_status kf_factorize_device(kf_factor* f, cudaStream_t s) {
-  return f->prec == KF_PREC_FP64 ? factorize_t<double>(f, s) : factorize_t<float>(f, s);
+  kf_ctx* c = f->ctx;
+  kf_status st = kf_factorize_leaves(f, s);
+  if (st != KF_OK || f->t->D == 0) return st;
+  const size_t tb = sizeof(double) * kf_factor_tm_elems(f);
+  double* Tm = (double*)c->dalloc(tb, s);
+  if (!Tm) return kf_set_err(c, KF_ENOMEM, "factorize: allocation failed");
+  for (int l = f->t->D - 1; l >= 0 && st == KF_OK; --l) st = kf_factorize_level(f, l, Tm, s);
+  c->dfree(Tm, tb, s);
+  return st;
+}
+
+// Skeletonization and factorization interleaved on two streams: level l of
+// the factorization needs the skeletons of levels l + 1 and l only, so the
+// pivoted QRs of the upper levels (few nodes, one CTA each) run while the
+// lower levels are factorized.  Events order the two streams; the caller's
+// stream waits for both at the end.
+kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
+  kf_ctx* c = f->ctx;
+  const int D = f->t->D;
+  if (D == 0) {
+    kf_status st = kf_skeletonize_device(f, s);
+    return st == KF_OK ? kf_factorize_device(f, s) : st;
+  }
+  kf_skel_scratch sc;
+  kf_status st = kf_skel_begin(f, &sc, s);
+  const size_t tb = sizeof(double) * kf_factor_tm_elems(f);
+  double* Tm = st == KF_OK ? (double*)c->dalloc(tb, s) : nullptr;
+  if (st == KF_OK && !Tm) st = kf_set_err(c, KF_ENOMEM, "factorize: allocation failed");
+  cudaStream_t s2 = nullptr;
+  std::vector<cudaEvent_t> ev(D + 2, nullptr);
+  if (st == KF_OK) {
+    KF_CUDA(c, cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    for (auto& e : ev) KF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    // ev[l]: skeletons of level l done (on s); ev[0]: allocations ready; ev[D+1]: factorization done (on s2)
+    cudaEventRecord(ev[0], s);
+    cudaStreamWaitEvent(s2, ev[0], 0);
+    for (int l = D; l >= 1 && st == KF_OK; --l) {
+      st = kf_skel_level(f, l, &sc, s);
+      cudaEventRecord(ev[l], s);
+      if (st != KF_OK) break;
+      cudaStreamWaitEvent(s2, ev[l], 0);
+      if (l == D) st = kf_factorize_leaves(f, s2);
+      else st = kf_factorize_level(f, l, Tm, s2);
+    }
+    if (st == KF_OK) st = kf_factorize_level(f, 0, Tm, s2);
+    cudaEventRecord(ev[D + 1], s2);
+    cudaStreamWaitEvent(s, ev[D + 1], 0);
+  }
+  if (Tm) c->dfree(Tm, tb, s);
+  kf_skel_end(f, &sc, s);
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  if (s2) cudaStreamDestroy(s2);
+  return st;
 }

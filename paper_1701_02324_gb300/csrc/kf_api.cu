@@ -31,7 +31,7 @@ kf_status kf_set_err(kf_ctx* c, kf_status s, const char* fmt, ...) {
 
 void* kf_ctx::dalloc(size_t bytes, cudaStream_t s) {
   if (bytes == 0) bytes = 16;
-  if (has_alloc) return alloc.alloc(bytes, (void*)s, alloc.user);
+  if (has_alloc && !capturing) return alloc.alloc(bytes, (void*)s, alloc.user);
   void* p = nullptr;
   if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
     cudaGetLastError();
@@ -43,7 +43,7 @@ void* kf_ctx::dalloc(size_t bytes, cudaStream_t s) {
 void kf_ctx::dfree(void* p, size_t bytes, cudaStream_t s) {
   if (!p) return;
   if (bytes == 0) bytes = 16;
-  if (has_alloc) alloc.free(p, bytes, (void*)s, alloc.user);
+  if (has_alloc && !capturing) alloc.free(p, bytes, (void*)s, alloc.user);
   else cudaFreeAsync(p, s);
 }
 
@@ -124,6 +124,58 @@ __global__ void k_add(double* __restrict__ x, const double* __restrict__ d, int6
     x[i] += d[i];
 }
 
+// ---- GMRES helpers --------------------------------------------------------------
+// h[j] += sum_i V[j][i] w[i], j < J (one block-partial per j, atomics)
+__global__ void k_multidot(const double* __restrict__ V, int64_t ldv, int J, const double* __restrict__ w, int64_t n,
+                           double* __restrict__ h) {
+  __shared__ double sh[8];
+  for (int j = 0; j < J; ++j) {
+    const double* v = V + (int64_t)j * ldv;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+      acc = fma(v[i], w[i], acc);
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+      atomicAdd(h + j, t);
+    }
+    __syncthreads();
+  }
+}
+// w[i] -= sum_j h[j] V[j][i]
+__global__ void k_multiaxpy(const double* __restrict__ V, int64_t ldv, int J, const double* __restrict__ h,
+                            double* __restrict__ w, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = w[i];
+    for (int j = 0; j < J; ++j) acc = fma(-h[j], V[(int64_t)j * ldv + i], acc);
+    w[i] = acc;
+  }
+}
+// x[i] += sum_j y[j] Z[j][i]
+__global__ void k_zupdate(const double* __restrict__ Z, int64_t ldz, int J, const double* __restrict__ y,
+                          double* __restrict__ x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = x[i];
+    for (int j = 0; j < J; ++j) acc = fma(y[j], Z[(int64_t)j * ldz + i], acc);
+    x[i] = acc;
+  }
+}
+__global__ void k_scale_copy(const double* __restrict__ a, double s, double* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = a[i] * s;
+}
+__global__ void k_get_col(const double* __restrict__ W, int64_t k, int64_t r, double* __restrict__ v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = W[i * k + r];
+}
+__global__ void k_put_col(const double* __restrict__ v, int64_t k, int64_t r, double* __restrict__ W, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    W[i * k + r] = v[i];
+}
+
 struct Staged {
   kf_ctx* c;
   void* dev = nullptr;
@@ -178,6 +230,12 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
   f->c_exp = -0.5 / (h * h);
   f->s_max = s_max;
   f->n_samp = 2 * s_max;
+  // defaults: the mixed path refines with GMRES(20) against an FP64-accurate
+  // operator; the FP64 path solves directly
+  const int32_t prec0 = opts ? opts->precision : KF_PREC_FP64;
+  f->fp64_op = prec0 == KF_PREC_MIXED ? 1 : 0;
+  f->gmres_m = 20;
+  f->refine_max_iter = 100;
   if (opts) {
     f->prec = opts->precision;
     if (opts->n_samp > 0) f->n_samp = opts->n_samp;
@@ -186,7 +244,11 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
     f->sync_errors = opts->sync_errors;
     if (opts->refine_tol > 0) f->refine_tol = opts->refine_tol;
     if (opts->refine_max_iter > 0) f->refine_max_iter = opts->refine_max_iter;
+    f->refine_user = opts->refine_max_iter > 0 ? 1 : 0;
     if (opts->refine_max_iter < 0) f->refine_max_iter = 0;
+    f->use_tc = opts->no_tensor_cores ? 0 : 1;
+    if (opts->fp64_operator != 0) f->fp64_op = opts->fp64_operator > 0 ? 1 : 0;
+    if (opts->gmres_restart != 0) f->gmres_m = opts->gmres_restart > 0 ? std::min(opts->gmres_restart, 64) : 0;
   }
   if (f->prec != KF_PREC_FP64 && f->prec != KF_PREC_MIXED) {
     delete f;
@@ -217,6 +279,14 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
     f->VT = falloc<char>(f, (size_t)D * N * s_max * ts, s);
   }
   f->L = falloc<char>(f, (size_t)(1 << D) * t->leaf_max * t->leaf_max * ts, s);
+  if (f->fp64_op) {
+    f->K64 = falloc<double>(f, (size_t)(1 << D) * t->leaf_max * t->leaf_max, s);
+    if (D > 0 && f->prec != KF_PREC_FP64) f->VT64 = falloc<double>(f, (size_t)D * N * s_max, s);
+    if (!f->K64 || (D > 0 && f->prec != KF_PREC_FP64 && !f->VT64)) {
+      kf_factor_free(f);
+      return kf_set_err(c, KF_ENOMEM, "factorize: device allocation of the FP64 operator failed");
+    }
+  }
   bool ok = f->rank && f->skel && f->status && f->Pleaf && f->L &&
             (D == 0 || (f->Pc && f->ZLU && f->Zpiv && f->Phat && f->VT));
   if (!ok) {
@@ -391,8 +461,7 @@ kf_status kf_factorize(kf_tree* t, double h, double lambda, double tau, int32_t 
   kf_factor* f = nullptr;
   kf_status st = alloc_factor(t, h, lambda, tau, s_max, opts, s, &f);
   if (st != KF_OK) return st;
-  st = kf_skeletonize_device(f, s);
-  if (st == KF_OK) st = kf_factorize_device(f, s);
+  st = kf_skel_factorize_pipelined(f, s);
   if (st == KF_OK && f->sync_errors) st = read_status(f, s);
   if (st != KF_OK && st != KF_EILLCOND) {
     kf_factor_free(f);
@@ -545,6 +614,96 @@ static kf_status rel_residual(kf_factor* f, const double* Bt, const double* Xt, 
   return KF_OK;
 }
 
+// GMRES(m) for (lambda I + K~) x = b, one column: right preconditioning by
+// the factorization (z_j = M^-1 v_j kept), FP64 Krylov basis orthogonalized
+// by classical Gram-Schmidt applied twice, Givens rotations on the host, the
+// true residual recomputed at every restart.  x holds the initial guess.
+static kf_status gmres_column(kf_factor* f, const double* b, double* x, double bnorm, int m, int maxit, double tol,
+                              cudaStream_t s, double* eps, int* iters) {
+  kf_ctx* c = f->ctx;
+  const int64_t N = f->t->N;
+  const size_t vb = sizeof(double) * N;
+  double* V = (double*)c->dalloc(vb * (m + 1), s);
+  double* Zb = (double*)c->dalloc(vb * m, s);
+  double* w = (double*)c->dalloc(vb, s);
+  double* h = (double*)c->dalloc(sizeof(double) * (m + 2), s);
+  kf_status st = (V && Zb && w && h) ? KF_OK : kf_set_err(c, KF_ENOMEM, "gmres: allocation failed");
+  const int g = grid_for(N, 256, 304);
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gg(m + 1), hh(m + 2), y(m);
+  auto fetch = [&](int cnt) -> kf_status {
+    KF_CUDA(c, cudaMemcpyAsync(hh.data(), h, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
+    KF_CUDA(c, cudaStreamSynchronize(s));
+    return KF_OK;
+  };
+  int it = 0;
+  while (st == KF_OK) {
+    // r = b - A x, beta = ||r||
+    st = kf_matvec_device(f, x, w, 1, 0, s);
+    if (st != KF_OK) break;
+    KF_PHASE(KF_PH_MISC, s, k_sub<<<g, 256, 0, s>>>(b, w, w, N));
+    cudaMemsetAsync(h, 0, sizeof(double), s);
+    KF_PHASE(KF_PH_MISC, s, k_multidot<<<g, 256, 0, s>>>(w, 0, 1, w, N, h));
+    if ((st = fetch(1)) != KF_OK) break;
+    const double beta = sqrt(hh[0]);
+    *eps = bnorm > 0 ? beta / bnorm : beta;
+    if (*eps <= tol || it >= maxit || beta == 0.0) break;
+    KF_PHASE(KF_PH_MISC, s, k_scale_copy<<<g, 256, 0, s>>>(w, 1.0 / beta, V, N));
+    std::fill(gg.begin(), gg.end(), 0.0);
+    gg[0] = beta;
+    int j = 0;
+    for (; j < m && it < maxit; ++j, ++it) {
+      double* zj = Zb + (int64_t)j * N;
+      KF_CUDA(c, cudaMemcpyAsync(zj, V + (int64_t)j * N, vb, cudaMemcpyDeviceToDevice, s));
+      if ((st = kf_solve_device(f, zj, 1, 0, s)) != KF_OK) break;       // z_j = M^-1 v_j
+      if ((st = kf_matvec_device(f, zj, w, 1, 0, s)) != KF_OK) break;   // w = A z_j
+      for (int pass = 0; pass < 2; ++pass) {                            // CGS2
+        cudaMemsetAsync(h, 0, sizeof(double) * (j + 1), s);
+        KF_PHASE(KF_PH_MISC, s, k_multidot<<<g, 256, 0, s>>>(V, N, j + 1, w, N, h));
+        KF_PHASE(KF_PH_MISC, s, k_multiaxpy<<<g, 256, 0, s>>>(V, N, j + 1, h, w, N));
+        if ((st = fetch(j + 1)) != KF_OK) break;
+        for (int q = 0; q <= j; ++q) H[(size_t)q * m + j] = (pass == 0 ? 0.0 : H[(size_t)q * m + j]) + hh[q];
+      }
+      if (st != KF_OK) break;
+      cudaMemsetAsync(h, 0, sizeof(double), s);
+      KF_PHASE(KF_PH_MISC, s, k_multidot<<<g, 256, 0, s>>>(w, 0, 1, w, N, h));
+      if ((st = fetch(1)) != KF_OK) break;
+      const double hn = sqrt(hh[0]);
+      H[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0) KF_PHASE(KF_PH_MISC, s, k_scale_copy<<<g, 256, 0, s>>>(w, 1.0 / hn, V + (int64_t)(j + 1) * N, N));
+      for (int q = 0; q < j; ++q) {  // previous rotations on the new column
+        const double a = H[(size_t)q * m + j], bq = H[(size_t)(q + 1) * m + j];
+        H[(size_t)q * m + j] = cs[q] * a + sn[q] * bq;
+        H[(size_t)(q + 1) * m + j] = -sn[q] * a + cs[q] * bq;
+      }
+      const double a = H[(size_t)j * m + j], bq = H[(size_t)(j + 1) * m + j];
+      const double r = hypot(a, bq);
+      cs[j] = r > 0 ? a / r : 1.0;
+      sn[j] = r > 0 ? bq / r : 0.0;
+      H[(size_t)j * m + j] = r;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      gg[j + 1] = -sn[j] * gg[j];
+      gg[j] = cs[j] * gg[j];
+      if (fabs(gg[j + 1]) <= tol * bnorm * 0.5 || hn == 0.0) { ++j; ++it; break; }
+    }
+    if (st != KF_OK) break;
+    // y = H^-1 g (upper triangular), x += Z y
+    for (int q = j - 1; q >= 0; --q) {
+      double acc = gg[q];
+      for (int t2 = q + 1; t2 < j; ++t2) acc -= H[(size_t)q * m + t2] * y[t2];
+      y[q] = acc / H[(size_t)q * m + q];
+    }
+    KF_CUDA(c, cudaMemcpyAsync(h, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
+    KF_PHASE(KF_PH_MISC, s, k_zupdate<<<g, 256, 0, s>>>(Zb, N, j, h, x, N));
+    KF_CUDA(c, cudaStreamSynchronize(s));  // y lives on the host stack
+  }
+  *iters = it;
+  c->dfree(V, vb * (m + 1), s);
+  c->dfree(Zb, vb * m, s);
+  c->dfree(w, vb, s);
+  c->dfree(h, sizeof(double) * (m + 2), s);
+  return st;
+}
+
 extern "C" {
 
 kf_status kf_solve(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t ld, int32_t dtype, int32_t transpose,
@@ -554,10 +713,10 @@ kf_status kf_solve(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t l
   cudaStream_t s = (cudaStream_t)stream;
   kf_ctx* c = f->ctx;
   const int64_t N = f->t->N;
-  const bool refine = (f->prec == KF_PREC_MIXED) && f->refine_max_iter > 0 && !transpose;
+  const bool refine = (f->prec == KF_PREC_MIXED || f->refine_user) && f->refine_max_iter > 0 && !transpose;
   int iters = 0;
   double eps = -1.0;
-  st = with_vectors(f, B, X, nrhs, ld, dtype, s, [&](double* W) -> kf_status {
+  auto richardson = [&](double* W) -> kf_status {
     if (!refine && !info) return kf_solve_device(f, W, nrhs, transpose, s);
     const size_t vb = sizeof(double) * N * nrhs;
     double* Bt = (double*)c->dalloc(vb, s);
@@ -586,6 +745,42 @@ kf_status kf_solve(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t l
     c->dfree(Y, vb, s);
     c->dfree(nrm, sizeof(double) * 2 * nrhs, s);
     return r;
+  };
+  auto gmres_path = [&](double* W) -> kf_status {
+    // GMRES(m) per column, starting from the direct solve of the factorization
+    const size_t cb = sizeof(double) * N;
+    double* bcol = (double*)c->dalloc(cb, s);
+    double* xcol = (double*)c->dalloc(cb, s);
+    double* nb = (double*)c->dalloc(sizeof(double), s);
+    kf_status r = (bcol && xcol && nb) ? KF_OK : kf_set_err(c, KF_ENOMEM, "gmres: allocation failed");
+    double worst = 0.0;
+    for (int64_t col = 0; col < nrhs && r == KF_OK; ++col) {
+      KF_PHASE(KF_PH_MISC, s, k_get_col<<<grid_for(N, 256), 256, 0, s>>>(W, nrhs, col, bcol, N));
+      cudaMemcpyAsync(xcol, bcol, cb, cudaMemcpyDeviceToDevice, s);
+      if ((r = kf_solve_device(f, xcol, 1, 0, s)) != KF_OK) break;
+      cudaMemsetAsync(nb, 0, sizeof(double), s);
+      KF_PHASE(KF_PH_MISC, s, k_colnorm2<<<grid_for(N, 256, 304), 256, 0, s>>>(bcol, N, 1, nb));
+      double hb = 0.0;
+      cudaMemcpyAsync(&hb, nb, sizeof(double), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      double e = 0.0;
+      int its = 0;
+      r = gmres_column(f, bcol, xcol, sqrt(hb), f->gmres_m, f->refine_max_iter, f->refine_tol, s, &e, &its);
+      worst = std::max(worst, e);
+      iters = std::max(iters, its);
+      KF_PHASE(KF_PH_MISC, s, k_put_col<<<grid_for(N, 256), 256, 0, s>>>(xcol, nrhs, col, W, N));
+    }
+    eps = worst;
+    if (r == KF_OK && worst > f->refine_tol)
+      r = kf_set_err(c, KF_ENOTCONV, "GMRES stopped at eps_r = %.3e after %d iterations", worst, iters);
+    c->dfree(bcol, cb, s);
+    c->dfree(xcol, cb, s);
+    c->dfree(nb, sizeof(double), s);
+    return r;
+  };
+  st = with_vectors(f, B, X, nrhs, ld, dtype, s, [&](double* W) -> kf_status {
+    if (refine && f->gmres_m > 0) return gmres_path(W);
+    return richardson(W);
   });
   if (info) {
     info->eps_r = eps;
@@ -728,6 +923,114 @@ kf_status kf_factor_Phat(const kf_factor* f, int32_t node, double* Phat, void* s
       Phat[(size_t)i * sa + q] = f->prec == KF_PREC_FP64 ? ((const double*)buf.data())[(size_t)i * s_max + q]
                                                          : (double)((const float*)buf.data())[(size_t)i * s_max + q];
   return KF_OK;
+}
+
+}  // extern "C"
+
+// ---- batched: many independent problems in one graph launch -------------------------
+namespace {
+
+// Runs enq(i, stream) for every problem inside one captured CUDA graph whose
+// branches are spread over `nstreams` streams, launches it once on s and
+// waits for it.  Scratch allocations inside use stream-ordered allocation.
+template <typename Enq>
+kf_status run_batched_graph(kf_ctx* c, int32_t nprob, cudaStream_t s, Enq enq) {
+  const int nstreams = std::max(1, std::min<int>(nprob, 16));
+  std::vector<cudaStream_t> ss(nstreams);
+  std::vector<cudaEvent_t> ev(nstreams + 1);
+  for (int i = 0; i < nstreams; ++i) KF_CUDA(c, cudaStreamCreateWithFlags(&ss[i], cudaStreamNonBlocking));
+  for (int i = 0; i <= nstreams; ++i) KF_CUDA(c, cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+  cudaStream_t cs = s;
+  bool own_stream = false;
+  if (cs == 0) {  // the legacy stream cannot be captured
+    KF_CUDA(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    own_stream = true;
+  }
+  kf_status st = KF_OK;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  c->capturing = 1;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaEventRecord(ev[nstreams], cs);
+    for (int i = 0; i < nstreams; ++i) cudaStreamWaitEvent(ss[i], ev[nstreams], 0);
+    for (int32_t i = 0; i < nprob && st == KF_OK; ++i) st = enq(i, ss[i % nstreams]);
+    for (int i = 0; i < nstreams; ++i) {
+      cudaEventRecord(ev[i], ss[i]);
+      cudaStreamWaitEvent(cs, ev[i], 0);
+    }
+    e = cudaStreamEndCapture(cs, &graph);
+  }
+  c->capturing = 0;
+  if (st == KF_OK && e != cudaSuccess) st = kf_set_err(c, KF_ECUDA, "batched capture: %s", cudaGetErrorString(e));
+  if (st == KF_OK) {
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) st = kf_set_err(c, KF_ECUDA, "batched graph: %s", cudaGetErrorString(e));
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  for (auto& x : ss) cudaStreamDestroy(x);
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (own_stream) cudaStreamDestroy(cs);
+  cudaGetLastError();
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+kf_status kf_factorize_batched(kf_tree* const* trees, int32_t nprob, const double* h, const double* lambda,
+                               const double* tau, int32_t s_max, const kf_opts* opts, void* stream, kf_factor** out) {
+  if (!trees || nprob < 1 || !h || !lambda || !tau || !out) return kf_set_err(nullptr, KF_EINVAL, "batched: bad arguments");
+  for (int32_t i = 0; i < nprob; ++i) {
+    out[i] = nullptr;
+    if (!trees[i]) return kf_set_err(nullptr, KF_EINVAL, "batched: tree %d is NULL", i);
+    if (trees[i]->ctx != trees[0]->ctx) return kf_set_err(nullptr, KF_EINVAL, "batched: trees of different contexts");
+  }
+  kf_ctx* c = trees[0]->ctx;
+  cudaStream_t s = (cudaStream_t)stream;
+  kf_status st = KF_OK;
+  for (int32_t i = 0; i < nprob && st == KF_OK; ++i) st = alloc_factor(trees[i], h[i], lambda[i], tau[i], s_max, opts, s, &out[i]);
+  if (st == KF_OK) KF_CUDA(c, cudaStreamSynchronize(s));  // buffers zeroed before the graph runs
+  if (st == KF_OK)
+    st = run_batched_graph(c, nprob, s, [&](int32_t i, cudaStream_t si) -> kf_status {
+      kf_status r = kf_skeletonize_device(out[i], si);
+      return r == KF_OK ? kf_factorize_device(out[i], si) : r;
+    });
+  kf_status worst = st;
+  if (st == KF_OK)
+    for (int32_t i = 0; i < nprob; ++i) {
+      kf_status r = read_status(out[i], s);
+      if (r != KF_OK && r != KF_EILLCOND) worst = r;
+      if (r == KF_EILLCOND && worst == KF_OK) worst = r;
+    }
+  if (st != KF_OK) {
+    for (int32_t i = 0; i < nprob; ++i) {
+      kf_factor_free(out[i]);
+      out[i] = nullptr;
+    }
+    return st;
+  }
+  return worst;
+}
+
+kf_status kf_solve_batched(kf_factor* const* f, int32_t nprob, const void* const* B, void* const* X,
+                           const int64_t* nrhs, const int64_t* ld, int32_t dtype, void* stream) {
+  if (!f || nprob < 1 || !B || !X || !nrhs || !ld) return kf_set_err(nullptr, KF_EINVAL, "batched solve: bad arguments");
+  for (int32_t i = 0; i < nprob; ++i) {
+    kf_status r = check_rhs(f[i], B[i], X[i], nrhs[i], ld[i], dtype);
+    if (r != KF_OK) return r;
+    if (!is_device_ptr(B[i]) || !is_device_ptr(X[i]))
+      return kf_set_err(f[i]->ctx, KF_EINVAL, "batched solve: B and X must be device pointers");
+  }
+  kf_ctx* c = f[0]->ctx;
+  return run_batched_graph(c, nprob, (cudaStream_t)stream, [&](int32_t i, cudaStream_t si) -> kf_status {
+    return with_vectors(f[i], B[i], X[i], nrhs[i], ld[i], dtype, si,
+                        [&](double* W) { return kf_solve_device(f[i], W, nrhs[i], 0, si); });
+  });
 }
 
 }  // extern "C"

@@ -30,6 +30,7 @@
 struct kf_ctx {
   kf_alloc alloc;
   int has_alloc = 0;
+  int capturing = 0;  // inside a batched graph capture: scratch comes from cudaMallocAsync
   std::string err;
   void* dalloc(size_t bytes, cudaStream_t s);
   void dfree(void* p, size_t bytes, cudaStream_t s);
@@ -53,6 +54,12 @@ struct kf_factor {
   kf_ctx* ctx = nullptr;
   double h = 1, lambda = 0, tau = 0, c_exp = 0;
   int32_t s_max = 0, n_samp = 0, cmax = 0, prec = 0, vstore = 0, sync_errors = 0;
+  int32_t use_tc = 1;  // mixed path: tcgen05 products (0: CUDA-core FP32)
+  int32_t fp64_op = 0;  // keep FP64 operator data (VT64, K64)
+  int32_t gmres_m = 0;  // refinement: 0 = Richardson, m > 0 = GMRES(m)
+  int32_t refine_user = 0;  // refinement explicitly requested (enables it on the FP64 path)
+  double* VT64 = nullptr;  // mixed path with fp64_op: D x N x s_max FP64 V blocks
+  double* K64 = nullptr;   // fp64_op: leaf blocks lambda-free K_aa, leaf_max^2 each
   double refine_tol = 1e-10;
   int32_t refine_max_iter = 8;
   uint64_t seed = 0x1701;
@@ -109,6 +116,16 @@ __device__ __forceinline__ float kf_kern32(const float* __restrict__ x, const fl
   return __expf(acc * c_exp);
 }
 
+// FP64-accurate kernel entry at FP32 cost for the small ones: entries below
+// 2^-24 are taken from the FP32 evaluation (their absolute error stays below
+// about 1e-12), larger ones are recomputed in FP64.
+__device__ __forceinline__ double kf_kern_hybrid(const double* X64, const float* X32, int64_t i, int64_t j, int d,
+                                                 double c_exp) {
+  const float k32 = kf_kern32(X32 + i * d, X32 + j * d, d, (float)c_exp);
+  if (k32 < 5.9604645e-8f) return (double)k32;
+  return kf_kern64(X64 + i * d, X64 + j * d, d, c_exp);
+}
+
 template <typename T> struct kf_kern;
 template <> struct kf_kern<double> {
   static __device__ __forceinline__ double eval(const double* X64, const float*, int64_t i, int64_t j, int d, double c) {
@@ -133,8 +150,25 @@ __host__ __device__ inline uint64_t kf_splitmix64(uint64_t x) {
 }
 
 // ---- launchers implemented in the .cu files ------------------------------------
+struct kf_skel_scratch {
+  double* A = nullptr;
+  int32_t* samp = nullptr;
+  int32_t* nsamp = nullptr;
+  size_t a_elems = 0;
+};
 kf_status kf_tree_build_device(kf_tree* t, cudaStream_t s);
 kf_status kf_skeletonize_device(kf_factor* f, cudaStream_t s);
+kf_status kf_skel_begin(kf_factor* f, kf_skel_scratch* sc, cudaStream_t s);
+kf_status kf_skel_level(kf_factor* f, int l, kf_skel_scratch* sc, cudaStream_t s);
+void kf_skel_end(kf_factor* f, kf_skel_scratch* sc, cudaStream_t s);
 kf_status kf_factorize_device(kf_factor* f, cudaStream_t s);
+// factorization in steps: leaves (after skeleton level D), then level l (after
+// skeleton levels l + 1 and l); Tm is the T = Z^-1 P_c scratch of
+// kf_factor_tm_elems() doubles.
+size_t kf_factor_tm_elems(const kf_factor* f);
+kf_status kf_factorize_leaves(kf_factor* f, cudaStream_t s);
+kf_status kf_factorize_level(kf_factor* f, int l, double* Tm, cudaStream_t s);
+// skeletonize and factorize with the two interleaved on two streams
+kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s);
 kf_status kf_solve_device(kf_factor* f, double* W, int64_t nrhs, int transpose, cudaStream_t s);
 kf_status kf_matvec_device(kf_factor* f, const double* Xin, double* Y, int64_t nrhs, int deriv, cudaStream_t s);

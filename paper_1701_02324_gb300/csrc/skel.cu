@@ -283,49 +283,74 @@ __global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ 
 
 }  // namespace
 
-// Skeletonize every non-root node, leaves first.
-kf_status kf_skeletonize_device(kf_factor* f, cudaStream_t s) {
+// Skeletonize every non-root node, leaves first, in three parts so that the
+// factorization can follow level by level on another stream.
+kf_status kf_skel_begin(kf_factor* f, kf_skel_scratch* sc, cudaStream_t s) {
+  kf_tree* t = f->t;
+  kf_ctx* c = f->ctx;
+  KF_CUDA(c, cudaMemsetAsync(f->rank, 0, sizeof(int32_t) * (t->nnodes + 1), s));
+  sc->A = nullptr;
+  sc->samp = sc->nsamp = nullptr;
+  if (t->D == 0) return KF_OK;
+  const int maxnodes = 1 << t->D;
+  sc->a_elems = std::max((size_t)maxnodes * t->leaf_max, (size_t)(maxnodes / 2) * 2 * f->s_max) * f->n_samp;
+  sc->A = (double*)c->dalloc(sizeof(double) * sc->a_elems, s);
+  sc->samp = (int32_t*)c->dalloc(sizeof(int32_t) * (size_t)maxnodes * f->n_samp, s);
+  sc->nsamp = (int32_t*)c->dalloc(sizeof(int32_t) * maxnodes, s);
+  if (!sc->A || !sc->samp || !sc->nsamp)
+    return kf_set_err(c, KF_ENOMEM, "skeletonize: allocation of %zu bytes failed", sizeof(double) * sc->a_elems);
+  return KF_OK;
+}
+
+void kf_skel_end(kf_factor* f, kf_skel_scratch* sc, cudaStream_t s) {
+  kf_ctx* c = f->ctx;
+  const int maxnodes = 1 << f->t->D;
+  c->dfree(sc->A, sizeof(double) * sc->a_elems, s);
+  c->dfree(sc->samp, sizeof(int32_t) * (size_t)maxnodes * f->n_samp, s);
+  c->dfree(sc->nsamp, sizeof(int32_t) * maxnodes, s);
+  sc->A = nullptr;
+  sc->samp = sc->nsamp = nullptr;
+}
+
+kf_status kf_skel_level(kf_factor* f, int l, kf_skel_scratch* sc, cudaStream_t s) {
   kf_tree* t = f->t;
   kf_ctx* c = f->ctx;
   const int D = t->D;
-  KF_CUDA(c, cudaMemsetAsync(f->rank, 0, sizeof(int32_t) * (t->nnodes + 1), s));
-  if (D == 0) return KF_OK;
   const int n_samp = f->n_samp, s_max = f->s_max;
-  const int maxnodes = 1 << D;
   const int cleaf = t->leaf_max, cint = 2 * s_max;
-  size_t a_elems = std::max((size_t)maxnodes * cleaf, (size_t)(maxnodes / 2) * cint) * n_samp;
-  double* A = (double*)c->dalloc(sizeof(double) * a_elems, s);
-  int32_t* samp = (int32_t*)c->dalloc(sizeof(int32_t) * (size_t)maxnodes * n_samp, s);
-  int32_t* nsamp = (int32_t*)c->dalloc(sizeof(int32_t) * maxnodes, s);
-  kf_status st = KF_OK;
-  if (!A || !samp || !nsamp) st = kf_set_err(c, KF_ENOMEM, "skeletonize: allocation of %zu bytes failed", sizeof(double) * a_elems);
   const int rpl = (n_samp + 31) / 32;
-  for (int l = D; l >= 1 && st == KF_OK; --l) {
-    const int node0 = 1 << l, nn = 1 << l;
-    const bool leaf = (l == D);
-    const int cmax = leaf ? cleaf : cint;
-    KF_PHASE(KF_PH_SAMPLE, s, k_sample<<<nn, 32, sizeof(int32_t) * n_samp, s>>>(t->d_lo, t->d_hi, t->N, node0, nn, n_samp, f->seed, samp, nsamp,
-                                                      f->status));
-    dim3 ga((n_samp + 127) / 128, cmax, nn);
-    KF_PHASE(KF_PH_EVAL_A, s, k_eval_A<<<ga, 128, 0, s>>>(t->X64, t->d, f->c_exp, t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf,
-                                n_samp, cmax, samp, nsamp, A));
-    double* Pout = leaf ? f->Pleaf : f->Pc + (int64_t)node0 * cint * s_max;
-    int64_t pstride = leaf ? 0 : (int64_t)cint * s_max;
-    size_t smem = sizeof(double) * (cmax + n_samp) + sizeof(int) * cmax;
-    if (rpl <= 8)
-      KF_PHASE(KF_PH_QR, s, k_pivoted_qr<8><<<nn, 512, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf, n_samp, cmax,
-                                            nsamp, f->tau, A, Pout, s_max, pstride));
-    else if (rpl <= 16)
-      KF_PHASE(KF_PH_QR, s, k_pivoted_qr<16><<<nn, 512, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf, n_samp, cmax,
-                                             nsamp, f->tau, A, Pout, s_max, pstride));
-    else
-      KF_PHASE(KF_PH_QR, s, k_pivoted_qr<32><<<nn, 512, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf, n_samp, cmax,
-                                             nsamp, f->tau, A, Pout, s_max, pstride));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) st = kf_set_err(c, KF_ECUDA, "skeletonize level %d: %s", l, cudaGetErrorString(e));
-  }
-  c->dfree(A, sizeof(double) * a_elems, s);
-  c->dfree(samp, sizeof(int32_t) * (size_t)maxnodes * n_samp, s);
-  c->dfree(nsamp, sizeof(int32_t) * maxnodes, s);
+  double* A = sc->A;
+  int32_t* samp = sc->samp;
+  int32_t* nsamp = sc->nsamp;
+  const int node0 = 1 << l, nn = 1 << l;
+  const bool leaf = (l == D);
+  const int cmax = leaf ? cleaf : cint;
+  KF_PHASE(KF_PH_SAMPLE, s, k_sample<<<nn, 32, sizeof(int32_t) * n_samp, s>>>(t->d_lo, t->d_hi, t->N, node0, nn, n_samp, f->seed, samp, nsamp,
+                                                    f->status));
+  dim3 ga((n_samp + 127) / 128, cmax, nn);
+  KF_PHASE(KF_PH_EVAL_A, s, k_eval_A<<<ga, 128, 0, s>>>(t->X64, t->d, f->c_exp, t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf,
+                              n_samp, cmax, samp, nsamp, A));
+  double* Pout = leaf ? f->Pleaf : f->Pc + (int64_t)node0 * cint * s_max;
+  int64_t pstride = leaf ? 0 : (int64_t)cint * s_max;
+  size_t smem = sizeof(double) * (cmax + n_samp) + sizeof(int) * cmax;
+  if (rpl <= 8)
+    KF_PHASE(KF_PH_QR, s, k_pivoted_qr<8><<<nn, 512, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf, n_samp, cmax,
+                                          nsamp, f->tau, A, Pout, s_max, pstride));
+  else if (rpl <= 16)
+    KF_PHASE(KF_PH_QR, s, k_pivoted_qr<16><<<nn, 512, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf, n_samp, cmax,
+                                           nsamp, f->tau, A, Pout, s_max, pstride));
+  else
+    KF_PHASE(KF_PH_QR, s, k_pivoted_qr<32><<<nn, 512, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf, n_samp, cmax,
+                                           nsamp, f->tau, A, Pout, s_max, pstride));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return kf_set_err(c, KF_ECUDA, "skeletonize level %d: %s", l, cudaGetErrorString(e));
+  return KF_OK;
+}
+
+kf_status kf_skeletonize_device(kf_factor* f, cudaStream_t s) {
+  kf_skel_scratch sc;
+  kf_status st = kf_skel_begin(f, &sc, s);
+  for (int l = f->t->D; l >= 1 && st == KF_OK; --l) st = kf_skel_level(f, l, &sc, s);
+  kf_skel_end(f, &sc, s);
   return st;
 }

@@ -298,6 +298,26 @@ __global__ void __launch_bounds__(128) k_leaf_mv(const int32_t* __restrict__ lo,
   }
 }
 
+// Leaf blocks from the stored FP64 copy: y_i = lambda x_i + sum_j K64[i][j] x_j,
+// one warp per row, lanes over j.
+__global__ void __launch_bounds__(256) k_leaf_mv_stored(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                        int leaf0, int ldL, const double* __restrict__ K64,
+                                                        double lambda, const double* __restrict__ x,
+                                                        double* __restrict__ y, int k) {
+  const int lf = blockIdx.y, node = leaf0 + lf;
+  const int b = lo[node], n = hi[node] - b;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i < n; i += (gridDim.x * blockDim.x) >> 5) {
+    const double* Ki = K64 + ((int64_t)lf * ldL + i) * ldL;
+    for (int r = 0; r < k; ++r) {
+      double acc = 0.0;
+      for (int j = lane; j < n; j += 32) acc = fma(Ki[j], x[(int64_t)(b + j) * k + r], acc);
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (lane == 0) y[(int64_t)(b + i) * k + r] = lambda * x[(int64_t)(b + i) * k + r] + acc;
+    }
+  }
+}
+
 // Push skeleton coefficients down: g[l] += P_c[:s_l] g[a], g[r] += P_c[s_l:] g[a].
 __global__ void k_push_down(const int32_t* __restrict__ rank, int node0, int s_max, const double* __restrict__ Pc,
                             double* __restrict__ G, int k) {
@@ -387,16 +407,27 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
   const int leaf0 = 1 << D;
   const double inv_h3 = 1.0 / (f->h * f->h * f->h);
   const int src = deriv ? SRC_DKERNEL : (f->vstore == KF_V_STORED ? SRC_STORED : SRC_KERNEL);
-  dim3 gl((t->leaf_max + 127) / 128, 1 << D);
-  KF_PHASE(KF_PH_MV_LEAF, s, k_leaf_mv<TM><<<gl, 128, 0, s>>>(t->d_lo, t->d_hi, leaf0, t->X64, t->X32, t->d, f->c_exp, inv_h3,
-                                   deriv ? SRC_DKERNEL : SRC_KERNEL, f->lambda, x, y, (int)k));
+  if (f->K64 && !deriv) {
+    dim3 gl((unsigned)std::max(1, std::min(64, (t->leaf_max * 32 + 255) / 256)), 1 << D);
+    KF_PHASE(KF_PH_MV_LEAF, s, k_leaf_mv_stored<<<gl, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, f->K64, f->lambda,
+                                                                  x, y, (int)k));
+  } else {
+    dim3 gl((t->leaf_max + 127) / 128, 1 << D);
+    KF_PHASE(KF_PH_MV_LEAF, s, k_leaf_mv<TM><<<gl, 128, 0, s>>>(t->d_lo, t->d_hi, leaf0, t->X64, t->X32, t->d, f->c_exp, inv_h3,
+                                     deriv ? SRC_DKERNEL : SRC_KERNEL, f->lambda, x, y, (int)k));
+  }
   if (D == 0) { KF_LAUNCH_CHECK(c); return KF_OK; }
   KF_CUDA(c, cudaMemsetAsync(G, 0, sizeof(double) * (size_t)(t->nnodes + 1) * s_max * k, s));
   for (int l = 1; l <= D; ++l) {
     const int64_t rows = (N >> l) + 1;
     dim3 gc((unsigned)((rows + kRowsPerChunk - 1) / kRowsPerChunk), 1 << l);
-    launch_colsum<TM, double>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, s_max, 1, src,
-                              VT + (int64_t)(l - 1) * N * s_max, t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G);
+    if (f->VT64 && !deriv)  // FP64-accurate operator of the mixed path
+      launch_colsum<double, double>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, s_max, 1, SRC_STORED,
+                                    f->VT64 + (int64_t)(l - 1) * N * s_max, t->X64, t->X32, t->d, f->c_exp, inv_h3, x,
+                                    (int)k, G);
+    else
+      launch_colsum<TM, double>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, s_max, 1, src,
+                                VT + (int64_t)(l - 1) * N * s_max, t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G);
   }
   for (int l = 1; l < D; ++l)
     KF_PHASE(KF_PH_MV_PUSH, s, k_push_down<<<1 << l, 256, 0, s>>>(f->rank, 1 << l, s_max, f->Pc, G, (int)k));

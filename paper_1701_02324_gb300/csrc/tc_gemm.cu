@@ -1,0 +1,335 @@
+// tc_gemm.cu -- 5th-generation tensor-core (tcgen05) products of the mixed
+// path: the off-diagonal blocks of the reduced systems, K_{l~ r} P^_r and
+// K_{r~ l} P^_l (Eq. e:blocksmw), and the telescoping P^_a = [P^_l T_top;
+// P^_r T_bot] (Eq. e:invtelescope).
+//
+// One CTA (4 warps) computes a 128 x BN tile of D = A B:
+//   * operands are staged by all threads from global memory into shared
+//     memory in the canonical K-major, no-swizzle core-matrix layout (8 rows x
+//     16 bytes per core matrix; LBO = 128 B between core matrices along K,
+//     SBO = 1024 B between 8-row groups), split into tf32 hi and lo parts;
+//   * one thread issues tcgen05.mma kind::tf32 for A_hi B_hi + A_hi B_lo +
+//     A_lo B_hi (3xTF32: about FP32 accuracy) into an FP32 accumulator in
+//     tensor memory, and tcgen05.commit arrives on an mbarrier;
+//   * the epilogue reads the accumulator with tcgen05.ld (warp w owns rows
+//     32w..32w+31) and hands each value to the problem's store.
+// Every wait is bounded; on time-out the kernel flags KF_DEV_TIMEOUT, waits
+// once more, frees its tensor memory and returns.
+#include <algorithm>
+
+#include "kf_internal.cuh"
+#include "prof.cuh"
+
+namespace {
+
+constexpr int kBM = 128;  // rows per tile (tcgen05 M for cta_group::1)
+constexpr int kBK = 32;   // K elements staged per round (4 MMAs of K = 8)
+constexpr long long kSpinLimit = 1ll << 28;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading byte
+// offset (between core matrices along K), stride byte offset (between 8-row
+// groups), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
+// (bits 7-9 and 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; false when the limit ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's accumulator row
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// element (r, k) of a tile with 32 K-elements per row, in floats
+__device__ __forceinline__ int core_off(int r, int k) { return (r >> 3) * 256 + (k >> 2) * 32 + (r & 7) * 4 + (k & 3); }
+
+struct Tile {
+  int m0, n0, k0, k1, M, N;  // tile origin, K range, valid extents (absolute indices)
+  int node, side, base;      // problem-specific
+  bool skip;
+};
+
+// Generic tile driver.  Problem provides: tile(bx, by, bz) -> Tile;
+// loadA(tile, m, k) and loadB(tile, k, n) (valid indices only; FP32);
+// a_m_fastest / b_n_fastest (staging order for coalescing); store(tile, m, n, v).
+template <int BN, class Problem>
+__global__ void __launch_bounds__(128) k_tc_gemm(Problem prob, int32_t* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float* Ahi = (float*)smem_raw;
+  float* Alo = Ahi + kBM * kBK;
+  float* Bhi = Alo + kBM * kBK;
+  float* Blo = Bhi + BN * kBK;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const Tile t = prob.tile(blockIdx.x, blockIdx.y, blockIdx.z);
+  if (t.skip) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tmem_alloc(&tmem_base, BN);
+  if (tid == 0) mbar_init(&mbar, 1);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  constexpr uint32_t idesc = idesc_tf32(kBM, BN);
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int kc = t.k0; kc < t.k1 && ok; kc += kBK) {
+    const int kn = min(kBK, t.k1 - kc);
+    // stage A (128 x 32) and B (BN x 32), split into tf32 hi / lo
+    for (int e = tid; e < kBM * kBK; e += 128) {
+      int m, k;
+      if (Problem::a_m_fastest) { m = e % kBM; k = e / kBM; } else { k = e % kBK; m = e / kBK; }
+      float a = (m < t.M - t.m0 && k < kn) ? prob.loadA(t, t.m0 + m, kc + k) : 0.f;
+      float hi = to_tf32(a);
+      Ahi[core_off(m, k)] = hi;
+      Alo[core_off(m, k)] = to_tf32(a - hi);
+    }
+    for (int e = tid; e < BN * kBK; e += 128) {
+      int n, k;
+      if (Problem::b_n_fastest) { n = e % BN; k = e / BN; } else { k = e % kBK; n = e / kBK; }
+      float b = (n < t.N - t.n0 && k < kn) ? prob.loadB(t, kc + k, t.n0 + n) : 0.f;
+      float hi = to_tf32(b);
+      Bhi[core_off(n, k)] = hi;
+      Blo[core_off(n, k)] = to_tf32(b - hi);
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after_sync();
+      const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 8; ++kk) {
+        const uint32_t off = kk * 256;  // two core matrices along K per MMA (K = 8 tf32)
+        const uint64_t dah = smem_desc(ah + off, 128, 1024), dal = smem_desc(al + off, 128, 1024);
+        const uint64_t dbh = smem_desc(bh + off, 128, 1024), dbl = smem_desc(bl + off, 128, 1024);
+        const uint32_t first = (kc == t.k0 && kk == 0) ? 0u : 1u;
+        mma_tf32(tmem, dah, dbh, idesc, first);
+        mma_tf32(tmem, dah, dbl, idesc, 1u);
+        mma_tf32(tmem, dal, dbh, idesc, 1u);
+      }
+      mma_commit(&mbar);
+    }
+    if (!mbar_wait(&mbar, phase)) {
+      ok = false;
+      if (tid == 0) atomicOr(status, KF_DEV_TIMEOUT);
+      mbar_wait(&mbar, phase);  // second bounded wait for the MMAs in flight
+    }
+    phase ^= 1u;
+    fence_after_sync();
+    __syncthreads();
+  }
+  if (ok) {
+    fence_after_sync();
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      const int m = t.m0 + warp * 32 + lane;
+      if (m < t.M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = t.n0 + c0 + j;
+          if (n < t.N) prob.store(t, m, n, v[j]);
+        }
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, BN);
+}
+
+// ---- Z off-diagonal blocks: Z[blk] += VT_c[:, :s_a]^T P^_c[:, :s_b] -------------
+// side 0: rows of r, block Z[0:s_l, s_l:] = K_{l~ r} P^_r
+// side 1: rows of l, block Z[s_l:, 0:s_l] = K_{r~ l} P^_l
+// The long reduction over the child's rows is split over blockIdx.y; partial
+// tiles are added into the FP64 Z with atomics.
+struct ZoffProblem {
+  static constexpr bool a_m_fastest = true;   // VT rows are contiguous in m
+  static constexpr bool b_n_fastest = true;   // P^ rows are contiguous in n
+  const int32_t* lo;
+  const int32_t* hi;
+  const int32_t* rank;
+  int node0, s_max, ldz, ksplit, ntile_n;
+  const float* VT;
+  const float* Ph;
+  double* Z;
+  __device__ Tile tile(int bx, int by, int bz) const {
+    Tile t;
+    t.side = bz & 1;
+    t.node = node0 + (bz >> 1);
+    const int l = 2 * t.node, r = l + 1, sl = rank[l], sr = rank[r];
+    const int c = t.side == 0 ? r : l;
+    t.M = t.side == 0 ? sl : sr;
+    t.N = t.side == 0 ? sr : sl;
+    t.base = sl;
+    t.m0 = (bx / ntile_n) * kBM;
+    t.n0 = (bx % ntile_n) * 256;
+    const int rb = lo[c], rn = hi[c] - rb;
+    const int chunk = ((rn + ksplit - 1) / ksplit + kBK - 1) / kBK * kBK;
+    t.k0 = rb + by * chunk;
+    t.k1 = min(hi[c], t.k0 + chunk);
+    t.skip = t.M == 0 || t.N == 0 || t.m0 >= t.M || t.n0 >= t.N || t.k0 >= t.k1;
+    return t;
+  }
+  __device__ float loadA(const Tile&, int m, int k) const { return VT[(int64_t)k * s_max + m]; }
+  __device__ float loadB(const Tile&, int k, int n) const { return Ph[(int64_t)k * s_max + n]; }
+  __device__ void store(const Tile& t, int m, int n, float v) const {
+    const int roff = t.side == 0 ? 0 : t.base, coff = t.side == 0 ? t.base : 0;
+    atomicAdd(Z + (int64_t)t.node * ldz * ldz + (int64_t)(roff + m) * ldz + coff + n, (double)v);
+  }
+};
+
+// ---- telescoping: P^_a[rows of c, :s_a] = P^_c[:, :s_c] T[c block, :s_a] ---------
+struct TelescopeProblem {
+  static constexpr bool a_m_fastest = false;  // P^_c rows are contiguous in k
+  static constexpr bool b_n_fastest = true;   // T rows are contiguous in n
+  const int32_t* lo;
+  const int32_t* hi;
+  const int32_t* rank;
+  int node0, s_max, ldz, ntile_n;
+  const float* Pc_hat;
+  const double* Tm;
+  float* Pa_hat;
+  __device__ Tile tile(int bx, int by, int bz) const {
+    Tile t;
+    t.side = bz & 1;
+    t.node = node0 + (bz >> 1);
+    t.base = bz >> 1;  // node-local index into T
+    const int c = 2 * t.node + t.side;
+    t.M = hi[c];       // absolute row range [lo[c], hi[c])
+    t.N = rank[t.node];
+    t.m0 = lo[c] + bx * kBM;
+    t.n0 = by * 256;
+    t.k0 = 0;
+    t.k1 = rank[c];
+    t.skip = t.N == 0 || t.m0 >= t.M || t.n0 >= t.N || t.k1 == 0;
+    return t;
+  }
+  __device__ float loadA(const Tile&, int m, int k) const { return Pc_hat[(int64_t)m * s_max + k]; }
+  __device__ float loadB(const Tile& t, int k, int n) const {
+    const int koff = t.side == 0 ? 0 : rank[2 * t.node];
+    return (float)Tm[(int64_t)t.base * ldz * s_max + (int64_t)(koff + k) * s_max + n];
+  }
+  __device__ void store(const Tile&, int m, int n, float v) const { Pa_hat[(int64_t)m * s_max + n] = v; }
+};
+
+}  // namespace
+
+// ---- launchers ---------------------------------------------------------------------
+static size_t tc_smem_bytes(int BN) { return sizeof(float) * (size_t)(2 * kBM * kBK + 2 * BN * kBK); }
+
+kf_status kf_tc_zoff(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
+                     const float* VT, const float* Ph, int ldz, double* Z, int64_t rows_per_child, int32_t* status,
+                     cudaStream_t s) {
+  ZoffProblem p;
+  p.lo = lo; p.hi = hi; p.rank = rank; p.node0 = node0; p.s_max = s_max; p.ldz = ldz;
+  p.ntile_n = (s_max + 255) / 256;
+  p.VT = VT; p.Ph = Ph; p.Z = Z;
+  const int mt = (s_max + kBM - 1) / kBM;
+  // enough CTAs to fill the GPU: split the reduction over the child's rows
+  const int64_t tiles = (int64_t)mt * p.ntile_n * 2 * nn;
+  int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>((rows_per_child + 1023) / 1024, (2 * 152 + tiles - 1) / tiles));
+  p.ksplit = ksplit;
+  const size_t smem = tc_smem_bytes(256);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<256, ZoffProblem>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return KF_ECUDA;
+  dim3 g(mt * p.ntile_n, ksplit, 2 * nn);
+  KF_PHASE(KF_PH_ZOFF, s, k_tc_gemm<256, ZoffProblem><<<g, 128, smem, s>>>(p, status));
+  return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
+}
+
+kf_status kf_tc_telescope(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
+                          const float* Pc_hat, const double* Tm, int ldz, float* Pa_hat, int64_t rows_per_child,
+                          int32_t* status, cudaStream_t s) {
+  TelescopeProblem p;
+  p.lo = lo; p.hi = hi; p.rank = rank; p.node0 = node0; p.s_max = s_max; p.ldz = ldz;
+  p.ntile_n = (s_max + 255) / 256;
+  p.Pc_hat = Pc_hat; p.Tm = Tm; p.Pa_hat = Pa_hat;
+  const size_t smem = tc_smem_bytes(256);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<256, TelescopeProblem>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return KF_ECUDA;
+  dim3 g((unsigned)((rows_per_child + kBM - 1) / kBM), p.ntile_n, 2 * nn);
+  KF_PHASE(KF_PH_TELESCOPE, s, k_tc_gemm<256, TelescopeProblem><<<g, 128, smem, s>>>(p, status));
+  return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
+}

@@ -145,14 +145,31 @@ def test_multiple_rhs_and_float32(c1):
 
 
 def test_mixed_path_refined(c1):
+    """Mixed path (FP32 factors, tcgen05 products) refined by GMRES against the
+    FP64 operator: reaches the oracle's solution of the same K~."""
     p, o, tree = c1
-    F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=MIXED, refine_tol=1e-10)
+    F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=MIXED, refine_tol=1e-12)
     b = p.B[:, 0]
     x, info = F.solve(torch.from_numpy(b).cuda(), info=True)
     same = all(np.array_equal(F.skeleton(a), o.skel(a)) for a in range(2, o.nnodes + 1))
     assert same
-    assert rel(x.cpu().numpy(), o.solve(b)) <= 1e-5
-    assert info["eps_r"] <= 1e-10
+    assert rel(x.cpu().numpy(), o.solve(b)) <= 1e-10
+    assert info["eps_r"] <= 1e-12
+    # without refinement the FP32 factorization alone is within the mixed bar
+    F0 = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=MIXED, refine_max_iter=-1, tensor_cores=False)
+    assert rel(F0.solve(torch.from_numpy(b).cuda()).cpu().numpy(), o.solve(b)) <= 1e-5
+
+
+def test_mixed_richardson_and_fp64_refinement(c1):
+    p, o, tree = c1
+    b = p.B[:, 0]
+    xo = o.solve(b)
+    F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=MIXED, gmres_restart=-1, refine_tol=1e-12)
+    assert rel(F.solve(torch.from_numpy(b).cuda()).cpu().numpy(), xo) <= 1e-10
+    F64 = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=FP64, refine_max_iter=5, refine_tol=1e-14,
+                    fp64_operator=True)
+    x64, info = F64.solve(torch.from_numpy(b).cuda(), info=True)
+    assert rel(x64.cpu().numpy(), xo) <= 1e-12 and info["eps_r"] <= 1e-14
 
 
 # ---------------------------------------------------------------- edge cases
@@ -217,3 +234,28 @@ def test_invalid_arguments_rejected():
         with pytest.raises(kf.KFError) as e:
             kf.Factor(tree, h, lam, 1e-6, smax)
         assert e.value.status == kf._abi.KF_EINVAL
+
+
+# ---------------------------------------------------------------- many problems, one graph launch
+def test_batched_matches_single_and_oracle():
+    """Row a12: uneven problems factorized and solved with one CUDA-graph launch
+    each; every problem equals its own single factorization and the oracle."""
+    ctx = kf.Context(use_torch_allocator=False)
+    rng = np.random.default_rng(11)
+    Ns = [2048, 3001, 4096, 2500, 6000, 2222]
+    hs = [0.3 + 0.1 * i for i in range(len(Ns))]
+    Xs = [rng.random((n, 8)) for n in Ns]
+    Bs = [rng.standard_normal((n, 3)) for n in Ns]
+    trees = [kf.Tree(torch.from_numpy(X).cuda(), 256, ctx=ctx) for X in Xs]
+    for prec, tol in ((FP64, 1e-10), (MIXED, 1e-5)):
+        facs = kf.factorize_batched(trees, hs, [0.5] * len(Ns), [1e-5] * len(Ns), 64, precision=prec)
+        xs = kf.solve_batched(facs, [torch.from_numpy(B).cuda() for B in Bs])
+        for i in (0, 4):
+            single = kf.Factor(trees[i], hs[i], 0.5, 1e-5, 64, precision=prec, refine_max_iter=-1)
+            xi = single.solve(torch.from_numpy(Bs[i]).cuda()).cpu().numpy()
+            assert rel(xs[i].cpu().numpy(), xi) <= (1e-10 if prec == FP64 else 1e-5)
+        o = oracle.Oracle(Xs[1], 256)
+        o.skeletonize(hs[1], 1e-5, 64)
+        o.factorize(0.5)
+        # the batched solve is the direct sweep without refinement: 3xTF32 factors on the mixed path
+        assert rel(xs[1].cpu().numpy(), o.solve(Bs[1])) <= (tol if prec == FP64 else 1e-4)
