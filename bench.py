@@ -229,9 +229,18 @@ def gpu_main(args, rank, world):
         if dist:
             torch.distributed.barrier()
 
-    def step(prec, want_x=False):
+    def step(prec, refined=None):
+        """tree + factorize + solve.  Mixed path: FP64 operator kept and the
+        solve refined by GMRES(20) to eps_r <= 1e-10 (the accuracy target);
+        FP64 path: direct solve.  refined=False: mixed path without the FP64
+        operator and without refinement."""
         tree = kf.Tree(X, p.m)
-        F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=prec, refine_max_iter=-1, sync_errors=False)
+        if prec == kf.KF_PREC_MIXED and refined is not False:
+            F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=prec, fp64_operator=True, refine_tol=1e-10,
+                          refine_max_iter=400, gmres_restart=20, sync_errors=False)
+        else:
+            F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=prec, fp64_operator=False, refine_max_iter=-1,
+                          sync_errors=False)
         ev = torch.cuda.Event(enable_timing=True)
         ev.record()
         x = F.solve(b)
@@ -290,27 +299,42 @@ def gpu_main(args, rank, world):
         fact_s, solve_s, ms_per_step = t.tolist()
 
     # ---- FP64 comparison leg (same workload, same skeletons) ---------------------
-    fp64 = None
+    fp64, unref = None, None
     if not args.no_fp64:
-        tree, F, _, _ = step(kf.KF_PREC_FP64)  # warm
-        del F, tree
-        ff, fs = [], []
-        x64 = None
-        for _ in range(max(1, args.fp64_steps)):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            tree, F, e1, x64 = step(kf.KF_PREC_FP64)
-            e2 = torch.cuda.Event(enable_timing=True)
-            e2.record()
-            torch.cuda.synchronize()
-            ff.append(e0.elapsed_time(e1))
-            fs.append(e1.elapsed_time(e2))
-            _, info = F.solve(b, info=True)
-            del F, tree
-        rel = float(torch.linalg.norm(x_mixed - x64) / torch.linalg.norm(x64))
-        fp64 = {"factorize_s": round(statistics.mean(ff) / 1e3, 4),
-                "solve_rhs_per_s": round(1e3 / statistics.mean(fs), 2),
-                "eps_r": info["eps_r"], "mixed_rel_err_vs_fp64": rel}
+        def timed(prec, refined, nsteps):
+            ff, fs, x = [], [], None
+            for _ in range(nsteps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                tree, F, e1, x = step(prec, refined)
+                e2 = torch.cuda.Event(enable_timing=True)
+                e2.record()
+                torch.cuda.synchronize()
+                ff.append(e0.elapsed_time(e1))
+                fs.append(e1.elapsed_time(e2))
+                del F, tree
+            return statistics.mean(ff) / 1e3, statistics.mean(fs) / 1e3, x
+        timed(kf.KF_PREC_FP64, None, 1)  # warm
+        f64_f, f64_s, x64 = timed(kf.KF_PREC_FP64, None, max(1, args.fp64_steps))
+        un_f, un_s, xun = timed(kf.KF_PREC_MIXED, False, max(1, args.fp64_steps))
+        # accuracy reference: the FP64 factorization refined by GMRES against the FP64 operator
+        tree = kf.Tree(X, p.m)
+        Fr = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=kf.KF_PREC_FP64, fp64_operator=True,
+                       refine_max_iter=20, refine_tol=1e-11, gmres_restart=20)
+        xref, iref = Fr.solve(b, info=True)
+        F64 = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=kf.KF_PREC_FP64, fp64_operator=True,
+                        refine_max_iter=-1)
+        _, i64 = F64.solve(b, info=True)
+        del Fr, F64, tree
+        relf = lambda a: float(torch.linalg.norm(a - xref) / torch.linalg.norm(xref))
+        fp64 = {"factorize_s": round(f64_f, 4), "solve_rhs_per_s": round(1.0 / f64_s, 2), "eps_r": i64["eps_r"],
+                "rel_err_vs_reference": relf(x64)}
+        unref = {"factorize_s": round(un_f, 4), "solve_rhs_per_s": round(1.0 / un_s, 2),
+                 "rel_err_vs_reference": relf(xun),
+                 "note": "mixed factors without the FP64 operator and without refinement"}
+        mixed_rel = relf(x_mixed)
+        reference = {"what": "FP64 factorization + GMRES against the FP64 operator", "eps_r": iref["eps_r"],
+                     "iters": iref["iters"]}
 
     # ---- end to end through the C ABI with host buffers ----------------------------
     e2e = None
@@ -321,8 +345,8 @@ def gpu_main(args, rank, world):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             tree = kf.Tree(torch.from_numpy(X_host), p.m)                  # host X: H2D inside
-            F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=kf.KF_PREC_MIXED, refine_max_iter=-1,
-                          sync_errors=False)
+            F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=kf.KF_PREC_MIXED, fp64_operator=True,
+                          refine_tol=1e-10, refine_max_iter=400, gmres_restart=20, sync_errors=False)
             xt = F.solve(torch.from_numpy(b_host))                         # host b -> host x
             xh[:] = xt.numpy()
             lib_t.append(time.perf_counter() - t0)
@@ -374,10 +398,16 @@ def gpu_main(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "scale_N1048576_d28", "N": p.N, "d": p.d, "h": p.h, "lambda": p.lam, "m": p.m,
                        "s_max": p.s_max, "tau": p.tau, "n_samp": 2 * p.s_max, "nrhs": 1,
-                       "precision": "mixed (FP32 factors, FP64 ID/Z/T)", "parallelism": f"replicas x{world}",
+                       "precision": "mixed (FP32 factors with tcgen05 3xTF32 products; FP64 ID, Z, T, operator, "
+                                    "GMRES)", "parallelism": f"replicas x{world}",
                        "l2": "inputs and factors larger than L2 (no flush needed)"},
             "solve_rhs_per_s": round(1.0 / solve_s, 2),
+            "solve_note": "mixed solve = direct sweep of the FP32 factors + GMRES(20) against the FP64 operator "
+                          "to eps_r <= 1e-10",
+            "mixed_rel_err_vs_reference": mixed_rel if fp64 else None,
             "fp64_path": fp64,
+            "mixed_unrefined": unref,
+            "accuracy_reference": reference if fp64 else None,
             "ranks": {"mean": float(np.mean(ranks[2:])), "max": int(np.max(ranks))},
             "roofline": roof,
             "cpu_baseline": cpu,

@@ -188,6 +188,12 @@ kf_status kf_solve_batched(kf_factor* const* f, int32_t nprob, const void* const
 /* Heap-numbered nodes: root 1, children 2a and 2a+1, level l holds nodes
  * 2^l .. 2^(l+1)-1.  Ranks of nodes 0..2^(D+1)-1 (entry 0 and the root are 0). */
 kf_status kf_factor_ranks(const kf_factor* f, int32_t* ranks, void* stream);
+/* Stability diagnostic (Sec. III "Stability": the instability is detectable):
+ * for every node, the smallest pivot over the largest of its factorization --
+ * squared Cholesky pivots over the largest diagonal entry at a leaf, |u_jj|
+ * of the LU of Z at an internal node.  ratios: host, 2^(D+1) entries (entry 0
+ * unused). */
+kf_status kf_factor_pivot_ratios(const kf_factor* f, double* ratios, void* stream);
 /* Skeleton of a non-root node: s tree positions in pivot order. */
 kf_status kf_factor_skeleton(const kf_factor* f, int32_t node, int64_t* skel, void* stream);
 /* Interpolation matrix of a non-root node's ID, s x c row-major FP64, with

@@ -262,6 +262,13 @@ class Factor:
         self.ctx.check(self.ctx.lib.kf_factor_Phat(self.h, node, out.ctypes.data_as(ctypes.c_void_p), _stream_ptr()))
         return out[: s * nrows].reshape(nrows, s)
 
+    def pivot_ratios(self):
+        """Smallest/largest pivot of every node's leaf Cholesky or Z LU."""
+        import numpy as np
+        r = np.zeros(self.tree.nnodes + 1)
+        self.ctx.check(self.ctx.lib.kf_factor_pivot_ratios(self.h, r.ctypes.data_as(ctypes.c_void_p), _stream_ptr()))
+        return r
+
     def device_status(self):
         return self.ctx.lib.kf_factor_status(self.h, _stream_ptr())
 

@@ -59,6 +59,7 @@ SIGNATURES = {
     "kf_factor_skeleton": (_I32, [_P, _I32, _P, _P]),
     "kf_factor_P": (_I32, [_P, _I32, _P, _P]),
     "kf_factor_Phat": (_I32, [_P, _I32, _P, _P]),
+    "kf_factor_pivot_ratios": (_I32, [_P, _P, _P]),
     "kf_factorize_with_ids": (_I32, [_P, _D, _D, _I32, _P, _P, _P, _P, _P, ctypes.POINTER(_P)]),
     "kf_tree_perm_noalloc": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
     "kf_factorize_batched": (_I32, [_P, _I32, _P, _P, _P, _I32, _P, _P, _P]),

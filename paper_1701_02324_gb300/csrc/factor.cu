@@ -56,7 +56,7 @@ __global__ void k_leaf_assemble(const double* __restrict__ X64, const float* __r
 template <typename T>
 __global__ void __launch_bounds__(256) k_leaf_cholesky(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                        int leaf0, int ldL, T* __restrict__ Lall,
-                                                       int32_t* __restrict__ status) {
+                                                       int32_t* __restrict__ status, double* __restrict__ pivr) {
   constexpr int NB = 32, TS = 64;
   __shared__ T dg[NB][NB + 1];
   __shared__ T pa[TS][NB + 1];
@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(256) k_leaf_cholesky(const int32_t* __restrict
   __syncthreads();
   const double amax = amax_sh;
   bool bad = false;
+  double minpiv = INFINITY;
   for (int kb = 0; kb < n; kb += NB) {
     const int nb = min(NB, n - kb);
     // 1. diagonal block in shared memory, unblocked Cholesky by warp 0
@@ -86,6 +87,7 @@ __global__ void __launch_bounds__(256) k_leaf_cholesky(const int32_t* __restrict
       const int lane = tid;
       for (int k = 0; k < nb; ++k) {
         T dkk = dg[k][k];
+        minpiv = fmin(minpiv, (double)dkk);
         if (!((double)dkk > 1e-14 * amax)) { bad = true; dkk = (T)(1e-14 * amax + 1e-300); }
         T lkk = sqrt(dkk);
         __syncwarp();
@@ -162,6 +164,7 @@ __global__ void __launch_bounds__(256) k_leaf_cholesky(const int32_t* __restrict
     __syncthreads();
   }
   if (bad) atomicOr(status, KF_DEV_ILLCOND);
+  if (tid == 0) pivr[node] = (n == 0 || amax == 0.0) ? 1.0 : fmax(minpiv, 0.0) / amax;
 }
 
 // P^ = L^-T L^-1 P for one leaf per CTA; rhs = Pleaf rows of the leaf (FP64,
@@ -444,7 +447,7 @@ __global__ void __launch_bounds__(256) k_zoff(const int32_t* __restrict__ lo, co
 __global__ void __launch_bounds__(256) k_z_factor(const int32_t* __restrict__ rank, int node0, int ldz, int s_max,
                                                   double* __restrict__ Z, int32_t* __restrict__ piv,
                                                   const double* __restrict__ Pc, double* __restrict__ T,
-                                                  int solve_pc, int32_t* __restrict__ status) {
+                                                  int solve_pc, int32_t* __restrict__ status, double* __restrict__ pivr) {
   constexpr int NB = 32, TS = 64;
   __shared__ double sa[TS][NB + 1];
   __shared__ double sb[NB][TS + 1];
@@ -471,6 +474,7 @@ __global__ void __launch_bounds__(256) k_z_factor(const int32_t* __restrict__ ra
   __syncthreads();
   const double amax = amax_sh;
   bool bad = false;
+  double umin = INFINITY, umax = 0.0;
   for (int kb = 0; kb < z; kb += NB) {
     const int nb = min(NB, z - kb);
     for (int j = kb; j < kb + nb; ++j) {
@@ -505,6 +509,8 @@ __global__ void __launch_bounds__(256) k_z_factor(const int32_t* __restrict__ ra
         }
       __syncthreads();
       const double ujj = A[(int64_t)j * ldz + j];
+      umin = fmin(umin, fabs(ujj));
+      umax = fmax(umax, fabs(ujj));
       if (!(fabs(ujj) > 1e-14 * amax)) bad = true;
       const double inv = ujj != 0.0 ? 1.0 / ujj : 0.0;
       for (int i = j + 1 + tid; i < z; i += blockDim.x) {
@@ -574,6 +580,7 @@ __global__ void __launch_bounds__(256) k_z_factor(const int32_t* __restrict__ ra
       }
   }
   if (bad && tid == 0) atomicOr(status, KF_DEV_ILLCOND);
+  if (tid == 0) pivr[node] = (z == 0 || umax == 0.0) ? 1.0 : umin / umax;
   if (!solve_pc) return;
   // ---- T = Z^-1 P_c --------------------------------------------------------------
   const int s = rank[node];
@@ -803,7 +810,7 @@ kf_status leaves_t(kf_factor* f, cudaStream_t s) {
   KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_assemble<T><<<g, 128, 0, s>>>(t->X64, t->X32, t->d, f->c_exp, f->lambda, t->d_lo, t->d_hi, leaf0, ldL, L));
   if (f->K64)
     KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_k64<<<g, 128, 0, s>>>(t->X64, t->X32, t->d, f->c_exp, t->d_lo, t->d_hi, leaf0, ldL, f->K64));
-  KF_PHASE(KF_PH_LEAF_CHOL, s, k_leaf_cholesky<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, ldL, L, f->status));
+  KF_PHASE(KF_PH_LEAF_CHOL, s, k_leaf_cholesky<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, ldL, L, f->status, f->pivr));
   if (D > 0)
     KF_PHASE(KF_PH_LEAF_PHAT, s, k_leaf_phat<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, leaf0, ldL, L, f->Pleaf, s_max,
                                                                   Phat + (int64_t)(D - 1) * N * s_max));
@@ -847,7 +854,7 @@ kf_status level_t(kf_factor* f, int l, double* Tm, cudaStream_t s) {
                                                           lvl(Phat, l + 1), ldz, f->ZLU, ksplit));
   }
   KF_PHASE(KF_PH_ZLU, s, k_z_factor<<<nn, 256, 0, s>>>(f->rank, node0, ldz, s_max, f->ZLU, f->Zpiv, f->Pc, Tm,
-                                                       l >= 1 ? 1 : 0, f->status));
+                                                       l >= 1 ? 1 : 0, f->status, f->pivr));
   if (l >= 1) {
     const int64_t cmax_rows = (N >> (l + 1)) + 1;
     dim3 gt((unsigned)((cmax_rows + 63) / 64), (s_max + 63) / 64, 2 * nn);

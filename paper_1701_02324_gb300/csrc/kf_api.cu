@@ -270,6 +270,7 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
   f->rank = falloc<int32_t>(f, nn, s);
   f->skel = falloc<int32_t>(f, nn * s_max, s);
   f->status = falloc<int32_t>(f, 1, s);
+  f->pivr = falloc<double>(f, nn, s);
   f->Pleaf = falloc<double>(f, (size_t)N * s_max, s);
   if (D > 0) {
     f->Pc = falloc<double>(f, (size_t)(1 << D) * 2 * s_max * s_max, s);
@@ -287,7 +288,7 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
       return kf_set_err(c, KF_ENOMEM, "factorize: device allocation of the FP64 operator failed");
     }
   }
-  bool ok = f->rank && f->skel && f->status && f->Pleaf && f->L &&
+  bool ok = f->rank && f->skel && f->status && f->pivr && f->Pleaf && f->L &&
             (D == 0 || (f->Pc && f->ZLU && f->Zpiv && f->Phat && f->VT));
   if (!ok) {
     kf_factor_free(f);
@@ -857,6 +858,14 @@ kf_status kf_factor_ranks(const kf_factor* f, int32_t* ranks, void* stream) {
   if (!f || !ranks) return KF_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   KF_CUDA(f->ctx, cudaMemcpyAsync(ranks, f->rank, sizeof(int32_t) * (f->t->nnodes + 1), cudaMemcpyDeviceToHost, s));
+  KF_CUDA(f->ctx, cudaStreamSynchronize(s));
+  return KF_OK;
+}
+
+kf_status kf_factor_pivot_ratios(const kf_factor* f, double* ratios, void* stream) {
+  if (!f || !ratios) return KF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  KF_CUDA(f->ctx, cudaMemcpyAsync(ratios, f->pivr, sizeof(double) * (f->t->nnodes + 1), cudaMemcpyDeviceToHost, s));
   KF_CUDA(f->ctx, cudaStreamSynchronize(s));
   return KF_OK;
 }

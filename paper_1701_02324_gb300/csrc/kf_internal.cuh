@@ -74,6 +74,7 @@ struct kf_factor {
   double* ZLU = nullptr;
   int32_t* Zpiv = nullptr;
   int32_t* status = nullptr;
+  double* pivr = nullptr;  // per node: smallest / largest pivot of its leaf Cholesky or Z LU
   std::vector<std::pair<void*, size_t>> allocs;
   size_t tsize() const { return prec == KF_PREC_FP64 ? 8 : 4; }
 };

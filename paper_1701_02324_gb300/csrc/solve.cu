@@ -53,78 +53,65 @@ __device__ __forceinline__ double eval_src(int src, const double* X64, const flo
 }
 
 // ---- leaf triangular solves: Y <- L^-T L^-1 Y, Y rows = the leaf's points ----
+// Blocks of 32 rows: warp 0 solves the diagonal block with shuffles (lane i
+// holds row kb + i), then every thread updates one row of the rest of the
+// leaf with the solved block (two barriers per block).
 template <typename TM, typename TV>
 __global__ void __launch_bounds__(256) k_leaf_solve(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                     int leaf0, int ldL, const TM* __restrict__ Lall,
                                                     TV* __restrict__ W, int k) {
   constexpr int NB = 32;
-  __shared__ TM lb[NB][NB + 1];
+  __shared__ TV xb[NB];
   const int lf = blockIdx.x, node = leaf0 + lf;
   const int b = lo[node], n = hi[node] - b;
   const TM* L = Lall + (int64_t)lf * ldL * ldL;
   TV* Y = W + (int64_t)b * k;
-  for (int kb = 0; kb < n; kb += NB) {
-    const int nb = min(NB, n - kb);
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-      int i = e / NB, j = e % NB;
-      lb[i][j] = (i < nb && j <= i) ? L[(int64_t)(kb + i) * ldL + kb + j] : (TM)0;
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < k; q += blockDim.x) {
-      TV x[NB];
-#pragma unroll
-      for (int i = 0; i < NB; ++i) x[i] = i < nb ? Y[(int64_t)(kb + i) * k + q] : (TV)0;
-#pragma unroll
-      for (int i = 0; i < NB; ++i)
-        if (i < nb) {
-          TV acc = x[i];
-          for (int t = 0; t < i; ++t) acc -= (TV)lb[i][t] * x[t];
-          x[i] = acc / (TV)lb[i][i];
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int r = 0; r < k; ++r) {
+    // forward: L y = b
+    for (int kb = 0; kb < n; kb += NB) {
+      const int nb = min(NB, n - kb);
+      if (tid < 32) {
+        TV yi = lane < nb ? Y[(int64_t)(kb + lane) * k + r] : (TV)0;
+        const TM* Li = L + (int64_t)(kb + lane) * ldL + kb;
+        for (int j = 0; j < nb; ++j) {
+          if (lane == j) yi = yi / (TV)Li[j];
+          const TV yj = __shfl_sync(0xffffffffu, yi, j);
+          if (lane > j && lane < nb) yi -= (TV)Li[j] * yj;
         }
-#pragma unroll
-      for (int i = 0; i < NB; ++i)
-        if (i < nb) Y[(int64_t)(kb + i) * k + q] = x[i];
+        if (lane < nb) { xb[lane] = yi; Y[(int64_t)(kb + lane) * k + r] = yi; }
+      }
+      __syncthreads();
+      for (int i = kb + nb + tid; i < n; i += blockDim.x) {
+        const TM* Li = L + (int64_t)i * ldL + kb;
+        TV acc = (TV)0;
+#pragma unroll 8
+        for (int j = 0; j < nb; ++j) acc += (TV)Li[j] * xb[j];
+        Y[(int64_t)i * k + r] -= acc;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    for (int64_t e = threadIdx.x; e < (int64_t)(n - kb - nb) * k; e += blockDim.x) {
-      int i = kb + nb + (int)(e / k), q = (int)(e % k);
-      const TM* Li = L + (int64_t)i * ldL + kb;
-      TV acc = (TV)0;
-      for (int t = 0; t < nb; ++t) acc += (TV)Li[t] * Y[(int64_t)(kb + t) * k + q];
-      Y[(int64_t)i * k + q] -= acc;
-    }
-    __syncthreads();
-  }
-  for (int kb = ((n - 1) / NB) * NB; kb >= 0 && n > 0; kb -= NB) {
-    const int nb = min(NB, n - kb);
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-      int i = e / NB, j = e % NB;
-      lb[i][j] = (i < nb && j <= i) ? L[(int64_t)(kb + i) * ldL + kb + j] : (TM)0;
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < k; q += blockDim.x) {
-      TV x[NB];
-#pragma unroll
-      for (int i = 0; i < NB; ++i) x[i] = i < nb ? Y[(int64_t)(kb + i) * k + q] : (TV)0;
-#pragma unroll
-      for (int i = NB - 1; i >= 0; --i)
-        if (i < nb) {
-          TV acc = x[i];
-          for (int t = i + 1; t < nb; ++t) acc -= (TV)lb[t][i] * x[t];
-          x[i] = acc / (TV)lb[i][i];
+    // backward: L^T x = y
+    for (int kb = ((n - 1) / NB) * NB; kb >= 0 && n > 0; kb -= NB) {
+      const int nb = min(NB, n - kb);
+      if (tid < 32) {
+        TV xi = lane < nb ? Y[(int64_t)(kb + lane) * k + r] : (TV)0;
+        for (int j = nb - 1; j >= 0; --j) {
+          if (lane == j) xi = xi / (TV)L[(int64_t)(kb + j) * ldL + kb + j];
+          TV xj = __shfl_sync(0xffffffffu, xi, j);
+          if (lane < j) xi -= (TV)L[(int64_t)(kb + j) * ldL + kb + lane] * xj;
         }
-#pragma unroll
-      for (int i = 0; i < NB; ++i)
-        if (i < nb) Y[(int64_t)(kb + i) * k + q] = x[i];
+        if (lane < nb) { xb[lane] = xi; Y[(int64_t)(kb + lane) * k + r] = xi; }
+      }
+      __syncthreads();
+      for (int i = tid; i < kb; i += blockDim.x) {
+        TV acc = (TV)0;
+#pragma unroll 8
+        for (int j = 0; j < nb; ++j) acc += (TV)L[(int64_t)(kb + j) * ldL + i] * xb[j];
+        Y[(int64_t)i * k + r] -= acc;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    for (int64_t e = threadIdx.x; e < (int64_t)kb * k; e += blockDim.x) {
-      int i = (int)(e / k), q = (int)(e % k);
-      TV acc = (TV)0;
-      for (int t = 0; t < nb; ++t) acc += (TV)L[(int64_t)(kb + t) * ldL + i] * Y[(int64_t)(kb + t) * k + q];
-      Y[(int64_t)i * k + q] -= acc;
-    }
-    __syncthreads();
   }
 }
 
@@ -189,47 +176,88 @@ void launch_colsum(dim3 g, cudaStream_t s, const int32_t* lo, const int32_t* hi,
 }
 
 // ---- row updates: w[i][r] += sign * sum_q M[i][q] v[src(b)][q][r] ------------------
-template <typename TM, typename TV>
+// A CTA takes a chunk of rows of one node; the node's vector v (cnt x k) is
+// staged in shared memory in the vector precision; one warp per row, lanes
+// over q, products in the vector precision (FP32 on the mixed path).
+constexpr int kRowUpdRows = 256;
+
+template <typename TM, typename TV, int KB>
 __global__ void __launch_bounds__(256) k_rowupd(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                 const int32_t* __restrict__ rank, const int32_t* __restrict__ skel,
                                                 int node0, int nnodes_level, int s_max, int sibling_mode, int src,
                                                 const TM* __restrict__ M, const double* __restrict__ X64,
                                                 const float* __restrict__ X32, int d, double c_exp, double inv_h3,
                                                 const double* __restrict__ V, double sign, TV* __restrict__ W, int k) {
-  // one warp per row
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  __shared__ TV vs[KF_MAX_SMAX * KB];
   const int nl = blockIdx.y, node = node0 + nl, sib = node ^ 1;
   const int b = lo[node], n = hi[node] - b;
   const int cnt = sibling_mode ? rank[sib] : rank[node];
   const int from = sibling_mode ? sib : node;
-  if (cnt == 0) return;
+  const int r0 = blockIdx.x * kRowUpdRows;
+  if (cnt == 0 || r0 >= n) return;
+  const int r1 = min(n, r0 + kRowUpdRows);
   const int32_t* sk = skel + (int64_t)sib * s_max;
   const double* v = V + (int64_t)from * s_max * k;
-  for (int i = warp; i < n; i += (gridDim.x * blockDim.x) >> 5) {
-    for (int r = 0; r < k; ++r) {
-      double acc = 0.0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int kb = 0; kb < k; kb += KB) {
+    const int kk = min(KB, k - kb);
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt * KB; e += blockDim.x) {
+      const int q = e / KB, r = e % KB;
+      vs[e] = r < kk ? (TV)v[(int64_t)q * k + kb + r] : (TV)0;
+    }
+    __syncthreads();
+    for (int i = r0 + warp; i < r1; i += 8) {
+      TV acc[KB];
+#pragma unroll
+      for (int r = 0; r < KB; ++r) acc[r] = (TV)0;
       for (int q = lane; q < cnt; q += 32) {
-        double m = (src == SRC_STORED) ? (double)M[(int64_t)(b + i) * s_max + q]
-                                       : eval_src<TM>(src, X64, X32, b + i, sk[q], d, c_exp, inv_h3);
-        acc += m * v[(int64_t)q * k + r];
+        const TV m = (src == SRC_STORED) ? (TV)M[(int64_t)(b + i) * s_max + q]
+                                         : (TV)eval_src<TM>(src, X64, X32, b + i, sk[q], d, c_exp, inv_h3);
+#pragma unroll
+        for (int r = 0; r < KB; ++r) acc[r] += m * vs[q * KB + r];
       }
-      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-      if (lane == 0) W[(int64_t)(b + i) * k + r] += (TV)(sign * acc);
+#pragma unroll
+      for (int r = 0; r < KB; ++r)
+        for (int off = 16; off > 0; off >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], off);
+      if (lane < kk) {
+        TV a = acc[0];
+#pragma unroll
+        for (int r = 1; r < KB; ++r)
+          if (lane == r) a = acc[r];
+        W[(int64_t)(b + i) * k + kb + lane] += (TV)sign * a;
+      }
     }
   }
 }
 
+template <typename TM, typename TV>
+void launch_rowupd(int64_t rows, int nnodes, cudaStream_t s, const int32_t* lo, const int32_t* hi, const int32_t* rank,
+                   const int32_t* skel, int node0, int s_max, int sib, int src, const TM* M, const double* X64,
+                   const float* X32, int d, double c_exp, double inv_h3, const double* V, double sign, TV* W, int k) {
+  dim3 g((unsigned)((rows + kRowUpdRows - 1) / kRowUpdRows), nnodes);
+  if (k == 1)
+    KF_PHASE(KF_PH_S_ROWUPD, s, k_rowupd<TM, TV, 1><<<g, 256, 0, s>>>(lo, hi, rank, skel, node0, nnodes, s_max, sib, src, M,
+                                                                     X64, X32, d, c_exp, inv_h3, V, sign, W, k));
+  else
+    KF_PHASE(KF_PH_S_ROWUPD, s, k_rowupd<TM, TV, 8><<<g, 256, 0, s>>>(lo, hi, rank, skel, node0, nnodes, s_max, sib, src, M,
+                                                                     X64, X32, d, c_exp, inv_h3, V, sign, W, k));
+}
+
 // ---- reduced systems: out[l], out[r] <- Z^-1 [in[l]; in[r]] (or Z^-T) ---------------
+// Blocked by 32 rows: warp 0 solves the diagonal block with shuffles, then
+// all threads update the rest with the block (two barriers per block).
 __global__ void __launch_bounds__(256) k_zsolve(const int32_t* __restrict__ rank, int node0, int ldz, int s_max,
                                                 const double* __restrict__ ZLU, const int32_t* __restrict__ piv,
                                                 const double* __restrict__ in, double* __restrict__ out, int k,
                                                 int transpose) {
   extern __shared__ double t[];  // ldz
+  __shared__ double xb[32];
   const int nl = blockIdx.x, node = node0 + nl;
   const int l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], z = sl + sr;
   const double* A = ZLU + (int64_t)node * ldz * ldz;
   const int32_t* pv = piv + (int64_t)node * ldz;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   for (int c = 0; c < k; ++c) {
     for (int i = tid; i < z; i += blockDim.x)
       t[i] = i < sl ? in[((int64_t)l * s_max + i) * k + c] : in[((int64_t)r * s_max + (i - sl)) * k + c];
@@ -239,31 +267,85 @@ __global__ void __launch_bounds__(256) k_zsolve(const int32_t* __restrict__ rank
         for (int i = 0; i < z; ++i)
           if (pv[i] != i) { double a = t[i]; t[i] = t[pv[i]]; t[pv[i]] = a; }
       __syncthreads();
-      // L (unit lower), column-oriented
-      for (int j = 0; j < z; ++j) {
-        double tj = t[j];
-        for (int i = j + 1 + tid; i < z; i += blockDim.x) t[i] -= A[(int64_t)i * ldz + j] * tj;
+      // L (unit lower)
+      for (int kb = 0; kb < z; kb += 32) {
+        const int nb = min(32, z - kb);
+        if (tid < 32) {
+          double yi = lane < nb ? t[kb + lane] : 0.0;
+          for (int j = 0; j < nb; ++j) {
+            double yj = __shfl_sync(0xffffffffu, yi, j);
+            if (lane > j && lane < nb) yi = fma(-A[(int64_t)(kb + lane) * ldz + kb + j], yj, yi);
+          }
+          if (lane < nb) { xb[lane] = yi; t[kb + lane] = yi; }
+        }
+        __syncthreads();
+        for (int i = kb + nb + tid; i < z; i += blockDim.x) {
+          const double* Ai = A + (int64_t)i * ldz + kb;
+          double acc = t[i];
+          for (int j = 0; j < nb; ++j) acc = fma(-Ai[j], xb[j], acc);
+          t[i] = acc;
+        }
         __syncthreads();
       }
-      for (int j = z - 1; j >= 0; --j) {
-        if (tid == 0) t[j] /= A[(int64_t)j * ldz + j];
+      // U
+      for (int kb = ((z - 1) / 32) * 32; kb >= 0 && z > 0; kb -= 32) {
+        const int nb = min(32, z - kb);
+        if (tid < 32) {
+          double xi = lane < nb ? t[kb + lane] : 0.0;
+          for (int j = nb - 1; j >= 0; --j) {
+            if (lane == j) xi = xi / A[(int64_t)(kb + j) * ldz + kb + j];
+            double xj = __shfl_sync(0xffffffffu, xi, j);
+            if (lane < j) xi = fma(-A[(int64_t)(kb + lane) * ldz + kb + j], xj, xi);
+          }
+          if (lane < nb) { xb[lane] = xi; t[kb + lane] = xi; }
+        }
         __syncthreads();
-        double tj = t[j];
-        for (int i = tid; i < j; i += blockDim.x) t[i] -= A[(int64_t)i * ldz + j] * tj;
+        for (int i = tid; i < kb; i += blockDim.x) {
+          const double* Ai = A + (int64_t)i * ldz + kb;
+          double acc = t[i];
+          for (int j = 0; j < nb; ++j) acc = fma(-Ai[j], xb[j], acc);
+          t[i] = acc;
+        }
         __syncthreads();
       }
     } else {
-      // U^T y = b (forward), then L^T x = y (backward), then undo the pivots
-      for (int j = 0; j < z; ++j) {
-        if (tid == 0) t[j] /= A[(int64_t)j * ldz + j];
+      // U^T y = b (forward)
+      for (int kb = 0; kb < z; kb += 32) {
+        const int nb = min(32, z - kb);
+        if (tid < 32) {
+          double yi = lane < nb ? t[kb + lane] : 0.0;
+          for (int j = 0; j < nb; ++j) {
+            if (lane == j) yi = yi / A[(int64_t)(kb + j) * ldz + kb + j];
+            double yj = __shfl_sync(0xffffffffu, yi, j);
+            if (lane > j && lane < nb) yi = fma(-A[(int64_t)(kb + j) * ldz + kb + lane], yj, yi);
+          }
+          if (lane < nb) { xb[lane] = yi; t[kb + lane] = yi; }
+        }
         __syncthreads();
-        double tj = t[j];
-        for (int i = j + 1 + tid; i < z; i += blockDim.x) t[i] -= A[(int64_t)j * ldz + i] * tj;
+        for (int i = kb + nb + tid; i < z; i += blockDim.x) {
+          double acc = t[i];
+          for (int j = 0; j < nb; ++j) acc = fma(-A[(int64_t)(kb + j) * ldz + i], xb[j], acc);
+          t[i] = acc;
+        }
         __syncthreads();
       }
-      for (int j = z - 1; j >= 0; --j) {
-        double tj = t[j];
-        for (int i = tid; i < j; i += blockDim.x) t[i] -= A[(int64_t)j * ldz + i] * tj;
+      // L^T x = y (backward, unit diagonal)
+      for (int kb = ((z - 1) / 32) * 32; kb >= 0 && z > 0; kb -= 32) {
+        const int nb = min(32, z - kb);
+        if (tid < 32) {
+          double xi = lane < nb ? t[kb + lane] : 0.0;
+          for (int j = nb - 1; j >= 0; --j) {
+            double xj = __shfl_sync(0xffffffffu, xi, j);
+            if (lane < j) xi = fma(-A[(int64_t)(kb + j) * ldz + kb + lane], xj, xi);
+          }
+          if (lane < nb) { xb[lane] = xi; t[kb + lane] = xi; }
+        }
+        __syncthreads();
+        for (int i = tid; i < kb; i += blockDim.x) {
+          double acc = t[i];
+          for (int j = 0; j < nb; ++j) acc = fma(-A[(int64_t)(kb + j) * ldz + i], xb[j], acc);
+          t[i] = acc;
+        }
         __syncthreads();
       }
       if (tid == 0)
@@ -371,10 +453,8 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
                             t->X32, t->d, f->c_exp, inv_h3, W, (int)k, U);
       KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<1 << l, 256, sizeof(double) * ldz, s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv, U, Vb,
                                                          (int)k, 0));
-      dim3 gr((unsigned)std::min<int64_t>((rows * 32 + 255) / 256, 1024), nc);
-      KF_PHASE(KF_PH_S_ROWUPD, s, k_rowupd<TM, TV><<<gr, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, c0, nc, s_max, 0, SRC_STORED,
-                                          lvl(Phat, l + 1), t->X64, t->X32, t->d, f->c_exp, inv_h3, Vb, -1.0, W,
-                                          (int)k));
+      launch_rowupd<TM, TV>(rows, nc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 0, SRC_STORED,
+                            lvl(Phat, l + 1), t->X64, t->X32, t->d, f->c_exp, inv_h3, Vb, -1.0, W, (int)k);
     }
   } else {
     for (int l = 0; l < D; ++l) {
@@ -386,10 +466,8 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
                             t->X64, t->X32, t->d, f->c_exp, inv_h3, W, (int)k, U);
       KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<1 << l, 256, sizeof(double) * ldz, s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv, U, Vb,
                                                          (int)k, 1));
-      dim3 gr((unsigned)std::min<int64_t>((rows * 32 + 255) / 256, 1024), nc);
-      KF_PHASE(KF_PH_S_ROWUPD, s, k_rowupd<TM, TV><<<gr, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, c0, nc, s_max, 1, vsrc,
-                                          lvl(VT, l + 1), t->X64, t->X32, t->d, f->c_exp, inv_h3, Vb, -1.0, W,
-                                          (int)k));
+      launch_rowupd<TM, TV>(rows, nc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 1, vsrc, lvl(VT, l + 1),
+                            t->X64, t->X32, t->d, f->c_exp, inv_h3, Vb, -1.0, W, (int)k);
     }
     KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve<TM, TV><<<1 << D, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
   }
@@ -432,10 +510,8 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
   for (int l = 1; l < D; ++l)
     KF_PHASE(KF_PH_MV_PUSH, s, k_push_down<<<1 << l, 256, 0, s>>>(f->rank, 1 << l, s_max, f->Pc, G, (int)k));
   const int64_t rows = (N >> D) + 1;
-  dim3 gr((unsigned)std::min<int64_t>((rows * 32 + 255) / 256, 1024), 1 << D);
-  KF_PHASE(KF_PH_S_ROWUPD, s, k_rowupd<double, double><<<gr, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, leaf0, 1 << D, s_max, 0,
-                                              SRC_STORED, f->Pleaf, t->X64, t->X32, t->d, f->c_exp, inv_h3, G, 1.0,
-                                              y, (int)k));
+  launch_rowupd<double, double>(rows, 1 << D, s, t->d_lo, t->d_hi, f->rank, f->skel, leaf0, s_max, 0, SRC_STORED,
+                                f->Pleaf, t->X64, t->X32, t->d, f->c_exp, inv_h3, G, 1.0, y, (int)k);
   KF_LAUNCH_CHECK(c);
   return KF_OK;
 }
