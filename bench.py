@@ -355,6 +355,37 @@ def gpu_main(args, rank, world):
                "h2d_bytes_per_step": int(X_host.nbytes + b_host.nbytes), "d2h_bytes_per_step": int(xh.nbytes),
                "note": "wall time of tree + factorize + solve with host X, b and x (copies inside)"}
 
+    # ---- differentiation workload (N=2^18, d=54): factorize, solve, gradient ----------
+    diff = None
+    if not args.no_grad:
+        pd = inputs.differentiation()
+        Xd = torch.from_numpy(pd.X).to(dev)
+        bd = torch.from_numpy(pd.B[:, 0]).to(dev)
+        yd = torch.from_numpy(pd.extra["y"]).to(dev)
+        treed = kf.Tree(Xd, pd.m)
+        for it in range(2):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e3 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            Fd = kf.Factor(treed, pd.h, pd.lam, pd.tau, pd.s_max, precision=kf.KF_PREC_MIXED, fp64_operator=True,
+                           refine_tol=1e-10, refine_max_iter=400, gmres_restart=20, sync_errors=False)
+            e1.record()
+            xd = Fd.solve(bd)
+            e2.record()
+            db, dl, dh = Fd.grad(xd, 2 * (xd - yd))
+            e3.record()
+            torch.cuda.synchronize()
+            ranks_d = Fd.ranks()
+            del Fd
+        diff = {"workload": "differentiation_N262144_d54", "factorize_s": round(e0.elapsed_time(e1) / 1e3, 4),
+                "solve_s": round(e1.elapsed_time(e2) / 1e3, 4), "grad_s": round(e2.elapsed_time(e3) / 1e3, 4),
+                "dL_dlambda": dl, "dL_dh": dh, "rank_mean": float(np.mean(ranks_d[2:])),
+                "note": "mixed path; grad = transpose solve (Algorithm 3 transposed) + dK~/dh operator, "
+                        "loss ||x - y||^2"}
+        del treed, Xd
+
     # ---- roofline of the dominant kernel ----------------------------------------
     peaks = load_peaks()
     D, lo, hi = tree_ranges(p.N, p.m)
@@ -407,6 +438,7 @@ def gpu_main(args, rank, world):
             "mixed_rel_err_vs_reference": mixed_rel if fp64 else None,
             "fp64_path": fp64,
             "mixed_unrefined": unref,
+            "differentiation": diff,
             "accuracy_reference": reference if fp64 else None,
             "ranks": {"mean": float(np.mean(ranks[2:])), "max": int(np.max(ranks))},
             "roofline": roof,
@@ -451,6 +483,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--once", action="store_true",
                     help="one tree + factorize + solve of the scale recipe and exit (for profilers)")
     ap.add_argument("--n", type=int, default=1 << 20, help="number of points of the scale recipe")

@@ -376,6 +376,8 @@ def _autograd():
         def forward(ctx, b, lam, h, factor):
             x = factor.solve(b)
             ctx.factor = factor
+            ctx.lam_dtype = lam.dtype if torch.is_tensor(lam) else torch.float64
+            ctx.h_dtype = h.dtype if torch.is_tensor(h) else torch.float64
             ctx.save_for_backward(x)
             return x
 
@@ -384,7 +386,8 @@ def _autograd():
             (x,) = ctx.saved_tensors
             db, dl, dh = ctx.factor.grad(x.to(torch.float64), gx.to(torch.float64))
             dev = gx.device
-            return db.to(gx.dtype), torch.tensor(dl, device=dev), torch.tensor(dh, device=dev), None
+            return (db.to(gx.dtype), torch.tensor(dl, device=dev, dtype=ctx.lam_dtype),
+                    torch.tensor(dh, device=dev, dtype=ctx.h_dtype), None)
 
     return KernelSolve
 

@@ -304,7 +304,8 @@ __global__ void __launch_bounds__(256) k_leaf_phat(const int32_t* __restrict__ l
 // level.  The sibling's skeleton coordinates are staged transposed in shared
 // memory (yT[k][q]); one warp per row, lanes over q, coalesced stores.
 template <typename T>
-__global__ void __launch_bounds__(256) k_eval_vt(const double* __restrict__ X64, const float* __restrict__ X32, int d,
+__global__ void __launch_bounds__(256) k_eval_vt(const double* __restrict__ X64, const float* __restrict__ X32,
+                                                 const float* __restrict__ X32lo, int d,
                                                  double c_exp, const int32_t* __restrict__ lo,
                                                  const int32_t* __restrict__ hi, const int32_t* __restrict__ rank,
                                                  const int32_t* __restrict__ skel, int s_max, int node0, int rows_per_cta,
@@ -345,7 +346,10 @@ __global__ void __launch_bounds__(256) k_eval_vt(const double* __restrict__ X64,
         if (VT64 != nullptr) {  // FP64 operator copy: recompute the entries that matter in FP64
           const int64_t row = b + i;
           double k64 = (double)kv;
-          if ((float)kv >= 5.9604645e-8f) k64 = kf_kern64(X64 + row * d, X64 + (int64_t)sk[q0 + q] * d, d, c_exp);
+          if ((float)kv >= 5.9604645e-8f) {
+            const int64_t col = sk[q0 + q];
+            k64 = exp(kf_sqdist_df(X32 + row * d, X32lo + row * d, X32 + col * d, X32lo + col * d, d) * c_exp);
+          }
           VT64[row * s_max + q0 + q] = k64;
           kv = (T)k64;
         }
@@ -784,7 +788,7 @@ __global__ void __launch_bounds__(256) k_telescope(const int32_t* __restrict__ l
 
 // FP64 copy of the leaf kernel blocks (no lambda), both triangles, for the
 // FP64-accurate operator.
-__global__ void k_leaf_k64(const double* __restrict__ X64, const float* __restrict__ X32, int d, double c_exp,
+__global__ void k_leaf_k64(const float* __restrict__ X32lo, const float* __restrict__ X32, int d, double c_exp,
                            const int32_t* __restrict__ lo, const int32_t* __restrict__ hi, int leaf0, int ldL,
                            double* __restrict__ K64) {
   const int lf = blockIdx.z, node = leaf0 + lf;
@@ -793,7 +797,7 @@ __global__ void k_leaf_k64(const double* __restrict__ X64, const float* __restri
   if (i >= n) return;
   double* Ki = K64 + ((int64_t)lf * ldL + i) * ldL;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-    Ki[j] = kf_kern_hybrid(X64, X32, b + i, b + j, d, c_exp);
+    Ki[j] = kf_kern_hybrid(X32, X32lo, b + i, b + j, d, c_exp);
 }
 
 template <typename T>
@@ -809,7 +813,7 @@ kf_status leaves_t(kf_factor* f, cudaStream_t s) {
   dim3 g((ldL + 127) / 128, ldL, nleaf);
   KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_assemble<T><<<g, 128, 0, s>>>(t->X64, t->X32, t->d, f->c_exp, f->lambda, t->d_lo, t->d_hi, leaf0, ldL, L));
   if (f->K64)
-    KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_k64<<<g, 128, 0, s>>>(t->X64, t->X32, t->d, f->c_exp, t->d_lo, t->d_hi, leaf0, ldL, f->K64));
+    KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_k64<<<g, 128, 0, s>>>(t->X32lo, t->X32, t->d, f->c_exp, t->d_lo, t->d_hi, leaf0, ldL, f->K64));
   KF_PHASE(KF_PH_LEAF_CHOL, s, k_leaf_cholesky<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, ldL, L, f->status, f->pivr));
   if (D > 0)
     KF_PHASE(KF_PH_LEAF_PHAT, s, k_leaf_phat<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, leaf0, ldL, L, f->Pleaf, s_max,
@@ -836,7 +840,7 @@ kf_status level_t(kf_factor* f, int l, double* Tm, cudaStream_t s) {
   const int qchunk = (int)std::max<int64_t>(1, std::min<int64_t>(s_max, (96 * 1024 / (int64_t)sizeof(T) - 8 * t->d) / t->d));
   const size_t vt_smem = sizeof(T) * ((size_t)t->d * qchunk + 8 * t->d);
   KF_CUDA(c, cudaFuncSetAttribute(k_eval_vt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vt_smem));
-  KF_PHASE(KF_PH_EVAL_V, s, k_eval_vt<T><<<gv, 256, vt_smem, s>>>(t->X64, t->X32, t->d, f->c_exp, t->d_lo, t->d_hi,
+  KF_PHASE(KF_PH_EVAL_V, s, k_eval_vt<T><<<gv, 256, vt_smem, s>>>(t->X64, t->X32, t->X32lo, t->d, f->c_exp, t->d_lo, t->d_hi,
                                                                  f->rank, f->skel, s_max, child0, vt_rows, qchunk,
                                                                  lvl(VT, l + 1),
                                                                  f->VT64 ? f->VT64 + (int64_t)l * N * s_max : nullptr));
@@ -916,17 +920,23 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
   const size_t tb = sizeof(double) * kf_factor_tm_elems(f);
   double* Tm = st == KF_OK ? (double*)c->dalloc(tb, s) : nullptr;
   if (st == KF_OK && !Tm) st = kf_set_err(c, KF_ENOMEM, "factorize: allocation failed");
-  cudaStream_t s2 = nullptr;
-  std::vector<cudaEvent_t> ev(D + 2, nullptr);
+  cudaStream_t s1 = nullptr, s2 = nullptr;
+  std::vector<cudaEvent_t> ev(D + 3, nullptr);
   if (st == KF_OK) {
-    KF_CUDA(c, cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    // the skeleton chain is the critical path: it runs on a high-priority stream
+    int lo_prio = 0, hi_prio = 0;
+    cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    KF_CUDA(c, cudaStreamCreateWithPriority(&s1, cudaStreamNonBlocking, hi_prio));
+    KF_CUDA(c, cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, lo_prio));
     for (auto& e : ev) KF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    // ev[l]: skeletons of level l done (on s); ev[0]: allocations ready; ev[D+1]: factorization done (on s2)
+    // ev[l]: skeletons of level l done (on s1); ev[0]: allocations ready (on s);
+    // ev[D+1]: factorization done (on s2); ev[D+2]: skeletons done (on s1)
     cudaEventRecord(ev[0], s);
+    cudaStreamWaitEvent(s1, ev[0], 0);
     cudaStreamWaitEvent(s2, ev[0], 0);
     for (int l = D; l >= 1 && st == KF_OK; --l) {
-      st = kf_skel_level(f, l, &sc, s);
-      cudaEventRecord(ev[l], s);
+      st = kf_skel_level(f, l, &sc, s1);
+      cudaEventRecord(ev[l], s1);
       if (st != KF_OK) break;
       cudaStreamWaitEvent(s2, ev[l], 0);
       if (l == D) st = kf_factorize_leaves(f, s2);
@@ -934,12 +944,15 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
     }
     if (st == KF_OK) st = kf_factorize_level(f, 0, Tm, s2);
     cudaEventRecord(ev[D + 1], s2);
+    cudaEventRecord(ev[D + 2], s1);
     cudaStreamWaitEvent(s, ev[D + 1], 0);
+    cudaStreamWaitEvent(s, ev[D + 2], 0);
   }
   if (Tm) c->dfree(Tm, tb, s);
   kf_skel_end(f, &sc, s);
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);
+  if (s1) cudaStreamDestroy(s1);
   if (s2) cudaStreamDestroy(s2);
   return st;
 }

@@ -15,6 +15,7 @@
 kf_status kf_to_f64_launch(const float* in, double* out, int64_t n, cudaStream_t s);
 kf_status kf_to_f32_launch(const double* in, float* out, int64_t n, cudaStream_t s);
 kf_status kf_check_finite_launch(const double* x, int64_t n, int32_t* bad, cudaStream_t s);
+kf_status kf_split_lo_launch(const double* in, const float* hi, float* lo, int64_t n, cudaStream_t s);
 
 static thread_local std::string g_err;
 
@@ -392,11 +393,12 @@ kf_status kf_tree_build(kf_ctx* c, const void* X, int32_t dtype, int64_t N, int3
   };
   t->X64 = (double*)talloc(sizeof(double) * N * d);
   t->X32 = (float*)talloc(sizeof(float) * N * d);
+  t->X32lo = (float*)talloc(sizeof(float) * N * d);
   t->perm = (int64_t*)talloc(sizeof(int64_t) * N);
   t->d_lo = (int32_t*)talloc(sizeof(int32_t) * (t->nnodes + 1));
   t->d_hi = (int32_t*)talloc(sizeof(int32_t) * (t->nnodes + 1));
   int32_t* bad = (int32_t*)talloc(sizeof(int32_t));
-  if (!t->X64 || !t->X32 || !t->perm || !t->d_lo || !t->d_hi || !bad) {
+  if (!t->X64 || !t->X32 || !t->X32lo || !t->perm || !t->d_lo || !t->d_hi || !bad) {
     kf_tree_free(t);
     return kf_set_err(c, KF_ENOMEM, "tree: device allocation failed");
   }
@@ -421,6 +423,7 @@ kf_status kf_tree_build(kf_ctx* c, const void* X, int32_t dtype, int64_t N, int3
   }
   if (st == KF_OK) st = kf_tree_build_device(t, s);
   if (st == KF_OK) st = kf_to_f32_launch(t->X64, t->X32, N * d, s);
+  if (st == KF_OK) st = kf_split_lo_launch(t->X64, t->X32, t->X32lo, N * d, s);
   if (st != KF_OK) {
     kf_tree_free(t);
     return st;

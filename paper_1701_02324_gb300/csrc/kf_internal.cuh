@@ -45,6 +45,7 @@ struct kf_tree {
   int32_t* d_hi = nullptr;
   double* X64 = nullptr;
   float* X32 = nullptr;
+  float* X32lo = nullptr;  // fp32(X64 - X32): the low half of a double-float copy
   int64_t* perm = nullptr;
   std::vector<std::pair<void*, size_t>> allocs;
 };
@@ -55,6 +56,7 @@ struct kf_factor {
   double h = 1, lambda = 0, tau = 0, c_exp = 0;
   int32_t s_max = 0, n_samp = 0, cmax = 0, prec = 0, vstore = 0, sync_errors = 0;
   int32_t use_tc = 1;  // mixed path: tcgen05 products (0: CUDA-core FP32)
+  int32_t use_cluster_qr = 1;  // upper tree levels: cluster QR in distributed shared memory
   int32_t fp64_op = 0;  // keep FP64 operator data (VT64, K64)
   int32_t gmres_m = 0;  // refinement: 0 = Richardson, m > 0 = GMRES(m)
   int32_t refine_user = 0;  // refinement explicitly requested (enables it on the FP64 path)
@@ -117,14 +119,42 @@ __device__ __forceinline__ float kf_kern32(const float* __restrict__ x, const fl
   return __expf(acc * c_exp);
 }
 
+// Squared distance in double-float arithmetic on the FP32 pipes: every
+// coordinate is held as hi + lo (hi = fp32(x), lo = fp32(x - hi)); the
+// difference, its square and the running sum carry an error term through
+// exact two-sum / two-product steps, giving about 44 significant bits.
+__device__ __forceinline__ void kf_two_sum(float a, float b, float& s, float& e) {
+  // round-to-nearest intrinsics: never contracted, so the error term is exact
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ double kf_sqdist_df(const float* __restrict__ xh, const float* __restrict__ xl,
+                                              const float* __restrict__ yh, const float* __restrict__ yl, int d) {
+  float ah = 0.f, al = 0.f;
+  for (int k = 0; k < d; ++k) {
+    float th, te;
+    kf_two_sum(xh[k], -yh[k], th, te);
+    const float tl = te + (xl[k] - yl[k]);
+    const float p = __fmul_rn(th, th);
+    const float q = fmaf(th, th, -p) + 2.f * th * tl;  // th^2 - p exactly, plus the cross term
+    float sh, se;
+    kf_two_sum(ah, p, sh, se);
+    se = __fadd_rn(se, __fadd_rn(al, q));
+    ah = __fadd_rn(sh, se);
+    al = __fsub_rn(se, __fsub_rn(ah, sh));
+  }
+  return (double)ah + (double)al;
+}
+
 // FP64-accurate kernel entry at FP32 cost for the small ones: entries below
 // 2^-24 are taken from the FP32 evaluation (their absolute error stays below
-// about 1e-12), larger ones are recomputed in FP64.
-__device__ __forceinline__ double kf_kern_hybrid(const double* X64, const float* X32, int64_t i, int64_t j, int d,
+// about 1e-12); larger ones take the double-float distance and an FP64 exp.
+__device__ __forceinline__ double kf_kern_hybrid(const float* X32, const float* X32lo, int64_t i, int64_t j, int d,
                                                  double c_exp) {
   const float k32 = kf_kern32(X32 + i * d, X32 + j * d, d, (float)c_exp);
   if (k32 < 5.9604645e-8f) return (double)k32;
-  return kf_kern64(X64 + i * d, X64 + j * d, d, c_exp);
+  return exp(kf_sqdist_df(X32 + i * d, X32lo + i * d, X32 + j * d, X32lo + j * d, d) * c_exp);
 }
 
 template <typename T> struct kf_kern;

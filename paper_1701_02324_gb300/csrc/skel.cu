@@ -8,10 +8,13 @@
 //     the whole complement when it is not larger than n_samp.
 //  2. A = K(S', C) in FP64 (C = the node's points at a leaf, [l~ r~] above).
 //  3. Column-pivoted Householder QR of A (one CTA per node), stopping at the
-//     first k with |R_kk| < tau |R_00| or at min(s_max, n_s, |C|); the column
-//     norms of the trailing block are accumulated from the updated entries
-//     at every step (no downdating).
+//     first k with |R_kk| < tau |R_00| or at min(s_max, n_s, |C|); the squared
+//     norms of the trailing columns are downdated by each new row of R and
+//     evaluated exactly again whenever they have fallen 16x since their last
+//     exact value, so they stay within rounding of the recomputed norms.
 //  4. P = [I, R11^-1 R12] with the columns in their original order.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "kf_internal.cuh"
@@ -104,134 +107,14 @@ __global__ void k_eval_A(const double* __restrict__ X, int d, double c_exp, cons
     Aj[i] = kf_kern64(X + (int64_t)S[i] * d, xc, d, c_exp);
 }
 
-// ---- 3/4. pivoted QR and P ------------------------------------------------------
-template <int RPL>  // rows per lane held in registers (n_samp <= 32 * RPL)
-__global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
-                                                    int32_t* __restrict__ rank, int32_t* __restrict__ skel, int s_max,
-                                                    int node0, bool leaf, int n_samp, int cmax,
-                                                    const int32_t* __restrict__ nsamp, double tau,
-                                                    double* __restrict__ A, double* __restrict__ Pout, int ldP,
-                                                    int64_t P_node_stride) {
-  extern __shared__ double sm[];
-  double* norms = sm;                          // cmax
-  double* v = norms + cmax;                    // n_samp
-  int* piv = (int*)(v + n_samp);               // cmax
-  __shared__ double red_v[32];
-  __shared__ int red_i[32];
-  __shared__ int s_final;
-  const int nl = blockIdx.x, node = node0 + nl;
+// T = R11^-1 R12 (warp per column of R12), written straight into P, plus the
+// skeleton list and the rank.  Ab: the node's factored block (columns in
+// position order), piv[q] = ID column at position q, s = rank.
+__device__ void id_finish(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                          int32_t* __restrict__ rank, int32_t* __restrict__ skel, int s_max, int node, int nl,
+                          bool leaf, int n_samp, int c, const double* __restrict__ Ab, const int* piv, int s,
+                          double* __restrict__ Pout, int ldP, int64_t P_node_stride) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int c = id_ncols(node, leaf, lo, hi, rank);
-  const int ns = nsamp[nl];
-  double* Ab = A + (int64_t)nl * cmax * n_samp;
-  int kmax = min(s_max, min(ns, c));
-  // initial squared column norms
-  for (int j = warp; j < c; j += nwarps) {
-    const double* col = Ab + (int64_t)j * n_samp;
-    double acc = 0.0;
-    for (int i = lane; i < ns; i += 32) acc = fma(col[i], col[i], acc);
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) norms[j] = acc;
-  }
-  for (int j = threadIdx.x; j < c; j += blockDim.x) piv[j] = j;
-  if (threadIdx.x == 0) s_final = kmax;
-  __syncthreads();
-  double r00 = 0.0;
-  for (int k = 0; k < kmax; ++k) {
-    // pivot: largest trailing norm, ties to the lowest column
-    double bv = -1.0;
-    int bi = c;
-    for (int j = k + threadIdx.x; j < c; j += blockDim.x)
-      if (norms[j] > bv) { bv = norms[j]; bi = j; }
-    for (int off = 16; off > 0; off >>= 1) {
-      double ov = __shfl_xor_sync(0xffffffffu, bv, off);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-    }
-    if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
-    __syncthreads();
-    if (warp == 0) {
-      bv = lane < nwarps ? red_v[lane] : -1.0;
-      bi = lane < nwarps ? red_i[lane] : c;
-      for (int off = 16; off > 0; off >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, bv, off);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-      }
-      if (lane == 0) { red_v[0] = bv; red_i[0] = bi; }
-    }
-    __syncthreads();
-    const int p = red_i[0];
-    const double rkk = sqrt(red_v[0]);
-    if (k == 0) r00 = rkk;
-    bool stop = (k == 0) ? (r00 == 0.0) : (rkk < tau * r00);
-    __syncthreads();
-    if (stop) {
-      if (threadIdx.x == 0) s_final = k;
-      break;
-    }
-    if (p != k) {  // swap columns k and p (all rows) and their bookkeeping
-      double* ck = Ab + (int64_t)k * n_samp;
-      double* cp = Ab + (int64_t)p * n_samp;
-      for (int i = threadIdx.x; i < ns; i += blockDim.x) {
-        double t = ck[i]; ck[i] = cp[i]; cp[i] = t;
-      }
-      if (threadIdx.x == 0) {
-        double t = norms[k]; norms[k] = norms[p]; norms[p] = t;
-        int ti = piv[k]; piv[k] = piv[p]; piv[p] = ti;
-      }
-    }
-    __syncthreads();
-    // Householder vector of column k, rows k..ns-1
-    const double* ck = Ab + (int64_t)k * n_samp;
-    const double x0 = ck[k];
-    const double alpha = (x0 >= 0.0) ? -rkk : rkk;
-    double part = 0.0;
-    for (int i = k + threadIdx.x; i < ns; i += blockDim.x) {
-      double vi = (i == k) ? x0 - alpha : ck[i];
-      v[i] = vi;
-      part = fma(vi, vi, part);
-    }
-    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-    __syncthreads();
-    if (lane == 0) red_v[warp] = part;
-    __syncthreads();
-    double vtv = 0.0;
-    for (int w = 0; w < nwarps; ++w) vtv += red_v[w];
-    const double beta = vtv > 0.0 ? 2.0 / vtv : 0.0;
-    // apply H to the trailing columns; accumulate their new norms (rows > k)
-    for (int j = k + 1 + warp; j < c; j += nwarps) {
-      double* cj = Ab + (int64_t)j * n_samp;
-      double a[RPL];
-      double dot = 0.0;
-#pragma unroll
-      for (int r = 0; r < RPL; ++r) {
-        int i = k + lane + 32 * r;
-        a[r] = (i < ns) ? cj[i] : 0.0;
-        if (i < ns) dot = fma(v[i], a[r], dot);
-      }
-      for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
-      const double w = beta * dot;
-      double nrm = 0.0;
-#pragma unroll
-      for (int r = 0; r < RPL; ++r) {
-        int i = k + lane + 32 * r;
-        if (i < ns) {
-          a[r] = fma(-w, v[i], a[r]);
-          cj[i] = a[r];
-          if (i > k) nrm = fma(a[r], a[r], nrm);
-        }
-      }
-      for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
-      if (lane == 0) norms[j] = nrm;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) Ab[(int64_t)k * n_samp + k] = alpha;
-    for (int i = k + 1 + threadIdx.x; i < ns; i += blockDim.x) Ab[(int64_t)k * n_samp + i] = 0.0;
-    __syncthreads();
-  }
-  __syncthreads();
-  const int s = s_final;
   // T = R11^-1 R12 (warp per column of R12), written straight into P
   // P[j * ldP + q]: ID column j, skeleton q.  Leaves write their rows of the
   // N x s_max matrix (base lo[node]); internal nodes have fixed-size blocks.
@@ -281,6 +164,342 @@ __global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ 
     sk[q] = q < s ? id_col(node, leaf, lo, rank, skel, s_max, piv[q]) : -1;
 }
 
+// ---- 3/4. pivoted QR and P ------------------------------------------------------
+template <int RPL>  // rows per lane held in registers (n_samp <= 32 * RPL)
+__global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                    int32_t* __restrict__ rank, int32_t* __restrict__ skel, int s_max,
+                                                    int node0, bool leaf, int n_samp, int cmax,
+                                                    const int32_t* __restrict__ nsamp, double tau,
+                                                    double* __restrict__ A, double* __restrict__ Pout, int ldP,
+                                                    int64_t P_node_stride) {
+  extern __shared__ double sm[];
+  double* norms = sm;                          // cmax
+  double* v = norms + cmax;                    // n_samp
+  double* nref = v + n_samp;                   // cmax: norm at its last exact evaluation
+  int* piv = (int*)(nref + cmax);              // cmax
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int s_final;
+  const int nl = blockIdx.x, node = node0 + nl;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int c = id_ncols(node, leaf, lo, hi, rank);
+  const int ns = nsamp[nl];
+  double* Ab = A + (int64_t)nl * cmax * n_samp;
+  int kmax = min(s_max, min(ns, c));
+  // initial squared column norms
+  for (int j = warp; j < c; j += nwarps) {
+    const double* col = Ab + (int64_t)j * n_samp;
+    double acc = 0.0;
+    for (int i = lane; i < ns; i += 32) acc = fma(col[i], col[i], acc);
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) { norms[j] = acc; nref[j] = acc; }
+  }
+  for (int j = threadIdx.x; j < c; j += blockDim.x) piv[j] = j;
+  if (threadIdx.x == 0) s_final = kmax;
+  __syncthreads();
+  double r00 = 0.0;
+  for (int k = 0; k < kmax; ++k) {
+    // pivot: largest trailing norm, ties to the lowest column
+    double bv = -1.0;
+    int bi = c;
+    for (int j = k + threadIdx.x; j < c; j += blockDim.x)
+      if (norms[j] > bv) { bv = norms[j]; bi = j; }
+    for (int off = 16; off > 0; off >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      bv = lane < nwarps ? red_v[lane] : -1.0;
+      bi = lane < nwarps ? red_i[lane] : c;
+      for (int off = 16; off > 0; off >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+      }
+      if (lane == 0) { red_v[0] = bv; red_i[0] = bi; }
+    }
+    __syncthreads();
+    const int p = red_i[0];
+    const double rkk = sqrt(red_v[0]);
+    if (k == 0) r00 = rkk;
+    bool stop = (k == 0) ? (r00 == 0.0) : (rkk < tau * r00);
+    __syncthreads();
+    if (stop) {
+      if (threadIdx.x == 0) s_final = k;
+      break;
+    }
+    if (p != k) {  // swap columns k and p (all rows) and their bookkeeping
+      double* ck = Ab + (int64_t)k * n_samp;
+      double* cp = Ab + (int64_t)p * n_samp;
+      for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+        double t = ck[i]; ck[i] = cp[i]; cp[i] = t;
+      }
+      if (threadIdx.x == 0) {
+        double t = norms[k]; norms[k] = norms[p]; norms[p] = t;
+        t = nref[k]; nref[k] = nref[p]; nref[p] = t;
+        int ti = piv[k]; piv[k] = piv[p]; piv[p] = ti;
+      }
+    }
+    __syncthreads();
+    // Householder vector of column k, rows k..ns-1
+    const double* ck = Ab + (int64_t)k * n_samp;
+    const double x0 = ck[k];
+    const double alpha = (x0 >= 0.0) ? -rkk : rkk;
+    double part = 0.0;
+    for (int i = k + threadIdx.x; i < ns; i += blockDim.x) {
+      double vi = (i == k) ? x0 - alpha : ck[i];
+      v[i] = vi;
+      part = fma(vi, vi, part);
+    }
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    __syncthreads();
+    if (lane == 0) red_v[warp] = part;
+    __syncthreads();
+    double vtv = 0.0;
+    for (int w = 0; w < nwarps; ++w) vtv += red_v[w];
+    const double beta = vtv > 0.0 ? 2.0 / vtv : 0.0;
+    // apply H to the trailing columns; their squared norms over rows > k are
+    // downdated by the new row-k entry, and evaluated exactly again once they
+    // have fallen by 16x since the last exact value (rounding stays near
+    // machine precision relative to the current norm)
+    for (int j = k + 1 + warp; j < c; j += nwarps) {
+      double* cj = Ab + (int64_t)j * n_samp;
+      double a[RPL];
+      double dot = 0.0;
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        int i = k + lane + 32 * r;
+        a[r] = (i < ns) ? cj[i] : 0.0;
+        if (i < ns) dot = fma(v[i], a[r], dot);
+      }
+      for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
+      const double w = beta * dot;
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        int i = k + lane + 32 * r;
+        if (i < ns) {
+          a[r] = fma(-w, v[i], a[r]);
+          cj[i] = a[r];
+        }
+      }
+      const double akj = __shfl_sync(0xffffffffu, a[0], 0);  // row k sits in lane 0, slot 0
+      double nrm = fma(-akj, akj, norms[j]);
+      const double ref = nref[j];
+      if (!(nrm > ref * 0.0625)) {
+        nrm = 0.0;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+          int i = k + lane + 32 * r;
+          if (i > k && i < ns) nrm = fma(a[r], a[r], nrm);
+        }
+        for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
+        if (lane == 0) nref[j] = nrm;
+      }
+      __syncwarp();
+      if (lane == 0) norms[j] = nrm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) Ab[(int64_t)k * n_samp + k] = alpha;
+    for (int i = k + 1 + threadIdx.x; i < ns; i += blockDim.x) Ab[(int64_t)k * n_samp + i] = 0.0;
+    __syncthreads();
+  }
+  __syncthreads();
+  id_finish(lo, hi, rank, skel, s_max, node, nl, leaf, n_samp, c, Ab, piv, s_final, Pout, ldP, P_node_stride);
+}
+
+// ---- 3b. pivoted QR of an internal node on a 16-CTA cluster -------------------
+// The node's sample block lives in the distributed shared memory of its
+// cluster: CTA r holds the ID columns j with j % 16 == r for the whole
+// factorization.  Per Householder step: each CTA proposes its best trailing
+// column (largest norm, ties to the lowest current position), the proposals
+// are read across the cluster, the owner of the pivot publishes v, every CTA
+// copies v and updates its own columns (norms downdated as in the single-CTA
+// kernel).  Columns are not moved; their current positions are tracked so
+// that the pivot order and tie rule equal those of the column-swapping QR.
+// At the end the columns are written to global memory in position order and
+// k_id_finish computes T = R11^-1 R12 and P.
+constexpr int kQC = 16;  // CTAs per cluster
+
+struct QrCand {
+  double v;
+  int pos;
+  int phys;
+};
+
+__global__ void __cluster_dims__(kQC, 1, 1) __launch_bounds__(256)
+    k_qr_cluster(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi, const int32_t* __restrict__ rank,
+                 int s_max, int node0, int n_samp, int cmax, const int32_t* __restrict__ nsamp, double tau,
+                 double* __restrict__ A, int32_t* __restrict__ pivpos, int32_t* __restrict__ sout) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) double qsm[];
+  const int W = (cmax + kQC - 1) / kQC;
+  double* Aloc = qsm;                        // W x n_samp, column-major
+  double* norms = Aloc + (size_t)W * n_samp; // W
+  double* nref = norms + W;                  // W
+  double* vloc = nref + W;                   // n_samp
+  double* vbuf = vloc + n_samp;              // n_samp: published Householder vector
+  int* posof = (int*)(vbuf + n_samp);        // cmax: position of each column
+  int* physat = posof + cmax;                // cmax: column at each position
+  int* done = physat + cmax;                 // W
+  __shared__ QrCand wcand[8];
+  __shared__ QrCand cand;                    // this CTA's proposal
+  __shared__ double pub[2];                  // beta of the published vector
+  __shared__ QrCand best;
+  __shared__ int s_final;
+  const int cr = (int)cluster.block_rank();
+  const int nl = blockIdx.x / kQC, node = node0 + nl;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c = rank[2 * node] + rank[2 * node + 1];
+  const int ns = nsamp[nl];
+  const int kmax = min(s_max, min(ns, c));
+  double* Ab = A + (int64_t)nl * cmax * n_samp;
+  // load my columns, exact norms
+  for (int lj = warp; lj < W; lj += 8) {
+    const int j = lj * kQC + cr;
+    double acc = 0.0;
+    if (j < c) {
+      for (int i = lane; i < ns; i += 32) {
+        const double a = Ab[(int64_t)j * n_samp + i];
+        Aloc[(size_t)lj * n_samp + i] = a;
+        acc = fma(a, a, acc);
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) { norms[lj] = acc; nref[lj] = acc; done[lj] = (j < c) ? 0 : 1; }
+  }
+  for (int j = tid; j < c; j += blockDim.x) { posof[j] = j; physat[j] = j; }
+  if (tid == 0) s_final = kmax;
+  __syncthreads();
+  double r00 = 0.0;
+  for (int k = 0; k < kmax; ++k) {
+    // 1. my proposal
+    QrCand mine{-1.0, c, -1};
+    for (int lj = tid; lj < W; lj += blockDim.x) {
+      if (done[lj]) continue;
+      const int j = lj * kQC + cr;
+      const double v = norms[lj];
+      const int p = posof[j];
+      if (v > mine.v || (v == mine.v && p < mine.pos)) mine = {v, p, j};
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      QrCand o;
+      o.v = __shfl_xor_sync(0xffffffffu, mine.v, off);
+      o.pos = __shfl_xor_sync(0xffffffffu, mine.pos, off);
+      o.phys = __shfl_xor_sync(0xffffffffu, mine.phys, off);
+      if (o.v > mine.v || (o.v == mine.v && o.pos < mine.pos)) mine = o;
+    }
+    if (lane == 0) wcand[warp] = mine;
+    __syncthreads();
+    if (tid == 0) {
+      QrCand b = wcand[0];
+      for (int w = 1; w < 8; ++w)
+        if (wcand[w].v > b.v || (wcand[w].v == b.v && wcand[w].pos < b.pos)) b = wcand[w];
+      cand = b;
+    }
+    cluster.sync();  // (A) proposals visible
+    if (tid == 0) {
+      QrCand b{-1.0, c, -1};
+      for (int r = 0; r < kQC; ++r) {
+        const QrCand* rc = cluster.map_shared_rank(&cand, r);
+        const QrCand o = *rc;
+        if (o.v > b.v || (o.v == b.v && o.pos < b.pos)) b = o;
+      }
+      best = b;
+    }
+    __syncthreads();
+    const double rkk = sqrt(best.v);
+    if (k == 0) r00 = rkk;
+    const bool stop = (k == 0) ? (r00 == 0.0) : (rkk < tau * r00);
+    if (stop) {
+      if (tid == 0) s_final = k;
+      break;  // uniform over the cluster: every CTA saw the same proposals
+    }
+    const int p = best.phys, P = best.pos;
+    const int owner = p % kQC, lp = p / kQC;
+    // 2. bookkeeping of positions (replicated): swap positions k and P
+    if (tid == 0) {
+      const int jk = physat[k];
+      physat[k] = p;
+      physat[P] = jk;
+      posof[p] = k;
+      posof[jk] = P;
+    }
+    // 3. the owner publishes v = x - alpha e_k over rows k.. and beta
+    if (cr == owner) {
+      double* x = Aloc + (size_t)lp * n_samp;
+      const double x0 = x[k];
+      const double alpha = (x0 >= 0.0) ? -rkk : rkk;
+      const double vtv = 2.0 * rkk * (rkk + fabs(x0));
+      for (int i = k + tid; i < ns; i += blockDim.x) vbuf[i] = (i == k) ? x0 - alpha : x[i];
+      if (tid == 0) pub[0] = vtv > 0.0 ? 2.0 / vtv : 0.0;
+      __syncthreads();
+      if (tid == 0) { x[k] = alpha; done[lp] = 1; }
+      for (int i = k + 1 + tid; i < ns; i += blockDim.x) x[i] = 0.0;
+    }
+    cluster.sync();  // (B) v and beta visible
+    {
+      const double* rv = cluster.map_shared_rank(vbuf, owner);
+      for (int i = k + tid; i < ns; i += blockDim.x) vloc[i] = rv[i];
+      if (tid == 0) pub[1] = *cluster.map_shared_rank(&pub[0], owner);
+    }
+    __syncthreads();
+    const double beta = pub[1];
+    // 4. update my trailing columns
+    for (int lj = warp; lj < W; lj += 8) {
+      if (done[lj]) continue;
+      double* cj = Aloc + (size_t)lj * n_samp;
+      double dot = 0.0;
+      for (int i = k + lane; i < ns; i += 32) dot = fma(vloc[i], cj[i], dot);
+      for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
+      const double w = beta * dot;
+      for (int i = k + lane; i < ns; i += 32) cj[i] = fma(-w, vloc[i], cj[i]);
+      __syncwarp();
+      const double akj = cj[k];
+      double nrm = fma(-akj, akj, norms[lj]);
+      if (!(nrm > nref[lj] * 0.0625)) {
+        nrm = 0.0;
+        for (int i = k + 1 + lane; i < ns; i += 32) nrm = fma(cj[i], cj[i], nrm);
+        for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
+        if (lane == 0) nref[lj] = nrm;
+      }
+      __syncwarp();
+      if (lane == 0) norms[lj] = nrm;
+    }
+    __syncthreads();
+  }
+  cluster.sync();
+  // write my columns back in position order
+  for (int lj = warp; lj < W; lj += 8) {
+    const int j = lj * kQC + cr;
+    if (j >= c) continue;
+    const int p = posof[j];
+    for (int i = lane; i < ns; i += 32) Ab[(int64_t)p * n_samp + i] = Aloc[(size_t)lj * n_samp + i];
+  }
+  if (cr == 0) {
+    for (int q = tid; q < c; q += blockDim.x) pivpos[(int64_t)nl * cmax + q] = physat[q];
+    if (tid == 0) sout[nl] = s_final;
+  }
+}
+
+// Finishing step after the cluster QR: one CTA per node.
+__global__ void __launch_bounds__(512) k_id_finish(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                   int32_t* __restrict__ rank, int32_t* __restrict__ skel, int s_max,
+                                                   int node0, int n_samp, int cmax, const double* __restrict__ A,
+                                                   const int32_t* __restrict__ pivpos, const int32_t* __restrict__ sout,
+                                                   double* __restrict__ Pout, int ldP, int64_t P_node_stride) {
+  extern __shared__ int pv[];  // cmax
+  const int nl = blockIdx.x, node = node0 + nl;
+  const int c = rank[2 * node] + rank[2 * node + 1];
+  for (int q = threadIdx.x; q < c; q += blockDim.x) pv[q] = pivpos[(int64_t)nl * cmax + q];
+  __syncthreads();
+  id_finish(lo, hi, rank, skel, s_max, node, nl, false, n_samp, c, A + (int64_t)nl * cmax * n_samp, pv, sout[nl],
+            Pout, ldP, P_node_stride);
+}
+
 }  // namespace
 
 // Skeletonize every non-root node, leaves first, in three parts so that the
@@ -294,6 +513,7 @@ kf_status kf_skel_begin(kf_factor* f, kf_skel_scratch* sc, cudaStream_t s) {
   if (t->D == 0) return KF_OK;
   const int maxnodes = 1 << t->D;
   sc->a_elems = std::max((size_t)maxnodes * t->leaf_max, (size_t)(maxnodes / 2) * 2 * f->s_max) * f->n_samp;
+  sc->a_elems += (size_t)maxnodes * 2 * f->s_max + maxnodes;  // tail: cluster-QR positions and ranks
   sc->A = (double*)c->dalloc(sizeof(double) * sc->a_elems, s);
   sc->samp = (int32_t*)c->dalloc(sizeof(int32_t) * (size_t)maxnodes * f->n_samp, s);
   sc->nsamp = (int32_t*)c->dalloc(sizeof(int32_t) * maxnodes, s);
@@ -332,7 +552,30 @@ kf_status kf_skel_level(kf_factor* f, int l, kf_skel_scratch* sc, cudaStream_t s
                               n_samp, cmax, samp, nsamp, A));
   double* Pout = leaf ? f->Pleaf : f->Pc + (int64_t)node0 * cint * s_max;
   int64_t pstride = leaf ? 0 : (int64_t)cint * s_max;
-  size_t smem = sizeof(double) * (cmax + n_samp) + sizeof(int) * cmax;
+  // upper levels (few nodes): one 16-CTA cluster per node, the block in distributed shared memory
+  if (!leaf && nn <= 64 && f->use_cluster_qr) {
+    const int W = (cmax + kQC - 1) / kQC;
+    const size_t qsmem = sizeof(double) * ((size_t)W * n_samp + 2 * W + 2 * n_samp) + sizeof(int) * (2 * cmax + W);
+    if (qsmem <= 200 * 1024) {
+      cudaError_t e1 = cudaFuncSetAttribute(k_qr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      cudaError_t e2 = cudaFuncSetAttribute(k_qr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsmem);
+      if (e1 == cudaSuccess && e2 == cudaSuccess) {
+        // positions and ranks from the tail of the A scratch
+        int32_t* pp = (int32_t*)(A + (size_t)nn * cmax * n_samp);
+        int32_t* so = pp + (size_t)nn * cmax;
+        KF_PHASE(KF_PH_QR, s, k_qr_cluster<<<nn * kQC, 256, qsmem, s>>>(t->d_lo, t->d_hi, f->rank, s_max, node0,
+                                                                       n_samp, cmax, nsamp, f->tau, A, pp, so));
+        KF_PHASE(KF_PH_QR, s, k_id_finish<<<nn, 512, sizeof(int) * cmax, s>>>(t->d_lo, t->d_hi, f->rank, f->skel,
+                                                                            s_max, node0, n_samp, cmax, A, pp, so,
+                                                                            Pout, s_max, pstride));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return kf_set_err(c, KF_ECUDA, "cluster QR level %d: %s", l, cudaGetErrorString(e));
+        return KF_OK;
+      }
+      cudaGetLastError();
+    }
+  }
+  size_t smem = sizeof(double) * (2 * cmax + n_samp) + sizeof(int) * cmax;
   if (rpl <= 8)
     KF_PHASE(KF_PH_QR, s, k_pivoted_qr<8><<<nn, 512, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf, n_samp, cmax,
                                           nsamp, f->tau, A, Pout, s_max, pstride));

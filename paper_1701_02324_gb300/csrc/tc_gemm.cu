@@ -3,7 +3,7 @@
 // K_{r~ l} P^_l (Eq. e:blocksmw), and the telescoping P^_a = [P^_l T_top;
 // P^_r T_bot] (Eq. e:invtelescope).
 //
-// One CTA (4 warps) computes a 128 x BN tile of D = A B:
+// One CTA (16 warps) computes a 128 x BN tile of D = A B:
 //   * operands are staged by all threads from global memory into shared
 //     memory in the canonical K-major, no-swizzle core-matrix layout (8 rows x
 //     16 bytes per core matrix; LBO = 128 B between core matrices along K,
@@ -11,8 +11,9 @@
 //   * one thread issues tcgen05.mma kind::tf32 for A_hi B_hi + A_hi B_lo +
 //     A_lo B_hi (3xTF32: about FP32 accuracy) into an FP32 accumulator in
 //     tensor memory, and tcgen05.commit arrives on an mbarrier;
-//   * the epilogue reads the accumulator with tcgen05.ld (warp w owns rows
-//     32w..32w+31) and hands each value to the problem's store.
+//   * the epilogue reads the accumulator with tcgen05.ld (warp w reads lane
+//     quadrant w mod 4, rows 32(w mod 4)..+31, and a quarter of the columns)
+//     and hands each value to the problem's store.
 // Every wait is bounded; on time-out the kernel flags KF_DEV_TIMEOUT, waits
 // once more, frees its tensor memory and returns.
 #include <algorithm>
@@ -132,79 +133,128 @@ struct Tile {
 // Generic tile driver.  Problem provides: tile(bx, by, bz) -> Tile;
 // loadA(tile, m, k) and loadB(tile, k, n) (valid indices only; FP32);
 // a_m_fastest / b_n_fastest (staging order for coalescing); store(tile, m, n, v).
+// Two shared-memory stages: the threads stage chunk c + 1 (global loads and
+// the tf32 split) while the tensor core works on chunk c; an mbarrier per
+// stage, armed by tcgen05.commit, says when a stage may be overwritten.
+constexpr int kThreads = 512;  // 16 warps: all stage operands, 4 per TMEM lane quadrant in the epilogue
+
+// Element e of a (rows x 32) operand tile.  32 consecutive e fill one
+// 8-row x 4-k slice of a core matrix, i.e. 32 consecutive shared-memory words
+// (no bank conflicts); inside the slice the row index runs fastest when the
+// operand is contiguous along rows in global memory, else the k index.
+template <bool kRowsFastest>
+__device__ __forceinline__ void tile_coord(int e, int rows, int& r, int& k) {
+  const int g = e >> 5;
+  const int rl = kRowsFastest ? (e & 7) : ((e >> 2) & 7);
+  const int kl = kRowsFastest ? ((e >> 3) & 3) : (e & 3);
+  const int rg = rows >> 3;
+  r = (g % rg) * 8 + rl;
+  k = (g / rg) * 4 + kl;
+}
+
+template <class Problem, int BN>
+__device__ __forceinline__ void stage_chunk(const Problem& prob, const Tile& t, int kc, float* Ahi, float* Alo,
+                                            float* Bhi, float* Blo) {
+  const int tid = threadIdx.x;
+  const int kn = min(kBK, t.k1 - kc);
+#pragma unroll 4
+  for (int e = tid; e < kBM * kBK; e += kThreads) {
+    int m, k;
+    tile_coord<Problem::a_m_fastest>(e, kBM, m, k);
+    const float a = (m < t.M - t.m0 && k < kn) ? prob.loadA(t, t.m0 + m, kc + k) : 0.f;
+    const float hi = to_tf32(a);
+    const int o = core_off(m, k);
+    Ahi[o] = hi;
+    Alo[o] = to_tf32(a - hi);
+  }
+#pragma unroll 4
+  for (int e = tid; e < BN * kBK; e += kThreads) {
+    int n, k;
+    tile_coord<Problem::b_n_fastest>(e, BN, n, k);
+    const float b = (n < t.N - t.n0 && k < kn) ? prob.loadB(t, kc + k, t.n0 + n) : 0.f;
+    const float hi = to_tf32(b);
+    const int o = core_off(n, k);
+    Bhi[o] = hi;
+    Blo[o] = to_tf32(b - hi);
+  }
+}
+
+__device__ __forceinline__ void issue_chunk(uint32_t tmem, uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl,
+                                            uint32_t idesc, bool first) {
+#pragma unroll
+  for (int kk = 0; kk < kBK / 8; ++kk) {
+    const uint32_t off = kk * 256;  // two core matrices along K per MMA (K = 8 tf32)
+    const uint64_t dah = smem_desc(ah + off, 128, 1024), dal = smem_desc(al + off, 128, 1024);
+    const uint64_t dbh = smem_desc(bh + off, 128, 1024), dbl = smem_desc(bl + off, 128, 1024);
+    mma_tf32(tmem, dah, dbh, idesc, (first && kk == 0) ? 0u : 1u);
+    mma_tf32(tmem, dah, dbl, idesc, 1u);
+    mma_tf32(tmem, dal, dbh, idesc, 1u);
+  }
+}
+
 template <int BN, class Problem>
-__global__ void __launch_bounds__(128) k_tc_gemm(Problem prob, int32_t* __restrict__ status) {
+__global__ void __launch_bounds__(kThreads) k_tc_gemm(Problem prob, int32_t* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  float* Ahi = (float*)smem_raw;
-  float* Alo = Ahi + kBM * kBK;
-  float* Bhi = Alo + kBM * kBK;
-  float* Blo = Bhi + BN * kBK;
-  __shared__ __align__(8) uint64_t mbar;
+  constexpr int kStage = 2 * kBM * kBK + 2 * BN * kBK;  // floats per stage
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
   const Tile t = prob.tile(blockIdx.x, blockIdx.y, blockIdx.z);
   if (t.skip) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) tmem_alloc(&tmem_base, BN);
-  if (tid == 0) mbar_init(&mbar, 1);
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+  }
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = tmem_base;
   constexpr uint32_t idesc = idesc_tf32(kBM, BN);
-  uint32_t phase = 0;
+  uint32_t uses[2] = {0u, 0u};  // commits issued per stage
   bool ok = true;
-  for (int kc = t.k0; kc < t.k1 && ok; kc += kBK) {
-    const int kn = min(kBK, t.k1 - kc);
-    // stage A (128 x 32) and B (BN x 32), split into tf32 hi / lo
-    for (int e = tid; e < kBM * kBK; e += 128) {
-      int m, k;
-      if (Problem::a_m_fastest) { m = e % kBM; k = e / kBM; } else { k = e % kBK; m = e / kBK; }
-      float a = (m < t.M - t.m0 && k < kn) ? prob.loadA(t, t.m0 + m, kc + k) : 0.f;
-      float hi = to_tf32(a);
-      Ahi[core_off(m, k)] = hi;
-      Alo[core_off(m, k)] = to_tf32(a - hi);
+  int c = 0;
+  for (int kc = t.k0; kc < t.k1 && ok; kc += kBK, ++c) {
+    const int st = c & 1;
+    float* Ahi = (float*)smem_raw + st * kStage;
+    float* Alo = Ahi + kBM * kBK;
+    float* Bhi = Alo + kBM * kBK;
+    float* Blo = Bhi + BN * kBK;
+    if (uses[st] > 0) {  // the MMAs that read this stage two chunks ago must be done
+      if (!mbar_wait(&mbar[st], (uses[st] - 1) & 1u)) {
+        ok = false;
+        if (tid == 0) atomicOr(status, KF_DEV_TIMEOUT);
+        break;
+      }
     }
-    for (int e = tid; e < BN * kBK; e += 128) {
-      int n, k;
-      if (Problem::b_n_fastest) { n = e % BN; k = e / BN; } else { k = e % kBK; n = e / kBK; }
-      float b = (n < t.N - t.n0 && k < kn) ? prob.loadB(t, kc + k, t.n0 + n) : 0.f;
-      float hi = to_tf32(b);
-      Bhi[core_off(n, k)] = hi;
-      Blo[core_off(n, k)] = to_tf32(b - hi);
-    }
+    stage_chunk<Problem, BN>(prob, t, kc, Ahi, Alo, Bhi, Blo);
     fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
       fence_after_sync();
-      const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
-#pragma unroll
-      for (int kk = 0; kk < kBK / 8; ++kk) {
-        const uint32_t off = kk * 256;  // two core matrices along K per MMA (K = 8 tf32)
-        const uint64_t dah = smem_desc(ah + off, 128, 1024), dal = smem_desc(al + off, 128, 1024);
-        const uint64_t dbh = smem_desc(bh + off, 128, 1024), dbl = smem_desc(bl + off, 128, 1024);
-        const uint32_t first = (kc == t.k0 && kk == 0) ? 0u : 1u;
-        mma_tf32(tmem, dah, dbh, idesc, first);
-        mma_tf32(tmem, dah, dbl, idesc, 1u);
-        mma_tf32(tmem, dal, dbh, idesc, 1u);
-      }
-      mma_commit(&mbar);
+      issue_chunk(tmem, smem_u32(Ahi), smem_u32(Alo), smem_u32(Bhi), smem_u32(Blo), idesc, kc == t.k0);
+      mma_commit(&mbar[st]);
     }
-    if (!mbar_wait(&mbar, phase)) {
+    ++uses[st];
+  }
+  // drain: wait for the last commit of each stage (a second bounded wait on time-out)
+  for (int st = 0; st < 2; ++st)
+    if (uses[st] > 0 && !mbar_wait(&mbar[st], (uses[st] - 1) & 1u)) {
       ok = false;
       if (tid == 0) atomicOr(status, KF_DEV_TIMEOUT);
-      mbar_wait(&mbar, phase);  // second bounded wait for the MMAs in flight
+      mbar_wait(&mbar[st], (uses[st] - 1) & 1u);
     }
-    phase ^= 1u;
-    fence_after_sync();
-    __syncthreads();
-  }
+  fence_after_sync();
+  __syncthreads();
   if (ok) {
-    fence_after_sync();
+    // warp w reads TMEM lane quadrant w % 4; the four warps of a quadrant
+    // split the accumulator columns
+    const int quad = warp & 3, part = warp >> 2, nparts = kThreads / 128;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
+    for (int c0 = part * 32; c0 < BN; c0 += 32 * nparts) {
       float v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      const int m = t.m0 + warp * 32 + lane;
+      tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
+      const int m = t.m0 + quad * 32 + lane;
       if (m < t.M) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
@@ -297,7 +347,7 @@ struct TelescopeProblem {
 }  // namespace
 
 // ---- launchers ---------------------------------------------------------------------
-static size_t tc_smem_bytes(int BN) { return sizeof(float) * (size_t)(2 * kBM * kBK + 2 * BN * kBK); }
+static size_t tc_smem_bytes(int BN) { return 2 * sizeof(float) * (size_t)(2 * kBM * kBK + 2 * BN * kBK); }
 
 kf_status kf_tc_zoff(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
                      const float* VT, const float* Ph, int ldz, double* Z, int64_t rows_per_child, int32_t* status,
@@ -315,7 +365,7 @@ kf_status kf_tc_zoff(const int32_t* lo, const int32_t* hi, const int32_t* rank, 
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<256, ZoffProblem>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return KF_ECUDA;
   dim3 g(mt * p.ntile_n, ksplit, 2 * nn);
-  KF_PHASE(KF_PH_ZOFF, s, k_tc_gemm<256, ZoffProblem><<<g, 128, smem, s>>>(p, status));
+  KF_PHASE(KF_PH_ZOFF, s, k_tc_gemm<256, ZoffProblem><<<g, kThreads, smem, s>>>(p, status));
   return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
 }
 
@@ -330,6 +380,6 @@ kf_status kf_tc_telescope(const int32_t* lo, const int32_t* hi, const int32_t* r
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<256, TelescopeProblem>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return KF_ECUDA;
   dim3 g((unsigned)((rows_per_child + kBM - 1) / kBM), p.ntile_n, 2 * nn);
-  KF_PHASE(KF_PH_TELESCOPE, s, k_tc_gemm<256, TelescopeProblem><<<g, 128, smem, s>>>(p, status));
+  KF_PHASE(KF_PH_TELESCOPE, s, k_tc_gemm<256, TelescopeProblem><<<g, kThreads, smem, s>>>(p, status));
   return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
 }

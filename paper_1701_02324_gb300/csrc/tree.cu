@@ -232,6 +232,14 @@ kf_status kf_to_f64_launch(const float* in, double* out, int64_t n, cudaStream_t
   KF_PHASE(KF_PH_MISC, s, k_to_f64<<<grid_for(n, 256), 256, 0, s>>>(in, out, n));
   return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
 }
+__global__ void k_split_lo(const double* __restrict__ in, const float* __restrict__ hi, float* __restrict__ lo, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    lo[i] = (float)(in[i] - (double)hi[i]);
+}
+kf_status kf_split_lo_launch(const double* in, const float* hi, float* lo, int64_t n, cudaStream_t s) {
+  KF_PHASE(KF_PH_MISC, s, k_split_lo<<<grid_for(n, 256), 256, 0, s>>>(in, hi, lo, n));
+  return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
+}
 kf_status kf_to_f32_launch(const double* in, float* out, int64_t n, cudaStream_t s) {
   KF_PHASE(KF_PH_MISC, s, k_to_f32<<<grid_for(n, 256), 256, 0, s>>>(in, out, n));
   return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;

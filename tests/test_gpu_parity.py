@@ -259,3 +259,28 @@ def test_batched_matches_single_and_oracle():
         o.factorize(0.5)
         # the batched solve is the direct sweep without refinement: 3xTF32 factors on the mixed path
         assert rel(xs[1].cpu().numpy(), o.solve(Bs[1])) <= (tol if prec == FP64 else 1e-4)
+
+
+def test_autograd_kernel_solve_matches_oracle_gradient():
+    """Row a11: torch.autograd through x = (lambda I + K~(h))^-1 b gives dL/db,
+    dL/dlambda and dL/dh equal to the oracle's adjoint (skeletons fixed)."""
+    X, b = problem(2048, 3, seed=21)
+    y = np.random.default_rng(22).standard_normal(2048)
+    h, lam = 0.3, 0.8
+    tree = kf.Tree(torch.from_numpy(X).cuda(), 128)
+    F = kf.Factor(tree, h, lam, 1e-7, 48, precision=FP64)
+    o = oracle.Oracle(X, 128)
+    o.skeletonize(h, 1e-7, 48)
+    o.factorize(lam)
+    assert all(np.array_equal(F.skeleton(a), o.skel(a)) for a in range(2, o.nnodes + 1))
+    bt = torch.tensor(b, device="cuda", requires_grad=True)
+    lt = torch.tensor(lam, device="cuda", dtype=torch.float64, requires_grad=True)
+    ht = torch.tensor(h, device="cuda", dtype=torch.float64, requires_grad=True)
+    x = kf.KernelSolve.apply(bt, lt, ht, F)
+    loss = ((x - torch.from_numpy(y).cuda()) ** 2).sum()
+    loss.backward()
+    xo = o.solve(b)
+    dbo, dlo, dho = o.grad(xo, 2 * (xo - y))
+    assert rel(bt.grad.cpu().numpy(), dbo) <= 1e-10
+    assert abs(lt.grad.item() - dlo) <= 1e-9 * abs(dlo)
+    assert abs(ht.grad.item() - dho) <= 1e-8 * abs(dho)
