@@ -229,18 +229,25 @@ def gpu_main(args, rank, world):
         if dist:
             torch.distributed.barrier()
 
+    gmres_iters = []
+
     def step(prec, refined=None):
         """tree + factorize + solve.  Mixed path: FP64 operator kept and the
-        solve refined by GMRES(20) to eps_r <= 1e-10 (the accuracy target);
-        FP64 path: direct solve.  refined=False: mixed path without the FP64
-        operator and without refinement."""
+        solve refined by GMRES(--gmres-m) to eps_r <= --mixed-tol (at least the
+        accuracy of the FP64 path's direct solve); FP64 path: direct solve.
+        refined=False: mixed path without the FP64 operator and without
+        refinement."""
         tree = kf.Tree(X, p.m)
         if prec == kf.KF_PREC_MIXED and refined is not False:
-            F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=prec, fp64_operator=True, refine_tol=1e-10,
-                          refine_max_iter=400, gmres_restart=20, sync_errors=False)
-        else:
-            F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=prec, fp64_operator=False, refine_max_iter=-1,
-                          sync_errors=False)
+            F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=prec, fp64_operator=True,
+                          refine_tol=args.mixed_tol, refine_max_iter=400, gmres_restart=args.gmres_m, sync_errors=False)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record()
+            x, inf = F.solve(b, info=True)
+            gmres_iters.append(inf["iters"])
+            return tree, F, ev, x
+        F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=prec, fp64_operator=False, refine_max_iter=-1,
+                      sync_errors=False)
         ev = torch.cuda.Event(enable_timing=True)
         ev.record()
         x = F.solve(b)
@@ -346,7 +353,7 @@ def gpu_main(args, rank, world):
             t0 = time.perf_counter()
             tree = kf.Tree(torch.from_numpy(X_host), p.m)                  # host X: H2D inside
             F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=kf.KF_PREC_MIXED, fp64_operator=True,
-                          refine_tol=1e-10, refine_max_iter=400, gmres_restart=20, sync_errors=False)
+                          refine_tol=args.mixed_tol, refine_max_iter=400, gmres_restart=args.gmres_m, sync_errors=False)
             xt = F.solve(torch.from_numpy(b_host))                         # host b -> host x
             xh[:] = xt.numpy()
             lib_t.append(time.perf_counter() - t0)
@@ -370,7 +377,7 @@ def gpu_main(args, rank, world):
             e3 = torch.cuda.Event(enable_timing=True)
             e0.record()
             Fd = kf.Factor(treed, pd.h, pd.lam, pd.tau, pd.s_max, precision=kf.KF_PREC_MIXED, fp64_operator=True,
-                           refine_tol=1e-10, refine_max_iter=400, gmres_restart=20, sync_errors=False)
+                           refine_tol=args.mixed_tol, refine_max_iter=400, gmres_restart=args.gmres_m, sync_errors=False)
             e1.record()
             xd = Fd.solve(bd)
             e2.record()
@@ -433,8 +440,9 @@ def gpu_main(args, rank, world):
                                     "GMRES)", "parallelism": f"replicas x{world}",
                        "l2": "inputs and factors larger than L2 (no flush needed)"},
             "solve_rhs_per_s": round(1.0 / solve_s, 2),
-            "solve_note": "mixed solve = direct sweep of the FP32 factors + GMRES(20) against the FP64 operator "
-                          "to eps_r <= 1e-10",
+            "solve_note": f"mixed solve = direct sweep of the FP32 factors + GMRES({args.gmres_m}) against the FP64 operator "
+                          f"to eps_r <= {args.mixed_tol:g}",
+            "gmres_iters": float(np.mean(gmres_iters[-args.steps:])) if gmres_iters else None,
             "mixed_rel_err_vs_reference": mixed_rel if fp64 else None,
             "fp64_path": fp64,
             "mixed_unrefined": unref,
@@ -461,7 +469,11 @@ def once(args):
     p = inputs.scale(args.n)
     prec = kf.KF_PREC_MIXED if args.precision == "mixed" else kf.KF_PREC_FP64
     tree = kf.Tree(torch.from_numpy(p.X).cuda(), p.m)
-    F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=prec, refine_max_iter=-1, fp64_operator=False)
+    if prec == kf.KF_PREC_MIXED and not args.unrefined:  # the timed step's configuration
+        F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=prec, fp64_operator=True, refine_tol=args.mixed_tol,
+                      refine_max_iter=400, gmres_restart=args.gmres_m, sync_errors=False)
+    else:
+        F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=prec, refine_max_iter=-1, fp64_operator=False)
     x = F.solve(torch.from_numpy(p.B[:, 0]).cuda())
     torch.cuda.synchronize()
     print(f"once: N={p.N} precision={args.precision} |x|={float(torch.linalg.norm(x)):.6e}")
@@ -488,6 +500,10 @@ def main():
                     help="one tree + factorize + solve of the scale recipe and exit (for profilers)")
     ap.add_argument("--n", type=int, default=1 << 20, help="number of points of the scale recipe")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--gmres-m", type=int, default=50, help="GMRES restart length of the mixed solve")
+    ap.add_argument("--mixed-tol", type=float, default=1e-9,
+                    help="GMRES target eps_r of the mixed solve (the FP64 direct solve reaches about 1e-8)")
+    ap.add_argument("--unrefined", action="store_true", help="--once: mixed factors without the FP64 operator or GMRES")
     args = ap.parse_args()
     if args.once:
         once(args)

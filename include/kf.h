@@ -93,9 +93,11 @@ typedef struct {
   int32_t fp64_operator;  /* keep FP64 V blocks and leaf blocks so that the refinement residual and
                              kf_matvec use an FP64-accurate operator: 0 = default (on for the mixed
                              path), 1 = on, -1 = off */
-  int32_t gmres_restart;  /* refinement method: 0 = GMRES(20), m > 0 = GMRES(m) in FP64,
+  int32_t gmres_restart;  /* refinement method: 0 = GMRES(50), m > 0 = GMRES(m) (m <= 64) in FP64,
                              right-preconditioned by the factorization; -1 = x += M^-1 r */
-  int32_t reserved[5];
+  int32_t no_cluster_kernels; /* 1 = one CTA per node everywhere (no thread-block clusters for the
+                             pivoted QR and reduced-system LU of the upper tree levels) */
+  int32_t reserved[4];
 } kf_opts;
 
 /* Filled by kf_solve when non-NULL (synchronizes the stream). */

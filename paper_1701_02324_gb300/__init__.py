@@ -155,8 +155,9 @@ class Tree:
 
 
 def _opts(precision=KF_PREC_FP64, n_samp=0, seed=0, v_storage=KF_V_STORED, sync_errors=0, refine_tol=0.0,
-          refine_max_iter=0, tensor_cores=True, fp64_operator=None, gmres_restart=0):
+          refine_max_iter=0, tensor_cores=True, fp64_operator=None, gmres_restart=0, cluster_kernels=True):
     o = kf_opts()
+    o.no_cluster_kernels = 0 if cluster_kernels else 1
     o.no_tensor_cores = 0 if tensor_cores else 1
     o.fp64_operator = 0 if fp64_operator is None else (1 if fp64_operator is True else
                                                        (-1 if fp64_operator is False else int(fp64_operator)))
@@ -172,11 +173,11 @@ class Factor:
     def __init__(self, tree: Tree, h: float, lam: float, tau: float, s_max: int, precision=KF_PREC_FP64,
                  n_samp: int = 0, seed: int = 0, v_storage=KF_V_STORED, refine_tol: float = 0.0,
                  refine_max_iter: int = 0, sync_errors: bool = True, tensor_cores: bool = True,
-                 fp64_operator=None, gmres_restart: int = 0, _ids=None):
+                 fp64_operator=None, gmres_restart: int = 0, cluster_kernels: bool = True, _ids=None):
         self.tree, self.ctx = tree, tree.ctx
         self.h_, self.lam, self.tau, self.s_max, self.precision = float(h), float(lam), float(tau), int(s_max), precision
         o = _opts(precision, n_samp, seed, v_storage, int(sync_errors), refine_tol, refine_max_iter, tensor_cores,
-                  fp64_operator, gmres_restart)
+                  fp64_operator, gmres_restart, cluster_kernels)
         h_out = ctypes.c_void_p()
         if _ids is None:
             st = self.ctx.lib.kf_factorize(tree.h, self.h_, self.lam, self.tau, self.s_max, ctypes.byref(o),

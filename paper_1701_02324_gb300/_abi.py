@@ -32,7 +32,8 @@ class kf_opts(ctypes.Structure):
         ("no_tensor_cores", ctypes.c_int32),
         ("fp64_operator", ctypes.c_int32),
         ("gmres_restart", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("no_cluster_kernels", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 

@@ -10,6 +10,8 @@
 //   P^_a    = W_a Z_a^-1 P_c = [P^_l T_top ; P^_r T_bot], T = Z_a^-1 P_c.
 // The last line is Solve(a, W P_c, false) of Algorithm 2 after the identity
 // u - W Z^-1 V u = W Z^-1 P_c for u = W P_c (since V W = Z - I).
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -309,10 +311,14 @@ __global__ void __launch_bounds__(256) k_eval_vt(const double* __restrict__ X64,
                                                  double c_exp, const int32_t* __restrict__ lo,
                                                  const int32_t* __restrict__ hi, const int32_t* __restrict__ rank,
                                                  const int32_t* __restrict__ skel, int s_max, int node0, int rows_per_cta,
-                                                 int qchunk, T* __restrict__ VT, double* __restrict__ VT64) {
+                                                 int qchunk, T* __restrict__ VT, double* __restrict__ VT64, float ch,
+                                                 float cl, const float2* __restrict__ tab) {
   extern __shared__ unsigned char smraw[];
   T* yT = (T*)smraw;                       // d x qchunk
   T* xs = yT + (size_t)d * qchunk;         // 8 warps x d
+  // low halves of the double-float coordinates, for the FP64 operator copy
+  float* yTlo = (float*)(xs + 8 * d);      // d x qchunk
+  float* xslo = yTlo + (size_t)d * qchunk; // 8 warps x d
   const int nl = blockIdx.y, node = node0 + nl, sib = node ^ 1;
   const int b = lo[node], n = hi[node] - b, ss = rank[sib];
   const int r0 = blockIdx.x * rows_per_cta;
@@ -321,6 +327,7 @@ __global__ void __launch_bounds__(256) k_eval_vt(const double* __restrict__ X64,
   const int32_t* sk = skel + (int64_t)sib * s_max;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T* xw = xs + warp * d;
+  float* xwlo = xslo + warp * d;
   const T c = (T)c_exp;
   for (int q0 = 0; q0 < ss; q0 += qchunk) {
     const int qn = min(qchunk, ss - q0);
@@ -329,11 +336,14 @@ __global__ void __launch_bounds__(256) k_eval_vt(const double* __restrict__ X64,
       int k = e / qn, q = e % qn;
       int64_t src = (int64_t)sk[q0 + q] * d + k;
       yT[(size_t)k * qn + q] = sizeof(T) == 8 ? (T)X64[src] : (T)X32[src];
+      if (VT64 != nullptr) yTlo[(size_t)k * qn + q] = X32lo[src];
     }
     __syncthreads();
     for (int i = r0 + warp; i < r1; i += 8) {
-      for (int k = lane; k < d; k += 32)
+      for (int k = lane; k < d; k += 32) {
         xw[k] = sizeof(T) == 8 ? (T)X64[(int64_t)(b + i) * d + k] : (T)X32[(int64_t)(b + i) * d + k];
+        if (VT64 != nullptr) xwlo[k] = X32lo[(int64_t)(b + i) * d + k];
+      }
       __syncwarp();
       T* out = VT + (int64_t)(b + i) * s_max + q0;
       for (int q = lane; q < qn; q += 32) {
@@ -347,8 +357,9 @@ __global__ void __launch_bounds__(256) k_eval_vt(const double* __restrict__ X64,
           const int64_t row = b + i;
           double k64 = (double)kv;
           if ((float)kv >= 5.9604645e-8f) {
-            const int64_t col = sk[q0 + q];
-            k64 = exp(kf_sqdist_df(X32 + row * d, X32lo + row * d, X32 + col * d, X32lo + col * d, d) * c_exp);
+            float ah, al;
+            kf_sqdist_df2((const float*)xw, xwlo, (const float*)yT + q, yTlo + q, qn, d, ah, al);
+            k64 = kf_kern_from_df(ah, al, ch, cl, tab);
           }
           VT64[row * s_max + q0 + q] = k64;
           kv = (T)k64;
@@ -440,291 +451,372 @@ __global__ void __launch_bounds__(256) k_zoff(const int32_t* __restrict__ lo, co
 }
 
 // Blocked LU with partial pivoting of Z (FP64) followed, for non-root nodes,
-// by T = Z^-1 P_c, one CTA (256 threads) per node.
-//   panel:    32 columns at a time; per column an arg-max over the rows
-//             (ties: lowest row), a full-row swap, scaling, and the rank-1
+// by T = Z^-1 P_c.  Row pivoting is implicit: rm[i] is the row of Z that
+// holds logical row i of the factorization (P Z = L U with (P Z)[i] =
+// Z[rm[i]]), so a pivot interchange swaps two entries of rm and no data.
+//   panel:    32 columns at a time; per column an arg-max over the logical
+//             rows (ties: lowest), the interchange, scaling, and the rank-1
 //             update restricted to the panel;
 //   U12:      L11^-1 A12 by the 32 x 32 unit-lower block;
 //   trailing: A22 -= L21 U12, 64 x 64 register-tiled FP64 tiles;
-// then X = P_c with the row swaps applied, L y = x and U t = y by 32-row
-// blocks (diagonal block per column thread, off-block updates tiled).
-__global__ void __launch_bounds__(256) k_z_factor(const int32_t* __restrict__ rank, int node0, int ldz, int s_max,
-                                                  double* __restrict__ Z, int32_t* __restrict__ piv,
-                                                  const double* __restrict__ Pc, double* __restrict__ T,
-                                                  int solve_pc, int32_t* __restrict__ status, double* __restrict__ pivr) {
-  constexpr int NB = 32, TS = 64;
-  __shared__ double sa[TS][NB + 1];
-  __shared__ double sb[NB][TS + 1];
-  __shared__ double rv[8];
-  __shared__ int ri[8];
-  __shared__ int pk;
-  __shared__ double amax_sh;
-  const int nl = blockIdx.x, node = node0 + nl;
-  const int z = rank[2 * node] + rank[2 * node + 1];
-  double* A = Z + (int64_t)node * ldz * ldz;
-  int32_t* pv = piv + (int64_t)node * ldz;
+// then X[i] = P_c[rm[i]], L y = x and U t = y by 32-row blocks (diagonal
+// block per column thread, off-block updates tiled).  rm is stored per node
+// (the solve sweep reads it).
+// k_z_factor runs one CTA per node.  k_z_factor_cluster spreads a node over
+// a thread-block cluster for the upper levels (few nodes): CTA 0 factors each
+// panel, the cluster shares U12 and the trailing tiles (a cluster barrier
+// between the phases), and each CTA solves its own slice of the columns of
+// P_c.  Z is read with L2-only loads there, since other CTAs write it between
+// the phases.
+constexpr int kZNB = 32, kZTS = 64;
+
+struct ZShared {
+  double sa[kZTS][kZNB + 1];
+  double sb[kZNB][kZTS + 1];
+  double sinv[kZNB];  // reciprocals of a staged diagonal block
+  double prow[kZNB];
+  double pinv;  // 1 / pivot of the current panel column
+  int rm[2 * KF_MAX_SMAX];
+  double rv[8];
+  int ri[8];
+  int pk;
+  double amax;
+};
+
+// L2 selects L2-only loads (the cluster kernel: other CTAs write Z between phases)
+template <bool L2>
+__device__ __forceinline__ double zld(const double* p) {
+  if (L2) return __ldcg(p);
+  return *p;
+}
+
+template <bool L2>
+__device__ double z_absmax(const double* A, int ldz, int z, ZShared& sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // max |Z| for the pivot test
-  double mx = 0.0;
-  for (int64_t e = tid; e < (int64_t)z * z; e += blockDim.x) mx = fmax(mx, fabs(A[(e / z) * ldz + e % z]));
-  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  if (lane == 0) rv[warp] = mx;
+  // the bit patterns of |v| order like the values: integer max keeps this off the FP64 pipe
+  long long mx = 0;
+  for (int i = tid / 32; i < z; i += blockDim.x / 32)
+    for (int c = lane; c < z; c += 32) mx = max(mx, __double_as_longlong(zld<L2>(A + (int64_t)i * ldz + c)) & 0x7fffffffffffffffll);
+  for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if (lane == 0) sh.rv[warp] = __longlong_as_double(mx);
   __syncthreads();
   if (tid == 0) {
-    double m2 = 0.0;
-    for (int w = 0; w < 8; ++w) m2 = fmax(m2, rv[w]);
-    amax_sh = m2;
+    long long m2 = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = max(m2, __double_as_longlong(sh.rv[w]));
+    sh.amax = __longlong_as_double(m2);
   }
   __syncthreads();
-  const double amax = amax_sh;
-  bool bad = false;
-  double umin = INFINITY, umax = 0.0;
-  for (int kb = 0; kb < z; kb += NB) {
-    const int nb = min(NB, z - kb);
-    for (int j = kb; j < kb + nb; ++j) {
-      double bv = -1.0;
-      int bi = z;
-      for (int i = j + tid; i < z; i += blockDim.x) {
-        double v = fabs(A[(int64_t)i * ldz + j]);
-        if (v > bv) { bv = v; bi = i; }
-      }
-      for (int off = 16; off > 0; off >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, bv, off);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-      }
-      if (lane == 0) { rv[warp] = bv; ri[warp] = bi; }
-      __syncthreads();
-      if (tid == 0) {
-        double b2 = -1.0;
-        int i2 = z;
-        for (int w = 0; w < 8; ++w)
-          if (rv[w] > b2 || (rv[w] == b2 && ri[w] < i2)) { b2 = rv[w]; i2 = ri[w]; }
-        pk = i2;
-        pv[j] = i2;
-      }
-      __syncthreads();
-      const int p = pk;
-      if (p != j)
-        for (int c = tid; c < z; c += blockDim.x) {
-          double t = A[(int64_t)j * ldz + c];
-          A[(int64_t)j * ldz + c] = A[(int64_t)p * ldz + c];
-          A[(int64_t)p * ldz + c] = t;
-        }
-      __syncthreads();
-      const double ujj = A[(int64_t)j * ldz + j];
-      umin = fmin(umin, fabs(ujj));
-      umax = fmax(umax, fabs(ujj));
-      if (!(fabs(ujj) > 1e-14 * amax)) bad = true;
-      const double inv = ujj != 0.0 ? 1.0 / ujj : 0.0;
-      for (int i = j + 1 + tid; i < z; i += blockDim.x) {
-        double* Ai = A + (int64_t)i * ldz;
-        const double l = Ai[j] * inv;
-        Ai[j] = l;
-        for (int c = j + 1; c < kb + nb; ++c) Ai[c] = fma(-l, A[(int64_t)j * ldz + c], Ai[c]);
-      }
-      __syncthreads();
+  return sh.amax;
+}
+
+// columns kb..kb+nb-1 of logical rows kb..z-1, one CTA
+template <bool L2>
+__device__ void zlu_panel(double* A, int ldz, int z, int kb, int nb, double amax, bool& bad, double& umin,
+                          double& umax, ZShared& sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  int* rm = sh.rm;
+  for (int j = kb; j < kb + nb; ++j) {
+    // arg-max of |A| by integer compares of the bit patterns (same order)
+    long long bv = -1;
+    int bi = z;
+    for (int i = j + tid; i < z; i += blockDim.x) {
+      const long long v = __double_as_longlong(zld<L2>(A + (int64_t)rm[i] * ldz + j)) & 0x7fffffffffffffffll;
+      if (v > bv) { bv = v; bi = i; }
     }
-    const int c0 = kb + nb;
-    if (c0 >= z) break;
-    // U12 = L11^-1 A12, thread per column
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-      int i = e / NB, j = e % NB;
-      sa[i][j] = (i < nb && j < i) ? A[(int64_t)(kb + i) * ldz + kb + j] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) {
+      const long long ov = __shfl_xor_sync(0xffffffffu, bv, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { sh.rv[warp] = __longlong_as_double(bv); sh.ri[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      long long b2 = -1;
+      int i2 = z;
+      for (int w = 0; w < nw; ++w) {
+        const long long v = __double_as_longlong(sh.rv[w]);
+        if (v > b2 || (v == b2 && sh.ri[w] < i2)) { b2 = v; i2 = sh.ri[w]; }
+      }
+      const int t = rm[j];
+      rm[j] = rm[i2];
+      rm[i2] = t;
     }
     __syncthreads();
-    for (int c = c0 + tid; c < z; c += blockDim.x) {
-      double x[NB];
-#pragma unroll
-      for (int r = 0; r < NB; ++r) x[r] = r < nb ? A[(int64_t)(kb + r) * ldz + c] : 0.0;
-#pragma unroll
-      for (int r = 1; r < NB; ++r) {
-        double acc = x[r];
-#pragma unroll
-        for (int t = 0; t < r; ++t) acc = fma(-sa[r][t], x[t], acc);
-        x[r] = acc;
+    const double* Aj = A + (int64_t)rm[j] * ldz;
+    for (int c = j + tid; c < kb + nb; c += blockDim.x) {
+      const double a = zld<L2>(Aj + c);
+      sh.prow[c - kb] = a;
+      if (c == j) {  // thread 0: the pivot; one FP64 division for the whole CTA
+        umin = fmin(umin, fabs(a));
+        umax = fmax(umax, fabs(a));
+        if (!(fabs(a) > 1e-14 * amax)) bad = true;
+        sh.pinv = a != 0.0 ? 1.0 / a : 0.0;
       }
-#pragma unroll
-      for (int r = 1; r < NB; ++r)
-        if (r < nb) A[(int64_t)(kb + r) * ldz + c] = x[r];
     }
     __syncthreads();
-    // A22 -= L21 U12
-    const int ty = tid / 16, tx = tid % 16;
-    for (int ti = c0; ti < z; ti += TS)
-      for (int tj = c0; tj < z; tj += TS) {
-        for (int e = tid; e < TS * NB; e += blockDim.x) {
-          int r = e / NB, cc = e % NB;
-          sa[r][cc] = (ti + r < z && cc < nb) ? A[(int64_t)(ti + r) * ldz + kb + cc] : 0.0;
-          int rr = e / TS, c2 = e % TS;
-          sb[rr][c2] = (rr < nb && tj + c2 < z) ? A[(int64_t)(kb + rr) * ldz + tj + c2] : 0.0;
-        }
-        __syncthreads();
-        double acc[4][4] = {};
+    const double inv = sh.pinv;
+    const int jj = j - kb;
+    for (int i = j + 1 + tid; i < z; i += blockDim.x) {
+      double* Ai = A + (int64_t)rm[i] * ldz + kb;
+      double v[kZNB];
+#pragma unroll
+      for (int c = 0; c < kZNB; ++c) v[c] = (c > jj && c < nb) ? zld<L2>(Ai + c) : 0.0;
+      const double l = zld<L2>(Ai + jj) * inv;
+#pragma unroll
+      for (int c = 0; c < kZNB; ++c)
+        if (c > jj && c < nb) Ai[c] = fma(-l, sh.prow[c], v[c]);
+      Ai[jj] = l;
+    }
+    __syncthreads();
+  }
+}
+
+// U12 = L11^-1 A12 for the columns of part `part` of `nparts` (thread per column)
+template <bool L2>
+__device__ void zlu_trsm(double* A, int ldz, int z, int kb, int nb, int part, int nparts, ZShared& sh) {
+  const int tid = threadIdx.x;
+  const int* rm = sh.rm;
+#pragma unroll 4
+  for (int e = tid; e < kZNB * kZNB; e += blockDim.x) {
+    int i = e / kZNB, j = e % kZNB;
+    sh.sa[i][j] = (i < nb && j < i) ? zld<L2>(A + (int64_t)rm[kb + i] * ldz + kb + j) : 0.0;
+  }
+  __syncthreads();
+  for (int c = kb + nb + part * (int)blockDim.x + tid; c < z; c += nparts * (int)blockDim.x) {
+    double x[kZNB];
+#pragma unroll
+    for (int r = 0; r < kZNB; ++r) x[r] = r < nb ? zld<L2>(A + (int64_t)rm[kb + r] * ldz + c) : 0.0;
+#pragma unroll
+    for (int r = 1; r < kZNB; ++r) {
+      double acc = x[r];
+#pragma unroll
+      for (int t = 0; t < r; ++t) acc = fma(-sh.sa[r][t], x[t], acc);
+      x[r] = acc;
+    }
+#pragma unroll
+    for (int r = 1; r < kZNB; ++r)
+      if (r < nb) A[(int64_t)rm[kb + r] * ldz + c] = x[r];
+  }
+  __syncthreads();
+}
+
+// C[r0 + i][q0 + j] -= sum_t Lp[i][t] Rp[t][j] over a 64 x TC tile, t < nb:
+// Lp rows from A (row stride ldz, columns k0..k0+nb), Rp rows k0..k0+nb of B
+// (row stride ldb); mA, mB, mC map logical rows to stored rows (nullptr:
+// identity).  Rows < rlim and columns < climit are valid.  256 threads: 16
+// row groups of 4 rows x 16 column groups of TC/16 columns.
+template <int TC, bool L2>
+__device__ void z_tile_sub(const double* A, int ldz, const int* mA, const double* B, int ldb, const int* mB,
+                           double* C, int ldc, const int* mC, int r0, int rlim, int q0, int climit, int k0, int nb,
+                           ZShared& sh) {
+  constexpr int CB = TC / 16;
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+#pragma unroll
+  for (int e0 = 0; e0 < kZTS * kZNB; e0 += 256) {
+    const int e = e0 + tid, r = e / kZNB, cc = e % kZNB;
+    const int row = r0 + r;
+    sh.sa[r][cc] = (row < rlim && cc < nb) ? zld<L2>(A + (int64_t)(mA ? mA[row] : row) * ldz + k0 + cc) : 0.0;
+  }
+#pragma unroll
+  for (int e0 = 0; e0 < kZNB * TC; e0 += 256) {
+    const int e = e0 + tid, rr = e / TC, c2 = e % TC;
+    if (rr < kZNB) {
+      const int row = k0 + rr;
+      sh.sb[rr][c2] = (rr < nb && q0 + c2 < climit) ? zld<L2>(B + (int64_t)(mB ? mB[row] : row) * ldb + q0 + c2) : 0.0;
+    }
+  }
+  __syncthreads();
+  double acc[4][CB] = {};
 #pragma unroll 8
-        for (int t = 0; t < NB; ++t) {
-          double av[4], bv[4];
+  for (int t = 0; t < kZNB; ++t) {
+    double av[4], bv[CB];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) av[a] = sa[ty * 4 + a][t];
+    for (int a = 0; a < 4; ++a) av[a] = sh.sa[ty * 4 + a][t];
 #pragma unroll
-          for (int b = 0; b < 4; ++b) bv[b] = sb[t][tx * 4 + b];
+    for (int b = 0; b < CB; ++b) bv[b] = sh.sb[t][tx * CB + b];
 #pragma unroll
-          for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            int i = ti + ty * 4 + a, j = tj + tx * 4 + b;
-            if (i < z && j < z) A[(int64_t)i * ldz + j] -= acc[a][b];
-          }
-        __syncthreads();
-      }
+      for (int b = 0; b < CB; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
   }
-  if (bad && tid == 0) atomicOr(status, KF_DEV_ILLCOND);
-  if (tid == 0) pivr[node] = (z == 0 || umax == 0.0) ? 1.0 : umin / umax;
-  if (!solve_pc) return;
-  // ---- T = Z^-1 P_c --------------------------------------------------------------
-  const int s = rank[node];
-  const double* B = Pc + (int64_t)node * ldz * s_max;
-  double* X = T + (int64_t)nl * ldz * s_max;
-  for (int64_t e = tid; e < (int64_t)ldz * s_max; e += blockDim.x) {
-    int i = (int)(e / s_max), q = (int)(e % s_max);
-    X[e] = (i < z && q < s) ? B[e] : 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = r0 + ty * 4 + a;
+    if (i >= rlim) continue;
+    double* Ci = C + (int64_t)(mC ? mC[i] : i) * ldc;
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+      const int j = q0 + tx * CB + b;
+      if (j < climit) Ci[j] = zld<L2>(Ci + j) - acc[a][b];
+    }
   }
   __syncthreads();
-  if (s == 0 || z == 0) return;
-  for (int k = 0; k < z; ++k) {  // row swaps in factorization order
-    const int p = pv[k];
-    if (p != k)
-      for (int q = tid; q < s; q += blockDim.x) {
-        double t = X[(int64_t)k * s_max + q];
-        X[(int64_t)k * s_max + q] = X[(int64_t)p * s_max + q];
-        X[(int64_t)p * s_max + q] = t;
-      }
-    __syncthreads();
+}
+
+// A22 -= L21 U12 for the tiles of part `part` of `nparts`
+template <bool L2>
+__device__ void zlu_update(double* A, int ldz, int z, int kb, int nb, int part, int nparts, ZShared& sh) {
+  const int c0 = kb + nb;
+  const int nt = (z - c0 + kZTS - 1) / kZTS;
+  for (int t = part; t < nt * nt; t += nparts) {
+    const int ti = c0 + (t / nt) * kZTS, tj = c0 + (t % nt) * kZTS;
+    z_tile_sub<kZTS, L2>(A, ldz, sh.rm, A, ldz, sh.rm, A, ldz, sh.rm, ti, z, tj, z, kb, nb, sh);
   }
-  const int ty = tid / 16, tx = tid % 16;
+}
+
+// X[:, q0:q1) = Z^-1 B[:, q0:q1) from the LU in A (columns >= s are zero)
+template <int TC, bool L2>
+__device__ void z_solve_cols(const double* A, int ldz, int z, const double* B, double* X, int s_max, int s, int q0,
+                             int q1, ZShared& sh) {
+  const int tid = threadIdx.x;
+  const int qw = q1 - q0;
+  const int* rm = sh.rm;
+  for (int64_t e = tid; e < (int64_t)ldz * qw; e += blockDim.x) {
+    int i = (int)(e / qw), q = q0 + (int)(e % qw);
+    X[(int64_t)i * s_max + q] = (i < z && q < s) ? B[(int64_t)rm[i] * s_max + q] : 0.0;
+  }
+  __syncthreads();
+  const int qe = min(q1, s);
+  if (qe <= q0 || z == 0) return;
   // forward: L (unit lower)
-  for (int kb = 0; kb < z; kb += NB) {
-    const int nb = min(NB, z - kb);
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-      int i = e / NB, j = e % NB;
-      sa[i][j] = (i < nb && j < i) ? A[(int64_t)(kb + i) * ldz + kb + j] : 0.0;
+  for (int kb = 0; kb < z; kb += kZNB) {
+    const int nb = min(kZNB, z - kb);
+#pragma unroll 4
+    for (int e = tid; e < kZNB * kZNB; e += blockDim.x) {
+      int i = e / kZNB, j = e % kZNB;
+      sh.sa[i][j] = (i < nb && j < i) ? zld<L2>(A + (int64_t)rm[kb + i] * ldz + kb + j) : 0.0;
     }
     __syncthreads();
-    for (int q = tid; q < s; q += blockDim.x) {
-      double x[NB];
+    for (int q = q0 + tid; q < qe; q += blockDim.x) {
+      double x[kZNB];
 #pragma unroll
-      for (int r = 0; r < NB; ++r) x[r] = r < nb ? X[(int64_t)(kb + r) * s_max + q] : 0.0;
+      for (int r = 0; r < kZNB; ++r) x[r] = r < nb ? X[(int64_t)(kb + r) * s_max + q] : 0.0;
 #pragma unroll
-      for (int r = 1; r < NB; ++r) {
+      for (int r = 1; r < kZNB; ++r) {
         double acc = x[r];
 #pragma unroll
-        for (int t = 0; t < r; ++t) acc = fma(-sa[r][t], x[t], acc);
+        for (int t = 0; t < r; ++t) acc = fma(-sh.sa[r][t], x[t], acc);
         x[r] = acc;
       }
 #pragma unroll
-      for (int r = 1; r < NB; ++r)
+      for (int r = 1; r < kZNB; ++r)
         if (r < nb) X[(int64_t)(kb + r) * s_max + q] = x[r];
     }
     __syncthreads();
-    for (int ti = kb + nb; ti < z; ti += TS)
-      for (int tj = 0; tj < s; tj += TS) {
-        for (int e = tid; e < TS * NB; e += blockDim.x) {
-          int r = e / NB, cc = e % NB;
-          sa[r][cc] = (ti + r < z && cc < nb) ? A[(int64_t)(ti + r) * ldz + kb + cc] : 0.0;
-          int rr = e / TS, c2 = e % TS;
-          sb[rr][c2] = (rr < nb && tj + c2 < s) ? X[(int64_t)(kb + rr) * s_max + tj + c2] : 0.0;
-        }
-        __syncthreads();
-        double acc[4][4] = {};
-#pragma unroll 8
-        for (int t = 0; t < NB; ++t) {
-          double av[4], bv[4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) av[a] = sa[ty * 4 + a][t];
-#pragma unroll
-          for (int b = 0; b < 4; ++b) bv[b] = sb[t][tx * 4 + b];
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            int i = ti + ty * 4 + a, j = tj + tx * 4 + b;
-            if (i < z && j < s) X[(int64_t)i * s_max + j] -= acc[a][b];
-          }
-        __syncthreads();
-      }
-    // the diagonal-block loads of the next panel reuse sa: wait for this one
-    __syncthreads();
+    for (int ti = kb + nb; ti < z; ti += kZTS)
+      for (int tj = q0; tj < qe; tj += TC)
+        z_tile_sub<TC, L2>(A, ldz, rm, X, s_max, nullptr, X, s_max, nullptr, ti, z, tj, qe, kb, nb, sh);
   }
   // backward: U
-  for (int kb = ((z - 1) / NB) * NB; kb >= 0; kb -= NB) {
-    const int nb = min(NB, z - kb);
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-      int i = e / NB, j = e % NB;
-      sa[i][j] = (i < nb && j < nb && j >= i) ? A[(int64_t)(kb + i) * ldz + kb + j] : 0.0;
+  for (int kb = ((z - 1) / kZNB) * kZNB; kb >= 0; kb -= kZNB) {
+    const int nb = min(kZNB, z - kb);
+#pragma unroll 4
+    for (int e = tid; e < kZNB * kZNB; e += blockDim.x) {
+      int i = e / kZNB, j = e % kZNB;
+      sh.sa[i][j] = (i < nb && j < nb && j >= i) ? zld<L2>(A + (int64_t)rm[kb + i] * ldz + kb + j) : 0.0;
     }
     __syncthreads();
-    for (int q = tid; q < s; q += blockDim.x) {
-      double x[NB];
+    if (tid < kZNB) sh.sinv[tid] = tid < nb ? 1.0 / sh.sa[tid][tid] : 0.0;  // divisions in parallel
+    __syncthreads();
+    for (int q = q0 + tid; q < qe; q += blockDim.x) {
+      double x[kZNB];
 #pragma unroll
-      for (int r = 0; r < NB; ++r) x[r] = r < nb ? X[(int64_t)(kb + r) * s_max + q] : 0.0;
+      for (int r = 0; r < kZNB; ++r) x[r] = r < nb ? X[(int64_t)(kb + r) * s_max + q] : 0.0;
 #pragma unroll
-      for (int r = NB - 1; r >= 0; --r) {
+      for (int r = kZNB - 1; r >= 0; --r) {
         if (r < nb) {
           double acc = x[r];
 #pragma unroll
-          for (int t = r + 1; t < NB; ++t) acc = fma(-sa[r][t], x[t], acc);
-          x[r] = acc / sa[r][r];
+          for (int t = r + 1; t < kZNB; ++t) acc = fma(-sh.sa[r][t], x[t], acc);
+          x[r] = acc * sh.sinv[r];
         }
       }
 #pragma unroll
-      for (int r = 0; r < NB; ++r)
+      for (int r = 0; r < kZNB; ++r)
         if (r < nb) X[(int64_t)(kb + r) * s_max + q] = x[r];
     }
     __syncthreads();
     // rows above: X[0:kb] -= U[0:kb, kb:kb+nb] X[kb:kb+nb]
-    for (int ti = 0; ti < kb; ti += TS)
-      for (int tj = 0; tj < s; tj += TS) {
-        for (int e = tid; e < TS * NB; e += blockDim.x) {
-          int r = e / NB, cc = e % NB;
-          sa[r][cc] = (ti + r < kb && cc < nb) ? A[(int64_t)(ti + r) * ldz + kb + cc] : 0.0;
-          int rr = e / TS, c2 = e % TS;
-          sb[rr][c2] = (rr < nb && tj + c2 < s) ? X[(int64_t)(kb + rr) * s_max + tj + c2] : 0.0;
-        }
-        __syncthreads();
-        double acc[4][4] = {};
-#pragma unroll 8
-        for (int t = 0; t < NB; ++t) {
-          double av[4], bv[4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) av[a] = sa[ty * 4 + a][t];
-#pragma unroll
-          for (int b = 0; b < 4; ++b) bv[b] = sb[t][tx * 4 + b];
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            int i = ti + ty * 4 + a, j = tj + tx * 4 + b;
-            if (i < kb && j < s) X[(int64_t)i * s_max + j] -= acc[a][b];
-          }
-        __syncthreads();
-      }
-    __syncthreads();
+    for (int ti = 0; ti < kb; ti += kZTS)
+      for (int tj = q0; tj < qe; tj += TC)
+        z_tile_sub<TC, L2>(A, ldz, rm, X, s_max, nullptr, X, s_max, nullptr, ti, kb, tj, qe, kb, nb, sh);
   }
+}
+
+__global__ void __launch_bounds__(256) k_z_factor(const int32_t* __restrict__ rank, int node0, int ldz, int s_max,
+                                                  double* __restrict__ Z, int32_t* __restrict__ piv,
+                                                  const double* __restrict__ Pc, double* __restrict__ T,
+                                                  int solve_pc, int32_t* __restrict__ status, double* __restrict__ pivr) {
+  __shared__ ZShared sh;
+  const int nl = blockIdx.x, node = node0 + nl;
+  const int z = rank[2 * node] + rank[2 * node + 1];
+  double* A = Z + (int64_t)node * ldz * ldz;
+  int32_t* pv = piv + (int64_t)node * ldz;
+  for (int i = threadIdx.x; i < z; i += blockDim.x) sh.rm[i] = i;
+  const double amax = z_absmax<false>(A, ldz, z, sh);
+  bool bad = false;
+  double umin = INFINITY, umax = 0.0;
+  for (int kb = 0; kb < z; kb += kZNB) {
+    const int nb = min(kZNB, z - kb);
+    zlu_panel<false>(A, ldz, z, kb, nb, amax, bad, umin, umax, sh);
+    if (kb + nb >= z) break;
+    zlu_trsm<false>(A, ldz, z, kb, nb, 0, 1, sh);
+    zlu_update<false>(A, ldz, z, kb, nb, 0, 1, sh);
+  }
+  for (int i = threadIdx.x; i < z; i += blockDim.x) pv[i] = sh.rm[i];
+  if (bad && threadIdx.x == 0) atomicOr(status, KF_DEV_ILLCOND);
+  if (threadIdx.x == 0) pivr[node] = (z == 0 || umax == 0.0) ? 1.0 : umin / umax;
+  if (!solve_pc) return;
+  z_solve_cols<kZTS, false>(A, ldz, z, Pc + (int64_t)node * ldz * s_max, T + (int64_t)nl * ldz * s_max, s_max,
+                            rank[node], 0, s_max, sh);
+}
+
+// cluster size is set at launch (cudaLaunchAttributeClusterDimension)
+__global__ void __launch_bounds__(256) k_z_factor_cluster(const int32_t* __restrict__ rank, int node0, int ldz,
+                                                          int s_max, double* __restrict__ Z,
+                                                          int32_t* __restrict__ piv, const double* __restrict__ Pc,
+                                                          double* __restrict__ T, int solve_pc,
+                                                          int32_t* __restrict__ status, double* __restrict__ pivr) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ ZShared sh;
+  const int cr = (int)cluster.block_rank(), nc = (int)cluster.num_blocks();
+  const int nl = blockIdx.x / nc, node = node0 + nl;
+  const int z = rank[2 * node] + rank[2 * node + 1];
+  double* A = Z + (int64_t)node * ldz * ldz;
+  int32_t* pv = piv + (int64_t)node * ldz;
+  for (int i = threadIdx.x; i < z; i += blockDim.x) sh.rm[i] = i;
+  double amax = 0.0;
+  if (cr == 0) amax = z_absmax<true>(A, ldz, z, sh);
+  bool bad = false;
+  double umin = INFINITY, umax = 0.0;
+  // CTA 0 owns the row map; the others take it from pv after each panel
+  for (int kb = 0; kb < z; kb += kZNB) {  // the same trip count in every CTA of the cluster
+    const int nb = min(kZNB, z - kb);
+    if (cr == 0) {
+      zlu_panel<true>(A, ldz, z, kb, nb, amax, bad, umin, umax, sh);
+      for (int i = kb + threadIdx.x; i < z; i += blockDim.x) pv[i] = sh.rm[i];
+    }
+    cluster.sync();
+    if (cr != 0) {
+      for (int i = kb + threadIdx.x; i < z; i += blockDim.x) sh.rm[i] = __ldcg(pv + i);
+      __syncthreads();
+    }
+    if (kb + nb >= z) break;
+    zlu_trsm<true>(A, ldz, z, kb, nb, cr, nc, sh);
+    cluster.sync();
+    zlu_update<true>(A, ldz, z, kb, nb, cr, nc, sh);
+    cluster.sync();
+  }
+  if (cr == 0 && threadIdx.x == 0) {
+    if (bad) atomicOr(status, KF_DEV_ILLCOND);
+    pivr[node] = (z == 0 || umax == 0.0) ? 1.0 : umin / umax;
+  }
+  if (!solve_pc) return;
+  const int qn = (s_max + nc - 1) / nc;
+  const int q0 = min(s_max, cr * qn), q1 = min(s_max, q0 + qn);
+  z_solve_cols<16, true>(A, ldz, z, Pc + (int64_t)node * ldz * s_max, T + (int64_t)nl * ldz * s_max, s_max,
+                         rank[node], q0, q1, sh);
 }
 
 // Telescoping GEMM: P^_a[rows of c, :s_a] = P^_c[:, :s_c] T[c block, :s_a].
@@ -790,14 +882,14 @@ __global__ void __launch_bounds__(256) k_telescope(const int32_t* __restrict__ l
 // FP64-accurate operator.
 __global__ void k_leaf_k64(const float* __restrict__ X32lo, const float* __restrict__ X32, int d, double c_exp,
                            const int32_t* __restrict__ lo, const int32_t* __restrict__ hi, int leaf0, int ldL,
-                           double* __restrict__ K64) {
+                           double* __restrict__ K64, float ch, float cl, const float2* __restrict__ tab) {
   const int lf = blockIdx.z, node = leaf0 + lf;
   const int b = lo[node], n = hi[node] - b;
   const int i = blockIdx.y;
   if (i >= n) return;
   double* Ki = K64 + ((int64_t)lf * ldL + i) * ldL;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-    Ki[j] = kf_kern_hybrid(X32, X32lo, b + i, b + j, d, c_exp);
+    Ki[j] = kf_kern_hybrid(X32, X32lo, b + i, b + j, d, c_exp, ch, cl, tab);
 }
 
 template <typename T>
@@ -813,7 +905,8 @@ kf_status leaves_t(kf_factor* f, cudaStream_t s) {
   dim3 g((ldL + 127) / 128, ldL, nleaf);
   KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_assemble<T><<<g, 128, 0, s>>>(t->X64, t->X32, t->d, f->c_exp, f->lambda, t->d_lo, t->d_hi, leaf0, ldL, L));
   if (f->K64)
-    KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_k64<<<g, 128, 0, s>>>(t->X32lo, t->X32, t->d, f->c_exp, t->d_lo, t->d_hi, leaf0, ldL, f->K64));
+    KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_k64<<<g, 128, 0, s>>>(t->X32lo, t->X32, t->d, f->c_exp, t->d_lo, t->d_hi, leaf0, ldL, f->K64,
+                                                          f->c_exp_hi, f->c_exp_lo, t->exp_tab));
   KF_PHASE(KF_PH_LEAF_CHOL, s, k_leaf_cholesky<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, ldL, L, f->status, f->pivr));
   if (D > 0)
     KF_PHASE(KF_PH_LEAF_PHAT, s, k_leaf_phat<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, leaf0, ldL, L, f->Pleaf, s_max,
@@ -822,8 +915,39 @@ kf_status leaves_t(kf_factor* f, cudaStream_t s) {
   return KF_OK;
 }
 
+// V blocks of the children of level l (rows of level l + 1): they need the
+// skeletons of level l + 1 only, so the pipelined driver runs them ahead on
+// a stream of their own.
 template <typename T>
-kf_status level_t(kf_factor* f, int l, double* Tm, cudaStream_t s) {
+kf_status level_eval_v(kf_factor* f, int l, cudaStream_t s) {
+  kf_tree* t = f->t;
+  kf_ctx* c = f->ctx;
+  const int s_max = f->s_max;
+  const int64_t N = t->N;
+  T* VT = (T*)f->VT;
+  auto lvl = [&](T* base, int lv) { return base + (int64_t)(lv - 1) * N * s_max; };
+  const int nn = 1 << l;
+  const int child0 = 1 << (l + 1);
+  // V blocks of the children's level
+  const int vt_rows = 64;
+  dim3 gv((unsigned)(((N >> (l + 1)) + vt_rows) / vt_rows), 2 * nn);
+  // skeleton coordinates of up to qchunk columns per pass, at most 96 KiB of shared memory
+  const int64_t per = (int64_t)sizeof(T) + (f->VT64 ? (int64_t)sizeof(float) : 0);  // bytes per staged coordinate
+  const int qchunk = (int)std::max<int64_t>(1, std::min<int64_t>(s_max, (96 * 1024 / per - 8 * t->d) / t->d));
+  const size_t vt_smem = (size_t)per * ((size_t)t->d * qchunk + 8 * t->d);
+  KF_CUDA(c, cudaFuncSetAttribute(k_eval_vt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vt_smem));
+  KF_PHASE(KF_PH_EVAL_V, s, k_eval_vt<T><<<gv, 256, vt_smem, s>>>(t->X64, t->X32, t->X32lo, t->d, f->c_exp, t->d_lo, t->d_hi,
+                                                                 f->rank, f->skel, s_max, child0, vt_rows, qchunk,
+                                                                 lvl(VT, l + 1),
+                                                                 f->VT64 ? f->VT64 + (int64_t)l * N * s_max : nullptr,
+                                                                 f->c_exp_hi, f->c_exp_lo, t->exp_tab));
+  KF_LAUNCH_CHECK(c);
+  return KF_OK;
+}
+
+// Z, its LU, T = Z^-1 P_c and the telescoped P^ of level l
+template <typename T>
+kf_status level_reduce(kf_factor* f, int l, double* Tm, cudaStream_t s) {
   kf_tree* t = f->t;
   kf_ctx* c = f->ctx;
   const int s_max = f->s_max, ldz = 2 * s_max;
@@ -832,18 +956,6 @@ kf_status level_t(kf_factor* f, int l, double* Tm, cudaStream_t s) {
   T* VT = (T*)f->VT;
   auto lvl = [&](T* base, int lv) { return base + (int64_t)(lv - 1) * N * s_max; };
   const int node0 = 1 << l, nn = 1 << l;
-  const int child0 = 1 << (l + 1);
-  // V blocks of the children's level
-  const int vt_rows = 64;
-  dim3 gv((unsigned)(((N >> (l + 1)) + vt_rows) / vt_rows), 2 * nn);
-  // skeleton coordinates of up to qchunk columns per pass, at most 96 KiB of shared memory
-  const int qchunk = (int)std::max<int64_t>(1, std::min<int64_t>(s_max, (96 * 1024 / (int64_t)sizeof(T) - 8 * t->d) / t->d));
-  const size_t vt_smem = sizeof(T) * ((size_t)t->d * qchunk + 8 * t->d);
-  KF_CUDA(c, cudaFuncSetAttribute(k_eval_vt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vt_smem));
-  KF_PHASE(KF_PH_EVAL_V, s, k_eval_vt<T><<<gv, 256, vt_smem, s>>>(t->X64, t->X32, t->X32lo, t->d, f->c_exp, t->d_lo, t->d_hi,
-                                                                 f->rank, f->skel, s_max, child0, vt_rows, qchunk,
-                                                                 lvl(VT, l + 1),
-                                                                 f->VT64 ? f->VT64 + (int64_t)l * N * s_max : nullptr));
   // Z
   KF_PHASE(KF_PH_ZOFF, s, k_z_init<<<dim3(grid_for((int64_t)ldz * ldz, 256, 64), nn), 256, 0, s>>>(f->rank, node0, ldz, f->ZLU));
   const int tiles = ((s_max + 63) / 64) * ((s_max + 63) / 64);
@@ -857,8 +969,35 @@ kf_status level_t(kf_factor* f, int l, double* Tm, cudaStream_t s) {
     KF_PHASE(KF_PH_ZOFF, s, k_zoff<T><<<dim3(tiles, ksplit, 2 * nn), 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, node0, s_max, lvl(VT, l + 1),
                                                           lvl(Phat, l + 1), ldz, f->ZLU, ksplit));
   }
-  KF_PHASE(KF_PH_ZLU, s, k_z_factor<<<nn, 256, 0, s>>>(f->rank, node0, ldz, s_max, f->ZLU, f->Zpiv, f->Pc, Tm,
-                                                       l >= 1 ? 1 : 0, f->status, f->pivr));
+  // few nodes: a cluster of CTAs per node, sized so that the level runs in
+  // one wave (one CTA per SM: the kernel takes 255 registers a thread)
+  int zc = 1;
+  if (f->use_cluster_lu)
+    while (zc < 16 && (int64_t)nn * zc * 2 <= 152) zc *= 2;
+  if (zc > 1) {
+    KF_CUDA(c, cudaFuncSetAttribute(k_z_factor_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nn * zc));
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)zc;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const int solve = l >= 1 ? 1 : 0;
+    cudaError_t le = cudaSuccess;
+    KF_PHASE(KF_PH_ZLU, s, le = cudaLaunchKernelEx(&cfg, k_z_factor_cluster, (const int32_t*)f->rank, node0, ldz,
+                                                   s_max, f->ZLU, f->Zpiv, (const double*)f->Pc, Tm, solve,
+                                                   f->status, f->pivr));
+    if (le != cudaSuccess)
+      return kf_set_err(c, KF_ECUDA, "reduced-system LU (cluster of %d) at level %d: %s", zc, l, cudaGetErrorString(le));
+  } else {
+    KF_PHASE(KF_PH_ZLU, s, k_z_factor<<<nn, 256, 0, s>>>(f->rank, node0, ldz, s_max, f->ZLU, f->Zpiv, f->Pc, Tm,
+                                                         l >= 1 ? 1 : 0, f->status, f->pivr));
+  }
   if (l >= 1) {
     const int64_t cmax_rows = (N >> (l + 1)) + 1;
     dim3 gt((unsigned)((cmax_rows + 63) / 64), (s_max + 63) / 64, 2 * nn);
@@ -887,8 +1026,17 @@ kf_status kf_factorize_leaves(kf_factor* f, cudaStream_t s) {
   return f->prec == KF_PREC_FP64 ? leaves_t<double>(f, s) : leaves_t<float>(f, s);
 }
 
+kf_status kf_factorize_level_v(kf_factor* f, int l, cudaStream_t s) {
+  return f->prec == KF_PREC_FP64 ? level_eval_v<double>(f, l, s) : level_eval_v<float>(f, l, s);
+}
+
+kf_status kf_factorize_level_z(kf_factor* f, int l, double* Tm, cudaStream_t s) {
+  return f->prec == KF_PREC_FP64 ? level_reduce<double>(f, l, Tm, s) : level_reduce<float>(f, l, Tm, s);
+}
+
 kf_status kf_factorize_level(kf_factor* f, int l, double* Tm, cudaStream_t s) {
-  return f->prec == KF_PREC_FP64 ? level_t<double>(f, l, Tm, s) : level_t<float>(f, l, Tm, s);
+  kf_status st = kf_factorize_level_v(f, l, s);
+  return st == KF_OK ? kf_factorize_level_z(f, l, Tm, s) : st;
 }
 
 kf_status kf_factorize_device(kf_factor* f, cudaStream_t s) {
@@ -920,39 +1068,60 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
   const size_t tb = sizeof(double) * kf_factor_tm_elems(f);
   double* Tm = st == KF_OK ? (double*)c->dalloc(tb, s) : nullptr;
   if (st == KF_OK && !Tm) st = kf_set_err(c, KF_ENOMEM, "factorize: allocation failed");
-  cudaStream_t s1 = nullptr, s2 = nullptr;
-  std::vector<cudaEvent_t> ev(D + 3, nullptr);
+  cudaStream_t s1 = nullptr, s2 = nullptr, s3 = nullptr;
+  std::vector<cudaEvent_t> ev(D + 4, nullptr), evv(D, nullptr);
   if (st == KF_OK) {
     // the skeleton chain is the critical path: it runs on a high-priority stream
     int lo_prio = 0, hi_prio = 0;
     cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
     KF_CUDA(c, cudaStreamCreateWithPriority(&s1, cudaStreamNonBlocking, hi_prio));
     KF_CUDA(c, cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, lo_prio));
+    KF_CUDA(c, cudaStreamCreateWithPriority(&s3, cudaStreamNonBlocking, lo_prio));
     for (auto& e : ev) KF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (auto& e : evv) KF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     // ev[l]: skeletons of level l done (on s1); ev[0]: allocations ready (on s);
-    // ev[D+1]: factorization done (on s2); ev[D+2]: skeletons done (on s1)
+    // ev[D+1]: factorization done (on s2); ev[D+2]: skeletons done (on s1);
+    // ev[D+3]: V blocks done (on s3); evv[l]: V blocks of level l done (on s3)
     cudaEventRecord(ev[0], s);
     cudaStreamWaitEvent(s1, ev[0], 0);
     cudaStreamWaitEvent(s2, ev[0], 0);
+    cudaStreamWaitEvent(s3, ev[0], 0);
     for (int l = D; l >= 1 && st == KF_OK; --l) {
       st = kf_skel_level(f, l, &sc, s1);
       cudaEventRecord(ev[l], s1);
       if (st != KF_OK) break;
+      // V blocks of level l - 1 (rows of level l) need the skeletons of level l
+      cudaStreamWaitEvent(s3, ev[l], 0);
+      st = kf_factorize_level_v(f, l - 1, s3);
+      cudaEventRecord(evv[l - 1], s3);
+      if (st != KF_OK) break;
       cudaStreamWaitEvent(s2, ev[l], 0);
-      if (l == D) st = kf_factorize_leaves(f, s2);
-      else st = kf_factorize_level(f, l, Tm, s2);
+      if (l == D) {
+        st = kf_factorize_leaves(f, s2);
+      } else {
+        cudaStreamWaitEvent(s2, evv[l], 0);
+        st = kf_factorize_level_z(f, l, Tm, s2);
+      }
     }
-    if (st == KF_OK) st = kf_factorize_level(f, 0, Tm, s2);
+    if (st == KF_OK) {
+      cudaStreamWaitEvent(s2, evv[0], 0);
+      st = kf_factorize_level_z(f, 0, Tm, s2);
+    }
     cudaEventRecord(ev[D + 1], s2);
     cudaEventRecord(ev[D + 2], s1);
+    cudaEventRecord(ev[D + 3], s3);
     cudaStreamWaitEvent(s, ev[D + 1], 0);
     cudaStreamWaitEvent(s, ev[D + 2], 0);
+    cudaStreamWaitEvent(s, ev[D + 3], 0);
   }
   if (Tm) c->dfree(Tm, tb, s);
   kf_skel_end(f, &sc, s);
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : evv)
+    if (e) cudaEventDestroy(e);
   if (s1) cudaStreamDestroy(s1);
   if (s2) cudaStreamDestroy(s2);
+  if (s3) cudaStreamDestroy(s3);
   return st;
 }

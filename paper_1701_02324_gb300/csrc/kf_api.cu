@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "kf_internal.cuh"
@@ -229,13 +230,15 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
   f->lambda = lambda;
   f->tau = tau;
   f->c_exp = -0.5 / (h * h);
+  f->c_exp_hi = (float)f->c_exp;
+  f->c_exp_lo = (float)(f->c_exp - (double)f->c_exp_hi);
   f->s_max = s_max;
   f->n_samp = 2 * s_max;
   // defaults: the mixed path refines with GMRES(20) against an FP64-accurate
   // operator; the FP64 path solves directly
   const int32_t prec0 = opts ? opts->precision : KF_PREC_FP64;
   f->fp64_op = prec0 == KF_PREC_MIXED ? 1 : 0;
-  f->gmres_m = 20;
+  f->gmres_m = 50;
   f->refine_max_iter = 100;
   if (opts) {
     f->prec = opts->precision;
@@ -250,6 +253,7 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
     f->use_tc = opts->no_tensor_cores ? 0 : 1;
     if (opts->fp64_operator != 0) f->fp64_op = opts->fp64_operator > 0 ? 1 : 0;
     if (opts->gmres_restart != 0) f->gmres_m = opts->gmres_restart > 0 ? std::min(opts->gmres_restart, 64) : 0;
+    if (opts->no_cluster_kernels) f->use_cluster_qr = f->use_cluster_lu = 0;
   }
   if (f->prec != KF_PREC_FP64 && f->prec != KF_PREC_MIXED) {
     delete f;
@@ -349,6 +353,21 @@ kf_status kf_destroy(kf_ctx* c) {
 
 const char* kf_last_error(const kf_ctx* c) { return c ? c->err.c_str() : g_err.c_str(); }
 
+// 2^(j/64), j < 64, split into double-float pairs (hi = fp32(v), lo = fp32(v - hi))
+// for the table-driven exponential of the kernel entries
+static const float2* exp2_table() {
+  static const std::vector<float2> tab = [] {
+    std::vector<float2> v(64);
+    for (int j = 0; j < 64; ++j) {
+      const double e = std::exp2((double)j / 64.0);
+      v[j].x = (float)e;
+      v[j].y = (float)(e - (double)v[j].x);
+    }
+    return v;
+  }();
+  return tab.data();
+}
+
 kf_status kf_tree_build(kf_ctx* c, const void* X, int32_t dtype, int64_t N, int32_t d, int32_t m, void* stream,
                         kf_tree** out) {
   if (!c || !out) return KF_EINVAL;
@@ -394,11 +413,12 @@ kf_status kf_tree_build(kf_ctx* c, const void* X, int32_t dtype, int64_t N, int3
   t->X64 = (double*)talloc(sizeof(double) * N * d);
   t->X32 = (float*)talloc(sizeof(float) * N * d);
   t->X32lo = (float*)talloc(sizeof(float) * N * d);
+  t->exp_tab = (float2*)talloc(sizeof(float2) * 64);
   t->perm = (int64_t*)talloc(sizeof(int64_t) * N);
   t->d_lo = (int32_t*)talloc(sizeof(int32_t) * (t->nnodes + 1));
   t->d_hi = (int32_t*)talloc(sizeof(int32_t) * (t->nnodes + 1));
   int32_t* bad = (int32_t*)talloc(sizeof(int32_t));
-  if (!t->X64 || !t->X32 || !t->X32lo || !t->perm || !t->d_lo || !t->d_hi || !bad) {
+  if (!t->X64 || !t->X32 || !t->X32lo || !t->exp_tab || !t->perm || !t->d_lo || !t->d_hi || !bad) {
     kf_tree_free(t);
     return kf_set_err(c, KF_ENOMEM, "tree: device allocation failed");
   }
@@ -412,6 +432,7 @@ kf_status kf_tree_build(kf_ctx* c, const void* X, int32_t dtype, int64_t N, int3
       else kf_to_f64_launch((const float*)xs.dev, t->X64, N * d, s);
       cudaMemcpyAsync(t->d_lo, t->lo.data(), sizeof(int32_t) * (t->nnodes + 1), cudaMemcpyHostToDevice, s);
       cudaMemcpyAsync(t->d_hi, t->hi.data(), sizeof(int32_t) * (t->nnodes + 1), cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(t->exp_tab, exp2_table(), sizeof(float2) * 64, cudaMemcpyHostToDevice, s);
       cudaMemsetAsync(bad, 0, sizeof(int32_t), s);
       kf_check_finite_launch(t->X64, N * d, bad, s);
       int32_t hb = 0;

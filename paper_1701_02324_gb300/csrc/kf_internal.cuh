@@ -46,6 +46,7 @@ struct kf_tree {
   double* X64 = nullptr;
   float* X32 = nullptr;
   float* X32lo = nullptr;  // fp32(X64 - X32): the low half of a double-float copy
+  float2* exp_tab = nullptr;  // 2^(j/64), j < 64, as double-float pairs (kf_exp_df)
   int64_t* perm = nullptr;
   std::vector<std::pair<void*, size_t>> allocs;
 };
@@ -54,9 +55,11 @@ struct kf_factor {
   kf_tree* t = nullptr;
   kf_ctx* ctx = nullptr;
   double h = 1, lambda = 0, tau = 0, c_exp = 0;
+  float c_exp_hi = 0, c_exp_lo = 0;  // c_exp as a double-float pair
   int32_t s_max = 0, n_samp = 0, cmax = 0, prec = 0, vstore = 0, sync_errors = 0;
   int32_t use_tc = 1;  // mixed path: tcgen05 products (0: CUDA-core FP32)
   int32_t use_cluster_qr = 1;  // upper tree levels: cluster QR in distributed shared memory
+  int32_t use_cluster_lu = 1;  // upper tree levels: reduced-system LU and T on a CTA cluster per node
   int32_t fp64_op = 0;  // keep FP64 operator data (VT64, K64)
   int32_t gmres_m = 0;  // refinement: 0 = Richardson, m > 0 = GMRES(m)
   int32_t refine_user = 0;  // refinement explicitly requested (enables it on the FP64 path)
@@ -119,42 +122,118 @@ __device__ __forceinline__ float kf_kern32(const float* __restrict__ x, const fl
   return __expf(acc * c_exp);
 }
 
-// Squared distance in double-float arithmetic on the FP32 pipes: every
-// coordinate is held as hi + lo (hi = fp32(x), lo = fp32(x - hi)); the
-// difference, its square and the running sum carry an error term through
-// exact two-sum / two-product steps, giving about 44 significant bits.
+// ---- double-float arithmetic on the FP32 pipes ------------------------------------
+// Every coordinate is also held as hi + lo (hi = fp32(x), lo = fp32(x - hi)):
+// differences, squares and sums then carry an error term through exact
+// two-sum / two-product steps, giving about 46 significant bits.
 __device__ __forceinline__ void kf_two_sum(float a, float b, float& s, float& e) {
   // round-to-nearest intrinsics: never contracted, so the error term is exact
   s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
-__device__ __forceinline__ double kf_sqdist_df(const float* __restrict__ xh, const float* __restrict__ xl,
-                                              const float* __restrict__ yh, const float* __restrict__ yl, int d) {
-  float ah = 0.f, al = 0.f;
+// A double-float value is the unevaluated sum hi + lo of two floats, |lo| at
+// most half an ulp of hi (Dekker 1971).  two_sum (Knuth) and two_prod (by
+// FMA) are error-free; the rest is built from them.
+__device__ __forceinline__ void kf_two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = fmaf(a, b, -p);
+}
+// |a| >= |b| (or a == 0)
+__device__ __forceinline__ void kf_fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// exp(y), y = yh + yl in [-20, 0], to about 2^-46 relative, on the FP32 pipes:
+// Tang's table-driven method (ACM TOMS 15(2), 1989).  y = n ln2/64 + r with n
+// an integer and |r| <= ln2/128, ln2/64 split Cody-Waite style into L1 (12
+// significant bits, so n L1 is exact for |n| < 4096) + L2 + L3;
+// exp(y) = 2^(n >> 6) 2^((n & 63)/64) (1 + q), q = r + r^2/2 + ... + r^5/120
+// (the r^6 term is below 4e-17).  tab[j] = 2^(j/64) as a double-float pair.
+__device__ __forceinline__ double kf_exp_df(float yh, float yl, const float2* __restrict__ tab) {
+  const float kInvL = 0x1.715476p+6f;  // 64 / ln 2
+  const float L1 = 0x1.62ep-7f, L2 = 0x1.0bfbe8p-21f, L3 = 0x1.cf79acp-46f;
+  const float n = rintf(__fmul_rn(yh, kInvL));
+  const float t1 = fmaf(-n, L1, yh);  // exact: yh and n L1 agree in their leading bits
+  float p, pe, s, e, s2, e2, rh, rl;
+  kf_two_prod(n, L2, p, pe);          // n L2 = p + pe
+  kf_two_sum(t1, -p, s, e);           // t1 - p = s + e
+  kf_two_sum(s, yl, s2, e2);
+  e2 = __fadd_rn(e2, __fsub_rn(__fsub_rn(e, pe), __fmul_rn(n, L3)));
+  kf_fast_two_sum(s2, e2, rh, rl);    // r = rh + rl
+  float sq, sqe;
+  kf_two_prod(rh, rh, sq, sqe);
+  sqe = fmaf(2.f * rh, rl, sqe);      // r^2 = sq + sqe
+  const float tail = __fmul_rn(__fmul_rn(sq, rh), fmaf(rh, fmaf(rh, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f));
+  float a, ae;
+  kf_two_sum(rh, 0.5f * sq, a, ae);   // q = a + ae
+  ae = __fadd_rn(ae, __fadd_rn(rl, __fadd_rn(0.5f * sqe, tail)));
+  const int ni = __float2int_rn(n);
+  const float2 T = __ldg(tab + (ni & 63));
+  float u, ue, v, ve;
+  kf_two_prod(T.x, a, u, ue);         // T q = u + ue
+  ue = fmaf(T.x, ae, fmaf(T.y, a, ue));
+  kf_two_sum(T.x, u, v, ve);          // T + T q
+  ve = __fadd_rn(ve, __fadd_rn(T.y, ue));
+  float hi, lo;
+  kf_fast_two_sum(v, ve, hi, lo);
+  const float sc = __int_as_float(((ni >> 6) + 127) << 23);  // 2^(n >> 6), exact
+  return (double)__fmul_rn(hi, sc) + (double)__fmul_rn(lo, sc);
+}
+
+// squared distance as a double-float pair (ah, al); y's coordinates are ys apart
+__device__ __forceinline__ void kf_sqdist_df2(const float* __restrict__ xh, const float* __restrict__ xl,
+                                              const float* __restrict__ yh, const float* __restrict__ yl, int ys,
+                                              int d, float& ah, float& al) {
+  ah = 0.f;
+  al = 0.f;
   for (int k = 0; k < d; ++k) {
     float th, te;
-    kf_two_sum(xh[k], -yh[k], th, te);
-    const float tl = te + (xl[k] - yl[k]);
+    kf_two_sum(xh[k], -yh[k * ys], th, te);
+    const float tl = te + (xl[k] - yl[k * ys]);
     const float p = __fmul_rn(th, th);
-    const float q = fmaf(th, th, -p) + 2.f * th * tl;  // th^2 - p exactly, plus the cross term
+    const float q = fmaf(th, th, -p) + 2.f * th * tl;
     float sh, se;
     kf_two_sum(ah, p, sh, se);
     se = __fadd_rn(se, __fadd_rn(al, q));
     ah = __fadd_rn(sh, se);
     al = __fsub_rn(se, __fsub_rn(ah, sh));
   }
-  return (double)ah + (double)al;
+}
+
+// Kernel entry exp(c |x - y|^2) to about 2^-46 relative with no FP64
+// arithmetic but the final conversion, from the squared distance ah + al and
+// c = ch + cl (kf_kern_df: from coordinates held as double-float pairs, X32 +
+// X32lo).  Arguments below -20 (entries below 2e-9) take the FP32
+// exponential, whose absolute error there is below 1e-16.
+__device__ __forceinline__ double kf_kern_from_df(float ah, float al, float ch, float cl,
+                                                  const float2* __restrict__ tab) {
+  float y, ye;
+  kf_two_prod(ah, ch, y, ye);
+  ye = fmaf(ah, cl, fmaf(al, ch, ye));
+  float zh, zl;
+  kf_fast_two_sum(y, ye, zh, zl);
+  if (zh < -20.f) return (double)__expf(zh);
+  return kf_exp_df(zh, zl, tab);
+}
+
+__device__ __forceinline__ double kf_kern_df(const float* __restrict__ xh, const float* __restrict__ xl,
+                                             const float* __restrict__ yh, const float* __restrict__ yl, int d,
+                                             float ch, float cl, const float2* __restrict__ tab) {
+  float ah, al;
+  kf_sqdist_df2(xh, xl, yh, yl, 1, d, ah, al);
+  return kf_kern_from_df(ah, al, ch, cl, tab);
 }
 
 // FP64-accurate kernel entry at FP32 cost for the small ones: entries below
 // 2^-24 are taken from the FP32 evaluation (their absolute error stays below
-// about 1e-12); larger ones take the double-float distance and an FP64 exp.
+// about 1e-14); larger ones take the double-float evaluation.
 __device__ __forceinline__ double kf_kern_hybrid(const float* X32, const float* X32lo, int64_t i, int64_t j, int d,
-                                                 double c_exp) {
+                                                 double c_exp, float ch, float cl, const float2* tab) {
   const float k32 = kf_kern32(X32 + i * d, X32 + j * d, d, (float)c_exp);
   if (k32 < 5.9604645e-8f) return (double)k32;
-  return exp(kf_sqdist_df(X32 + i * d, X32lo + i * d, X32 + j * d, X32lo + j * d, d) * c_exp);
+  return kf_kern_df(X32 + i * d, X32lo + i * d, X32 + j * d, X32lo + j * d, d, ch, cl, tab);
 }
 
 template <typename T> struct kf_kern;
@@ -199,6 +278,8 @@ kf_status kf_factorize_device(kf_factor* f, cudaStream_t s);
 size_t kf_factor_tm_elems(const kf_factor* f);
 kf_status kf_factorize_leaves(kf_factor* f, cudaStream_t s);
 kf_status kf_factorize_level(kf_factor* f, int l, double* Tm, cudaStream_t s);
+kf_status kf_factorize_level_v(kf_factor* f, int l, cudaStream_t s);
+kf_status kf_factorize_level_z(kf_factor* f, int l, double* Tm, cudaStream_t s);
 // skeletonize and factorize with the two interleaved on two streams
 kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s);
 kf_status kf_solve_device(kf_factor* f, double* W, int64_t nrhs, int transpose, cudaStream_t s);

@@ -113,8 +113,12 @@ __global__ void k_eval_A(const double* __restrict__ X, int d, double c_exp, cons
 __device__ void id_finish(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                           int32_t* __restrict__ rank, int32_t* __restrict__ skel, int s_max, int node, int nl,
                           bool leaf, int n_samp, int c, const double* __restrict__ Ab, const int* piv, int s,
-                          double* __restrict__ Pout, int ldP, int64_t P_node_stride) {
+                          double* __restrict__ Pout, int ldP, int64_t P_node_stride, double* rinv) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  // reciprocals of the diagonal of R11 (shared memory, s entries), so that the
+  // back substitution multiplies instead of dividing in every lane
+  for (int t = threadIdx.x; t < s; t += blockDim.x) rinv[t] = 1.0 / Ab[(int64_t)t * n_samp + t];
+  __syncthreads();
   // T = R11^-1 R12 (warp per column of R12), written straight into P
   // P[j * ldP + q]: ID column j, skeleton q.  Leaves write their rows of the
   // N x s_max matrix (base lo[node]); internal nodes have fixed-size blocks.
@@ -129,14 +133,16 @@ __device__ void id_finish(const int32_t* __restrict__ lo, const int32_t* __restr
     }
     for (int t = s - 1; t >= 0; --t) {
       const double* ct = Ab + (int64_t)t * n_samp;
+      const int rt = t >> 5;  // register slot of row t (lane t & 31)
       double bt = 0.0;
 #pragma unroll
       for (int r = 0; r < KF_MAX_SMAX / 32; ++r)
-        if (lane + 32 * r == t) bt = b[r];
+        if (r == rt) bt = b[r];
       bt = __shfl_sync(0xffffffffu, bt, t & 31);
-      double xt = bt / ct[t];
+      const double xt = bt * rinv[t];
 #pragma unroll
       for (int r = 0; r < KF_MAX_SMAX / 32; ++r) {
+        if (r > rt) break;  // rows above t are final
         int i = lane + 32 * r;
         if (i == t) b[r] = xt;
         else if (i < t) b[r] = fma(-ct[i], xt, b[r]);
@@ -261,6 +267,7 @@ __global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ 
     double vtv = 0.0;
     for (int w = 0; w < nwarps; ++w) vtv += red_v[w];
     const double beta = vtv > 0.0 ? 2.0 / vtv : 0.0;
+    const int nr = (ns - k + 31) >> 5;  // 32-row chunks of rows k..ns-1
     // apply H to the trailing columns; their squared norms over rows > k are
     // downdated by the new row-k entry, and evaluated exactly again once they
     // have fallen by 16x since the last exact value (rounding stays near
@@ -271,6 +278,7 @@ __global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ 
       double dot = 0.0;
 #pragma unroll
       for (int r = 0; r < RPL; ++r) {
+        if (r >= nr) break;  // slots past the last row chunk hold nothing
         int i = k + lane + 32 * r;
         a[r] = (i < ns) ? cj[i] : 0.0;
         if (i < ns) dot = fma(v[i], a[r], dot);
@@ -279,6 +287,7 @@ __global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ 
       const double w = beta * dot;
 #pragma unroll
       for (int r = 0; r < RPL; ++r) {
+        if (r >= nr) break;
         int i = k + lane + 32 * r;
         if (i < ns) {
           a[r] = fma(-w, v[i], a[r]);
@@ -292,6 +301,7 @@ __global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ 
         nrm = 0.0;
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
+          if (r >= nr) break;
           int i = k + lane + 32 * r;
           if (i > k && i < ns) nrm = fma(a[r], a[r], nrm);
         }
@@ -307,7 +317,8 @@ __global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ 
     __syncthreads();
   }
   __syncthreads();
-  id_finish(lo, hi, rank, skel, s_max, node, nl, leaf, n_samp, c, Ab, piv, s_final, Pout, ldP, P_node_stride);
+  // v (n_samp >= s entries) is free now: it holds the reciprocals of diag(R11)
+  id_finish(lo, hi, rank, skel, s_max, node, nl, leaf, n_samp, c, Ab, piv, s_final, Pout, ldP, P_node_stride, v);
 }
 
 // ---- 3b. pivoted QR of an internal node on a 16-CTA cluster -------------------
@@ -491,13 +502,15 @@ __global__ void __launch_bounds__(512) k_id_finish(const int32_t* __restrict__ l
                                                    int node0, int n_samp, int cmax, const double* __restrict__ A,
                                                    const int32_t* __restrict__ pivpos, const int32_t* __restrict__ sout,
                                                    double* __restrict__ Pout, int ldP, int64_t P_node_stride) {
-  extern __shared__ int pv[];  // cmax
+  extern __shared__ double fin_sm[];
+  double* rinv = fin_sm;            // s_max
+  int* pv = (int*)(rinv + s_max);   // cmax
   const int nl = blockIdx.x, node = node0 + nl;
   const int c = rank[2 * node] + rank[2 * node + 1];
   for (int q = threadIdx.x; q < c; q += blockDim.x) pv[q] = pivpos[(int64_t)nl * cmax + q];
   __syncthreads();
   id_finish(lo, hi, rank, skel, s_max, node, nl, false, n_samp, c, A + (int64_t)nl * cmax * n_samp, pv, sout[nl],
-            Pout, ldP, P_node_stride);
+            Pout, ldP, P_node_stride, rinv);
 }
 
 }  // namespace
@@ -548,6 +561,9 @@ kf_status kf_skel_level(kf_factor* f, int l, kf_skel_scratch* sc, cudaStream_t s
   KF_PHASE(KF_PH_SAMPLE, s, k_sample<<<nn, 32, sizeof(int32_t) * n_samp, s>>>(t->d_lo, t->d_hi, t->N, node0, nn, n_samp, f->seed, samp, nsamp,
                                                     f->status));
   dim3 ga((n_samp + 127) / 128, cmax, nn);
+  // FP64 entries on both paths: late pivots of the QR hinge on downdated norms
+  // whose relative error is far above that of the entries, so any change of
+  // the entries' rounding can change the skeletons
   KF_PHASE(KF_PH_EVAL_A, s, k_eval_A<<<ga, 128, 0, s>>>(t->X64, t->d, f->c_exp, t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf,
                               n_samp, cmax, samp, nsamp, A));
   double* Pout = leaf ? f->Pleaf : f->Pc + (int64_t)node0 * cint * s_max;
@@ -565,7 +581,7 @@ kf_status kf_skel_level(kf_factor* f, int l, kf_skel_scratch* sc, cudaStream_t s
         int32_t* so = pp + (size_t)nn * cmax;
         KF_PHASE(KF_PH_QR, s, k_qr_cluster<<<nn * kQC, 256, qsmem, s>>>(t->d_lo, t->d_hi, f->rank, s_max, node0,
                                                                        n_samp, cmax, nsamp, f->tau, A, pp, so));
-        KF_PHASE(KF_PH_QR, s, k_id_finish<<<nn, 512, sizeof(int) * cmax, s>>>(t->d_lo, t->d_hi, f->rank, f->skel,
+        KF_PHASE(KF_PH_QR, s, k_id_finish<<<nn, 512, sizeof(double) * s_max + sizeof(int) * cmax, s>>>(t->d_lo, t->d_hi, f->rank, f->skel,
                                                                             s_max, node0, n_samp, cmax, A, pp, so,
                                                                             Pout, s_max, pstride));
         cudaError_t e = cudaGetLastError();

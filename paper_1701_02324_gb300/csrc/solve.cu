@@ -245,112 +245,143 @@ void launch_rowupd(int64_t rows, int nnodes, cudaStream_t s, const int32_t* lo, 
 }
 
 // ---- reduced systems: out[l], out[r] <- Z^-1 [in[l]; in[r]] (or Z^-T) ---------------
-// Blocked by 32 rows: warp 0 solves the diagonal block with shuffles, then
-// all threads update the rest with the block (two barriers per block).
+// P Z = L U with implicit pivoting: logical row i of L and U is stored in row
+// pm[i] of ZLU, and (P b)[i] = b[pm[i]].  Blocked by 32 rows: the 32 x 32
+// diagonal block is staged in shared memory, warp 0 solves it with shuffles,
+// then all threads update the remaining rows with it.
+// acc - sum_{j < nb} a[j] x[j] (a contiguous) or a[j * lda] x[j]: fully
+// unrolled with predicated loads, so that the 32 loads are in flight together
+__device__ __forceinline__ double row_update(const double* __restrict__ a, int nb, const double* x, double acc) {
+  double v[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = j < nb ? a[j] : 0.0;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) acc = fma(-v[j], x[j], acc);
+  return acc;
+}
+
+// column i of rows rows[0..nb) of A (row stride lda)
+__device__ __forceinline__ double col_update(const double* __restrict__ A, int lda, const int* rows, int i, int nb,
+                                             const double* x, double acc) {
+  double v[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = j < nb ? A[(int64_t)rows[j] * lda + i] : 0.0;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) acc = fma(-v[j], x[j], acc);
+  return acc;
+}
+
 __global__ void __launch_bounds__(256) k_zsolve(const int32_t* __restrict__ rank, int node0, int ldz, int s_max,
                                                 const double* __restrict__ ZLU, const int32_t* __restrict__ piv,
                                                 const double* __restrict__ in, double* __restrict__ out, int k,
                                                 int transpose) {
-  extern __shared__ double t[];  // ldz
+  extern __shared__ double zsm[];
+  double* t = zsm;                   // ldz
+  double* u = t + ldz;               // ldz
+  int* pm = (int*)(u + ldz);         // ldz
+  __shared__ double db[32][33];
+  __shared__ double dinv[32];  // reciprocals of the diagonal of the staged block
   __shared__ double xb[32];
   const int nl = blockIdx.x, node = node0 + nl;
   const int l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], z = sl + sr;
   const double* A = ZLU + (int64_t)node * ldz * ldz;
   const int32_t* pv = piv + (int64_t)node * ldz;
   const int tid = threadIdx.x, lane = tid & 31;
+  for (int i = tid; i < z; i += blockDim.x) pm[i] = pv[i];
+  __syncthreads();
+  // stage the diagonal block of logical rows kb..kb+nb
+  auto stage = [&](int kb, int nb) {
+#pragma unroll
+    for (int e0 = 0; e0 < 32 * 32; e0 += 256) {
+      const int e = e0 + tid, i = e >> 5, j = e & 31;
+      if (e < 32 * 32) db[i][j] = (i < nb && j < nb) ? A[(int64_t)pm[kb + i] * ldz + kb + j] : 0.0;
+    }
+    __syncthreads();
+    // one division per lane in parallel: the solve below then multiplies (an
+    // FP64 division in its dependent chain would cost about 1000 cycles)
+    if (tid < 32) dinv[tid] = tid < nb ? 1.0 / db[tid][tid] : 0.0;
+    __syncthreads();
+  };
   for (int c = 0; c < k; ++c) {
     for (int i = tid; i < z; i += blockDim.x)
-      t[i] = i < sl ? in[((int64_t)l * s_max + i) * k + c] : in[((int64_t)r * s_max + (i - sl)) * k + c];
+      u[i] = i < sl ? in[((int64_t)l * s_max + i) * k + c] : in[((int64_t)r * s_max + (i - sl)) * k + c];
     __syncthreads();
     if (!transpose) {
-      if (tid == 0)
-        for (int i = 0; i < z; ++i)
-          if (pv[i] != i) { double a = t[i]; t[i] = t[pv[i]]; t[pv[i]] = a; }
+      for (int i = tid; i < z; i += blockDim.x) t[i] = u[pm[i]];
       __syncthreads();
       // L (unit lower)
       for (int kb = 0; kb < z; kb += 32) {
         const int nb = min(32, z - kb);
+        stage(kb, nb);
         if (tid < 32) {
           double yi = lane < nb ? t[kb + lane] : 0.0;
           for (int j = 0; j < nb; ++j) {
             double yj = __shfl_sync(0xffffffffu, yi, j);
-            if (lane > j && lane < nb) yi = fma(-A[(int64_t)(kb + lane) * ldz + kb + j], yj, yi);
+            if (lane > j && lane < nb) yi = fma(-db[lane][j], yj, yi);
           }
-          if (lane < nb) { xb[lane] = yi; t[kb + lane] = yi; }
+          if (lane < nb) { xb[lane] = yi; t[kb + lane] = yi; } else { xb[lane] = 0.0; }
         }
         __syncthreads();
-        for (int i = kb + nb + tid; i < z; i += blockDim.x) {
-          const double* Ai = A + (int64_t)i * ldz + kb;
-          double acc = t[i];
-          for (int j = 0; j < nb; ++j) acc = fma(-Ai[j], xb[j], acc);
-          t[i] = acc;
-        }
+        for (int i = kb + nb + tid; i < z; i += blockDim.x) t[i] = row_update(A + (int64_t)pm[i] * ldz + kb, nb, xb, t[i]);
         __syncthreads();
       }
       // U
       for (int kb = ((z - 1) / 32) * 32; kb >= 0 && z > 0; kb -= 32) {
         const int nb = min(32, z - kb);
+        stage(kb, nb);
         if (tid < 32) {
           double xi = lane < nb ? t[kb + lane] : 0.0;
           for (int j = nb - 1; j >= 0; --j) {
-            if (lane == j) xi = xi / A[(int64_t)(kb + j) * ldz + kb + j];
+            if (lane == j) xi *= dinv[j];
             double xj = __shfl_sync(0xffffffffu, xi, j);
-            if (lane < j) xi = fma(-A[(int64_t)(kb + lane) * ldz + kb + j], xj, xi);
+            if (lane < j) xi = fma(-db[lane][j], xj, xi);
           }
-          if (lane < nb) { xb[lane] = xi; t[kb + lane] = xi; }
+          if (lane < nb) { xb[lane] = xi; t[kb + lane] = xi; } else { xb[lane] = 0.0; }
         }
         __syncthreads();
-        for (int i = tid; i < kb; i += blockDim.x) {
-          const double* Ai = A + (int64_t)i * ldz + kb;
-          double acc = t[i];
-          for (int j = 0; j < nb; ++j) acc = fma(-Ai[j], xb[j], acc);
-          t[i] = acc;
-        }
+        for (int i = tid; i < kb; i += blockDim.x) t[i] = row_update(A + (int64_t)pm[i] * ldz + kb, nb, xb, t[i]);
         __syncthreads();
       }
     } else {
+      for (int i = tid; i < z; i += blockDim.x) t[i] = u[i];
+      __syncthreads();
       // U^T y = b (forward)
       for (int kb = 0; kb < z; kb += 32) {
         const int nb = min(32, z - kb);
+        stage(kb, nb);
         if (tid < 32) {
           double yi = lane < nb ? t[kb + lane] : 0.0;
           for (int j = 0; j < nb; ++j) {
-            if (lane == j) yi = yi / A[(int64_t)(kb + j) * ldz + kb + j];
+            if (lane == j) yi *= dinv[j];
             double yj = __shfl_sync(0xffffffffu, yi, j);
-            if (lane > j && lane < nb) yi = fma(-A[(int64_t)(kb + j) * ldz + kb + lane], yj, yi);
+            if (lane > j && lane < nb) yi = fma(-db[j][lane], yj, yi);
           }
-          if (lane < nb) { xb[lane] = yi; t[kb + lane] = yi; }
+          if (lane < nb) { xb[lane] = yi; t[kb + lane] = yi; } else { xb[lane] = 0.0; }
         }
         __syncthreads();
-        for (int i = kb + nb + tid; i < z; i += blockDim.x) {
-          double acc = t[i];
-          for (int j = 0; j < nb; ++j) acc = fma(-A[(int64_t)(kb + j) * ldz + i], xb[j], acc);
-          t[i] = acc;
-        }
+        for (int i = kb + nb + tid; i < z; i += blockDim.x) t[i] = col_update(A, ldz, pm + kb, i, nb, xb, t[i]);
         __syncthreads();
       }
       // L^T x = y (backward, unit diagonal)
       for (int kb = ((z - 1) / 32) * 32; kb >= 0 && z > 0; kb -= 32) {
         const int nb = min(32, z - kb);
+        stage(kb, nb);
         if (tid < 32) {
           double xi = lane < nb ? t[kb + lane] : 0.0;
           for (int j = nb - 1; j >= 0; --j) {
             double xj = __shfl_sync(0xffffffffu, xi, j);
-            if (lane < j) xi = fma(-A[(int64_t)(kb + j) * ldz + kb + lane], xj, xi);
+            if (lane < j) xi = fma(-db[j][lane], xj, xi);
           }
-          if (lane < nb) { xb[lane] = xi; t[kb + lane] = xi; }
+          if (lane < nb) { xb[lane] = xi; t[kb + lane] = xi; } else { xb[lane] = 0.0; }
         }
         __syncthreads();
-        for (int i = tid; i < kb; i += blockDim.x) {
-          double acc = t[i];
-          for (int j = 0; j < nb; ++j) acc = fma(-A[(int64_t)(kb + j) * ldz + i], xb[j], acc);
-          t[i] = acc;
-        }
+        for (int i = tid; i < kb; i += blockDim.x) t[i] = col_update(A, ldz, pm + kb, i, nb, xb, t[i]);
         __syncthreads();
       }
-      if (tid == 0)
-        for (int i = z - 1; i >= 0; --i)
-          if (pv[i] != i) { double a = t[i]; t[i] = t[pv[i]]; t[pv[i]] = a; }
+      // x = P w: x[pm[i]] = w[i]
+      for (int i = tid; i < z; i += blockDim.x) u[pm[i]] = t[i];
+      __syncthreads();
+      for (int i = tid; i < z; i += blockDim.x) t[i] = u[i];
       __syncthreads();
     }
     for (int i = tid; i < z; i += blockDim.x) {
@@ -451,7 +482,7 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
       dim3 gc((unsigned)((rows + kRowsPerChunk - 1) / kRowsPerChunk), nc);
       launch_colsum<TM, TV>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 1, vsrc, lvl(VT, l + 1), t->X64,
                             t->X32, t->d, f->c_exp, inv_h3, W, (int)k, U);
-      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<1 << l, 256, sizeof(double) * ldz, s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv, U, Vb,
+      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<1 << l, 256, (2 * sizeof(double) + sizeof(int)) * ldz, s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv, U, Vb,
                                                          (int)k, 0));
       launch_rowupd<TM, TV>(rows, nc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 0, SRC_STORED,
                             lvl(Phat, l + 1), t->X64, t->X32, t->d, f->c_exp, inv_h3, Vb, -1.0, W, (int)k);
@@ -464,7 +495,7 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
       dim3 gc((unsigned)((rows + kRowsPerChunk - 1) / kRowsPerChunk), nc);
       launch_colsum<TM, TV>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 0, SRC_STORED, lvl(Phat, l + 1),
                             t->X64, t->X32, t->d, f->c_exp, inv_h3, W, (int)k, U);
-      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<1 << l, 256, sizeof(double) * ldz, s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv, U, Vb,
+      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<1 << l, 256, (2 * sizeof(double) + sizeof(int)) * ldz, s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv, U, Vb,
                                                          (int)k, 1));
       launch_rowupd<TM, TV>(rows, nc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 1, vsrc, lvl(VT, l + 1),
                             t->X64, t->X32, t->d, f->c_exp, inv_h3, Vb, -1.0, W, (int)k);

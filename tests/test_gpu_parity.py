@@ -115,6 +115,43 @@ def test_factorization_with_oracle_ids(c1, prec, tol):
     assert rel(x, o.solve(b)) <= tol
 
 
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-5)])
+def test_cluster_and_single_cta_kernels_agree(c1, prec, tol):
+    """The upper levels run the pivoted QR and the reduced-system LU on CTA
+    clusters; one CTA per node everywhere must give the same skeletons and,
+    with the oracle's skeletons imported, the same solution."""
+    p, o, tree = c1
+    Fa = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=FP64)
+    Fb = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=FP64, cluster_kernels=False)
+    assert np.array_equal(Fa.ranks(), Fb.ranks())
+    for a in range(2, o.nnodes + 1):
+        assert np.array_equal(Fa.skeleton(a), Fb.skeleton(a))
+    ranks, skel, P = ids_from_oracle(o, p.s_max)
+    b = p.B[:, 0]
+    xo = o.solve(b)
+    for cl in (True, False):
+        F = kf.factorize_with_ids(tree, p.h, p.lam, p.s_max, ranks, skel, P, precision=prec, cluster_kernels=cl)
+        assert rel(F.solve(torch.from_numpy(b).cuda()).cpu().numpy(), xo) <= tol
+
+
+@pytest.mark.parametrize("h", [0.5, 2.0])
+def test_fp64_operator_matches_oracle_matvec(h):
+    """The FP64-accurate operator of the mixed path (V blocks and leaf blocks
+    in double-float arithmetic with a table-driven exponential, FP32 for the
+    entries below 2^-24) against the oracle's FP64 matvec, same skeletons.
+    h = 0.5 on [0,1]^8 puts the exponent arguments over [-16, 0]."""
+    X, _ = problem(4096, 8, seed=11)
+    o = oracle.Oracle(X, 256)
+    o.skeletonize(h, 1e-6, 64)
+    o.factorize(1.0)
+    tree = kf.Tree(torch.from_numpy(X).cuda(), 256)
+    ranks, skel, P = ids_from_oracle(o, 64)
+    F = kf.factorize_with_ids(tree, h, 1.0, 64, ranks, skel, P, precision=MIXED, fp64_operator=True)
+    x = np.random.default_rng(12).standard_normal(4096)
+    y = F.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, o.matvec(x)) <= 1e-13
+
+
 def test_matvec_transpose_and_grad_parity(c1):
     p, o, tree = c1
     ranks, skel, P = ids_from_oracle(o, p.s_max)
