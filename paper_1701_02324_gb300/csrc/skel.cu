@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ 
   extern __shared__ double sm[];
   double* norms = sm;                          // cmax
   double* v = norms + cmax;                    // n_samp
-  double* nref = v + n_samp;                   // cmax: norm at its last exact evaluation
+  double* nref = v + n_samp;                   // cmax: 1/16 of the norm at its last exact evaluation
   int* piv = (int*)(nref + cmax);              // cmax
   __shared__ double red_v[32];
   __shared__ int red_i[32];
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ 
     double acc = 0.0;
     for (int i = lane; i < ns; i += 32) acc = fma(col[i], col[i], acc);
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) { norms[j] = acc; nref[j] = acc; }
+    if (lane == 0) { norms[j] = acc; nref[j] = acc * 0.0625; }
   }
   for (int j = threadIdx.x; j < c; j += blockDim.x) piv[j] = j;
   if (threadIdx.x == 0) s_final = kmax;
@@ -272,15 +272,37 @@ __global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ 
     // downdated by the new row-k entry, and evaluated exactly again once they
     // have fallen by 16x since the last exact value (rounding stays near
     // machine precision relative to the current norm)
+    // each warp walks its columns with the next one's loads in flight
+    // (register double buffering: the loads are the long pole)
+    double an[RPL];
+    if (k + 1 + warp < c) {
+      const double* cn = Ab + (int64_t)(k + 1 + warp) * n_samp;
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        if (r >= nr) break;
+        const int i = k + lane + 32 * r;
+        an[r] = (i < ns) ? cn[i] : 0.0;
+      }
+    }
     for (int j = k + 1 + warp; j < c; j += nwarps) {
       double* cj = Ab + (int64_t)j * n_samp;
       double a[RPL];
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) a[r] = an[r];
+      if (j + nwarps < c) {
+        const double* cn = Ab + (int64_t)(j + nwarps) * n_samp;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+          if (r >= nr) break;
+          const int i = k + lane + 32 * r;
+          an[r] = (i < ns) ? cn[i] : 0.0;
+        }
+      }
       double dot = 0.0;
 #pragma unroll
       for (int r = 0; r < RPL; ++r) {
         if (r >= nr) break;  // slots past the last row chunk hold nothing
         int i = k + lane + 32 * r;
-        a[r] = (i < ns) ? cj[i] : 0.0;
         if (i < ns) dot = fma(v[i], a[r], dot);
       }
       for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
@@ -296,8 +318,10 @@ __global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ 
       }
       const double akj = __shfl_sync(0xffffffffu, a[0], 0);  // row k sits in lane 0, slot 0
       double nrm = fma(-akj, akj, norms[j]);
-      const double ref = nref[j];
-      if (!(nrm > ref * 0.0625)) {
+      // nref holds 1/16 of the last exact value; the bit patterns of a
+      // non-negative threshold and of nrm compare like the values (a negative
+      // nrm compares below), which keeps the test off the FP64 pipe
+      if (!(__double_as_longlong(nrm) > __double_as_longlong(nref[j]))) {
         nrm = 0.0;
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
@@ -306,7 +330,7 @@ __global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ 
           if (i > k && i < ns) nrm = fma(a[r], a[r], nrm);
         }
         for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
-        if (lane == 0) nref[j] = nrm;
+        if (lane == 0) nref[j] = nrm * 0.0625;
       }
       __syncwarp();
       if (lane == 0) norms[j] = nrm;
