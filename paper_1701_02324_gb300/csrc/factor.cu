@@ -67,13 +67,22 @@ __global__ void __launch_bounds__(256) k_leaf_cholesky(const int32_t* __restrict
   const int lf = blockIdx.x, node = leaf0 + lf;
   const int n = hi[node] - lo[node];
   T* L = Lall + (int64_t)lf * ldL * ldL;
+  __shared__ double dinv[NB];  // reciprocals of the factored diagonal block
+  __shared__ float red[8];
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    double mx = 0.0;
-    for (int i = 0; i < n; ++i) mx = fmax(mx, fabs((double)L[(int64_t)i * ldL + i]));
-    amax_sh = mx;
+  {  // max |diagonal| (FP32 compare; only a scale for the pivot test)
+    float mx = 0.f;
+    for (int i = tid; i < n; i += blockDim.x) mx = fmaxf(mx, fabsf((float)L[(int64_t)i * ldL + i]));
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      float m2 = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmaxf(m2, red[w]);
+      amax_sh = (double)m2;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   const double amax = amax_sh;
   bool bad = false;
   double minpiv = INFINITY;
@@ -101,6 +110,7 @@ __global__ void __launch_bounds__(256) k_leaf_cholesky(const int32_t* __restrict
         __syncwarp();
       }
     }
+    if (tid < NB) dinv[tid] = tid < nb ? 1.0 / (double)dg[tid][tid] : 0.0;  // divisions in parallel
     __syncthreads();
     for (int e = tid; e < NB * NB; e += blockDim.x) {
       int i = e / NB, j = e % NB;
@@ -117,7 +127,7 @@ __global__ void __launch_bounds__(256) k_leaf_cholesky(const int32_t* __restrict
         if (j < nb) {
           T acc = x[j];
           for (int t = 0; t < j; ++t) acc -= x[t] * dg[j][t];
-          x[j] = acc / dg[j][j];
+          x[j] = acc * (T)dinv[j];
         }
       }
 #pragma unroll
@@ -129,8 +139,9 @@ __global__ void __launch_bounds__(256) k_leaf_cholesky(const int32_t* __restrict
     const int t0 = kb + nb;
     for (int ti = t0; ti < n; ti += TS) {
       for (int tj = t0; tj <= ti; tj += TS) {
-        for (int e = tid; e < TS * NB; e += blockDim.x) {
-          int r = e / NB, cc = e % NB;
+#pragma unroll
+        for (int e0 = 0; e0 < TS * NB; e0 += 256) {  // all loads in flight together
+          const int e = e0 + tid, r = e / NB, cc = e % NB;
           pa[r][cc] = (ti + r < n && cc < nb) ? L[(int64_t)(ti + r) * ldL + kb + cc] : (T)0;
           pb[r][cc] = (tj + r < n && cc < nb) ? L[(int64_t)(tj + r) * ldL + kb + cc] : (T)0;
         }
@@ -203,13 +214,14 @@ __device__ __forceinline__ void tile_update(T (*sa)[33], T (*sb)[65], int ty, in
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_leaf_phat(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_leaf_phat(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                    const int32_t* __restrict__ rank, int leaf0, int ldL,
                                                    const T* __restrict__ Lall, const double* __restrict__ Pleaf,
                                                    int s_max, T* __restrict__ Phat) {
   constexpr int NB = 32, TS = 64;
   __shared__ T sa[TS][NB + 1];
   __shared__ T sb[NB][TS + 1];
+  __shared__ T rdg[NB];  // reciprocals of the staged diagonal block
   const int lf = blockIdx.x, node = leaf0 + lf;
   const int b = lo[node], n = hi[node] - b, s = rank[node];
   const T* L = Lall + (int64_t)lf * ldL * ldL;
@@ -230,6 +242,8 @@ __global__ void __launch_bounds__(256) k_leaf_phat(const int32_t* __restrict__ l
       sa[i][j] = (i < nb && j <= i) ? L[(int64_t)(kb + i) * ldL + kb + j] : (T)0;
     }
     __syncthreads();
+    if (tid < NB) rdg[tid] = tid < nb ? (T)1 / sa[tid][tid] : (T)0;
+    __syncthreads();
     for (int q = tid; q < s; q += blockDim.x) {
       T x[NB];
 #pragma unroll
@@ -240,7 +254,7 @@ __global__ void __launch_bounds__(256) k_leaf_phat(const int32_t* __restrict__ l
           T acc = x[i];
 #pragma unroll
           for (int t = 0; t < i; ++t) acc = fma(-sa[i][t], x[t], acc);
-          x[i] = acc / sa[i][i];
+          x[i] = acc * rdg[i];
         }
 #pragma unroll
       for (int i = 0; i < NB; ++i)
@@ -249,10 +263,11 @@ __global__ void __launch_bounds__(256) k_leaf_phat(const int32_t* __restrict__ l
     __syncthreads();
     for (int ti = kb + nb; ti < n; ti += TS)
       for (int tj = 0; tj < s; tj += TS) {
-        for (int e = tid; e < TS * NB; e += blockDim.x) {
-          int r = e / NB, cc = e % NB;
+#pragma unroll
+        for (int e0 = 0; e0 < TS * NB; e0 += 256) {  // all loads in flight together
+          const int e = e0 + tid, r = e / NB, cc = e % NB;
           sa[r][cc] = (ti + r < n && cc < nb) ? L[(int64_t)(ti + r) * ldL + kb + cc] : (T)0;
-          int rr = e / TS, c2 = e % TS;
+          const int rr = e / TS, c2 = e % TS;
           sb[rr][c2] = (rr < nb && tj + c2 < s) ? Y[(int64_t)(kb + rr) * s_max + tj + c2] : (T)0;
         }
         __syncthreads();
@@ -268,6 +283,8 @@ __global__ void __launch_bounds__(256) k_leaf_phat(const int32_t* __restrict__ l
       sa[i][j] = (i < nb && j <= i) ? L[(int64_t)(kb + i) * ldL + kb + j] : (T)0;
     }
     __syncthreads();
+    if (tid < NB) rdg[tid] = tid < nb ? (T)1 / sa[tid][tid] : (T)0;
+    __syncthreads();
     for (int q = tid; q < s; q += blockDim.x) {
       T x[NB];
 #pragma unroll
@@ -278,7 +295,7 @@ __global__ void __launch_bounds__(256) k_leaf_phat(const int32_t* __restrict__ l
           T acc = x[i];
 #pragma unroll
           for (int t = i + 1; t < NB; ++t) acc = fma(-sa[t][i], x[t], acc);
-          x[i] = acc / sa[i][i];
+          x[i] = acc * rdg[i];
         }
 #pragma unroll
       for (int i = 0; i < NB; ++i)
@@ -288,10 +305,11 @@ __global__ void __launch_bounds__(256) k_leaf_phat(const int32_t* __restrict__ l
     // rows above: y[0:kb] -= L[kb:kb+nb, 0:kb]^T x_block
     for (int ti = 0; ti < kb; ti += TS)
       for (int tj = 0; tj < s; tj += TS) {
-        for (int e = tid; e < TS * NB; e += blockDim.x) {
-          int r = e % TS, cc = e / TS;   // coalesced over r (contiguous in a row of L)
+#pragma unroll
+        for (int e0 = 0; e0 < TS * NB; e0 += 256) {  // all loads in flight together
+          const int e = e0 + tid, r = e % TS, cc = e / TS;   // coalesced over r (contiguous in a row of L)
           sa[r][cc] = (ti + r < kb && cc < nb) ? L[(int64_t)(kb + cc) * ldL + ti + r] : (T)0;
-          int rr = e / TS, c2 = e % TS;
+          const int rr = e / TS, c2 = e % TS;
           sb[rr][c2] = (rr < nb && tj + c2 < s) ? Y[(int64_t)(kb + rr) * s_max + tj + c2] : (T)0;
         }
         __syncthreads();
@@ -367,6 +385,109 @@ __global__ void __launch_bounds__(256) k_eval_vt(const double* __restrict__ X64,
         out[q] = kv;
       }
       __syncwarp();
+    }
+  }
+}
+
+// Mixed path: the same V blocks in FP32, plus (VT64 != nullptr) their FP64
+// operator copy, tiled 64 points x 64 skeleton columns per CTA with both
+// coordinate tiles (hi and lo halves) staged transposed in shared memory and
+// 4 x 4 entries per thread.  The FP32 value is exp(c |x - y|^2) of the FP32
+// coordinates (as k_eval_vt); entries at or above 2^-24 of the operator copy
+// take the double-float evaluation, which also replaces the FP32 value.
+constexpr int kVT = 64;
+__global__ void __launch_bounds__(256) k_eval_vt_tiled(const float* __restrict__ X32, const float* __restrict__ X32lo,
+                                                       int d, double c_exp, const int32_t* __restrict__ lo,
+                                                       const int32_t* __restrict__ hi,
+                                                       const int32_t* __restrict__ rank,
+                                                       const int32_t* __restrict__ skel, int s_max, int node0,
+                                                       float* __restrict__ VT, double* __restrict__ VT64, float ch,
+                                                       float cl, const float2* __restrict__ tab) {
+  extern __shared__ float vts[];  // x hi, x lo, y hi, y lo: d x 64 each
+  const int nl = blockIdx.z, node = node0 + nl, sib = node ^ 1;
+  const int b = lo[node], n = hi[node] - b, ss = rank[sib];
+  const int r0 = blockIdx.x * kVT, q0 = blockIdx.y * kVT;
+  if (r0 >= n || q0 >= ss) return;
+  const int32_t* sk = skel + (int64_t)sib * s_max;
+  float* xh = vts;
+  float* xl = xh + d * kVT;
+  float* yh = xl + d * kVT;
+  float* yl = yh + d * kVT;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const bool df = VT64 != nullptr;
+  for (int e = tid; e < d * kVT; e += blockDim.x) {
+    const int k = e % d, r = e / d;
+    const int pi = r0 + r, pq = q0 + r;
+    const int64_t xi = (int64_t)(b + min(pi, n - 1)) * d + k;
+    const int64_t yi = (int64_t)sk[min(pq, ss - 1)] * d + k;
+    xh[k * kVT + r] = X32[xi];
+    yh[k * kVT + r] = X32[yi];
+    if (df) {
+      xl[k * kVT + r] = X32lo[xi];
+      yl[k * kVT + r] = X32lo[yi];
+    }
+  }
+  __syncthreads();
+  float a32[4][4], ah[4][4], al[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) a32[a][c] = ah[a][c] = al[a][c] = 0.f;
+  if (df) {
+    for (int k = 0; k < d; ++k) {
+      const float4 x4h = *(const float4*)(xh + k * kVT + ty * 4), x4l = *(const float4*)(xl + k * kVT + ty * 4);
+      const float4 y4h = *(const float4*)(yh + k * kVT + tx * 4), y4l = *(const float4*)(yl + k * kVT + tx * 4);
+      const float xhv[4] = {x4h.x, x4h.y, x4h.z, x4h.w}, xlv[4] = {x4l.x, x4l.y, x4l.z, x4l.w};
+      const float yhv[4] = {y4h.x, y4h.y, y4h.z, y4h.w}, ylv[4] = {y4l.x, y4l.y, y4l.z, y4l.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float th, te;
+          kf_two_sum(xhv[a], -yhv[c], th, te);  // th = fl(x - y): the FP32 difference
+          a32[a][c] = fmaf(th, th, a32[a][c]);
+          const float tl = te + (xlv[a] - ylv[c]);
+          const float p = __fmul_rn(th, th);
+          const float q = fmaf(th, th, -p) + 2.f * th * tl;
+          float sh, se;
+          kf_two_sum(ah[a][c], p, sh, se);
+          se = __fadd_rn(se, __fadd_rn(al[a][c], q));
+          ah[a][c] = __fadd_rn(sh, se);
+          al[a][c] = __fsub_rn(se, __fsub_rn(ah[a][c], sh));
+        }
+    }
+  } else {
+    for (int k = 0; k < d; ++k) {
+      const float4 x4 = *(const float4*)(xh + k * kVT + ty * 4);
+      const float4 y4 = *(const float4*)(yh + k * kVT + tx * 4);
+      const float xv[4] = {x4.x, x4.y, x4.z, x4.w}, yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float t = xv[a] - yv[c];
+          a32[a][c] = fmaf(t, t, a32[a][c]);
+        }
+    }
+  }
+  const float c32 = (float)c_exp;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = r0 + ty * 4 + a;
+    if (i >= n) continue;
+    const int64_t row = (int64_t)(b + i) * s_max;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int q = q0 + tx * 4 + c;
+      if (q >= ss) continue;
+      float kv = __expf(a32[a][c] * c32);
+      if (df) {
+        double k64 = (double)kv;
+        if (kv >= 5.9604645e-8f) k64 = kf_kern_from_df(ah[a][c], al[a][c], ch, cl, tab);
+        VT64[row + q] = k64;
+        kv = (float)k64;
+      }
+      VT[row + q] = kv;
     }
   }
 }
@@ -879,21 +1000,83 @@ __global__ void __launch_bounds__(256) k_telescope(const int32_t* __restrict__ l
 }
 
 // FP64 copy of the leaf kernel blocks (no lambda), both triangles, for the
-// FP64-accurate operator.
-__global__ void k_leaf_k64(const float* __restrict__ X32lo, const float* __restrict__ X32, int d, double c_exp,
-                           const int32_t* __restrict__ lo, const int32_t* __restrict__ hi, int leaf0, int ldL,
-                           double* __restrict__ K64, float ch, float cl, const float2* __restrict__ tab) {
-  const int lf = blockIdx.z, node = leaf0 + lf;
+// FP64-accurate operator.  One CTA per 64 x 64 tile (I, J) of a leaf block
+// with I <= J, written to (I, J) and, transposed, to (J, I); the tile's
+// coordinates (double-float, hi + lo) are staged in shared memory, transposed
+// so that a thread's 4 rows and 4 columns are 4 consecutive words.  Entries
+// below 2^-24 take the FP32 value exp(c d_hi), the rest kf_kern_from_df.
+constexpr int kK64T = 64;
+__global__ void __launch_bounds__(256) k_leaf_k64(const float* __restrict__ X32lo, const float* __restrict__ X32,
+                                                  int d, double c_exp, const int32_t* __restrict__ lo,
+                                                  const int32_t* __restrict__ hi, int leaf0, int ldL,
+                                                  double* __restrict__ K64, float ch, float cl,
+                                                  const float2* __restrict__ tab) {
+  extern __shared__ float k64s[];  // 4 arrays of d x 64: x hi, x lo, y hi, y lo
+  const int lf = blockIdx.y, node = leaf0 + lf;
   const int b = lo[node], n = hi[node] - b;
-  const int i = blockIdx.y;
-  if (i >= n) return;
-  double* Ki = K64 + ((int64_t)lf * ldL + i) * ldL;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-    Ki[j] = kf_kern_hybrid(X32, X32lo, b + i, b + j, d, c_exp, ch, cl, tab);
+  const int nt = (n + kK64T - 1) / kK64T;
+  // tile index -> (I, J), I <= J, row by row of the upper triangle
+  int t = blockIdx.x, I = 0;
+  while (I < nt && t >= nt - I) { t -= nt - I; ++I; }
+  if (I >= nt) return;
+  const int J = I + t;
+  float* xh = k64s;
+  float* xl = xh + d * kK64T;
+  float* yh = xl + d * kK64T;
+  float* yl = yh + d * kK64T;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int e = tid; e < d * kK64T; e += blockDim.x) {
+    const int k = e % d, r = e / d;  // coalesced over (point, dim)
+    const int pi = I * kK64T + r, pj = J * kK64T + r;
+    xh[k * kK64T + r] = pi < n ? X32[(int64_t)(b + pi) * d + k] : 0.f;
+    xl[k * kK64T + r] = pi < n ? X32lo[(int64_t)(b + pi) * d + k] : 0.f;
+    yh[k * kK64T + r] = pj < n ? X32[(int64_t)(b + pj) * d + k] : 0.f;
+    yl[k * kK64T + r] = pj < n ? X32lo[(int64_t)(b + pj) * d + k] : 0.f;
+  }
+  __syncthreads();
+  float ah[4][4], al[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) ah[a][c] = al[a][c] = 0.f;
+  for (int k = 0; k < d; ++k) {
+    const float4 x4h = *(const float4*)(xh + k * kK64T + ty * 4), x4l = *(const float4*)(xl + k * kK64T + ty * 4);
+    const float4 y4h = *(const float4*)(yh + k * kK64T + tx * 4), y4l = *(const float4*)(yl + k * kK64T + tx * 4);
+    const float xhv[4] = {x4h.x, x4h.y, x4h.z, x4h.w}, xlv[4] = {x4l.x, x4l.y, x4l.z, x4l.w};
+    const float yhv[4] = {y4h.x, y4h.y, y4h.z, y4h.w}, ylv[4] = {y4l.x, y4l.y, y4l.z, y4l.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float th, te;
+        kf_two_sum(xhv[a], -yhv[c], th, te);
+        const float tl = te + (xlv[a] - ylv[c]);
+        const float p = __fmul_rn(th, th);
+        const float q = fmaf(th, th, -p) + 2.f * th * tl;
+        float sh, se;
+        kf_two_sum(ah[a][c], p, sh, se);
+        se = __fadd_rn(se, __fadd_rn(al[a][c], q));
+        ah[a][c] = __fadd_rn(sh, se);
+        al[a][c] = __fsub_rn(se, __fsub_rn(ah[a][c], sh));
+      }
+  }
+  const float c32 = (float)c_exp;
+  double* Kb = K64 + (int64_t)lf * ldL * ldL;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = I * kK64T + ty * 4 + a, j = J * kK64T + tx * 4 + c;
+      if (i >= n || j >= n) continue;
+      const float k32 = __expf(ah[a][c] * c32);
+      const double kv = k32 < 5.9604645e-8f ? (double)k32 : kf_kern_from_df(ah[a][c], al[a][c], ch, cl, tab);
+      Kb[(int64_t)i * ldL + j] = kv;
+      if (I != J) Kb[(int64_t)j * ldL + i] = kv;
+    }
 }
 
 template <typename T>
-kf_status leaves_t(kf_factor* f, cudaStream_t s) {
+kf_status leaves_t(kf_factor* f, cudaStream_t s, bool with_k64) {
   kf_tree* t = f->t;
   kf_ctx* c = f->ctx;
   const int D = t->D, s_max = f->s_max;
@@ -904,9 +1087,10 @@ kf_status leaves_t(kf_factor* f, cudaStream_t s) {
   const int leaf0 = 1 << D, nleaf = 1 << D;
   dim3 g((ldL + 127) / 128, ldL, nleaf);
   KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_assemble<T><<<g, 128, 0, s>>>(t->X64, t->X32, t->d, f->c_exp, f->lambda, t->d_lo, t->d_hi, leaf0, ldL, L));
-  if (f->K64)
-    KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_k64<<<g, 128, 0, s>>>(t->X32lo, t->X32, t->d, f->c_exp, t->d_lo, t->d_hi, leaf0, ldL, f->K64,
-                                                          f->c_exp_hi, f->c_exp_lo, t->exp_tab));
+  if (f->K64 && with_k64) {
+    kf_status r = kf_leaf_k64_launch(f, s);
+    if (r != KF_OK) return r;
+  }
   KF_PHASE(KF_PH_LEAF_CHOL, s, k_leaf_cholesky<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, ldL, L, f->status, f->pivr));
   if (D > 0)
     KF_PHASE(KF_PH_LEAF_PHAT, s, k_leaf_phat<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, leaf0, ldL, L, f->Pleaf, s_max,
@@ -935,12 +1119,24 @@ kf_status level_eval_v(kf_factor* f, int l, cudaStream_t s) {
   const int64_t per = (int64_t)sizeof(T) + (f->VT64 ? (int64_t)sizeof(float) : 0);  // bytes per staged coordinate
   const int qchunk = (int)std::max<int64_t>(1, std::min<int64_t>(s_max, (96 * 1024 / per - 8 * t->d) / t->d));
   const size_t vt_smem = (size_t)per * ((size_t)t->d * qchunk + 8 * t->d);
-  KF_CUDA(c, cudaFuncSetAttribute(k_eval_vt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vt_smem));
-  KF_PHASE(KF_PH_EVAL_V, s, k_eval_vt<T><<<gv, 256, vt_smem, s>>>(t->X64, t->X32, t->X32lo, t->d, f->c_exp, t->d_lo, t->d_hi,
-                                                                 f->rank, f->skel, s_max, child0, vt_rows, qchunk,
-                                                                 lvl(VT, l + 1),
-                                                                 f->VT64 ? f->VT64 + (int64_t)l * N * s_max : nullptr,
-                                                                 f->c_exp_hi, f->c_exp_lo, t->exp_tab));
+  if (sizeof(T) == 4) {  // mixed path: register-tiled FP32 (+ double-float) evaluation
+    const size_t ts = sizeof(float) * 4 * (size_t)t->d * kVT;
+    KF_CUDA(c, cudaFuncSetAttribute(k_eval_vt_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts));
+    const int64_t rows = (N >> (l + 1)) + 1;
+    dim3 gt((unsigned)((rows + kVT - 1) / kVT), (unsigned)((s_max + kVT - 1) / kVT), 2 * nn);
+    KF_PHASE(KF_PH_EVAL_V, s, k_eval_vt_tiled<<<gt, 256, ts, s>>>(t->X32, t->X32lo, t->d, f->c_exp, t->d_lo, t->d_hi,
+                                                                f->rank, f->skel, s_max, child0,
+                                                                (float*)lvl(VT, l + 1),
+                                                                f->VT64 ? f->VT64 + (int64_t)l * N * s_max : nullptr,
+                                                                f->c_exp_hi, f->c_exp_lo, t->exp_tab));
+  } else {
+    KF_CUDA(c, cudaFuncSetAttribute(k_eval_vt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vt_smem));
+    KF_PHASE(KF_PH_EVAL_V, s, k_eval_vt<T><<<gv, 256, vt_smem, s>>>(t->X64, t->X32, t->X32lo, t->d, f->c_exp, t->d_lo, t->d_hi,
+                                                                   f->rank, f->skel, s_max, child0, vt_rows, qchunk,
+                                                                   lvl(VT, l + 1),
+                                                                   f->VT64 ? f->VT64 + (int64_t)l * N * s_max : nullptr,
+                                                                   f->c_exp_hi, f->c_exp_lo, t->exp_tab));
+  }
   KF_LAUNCH_CHECK(c);
   return KF_OK;
 }
@@ -1022,8 +1218,21 @@ size_t kf_factor_tm_elems(const kf_factor* f) {
   return D > 0 ? (size_t)(1 << (D - 1)) * 2 * f->s_max * f->s_max : 1;
 }
 
-kf_status kf_factorize_leaves(kf_factor* f, cudaStream_t s) {
-  return f->prec == KF_PREC_FP64 ? leaves_t<double>(f, s) : leaves_t<float>(f, s);
+kf_status kf_leaf_k64_launch(kf_factor* f, cudaStream_t s) {
+  kf_tree* t = f->t;
+  const int nt = (t->leaf_max + kK64T - 1) / kK64T;
+  const size_t smem = sizeof(float) * 4 * (size_t)t->d * kK64T;
+  KF_CUDA(f->ctx, cudaFuncSetAttribute(k_leaf_k64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 g((unsigned)(nt * (nt + 1) / 2), 1u << t->D);
+  KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_k64<<<g, 256, smem, s>>>(t->X32lo, t->X32, t->d, f->c_exp, t->d_lo, t->d_hi,
+                                                              1 << t->D, t->leaf_max, f->K64, f->c_exp_hi,
+                                                              f->c_exp_lo, t->exp_tab));
+  KF_LAUNCH_CHECK(f->ctx);
+  return KF_OK;
+}
+
+kf_status kf_factorize_leaves(kf_factor* f, cudaStream_t s, bool with_k64) {
+  return f->prec == KF_PREC_FP64 ? leaves_t<double>(f, s, with_k64) : leaves_t<float>(f, s, with_k64);
 }
 
 kf_status kf_factorize_level_v(kf_factor* f, int l, cudaStream_t s) {
@@ -1041,7 +1250,7 @@ kf_status kf_factorize_level(kf_factor* f, int l, double* Tm, cudaStream_t s) {
 
 kf_status kf_factorize_device(kf_factor* f, cudaStream_t s) {
   kf_ctx* c = f->ctx;
-  kf_status st = kf_factorize_leaves(f, s);
+  kf_status st = kf_factorize_leaves(f, s, true);
   if (st != KF_OK || f->t->D == 0) return st;
   const size_t tb = sizeof(double) * kf_factor_tm_elems(f);
   double* Tm = (double*)c->dalloc(tb, s);
@@ -1086,6 +1295,8 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
     cudaStreamWaitEvent(s1, ev[0], 0);
     cudaStreamWaitEvent(s2, ev[0], 0);
     cudaStreamWaitEvent(s3, ev[0], 0);
+    // the FP64 operator's leaf blocks need the tree only
+    if (f->K64) st = kf_leaf_k64_launch(f, s3);
     for (int l = D; l >= 1 && st == KF_OK; --l) {
       st = kf_skel_level(f, l, &sc, s1);
       cudaEventRecord(ev[l], s1);
@@ -1097,7 +1308,7 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
       if (st != KF_OK) break;
       cudaStreamWaitEvent(s2, ev[l], 0);
       if (l == D) {
-        st = kf_factorize_leaves(f, s2);
+        st = kf_factorize_leaves(f, s2, false);
       } else {
         cudaStreamWaitEvent(s2, evv[l], 0);
         st = kf_factorize_level_z(f, l, Tm, s2);

@@ -184,8 +184,11 @@ __global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ 
   double* nref = v + n_samp;                   // cmax: 1/16 of the norm at its last exact evaluation
   int* piv = (int*)(nref + cmax);              // cmax
   __shared__ double red_v[32];
+  __shared__ long long red_k[32];
   __shared__ int red_i[32];
-  __shared__ int s_final;
+  __shared__ int s_final, step_p;
+  __shared__ double step_rkk, step_beta;
+  __shared__ bool step_stop;
   const int nl = blockIdx.x, node = node0 + nl;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int c = id_ncols(node, leaf, lo, hi, rank);
@@ -205,34 +208,38 @@ __global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ 
   __syncthreads();
   double r00 = 0.0;
   for (int k = 0; k < kmax; ++k) {
-    // pivot: largest trailing norm, ties to the lowest column
-    double bv = -1.0;
+    // pivot: largest trailing norm, ties to the lowest column.  The keys are
+    // the norms' bit patterns (non-negative doubles order like their bits;
+    // a negative rounding residue counts as 0), compared on the integer
+    // pipes; the scalar FP64 work of the step runs in one thread
+    long long bv = -1;
     int bi = c;
-    for (int j = k + threadIdx.x; j < c; j += blockDim.x)
-      if (norms[j] > bv) { bv = norms[j]; bi = j; }
+    for (int j = k + threadIdx.x; j < c; j += blockDim.x) {
+      const long long key = max(__double_as_longlong(norms[j]), 0ll);
+      if (key > bv) { bv = key; bi = j; }
+    }
     for (int off = 16; off > 0; off >>= 1) {
-      double ov = __shfl_xor_sync(0xffffffffu, bv, off);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      const long long ov = __shfl_xor_sync(0xffffffffu, bv, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
       if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
     }
-    if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
+    if (lane == 0) { red_k[warp] = bv; red_i[warp] = bi; }
     __syncthreads();
-    if (warp == 0) {
-      bv = lane < nwarps ? red_v[lane] : -1.0;
-      bi = lane < nwarps ? red_i[lane] : c;
-      for (int off = 16; off > 0; off >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, bv, off);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-      }
-      if (lane == 0) { red_v[0] = bv; red_i[0] = bi; }
+    if (threadIdx.x == 0) {
+      long long b2 = -1;
+      int i2 = c;
+      for (int w = 0; w < nwarps; ++w)
+        if (red_k[w] > b2 || (red_k[w] == b2 && red_i[w] < i2)) { b2 = red_k[w]; i2 = red_i[w]; }
+      const double rkk = sqrt(__longlong_as_double(b2));
+      if (k == 0) r00 = rkk;
+      step_p = i2;
+      step_rkk = rkk;
+      step_stop = (k == 0) ? (r00 == 0.0) : (rkk < tau * r00);
     }
     __syncthreads();
-    const int p = red_i[0];
-    const double rkk = sqrt(red_v[0]);
-    if (k == 0) r00 = rkk;
-    bool stop = (k == 0) ? (r00 == 0.0) : (rkk < tau * r00);
-    __syncthreads();
+    const int p = step_p;
+    const double rkk = step_rkk;
+    const bool stop = step_stop;
     if (stop) {
       if (threadIdx.x == 0) s_final = k;
       break;
@@ -264,9 +271,13 @@ __global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ 
     __syncthreads();
     if (lane == 0) red_v[warp] = part;
     __syncthreads();
-    double vtv = 0.0;
-    for (int w = 0; w < nwarps; ++w) vtv += red_v[w];
-    const double beta = vtv > 0.0 ? 2.0 / vtv : 0.0;
+    if (threadIdx.x == 0) {
+      double vtv = 0.0;
+      for (int w = 0; w < nwarps; ++w) vtv += red_v[w];
+      step_beta = vtv > 0.0 ? 2.0 / vtv : 0.0;
+    }
+    __syncthreads();
+    const double beta = step_beta;
     const int nr = (ns - k + 31) >> 5;  // 32-row chunks of rows k..ns-1
     // apply H to the trailing columns; their squared norms over rows > k are
     // downdated by the new row-k entry, and evaluated exactly again once they

@@ -157,25 +157,38 @@ __device__ __forceinline__ void stage_chunk(const Problem& prob, const Tile& t, 
                                             float* Bhi, float* Blo) {
   const int tid = threadIdx.x;
   const int kn = min(kBK, t.k1 - kc);
-#pragma unroll 4
-  for (int e = tid; e < kBM * kBK; e += kThreads) {
+  // all global loads of the chunk first (in flight together), then the split
+  constexpr int NA = kBM * kBK / kThreads, NB = BN * kBK / kThreads;
+  float va[NA], vb[NB];
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
     int m, k;
-    tile_coord<Problem::a_m_fastest>(e, kBM, m, k);
-    const float a = (m < t.M - t.m0 && k < kn) ? prob.loadA(t, t.m0 + m, kc + k) : 0.f;
-    const float hi = to_tf32(a);
+    tile_coord<Problem::a_m_fastest>(tid + q * kThreads, kBM, m, k);
+    va[q] = (m < t.M - t.m0 && k < kn) ? prob.loadA(t, t.m0 + m, kc + k) : 0.f;
+  }
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    int n, k;
+    tile_coord<Problem::b_n_fastest>(tid + q * kThreads, BN, n, k);
+    vb[q] = (n < t.N - t.n0 && k < kn) ? prob.loadB(t, kc + k, t.n0 + n) : 0.f;
+  }
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    int m, k;
+    tile_coord<Problem::a_m_fastest>(tid + q * kThreads, kBM, m, k);
+    const float hi = to_tf32(va[q]);
     const int o = core_off(m, k);
     Ahi[o] = hi;
-    Alo[o] = to_tf32(a - hi);
+    Alo[o] = to_tf32(va[q] - hi);
   }
-#pragma unroll 4
-  for (int e = tid; e < BN * kBK; e += kThreads) {
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
     int n, k;
-    tile_coord<Problem::b_n_fastest>(e, BN, n, k);
-    const float b = (n < t.N - t.n0 && k < kn) ? prob.loadB(t, kc + k, t.n0 + n) : 0.f;
-    const float hi = to_tf32(b);
+    tile_coord<Problem::b_n_fastest>(tid + q * kThreads, BN, n, k);
+    const float hi = to_tf32(vb[q]);
     const int o = core_off(n, k);
     Bhi[o] = hi;
-    Blo[o] = to_tf32(b - hi);
+    Blo[o] = to_tf32(vb[q] - hi);
   }
 }
 
@@ -247,21 +260,25 @@ __global__ void __launch_bounds__(kThreads) k_tc_gemm(Problem prob, int32_t* __r
   fence_after_sync();
   __syncthreads();
   if (ok) {
-    // warp w reads TMEM lane quadrant w % 4; the four warps of a quadrant
-    // split the accumulator columns
+    // accumulator -> shared memory (the operand stages are idle now), then
+    // stored row by row so that a warp's stores are contiguous.  Warp w reads
+    // TMEM lane quadrant w % 4 (rows 32(w % 4) + lane); the four warps of a
+    // quadrant split the columns.  Row stride BN + 1 words: conflict-free.
+    float* Cs = (float*)smem_raw;
     const int quad = warp & 3, part = warp >> 2, nparts = kThreads / 128;
 #pragma unroll 1
     for (int c0 = part * 32; c0 < BN; c0 += 32 * nparts) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
-      const int m = t.m0 + quad * 32 + lane;
-      if (m < t.M) {
+      float* row = Cs + (size_t)(quad * 32 + lane) * (BN + 1) + c0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int n = t.n0 + c0 + j;
-          if (n < t.N) prob.store(t, m, n, v[j]);
-        }
-      }
+      for (int j = 0; j < 32; ++j) row[j] = v[j];
+    }
+    __syncthreads();
+    const int nrow = min(kBM, t.M - t.m0), ncol = min(BN, t.N - t.n0);
+    for (int r = warp; r < nrow; r += kThreads / 32) {
+      const float* row = Cs + (size_t)r * (BN + 1);
+      for (int cidx = lane; cidx < ncol; cidx += 32) prob.store(t, t.m0 + r, t.n0 + cidx, row[cidx]);
     }
   }
   fence_before_sync();

@@ -134,20 +134,21 @@ def test_cluster_and_single_cta_kernels_agree(c1, prec, tol):
         assert rel(F.solve(torch.from_numpy(b).cuda()).cpu().numpy(), xo) <= tol
 
 
-@pytest.mark.parametrize("h", [0.5, 2.0])
-def test_fp64_operator_matches_oracle_matvec(h):
+@pytest.mark.parametrize("h,N,m", [(0.5, 4096, 256), (2.0, 4096, 256), (0.5, 5000, 300)])
+def test_fp64_operator_matches_oracle_matvec(h, N, m):
     """The FP64-accurate operator of the mixed path (V blocks and leaf blocks
     in double-float arithmetic with a table-driven exponential, FP32 for the
     entries below 2^-24) against the oracle's FP64 matvec, same skeletons.
-    h = 0.5 on [0,1]^8 puts the exponent arguments over [-16, 0]."""
-    X, _ = problem(4096, 8, seed=11)
-    o = oracle.Oracle(X, 256)
+    h = 0.5 on [0,1]^8 puts the exponent arguments over [-16, 0]; N = 5000
+    gives ragged leaves (312 and 313 points: a partial 64 x 64 tile)."""
+    X, _ = problem(N, 8, seed=11)
+    o = oracle.Oracle(X, m)
     o.skeletonize(h, 1e-6, 64)
     o.factorize(1.0)
-    tree = kf.Tree(torch.from_numpy(X).cuda(), 256)
+    tree = kf.Tree(torch.from_numpy(X).cuda(), m)
     ranks, skel, P = ids_from_oracle(o, 64)
     F = kf.factorize_with_ids(tree, h, 1.0, 64, ranks, skel, P, precision=MIXED, fp64_operator=True)
-    x = np.random.default_rng(12).standard_normal(4096)
+    x = np.random.default_rng(12).standard_normal(N)
     y = F.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
     assert rel(y, o.matvec(x)) <= 1e-13
 
