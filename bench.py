@@ -35,6 +35,12 @@ sys.path.insert(0, ROOT)
 METRIC = "factorize sec & solve RHS/s at N=1M, rel err≤1e-5; mixed vs FP64 GPU path"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 1.25          # recipe's nominal FP64 rate (152 SMs, 2.07 GHz)
+# DRAM bytes (read + write) of the leaf-level k_pivoted_qr launch at N = 2^20,
+# from the ncu capture summarised in profiles/k_pivoted_qr_leaf_level_N131072.md
+# (leaf level at N = 2^17, 128 leaves, scaled by the 8x leaf count); None while
+# the kernel differs from the captured one.
+QR_TRAFFIC_PER_LAUNCH = 1.40e12
+QR_TRAFFIC_SRC = "profiles/k_pivoted_qr_leaf_level_N131072.md"
 ORACLE_SAMPLE_N = 8192           # points per oracle sample step
 
 
@@ -398,16 +404,22 @@ def gpu_main(args, rank, world):
     D, lo, hi = tree_ranges(p.N, p.m)
     phase_ms = {n: float(ms_ph[i]) for i, n in enumerate(_abi.PHASES)}
     phase_launches = {n: int(ln_ph[i]) for i, n in enumerate(_abi.PHASES)}
-    dominant = max(phase_ms, key=phase_ms.get)
+    qr_total = phase_ms["qr"] + phase_ms["qr_leaf"] + phase_ms["qr_cluster"]
+    dominant = "qr" if qr_total >= max(phase_ms.values()) else max(phase_ms, key=phase_ms.get)
     roof = None
-    if dominant == "qr" and phase_launches["qr"] > 0:
-        flops = sum(level_qr_flops(None, ranks, p.N, D, 2 * p.s_max, p.s_max, lo, hi).values()) * args.steps
-        avg_ms = phase_ms["qr"] / phase_launches["qr"]
-        per_launch = flops / phase_launches["qr"]
+    if dominant in ("qr", "qr_leaf") and phase_launches["qr_leaf"] > 0:
+        # the leaf level's k_pivoted_qr launch (one CTA per leaf), the largest
+        # single launch of the step; the other levels are phases qr and qr_cluster
+        per_level = level_qr_flops(None, ranks, p.N, D, 2 * p.s_max, p.s_max, lo, hi)
+        flops = per_level[D] * args.steps
+        avg_ms = phase_ms["qr_leaf"] / phase_launches["qr_leaf"]
+        per_launch = flops / phase_launches["qr_leaf"]
         achieved = per_launch / (avg_ms * 1e-3) / 1e12
-        roof = {"kernel": "k_pivoted_qr (FP64 ID)", "bound": "alu", "achieved": round(achieved, 4),
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-                "traffic": None, "peak_src": "recipe nominal FP64 rate (1.25 TFLOP/s; 1.20 measured by an FMA loop)",
+        roof = {"kernel": "k_pivoted_qr, leaf level (FP64 ID, one CTA per leaf)", "bound": "alu",
+                "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                "traffic": QR_TRAFFIC_PER_LAUNCH, "traffic_src": QR_TRAFFIC_SRC,
+                "peak_src": "recipe nominal FP64 rate (1.25 TFLOP/s; 1.20 measured by an FMA loop)",
                 "work_per_launch": per_launch, "avg_launch_ms": avg_ms}
     else:
         sb = solve_bytes(p.N, D, ranks, lo, hi, 4) * args.steps

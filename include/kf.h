@@ -249,8 +249,11 @@ kf_status kf_profile_enable(int32_t on);
  * KF_PHASE_COUNT.  Synchronizes the recorded events.  Phases, in order: tree,
  * sample, eval_A, qr, leaf_assemble, leaf_cholesky, leaf_phat, eval_V, zoff,
  * z_lu, z_solve_pc, telescope, solve_leaf, solve_colsum, solve_zsolve,
- * solve_rowupd, matvec_leaf, matvec_push, misc. */
-#define KF_PHASE_COUNT 19
+ * solve_rowupd, matvec_leaf, matvec_push, misc, qr_cluster (the pivoted QR of
+ * the upper levels on thread-block clusters and its R11^-1 R12 step), qr_leaf
+ * (the pivoted QR of the leaf level; "qr" holds the other one-CTA-per-node
+ * levels). */
+#define KF_PHASE_COUNT 21
 kf_status kf_profile_read(double* ms, int64_t* launches, int32_t nphase);
 
 #ifdef __cplusplus

@@ -28,6 +28,8 @@ enum kf_phase {
   KF_PH_MV_LEAF,
   KF_PH_MV_PUSH,
   KF_PH_MISC,
+  KF_PH_QR_CLUSTER,
+  KF_PH_QR_LEAF,
   KF_PH_COUNT
 };
 

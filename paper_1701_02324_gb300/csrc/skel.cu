@@ -614,9 +614,9 @@ kf_status kf_skel_level(kf_factor* f, int l, kf_skel_scratch* sc, cudaStream_t s
         // positions and ranks from the tail of the A scratch
         int32_t* pp = (int32_t*)(A + (size_t)nn * cmax * n_samp);
         int32_t* so = pp + (size_t)nn * cmax;
-        KF_PHASE(KF_PH_QR, s, k_qr_cluster<<<nn * kQC, 256, qsmem, s>>>(t->d_lo, t->d_hi, f->rank, s_max, node0,
+        KF_PHASE(KF_PH_QR_CLUSTER, s, k_qr_cluster<<<nn * kQC, 256, qsmem, s>>>(t->d_lo, t->d_hi, f->rank, s_max, node0,
                                                                        n_samp, cmax, nsamp, f->tau, A, pp, so));
-        KF_PHASE(KF_PH_QR, s, k_id_finish<<<nn, 512, sizeof(double) * s_max + sizeof(int) * cmax, s>>>(t->d_lo, t->d_hi, f->rank, f->skel,
+        KF_PHASE(KF_PH_QR_CLUSTER, s, k_id_finish<<<nn, 512, sizeof(double) * s_max + sizeof(int) * cmax, s>>>(t->d_lo, t->d_hi, f->rank, f->skel,
                                                                             s_max, node0, n_samp, cmax, A, pp, so,
                                                                             Pout, s_max, pstride));
         cudaError_t e = cudaGetLastError();
@@ -628,13 +628,13 @@ kf_status kf_skel_level(kf_factor* f, int l, kf_skel_scratch* sc, cudaStream_t s
   }
   size_t smem = sizeof(double) * (2 * cmax + n_samp) + sizeof(int) * cmax;
   if (rpl <= 8)
-    KF_PHASE(KF_PH_QR, s, k_pivoted_qr<8><<<nn, 512, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf, n_samp, cmax,
+    KF_PHASE(leaf ? KF_PH_QR_LEAF : KF_PH_QR, s, k_pivoted_qr<8><<<nn, 512, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf, n_samp, cmax,
                                           nsamp, f->tau, A, Pout, s_max, pstride));
   else if (rpl <= 16)
-    KF_PHASE(KF_PH_QR, s, k_pivoted_qr<16><<<nn, 512, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf, n_samp, cmax,
+    KF_PHASE(leaf ? KF_PH_QR_LEAF : KF_PH_QR, s, k_pivoted_qr<16><<<nn, 512, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf, n_samp, cmax,
                                            nsamp, f->tau, A, Pout, s_max, pstride));
   else
-    KF_PHASE(KF_PH_QR, s, k_pivoted_qr<32><<<nn, 512, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf, n_samp, cmax,
+    KF_PHASE(leaf ? KF_PH_QR_LEAF : KF_PH_QR, s, k_pivoted_qr<32><<<nn, 512, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf, n_samp, cmax,
                                            nsamp, f->tau, A, Pout, s_max, pstride));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return kf_set_err(c, KF_ECUDA, "skeletonize level %d: %s", l, cudaGetErrorString(e));
