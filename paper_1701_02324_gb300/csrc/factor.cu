@@ -22,7 +22,7 @@ kf_status kf_tc_zoff(const int32_t* lo, const int32_t* hi, const int32_t* rank, 
                      const float* VT, const float* Ph, int ldz, double* Z, int64_t rows_per_child, int32_t* status,
                      cudaStream_t s);
 kf_status kf_tc_telescope(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
-                          const float* Pc_hat, const double* Tm, int ldz, float* Pa_hat, int64_t rows_per_child,
+                          const float* Pc_hat, const float* Tm, int ldz, float* Pa_hat, int64_t rows_per_child,
                           int32_t* status, cudaStream_t s);
 
 namespace {
@@ -787,8 +787,27 @@ __device__ void zlu_update(double* A, int ldz, int z, int kb, int nb, int part, 
 
 // X[:, q0:q1) = Z^-1 B[:, q0:q1) from the LU in A (columns >= s are zero)
 template <int TC, bool L2>
-__device__ void z_solve_cols(const double* A, int ldz, int z, const double* B, double* X, int s_max, int s, int q0,
-                             int q1, ZShared& sh) {
+__device__ void z_solve_cols_impl(const double* A, int ldz, int z, const double* B, double* X, int s_max, int s,
+                                  int q0, int q1, ZShared& sh);
+
+// ... and, when X32 is given, an FP32 copy of the same columns (the mixed
+// path's telescoping reads T in FP32)
+template <int TC, bool L2>
+__device__ void z_solve_cols(const double* A, int ldz, int z, const double* B, double* X, float* X32, int s_max,
+                             int s, int q0, int q1, ZShared& sh) {
+  z_solve_cols_impl<TC, L2>(A, ldz, z, B, X, s_max, s, q0, q1, sh);
+  if (X32 == nullptr) return;
+  __syncthreads();
+  const int qw = q1 - q0;
+  for (int64_t e = threadIdx.x; e < (int64_t)ldz * qw; e += blockDim.x) {
+    const int64_t o = (e / qw) * s_max + q0 + e % qw;
+    X32[o] = (float)X[o];
+  }
+}
+
+template <int TC, bool L2>
+__device__ void z_solve_cols_impl(const double* A, int ldz, int z, const double* B, double* X, int s_max, int s,
+                                  int q0, int q1, ZShared& sh) {
   const int tid = threadIdx.x;
   const int qw = q1 - q0;
   const int* rm = sh.rm;
@@ -867,7 +886,8 @@ __device__ void z_solve_cols(const double* A, int ldz, int z, const double* B, d
 __global__ void __launch_bounds__(256) k_z_factor(const int32_t* __restrict__ rank, int node0, int ldz, int s_max,
                                                   double* __restrict__ Z, int32_t* __restrict__ piv,
                                                   const double* __restrict__ Pc, double* __restrict__ T,
-                                                  int solve_pc, int32_t* __restrict__ status, double* __restrict__ pivr) {
+                                                  float* __restrict__ T32, int solve_pc, int32_t* __restrict__ status,
+                                                  double* __restrict__ pivr) {
   __shared__ ZShared sh;
   const int nl = blockIdx.x, node = node0 + nl;
   const int z = rank[2 * node] + rank[2 * node + 1];
@@ -888,16 +908,17 @@ __global__ void __launch_bounds__(256) k_z_factor(const int32_t* __restrict__ ra
   if (bad && threadIdx.x == 0) atomicOr(status, KF_DEV_ILLCOND);
   if (threadIdx.x == 0) pivr[node] = (z == 0 || umax == 0.0) ? 1.0 : umin / umax;
   if (!solve_pc) return;
-  z_solve_cols<kZTS, false>(A, ldz, z, Pc + (int64_t)node * ldz * s_max, T + (int64_t)nl * ldz * s_max, s_max,
-                            rank[node], 0, s_max, sh);
+  z_solve_cols<kZTS, false>(A, ldz, z, Pc + (int64_t)node * ldz * s_max, T + (int64_t)nl * ldz * s_max,
+                            T32 ? T32 + (int64_t)nl * ldz * s_max : nullptr, s_max, rank[node], 0, s_max, sh);
 }
 
 // cluster size is set at launch (cudaLaunchAttributeClusterDimension)
 __global__ void __launch_bounds__(256) k_z_factor_cluster(const int32_t* __restrict__ rank, int node0, int ldz,
                                                           int s_max, double* __restrict__ Z,
                                                           int32_t* __restrict__ piv, const double* __restrict__ Pc,
-                                                          double* __restrict__ T, int solve_pc,
-                                                          int32_t* __restrict__ status, double* __restrict__ pivr) {
+                                                          double* __restrict__ T, float* __restrict__ T32,
+                                                          int solve_pc, int32_t* __restrict__ status,
+                                                          double* __restrict__ pivr) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   __shared__ ZShared sh;
@@ -936,8 +957,8 @@ __global__ void __launch_bounds__(256) k_z_factor_cluster(const int32_t* __restr
   if (!solve_pc) return;
   const int qn = (s_max + nc - 1) / nc;
   const int q0 = min(s_max, cr * qn), q1 = min(s_max, q0 + qn);
-  z_solve_cols<16, true>(A, ldz, z, Pc + (int64_t)node * ldz * s_max, T + (int64_t)nl * ldz * s_max, s_max,
-                         rank[node], q0, q1, sh);
+  z_solve_cols<16, true>(A, ldz, z, Pc + (int64_t)node * ldz * s_max, T + (int64_t)nl * ldz * s_max,
+                         T32 ? T32 + (int64_t)nl * ldz * s_max : nullptr, s_max, rank[node], q0, q1, sh);
 }
 
 // Telescoping GEMM: P^_a[rows of c, :s_a] = P^_c[:, :s_c] T[c block, :s_a].
@@ -1144,6 +1165,7 @@ kf_status level_eval_v(kf_factor* f, int l, cudaStream_t s) {
 // Z, its LU, T = Z^-1 P_c and the telescoped P^ of level l
 template <typename T>
 kf_status level_reduce(kf_factor* f, int l, double* Tm, cudaStream_t s) {
+  float* Tm32 = f->prec == KF_PREC_FP64 ? nullptr : (float*)(Tm + kf_factor_tm_elems(f));
   kf_tree* t = f->t;
   kf_ctx* c = f->ctx;
   const int s_max = f->s_max, ldz = 2 * s_max;
@@ -1186,19 +1208,19 @@ kf_status level_reduce(kf_factor* f, int l, double* Tm, cudaStream_t s) {
     const int solve = l >= 1 ? 1 : 0;
     cudaError_t le = cudaSuccess;
     KF_PHASE(KF_PH_ZLU, s, le = cudaLaunchKernelEx(&cfg, k_z_factor_cluster, (const int32_t*)f->rank, node0, ldz,
-                                                   s_max, f->ZLU, f->Zpiv, (const double*)f->Pc, Tm, solve,
+                                                   s_max, f->ZLU, f->Zpiv, (const double*)f->Pc, Tm, Tm32, solve,
                                                    f->status, f->pivr));
     if (le != cudaSuccess)
       return kf_set_err(c, KF_ECUDA, "reduced-system LU (cluster of %d) at level %d: %s", zc, l, cudaGetErrorString(le));
   } else {
-    KF_PHASE(KF_PH_ZLU, s, k_z_factor<<<nn, 256, 0, s>>>(f->rank, node0, ldz, s_max, f->ZLU, f->Zpiv, f->Pc, Tm,
+    KF_PHASE(KF_PH_ZLU, s, k_z_factor<<<nn, 256, 0, s>>>(f->rank, node0, ldz, s_max, f->ZLU, f->Zpiv, f->Pc, Tm, Tm32,
                                                          l >= 1 ? 1 : 0, f->status, f->pivr));
   }
   if (l >= 1) {
     const int64_t cmax_rows = (N >> (l + 1)) + 1;
     dim3 gt((unsigned)((cmax_rows + 63) / 64), (s_max + 63) / 64, 2 * nn);
     if (sizeof(T) == 4 && f->use_tc) {
-      kf_status r = kf_tc_telescope(t->d_lo, t->d_hi, f->rank, node0, nn, s_max, (const float*)lvl(Phat, l + 1), Tm,
+      kf_status r = kf_tc_telescope(t->d_lo, t->d_hi, f->rank, node0, nn, s_max, (const float*)lvl(Phat, l + 1), Tm32,
                                     ldz, (float*)lvl(Phat, l), cmax_rows, f->status, s);
       if (r != KF_OK) return kf_set_err(c, r, "tensor-core telescoping failed at level %d", l);
     } else {
@@ -1212,6 +1234,11 @@ kf_status level_reduce(kf_factor* f, int l, double* Tm, cudaStream_t s) {
 }
 
 }  // namespace
+
+// T = Z^-1 P_c of one level (FP64) and, on the mixed path, its FP32 copy right after it
+size_t kf_factor_tm_bytes(const kf_factor* f) {
+  return (sizeof(double) + (f->prec == KF_PREC_FP64 ? 0 : sizeof(float))) * kf_factor_tm_elems(f);
+}
 
 size_t kf_factor_tm_elems(const kf_factor* f) {
   const int D = f->t->D;
@@ -1252,7 +1279,7 @@ kf_status kf_factorize_device(kf_factor* f, cudaStream_t s) {
   kf_ctx* c = f->ctx;
   kf_status st = kf_factorize_leaves(f, s, true);
   if (st != KF_OK || f->t->D == 0) return st;
-  const size_t tb = sizeof(double) * kf_factor_tm_elems(f);
+  const size_t tb = kf_factor_tm_bytes(f);
   double* Tm = (double*)c->dalloc(tb, s);
   if (!Tm) return kf_set_err(c, KF_ENOMEM, "factorize: allocation failed");
   for (int l = f->t->D - 1; l >= 0 && st == KF_OK; --l) st = kf_factorize_level(f, l, Tm, s);
@@ -1274,7 +1301,7 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
   }
   kf_skel_scratch sc;
   kf_status st = kf_skel_begin(f, &sc, s);
-  const size_t tb = sizeof(double) * kf_factor_tm_elems(f);
+  const size_t tb = kf_factor_tm_bytes(f);
   double* Tm = st == KF_OK ? (double*)c->dalloc(tb, s) : nullptr;
   if (st == KF_OK && !Tm) st = kf_set_err(c, KF_ENOMEM, "factorize: allocation failed");
   cudaStream_t s1 = nullptr, s2 = nullptr, s3 = nullptr;

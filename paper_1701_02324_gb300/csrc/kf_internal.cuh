@@ -276,6 +276,7 @@ kf_status kf_factorize_device(kf_factor* f, cudaStream_t s);
 // skeleton levels l + 1 and l); Tm is the T = Z^-1 P_c scratch of
 // kf_factor_tm_elems() doubles.
 size_t kf_factor_tm_elems(const kf_factor* f);
+size_t kf_factor_tm_bytes(const kf_factor* f);
 kf_status kf_factorize_leaves(kf_factor* f, cudaStream_t s, bool with_k64);
 kf_status kf_leaf_k64_launch(kf_factor* f, cudaStream_t s);
 kf_status kf_factorize_level(kf_factor* f, int l, double* Tm, cudaStream_t s);

@@ -447,14 +447,17 @@ __global__ void __cluster_dims__(kQC, 1, 1) __launch_bounds__(256)
       cand = b;
     }
     cluster.sync();  // (A) proposals visible
-    if (tid == 0) {
+    if (warp == 0) {  // lane r reads CTA r's proposal; positions are distinct, so the max is unique
       QrCand b{-1.0, c, -1};
-      for (int r = 0; r < kQC; ++r) {
-        const QrCand* rc = cluster.map_shared_rank(&cand, r);
-        const QrCand o = *rc;
+      if (lane < kQC) b = *cluster.map_shared_rank(&cand, lane);
+      for (int off = 16; off > 0; off >>= 1) {
+        QrCand o;
+        o.v = __shfl_xor_sync(0xffffffffu, b.v, off);
+        o.pos = __shfl_xor_sync(0xffffffffu, b.pos, off);
+        o.phys = __shfl_xor_sync(0xffffffffu, b.phys, off);
         if (o.v > b.v || (o.v == b.v && o.pos < b.pos)) b = o;
       }
-      best = b;
+      if (lane == 0) best = b;
     }
     __syncthreads();
     const double rkk = sqrt(best.v);

@@ -336,7 +336,7 @@ struct TelescopeProblem {
   const int32_t* rank;
   int node0, s_max, ldz, ntile_n;
   const float* Pc_hat;
-  const double* Tm;
+  const float* Tm;  // T = Z^-1 P_c, FP32 copy
   float* Pa_hat;
   __device__ Tile tile(int bx, int by, int bz) const {
     Tile t;
@@ -356,7 +356,7 @@ struct TelescopeProblem {
   __device__ float loadA(const Tile&, int m, int k) const { return Pc_hat[(int64_t)m * s_max + k]; }
   __device__ float loadB(const Tile& t, int k, int n) const {
     const int koff = t.side == 0 ? 0 : rank[2 * t.node];
-    return (float)Tm[(int64_t)t.base * ldz * s_max + (int64_t)(koff + k) * s_max + n];
+    return Tm[(int64_t)t.base * ldz * s_max + (int64_t)(koff + k) * s_max + n];
   }
   __device__ void store(const Tile&, int m, int n, float v) const { Pa_hat[(int64_t)m * s_max + n] = v; }
 };
@@ -387,7 +387,7 @@ kf_status kf_tc_zoff(const int32_t* lo, const int32_t* hi, const int32_t* rank, 
 }
 
 kf_status kf_tc_telescope(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
-                          const float* Pc_hat, const double* Tm, int ldz, float* Pa_hat, int64_t rows_per_child,
+                          const float* Pc_hat, const float* Tm, int ldz, float* Pa_hat, int64_t rows_per_child,
                           int32_t* status, cudaStream_t s) {
   TelescopeProblem p;
   p.lo = lo; p.hi = hi; p.rank = rank; p.node0 = node0; p.s_max = s_max; p.ldz = ldz;

@@ -153,6 +153,24 @@ def test_fp64_operator_matches_oracle_matvec(h, N, m):
     assert rel(y, o.matvec(x)) <= 1e-13
 
 
+def test_cluster_kernels_medium_tree():
+    """N = 65,536 with 512-point leaves (D = 7) puts 64, 32 and 16 nodes on the
+    upper levels, i.e. LU clusters of 2, 4 and 8 CTAs and the cluster QR on
+    levels of 64 nodes and fewer.  The skeletons and the FP64 solution must not
+    depend on whether those kernels or one CTA per node run."""
+    X, b = problem(65536, 8, seed=21)
+    tree = kf.Tree(torch.from_numpy(X).cuda(), 512)
+    Fa = kf.Factor(tree, 0.4, 0.5, 1e-5, 64, precision=FP64)
+    Fb = kf.Factor(tree, 0.4, 0.5, 1e-5, 64, precision=FP64, cluster_kernels=False)
+    ra, rb = Fa.ranks(), Fb.ranks()
+    assert np.array_equal(ra, rb)
+    for a in range(2, 256):
+        assert np.array_equal(Fa.skeleton(a), Fb.skeleton(a))
+    bt = torch.from_numpy(b).cuda()
+    xa, xb = Fa.solve(bt).cpu().numpy(), Fb.solve(bt).cpu().numpy()
+    assert rel(xa, xb) <= 1e-10
+
+
 def test_matvec_transpose_and_grad_parity(c1):
     p, o, tree = c1
     ranks, skel, P = ids_from_oracle(o, p.s_max)
