@@ -119,6 +119,105 @@ def level_qr_flops(sizes, ranks, N, D, n_samp, s_max, lo, hi):
     return out
 
 
+FP32_PEAK_TFLOPS = 80.5          # nominal: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
+FP32_INSTR_PEAK = 40.3e12         # FP32 lane instructions per second at the same clock
+TF32_OVER_BF16 = 0.49             # recipe's nominal dense ratio (1.1 / 2.25 PFLOP/s)
+
+
+def max_over_ranks(values, device=None):
+    """Element-wise maximum of a list of numbers over all ranks of the default
+    process group (the replicas' timings: the job ends with its slowest
+    replica); the values themselves on a single process."""
+    import torch
+    import torch.distributed as td
+    if not (td.is_available() and td.is_initialized()) or td.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return t.tolist()
+
+
+def phase_work(p, D, lo, hi, ranks, n_samp):
+    """Algorithmic work of one factorization (per phase) and of one solve
+    sweep / one operator product, from the realized ranks.  Returns
+    {phase: (kind, amount, per)} with kind in fp64 / fp32 / fp32i (FP32
+    lane instructions, an estimate) / tf32 (tensor flops of 3xTF32) / hbm
+    (bytes) and per in {"step", "sweep", "matvec"}."""
+    N, d, s_max = p.N, p.d, p.s_max
+    r = ranks
+    per_level = level_qr_flops(None, ranks, N, D, n_samp, s_max, lo, hi)
+    clus = [l for l in range(1, D) if (1 << l) <= 64]
+    w = {"qr_leaf": ("fp64", per_level[D], "step"),
+         "qr": ("fp64", sum(per_level[l] for l in range(1, D) if l not in clus), "step"),
+         "qr_cluster": ("fp64", sum(per_level[l] for l in clus), "step")}
+    ent = ventries = 0.0
+    zoff = tel = zlu = 0.0
+    chol = phat = 0.0
+    b_leaf = b_cs = b_ru = b_z = 0.0
+    m_leaf = m_cs = m_ru = 0.0
+    for l in range(1, D + 1):
+        for a in range(1 << l, 1 << (l + 1)):
+            n = hi[a] - lo[a]
+            ns = min(n_samp, N - n)
+            c = n if l == D else r[2 * a] + r[2 * a + 1]
+            ent += ns * c
+            ventries += n * r[a ^ 1]
+            b_cs += 4.0 * n * r[a ^ 1]
+            b_ru += 4.0 * n * r[a]
+            m_cs += 8.0 * n * r[a ^ 1]
+            if l == D:
+                chol += n ** 3 / 3.0
+                phat += 2.0 * n * n * r[a]
+                b_leaf += 4.0 * n * (n + 1)
+                m_leaf += 8.0 * n * n
+                m_ru += 8.0 * n * r[a]
+    for a in range(1, 1 << D):
+        cl, cr = 2 * a, 2 * a + 1
+        nl, nr = hi[cl] - lo[cl], hi[cr] - lo[cr]
+        z = r[cl] + r[cr]
+        zoff += 3 * 2.0 * r[cl] * r[cr] * (nl + nr)
+        zlu += 2.0 / 3.0 * z ** 3 + (2.0 * z * z * r[a] if a >= 2 else 0.0)
+        if a >= 2:
+            tel += 3 * 2.0 * (nl * r[cl] + nr * r[cr]) * r[a]
+        b_z += 8.0 * z * z
+    w.update({"eval_A": ("fp64", 3.0 * d * ent, "step"),
+              "leaf_cholesky": ("fp32", chol, "step"), "leaf_phat": ("fp32", phat, "step"),
+              "eval_V": ("fp32i", ventries * (21.0 * d + 70.0), "step"),
+              "zoff": ("tf32", zoff, "step"), "telescope": ("tf32", tel, "step"), "z_lu": ("fp64", zlu, "step"),
+              "solve_leaf": ("hbm", b_leaf, "sweep"), "solve_colsum": ("hbm", b_cs, "sweep"),
+              "solve_rowupd": ("hbm", b_ru, "sweep"), "solve_zsolve": ("hbm", b_z, "sweep"),
+              "matvec_leaf": ("hbm", m_leaf, "matvec"), "matvec_colsum": ("hbm", m_cs, "matvec"),
+              "matvec_rowupd": ("hbm", m_ru, "matvec")})
+    return w
+
+
+def phase_rooflines(work, phase_ms, phase_launches, steps, peaks):
+    """Achieved rate and fraction of the roofline per phase; the phase time is
+    the sum of its launches' CUDA-event durations, which on the factorization's
+    overlapped streams includes time spent sharing the SMs (a lower bound on
+    each kernel's own fraction)."""
+    sweeps = phase_launches.get("solve_leaf", 0) / max(steps, 1)
+    mvs = phase_launches.get("matvec_leaf", 0) / max(steps, 1)
+    peak = {"fp64": (FP64_PEAK_TFLOPS * 1e12, "TFLOP/s", 1e12, "nominal"),
+            "fp32": (FP32_PEAK_TFLOPS * 1e12, "TFLOP/s", 1e12, "nominal"),
+            "fp32i": (FP32_INSTR_PEAK, "Tinstr/s", 1e12, "nominal"),
+            "tf32": (peaks["bf16_tflops"] * TF32_OVER_BF16 * 1e12, "TFLOP/s", 1e12,
+                     "measured bf16 x nominal tf32/bf16"),
+            "hbm": (peaks["hbm_gbs"] * 1e9, "GB/s", 1e9, "measured")}
+    out = {}
+    for ph, (kind, amount, per) in work.items():
+        ms = phase_ms.get(ph, 0.0)
+        if ms <= 0 or amount <= 0:
+            continue
+        count = steps * (1 if per == "step" else (sweeps if per == "sweep" else mvs))
+        rate = amount * count / (ms * 1e-3)
+        pk, unit, scale, src = peak[kind]
+        out[ph] = {"bound": {"fp64": "alu", "fp32": "alu", "fp32i": "alu", "tf32": "tensor", "hbm": "hbm"}[kind],
+                   "achieved": round(rate / scale, 3), "unit": unit, "peak": round(pk / scale, 1),
+                   "frac": round(rate / pk, 4), "peak_src": src, "per_step": round(count / steps, 2)}
+    return out
+
+
 def tree_ranges(N, m):
     D = 0
     while (m << D) < N:
@@ -306,10 +405,7 @@ def gpu_main(args, rank, world):
     fact_s = statistics.mean(fact_ms) / 1e3
     solve_s = statistics.mean(solve_ms) / 1e3
     ms_per_step = total_ms / args.steps
-    if dist:
-        t = torch.tensor([fact_s, solve_s, ms_per_step], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        fact_s, solve_s, ms_per_step = t.tolist()
+    fact_s, solve_s, ms_per_step = max_over_ranks([fact_s, solve_s, ms_per_step], dev)
 
     # ---- FP64 comparison leg (same workload, same skeletons) ---------------------
     fp64, unref = None, None
@@ -429,6 +525,8 @@ def gpu_main(args, rank, world):
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
                 "traffic": None}
     roof["phase_ms_per_step"] = {k: round(v / args.steps, 3) for k, v in phase_ms.items() if v > 0}
+    roof["phase_rooflines"] = phase_rooflines(phase_work(p, D, lo, hi, ranks, 2 * p.s_max), phase_ms,
+                                              phase_launches, args.steps, peaks)
 
     # ---- CPU baseline (oracle, bounded sample) ------------------------------------------
     cpu = None

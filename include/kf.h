@@ -252,8 +252,10 @@ kf_status kf_profile_enable(int32_t on);
  * solve_rowupd, matvec_leaf, matvec_push, misc, qr_cluster (the pivoted QR of
  * the upper levels on thread-block clusters and its R11^-1 R12 step), qr_leaf
  * (the pivoted QR of the leaf level; "qr" holds the other one-CTA-per-node
- * levels). */
-#define KF_PHASE_COUNT 21
+ * levels), matvec_colsum and matvec_rowupd (the V-block passes of kf_matvec
+ * and of the refinement's operator; solve_colsum and solve_rowupd are those of
+ * the solve sweep). */
+#define KF_PHASE_COUNT 23
 kf_status kf_profile_read(double* ms, int64_t* launches, int32_t nphase);
 
 #ifdef __cplusplus

@@ -30,6 +30,8 @@ enum kf_phase {
   KF_PH_MISC,
   KF_PH_QR_CLUSTER,
   KF_PH_QR_LEAF,
+  KF_PH_MV_COLSUM,
+  KF_PH_MV_ROWUPD,
   KF_PH_COUNT
 };
 

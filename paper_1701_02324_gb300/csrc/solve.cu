@@ -166,12 +166,13 @@ __global__ void __launch_bounds__(256) k_colsum(const int32_t* __restrict__ lo, 
 template <typename TM, typename TV>
 void launch_colsum(dim3 g, cudaStream_t s, const int32_t* lo, const int32_t* hi, const int32_t* rank,
                    const int32_t* skel, int node0, int s_max, int sib, int src, const TM* M, const double* X64,
-                   const float* X32, int d, double c_exp, double inv_h3, const TV* W, int k, double* U) {
+                   const float* X32, int d, double c_exp, double inv_h3, const TV* W, int k, double* U,
+                   int phase = KF_PH_S_COLSUM) {
   if (k == 1)
-    KF_PHASE(KF_PH_S_COLSUM, s, k_colsum<TM, TV, 1><<<g, 256, 0, s>>>(lo, hi, rank, skel, node0, s_max, sib, src, M, X64, X32, d, c_exp, inv_h3,
+    KF_PHASE(phase, s, k_colsum<TM, TV, 1><<<g, 256, 0, s>>>(lo, hi, rank, skel, node0, s_max, sib, src, M, X64, X32, d, c_exp, inv_h3,
                                           W, k, U));
   else
-    KF_PHASE(KF_PH_S_COLSUM, s, k_colsum<TM, TV, 8><<<g, 256, 0, s>>>(lo, hi, rank, skel, node0, s_max, sib, src, M, X64, X32, d, c_exp, inv_h3,
+    KF_PHASE(phase, s, k_colsum<TM, TV, 8><<<g, 256, 0, s>>>(lo, hi, rank, skel, node0, s_max, sib, src, M, X64, X32, d, c_exp, inv_h3,
                                           W, k, U));
 }
 
@@ -234,13 +235,14 @@ __global__ void __launch_bounds__(256) k_rowupd(const int32_t* __restrict__ lo, 
 template <typename TM, typename TV>
 void launch_rowupd(int64_t rows, int nnodes, cudaStream_t s, const int32_t* lo, const int32_t* hi, const int32_t* rank,
                    const int32_t* skel, int node0, int s_max, int sib, int src, const TM* M, const double* X64,
-                   const float* X32, int d, double c_exp, double inv_h3, const double* V, double sign, TV* W, int k) {
+                   const float* X32, int d, double c_exp, double inv_h3, const double* V, double sign, TV* W, int k,
+                   int phase = KF_PH_S_ROWUPD) {
   dim3 g((unsigned)((rows + kRowUpdRows - 1) / kRowUpdRows), nnodes);
   if (k == 1)
-    KF_PHASE(KF_PH_S_ROWUPD, s, k_rowupd<TM, TV, 1><<<g, 256, 0, s>>>(lo, hi, rank, skel, node0, nnodes, s_max, sib, src, M,
+    KF_PHASE(phase, s, k_rowupd<TM, TV, 1><<<g, 256, 0, s>>>(lo, hi, rank, skel, node0, nnodes, s_max, sib, src, M,
                                                                      X64, X32, d, c_exp, inv_h3, V, sign, W, k));
   else
-    KF_PHASE(KF_PH_S_ROWUPD, s, k_rowupd<TM, TV, 8><<<g, 256, 0, s>>>(lo, hi, rank, skel, node0, nnodes, s_max, sib, src, M,
+    KF_PHASE(phase, s, k_rowupd<TM, TV, 8><<<g, 256, 0, s>>>(lo, hi, rank, skel, node0, nnodes, s_max, sib, src, M,
                                                                      X64, X32, d, c_exp, inv_h3, V, sign, W, k));
 }
 
@@ -533,16 +535,17 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
     if (f->VT64 && !deriv)  // FP64-accurate operator of the mixed path
       launch_colsum<double, double>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, s_max, 1, SRC_STORED,
                                     f->VT64 + (int64_t)(l - 1) * N * s_max, t->X64, t->X32, t->d, f->c_exp, inv_h3, x,
-                                    (int)k, G);
+                                    (int)k, G, KF_PH_MV_COLSUM);
     else
       launch_colsum<TM, double>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, s_max, 1, src,
-                                VT + (int64_t)(l - 1) * N * s_max, t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G);
+                                VT + (int64_t)(l - 1) * N * s_max, t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G,
+                                KF_PH_MV_COLSUM);
   }
   for (int l = 1; l < D; ++l)
     KF_PHASE(KF_PH_MV_PUSH, s, k_push_down<<<1 << l, 256, 0, s>>>(f->rank, 1 << l, s_max, f->Pc, G, (int)k));
   const int64_t rows = (N >> D) + 1;
   launch_rowupd<double, double>(rows, 1 << D, s, t->d_lo, t->d_hi, f->rank, f->skel, leaf0, s_max, 0, SRC_STORED,
-                                f->Pleaf, t->X64, t->X32, t->d, f->c_exp, inv_h3, G, 1.0, y, (int)k);
+                                f->Pleaf, t->X64, t->X32, t->d, f->c_exp, inv_h3, G, 1.0, y, (int)k, KF_PH_MV_ROWUPD);
   KF_LAUNCH_CHECK(c);
   return KF_OK;
 }
