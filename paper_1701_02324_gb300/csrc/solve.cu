@@ -56,58 +56,115 @@ __device__ __forceinline__ double eval_src(int src, const double* X64, const flo
 // Blocks of 32 rows: warp 0 solves the diagonal block with shuffles (lane i
 // holds row kb + i), then every thread updates one row of the rest of the
 // leaf with the solved block (two barriers per block).
+// y[i] -= sum_{j < nb} M[i][kb + j] x[j] for rows [r0, r1) of a row-major
+// matrix (row i at rowp(i)): a warp takes 32 rows at a time, loads the 32 x 32
+// tile row by row (each row one coalesced segment) into its shared-memory
+// tile, then lane q forms row q's dot product.  x has 32 entries (zero past nb).
+template <typename TM, typename TV, typename RowPtr, typename Out>
+__device__ __forceinline__ void warp_tile_rowupd(int r0, int r1, int kb, int nb, RowPtr rowp, const TV* x,
+                                                 Out out, TM (*tile)[33]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i0 = r0 + warp * 32; i0 < r1; i0 += nw * 32) {
+    TM v[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = (i0 + q < r1 && lane < nb) ? rowp(i0 + q)[kb + lane] : (TM)0;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) tile[q][lane] = v[q];
+    __syncwarp();
+    if (i0 + lane < r1) {
+      TV acc = (TV)0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc += (TV)tile[lane][j] * x[j];
+      out(i0 + lane, acc);
+    }
+    __syncwarp();
+  }
+}
+
 template <typename TM, typename TV>
-__global__ void __launch_bounds__(256) k_leaf_solve(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+__global__ void __launch_bounds__(256, sizeof(TM) == 4 ? 2 : 1) k_leaf_solve(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                     int leaf0, int ldL, const TM* __restrict__ Lall,
                                                     TV* __restrict__ W, int k) {
   constexpr int NB = 32;
   __shared__ TV xb[NB];
+  __shared__ TM db[NB][NB + 1];  // the staged diagonal block
+  __shared__ TV dinv[NB];        // reciprocals of its diagonal (divisions in parallel)
+  extern __shared__ unsigned char lsm[];
+  TM (*wtile)[33] = (TM (*)[33])lsm;  // one 32 x 32 row tile per warp (row updates), dynamic
   const int lf = blockIdx.x, node = leaf0 + lf;
   const int b = lo[node], n = hi[node] - b;
   const TM* L = Lall + (int64_t)lf * ldL * ldL;
   TV* Y = W + (int64_t)b * k;
   const int tid = threadIdx.x, lane = tid & 31;
+  // diagonal blocks fetched into registers one block ahead, then committed
+  // to shared memory; warp 0 forms the reciprocals of the diagonal
+  TM pre[4];
+  auto fetch = [&](int kb, int nb) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = q * 256 + tid, i = e >> 5, j = e & 31;
+      pre[q] = (i < nb && j <= i) ? L[(int64_t)(kb + i) * ldL + kb + j] : (TM)0;
+    }
+  };
+  auto commit = [&](int nb) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = q * 256 + tid;
+      db[e >> 5][e & 31] = pre[q];
+    }
+    __syncthreads();
+    if (tid < NB) {
+      dinv[lane] = lane < nb ? (TV)1 / (TV)db[lane][lane] : (TV)0;
+      __syncwarp();
+    }
+  };
+  const int top = n > 0 ? ((n - 1) / NB) * NB : 0;
   for (int r = 0; r < k; ++r) {
     // forward: L y = b
+    if (n > 0) fetch(0, min(NB, n));
     for (int kb = 0; kb < n; kb += NB) {
       const int nb = min(NB, n - kb);
+      commit(nb);
       if (tid < 32) {
         TV yi = lane < nb ? Y[(int64_t)(kb + lane) * k + r] : (TV)0;
-        const TM* Li = L + (int64_t)(kb + lane) * ldL + kb;
         for (int j = 0; j < nb; ++j) {
-          if (lane == j) yi = yi / (TV)Li[j];
+          if (lane == j) yi *= dinv[j];
           const TV yj = __shfl_sync(0xffffffffu, yi, j);
-          if (lane > j && lane < nb) yi -= (TV)Li[j] * yj;
+          if (lane > j && lane < nb) yi -= (TV)db[lane][j] * yj;
         }
-        if (lane < nb) { xb[lane] = yi; Y[(int64_t)(kb + lane) * k + r] = yi; }
+        xb[lane] = lane < nb ? yi : (TV)0;
+        if (lane < nb) Y[(int64_t)(kb + lane) * k + r] = yi;
       }
       __syncthreads();
-      for (int i = kb + nb + tid; i < n; i += blockDim.x) {
-        const TM* Li = L + (int64_t)i * ldL + kb;
-        TV acc = (TV)0;
-#pragma unroll 8
-        for (int j = 0; j < nb; ++j) acc += (TV)Li[j] * xb[j];
-        Y[(int64_t)i * k + r] -= acc;
-      }
+      if (kb + NB < n) fetch(kb + NB, min(NB, n - kb - NB));
+      warp_tile_rowupd<TM, TV>(kb + nb, n, kb, nb, [&](int i) { return L + (int64_t)i * ldL; }, xb,
+                               [&](int i, TV acc) { Y[(int64_t)i * k + r] -= acc; }, wtile + (tid >> 5) * 32);
       __syncthreads();
     }
     // backward: L^T x = y
-    for (int kb = ((n - 1) / NB) * NB; kb >= 0 && n > 0; kb -= NB) {
+    if (n > 0) fetch(top, n - top);
+    for (int kb = top; kb >= 0 && n > 0; kb -= NB) {
       const int nb = min(NB, n - kb);
+      commit(nb);
       if (tid < 32) {
         TV xi = lane < nb ? Y[(int64_t)(kb + lane) * k + r] : (TV)0;
         for (int j = nb - 1; j >= 0; --j) {
-          if (lane == j) xi = xi / (TV)L[(int64_t)(kb + j) * ldL + kb + j];
-          TV xj = __shfl_sync(0xffffffffu, xi, j);
-          if (lane < j) xi -= (TV)L[(int64_t)(kb + j) * ldL + kb + lane] * xj;
+          if (lane == j) xi *= dinv[j];
+          const TV xj = __shfl_sync(0xffffffffu, xi, j);
+          if (lane < j) xi -= (TV)db[j][lane] * xj;
         }
-        if (lane < nb) { xb[lane] = xi; Y[(int64_t)(kb + lane) * k + r] = xi; }
+        xb[lane] = lane < nb ? xi : (TV)0;
+        if (lane < nb) Y[(int64_t)(kb + lane) * k + r] = xi;
       }
       __syncthreads();
+      if (kb >= NB) fetch(kb - NB, NB);
       for (int i = tid; i < kb; i += blockDim.x) {
+        TM v[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) v[j] = j < nb ? L[(int64_t)(kb + j) * ldL + i] : (TM)0;
         TV acc = (TV)0;
-#pragma unroll 8
-        for (int j = 0; j < nb; ++j) acc += (TV)L[(int64_t)(kb + j) * ldL + i] * xb[j];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) acc += (TV)v[j] * xb[j];
         Y[(int64_t)i * k + r] -= acc;
       }
       __syncthreads();
@@ -251,17 +308,8 @@ void launch_rowupd(int64_t rows, int nnodes, cudaStream_t s, const int32_t* lo, 
 // pm[i] of ZLU, and (P b)[i] = b[pm[i]].  Blocked by 32 rows: the 32 x 32
 // diagonal block is staged in shared memory, warp 0 solves it with shuffles,
 // then all threads update the remaining rows with it.
-// acc - sum_{j < nb} a[j] x[j] (a contiguous) or a[j * lda] x[j]: fully
-// unrolled with predicated loads, so that the 32 loads are in flight together
-__device__ __forceinline__ double row_update(const double* __restrict__ a, int nb, const double* x, double acc) {
-  double v[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = j < nb ? a[j] : 0.0;
-#pragma unroll
-  for (int j = 0; j < 32; ++j) acc = fma(-v[j], x[j], acc);
-  return acc;
-}
-
+// acc - sum_{j < nb} A[rows[j]][i] x[j]: fully unrolled with predicated loads, so
+// that the 32 loads are in flight together
 // column i of rows rows[0..nb) of A (row stride lda)
 __device__ __forceinline__ double col_update(const double* __restrict__ A, int lda, const int* rows, int i, int nb,
                                              const double* x, double acc) {
@@ -281,6 +329,7 @@ __global__ void __launch_bounds__(256) k_zsolve(const int32_t* __restrict__ rank
   double* t = zsm;                   // ldz
   double* u = t + ldz;               // ldz
   int* pm = (int*)(u + ldz);         // ldz
+  double (*wtile)[33] = (double (*)[33])(zsm + 2 * ldz + (ldz + 1) / 2);  // 8 warps x 32 x 33: row tiles
   __shared__ double db[32][33];
   __shared__ double dinv[32];  // reciprocals of the diagonal of the staged block
   __shared__ double xb[32];
@@ -291,19 +340,32 @@ __global__ void __launch_bounds__(256) k_zsolve(const int32_t* __restrict__ rank
   const int tid = threadIdx.x, lane = tid & 31;
   for (int i = tid; i < z; i += blockDim.x) pm[i] = pv[i];
   __syncthreads();
-  // stage the diagonal block of logical rows kb..kb+nb
-  auto stage = [&](int kb, int nb) {
+  // The 32 x 32 diagonal block of logical rows kb..kb+nb: fetched into
+  // registers one block ahead (its loads fly while the previous block's rows
+  // are updated), then committed to shared memory.  Warp 0 forms the
+  // reciprocals of its diagonal, one division per lane in parallel (an FP64
+  // division inside the dependent chain would cost about 1000 cycles).
+  double pre[4];
+  auto fetch = [&](int kb, int nb) {
 #pragma unroll
-    for (int e0 = 0; e0 < 32 * 32; e0 += 256) {
-      const int e = e0 + tid, i = e >> 5, j = e & 31;
-      if (e < 32 * 32) db[i][j] = (i < nb && j < nb) ? A[(int64_t)pm[kb + i] * ldz + kb + j] : 0.0;
+    for (int q = 0; q < 4; ++q) {
+      const int e = q * 256 + tid, i = e >> 5, j = e & 31;
+      pre[q] = (i < nb && j < nb) ? A[(int64_t)pm[kb + i] * ldz + kb + j] : 0.0;
+    }
+  };
+  auto commit = [&](int nb, bool recip) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = q * 256 + tid;
+      db[e >> 5][e & 31] = pre[q];
     }
     __syncthreads();
-    // one division per lane in parallel: the solve below then multiplies (an
-    // FP64 division in its dependent chain would cost about 1000 cycles)
-    if (tid < 32) dinv[tid] = tid < nb ? 1.0 / db[tid][tid] : 0.0;
-    __syncthreads();
+    if (recip && tid < 32) {
+      dinv[lane] = lane < nb ? 1.0 / db[lane][lane] : 0.0;
+      __syncwarp();
+    }
   };
+  const int top = z > 0 ? ((z - 1) / 32) * 32 : 0;
   for (int c = 0; c < k; ++c) {
     for (int i = tid; i < z; i += blockDim.x)
       u[i] = i < sl ? in[((int64_t)l * s_max + i) * k + c] : in[((int64_t)r * s_max + (i - sl)) * k + c];
@@ -312,9 +374,10 @@ __global__ void __launch_bounds__(256) k_zsolve(const int32_t* __restrict__ rank
       for (int i = tid; i < z; i += blockDim.x) t[i] = u[pm[i]];
       __syncthreads();
       // L (unit lower)
+      if (z > 0) fetch(0, min(32, z));
       for (int kb = 0; kb < z; kb += 32) {
         const int nb = min(32, z - kb);
-        stage(kb, nb);
+        commit(nb, false);
         if (tid < 32) {
           double yi = lane < nb ? t[kb + lane] : 0.0;
           for (int j = 0; j < nb; ++j) {
@@ -324,13 +387,16 @@ __global__ void __launch_bounds__(256) k_zsolve(const int32_t* __restrict__ rank
           if (lane < nb) { xb[lane] = yi; t[kb + lane] = yi; } else { xb[lane] = 0.0; }
         }
         __syncthreads();
-        for (int i = kb + nb + tid; i < z; i += blockDim.x) t[i] = row_update(A + (int64_t)pm[i] * ldz + kb, nb, xb, t[i]);
+        if (kb + 32 < z) fetch(kb + 32, min(32, z - kb - 32));
+        warp_tile_rowupd<double, double>(kb + nb, z, kb, nb, [&](int i) { return A + (int64_t)pm[i] * ldz; }, xb,
+                                         [&](int i, double acc) { t[i] -= acc; }, wtile + (tid >> 5) * 32);
         __syncthreads();
       }
       // U
-      for (int kb = ((z - 1) / 32) * 32; kb >= 0 && z > 0; kb -= 32) {
+      if (z > 0) fetch(top, z - top);
+      for (int kb = top; kb >= 0 && z > 0; kb -= 32) {
         const int nb = min(32, z - kb);
-        stage(kb, nb);
+        commit(nb, true);
         if (tid < 32) {
           double xi = lane < nb ? t[kb + lane] : 0.0;
           for (int j = nb - 1; j >= 0; --j) {
@@ -341,16 +407,19 @@ __global__ void __launch_bounds__(256) k_zsolve(const int32_t* __restrict__ rank
           if (lane < nb) { xb[lane] = xi; t[kb + lane] = xi; } else { xb[lane] = 0.0; }
         }
         __syncthreads();
-        for (int i = tid; i < kb; i += blockDim.x) t[i] = row_update(A + (int64_t)pm[i] * ldz + kb, nb, xb, t[i]);
+        if (kb >= 32) fetch(kb - 32, 32);
+        warp_tile_rowupd<double, double>(0, kb, kb, nb, [&](int i) { return A + (int64_t)pm[i] * ldz; }, xb,
+                                         [&](int i, double acc) { t[i] -= acc; }, wtile + (tid >> 5) * 32);
         __syncthreads();
       }
     } else {
       for (int i = tid; i < z; i += blockDim.x) t[i] = u[i];
       __syncthreads();
       // U^T y = b (forward)
+      if (z > 0) fetch(0, min(32, z));
       for (int kb = 0; kb < z; kb += 32) {
         const int nb = min(32, z - kb);
-        stage(kb, nb);
+        commit(nb, true);
         if (tid < 32) {
           double yi = lane < nb ? t[kb + lane] : 0.0;
           for (int j = 0; j < nb; ++j) {
@@ -361,13 +430,15 @@ __global__ void __launch_bounds__(256) k_zsolve(const int32_t* __restrict__ rank
           if (lane < nb) { xb[lane] = yi; t[kb + lane] = yi; } else { xb[lane] = 0.0; }
         }
         __syncthreads();
+        if (kb + 32 < z) fetch(kb + 32, min(32, z - kb - 32));
         for (int i = kb + nb + tid; i < z; i += blockDim.x) t[i] = col_update(A, ldz, pm + kb, i, nb, xb, t[i]);
         __syncthreads();
       }
       // L^T x = y (backward, unit diagonal)
-      for (int kb = ((z - 1) / 32) * 32; kb >= 0 && z > 0; kb -= 32) {
+      if (z > 0) fetch(top, z - top);
+      for (int kb = top; kb >= 0 && z > 0; kb -= 32) {
         const int nb = min(32, z - kb);
-        stage(kb, nb);
+        commit(nb, false);
         if (tid < 32) {
           double xi = lane < nb ? t[kb + lane] : 0.0;
           for (int j = nb - 1; j >= 0; --j) {
@@ -377,6 +448,7 @@ __global__ void __launch_bounds__(256) k_zsolve(const int32_t* __restrict__ rank
           if (lane < nb) { xb[lane] = xi; t[kb + lane] = xi; } else { xb[lane] = 0.0; }
         }
         __syncthreads();
+        if (kb >= 32) fetch(kb - 32, 32);
         for (int i = tid; i < kb; i += blockDim.x) t[i] = col_update(A, ldz, pm + kb, i, nb, xb, t[i]);
         __syncthreads();
       }
@@ -475,8 +547,13 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
   const size_t ubytes = sizeof(double) * (size_t)(t->nnodes + 1) * s_max * k;
   const double inv_h3 = 1.0 / (f->h * f->h * f->h);
   const int vsrc = f->vstore == KF_V_STORED ? SRC_STORED : SRC_KERNEL;
+  // dynamic shared memory: the warps' 32 x 33 row tiles (plus the Z solve's vectors and row map)
+  const size_t ls_smem = sizeof(TM) * 8 * 32 * 33;
+  const size_t zs_smem = sizeof(double) * (2 * (size_t)ldz + (ldz + 1) / 2 + 8 * 32 * 33);
+  KF_CUDA(c, cudaFuncSetAttribute(k_leaf_solve<TM, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls_smem));
+  KF_CUDA(c, cudaFuncSetAttribute(k_zsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs_smem));
   if (!transpose) {
-    KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve<TM, TV><<<1 << D, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
+    KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve<TM, TV><<<1 << D, 256, ls_smem, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
     for (int l = D - 1; l >= 0; --l) {
       const int c0 = 1 << (l + 1), nc = 1 << (l + 1);
       const int64_t rows = (N >> (l + 1)) + 1;
@@ -484,7 +561,7 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
       dim3 gc((unsigned)((rows + kRowsPerChunk - 1) / kRowsPerChunk), nc);
       launch_colsum<TM, TV>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 1, vsrc, lvl(VT, l + 1), t->X64,
                             t->X32, t->d, f->c_exp, inv_h3, W, (int)k, U);
-      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<1 << l, 256, (2 * sizeof(double) + sizeof(int)) * ldz, s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv, U, Vb,
+      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<1 << l, 256, zs_smem, s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv, U, Vb,
                                                          (int)k, 0));
       launch_rowupd<TM, TV>(rows, nc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 0, SRC_STORED,
                             lvl(Phat, l + 1), t->X64, t->X32, t->d, f->c_exp, inv_h3, Vb, -1.0, W, (int)k);
@@ -497,12 +574,12 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
       dim3 gc((unsigned)((rows + kRowsPerChunk - 1) / kRowsPerChunk), nc);
       launch_colsum<TM, TV>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 0, SRC_STORED, lvl(Phat, l + 1),
                             t->X64, t->X32, t->d, f->c_exp, inv_h3, W, (int)k, U);
-      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<1 << l, 256, (2 * sizeof(double) + sizeof(int)) * ldz, s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv, U, Vb,
+      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<1 << l, 256, zs_smem, s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv, U, Vb,
                                                          (int)k, 1));
       launch_rowupd<TM, TV>(rows, nc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 1, vsrc, lvl(VT, l + 1),
                             t->X64, t->X32, t->d, f->c_exp, inv_h3, Vb, -1.0, W, (int)k);
     }
-    KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve<TM, TV><<<1 << D, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
+    KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve<TM, TV><<<1 << D, 256, ls_smem, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
   }
   KF_LAUNCH_CHECK(c);
   return KF_OK;
