@@ -72,6 +72,17 @@ def _torch_free(ptr, nbytes, stream, user):
 
 
 _DELETE = [None]
+# Set at interpreter exit (an atexit handler registered after torch is
+# imported, so it runs before torch's own): from then on handles are not freed
+# (the process releases the device memory) and the free callback does nothing,
+# so that no call reaches torch or the CUDA runtime while they shut down.
+_EXITING = [False]
+_EXIT_HOOK = [False]
+
+
+def _at_exit():
+    _EXITING[0] = True
+    _DELETE[0] = None
 
 
 class Context:
@@ -80,6 +91,11 @@ class Context:
     def __init__(self, use_torch_allocator: bool = True):
         self.lib = _abi.load()
         self._alloc = None
+        if not _EXIT_HOOK[0]:
+            import atexit
+            _torch()
+            atexit.register(_at_exit)
+            _EXIT_HOOK[0] = True
         if use_torch_allocator:
             _DELETE[0] = _torch().cuda.caching_allocator_delete
             self._alloc = _abi.kf_alloc(ctypes.cast(_torch_alloc, ctypes.c_void_p).value,
@@ -92,7 +108,7 @@ class Context:
         return _abi.check(status, self.h, allow)
 
     def __del__(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and not _EXITING[0]:
             self.lib.kf_destroy(self.h)
             self.h = None
 
@@ -146,7 +162,7 @@ class Tree:
         return out
 
     def free(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and not _EXITING[0]:
             self.ctx.lib.kf_tree_free(self.h)
             self.h = None
 
@@ -274,7 +290,7 @@ class Factor:
         return self.ctx.lib.kf_factor_status(self.h, _stream_ptr())
 
     def free(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and not _EXITING[0]:
             self.ctx.lib.kf_factor_free(self.h)
             self.h = None
 

@@ -321,22 +321,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_leaf_phat(const
 
 // ---- V blocks: VT rows of every point of the level -------------------------------
 // VT[i][q] = K(x_i, x_{skel(sib)[q]}) for the points i of every node of the
-// level.  The sibling's skeleton coordinates are staged transposed in shared
-// memory (yT[k][q]); one warp per row, lanes over q, coalesced stores.
+// level (FP64 path).  The sibling's skeleton coordinates are staged transposed
+// in shared memory (yT[k][q]); one warp per row, lanes over q, coalesced stores.
 template <typename T>
-__global__ void __launch_bounds__(256) k_eval_vt(const double* __restrict__ X64, const float* __restrict__ X32,
-                                                 const float* __restrict__ X32lo, int d,
+__global__ void __launch_bounds__(256) k_eval_vt(const double* __restrict__ X64, const float* __restrict__ X32, int d,
                                                  double c_exp, const int32_t* __restrict__ lo,
                                                  const int32_t* __restrict__ hi, const int32_t* __restrict__ rank,
                                                  const int32_t* __restrict__ skel, int s_max, int node0, int rows_per_cta,
-                                                 int qchunk, T* __restrict__ VT, double* __restrict__ VT64, float ch,
-                                                 float cl, const float2* __restrict__ tab) {
+                                                 int qchunk, T* __restrict__ VT) {
   extern __shared__ unsigned char smraw[];
   T* yT = (T*)smraw;                       // d x qchunk
   T* xs = yT + (size_t)d * qchunk;         // 8 warps x d
-  // low halves of the double-float coordinates, for the FP64 operator copy
-  float* yTlo = (float*)(xs + 8 * d);      // d x qchunk
-  float* xslo = yTlo + (size_t)d * qchunk; // 8 warps x d
   const int nl = blockIdx.y, node = node0 + nl, sib = node ^ 1;
   const int b = lo[node], n = hi[node] - b, ss = rank[sib];
   const int r0 = blockIdx.x * rows_per_cta;
@@ -345,7 +340,6 @@ __global__ void __launch_bounds__(256) k_eval_vt(const double* __restrict__ X64,
   const int32_t* sk = skel + (int64_t)sib * s_max;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T* xw = xs + warp * d;
-  float* xwlo = xslo + warp * d;
   const T c = (T)c_exp;
   for (int q0 = 0; q0 < ss; q0 += qchunk) {
     const int qn = min(qchunk, ss - q0);
@@ -354,14 +348,11 @@ __global__ void __launch_bounds__(256) k_eval_vt(const double* __restrict__ X64,
       int k = e / qn, q = e % qn;
       int64_t src = (int64_t)sk[q0 + q] * d + k;
       yT[(size_t)k * qn + q] = sizeof(T) == 8 ? (T)X64[src] : (T)X32[src];
-      if (VT64 != nullptr) yTlo[(size_t)k * qn + q] = X32lo[src];
     }
     __syncthreads();
     for (int i = r0 + warp; i < r1; i += 8) {
-      for (int k = lane; k < d; k += 32) {
+      for (int k = lane; k < d; k += 32)
         xw[k] = sizeof(T) == 8 ? (T)X64[(int64_t)(b + i) * d + k] : (T)X32[(int64_t)(b + i) * d + k];
-        if (VT64 != nullptr) xwlo[k] = X32lo[(int64_t)(b + i) * d + k];
-      }
       __syncwarp();
       T* out = VT + (int64_t)(b + i) * s_max + q0;
       for (int q = lane; q < qn; q += 32) {
@@ -370,27 +361,16 @@ __global__ void __launch_bounds__(256) k_eval_vt(const double* __restrict__ X64,
           T t = xw[k] - yT[(size_t)k * qn + q];
           acc = fma(t, t, acc);
         }
-        T kv = sizeof(T) == 8 ? (T)exp((double)(acc * c)) : (T)__expf((float)(acc * c));
-        if (VT64 != nullptr) {  // FP64 operator copy: recompute the entries that matter in FP64
-          const int64_t row = b + i;
-          double k64 = (double)kv;
-          if ((float)kv >= 5.9604645e-8f) {
-            float ah, al;
-            kf_sqdist_df2((const float*)xw, xwlo, (const float*)yT + q, yTlo + q, qn, d, ah, al);
-            k64 = kf_kern_from_df(ah, al, ch, cl, tab);
-          }
-          VT64[row * s_max + q0 + q] = k64;
-          kv = (T)k64;
-        }
-        out[q] = kv;
+        out[q] = sizeof(T) == 8 ? (T)exp((double)(acc * c)) : (T)__expf((float)(acc * c));
       }
       __syncwarp();
     }
   }
 }
 
-// Mixed path: the same V blocks in FP32, plus (VT64 != nullptr) their FP64
-// operator copy, tiled 64 points x 64 skeleton columns per CTA with both
+// Mixed path: the same V blocks in FP32, plus (VTdf != nullptr) their FP64-
+// accurate operator copy as double-float pairs, tiled 64 points x 64 skeleton
+// columns per CTA with both
 // coordinate tiles (hi and lo halves) staged transposed in shared memory and
 // 4 x 4 entries per thread.  The FP32 value is exp(c |x - y|^2) of the FP32
 // coordinates (as k_eval_vt); entries at or above 2^-24 of the operator copy
@@ -401,7 +381,7 @@ __global__ void __launch_bounds__(256) k_eval_vt_tiled(const float* __restrict__
                                                        const int32_t* __restrict__ hi,
                                                        const int32_t* __restrict__ rank,
                                                        const int32_t* __restrict__ skel, int s_max, int node0,
-                                                       float* __restrict__ VT, double* __restrict__ VT64, float ch,
+                                                       float* __restrict__ VT, float2* __restrict__ VTdf, float ch,
                                                        float cl, const float2* __restrict__ tab) {
   extern __shared__ float vts[];  // x hi, x lo, y hi, y lo: d x 64 each
   const int nl = blockIdx.z, node = node0 + nl, sib = node ^ 1;
@@ -414,7 +394,7 @@ __global__ void __launch_bounds__(256) k_eval_vt_tiled(const float* __restrict__
   float* yh = xl + d * kVT;
   float* yl = yh + d * kVT;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const bool df = VT64 != nullptr;
+  const bool df = VTdf != nullptr;
   for (int e = tid; e < d * kVT; e += blockDim.x) {
     const int k = e % d, r = e / d;
     const int pi = r0 + r, pq = q0 + r;
@@ -482,10 +462,10 @@ __global__ void __launch_bounds__(256) k_eval_vt_tiled(const float* __restrict__
       if (q >= ss) continue;
       float kv = __expf(a32[a][c] * c32);
       if (df) {
-        double k64 = (double)kv;
-        if (kv >= 5.9604645e-8f) k64 = kf_kern_from_df(ah[a][c], al[a][c], ch, cl, tab);
-        VT64[row + q] = k64;
-        kv = (float)k64;
+        float2 kd = make_float2(kv, 0.f);
+        if (kv >= 5.9604645e-8f) kd = kf_kern_from_df(ah[a][c], al[a][c], ch, cl, tab);
+        VTdf[row + q] = kd;
+        kv = kd.x;  // hi is the pair rounded to FP32
       }
       VT[row + q] = kv;
     }
@@ -1020,8 +1000,8 @@ __global__ void __launch_bounds__(256) k_telescope(const int32_t* __restrict__ l
     }
 }
 
-// FP64 copy of the leaf kernel blocks (no lambda), both triangles, for the
-// FP64-accurate operator.  One CTA per 64 x 64 tile (I, J) of a leaf block
+// FP64-accurate copy of the leaf kernel blocks (no lambda) as double-float
+// pairs, both triangles, for the operator.  One CTA per 64 x 64 tile (I, J) of a leaf block
 // with I <= J, written to (I, J) and, transposed, to (J, I); the tile's
 // coordinates (double-float, hi + lo) are staged in shared memory, transposed
 // so that a thread's 4 rows and 4 columns are 4 consecutive words.  Entries
@@ -1030,7 +1010,7 @@ constexpr int kK64T = 64;
 __global__ void __launch_bounds__(256) k_leaf_k64(const float* __restrict__ X32lo, const float* __restrict__ X32,
                                                   int d, double c_exp, const int32_t* __restrict__ lo,
                                                   const int32_t* __restrict__ hi, int leaf0, int ldL,
-                                                  double* __restrict__ K64, float ch, float cl,
+                                                  float2* __restrict__ Kdf, float ch, float cl,
                                                   const float2* __restrict__ tab) {
   extern __shared__ float k64s[];  // 4 arrays of d x 64: x hi, x lo, y hi, y lo
   const int lf = blockIdx.y, node = leaf0 + lf;
@@ -1082,7 +1062,7 @@ __global__ void __launch_bounds__(256) k_leaf_k64(const float* __restrict__ X32l
       }
   }
   const float c32 = (float)c_exp;
-  double* Kb = K64 + (int64_t)lf * ldL * ldL;
+  float2* Kb = Kdf + (int64_t)lf * ldL * ldL;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -1090,7 +1070,7 @@ __global__ void __launch_bounds__(256) k_leaf_k64(const float* __restrict__ X32l
       const int i = I * kK64T + ty * 4 + a, j = J * kK64T + tx * 4 + c;
       if (i >= n || j >= n) continue;
       const float k32 = __expf(ah[a][c] * c32);
-      const double kv = k32 < 5.9604645e-8f ? (double)k32 : kf_kern_from_df(ah[a][c], al[a][c], ch, cl, tab);
+      const float2 kv = k32 < 5.9604645e-8f ? make_float2(k32, 0.f) : kf_kern_from_df(ah[a][c], al[a][c], ch, cl, tab);
       Kb[(int64_t)i * ldL + j] = kv;
       if (I != J) Kb[(int64_t)j * ldL + i] = kv;
     }
@@ -1108,7 +1088,7 @@ kf_status leaves_t(kf_factor* f, cudaStream_t s, bool with_k64) {
   const int leaf0 = 1 << D, nleaf = 1 << D;
   dim3 g((ldL + 127) / 128, ldL, nleaf);
   KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_assemble<T><<<g, 128, 0, s>>>(t->X64, t->X32, t->d, f->c_exp, f->lambda, t->d_lo, t->d_hi, leaf0, ldL, L));
-  if (f->K64 && with_k64) {
+  if (f->Kdf && with_k64) {
     kf_status r = kf_leaf_k64_launch(f, s);
     if (r != KF_OK) return r;
   }
@@ -1137,9 +1117,9 @@ kf_status level_eval_v(kf_factor* f, int l, cudaStream_t s) {
   const int vt_rows = 64;
   dim3 gv((unsigned)(((N >> (l + 1)) + vt_rows) / vt_rows), 2 * nn);
   // skeleton coordinates of up to qchunk columns per pass, at most 96 KiB of shared memory
-  const int64_t per = (int64_t)sizeof(T) + (f->VT64 ? (int64_t)sizeof(float) : 0);  // bytes per staged coordinate
-  const int qchunk = (int)std::max<int64_t>(1, std::min<int64_t>(s_max, (96 * 1024 / per - 8 * t->d) / t->d));
-  const size_t vt_smem = (size_t)per * ((size_t)t->d * qchunk + 8 * t->d);
+  // skeleton coordinates of up to qchunk columns per pass, at most 96 KiB of shared memory
+  const int qchunk = (int)std::max<int64_t>(1, std::min<int64_t>(s_max, (96 * 1024 / (int64_t)sizeof(T) - 8 * t->d) / t->d));
+  const size_t vt_smem = sizeof(T) * ((size_t)t->d * qchunk + 8 * t->d);
   if (sizeof(T) == 4) {  // mixed path: register-tiled FP32 (+ double-float) evaluation
     const size_t ts = sizeof(float) * 4 * (size_t)t->d * kVT;
     KF_CUDA(c, cudaFuncSetAttribute(k_eval_vt_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts));
@@ -1148,15 +1128,13 @@ kf_status level_eval_v(kf_factor* f, int l, cudaStream_t s) {
     KF_PHASE(KF_PH_EVAL_V, s, k_eval_vt_tiled<<<gt, 256, ts, s>>>(t->X32, t->X32lo, t->d, f->c_exp, t->d_lo, t->d_hi,
                                                                 f->rank, f->skel, s_max, child0,
                                                                 (float*)lvl(VT, l + 1),
-                                                                f->VT64 ? f->VT64 + (int64_t)l * N * s_max : nullptr,
+                                                                f->VTdf ? f->VTdf + (int64_t)l * N * s_max : nullptr,
                                                                 f->c_exp_hi, f->c_exp_lo, t->exp_tab));
   } else {
     KF_CUDA(c, cudaFuncSetAttribute(k_eval_vt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vt_smem));
-    KF_PHASE(KF_PH_EVAL_V, s, k_eval_vt<T><<<gv, 256, vt_smem, s>>>(t->X64, t->X32, t->X32lo, t->d, f->c_exp, t->d_lo, t->d_hi,
+    KF_PHASE(KF_PH_EVAL_V, s, k_eval_vt<T><<<gv, 256, vt_smem, s>>>(t->X64, t->X32, t->d, f->c_exp, t->d_lo, t->d_hi,
                                                                    f->rank, f->skel, s_max, child0, vt_rows, qchunk,
-                                                                   lvl(VT, l + 1),
-                                                                   f->VT64 ? f->VT64 + (int64_t)l * N * s_max : nullptr,
-                                                                   f->c_exp_hi, f->c_exp_lo, t->exp_tab));
+                                                                   lvl(VT, l + 1)));
   }
   KF_LAUNCH_CHECK(c);
   return KF_OK;
@@ -1252,7 +1230,7 @@ kf_status kf_leaf_k64_launch(kf_factor* f, cudaStream_t s) {
   KF_CUDA(f->ctx, cudaFuncSetAttribute(k_leaf_k64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 g((unsigned)(nt * (nt + 1) / 2), 1u << t->D);
   KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_k64<<<g, 256, smem, s>>>(t->X32lo, t->X32, t->d, f->c_exp, t->d_lo, t->d_hi,
-                                                              1 << t->D, t->leaf_max, f->K64, f->c_exp_hi,
+                                                              1 << t->D, t->leaf_max, f->Kdf, f->c_exp_hi,
                                                               f->c_exp_lo, t->exp_tab));
   KF_LAUNCH_CHECK(f->ctx);
   return KF_OK;
@@ -1323,7 +1301,7 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
     cudaStreamWaitEvent(s2, ev[0], 0);
     cudaStreamWaitEvent(s3, ev[0], 0);
     // the FP64 operator's leaf blocks need the tree only
-    if (f->K64) st = kf_leaf_k64_launch(f, s3);
+    if (f->Kdf) st = kf_leaf_k64_launch(f, s3);
     for (int l = D; l >= 1 && st == KF_OK; --l) {
       st = kf_skel_level(f, l, &sc, s1);
       cudaEventRecord(ev[l], s1);

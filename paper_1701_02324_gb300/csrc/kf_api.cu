@@ -286,9 +286,9 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
   }
   f->L = falloc<char>(f, (size_t)(1 << D) * t->leaf_max * t->leaf_max * ts, s);
   if (f->fp64_op) {
-    f->K64 = falloc<double>(f, (size_t)(1 << D) * t->leaf_max * t->leaf_max, s);
-    if (D > 0 && f->prec != KF_PREC_FP64) f->VT64 = falloc<double>(f, (size_t)D * N * s_max, s);
-    if (!f->K64 || (D > 0 && f->prec != KF_PREC_FP64 && !f->VT64)) {
+    f->Kdf = falloc<float2>(f, (size_t)(1 << D) * t->leaf_max * t->leaf_max, s);
+    if (D > 0 && f->prec != KF_PREC_FP64) f->VTdf = falloc<float2>(f, (size_t)D * N * s_max, s);
+    if (!f->Kdf || (D > 0 && f->prec != KF_PREC_FP64 && !f->VTdf)) {
       kf_factor_free(f);
       return kf_set_err(c, KF_ENOMEM, "factorize: device allocation of the FP64 operator failed");
     }

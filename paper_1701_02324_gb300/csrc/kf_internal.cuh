@@ -60,11 +60,12 @@ struct kf_factor {
   int32_t use_tc = 1;  // mixed path: tcgen05 products (0: CUDA-core FP32)
   int32_t use_cluster_qr = 1;  // upper tree levels: cluster QR in distributed shared memory
   int32_t use_cluster_lu = 1;  // upper tree levels: reduced-system LU and T on a CTA cluster per node
-  int32_t fp64_op = 0;  // keep FP64 operator data (VT64, K64)
+  int32_t fp64_op = 0;  // keep the FP64-accurate operator data (VTdf, Kdf)
   int32_t gmres_m = 0;  // refinement: 0 = Richardson, m > 0 = GMRES(m)
   int32_t refine_user = 0;  // refinement explicitly requested (enables it on the FP64 path)
-  double* VT64 = nullptr;  // mixed path with fp64_op: D x N x s_max FP64 V blocks
-  double* K64 = nullptr;   // fp64_op: leaf blocks lambda-free K_aa, leaf_max^2 each
+  // FP64-accurate operator (fp64_op), stored as double-float pairs (hi, lo):
+  float2* VTdf = nullptr;  // mixed path: D x N x s_max V blocks
+  float2* Kdf = nullptr;   // leaf blocks lambda-free K_aa, leaf_max^2 each
   double refine_tol = 1e-10;
   int32_t refine_max_iter = 8;
   uint64_t seed = 0x1701;
@@ -151,7 +152,7 @@ __device__ __forceinline__ void kf_fast_two_sum(float a, float b, float& s, floa
 // significant bits, so n L1 is exact for |n| < 4096) + L2 + L3;
 // exp(y) = 2^(n >> 6) 2^((n & 63)/64) (1 + q), q = r + r^2/2 + ... + r^5/120
 // (the r^6 term is below 4e-17).  tab[j] = 2^(j/64) as a double-float pair.
-__device__ __forceinline__ double kf_exp_df(float yh, float yl, const float2* __restrict__ tab) {
+__device__ __forceinline__ float2 kf_exp_df(float yh, float yl, const float2* __restrict__ tab) {
   const float kInvL = 0x1.715476p+6f;  // 64 / ln 2
   const float L1 = 0x1.62ep-7f, L2 = 0x1.0bfbe8p-21f, L3 = 0x1.cf79acp-46f;
   const float n = rintf(__fmul_rn(yh, kInvL));
@@ -179,7 +180,7 @@ __device__ __forceinline__ double kf_exp_df(float yh, float yl, const float2* __
   float hi, lo;
   kf_fast_two_sum(v, ve, hi, lo);
   const float sc = __int_as_float(((ni >> 6) + 127) << 23);  // 2^(n >> 6), exact
-  return (double)__fmul_rn(hi, sc) + (double)__fmul_rn(lo, sc);
+  return make_float2(__fmul_rn(hi, sc), __fmul_rn(lo, sc));
 }
 
 // squared distance as a double-float pair (ah, al); y's coordinates are ys apart
@@ -202,39 +203,39 @@ __device__ __forceinline__ void kf_sqdist_df2(const float* __restrict__ xh, cons
   }
 }
 
-// Kernel entry exp(c |x - y|^2) to about 2^-46 relative with no FP64
-// arithmetic but the final conversion, from the squared distance ah + al and
-// c = ch + cl (kf_kern_df: from coordinates held as double-float pairs, X32 +
-// X32lo).  Arguments below -20 (entries below 2e-9) take the FP32
-// exponential, whose absolute error there is below 1e-16.
-__device__ __forceinline__ double kf_kern_from_df(float ah, float al, float ch, float cl,
+// Kernel entry exp(c |x - y|^2) as a double-float pair, to about 2^-46
+// relative with no FP64 arithmetic, from the squared distance ah + al
+// (kf_sqdist_df2 of coordinates held as pairs X32 + X32lo) and c = ch + cl.
+// Arguments below -20 (entries below 2e-9) take the FP32 exponential, whose
+// absolute error there is below 1e-16.
+__device__ __forceinline__ float2 kf_kern_from_df(float ah, float al, float ch, float cl,
                                                   const float2* __restrict__ tab) {
   float y, ye;
   kf_two_prod(ah, ch, y, ye);
   ye = fmaf(ah, cl, fmaf(al, ch, ye));
   float zh, zl;
   kf_fast_two_sum(y, ye, zh, zl);
-  if (zh < -20.f) return (double)__expf(zh);
+  if (zh < -20.f) return make_float2(__expf(zh), 0.f);
   return kf_exp_df(zh, zl, tab);
 }
 
-__device__ __forceinline__ double kf_kern_df(const float* __restrict__ xh, const float* __restrict__ xl,
-                                             const float* __restrict__ yh, const float* __restrict__ yl, int d,
-                                             float ch, float cl, const float2* __restrict__ tab) {
-  float ah, al;
-  kf_sqdist_df2(xh, xl, yh, yl, 1, d, ah, al);
-  return kf_kern_from_df(ah, al, ch, cl, tab);
+// (sh, sl) += (ah + al)(bh + bl) in double-float arithmetic (about 2^-46 relative)
+__device__ __forceinline__ void kf_df_fma(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  float p, e, s, t;
+  kf_two_prod(ah, bh, p, e);
+  e = fmaf(ah, bl, fmaf(al, bh, e));
+  kf_two_sum(sh, p, s, t);
+  t = __fadd_rn(t, __fadd_rn(sl, e));
+  kf_fast_two_sum(s, t, sh, sl);
 }
 
-// FP64-accurate kernel entry at FP32 cost for the small ones: entries below
-// 2^-24 are taken from the FP32 evaluation (their absolute error stays below
-// about 1e-14); larger ones take the double-float evaluation.
-__device__ __forceinline__ double kf_kern_hybrid(const float* X32, const float* X32lo, int64_t i, int64_t j, int d,
-                                                 double c_exp, float ch, float cl, const float2* tab) {
-  const float k32 = kf_kern32(X32 + i * d, X32 + j * d, d, (float)c_exp);
-  if (k32 < 5.9604645e-8f) return (double)k32;
-  return kf_kern_df(X32 + i * d, X32lo + i * d, X32 + j * d, X32lo + j * d, d, ch, cl, tab);
+// a double as a double-float pair (two conversions, off the hot loops)
+__device__ __forceinline__ float2 kf_split_df(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
 }
+
+
 
 template <typename T> struct kf_kern;
 template <> struct kf_kern<double> {

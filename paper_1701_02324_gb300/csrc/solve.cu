@@ -485,22 +485,85 @@ __global__ void __launch_bounds__(128) k_leaf_mv(const int32_t* __restrict__ lo,
   }
 }
 
-// Leaf blocks from the stored FP64 copy: y_i = lambda x_i + sum_j K64[i][j] x_j,
-// one warp per row, lanes over j.
-__global__ void __launch_bounds__(256) k_leaf_mv_stored(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
-                                                        int leaf0, int ldL, const double* __restrict__ K64,
-                                                        double lambda, const double* __restrict__ x,
-                                                        double* __restrict__ y, int k) {
+// Leaf blocks from the stored FP64-accurate copy (double-float pairs):
+// y_i = lambda x_i + sum_j K[i][j] x_j, the products and sums in double-float
+// arithmetic on the FP32 pipes.  The leaf's x is split into pairs once per
+// CTA in shared memory; one warp per row, lanes over j.
+__global__ void __launch_bounds__(256) k_leaf_mv_df(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                    int leaf0, int ldL, const float2* __restrict__ Kdf,
+                                                    double lambda, const double* __restrict__ x,
+                                                    double* __restrict__ y, int k, int r) {
+  extern __shared__ float2 xs[];  // n
   const int lf = blockIdx.y, node = leaf0 + lf;
   const int b = lo[node], n = hi[node] - b;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) xs[j] = kf_split_df(x[(int64_t)(b + j) * k + r]);
+  __syncthreads();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   for (int i = warp; i < n; i += (gridDim.x * blockDim.x) >> 5) {
-    const double* Ki = K64 + ((int64_t)lf * ldL + i) * ldL;
-    for (int r = 0; r < k; ++r) {
-      double acc = 0.0;
-      for (int j = lane; j < n; j += 32) acc = fma(Ki[j], x[(int64_t)(b + j) * k + r], acc);
-      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-      if (lane == 0) y[(int64_t)(b + i) * k + r] = lambda * x[(int64_t)(b + i) * k + r] + acc;
+    const float2* Ki = Kdf + ((int64_t)lf * ldL + i) * ldL;
+    float sh = 0.f, sl = 0.f;
+    for (int j = lane; j < n; j += 32) {
+      const float2 m = Ki[j], v = xs[j];
+      kf_df_fma(m.x, m.y, v.x, v.y, sh, sl);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, sh, off), ol = __shfl_xor_sync(0xffffffffu, sl, off);
+      float t, e;
+      kf_two_sum(sh, oh, t, e);
+      e = __fadd_rn(e, __fadd_rn(sl, ol));
+      kf_fast_two_sum(t, e, sh, sl);
+    }
+    if (lane == 0) y[(int64_t)(b + i) * k + r] = lambda * x[(int64_t)(b + i) * k + r] + ((double)sh + (double)sl);
+  }
+}
+
+// V pass of the FP64-accurate operator: u[sib][q][r] += sum_i V[i][q] w[i][r]
+// over the rows of every node of a level, V as double-float pairs, in
+// double-float arithmetic on the FP32 pipes (the same partition as k_colsum,
+// one thread per skeleton column, the chunk's w split into pairs in shared
+// memory, 8 rows' loads in flight).
+template <int KB>
+__global__ void __launch_bounds__(256) k_colsum_df(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                   const int32_t* __restrict__ rank, int node0, int s_max,
+                                                   const float2* __restrict__ M, const double* __restrict__ W, int k,
+                                                   double* __restrict__ U) {
+  __shared__ float2 ws[kRowsPerChunk][KB];
+  const int nl = blockIdx.y, node = node0 + nl, sib = node ^ 1;
+  const int b = lo[node], n = hi[node] - b;
+  const int cnt = rank[sib];
+  const int r0 = blockIdx.x * kRowsPerChunk;
+  if (r0 >= n || cnt == 0) return;
+  const int r1 = min(n, r0 + kRowsPerChunk), nr = r1 - r0;
+  for (int kb = 0; kb < k; kb += KB) {
+    const int kk = min(KB, k - kb);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * KB; e += blockDim.x) {
+      const int i = e / KB, c = e % KB;
+      ws[i][c] = c < kk ? kf_split_df(W[(int64_t)(b + r0 + i) * k + kb + c]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+      float sh[KB], sl[KB];
+#pragma unroll
+      for (int c = 0; c < KB; ++c) sh[c] = sl[c] = 0.f;
+      const float2* Mq = M + (int64_t)(b + r0) * s_max + q;
+      int i = 0;
+      for (; i + 8 <= nr; i += 8) {
+        float2 m[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) m[u] = Mq[(int64_t)(i + u) * s_max];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int c = 0; c < KB; ++c) kf_df_fma(m[u].x, m[u].y, ws[i + u][c].x, ws[i + u][c].y, sh[c], sl[c]);
+      }
+      for (; i < nr; ++i) {
+        const float2 m = Mq[(int64_t)i * s_max];
+#pragma unroll
+        for (int c = 0; c < KB; ++c) kf_df_fma(m.x, m.y, ws[i][c].x, ws[i][c].y, sh[c], sl[c]);
+      }
+      double* out = U + ((int64_t)sib * s_max + q) * k + kb;
+      for (int c = 0; c < kk; ++c) atomicAdd(out + c, (double)sh[c] + (double)sl[c]);
     }
   }
 }
@@ -595,10 +658,13 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
   const int leaf0 = 1 << D;
   const double inv_h3 = 1.0 / (f->h * f->h * f->h);
   const int src = deriv ? SRC_DKERNEL : (f->vstore == KF_V_STORED ? SRC_STORED : SRC_KERNEL);
-  if (f->K64 && !deriv) {
+  if (f->Kdf && !deriv) {
     dim3 gl((unsigned)std::max(1, std::min(64, (t->leaf_max * 32 + 255) / 256)), 1 << D);
-    KF_PHASE(KF_PH_MV_LEAF, s, k_leaf_mv_stored<<<gl, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, f->K64, f->lambda,
-                                                                  x, y, (int)k));
+    const size_t xsm = sizeof(float2) * t->leaf_max;
+    KF_CUDA(c, cudaFuncSetAttribute(k_leaf_mv_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
+    for (int r = 0; r < k; ++r)
+      KF_PHASE(KF_PH_MV_LEAF, s, k_leaf_mv_df<<<gl, 256, xsm, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, f->Kdf,
+                                                                  f->lambda, x, y, (int)k, r));
   } else {
     dim3 gl((t->leaf_max + 127) / 128, 1 << D);
     KF_PHASE(KF_PH_MV_LEAF, s, k_leaf_mv<TM><<<gl, 128, 0, s>>>(t->d_lo, t->d_hi, leaf0, t->X64, t->X32, t->d, f->c_exp, inv_h3,
@@ -609,11 +675,15 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
   for (int l = 1; l <= D; ++l) {
     const int64_t rows = (N >> l) + 1;
     dim3 gc((unsigned)((rows + kRowsPerChunk - 1) / kRowsPerChunk), 1 << l);
-    if (f->VT64 && !deriv)  // FP64-accurate operator of the mixed path
-      launch_colsum<double, double>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, s_max, 1, SRC_STORED,
-                                    f->VT64 + (int64_t)(l - 1) * N * s_max, t->X64, t->X32, t->d, f->c_exp, inv_h3, x,
-                                    (int)k, G, KF_PH_MV_COLSUM);
-    else
+    if (f->VTdf && !deriv) {  // FP64-accurate operator of the mixed path
+      const float2* Vl = f->VTdf + (int64_t)(l - 1) * N * s_max;
+      if (k == 1)
+        KF_PHASE(KF_PH_MV_COLSUM, s, k_colsum_df<1><<<gc, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, 1 << l, s_max, Vl, x,
+                                                                        (int)k, G));
+      else
+        KF_PHASE(KF_PH_MV_COLSUM, s, k_colsum_df<4><<<gc, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, 1 << l, s_max, Vl, x,
+                                                                        (int)k, G));
+    } else
       launch_colsum<TM, double>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, s_max, 1, src,
                                 VT + (int64_t)(l - 1) * N * s_max, t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G,
                                 KF_PH_MV_COLSUM);
