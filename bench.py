@@ -335,6 +335,19 @@ def gpu_main(args, rank, world):
             torch.distributed.barrier()
 
     gmres_iters = []
+    # kernel variants picked by the library's autotuner on this workload
+    # (untimed; the timed steps then use them, as a user would)
+    tuned = {}
+    if not args.no_autotune:
+        tree_t = kf.Tree(X, p.m)
+        for prec in (kf.KF_PREC_MIXED, kf.KF_PREC_FP64):
+            if prec == kf.KF_PREC_FP64 and args.no_fp64:
+                continue
+            ch, ms = kf.autotune(tree_t, p.h, p.lam, p.tau, p.s_max, precision=prec,
+                                 fp64_operator=(prec == kf.KF_PREC_MIXED))
+            tuned[prec] = (ch, ms)
+        del tree_t
+    opt = lambda prec: tuned[prec][0] if prec in tuned else {}
 
     def step(prec, refined=None):
         """tree + factorize + solve.  Mixed path: FP64 operator kept and the
@@ -345,14 +358,15 @@ def gpu_main(args, rank, world):
         tree = kf.Tree(X, p.m)
         if prec == kf.KF_PREC_MIXED and refined is not False:
             F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=prec, fp64_operator=True,
-                          refine_tol=args.mixed_tol, refine_max_iter=400, gmres_restart=args.gmres_m, sync_errors=False)
+                          refine_tol=args.mixed_tol, refine_max_iter=400, gmres_restart=args.gmres_m, sync_errors=False,
+                          **opt(prec))
             ev = torch.cuda.Event(enable_timing=True)
             ev.record()
             x, inf = F.solve(b, info=True)
             gmres_iters.append(inf["iters"])
             return tree, F, ev, x
         F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=prec, fp64_operator=False, refine_max_iter=-1,
-                      sync_errors=False)
+                      sync_errors=False, **opt(prec))
         ev = torch.cuda.Event(enable_timing=True)
         ev.record()
         x = F.solve(b)
@@ -455,7 +469,8 @@ def gpu_main(args, rank, world):
             t0 = time.perf_counter()
             tree = kf.Tree(torch.from_numpy(X_host), p.m)                  # host X: H2D inside
             F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=kf.KF_PREC_MIXED, fp64_operator=True,
-                          refine_tol=args.mixed_tol, refine_max_iter=400, gmres_restart=args.gmres_m, sync_errors=False)
+                          refine_tol=args.mixed_tol, refine_max_iter=400, gmres_restart=args.gmres_m, sync_errors=False,
+                          **opt(kf.KF_PREC_MIXED))
             xt = F.solve(torch.from_numpy(b_host))                         # host b -> host x
             xh[:] = xt.numpy()
             lib_t.append(time.perf_counter() - t0)
@@ -463,6 +478,57 @@ def gpu_main(args, rank, world):
         e2e = {"value": round(statistics.mean(lib_t), 4), "unit": "s",
                "h2d_bytes_per_step": int(X_host.nbytes + b_host.nbytes), "d2h_bytes_per_step": int(xh.nbytes),
                "note": "wall time of tree + factorize + solve with host X, b and x (copies inside)"}
+
+    # ---- batched workload: 256 uneven problems, 64 RHS each, one graph launch each ----
+    batched = None
+    if not args.no_batched:
+        probs = inputs.batched(args.batched_n, 64)
+        trees_b = [kf.Tree(torch.from_numpy(q.X).to(dev), q.m) for q in probs]
+        Bb = [torch.from_numpy(q.B).to(dev) for q in probs]
+        hs, lams, taus = [q.h for q in probs], [q.lam for q in probs], [q.tau for q in probs]
+        # kernel variants of the batch picked by the autotuner on its median-size problem (untimed)
+        im = int(np.argsort([q.X.shape[0] for q in probs])[len(probs) // 2])
+        tuned_b, tune_ms = kf.autotune(trees_b[im], hs[im], lams[im], taus[im], probs[im].s_max,
+                                       precision=kf.KF_PREC_MIXED)
+        tuned_b64, tune_ms64 = kf.autotune(trees_b[im], hs[im], lams[im], taus[im], probs[im].s_max,
+                                           precision=kf.KF_PREC_FP64)
+        def run_batched(prec):
+            fb_ms, sb_ms = [], []
+            for it in range(3):  # one warm-up pass, two timed
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e2 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                facs = kf.factorize_batched(trees_b, hs, lams, taus, probs[0].s_max, precision=prec,
+                                            **(tuned_b if prec == kf.KF_PREC_MIXED else tuned_b64))
+                e1.record()
+                xs = kf.solve_batched(facs, Bb)
+                e2.record()
+                torch.cuda.synchronize()
+                if it > 0:
+                    fb_ms.append(e0.elapsed_time(e1))
+                    sb_ms.append(e1.elapsed_time(e2))
+                del facs
+            return statistics.mean(fb_ms) / 1e3, statistics.mean(sb_ms) / 1e3, xs
+
+        fb, sb, xs = run_batched(kf.KF_PREC_MIXED)
+        fb64, sb64, xs64 = run_batched(kf.KF_PREC_FP64)
+        errs = [float(torch.linalg.norm(a - c) / torch.linalg.norm(c)) for a, c in zip(xs, xs64)]
+        npts = sum(q.X.shape[0] for q in probs)
+        nr = len(probs) * 64
+        batched = {"workload": f"batched_{len(probs)}_problems", "problems": len(probs), "points": int(npts),
+                   "nrhs_each": 64,
+                   "mixed": {"factorize_s": round(fb, 4), "solve_s": round(sb, 4), "rhs_per_s": round(nr / sb, 1),
+                             "rel_err_vs_fp64": {"median": float(np.median(errs)), "max": float(np.max(errs)),
+                                                 "problems_above_1e-5": int(sum(e > 1e-5 for e in errs))}},
+                   "fp64": {"factorize_s": round(fb64, 4), "solve_s": round(sb64, 4), "rhs_per_s": round(nr / sb64, 1)},
+                   "autotuned": {"chosen": tuned_b, "candidate_ms": [round(t, 3) for t in tune_ms],
+                                 "fp64_chosen": tuned_b64, "fp64_candidate_ms": [round(t, 3) for t in tune_ms64],
+                                 "candidates": "clusters x (tcgen05 256, tcgen05 128, CUDA cores), then one CTA "
+                                               "per node x the same"},
+                   "note": "factorize_batched and solve_batched (one CUDA-graph launch each), direct sweeps; the "
+                           "mixed error is per problem against the FP64 path's solution"}
+        del xs, xs64, trees_b, Bb
 
     # ---- differentiation workload (N=2^18, d=54): factorize, solve, gradient ----------
     diff = None
@@ -553,10 +619,13 @@ def gpu_main(args, rank, world):
             "solve_note": f"mixed solve = direct sweep of the FP32 factors + GMRES({args.gmres_m}) against the FP64 operator "
                           f"to eps_r <= {args.mixed_tol:g}",
             "gmres_iters": float(np.mean(gmres_iters[-args.steps:])) if gmres_iters else None,
+            "autotuned": {("mixed" if k == kf.KF_PREC_MIXED else "fp64"): {"chosen": v[0],
+                          "candidate_ms": [round(t, 2) for t in v[1]]} for k, v in tuned.items()} or None,
             "mixed_rel_err_vs_reference": mixed_rel if fp64 else None,
             "fp64_path": fp64,
             "mixed_unrefined": unref,
             "differentiation": diff,
+            "batched": batched,
             "accuracy_reference": reference if fp64 else None,
             "ranks": {"mean": float(np.mean(ranks[2:])), "max": int(np.max(ranks))},
             "roofline": roof,
@@ -606,6 +675,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="default kernel variants instead of kf_autotune's")
+    ap.add_argument("--batched-n", type=int, default=256, help="problems of the batched workload")
     ap.add_argument("--once", action="store_true",
                     help="one tree + factorize + solve of the scale recipe and exit (for profilers)")
     ap.add_argument("--n", type=int, default=1 << 20, help="number of points of the scale recipe")

@@ -97,7 +97,8 @@ typedef struct {
                              right-preconditioned by the factorization; -1 = x += M^-1 r */
   int32_t no_cluster_kernels; /* 1 = one CTA per node everywhere (no thread-block clusters for the
                              pivoted QR and reduced-system LU of the upper tree levels) */
-  int32_t reserved[4];
+  int32_t tc_tile_n;      /* mixed path: tile width of the tcgen05 products, 128 or 256 (0 = 256) */
+  int32_t reserved[3];
 } kf_opts;
 
 /* Filled by kf_solve when non-NULL (synchronizes the stream). */
@@ -238,6 +239,22 @@ kf_status kf_factorize_with_ids(kf_tree* t, double h, double lambda, int32_t s_m
  * `stream` once to read the finiteness check of X. */
 kf_status kf_tree_perm_noalloc(const double* X, int64_t N, int32_t d, int32_t m, double* Xt, int64_t* perm,
                                void* stream);
+
+/* Kernel-variant autotuner (no counterpart in the paper; an implementation
+ * knob).  Factorizes the given problem once per candidate and keeps the
+ * fastest: one CTA per node or thread-block clusters for the upper tree levels
+ * (no_cluster_kernels), and on the mixed path CUDA-core or tcgen05 products
+ * (no_tensor_cores) with tcgen05 tiles of 256 or 128 columns (tc_tile_n).
+ * After one untimed factorization with `base`, each candidate is timed with
+ * CUDA events on `stream` (two factorizations, the faster counts).  `best`
+ * receives `base` with the fastest choice; ms (nullable, KF_AUTOTUNE_MAX
+ * entries) the candidates' times in milliseconds in the order above, and
+ * *ncand (nullable) their number.  The choice changes no result beyond
+ * rounding (the skeletons come from the same FP64 QR).  Synchronizes
+ * `stream`.  Errors: those of kf_factorize. */
+#define KF_AUTOTUNE_MAX 8
+kf_status kf_autotune(kf_tree* t, double h, double lambda, double tau, int32_t s_max, const kf_opts* base,
+                      void* stream, kf_opts* best, float* ms, int32_t* ncand);
 
 /* ---- diagnostics ------------------------------------------------------------- */
 /* Number of kernel launches this process has made through the library. */

@@ -24,7 +24,7 @@ from ._abi import (KF_F32, KF_F64, KF_PREC_FP64, KF_PREC_MIXED, KF_V_RECOMPUTE, 
 __all__ = [
     "build", "Context", "Tree", "Factor", "tree_build", "factorize", "factorize_with_ids", "solve", "matvec",
     "grad", "tree_free", "factor_free", "KernelSolve", "KF_PREC_FP64", "KF_PREC_MIXED", "KF_V_STORED",
-    "KF_V_RECOMPUTE", "KFError", "factorize_batched", "solve_batched",
+    "KF_V_RECOMPUTE", "KFError", "factorize_batched", "solve_batched", "autotune",
 ]
 
 
@@ -171,9 +171,11 @@ class Tree:
 
 
 def _opts(precision=KF_PREC_FP64, n_samp=0, seed=0, v_storage=KF_V_STORED, sync_errors=0, refine_tol=0.0,
-          refine_max_iter=0, tensor_cores=True, fp64_operator=None, gmres_restart=0, cluster_kernels=True):
+          refine_max_iter=0, tensor_cores=True, fp64_operator=None, gmres_restart=0, cluster_kernels=True,
+          tc_tile_n=0):
     o = kf_opts()
     o.no_cluster_kernels = 0 if cluster_kernels else 1
+    o.tc_tile_n = int(tc_tile_n)
     o.no_tensor_cores = 0 if tensor_cores else 1
     o.fp64_operator = 0 if fp64_operator is None else (1 if fp64_operator is True else
                                                        (-1 if fp64_operator is False else int(fp64_operator)))
@@ -189,11 +191,12 @@ class Factor:
     def __init__(self, tree: Tree, h: float, lam: float, tau: float, s_max: int, precision=KF_PREC_FP64,
                  n_samp: int = 0, seed: int = 0, v_storage=KF_V_STORED, refine_tol: float = 0.0,
                  refine_max_iter: int = 0, sync_errors: bool = True, tensor_cores: bool = True,
-                 fp64_operator=None, gmres_restart: int = 0, cluster_kernels: bool = True, _ids=None):
+                 fp64_operator=None, gmres_restart: int = 0, cluster_kernels: bool = True, tc_tile_n: int = 0,
+                 _ids=None):
         self.tree, self.ctx = tree, tree.ctx
         self.h_, self.lam, self.tau, self.s_max, self.precision = float(h), float(lam), float(tau), int(s_max), precision
         o = _opts(precision, n_samp, seed, v_storage, int(sync_errors), refine_tol, refine_max_iter, tensor_cores,
-                  fp64_operator, gmres_restart, cluster_kernels)
+                  fp64_operator, gmres_restart, cluster_kernels, tc_tile_n)
         h_out = ctypes.c_void_p()
         if _ids is None:
             st = self.ctx.lib.kf_factorize(tree.h, self.h_, self.lam, self.tau, self.s_max, ctypes.byref(o),
@@ -336,7 +339,24 @@ def _ptr_array(vals):
     return arr
 
 
-def factorize_batched(trees, hs, lams, taus, s_max: int, precision=KF_PREC_MIXED, n_samp: int = 0, seed: int = 0):
+def autotune(tree: Tree, h: float, lam: float, tau: float, s_max: int, precision=KF_PREC_MIXED, **kw):
+    """Pick the kernel variants for factorizations like this one
+    (kf_autotune): returns the fastest candidate's keyword options for
+    Factor / factorize_batched, and every candidate's time in ms."""
+    o = _opts(precision, kw.get("n_samp", 0), kw.get("seed", 0), KF_V_STORED, 0, 0.0, -1,
+              fp64_operator=kw.get("fp64_operator"))
+    best = kf_opts()
+    ms = (ctypes.c_float * 8)()
+    nc = ctypes.c_int32()
+    tree.ctx.check(tree.ctx.lib.kf_autotune(tree.h, float(h), float(lam), float(tau), int(s_max), ctypes.byref(o),
+                                            _stream_ptr(), ctypes.byref(best), ms, ctypes.byref(nc)))
+    chosen = {"cluster_kernels": not best.no_cluster_kernels, "tensor_cores": not best.no_tensor_cores,
+              "tc_tile_n": int(best.tc_tile_n)}
+    return chosen, [float(ms[i]) for i in range(nc.value)]
+
+
+def factorize_batched(trees, hs, lams, taus, s_max: int, precision=KF_PREC_MIXED, n_samp: int = 0, seed: int = 0,
+                      **kw):
     """Factorize many independent problems with one CUDA-graph launch
     (kf_factorize_batched).  Returns a list of Factor objects."""
     import numpy as np
@@ -345,7 +365,8 @@ def factorize_batched(trees, hs, lams, taus, s_max: int, precision=KF_PREC_MIXED
     h = np.ascontiguousarray(hs, dtype=np.float64)
     lam = np.ascontiguousarray(lams, dtype=np.float64)
     tau = np.ascontiguousarray(taus, dtype=np.float64)
-    o = _opts(precision, n_samp, seed, KF_V_STORED, 0, 0.0, -1)
+    o = _opts(precision, n_samp, seed, KF_V_STORED, 0, 0.0, -1, tensor_cores=kw.get("tensor_cores", True),
+              cluster_kernels=kw.get("cluster_kernels", True), tc_tile_n=kw.get("tc_tile_n", 0))
     out = (ctypes.c_void_p * n)()
     tarr = _ptr_array([t.h.value for t in trees])
     st = ctx.lib.kf_factorize_batched(tarr, n, h.ctypes.data_as(ctypes.c_void_p), lam.ctypes.data_as(ctypes.c_void_p),

@@ -33,7 +33,8 @@ class kf_opts(ctypes.Structure):
         ("fp64_operator", ctypes.c_int32),
         ("gmres_restart", ctypes.c_int32),
         ("no_cluster_kernels", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("tc_tile_n", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -65,6 +66,7 @@ SIGNATURES = {
     "kf_tree_perm_noalloc": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
     "kf_factorize_batched": (_I32, [_P, _I32, _P, _P, _P, _I32, _P, _P, _P]),
     "kf_solve_batched": (_I32, [_P, _I32, _P, _P, _P, _P, _I32, _P]),
+    "kf_autotune": (_I32, [_P, _D, _D, _D, _I32, _P, _P, _P, _P, _P]),
     "kf_launch_count": (_I64, []),
     "kf_profile_enable": (_I32, [_I32]),
     "kf_profile_read": (_I32, [_P, _P, _I32]),

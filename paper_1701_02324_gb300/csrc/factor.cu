@@ -20,10 +20,10 @@
 
 kf_status kf_tc_zoff(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
                      const float* VT, const float* Ph, int ldz, double* Z, int64_t rows_per_child, int32_t* status,
-                     cudaStream_t s);
+                     cudaStream_t s, int tile_n);
 kf_status kf_tc_telescope(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
                           const float* Pc_hat, const float* Tm, int ldz, float* Pa_hat, int64_t rows_per_child,
-                          int32_t* status, cudaStream_t s);
+                          int32_t* status, cudaStream_t s, int tile_n);
 
 namespace {
 
@@ -1159,7 +1159,7 @@ kf_status level_reduce(kf_factor* f, int l, double* Tm, cudaStream_t s) {
   int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(rows / 512, (152 * 8) / std::max(1, 2 * nn * tiles) + 1));
   if (sizeof(T) == 4 && f->use_tc) {
     kf_status r = kf_tc_zoff(t->d_lo, t->d_hi, f->rank, node0, nn, s_max, (const float*)lvl(VT, l + 1),
-                             (const float*)lvl(Phat, l + 1), ldz, f->ZLU, rows, f->status, s);
+                             (const float*)lvl(Phat, l + 1), ldz, f->ZLU, rows, f->status, s, f->tc_bn);
     if (r != KF_OK) return kf_set_err(c, r, "tensor-core Z blocks failed at level %d", l);
   } else {
     KF_PHASE(KF_PH_ZOFF, s, k_zoff<T><<<dim3(tiles, ksplit, 2 * nn), 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, node0, s_max, lvl(VT, l + 1),
@@ -1199,7 +1199,7 @@ kf_status level_reduce(kf_factor* f, int l, double* Tm, cudaStream_t s) {
     dim3 gt((unsigned)((cmax_rows + 63) / 64), (s_max + 63) / 64, 2 * nn);
     if (sizeof(T) == 4 && f->use_tc) {
       kf_status r = kf_tc_telescope(t->d_lo, t->d_hi, f->rank, node0, nn, s_max, (const float*)lvl(Phat, l + 1), Tm32,
-                                    ldz, (float*)lvl(Phat, l), cmax_rows, f->status, s);
+                                    ldz, (float*)lvl(Phat, l), cmax_rows, f->status, s, f->tc_bn);
       if (r != KF_OK) return kf_set_err(c, r, "tensor-core telescoping failed at level %d", l);
     } else {
       KF_PHASE(KF_PH_TELESCOPE, s, k_telescope<T><<<gt, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, node0, s_max, lvl(Phat, l + 1), Tm, ldz,

@@ -254,6 +254,11 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
     if (opts->fp64_operator != 0) f->fp64_op = opts->fp64_operator > 0 ? 1 : 0;
     if (opts->gmres_restart != 0) f->gmres_m = opts->gmres_restart > 0 ? std::min(opts->gmres_restart, 64) : 0;
     if (opts->no_cluster_kernels) f->use_cluster_qr = f->use_cluster_lu = 0;
+    if (opts->tc_tile_n == 128) f->tc_bn = 128;
+    else if (opts->tc_tile_n != 0 && opts->tc_tile_n != 256) {
+      delete f;
+      return kf_set_err(c, KF_EINVAL, "tc_tile_n must be 128 or 256");
+    }
   }
   if (f->prec != KF_PREC_FP64 && f->prec != KF_PREC_MIXED) {
     delete f;
@@ -494,6 +499,66 @@ kf_status kf_factorize(kf_tree* t, double h, double lambda, double tau, int32_t 
   }
   *out = f;
   return st;
+}
+
+kf_status kf_autotune(kf_tree* t, double h, double lambda, double tau, int32_t s_max, const kf_opts* base,
+                      void* stream, kf_opts* best, float* ms, int32_t* ncand) {
+  if (!t || !best) return KF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  kf_ctx* c = t->ctx;
+  kf_opts b0 = {};
+  if (base) b0 = *base;
+  b0.sync_errors = 0;
+  std::vector<kf_opts> cand;
+  for (int cl = 0; cl < 2; ++cl) {
+    kf_opts o = b0;
+    o.no_cluster_kernels = cl;
+    if (b0.precision == KF_PREC_MIXED) {
+      for (int tile : {256, 128}) {
+        o.no_tensor_cores = 0;
+        o.tc_tile_n = tile;
+        cand.push_back(o);
+      }
+      o.no_tensor_cores = 1;
+      o.tc_tile_n = 0;
+      cand.push_back(o);
+    } else {
+      cand.push_back(o);
+    }
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  KF_CUDA(c, cudaEventCreate(&e0));
+  KF_CUDA(c, cudaEventCreate(&e1));
+  auto run = [&](const kf_opts& o, float* t_ms) -> kf_status {
+    kf_factor* f = nullptr;
+    cudaEventRecord(e0, s);
+    kf_status st = kf_factorize(t, h, lambda, tau, s_max, &o, stream, &f);
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (f) kf_factor_free(f);
+    if (st != KF_OK && st != KF_EILLCOND) return st;
+    if (e != cudaSuccess) return kf_set_err(c, KF_ECUDA, "autotune: %s", cudaGetErrorString(e));
+    if (t_ms) cudaEventElapsedTime(t_ms, e0, e1);
+    return KF_OK;
+  };
+  kf_status st = run(b0, nullptr);  // warm-up: module loading, allocator pools
+  int bi = 0;
+  float bt = 0.f;
+  for (size_t i = 0; i < cand.size() && st == KF_OK; ++i) {
+    float t1 = 0.f, t2 = 0.f;
+    st = run(cand[i], &t1);
+    if (st == KF_OK) st = run(cand[i], &t2);
+    const float tm = std::min(t1, t2);
+    if (ms && i < KF_AUTOTUNE_MAX) ms[i] = tm;
+    if (st == KF_OK && (i == 0 || tm < bt)) { bt = tm; bi = (int)i; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != KF_OK) return st;
+  *best = cand[bi];
+  if (base) best->sync_errors = base->sync_errors;
+  if (ncand) *ncand = (int32_t)cand.size();
+  return KF_OK;
 }
 
 kf_status kf_factorize_with_ids(kf_tree* t, double h, double lambda, int32_t s_max, const int32_t* ranks,

@@ -58,6 +58,7 @@ struct kf_factor {
   float c_exp_hi = 0, c_exp_lo = 0;  // c_exp as a double-float pair
   int32_t s_max = 0, n_samp = 0, cmax = 0, prec = 0, vstore = 0, sync_errors = 0;
   int32_t use_tc = 1;  // mixed path: tcgen05 products (0: CUDA-core FP32)
+  int32_t tc_bn = 256; // tile width of the tcgen05 products: 128 or 256 columns
   int32_t use_cluster_qr = 1;  // upper tree levels: cluster QR in distributed shared memory
   int32_t use_cluster_lu = 1;  // upper tree levels: reduced-system LU and T on a CTA cluster per node
   int32_t fp64_op = 0;  // keep the FP64-accurate operator data (VTdf, Kdf)

@@ -297,7 +297,7 @@ struct ZoffProblem {
   const int32_t* lo;
   const int32_t* hi;
   const int32_t* rank;
-  int node0, s_max, ldz, ksplit, ntile_n;
+  int node0, s_max, ldz, ksplit, ntile_n, tile_n;
   const float* VT;
   const float* Ph;
   double* Z;
@@ -311,7 +311,7 @@ struct ZoffProblem {
     t.N = t.side == 0 ? sr : sl;
     t.base = sl;
     t.m0 = (bx / ntile_n) * kBM;
-    t.n0 = (bx % ntile_n) * 256;
+    t.n0 = (bx % ntile_n) * tile_n;
     const int rb = lo[c], rn = hi[c] - rb;
     const int chunk = ((rn + ksplit - 1) / ksplit + kBK - 1) / kBK * kBK;
     t.k0 = rb + by * chunk;
@@ -334,7 +334,7 @@ struct TelescopeProblem {
   const int32_t* lo;
   const int32_t* hi;
   const int32_t* rank;
-  int node0, s_max, ldz, ntile_n;
+  int node0, s_max, ldz, ntile_n, tile_n;
   const float* Pc_hat;
   const float* Tm;  // T = Z^-1 P_c, FP32 copy
   float* Pa_hat;
@@ -347,7 +347,7 @@ struct TelescopeProblem {
     t.M = hi[c];       // absolute row range [lo[c], hi[c])
     t.N = rank[t.node];
     t.m0 = lo[c] + bx * kBM;
-    t.n0 = by * 256;
+    t.n0 = by * tile_n;
     t.k0 = 0;
     t.k1 = rank[c];
     t.skip = t.N == 0 || t.m0 >= t.M || t.n0 >= t.N || t.k1 == 0;
@@ -366,37 +366,57 @@ struct TelescopeProblem {
 // ---- launchers ---------------------------------------------------------------------
 static size_t tc_smem_bytes(int BN) { return 2 * sizeof(float) * (size_t)(2 * kBM * kBK + 2 * BN * kBK); }
 
-kf_status kf_tc_zoff(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
-                     const float* VT, const float* Ph, int ldz, double* Z, int64_t rows_per_child, int32_t* status,
-                     cudaStream_t s) {
+template <int BN>
+static kf_status tc_zoff_bn(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
+                            const float* VT, const float* Ph, int ldz, double* Z, int64_t rows_per_child,
+                            int32_t* status, cudaStream_t s) {
   ZoffProblem p;
   p.lo = lo; p.hi = hi; p.rank = rank; p.node0 = node0; p.s_max = s_max; p.ldz = ldz;
-  p.ntile_n = (s_max + 255) / 256;
+  p.ntile_n = (s_max + BN - 1) / BN;
+  p.tile_n = BN;
   p.VT = VT; p.Ph = Ph; p.Z = Z;
   const int mt = (s_max + kBM - 1) / kBM;
   // enough CTAs to fill the GPU: split the reduction over the child's rows
   const int64_t tiles = (int64_t)mt * p.ntile_n * 2 * nn;
   int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>((rows_per_child + 1023) / 1024, (2 * 152 + tiles - 1) / tiles));
   p.ksplit = ksplit;
-  const size_t smem = tc_smem_bytes(256);
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<256, ZoffProblem>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = tc_smem_bytes(BN);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN, ZoffProblem>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return KF_ECUDA;
   dim3 g(mt * p.ntile_n, ksplit, 2 * nn);
-  KF_PHASE(KF_PH_ZOFF, s, k_tc_gemm<256, ZoffProblem><<<g, kThreads, smem, s>>>(p, status));
+  KF_PHASE(KF_PH_ZOFF, s, k_tc_gemm<BN, ZoffProblem><<<g, kThreads, smem, s>>>(p, status));
   return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
+}
+
+template <int BN>
+static kf_status tc_telescope_bn(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn,
+                                 int s_max, const float* Pc_hat, const float* Tm, int ldz, float* Pa_hat,
+                                 int64_t rows_per_child, int32_t* status, cudaStream_t s) {
+  TelescopeProblem p;
+  p.lo = lo; p.hi = hi; p.rank = rank; p.node0 = node0; p.s_max = s_max; p.ldz = ldz;
+  p.ntile_n = (s_max + BN - 1) / BN;
+  p.tile_n = BN;
+  p.Pc_hat = Pc_hat; p.Tm = Tm; p.Pa_hat = Pa_hat;
+  const size_t smem = tc_smem_bytes(BN);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN, TelescopeProblem>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return KF_ECUDA;
+  dim3 g((unsigned)((rows_per_child + kBM - 1) / kBM), p.ntile_n, 2 * nn);
+  KF_PHASE(KF_PH_TELESCOPE, s, k_tc_gemm<BN, TelescopeProblem><<<g, kThreads, smem, s>>>(p, status));
+  return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
+}
+
+// tile_n: the tile width BN of the products, 128 or 256 columns
+kf_status kf_tc_zoff(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
+                     const float* VT, const float* Ph, int ldz, double* Z, int64_t rows_per_child, int32_t* status,
+                     cudaStream_t s, int tile_n) {
+  return tile_n == 128 ? tc_zoff_bn<128>(lo, hi, rank, node0, nn, s_max, VT, Ph, ldz, Z, rows_per_child, status, s)
+                       : tc_zoff_bn<256>(lo, hi, rank, node0, nn, s_max, VT, Ph, ldz, Z, rows_per_child, status, s);
 }
 
 kf_status kf_tc_telescope(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
                           const float* Pc_hat, const float* Tm, int ldz, float* Pa_hat, int64_t rows_per_child,
-                          int32_t* status, cudaStream_t s) {
-  TelescopeProblem p;
-  p.lo = lo; p.hi = hi; p.rank = rank; p.node0 = node0; p.s_max = s_max; p.ldz = ldz;
-  p.ntile_n = (s_max + 255) / 256;
-  p.Pc_hat = Pc_hat; p.Tm = Tm; p.Pa_hat = Pa_hat;
-  const size_t smem = tc_smem_bytes(256);
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<256, TelescopeProblem>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return KF_ECUDA;
-  dim3 g((unsigned)((rows_per_child + kBM - 1) / kBM), p.ntile_n, 2 * nn);
-  KF_PHASE(KF_PH_TELESCOPE, s, k_tc_gemm<256, TelescopeProblem><<<g, kThreads, smem, s>>>(p, status));
-  return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
+                          int32_t* status, cudaStream_t s, int tile_n) {
+  return tile_n == 128
+             ? tc_telescope_bn<128>(lo, hi, rank, node0, nn, s_max, Pc_hat, Tm, ldz, Pa_hat, rows_per_child, status, s)
+             : tc_telescope_bn<256>(lo, hi, rank, node0, nn, s_max, Pc_hat, Tm, ldz, Pa_hat, rows_per_child, status, s);
 }

@@ -171,6 +171,35 @@ def test_cluster_kernels_medium_tree():
     assert rel(xa, xb) <= 1e-10
 
 
+def test_tc_tile_width_128(c1):
+    """The tcgen05 products with 128-column tiles (the autotuner's other tile
+    width) against the oracle, with the oracle's skeletons imported."""
+    p, o, tree = c1
+    ranks, skel, P = ids_from_oracle(o, p.s_max)
+    F = kf.factorize_with_ids(tree, p.h, p.lam, p.s_max, ranks, skel, P, precision=MIXED, tc_tile_n=128)
+    b = p.B[:, 0]
+    assert rel(F.solve(torch.from_numpy(b).cuda()).cpu().numpy(), o.solve(b)) <= 1e-5
+    with pytest.raises(kf.KFError):
+        kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=MIXED, tc_tile_n=64)
+
+
+def test_autotune_picks_a_candidate_that_solves(c1):
+    """kf_autotune times the kernel variants (cluster kernels, tcgen05 or CUDA-
+    core products, tile width) and returns the fastest; the chosen options give
+    the same skeletons and a solution within the mixed tolerance."""
+    p, o, tree = c1
+    chosen, ms = kf.autotune(tree, p.h, p.lam, p.tau, p.s_max, precision=MIXED)
+    assert len(ms) == 6 and all(t > 0 for t in ms)
+    assert chosen["tc_tile_n"] in (0, 128, 256)
+    F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=MIXED, **chosen)
+    F0 = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=MIXED)
+    assert np.array_equal(F.ranks(), F0.ranks())
+    b = p.B[:, 0]
+    assert rel(F.solve(torch.from_numpy(b).cuda()).cpu().numpy(), o.solve(b)) <= 1e-5
+    chosen64, ms64 = kf.autotune(tree, p.h, p.lam, p.tau, p.s_max, precision=FP64)
+    assert len(ms64) == 2
+
+
 def test_matvec_transpose_and_grad_parity(c1):
     p, o, tree = c1
     ranks, skel, P = ids_from_oracle(o, p.s_max)
