@@ -107,54 +107,101 @@ __global__ void k_eval_A(const double* __restrict__ X, int d, double c_exp, cons
     Aj[i] = kf_kern64(X + (int64_t)S[i] * d, xc, d, c_exp);
 }
 
-// T = R11^-1 R12 (warp per column of R12), written straight into P, plus the
-// skeleton list and the rank.  Ab: the node's factored block (columns in
-// position order), piv[q] = ID column at position q, s = rank.
+// T = R11^-1 R12 in place over R12 (rows 0..s-1 of the columns s..c-1 of the
+// factored block Ab, column-major with stride n_samp), by 32-row blocks from
+// the bottom: the upper-triangular diagonal block is staged in shared memory
+// (reciprocal pivots formed once) and solved with shuffles, a warp per column;
+// the rows above are then updated for all columns at once by 64 x 64 FP64
+// tiles staged in shared memory (thread: 4 consecutive rows x 2 columns, so
+// that a warp's stores to the column-major block are contiguous).
+struct IdSolveShared {
+  double du[32][33];
+  double rd[32];
+  double ta[32][64];  // R11[ti + r][kb + t] at [t][r]
+  double tb[32][65];  // X[kb + t][tj + j] at [t][j]
+};
+
+__device__ void id_solve_t(double* __restrict__ Ab, int n_samp, int s, int c, IdSolveShared& sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int nc = c - s;
+  if (s == 0 || nc <= 0) return;
+  const int tx = tid & 15, ty = tid >> 4;  // 16 x (blockDim / 16)
+  const int nty = blockDim.x >> 4;
+  for (int kb = ((s - 1) / 32) * 32; kb >= 0; kb -= 32) {
+    const int nb = min(32, s - kb);
+    for (int e = tid; e < 32 * 32; e += blockDim.x) {
+      const int i = e & 31, t = e >> 5;
+      sh.du[i][t] = (i < nb && t < nb && i <= t) ? Ab[(int64_t)(kb + t) * n_samp + kb + i] : 0.0;
+    }
+    __syncthreads();
+    if (tid < 32) sh.rd[tid] = tid < nb ? 1.0 / sh.du[tid][tid] : 0.0;
+    __syncthreads();
+    for (int jj = warp; jj < nc; jj += nw) {
+      double* col = Ab + (int64_t)(s + jj) * n_samp + kb;
+      double bi = lane < nb ? col[lane] : 0.0;
+      for (int t = nb - 1; t >= 0; --t) {
+        if (lane == t) bi *= sh.rd[t];
+        const double xt = __shfl_sync(0xffffffffu, bi, t);
+        if (lane < t) bi = fma(-sh.du[lane][t], xt, bi);
+      }
+      if (lane < nb) col[lane] = bi;
+    }
+    __syncthreads();
+    // rows above: X[0:kb, :] -= R11[0:kb, kb:kb+nb] X[kb:kb+nb, :]
+    for (int ti = 0; ti < kb; ti += 64)
+      for (int tj = 0; tj < nc; tj += 2 * nty) {
+        for (int e = tid; e < 32 * 64; e += blockDim.x) {
+          const int r = e & 63, t = e >> 6;
+          sh.ta[t][r] = (ti + r < kb && t < nb) ? Ab[(int64_t)(kb + t) * n_samp + ti + r] : 0.0;
+          const int t2 = e & 31, j2 = e >> 5;
+          if (j2 < 2 * nty) sh.tb[t2][j2] = (t2 < nb && tj + j2 < nc) ? Ab[(int64_t)(s + tj + j2) * n_samp + kb + t2] : 0.0;
+        }
+        __syncthreads();
+        double acc[4][2] = {};
+#pragma unroll 8
+        for (int t = 0; t < 32; ++t) {
+          double av[4], bv[2];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) av[a] = sh.ta[t][tx * 4 + a];
+#pragma unroll
+          for (int bq = 0; bq < 2; ++bq) bv[bq] = sh.tb[t][ty * 2 + bq];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int bq = 0; bq < 2; ++bq) acc[a][bq] = fma(av[a], bv[bq], acc[a][bq]);
+        }
+#pragma unroll
+        for (int bq = 0; bq < 2; ++bq) {
+          const int j = tj + ty * 2 + bq;
+          if (j >= nc) continue;
+          double* colj = Ab + (int64_t)(s + j) * n_samp;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int i = ti + tx * 4 + a;
+            if (i < kb) colj[i] -= acc[a][bq];
+          }
+        }
+        __syncthreads();
+      }
+  }
+}
+
+// P, the skeleton list and the rank from the factored block (columns in
+// position order, piv[q] = ID column at position q, s = rank):
+// P[j * ldP + q]: ID column j, skeleton q.  Leaves write their rows of the
+// N x s_max matrix (base lo[node]); internal nodes have fixed-size blocks.
 __device__ void id_finish(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                           int32_t* __restrict__ rank, int32_t* __restrict__ skel, int s_max, int node, int nl,
-                          bool leaf, int n_samp, int c, const double* __restrict__ Ab, const int* piv, int s,
-                          double* __restrict__ Pout, int ldP, int64_t P_node_stride, double* rinv) {
+                          bool leaf, int n_samp, int c, double* __restrict__ Ab, const int* piv, int s,
+                          double* __restrict__ Pout, int ldP, int64_t P_node_stride, IdSolveShared& ish) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  // reciprocals of the diagonal of R11 (shared memory, s entries), so that the
-  // back substitution multiplies instead of dividing in every lane
-  for (int t = threadIdx.x; t < s; t += blockDim.x) rinv[t] = 1.0 / Ab[(int64_t)t * n_samp + t];
+  id_solve_t(Ab, n_samp, s, c, ish);  // R12 now holds T = R11^-1 R12
   __syncthreads();
-  // T = R11^-1 R12 (warp per column of R12), written straight into P
-  // P[j * ldP + q]: ID column j, skeleton q.  Leaves write their rows of the
-  // N x s_max matrix (base lo[node]); internal nodes have fixed-size blocks.
   double* P = leaf ? Pout + (int64_t)lo[node] * ldP : Pout + (int64_t)nl * P_node_stride;
   for (int j = s + warp; j < c; j += nwarps) {
-    const double* cj = Ab + (int64_t)j * n_samp;
-    double b[KF_MAX_SMAX / 32];
-#pragma unroll
-    for (int r = 0; r < KF_MAX_SMAX / 32; ++r) {
-      int i = lane + 32 * r;
-      b[r] = (i < s) ? cj[i] : 0.0;
-    }
-    for (int t = s - 1; t >= 0; --t) {
-      const double* ct = Ab + (int64_t)t * n_samp;
-      const int rt = t >> 5;  // register slot of row t (lane t & 31)
-      double bt = 0.0;
-#pragma unroll
-      for (int r = 0; r < KF_MAX_SMAX / 32; ++r)
-        if (r == rt) bt = b[r];
-      bt = __shfl_sync(0xffffffffu, bt, t & 31);
-      const double xt = bt * rinv[t];
-#pragma unroll
-      for (int r = 0; r < KF_MAX_SMAX / 32; ++r) {
-        if (r > rt) break;  // rows above t are final
-        int i = lane + 32 * r;
-        if (i == t) b[r] = xt;
-        else if (i < t) b[r] = fma(-ct[i], xt, b[r]);
-      }
-    }
+    const double* tj = Ab + (int64_t)j * n_samp;
     double* Pj = P + (int64_t)piv[j] * ldP;
-#pragma unroll
-    for (int r = 0; r < KF_MAX_SMAX / 32; ++r) {
-      int q = lane + 32 * r;
-      if (q < s) Pj[q] = b[r];
-      else if (q < s_max) Pj[q] = 0.0;
-    }
+    for (int q = lane; q < s_max; q += 32) Pj[q] = q < s ? tj[q] : 0.0;
   }
   for (int j = warp; j < s; j += nwarps) {
     double* Pj = P + (int64_t)piv[j] * ldP;
@@ -352,8 +399,8 @@ __global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ 
     __syncthreads();
   }
   __syncthreads();
-  // v (n_samp >= s entries) is free now: it holds the reciprocals of diag(R11)
-  id_finish(lo, hi, rank, skel, s_max, node, nl, leaf, n_samp, c, Ab, piv, s_final, Pout, ldP, P_node_stride, v);
+  __shared__ IdSolveShared ish;
+  id_finish(lo, hi, rank, skel, s_max, node, nl, leaf, n_samp, c, Ab, piv, s_final, Pout, ldP, P_node_stride, ish);
 }
 
 // ---- 3b. pivoted QR of an internal node on a 16-CTA cluster -------------------
@@ -537,18 +584,17 @@ __global__ void __cluster_dims__(kQC, 1, 1) __launch_bounds__(256)
 // Finishing step after the cluster QR: one CTA per node.
 __global__ void __launch_bounds__(512) k_id_finish(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                    int32_t* __restrict__ rank, int32_t* __restrict__ skel, int s_max,
-                                                   int node0, int n_samp, int cmax, const double* __restrict__ A,
+                                                   int node0, int n_samp, int cmax, double* __restrict__ A,
                                                    const int32_t* __restrict__ pivpos, const int32_t* __restrict__ sout,
                                                    double* __restrict__ Pout, int ldP, int64_t P_node_stride) {
-  extern __shared__ double fin_sm[];
-  double* rinv = fin_sm;            // s_max
-  int* pv = (int*)(rinv + s_max);   // cmax
+  extern __shared__ int pv[];  // cmax
+  __shared__ IdSolveShared ish;
   const int nl = blockIdx.x, node = node0 + nl;
   const int c = rank[2 * node] + rank[2 * node + 1];
   for (int q = threadIdx.x; q < c; q += blockDim.x) pv[q] = pivpos[(int64_t)nl * cmax + q];
   __syncthreads();
   id_finish(lo, hi, rank, skel, s_max, node, nl, false, n_samp, c, A + (int64_t)nl * cmax * n_samp, pv, sout[nl],
-            Pout, ldP, P_node_stride, rinv);
+            Pout, ldP, P_node_stride, ish);
 }
 
 }  // namespace
@@ -619,7 +665,8 @@ kf_status kf_skel_level(kf_factor* f, int l, kf_skel_scratch* sc, cudaStream_t s
         int32_t* so = pp + (size_t)nn * cmax;
         KF_PHASE(KF_PH_QR_CLUSTER, s, k_qr_cluster<<<nn * kQC, 256, qsmem, s>>>(t->d_lo, t->d_hi, f->rank, s_max, node0,
                                                                        n_samp, cmax, nsamp, f->tau, A, pp, so));
-        KF_PHASE(KF_PH_QR_CLUSTER, s, k_id_finish<<<nn, 512, sizeof(double) * s_max + sizeof(int) * cmax, s>>>(t->d_lo, t->d_hi, f->rank, f->skel,
+        KF_CUDA(c, cudaFuncSetAttribute(k_id_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(int) * cmax)));
+        KF_PHASE(KF_PH_QR_CLUSTER, s, k_id_finish<<<nn, 512, sizeof(int) * cmax, s>>>(t->d_lo, t->d_hi, f->rank, f->skel,
                                                                             s_max, node0, n_samp, cmax, A, pp, so,
                                                                             Pout, s_max, pstride));
         cudaError_t e = cudaGetLastError();
@@ -630,6 +677,10 @@ kf_status kf_skel_level(kf_factor* f, int l, kf_skel_scratch* sc, cudaStream_t s
     }
   }
   size_t smem = sizeof(double) * (2 * cmax + n_samp) + sizeof(int) * cmax;
+  // the static part (the blocked R11^-1 R12 tiles) plus this may pass 48 KiB
+  KF_CUDA(c, cudaFuncSetAttribute(k_pivoted_qr<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  KF_CUDA(c, cudaFuncSetAttribute(k_pivoted_qr<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  KF_CUDA(c, cudaFuncSetAttribute(k_pivoted_qr<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (rpl <= 8)
     KF_PHASE(leaf ? KF_PH_QR_LEAF : KF_PH_QR, s, k_pivoted_qr<8><<<nn, 512, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf, n_samp, cmax,
                                           nsamp, f->tau, A, Pout, s_max, pstride));
