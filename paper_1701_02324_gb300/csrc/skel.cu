@@ -218,8 +218,9 @@ __device__ void id_finish(const int32_t* __restrict__ lo, const int32_t* __restr
 }
 
 // ---- 3/4. pivoted QR and P ------------------------------------------------------
-template <int RPL>  // rows per lane held in registers (n_samp <= 32 * RPL)
-__global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+// RPL: rows per lane held in registers (n_samp <= 32 * RPL); NT threads
+template <int RPL, int NT>
+__global__ void __launch_bounds__(NT, 1) k_pivoted_qr(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                     int32_t* __restrict__ rank, int32_t* __restrict__ skel, int s_max,
                                                     int node0, bool leaf, int n_samp, int cmax,
                                                     const int32_t* __restrict__ nsamp, double tau,
@@ -329,69 +330,96 @@ __global__ void __launch_bounds__(512) k_pivoted_qr(const int32_t* __restrict__ 
     // apply H to the trailing columns; their squared norms over rows > k are
     // downdated by the new row-k entry, and evaluated exactly again once they
     // have fallen by 16x since the last exact value (rounding stays near
-    // machine precision relative to the current norm)
-    // each warp walks its columns with the next one's loads in flight
-    // (register double buffering: the loads are the long pole)
-    double an[RPL];
-    if (k + 1 + warp < c) {
-      const double* cn = Ab + (int64_t)(k + 1 + warp) * n_samp;
+    // machine precision relative to the current norm).
+    // A warp takes the trailing columns two at a time (k+1+2q, k+2+2q), both
+    // held in registers (their 2 x RPL independent loads per lane keep enough
+    // requests in flight; loading the next pair ahead measured no faster).
+    // Every FP64 warp instruction costs the same whatever its active
+    // lanes, so the per-column scalar work is shared by the pair: one
+    // butterfly reduces both dot products (lanes 0-15 end with the first
+    // column's, lanes 16-31 with the second's), one multiply forms both
+    // Householder weights and one fma downdates both norms (lanes 0 and 1).
+    const int npair = (c - k) >> 1;  // ceil((c - k - 1) / 2) trailing pairs
+    for (int q = warp; q < npair; q += nwarps) {
+      const int j0 = k + 1 + 2 * q, j1 = j0 + 1;
+      const bool has1 = j1 < c;
+      double* c0 = Ab + (int64_t)j0 * n_samp;
+      double* c1 = c0 + n_samp;
+      double a[RPL], b[RPL];
 #pragma unroll
       for (int r = 0; r < RPL; ++r) {
         if (r >= nr) break;
         const int i = k + lane + 32 * r;
-        an[r] = (i < ns) ? cn[i] : 0.0;
+        a[r] = (i < ns) ? c0[i] : 0.0;
+        b[r] = (has1 && i < ns) ? c1[i] : 0.0;
       }
-    }
-    for (int j = k + 1 + warp; j < c; j += nwarps) {
-      double* cj = Ab + (int64_t)j * n_samp;
-      double a[RPL];
+      double d0 = 0.0, d1 = 0.0;
 #pragma unroll
-      for (int r = 0; r < RPL; ++r) a[r] = an[r];
-      if (j + nwarps < c) {
-        const double* cn = Ab + (int64_t)(j + nwarps) * n_samp;
+      for (int r = 0; r < RPL; ++r) {
+        if (r >= nr) break;  // slots past the last row chunk hold nothing
+        const int i = k + lane + 32 * r;
+        if (i < ns) {
+          const double vi = v[i];
+          d0 = fma(vi, a[r], d0);
+          d1 = fma(vi, b[r], d1);
+        }
+      }
+      const bool upper = lane & 16;
+      double dsum = (upper ? d1 : d0) + __shfl_xor_sync(0xffffffffu, upper ? d0 : d1, 16);
+      for (int off = 8; off > 0; off >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, off);
+      const double wl = beta * dsum;
+      const double w0 = __shfl_sync(0xffffffffu, wl, 0), w1 = __shfl_sync(0xffffffffu, wl, 16);
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        if (r >= nr) break;
+        const int i = k + lane + 32 * r;
+        if (i < ns) {
+          const double vi = v[i];
+          a[r] = fma(-w0, vi, a[r]);
+          b[r] = fma(-w1, vi, b[r]);
+          c0[i] = a[r];
+          if (has1) c1[i] = b[r];
+        }
+      }
+      // row k sits in lane 0, slot 0 of both columns
+      const double x0 = __shfl_sync(0xffffffffu, a[0], 0), x1 = __shfl_sync(0xffffffffu, b[0], 0);
+      const int jl = (lane & 1) ? j1 : j0;
+      const bool mine = lane < 2 && jl < c;
+      double nrm = 0.0;
+      bool redo = false;
+      if (mine) {
+        const double akj = (lane & 1) ? x1 : x0;
+        nrm = fma(-akj, akj, norms[jl]);
+        // nref holds 1/16 of the last exact value; the bit patterns of a
+        // non-negative threshold and of nrm compare like the values (a
+        // negative nrm compares below), which keeps the test off the FP64 pipe
+        redo = !(__double_as_longlong(nrm) > __double_as_longlong(nref[jl]));
+      }
+      const unsigned rm = __ballot_sync(0xffffffffu, redo);
+      if (rm & 1u) {
+        double e = 0.0;
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
           if (r >= nr) break;
           const int i = k + lane + 32 * r;
-          an[r] = (i < ns) ? cn[i] : 0.0;
+          if (i > k && i < ns) e = fma(a[r], a[r], e);
         }
+        for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+        if (lane == 0) { nrm = e; nref[j0] = e * 0.0625; }
       }
-      double dot = 0.0;
-#pragma unroll
-      for (int r = 0; r < RPL; ++r) {
-        if (r >= nr) break;  // slots past the last row chunk hold nothing
-        int i = k + lane + 32 * r;
-        if (i < ns) dot = fma(v[i], a[r], dot);
-      }
-      for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
-      const double w = beta * dot;
-#pragma unroll
-      for (int r = 0; r < RPL; ++r) {
-        if (r >= nr) break;
-        int i = k + lane + 32 * r;
-        if (i < ns) {
-          a[r] = fma(-w, v[i], a[r]);
-          cj[i] = a[r];
-        }
-      }
-      const double akj = __shfl_sync(0xffffffffu, a[0], 0);  // row k sits in lane 0, slot 0
-      double nrm = fma(-akj, akj, norms[j]);
-      // nref holds 1/16 of the last exact value; the bit patterns of a
-      // non-negative threshold and of nrm compare like the values (a negative
-      // nrm compares below), which keeps the test off the FP64 pipe
-      if (!(__double_as_longlong(nrm) > __double_as_longlong(nref[j]))) {
-        nrm = 0.0;
+      if (rm & 2u) {
+        double e = 0.0;
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
           if (r >= nr) break;
-          int i = k + lane + 32 * r;
-          if (i > k && i < ns) nrm = fma(a[r], a[r], nrm);
+          const int i = k + lane + 32 * r;
+          if (i > k && i < ns) e = fma(b[r], b[r], e);
         }
-        for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
-        if (lane == 0) nref[j] = nrm * 0.0625;
+        for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+        if (lane == 1) { nrm = e; nref[j1] = e * 0.0625; }
       }
       __syncwarp();
-      if (lane == 0) norms[j] = nrm;
+      if (mine) norms[jl] = nrm;
     }
     __syncthreads();
     if (threadIdx.x == 0) Ab[(int64_t)k * n_samp + k] = alpha;
@@ -462,7 +490,7 @@ __global__ void __cluster_dims__(kQC, 1, 1) __launch_bounds__(256)
       }
     }
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) { norms[lj] = acc; nref[lj] = acc; done[lj] = (j < c) ? 0 : 1; }
+    if (lane == 0) { norms[lj] = acc; nref[lj] = acc * 0.0625; done[lj] = (j < c) ? 0 : 1; }
   }
   for (int j = tid; j < c; j += blockDim.x) { posof[j] = j; physat[j] = j; }
   if (tid == 0) s_final = kmax;
@@ -544,26 +572,54 @@ __global__ void __cluster_dims__(kQC, 1, 1) __launch_bounds__(256)
     }
     __syncthreads();
     const double beta = pub[1];
-    // 4. update my trailing columns
-    for (int lj = warp; lj < W; lj += 8) {
-      if (done[lj]) continue;
-      double* cj = Aloc + (size_t)lj * n_samp;
-      double dot = 0.0;
-      for (int i = k + lane; i < ns; i += 32) dot = fma(vloc[i], cj[i], dot);
-      for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
-      const double w = beta * dot;
-      for (int i = k + lane; i < ns; i += 32) cj[i] = fma(-w, vloc[i], cj[i]);
-      __syncwarp();
-      const double akj = cj[k];
-      double nrm = fma(-akj, akj, norms[lj]);
-      if (!(nrm > nref[lj] * 0.0625)) {
-        nrm = 0.0;
-        for (int i = k + 1 + lane; i < ns; i += 32) nrm = fma(cj[i], cj[i], nrm);
-        for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
-        if (lane == 0) nref[lj] = nrm;
+    // 4. update my trailing columns, two per warp (local columns lj and
+    // lj + 8) as in k_pivoted_qr: one butterfly for both dot products, one
+    // multiply for both weights, one fma for both norm downdates
+    for (int lj0 = warp; lj0 < W; lj0 += 16) {
+      const int lj1 = lj0 + 8;
+      const bool u0 = !done[lj0], u1 = lj1 < W && !done[lj1];
+      if (!u0 && !u1) continue;
+      double* c0 = Aloc + (size_t)lj0 * n_samp;
+      double* c1 = Aloc + (size_t)lj1 * n_samp;
+      double d0 = 0.0, d1 = 0.0;
+      for (int i = k + lane; i < ns; i += 32) {
+        const double vi = vloc[i];
+        if (u0) d0 = fma(vi, c0[i], d0);
+        if (u1) d1 = fma(vi, c1[i], d1);
+      }
+      const bool upper = lane & 16;
+      double dsum = (upper ? d1 : d0) + __shfl_xor_sync(0xffffffffu, upper ? d0 : d1, 16);
+      for (int off = 8; off > 0; off >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, off);
+      const double wl = beta * dsum;
+      const double w0 = __shfl_sync(0xffffffffu, wl, 0), w1 = __shfl_sync(0xffffffffu, wl, 16);
+      for (int i = k + lane; i < ns; i += 32) {
+        const double vi = vloc[i];
+        if (u0) c0[i] = fma(-w0, vi, c0[i]);
+        if (u1) c1[i] = fma(-w1, vi, c1[i]);
       }
       __syncwarp();
-      if (lane == 0) norms[lj] = nrm;
+      // lane 0: column lj0, lane 1: column lj1.  nref holds 1/16 of the last
+      // exact norm; non-negative doubles compare like their bit patterns
+      const int ljl = (lane & 1) ? lj1 : lj0;
+      const bool mine = (lane == 0 && u0) || (lane == 1 && u1);
+      double nrm = 0.0;
+      bool redo = false;
+      if (mine) {
+        const double akj = (lane & 1) ? c1[k] : c0[k];
+        nrm = fma(-akj, akj, norms[ljl]);
+        redo = !(__double_as_longlong(nrm) > __double_as_longlong(nref[ljl]));
+      }
+      const unsigned rm = __ballot_sync(0xffffffffu, redo);
+      for (int h = 0; h < 2; ++h) {
+        if (!(rm & (1u << h))) continue;
+        const double* ch = h ? c1 : c0;
+        double e = 0.0;
+        for (int i = k + 1 + lane; i < ns; i += 32) e = fma(ch[i], ch[i], e);
+        for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+        if (lane == h) { nrm = e; nref[ljl] = e * 0.0625; }
+      }
+      __syncwarp();
+      if (mine) norms[ljl] = nrm;
     }
     __syncthreads();
   }
@@ -678,18 +734,21 @@ kf_status kf_skel_level(kf_factor* f, int l, kf_skel_scratch* sc, cudaStream_t s
   }
   size_t smem = sizeof(double) * (2 * cmax + n_samp) + sizeof(int) * cmax;
   // the static part (the blocked R11^-1 R12 tiles) plus this may pass 48 KiB
-  KF_CUDA(c, cudaFuncSetAttribute(k_pivoted_qr<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  KF_CUDA(c, cudaFuncSetAttribute(k_pivoted_qr<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  KF_CUDA(c, cudaFuncSetAttribute(k_pivoted_qr<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+#define KF_QR_GO(R, NT)                                                                                          \
+  do {                                                                                                          \
+    KF_CUDA(c, cudaFuncSetAttribute(k_pivoted_qr<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    KF_PHASE(leaf ? KF_PH_QR_LEAF : KF_PH_QR, s,                                                                \
+             (k_pivoted_qr<R, NT><<<nn, NT, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf,     \
+                                                      n_samp, cmax, nsamp, f->tau, A, Pout, s_max, pstride)));       \
+  } while (0)
+  // 512 threads (16 warps) while two columns of RPL rows fit in 128 registers
   if (rpl <= 8)
-    KF_PHASE(leaf ? KF_PH_QR_LEAF : KF_PH_QR, s, k_pivoted_qr<8><<<nn, 512, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf, n_samp, cmax,
-                                          nsamp, f->tau, A, Pout, s_max, pstride));
+    KF_QR_GO(8, 512);
   else if (rpl <= 16)
-    KF_PHASE(leaf ? KF_PH_QR_LEAF : KF_PH_QR, s, k_pivoted_qr<16><<<nn, 512, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf, n_samp, cmax,
-                                           nsamp, f->tau, A, Pout, s_max, pstride));
+    KF_QR_GO(16, 512);
   else
-    KF_PHASE(leaf ? KF_PH_QR_LEAF : KF_PH_QR, s, k_pivoted_qr<32><<<nn, 512, smem, s>>>(t->d_lo, t->d_hi, f->rank, f->skel, s_max, node0, leaf, n_samp, cmax,
-                                           nsamp, f->tau, A, Pout, s_max, pstride));
+    KF_QR_GO(32, 256);
+#undef KF_QR_GO
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return kf_set_err(c, KF_ECUDA, "skeletonize level %d: %s", l, cudaGetErrorString(e));
   return KF_OK;
