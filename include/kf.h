@@ -274,6 +274,15 @@ kf_status kf_profile_enable(int32_t on);
  * the solve sweep). */
 #define KF_PHASE_COUNT 23
 kf_status kf_profile_read(double* ms, int64_t* launches, int32_t nphase);
+/* Per-launch timeline of the launches recorded since the last kf_profile_read
+ * (which it leaves in place): for launch q < *n, its start and end in ms
+ * relative to the start of the first recorded launch, its phase and the
+ * index of its stream in order of first appearance.  Host arrays of cap
+ * entries; *n receives the number of records (entries past cap are not
+ * written).  Synchronizes the recorded events.  KF_EINVAL on a null pointer
+ * or a negative cap. */
+kf_status kf_profile_timeline(double* t0_ms, double* t1_ms, int32_t* phase, int32_t* stream, int64_t cap,
+                              int64_t* n);
 
 #ifdef __cplusplus
 }

@@ -70,6 +70,7 @@ SIGNATURES = {
     "kf_launch_count": (_I64, []),
     "kf_profile_enable": (_I32, [_I32]),
     "kf_profile_read": (_I32, [_P, _P, _I32]),
+    "kf_profile_timeline": (_I32, [_P, _P, _P, _P, _I64, _P]),
 }
 
 PHASES = ["tree", "sample", "eval_A", "qr", "leaf_assemble", "leaf_cholesky", "leaf_phat", "eval_V", "zoff", "z_lu",

@@ -1077,7 +1077,7 @@ __global__ void __launch_bounds__(256) k_leaf_k64(const float* __restrict__ X32l
 }
 
 template <typename T>
-kf_status leaves_t(kf_factor* f, cudaStream_t s, bool with_k64) {
+kf_status leaves_t(kf_factor* f, cudaStream_t s, bool with_k64, int part) {
   kf_tree* t = f->t;
   kf_ctx* c = f->ctx;
   const int D = t->D, s_max = f->s_max;
@@ -1087,13 +1087,15 @@ kf_status leaves_t(kf_factor* f, cudaStream_t s, bool with_k64) {
   T* Phat = (T*)f->Phat;
   const int leaf0 = 1 << D, nleaf = 1 << D;
   dim3 g((ldL + 127) / 128, ldL, nleaf);
-  KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_assemble<T><<<g, 128, 0, s>>>(t->X64, t->X32, t->d, f->c_exp, f->lambda, t->d_lo, t->d_hi, leaf0, ldL, L));
-  if (f->Kdf && with_k64) {
-    kf_status r = kf_leaf_k64_launch(f, s);
-    if (r != KF_OK) return r;
+  if (part != 2) {
+    KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_assemble<T><<<g, 128, 0, s>>>(t->X64, t->X32, t->d, f->c_exp, f->lambda, t->d_lo, t->d_hi, leaf0, ldL, L));
+    if (f->Kdf && with_k64) {
+      kf_status r = kf_leaf_k64_launch(f, s);
+      if (r != KF_OK) return r;
+    }
+    KF_PHASE(KF_PH_LEAF_CHOL, s, k_leaf_cholesky<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, ldL, L, f->status, f->pivr));
   }
-  KF_PHASE(KF_PH_LEAF_CHOL, s, k_leaf_cholesky<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, ldL, L, f->status, f->pivr));
-  if (D > 0)
+  if (D > 0 && part != 1)
     KF_PHASE(KF_PH_LEAF_PHAT, s, k_leaf_phat<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, leaf0, ldL, L, f->Pleaf, s_max,
                                                                   Phat + (int64_t)(D - 1) * N * s_max));
   KF_LAUNCH_CHECK(c);
@@ -1165,11 +1167,34 @@ kf_status level_reduce(kf_factor* f, int l, double* Tm, cudaStream_t s) {
     KF_PHASE(KF_PH_ZOFF, s, k_zoff<T><<<dim3(tiles, ksplit, 2 * nn), 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, node0, s_max, lvl(VT, l + 1),
                                                           lvl(Phat, l + 1), ldz, f->ZLU, ksplit));
   }
-  // few nodes: a cluster of CTAs per node, sized so that the level runs in
-  // one wave (one CTA per SM: the kernel takes 255 registers a thread)
+  // few nodes: a cluster of CTAs per node (one CTA per SM: the kernel takes
+  // 255 registers a thread), the largest size whose nn clusters are all
+  // resident at once (16-CTA clusters need 16 free SMs of one GPC, and only a
+  // few GPCs offer them); a level that does not fit one wave keeps one CTA
+  // per node
   int zc = 1;
-  if (f->use_cluster_lu)
-    while (zc < 16 && (int64_t)nn * zc * 2 <= 152) zc *= 2;
+  if (f->use_cluster_lu && (int64_t)nn * 2 <= 152) {
+    cudaError_t ea = cudaFuncSetAttribute(k_z_factor_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int cand = 16; cand >= 2 && ea == cudaSuccess; cand >>= 1) {
+      if ((int64_t)nn * cand > 152) continue;
+      cudaLaunchConfig_t qc = {};
+      qc.gridDim = dim3((unsigned)(nn * cand));
+      qc.blockDim = dim3(256);
+      cudaLaunchAttribute qa[1];
+      qa[0].id = cudaLaunchAttributeClusterDimension;
+      qa[0].val.clusterDim.x = (unsigned)cand;
+      qa[0].val.clusterDim.y = 1;
+      qa[0].val.clusterDim.z = 1;
+      qc.attrs = qa;
+      qc.numAttrs = 1;
+      int act = 0;
+      if (cudaOccupancyMaxActiveClusters(&act, k_z_factor_cluster, &qc) == cudaSuccess && act >= nn) {
+        zc = cand;
+        break;
+      }
+    }
+    cudaGetLastError();
+  }
   if (zc > 1) {
     KF_CUDA(c, cudaFuncSetAttribute(k_z_factor_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg = {};
@@ -1236,8 +1261,8 @@ kf_status kf_leaf_k64_launch(kf_factor* f, cudaStream_t s) {
   return KF_OK;
 }
 
-kf_status kf_factorize_leaves(kf_factor* f, cudaStream_t s, bool with_k64) {
-  return f->prec == KF_PREC_FP64 ? leaves_t<double>(f, s, with_k64) : leaves_t<float>(f, s, with_k64);
+kf_status kf_factorize_leaves(kf_factor* f, cudaStream_t s, bool with_k64, int part) {
+  return f->prec == KF_PREC_FP64 ? leaves_t<double>(f, s, with_k64, part) : leaves_t<float>(f, s, with_k64, part);
 }
 
 kf_status kf_factorize_level_v(kf_factor* f, int l, cudaStream_t s) {
@@ -1255,7 +1280,7 @@ kf_status kf_factorize_level(kf_factor* f, int l, double* Tm, cudaStream_t s) {
 
 kf_status kf_factorize_device(kf_factor* f, cudaStream_t s) {
   kf_ctx* c = f->ctx;
-  kf_status st = kf_factorize_leaves(f, s, true);
+  kf_status st = kf_factorize_leaves(f, s, true, 0);
   if (st != KF_OK || f->t->D == 0) return st;
   const size_t tb = kf_factor_tm_bytes(f);
   double* Tm = (double*)c->dalloc(tb, s);
@@ -1265,11 +1290,13 @@ kf_status kf_factorize_device(kf_factor* f, cudaStream_t s) {
   return st;
 }
 
-// Skeletonization and factorization interleaved on two streams: level l of
+// Skeletonization and factorization interleaved on three streams: level l of
 // the factorization needs the skeletons of levels l + 1 and l only, so the
-// pivoted QRs of the upper levels (few nodes, one CTA each) run while the
-// lower levels are factorized.  Events order the two streams; the caller's
-// stream waits for both at the end.
+// pivoted QRs of the upper levels run while the lower levels are factorized
+// (s1: skeletons; s2: leaf factors and reduced systems; s3: V blocks and the
+// FP64 operator's leaf blocks).  The leaf blocks and their Cholesky factors
+// need no skeleton and start at once.  Events order the streams; the
+// caller's stream waits for all three at the end.
 kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
   kf_ctx* c = f->ctx;
   const int D = f->t->D;
@@ -1285,11 +1312,12 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
   cudaStream_t s1 = nullptr, s2 = nullptr, s3 = nullptr;
   std::vector<cudaEvent_t> ev(D + 4, nullptr), evv(D, nullptr);
   if (st == KF_OK) {
-    // the skeleton chain is the critical path: it runs on a high-priority stream
+    // the skeleton chain and the reduced systems that follow it form the
+    // critical path: high-priority streams; the V blocks fill in
     int lo_prio = 0, hi_prio = 0;
     cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
     KF_CUDA(c, cudaStreamCreateWithPriority(&s1, cudaStreamNonBlocking, hi_prio));
-    KF_CUDA(c, cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, lo_prio));
+    KF_CUDA(c, cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, hi_prio));
     KF_CUDA(c, cudaStreamCreateWithPriority(&s3, cudaStreamNonBlocking, lo_prio));
     for (auto& e : ev) KF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     for (auto& e : evv) KF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -1302,6 +1330,9 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
     cudaStreamWaitEvent(s3, ev[0], 0);
     // the FP64 operator's leaf blocks need the tree only
     if (f->Kdf) st = kf_leaf_k64_launch(f, s3);
+    // so do the leaf blocks and their Cholesky factors (FP32 or FP64 work
+    // that shares the SMs with the FP64 sample blocks of the leaf level)
+    if (st == KF_OK) st = kf_factorize_leaves(f, s2, false, 1);
     for (int l = D; l >= 1 && st == KF_OK; --l) {
       st = kf_skel_level(f, l, &sc, s1);
       cudaEventRecord(ev[l], s1);
@@ -1313,7 +1344,7 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
       if (st != KF_OK) break;
       cudaStreamWaitEvent(s2, ev[l], 0);
       if (l == D) {
-        st = kf_factorize_leaves(f, s2, false);
+        st = kf_factorize_leaves(f, s2, false, 2);
       } else {
         cudaStreamWaitEvent(s2, evv[l], 0);
         st = kf_factorize_level_z(f, l, Tm, s2);

@@ -279,7 +279,8 @@ kf_status kf_factorize_device(kf_factor* f, cudaStream_t s);
 // kf_factor_tm_elems() doubles.
 size_t kf_factor_tm_elems(const kf_factor* f);
 size_t kf_factor_tm_bytes(const kf_factor* f);
-kf_status kf_factorize_leaves(kf_factor* f, cudaStream_t s, bool with_k64);
+// part 0: all; 1: leaf blocks and their Cholesky factors; 2: P^ = A^-1 P
+kf_status kf_factorize_leaves(kf_factor* f, cudaStream_t s, bool with_k64, int part);
 kf_status kf_leaf_k64_launch(kf_factor* f, cudaStream_t s);
 kf_status kf_factorize_level(kf_factor* f, int l, double* Tm, cudaStream_t s);
 kf_status kf_factorize_level_v(kf_factor* f, int l, cudaStream_t s);

@@ -10,6 +10,7 @@ namespace {
 struct Rec {
   int phase;
   cudaEvent_t a, b;
+  cudaStream_t s;
 };
 std::mutex g_mu;
 std::atomic<long long> g_launches{0};
@@ -43,7 +44,7 @@ void kf_prof_end(int phase, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_mu);
   cudaEvent_t b = get_event();
   cudaEventRecord(b, s);
-  g_recs.push_back({phase, t_open, b});
+  g_recs.push_back({phase, t_open, b, s});
   t_open = nullptr;
 }
 
@@ -74,6 +75,32 @@ kf_status kf_profile_read(double* ms, int64_t* launches, int32_t nphase) {
     g_pool.push_back(r.b);
   }
   g_recs.clear();
+  cudaGetLastError();
+  return st;
+}
+
+kf_status kf_profile_timeline(double* t0_ms, double* t1_ms, int32_t* phase, int32_t* stream, int64_t cap,
+                              int64_t* n) {
+  if (!t0_ms || !t1_ms || !phase || !stream || !n || cap < 0) return KF_EINVAL;
+  std::lock_guard<std::mutex> lk(g_mu);
+  *n = (int64_t)g_recs.size();
+  if (g_recs.empty()) return KF_OK;
+  kf_status st = KF_OK;
+  std::vector<cudaStream_t> seen;
+  for (int64_t q = 0; q < (int64_t)g_recs.size() && q < cap; ++q) {
+    const Rec& r = g_recs[q];
+    if (cudaEventSynchronize(r.b) != cudaSuccess) st = KF_ECUDA;
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, g_recs[0].a, r.a) != cudaSuccess) st = KF_ECUDA;
+    if (cudaEventElapsedTime(&b, g_recs[0].a, r.b) != cudaSuccess) st = KF_ECUDA;
+    t0_ms[q] = a;
+    t1_ms[q] = b;
+    phase[q] = r.phase;
+    int si = 0;
+    while (si < (int)seen.size() && seen[si] != r.s) ++si;
+    if (si == (int)seen.size()) seen.push_back(r.s);
+    stream[q] = si;
+  }
   cudaGetLastError();
   return st;
 }

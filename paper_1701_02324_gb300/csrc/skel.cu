@@ -709,7 +709,8 @@ kf_status kf_skel_level(kf_factor* f, int l, kf_skel_scratch* sc, cudaStream_t s
   double* Pout = leaf ? f->Pleaf : f->Pc + (int64_t)node0 * cint * s_max;
   int64_t pstride = leaf ? 0 : (int64_t)cint * s_max;
   // upper levels (few nodes): one 16-CTA cluster per node, the block in distributed shared memory
-  if (!leaf && nn <= 64 && f->use_cluster_qr) {
+  // (at 64 nodes and more, one CTA per node in one wave is faster)
+  if (!leaf && nn <= 32 && f->use_cluster_qr) {
     const int W = (cmax + kQC - 1) / kQC;
     const size_t qsmem = sizeof(double) * ((size_t)W * n_samp + 2 * W + 2 * n_samp) + sizeof(int) * (2 * cmax + W);
     if (qsmem <= 200 * 1024) {
