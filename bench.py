@@ -39,7 +39,7 @@ FP64_PEAK_TFLOPS = 1.25          # recipe's nominal FP64 rate (152 SMs, 2.07 GHz
 # from the ncu capture summarised in profiles/k_pivoted_qr_leaf_level_N131072.md
 # (leaf level at N = 2^17, 128 leaves, scaled by the 8x leaf count); None while
 # the kernel differs from the captured one.
-QR_TRAFFIC_PER_LAUNCH = None
+QR_TRAFFIC_PER_LAUNCH = 1.41e12
 QR_TRAFFIC_SRC = "profiles/k_pivoted_qr_leaf_level_N131072.md"
 ORACLE_SAMPLE_N = 8192           # points per oracle sample step
 
