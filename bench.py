@@ -459,6 +459,31 @@ def gpu_main(args, rank, world):
         reference = {"what": "FP64 factorization + GMRES against the FP64 operator", "eps_r": iref["eps_r"],
                      "iters": iref["iters"]}
 
+    # ---- GMRES iterations of the mixed solve at other sampler seeds ------------------
+    # (the default seed's K~ is the most ill-conditioned of those tried: its
+    # iteration count moves with rounding-level changes of the FP32 factors)
+    seed_study = None
+    if not args.no_seed_study:
+        tree = kf.Tree(X, p.m)
+        rows = []
+        for sd in (1, 2, 3):
+            F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=kf.KF_PREC_MIXED, fp64_operator=True,
+                          refine_tol=args.mixed_tol, refine_max_iter=400, gmres_restart=args.gmres_m,
+                          sync_errors=False, seed=sd, **opt(kf.KF_PREC_MIXED))
+            F.solve(b)  # warm
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, inf = F.solve(b, info=True)
+            e1.record()
+            torch.cuda.synchronize()
+            rows.append({"seed": sd, "gmres_iters": inf["iters"], "eps_r": inf["eps_r"],
+                         "solve_rhs_per_s": round(1e3 / e0.elapsed_time(e1), 2)})
+            del F
+        del tree
+        seed_study = {"what": "mixed solve (GMRES to the same eps_r) at sampler seeds other than the default",
+                      "runs": rows}
+
     # ---- end to end through the C ABI with host buffers ----------------------------
     e2e = None
     if not args.no_e2e:
@@ -624,6 +649,7 @@ def gpu_main(args, rank, world):
             "mixed_rel_err_vs_reference": mixed_rel if fp64 else None,
             "fp64_path": fp64,
             "mixed_unrefined": unref,
+            "solve_seed_study": seed_study,
             "differentiation": diff,
             "batched": batched,
             "accuracy_reference": reference if fp64 else None,
@@ -676,6 +702,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-seed-study", action="store_true", help="skip the mixed solve at other sampler seeds")
     ap.add_argument("--no-autotune", action="store_true", help="default kernel variants instead of kf_autotune's")
     ap.add_argument("--batched-n", type=int, default=256, help="problems of the batched workload")
     ap.add_argument("--once", action="store_true",

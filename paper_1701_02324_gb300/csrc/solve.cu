@@ -82,7 +82,7 @@ __device__ __forceinline__ void warp_tile_rowupd(int r0, int r1, int kb, int nb,
 }
 
 template <typename TM, typename TV>
-__global__ void __launch_bounds__(256, sizeof(TM) == 4 ? 2 : 1) k_leaf_solve(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+__global__ void __launch_bounds__(256, 2) k_leaf_solve(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                     int leaf0, int ldL, const TM* __restrict__ Lall,
                                                     TV* __restrict__ W, int k) {
   constexpr int NB = 32;
@@ -289,12 +289,71 @@ __global__ void __launch_bounds__(256) k_rowupd(const int32_t* __restrict__ lo, 
   }
 }
 
+// One right-hand side, stored M: a warp takes 32 rows and walks the columns
+// in 32-wide tiles, each tile loaded row by row (coalesced) into the warp's
+// shared-memory tile and read back transposed, so that lane q accumulates row
+// q's dot product with no cross-lane reduction.  Every FMA is then a useful
+// one: on the FP64 path this pass is bound by the FP64 pipe (one FMA per 8
+// bytes of M), and the shuffle reductions of k_rowupd cost it another 60%.
+template <typename TM, typename TV>
+__global__ void __launch_bounds__(256) k_rowupd_tile(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                     const int32_t* __restrict__ rank, int node0, int s_max,
+                                                     int sibling_mode, const TM* __restrict__ M,
+                                                     const double* __restrict__ V, double sign, TV* __restrict__ W) {
+  __shared__ TV vs[KF_MAX_SMAX + 32];
+  extern __shared__ __align__(16) unsigned char rt_smem[];
+  TM(*tile)[32][33] = (TM(*)[32][33])rt_smem;  // 8 warps x 32 x 33, dynamic
+  const int nl = blockIdx.y, node = node0 + nl, sib = node ^ 1;
+  const int b = lo[node], n = hi[node] - b;
+  const int cnt = sibling_mode ? rank[sib] : rank[node];
+  const int from = sibling_mode ? sib : node;
+  const int r0 = blockIdx.x * kRowUpdRows;
+  if (cnt == 0 || r0 >= n) return;
+  const int r1 = min(n, r0 + kRowUpdRows);
+  const double* v = V + (int64_t)from * s_max;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cpad = (cnt + 31) & ~31;
+  for (int q = threadIdx.x; q < cpad; q += blockDim.x) vs[q] = q < cnt ? (TV)v[q] : (TV)0;
+  __syncthreads();
+  TM(*t)[33] = tile[warp];
+  for (int i0 = r0 + warp * 32; i0 < r1; i0 += 8 * 32) {
+    TV acc = (TV)0;
+    for (int q0 = 0; q0 < cnt; q0 += 32) {
+      TM x[32];
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr)
+        x[rr] = (i0 + rr < r1 && q0 + lane < cnt) ? M[(int64_t)(b + i0 + rr) * s_max + q0 + lane] : (TM)0;
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) t[rr][lane] = x[rr];
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc += (TV)t[lane][j] * vs[q0 + j];
+      __syncwarp();
+    }
+    if (i0 + lane < r1) W[b + i0 + lane] += (TV)sign * acc;
+  }
+}
+
 template <typename TM, typename TV>
 void launch_rowupd(int64_t rows, int nnodes, cudaStream_t s, const int32_t* lo, const int32_t* hi, const int32_t* rank,
                    const int32_t* skel, int node0, int s_max, int sib, int src, const TM* M, const double* X64,
                    const float* X32, int d, double c_exp, double inv_h3, const double* V, double sign, TV* W, int k,
                    int phase = KF_PH_S_ROWUPD) {
   dim3 g((unsigned)((rows + kRowUpdRows - 1) / kRowUpdRows), nnodes);
+  // FP64 M: the tiled form (FP64-pipe bound); FP32 M: the warp-per-row form,
+  // which streams at about 75% of HBM bandwidth
+  if constexpr (sizeof(TM) == 8) {
+    if (k == 1 && src == SRC_STORED) {
+      const int smem = (int)(sizeof(TM) * 8 * 32 * 33);
+      static bool attr_set = false;  // per instantiation; setting it twice is harmless
+      if (!attr_set) {
+        cudaFuncSetAttribute(k_rowupd_tile<TM, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr_set = true;
+      }
+      KF_PHASE(phase, s, k_rowupd_tile<TM, TV><<<g, 256, smem, s>>>(lo, hi, rank, node0, s_max, sib, M, V, sign, W));
+      return;
+    }
+  }
   if (k == 1)
     KF_PHASE(phase, s, k_rowupd<TM, TV, 1><<<g, 256, 0, s>>>(lo, hi, rank, skel, node0, nnodes, s_max, sib, src, M,
                                                                      X64, X32, d, c_exp, inv_h3, V, sign, W, k));
