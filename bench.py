@@ -213,7 +213,7 @@ def phase_rooflines(work, phase_ms, phase_launches, steps, peaks):
         rate = amount * count / (ms * 1e-3)
         pk, unit, scale, src = peak[kind]
         out[ph] = {"bound": {"fp64": "alu", "fp32": "alu", "fp32i": "alu", "tf32": "tensor", "hbm": "hbm"}[kind],
-                   "achieved": round(rate / scale, 3), "unit": unit, "peak": round(pk / scale, 1),
+                   "achieved": round(rate / scale, 3), "unit": unit, "peak": round(pk / scale, 2),
                    "frac": round(rate / pk, 4), "peak_src": src, "per_step": round(count / steps, 2)}
     return out
 
