@@ -82,7 +82,7 @@ __device__ __forceinline__ void warp_tile_rowupd(int r0, int r1, int kb, int nb,
 }
 
 template <typename TM, typename TV>
-__global__ void __launch_bounds__(256, 2) k_leaf_solve(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+__global__ void __launch_bounds__(256, sizeof(TM) == 4 ? 4 : 2) k_leaf_solve(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                     int leaf0, int ldL, const TM* __restrict__ Lall,
                                                     TV* __restrict__ W, int k) {
   constexpr int NB = 32;

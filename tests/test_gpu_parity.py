@@ -371,3 +371,48 @@ def test_autograd_kernel_solve_matches_oracle_gradient():
     assert rel(bt.grad.cpu().numpy(), dbo) <= 1e-10
     assert abs(lt.grad.item() - dlo) <= 1e-9 * abs(dlo)
     assert abs(ht.grad.item() - dho) <= 1e-8 * abs(dho)
+
+
+# ---------------------------------------------------------------- profiler
+def test_profile_totals_and_timeline(c1):
+    """kf_profile_read totals and kf_profile_timeline records of one
+    factorization: every launch recorded once, in order of issue per stream,
+    with its phase; the per-phase sums of the timeline equal the totals."""
+    import ctypes
+    from paper_1701_02324_gb300 import _abi
+    p, _, tree = c1
+    lib = _abi.load()
+    nph = len(_abi.PHASES)
+    ms = np.zeros(nph)
+    ln = np.zeros(nph, dtype=np.int64)
+    torch.cuda.synchronize()
+    assert lib.kf_profile_enable(1) == 0
+    try:
+        lib.kf_profile_read(ms.ctypes.data, ln.ctypes.data, nph)  # clears earlier records
+        F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=FP64)
+        F.solve(torch.from_numpy(p.B[:, 0]).cuda())
+        torch.cuda.synchronize()
+        cap = 4096
+        t0, t1 = np.zeros(cap), np.zeros(cap)
+        ph, st = np.zeros(cap, np.int32), np.zeros(cap, np.int32)
+        n = ctypes.c_int64(0)
+        assert lib.kf_profile_timeline(t0.ctypes.data, t1.ctypes.data, ph.ctypes.data, st.ctypes.data, cap,
+                                       ctypes.byref(n)) == 0
+        k = n.value
+        assert 0 < k <= cap
+        t0, t1, ph, st = t0[:k], t1[:k], ph[:k], st[:k]
+        assert t0[0] == 0.0 and np.all(t1 >= t0) and np.all(t0 >= 0.0)
+        assert np.all((ph >= 0) & (ph < nph)) and st.min() == 0
+        for s in np.unique(st):  # launches of one stream run in issue order
+            a, b = t0[st == s], t1[st == s]
+            assert np.all(a[1:] >= b[:-1] - 1e-3)
+        assert lib.kf_profile_read(ms.ctypes.data, ln.ctypes.data, nph) == 0
+        assert int(ln.sum()) == k
+        for q in range(nph):
+            assert ln[q] == int(np.sum(ph == q))
+            # event timestamps resolve about 0.5 us: allow 2 us per launch
+            assert abs(ms[q] - float(np.sum((t1 - t0)[ph == q]))) <= 2e-3 * ln[q] + 1e-3 * ms[q]
+        bad = ctypes.c_int64(0)
+        assert lib.kf_profile_timeline(None, None, None, None, 0, ctypes.byref(bad)) == _abi.KF_EINVAL
+    finally:
+        lib.kf_profile_enable(0)
