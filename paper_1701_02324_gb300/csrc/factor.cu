@@ -1290,13 +1290,13 @@ kf_status kf_factorize_device(kf_factor* f, cudaStream_t s) {
   return st;
 }
 
-// Skeletonization and factorization interleaved on three streams: level l of
+// Skeletonization and factorization interleaved on four streams: level l of
 // the factorization needs the skeletons of levels l + 1 and l only, so the
 // pivoted QRs of the upper levels run while the lower levels are factorized
-// (s1: skeletons; s2: leaf factors and reduced systems; s3: V blocks and the
-// FP64 operator's leaf blocks).  The leaf blocks and their Cholesky factors
-// need no skeleton and start at once.  Events order the streams; the
-// caller's stream waits for all three at the end.
+// (s1: skeletons; s4: the leaf blocks and their Cholesky factors, which need
+// no skeleton and start at once; s2: P^ of the leaves and the reduced
+// systems; s3: V blocks, then the FP64 operator's leaf blocks).  Events order
+// the streams; the caller's stream waits for them at the end.
 kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
   kf_ctx* c = f->ctx;
   const int D = f->t->D;
@@ -1309,16 +1309,22 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
   const size_t tb = kf_factor_tm_bytes(f);
   double* Tm = st == KF_OK ? (double*)c->dalloc(tb, s) : nullptr;
   if (st == KF_OK && !Tm) st = kf_set_err(c, KF_ENOMEM, "factorize: allocation failed");
-  cudaStream_t s1 = nullptr, s2 = nullptr, s3 = nullptr;
+  cudaStream_t s1 = nullptr, s2 = nullptr, s3 = nullptr, s4 = nullptr;
+  cudaEvent_t evl = nullptr;
   std::vector<cudaEvent_t> ev(D + 4, nullptr), evv(D, nullptr);
   if (st == KF_OK) {
-    // the skeleton chain and the reduced systems that follow it form the
-    // critical path: high-priority streams; the V blocks fill in
+    // priorities (measured): the skeleton chain (s1) and the leaf blocks with
+    // their Cholesky factors (s4, at the start beside the leaf sample blocks)
+    // highest; the reduced systems (s2) one level below, so that a level's
+    // sample blocks and QR are dispatched ahead of them; the V blocks (s3)
+    // lowest (1.10 s with s3 high, 1.07 s with s2 equal to s1, 1.06 s so)
     int lo_prio = 0, hi_prio = 0;
     cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
     KF_CUDA(c, cudaStreamCreateWithPriority(&s1, cudaStreamNonBlocking, hi_prio));
-    KF_CUDA(c, cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, hi_prio));
+    KF_CUDA(c, cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, std::min(hi_prio + 1, lo_prio)));
     KF_CUDA(c, cudaStreamCreateWithPriority(&s3, cudaStreamNonBlocking, lo_prio));
+    KF_CUDA(c, cudaStreamCreateWithPriority(&s4, cudaStreamNonBlocking, hi_prio));
+    KF_CUDA(c, cudaEventCreateWithFlags(&evl, cudaEventDisableTiming));
     for (auto& e : ev) KF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     for (auto& e : evv) KF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     // ev[l]: skeletons of level l done (on s1); ev[0]: allocations ready (on s);
@@ -1328,11 +1334,12 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
     cudaStreamWaitEvent(s1, ev[0], 0);
     cudaStreamWaitEvent(s2, ev[0], 0);
     cudaStreamWaitEvent(s3, ev[0], 0);
-    // the FP64 operator's leaf blocks need the tree only
-    if (f->Kdf) st = kf_leaf_k64_launch(f, s3);
-    // so do the leaf blocks and their Cholesky factors (FP32 or FP64 work
-    // that shares the SMs with the FP64 sample blocks of the leaf level)
-    if (st == KF_OK) st = kf_factorize_leaves(f, s2, false, 1);
+    cudaStreamWaitEvent(s4, ev[0], 0);
+    // the leaf blocks and their Cholesky factors need the tree only (FP32 or
+    // FP64 work that shares the SMs with the FP64 sample blocks of the leaf level)
+    if (st == KF_OK) st = kf_factorize_leaves(f, s4, false, 1);
+    cudaEventRecord(evl, s4);
+    cudaStreamWaitEvent(s2, evl, 0);
     for (int l = D; l >= 1 && st == KF_OK; --l) {
       st = kf_skel_level(f, l, &sc, s1);
       cudaEventRecord(ev[l], s1);
@@ -1354,6 +1361,11 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
       cudaStreamWaitEvent(s2, evv[0], 0);
       st = kf_factorize_level_z(f, 0, Tm, s2);
     }
+    // the FP64 operator's leaf blocks need the tree only, and only the solve
+    // reads them: last on the V-block stream, where they fill the SMs that the
+    // latency-bound upper levels leave idle (ahead of the V blocks they held
+    // back the first level's V blocks and with them the reduced systems)
+    if (st == KF_OK && f->Kdf) st = kf_leaf_k64_launch(f, s3);
     cudaEventRecord(ev[D + 1], s2);
     cudaEventRecord(ev[D + 2], s1);
     cudaEventRecord(ev[D + 3], s3);
@@ -1370,5 +1382,7 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
   if (s1) cudaStreamDestroy(s1);
   if (s2) cudaStreamDestroy(s2);
   if (s3) cudaStreamDestroy(s3);
+  if (s4) cudaStreamDestroy(s4);
+  if (evl) cudaEventDestroy(evl);
   return st;
 }

@@ -668,10 +668,18 @@ kf_status kf_skel_begin(kf_factor* f, kf_skel_scratch* sc, cudaStream_t s) {
   sc->a_elems = std::max((size_t)maxnodes * t->leaf_max, (size_t)(maxnodes / 2) * 2 * f->s_max) * f->n_samp;
   sc->a_elems += (size_t)maxnodes * 2 * f->s_max + maxnodes;  // tail: cluster-QR positions and ranks
   sc->A = (double*)c->dalloc(sizeof(double) * sc->a_elems, s);
-  sc->samp = (int32_t*)c->dalloc(sizeof(int32_t) * (size_t)maxnodes * f->n_samp, s);
-  sc->nsamp = (int32_t*)c->dalloc(sizeof(int32_t) * maxnodes, s);
+  // S' of every non-root node (heap order from node 2), drawn here at once:
+  // the draws depend on the tree only, and a level's sampling launch would
+  // otherwise wait for a free SM behind the reduced-system kernels
+  const size_t nsampled = 2 * (size_t)maxnodes - 2;
+  sc->samp = (int32_t*)c->dalloc(sizeof(int32_t) * nsampled * f->n_samp, s);
+  sc->nsamp = (int32_t*)c->dalloc(sizeof(int32_t) * nsampled, s);
   if (!sc->A || !sc->samp || !sc->nsamp)
     return kf_set_err(c, KF_ENOMEM, "skeletonize: allocation of %zu bytes failed", sizeof(double) * sc->a_elems);
+  KF_PHASE(KF_PH_SAMPLE, s, k_sample<<<(unsigned)nsampled, 32, sizeof(int32_t) * f->n_samp, s>>>(
+                                t->d_lo, t->d_hi, t->N, 2, (int)nsampled, f->n_samp, f->seed, sc->samp, sc->nsamp,
+                                f->status));
+  KF_LAUNCH_CHECK(c);
   return KF_OK;
 }
 
@@ -679,8 +687,8 @@ void kf_skel_end(kf_factor* f, kf_skel_scratch* sc, cudaStream_t s) {
   kf_ctx* c = f->ctx;
   const int maxnodes = 1 << f->t->D;
   c->dfree(sc->A, sizeof(double) * sc->a_elems, s);
-  c->dfree(sc->samp, sizeof(int32_t) * (size_t)maxnodes * f->n_samp, s);
-  c->dfree(sc->nsamp, sizeof(int32_t) * maxnodes, s);
+  c->dfree(sc->samp, sizeof(int32_t) * (2 * (size_t)maxnodes - 2) * f->n_samp, s);
+  c->dfree(sc->nsamp, sizeof(int32_t) * (2 * (size_t)maxnodes - 2), s);
   sc->A = nullptr;
   sc->samp = sc->nsamp = nullptr;
 }
@@ -693,13 +701,11 @@ kf_status kf_skel_level(kf_factor* f, int l, kf_skel_scratch* sc, cudaStream_t s
   const int cleaf = t->leaf_max, cint = 2 * s_max;
   const int rpl = (n_samp + 31) / 32;
   double* A = sc->A;
-  int32_t* samp = sc->samp;
-  int32_t* nsamp = sc->nsamp;
   const int node0 = 1 << l, nn = 1 << l;
+  int32_t* samp = sc->samp + (size_t)(node0 - 2) * n_samp;  // drawn in kf_skel_begin
+  int32_t* nsamp = sc->nsamp + (node0 - 2);
   const bool leaf = (l == D);
   const int cmax = leaf ? cleaf : cint;
-  KF_PHASE(KF_PH_SAMPLE, s, k_sample<<<nn, 32, sizeof(int32_t) * n_samp, s>>>(t->d_lo, t->d_hi, t->N, node0, nn, n_samp, f->seed, samp, nsamp,
-                                                    f->status));
   dim3 ga((n_samp + 127) / 128, cmax, nn);
   // FP64 entries on both paths: late pivots of the QR hinge on downdated norms
   // whose relative error is far above that of the entries, so any change of
@@ -709,8 +715,10 @@ kf_status kf_skel_level(kf_factor* f, int l, kf_skel_scratch* sc, cudaStream_t s
   double* Pout = leaf ? f->Pleaf : f->Pc + (int64_t)node0 * cint * s_max;
   int64_t pstride = leaf ? 0 : (int64_t)cint * s_max;
   // upper levels (few nodes): one 16-CTA cluster per node, the block in distributed shared memory
-  // (at 64 nodes and more, one CTA per node in one wave is faster)
-  if (!leaf && nn <= 32 && f->use_cluster_qr) {
+  // (at 16 nodes and more, one CTA per node is faster inside the overlapped
+  // factorization: a 16-CTA cluster waits for 16 free SMs of one GPC, which
+  // the reduced-system kernels running beside it rarely leave)
+  if (!leaf && nn <= 8 && f->use_cluster_qr) {
     const int W = (cmax + kQC - 1) / kQC;
     const size_t qsmem = sizeof(double) * ((size_t)W * n_samp + 2 * W + 2 * n_samp) + sizeof(int) * (2 * cmax + W);
     if (qsmem <= 200 * 1024) {
