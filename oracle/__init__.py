@@ -73,6 +73,7 @@ def _load():
             "kfo_solve": (I32, [P, P, P, I32]),
             "kfo_matvec": (I32, [P, P, P, I32]),
             "kfo_grad": (I32, [P, P, P, P, P, P]),
+            "kfo_subtrees": (I32, [P, P, I32, D, D, I32, I32, U64, D]),
             "kfo_splitmix64": (U64, [U64]),
         }
         for name, (res, args) in sig.items():
@@ -172,6 +173,20 @@ class Oracle:
         st = self._lib.kfo_set_id(self._h, a, len(skel), _ptr(skel), _ptr(P))
         if st != KFO_OK:
             raise ValueError(f"oracle set_id status {st}")
+
+    def subtrees(self, roots, h: float, tau: float, s_max: int, lam: float, n_samp: int | None = None,
+                 seed: int = 0x1701) -> int:
+        """Algorithms 1 and 2 on the disjoint subtrees under ``roots`` only
+        (the nodes there get the values a whole run gives them)."""
+        if n_samp is None:
+            n_samp = 2 * s_max
+        r = np.ascontiguousarray(roots, dtype=np.int32)
+        self.h, self.tau, self.s_max, self.lam = float(h), float(tau), int(s_max), float(lam)
+        st = self._lib.kfo_subtrees(self._h, _ptr(r), len(r), float(h), float(tau), int(s_max), int(n_samp),
+                                    ctypes.c_uint64(seed), float(lam))
+        if st not in (KFO_OK, KFO_EILLCOND):
+            raise ValueError(f"oracle subtrees status {st}")
+        return int(st)
 
     # ---- factorization ------------------------------------------------------
     def factorize(self, lam: float, variant: int = 0) -> int:

@@ -830,3 +830,50 @@ int32_t kfo_grad(const kfo* o, const double* x, const double* g, double* dLdb, d
   free(dx);
   return KFO_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Algorithms 1 and 2 on chosen subtrees only.  The ID of a node reads its own
+ * columns and its sampled rows S' (drawn from the complement in the whole
+ * tree), and Z, P^ and the leaf factors of a node read only its descendants'
+ * skeletons and factors; so every node under the given roots gets exactly the
+ * values kfo_skeletonize followed by kfo_factorize give it (a root that is the
+ * tree root gets no ID and no P^, as there).  The rest of the tree is not
+ * touched.  This checks single nodes of trees too large for a whole run. */
+static void clear_node(node_t* n) {
+  free(n->skel); free(n->P); free(n->Pfull);
+  free(n->LU); free(n->piv); free(n->Phat); free(n->Vl); free(n->Vr);
+  free(n->Z); free(n->ZLU); free(n->Zpiv);
+  memset(n, 0, sizeof(node_t));
+}
+
+static int is_ancestor_or_self(int32_t a, int32_t b) {
+  while (b > a) b >>= 1;
+  return a == b;
+}
+
+int32_t kfo_subtrees(kfo* o, const int32_t* roots, int32_t nroots, double h, double tau, int32_t s_max,
+                     int32_t n_samp, uint64_t seed, double lambda) {
+  if (!o || !roots || nroots < 1 || !(h > 0.0) || !(tau >= 0.0) || s_max < 0 || n_samp < 0 || !(lambda >= 0.0))
+    return KFO_EINVAL;
+  for (int32_t i = 0; i < nroots; ++i) {
+    if (roots[i] < 1 || roots[i] > o->nnodes) return KFO_EINVAL;
+    for (int32_t j = 0; j < nroots; ++j)
+      if (i != j && (is_ancestor_or_self(roots[i], roots[j]) || is_ancestor_or_self(roots[j], roots[i])))
+        return KFO_EINVAL;  /* subtrees must be disjoint */
+  }
+  for (int32_t i = 0; i < nroots; ++i)
+    for (int32_t lv = 0; ((int64_t)roots[i] << lv) <= o->nnodes; ++lv)
+      for (int64_t b = (int64_t)roots[i] << lv; b < ((int64_t)roots[i] + 1) << lv; ++b) clear_node(&o->nd[b]);
+  o->h = h;
+  o->c_exp = -0.5 / (h * h);
+  o->lambda = lambda;
+  o->variant = 0;
+  o->illcond = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int32_t i = 0; i < nroots; ++i) {
+    skeletonize_rec(o, roots[i], tau, s_max, n_samp, seed);
+    factorize_rec(o, roots[i]);
+  }
+  if (nroots == 1 && roots[0] == 1) o->skeletonized = o->factorized = 1; /* the whole tree */
+  return o->illcond ? KFO_EILLCOND : KFO_OK;
+}

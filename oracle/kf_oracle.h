@@ -72,6 +72,15 @@ int32_t kfo_matvec(const kfo* o, const double* x, double* y, int32_t deriv);
  * returns dL/db (N), dL/dlambda and dL/dh. */
 int32_t kfo_grad(const kfo* o, const double* x, const double* g, double* dLdb, double* dLdlambda, double* dLdh);
 
+/* Algorithms 1 and 2 restricted to the disjoint subtrees under the given
+ * roots: each of their nodes gets the skeleton, P, Z and P^ that
+ * kfo_skeletonize + kfo_factorize would give it; other nodes are untouched
+ * (their accessors then return nothing meaningful).  For checks of sampled
+ * nodes at sizes where the whole tree takes too long.  KFO_EINVAL when a
+ * root is out of range or lies inside another root's subtree. */
+int32_t kfo_subtrees(kfo* o, const int32_t* roots, int32_t nroots, double h, double tau, int32_t s_max,
+                     int32_t n_samp, uint64_t seed, double lambda);
+
 /* splitmix64 output function (used by the sampler); exposed for its pin. */
 uint64_t kfo_splitmix64(uint64_t x);
 

@@ -401,3 +401,35 @@ def test_gradient_close_to_dense_reference():
     assert np.linalg.norm(db - ad) / np.linalg.norm(ad) < 1e-5
     assert abs(dlam - (-ad @ xd)) / abs(ad @ xd) < 1e-5
     assert abs(dh - (-ad @ dK @ xd)) / abs(ad @ dK @ xd) < 1e-4
+
+
+def test_subtrees_equal_the_whole_run():
+    """kfo_subtrees (Algorithms 1 and 2 on chosen subtrees only, used to check
+    sampled nodes of trees too large for a whole oracle run) gives every node
+    of those subtrees bit for bit what the whole run gives it: each node's ID
+    reads only its own columns and its sampled rows, each P^ only its
+    descendants.  The whole run is pinned by the tests above.  Also a subtree
+    root at the tree root, and overlapping roots rejected."""
+    X, _ = make(N=3000, d=4, m=100, seed=14)
+    whole, part = Oracle(X, 100), Oracle(X, 100)
+    whole.skeletonize(0.4, 1e-6, 24)
+    assert whole.factorize(0.6) == KFO_OK
+    roots = [8, 11, 13]                               # disjoint level-3 subtrees
+    assert part.subtrees(roots, 0.4, 1e-6, 24, 0.6) == KFO_OK
+    for a in roots:
+        for lv in range(whole.D - 3 + 1):
+            for b in range(a << lv, (a + 1) << lv):
+                assert part.rank(b) == whole.rank(b)
+                assert np.array_equal(part.skel(b), whole.skel(b))
+                assert np.array_equal(part.P(b), whole.P(b))
+                assert np.array_equal(part.Phat(b), whole.Phat(b))
+                if not whole.is_leaf(b):
+                    assert np.array_equal(part.Z(b), whole.Z(b))
+    full = Oracle(X, 100)
+    full.subtrees([1], 0.4, 1e-6, 24, 0.6)
+    for b in range(2, whole.nnodes + 1):
+        assert np.array_equal(full.Phat(b), whole.Phat(b))
+    b = np.random.default_rng(3).standard_normal(3000)
+    np.testing.assert_array_equal(full.solve(b), whole.solve(b))
+    with pytest.raises(ValueError):
+        part.subtrees([4, 9], 0.4, 1e-6, 24, 0.6)     # 9 lies under 4
