@@ -152,8 +152,11 @@ kf_status kf_factor_free(kf_factor* f);
  * the solve is refined against the hierarchical operator, with FP64
  * accumulation, until the relative residual (Eq. e:errors) is below
  * opts.refine_tol: by x += M^-1 r or by GMRES(m) (opts.gmres_restart), M being
- * the factorization.  The operator is FP64-accurate when opts.fp64_operator is
- * set (or on the FP64 path); otherwise the mixed path evaluates it in FP32. */
+ * the factorization.  A transpose solve is refined the same way against the
+ * transposed operator, M^-T being the transpose sweep.  The operator is
+ * FP64-accurate when opts.fp64_operator is set (or on the FP64 path);
+ * otherwise the mixed path evaluates it in FP32.  KF_ENOTCONV when the
+ * refinement stops above refine_tol (X then holds the last iterate). */
 kf_status kf_solve(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t ld, int32_t dtype,
                    int32_t transpose, void* stream, kf_solve_info* info);
 /* Y = (lambda I + K~) X with the operator the factorization inverts
@@ -162,9 +165,13 @@ kf_status kf_solve(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t l
 kf_status kf_matvec(kf_factor* f, const void* X, void* Y, int64_t nrhs, int64_t ld, int32_t dtype, void* stream);
 /* Gradient of a loss L through x = (lambda I + K~)^-1 b given x and dL/dx:
  * a = (lambda I + K~)^-T dL/dx; dL/db = a; dL/dlambda = -sum a.x;
- * dL/dh = -sum a.(dK~/dh) x with skeletons and P held fixed.  x, dLdx, dLdb:
- * N x nrhs (ld), device or host, FP64.  dLdlambda, dLdh: host, one value
- * summed over the RHS columns. */
+ * dL/dh = -sum a.(dK~/dh) x with skeletons and P held fixed.  The adjoint
+ * solve for a is refined like kf_solve(transpose = 1) whenever the factor's
+ * solves are refined (mixed path by default); dK~/dh is evaluated from the FP64
+ * coordinates on both paths.  x, dLdx, dLdb: N x nrhs (ld), device or host,
+ * FP64.  dLdlambda, dLdh: host, one value summed over the RHS columns.  Not in
+ * the paper: the adjoint of Algorithm 3 through the factorization of
+ * Eq. (e:smw). */
 kf_status kf_grad(kf_factor* f, const void* x, const void* dLdx, void* dLdb, double* dLdlambda,
                   double* dLdh, int64_t nrhs, int64_t ld, void* stream);
 

@@ -685,11 +685,16 @@ static kf_status with_vectors(kf_factor* f, const void* B, void* X, int64_t nrhs
 }
 
 // max over columns of ||r_j|| / ||b_j||
+// y = A x or A^T x with A = lambda I + K~ (the operator the refinement uses).
+static kf_status apply_op(kf_factor* f, const double* x, double* y, int64_t k, int transpose, cudaStream_t s) {
+  return transpose ? kf_matvec_transpose_device(f, x, y, k, s) : kf_matvec_device(f, x, y, k, 0, s);
+}
+
 static kf_status rel_residual(kf_factor* f, const double* Bt, const double* Xt, int64_t k, double* R, double* Y,
-                              double* nrm, cudaStream_t s, double* out) {
+                              double* nrm, int transpose, cudaStream_t s, double* out) {
   kf_ctx* c = f->ctx;
   const int64_t N = f->t->N;
-  kf_status st = kf_matvec_device(f, Xt, Y, k, 0, s);
+  kf_status st = apply_op(f, Xt, Y, k, transpose, s);
   if (st != KF_OK) return st;
   KF_PHASE(KF_PH_MISC, s, k_sub<<<grid_for(N * k, 256), 256, 0, s>>>(Bt, Y, R, N * k));
   KF_CUDA(c, cudaMemsetAsync(nrm, 0, sizeof(double) * 2 * k, s));
@@ -704,12 +709,13 @@ static kf_status rel_residual(kf_factor* f, const double* Bt, const double* Xt, 
   return KF_OK;
 }
 
-// GMRES(m) for (lambda I + K~) x = b, one column: right preconditioning by
-// the factorization (z_j = M^-1 v_j kept), FP64 Krylov basis orthogonalized
-// by classical Gram-Schmidt applied twice, Givens rotations on the host, the
-// true residual recomputed at every restart.  x holds the initial guess.
+// GMRES(m) for (lambda I + K~) x = b (or its transpose system), one column:
+// right preconditioning by the factorization (z_j = M^-1 v_j, or M^-T v_j,
+// kept), FP64 Krylov basis orthogonalized by classical Gram-Schmidt applied
+// twice, Givens rotations on the host, the true residual recomputed at every
+// restart.  x holds the initial guess.
 static kf_status gmres_column(kf_factor* f, const double* b, double* x, double bnorm, int m, int maxit, double tol,
-                              cudaStream_t s, double* eps, int* iters) {
+                              int transpose, cudaStream_t s, double* eps, int* iters) {
   kf_ctx* c = f->ctx;
   const int64_t N = f->t->N;
   const size_t vb = sizeof(double) * N;
@@ -728,7 +734,7 @@ static kf_status gmres_column(kf_factor* f, const double* b, double* x, double b
   int it = 0;
   while (st == KF_OK) {
     // r = b - A x, beta = ||r||
-    st = kf_matvec_device(f, x, w, 1, 0, s);
+    st = apply_op(f, x, w, 1, transpose, s);
     if (st != KF_OK) break;
     KF_PHASE(KF_PH_MISC, s, k_sub<<<g, 256, 0, s>>>(b, w, w, N));
     cudaMemsetAsync(h, 0, sizeof(double), s);
@@ -744,8 +750,8 @@ static kf_status gmres_column(kf_factor* f, const double* b, double* x, double b
     for (; j < m && it < maxit; ++j, ++it) {
       double* zj = Zb + (int64_t)j * N;
       KF_CUDA(c, cudaMemcpyAsync(zj, V + (int64_t)j * N, vb, cudaMemcpyDeviceToDevice, s));
-      if ((st = kf_solve_device(f, zj, 1, 0, s)) != KF_OK) break;       // z_j = M^-1 v_j
-      if ((st = kf_matvec_device(f, zj, w, 1, 0, s)) != KF_OK) break;   // w = A z_j
+      if ((st = kf_solve_device(f, zj, 1, transpose, s)) != KF_OK) break;  // z_j = M^-1 v_j (M^-T v_j)
+      if ((st = apply_op(f, zj, w, 1, transpose, s)) != KF_OK) break;     // w = A z_j (A^T z_j)
       for (int pass = 0; pass < 2; ++pass) {                            // CGS2
         cudaMemsetAsync(h, 0, sizeof(double) * (j + 1), s);
         KF_PHASE(KF_PH_MISC, s, k_multidot<<<g, 256, 0, s>>>(V, N, j + 1, w, N, h));
@@ -794,20 +800,19 @@ static kf_status gmres_column(kf_factor* f, const double* b, double* x, double b
   return st;
 }
 
-extern "C" {
-
-kf_status kf_solve(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t ld, int32_t dtype, int32_t transpose,
-                   void* stream, kf_solve_info* info) {
-  kf_status st = check_rhs(f, B, X, nrhs, ld, dtype);
-  if (st != KF_OK) return st;
-  cudaStream_t s = (cudaStream_t)stream;
+// Solve in place, W: N x nrhs FP64 in tree order.  The direct sweep of the
+// factorization (Algorithm 3 or its transpose); with refine, GMRES(m) (or
+// x += M^-1 r when gmres_m <= 0) against the operator A (A^T for transpose)
+// until eps_r <= refine_tol; want_eps alone computes the residual of the
+// direct sweep.  Shared by kf_solve and the adjoint solve of kf_grad.
+static kf_status solve_refined(kf_factor* f, double* W, int64_t nrhs, int transpose, bool refine, bool want_eps,
+                               cudaStream_t s, double* eps_out, int* iters_out) {
   kf_ctx* c = f->ctx;
   const int64_t N = f->t->N;
-  const bool refine = (f->prec == KF_PREC_MIXED || f->refine_user) && f->refine_max_iter > 0 && !transpose;
   int iters = 0;
   double eps = -1.0;
-  auto richardson = [&](double* W) -> kf_status {
-    if (!refine && !info) return kf_solve_device(f, W, nrhs, transpose, s);
+  auto richardson = [&]() -> kf_status {
+    if (!refine && !want_eps) return kf_solve_device(f, W, nrhs, transpose, s);
     const size_t vb = sizeof(double) * N * nrhs;
     double* Bt = (double*)c->dalloc(vb, s);
     double* R = (double*)c->dalloc(vb, s);
@@ -817,14 +822,14 @@ kf_status kf_solve(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t l
     if (r == KF_OK) {
       cudaMemcpyAsync(Bt, W, vb, cudaMemcpyDeviceToDevice, s);
       r = kf_solve_device(f, W, nrhs, transpose, s);
-      if (r == KF_OK && !transpose) {
-        r = rel_residual(f, Bt, W, nrhs, R, Y, nrm, s, &eps);
+      if (r == KF_OK) {
+        r = rel_residual(f, Bt, W, nrhs, R, Y, nrm, transpose, s, &eps);
         while (r == KF_OK && refine && eps > f->refine_tol && iters < f->refine_max_iter) {
-          r = kf_solve_device(f, R, nrhs, 0, s);  // correction M^-1 r
+          r = kf_solve_device(f, R, nrhs, transpose, s);  // correction M^-1 r (M^-T r)
           if (r != KF_OK) break;
           KF_PHASE(KF_PH_MISC, s, k_add<<<grid_for(N * nrhs, 256), 256, 0, s>>>(W, R, N * nrhs));
           ++iters;
-          r = rel_residual(f, Bt, W, nrhs, R, Y, nrm, s, &eps);
+          r = rel_residual(f, Bt, W, nrhs, R, Y, nrm, transpose, s, &eps);
         }
         if (r == KF_OK && refine && eps > f->refine_tol)
           r = kf_set_err(c, KF_ENOTCONV, "refinement stopped at eps_r = %.3e after %d steps", eps, iters);
@@ -836,7 +841,7 @@ kf_status kf_solve(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t l
     c->dfree(nrm, sizeof(double) * 2 * nrhs, s);
     return r;
   };
-  auto gmres_path = [&](double* W) -> kf_status {
+  auto gmres_path = [&]() -> kf_status {
     // GMRES(m) per column, starting from the direct solve of the factorization
     const size_t cb = sizeof(double) * N;
     double* bcol = (double*)c->dalloc(cb, s);
@@ -847,7 +852,7 @@ kf_status kf_solve(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t l
     for (int64_t col = 0; col < nrhs && r == KF_OK; ++col) {
       KF_PHASE(KF_PH_MISC, s, k_get_col<<<grid_for(N, 256), 256, 0, s>>>(W, nrhs, col, bcol, N));
       cudaMemcpyAsync(xcol, bcol, cb, cudaMemcpyDeviceToDevice, s);
-      if ((r = kf_solve_device(f, xcol, 1, 0, s)) != KF_OK) break;
+      if ((r = kf_solve_device(f, xcol, 1, transpose, s)) != KF_OK) break;
       cudaMemsetAsync(nb, 0, sizeof(double), s);
       KF_PHASE(KF_PH_MISC, s, k_colnorm2<<<grid_for(N, 256, 304), 256, 0, s>>>(bcol, N, 1, nb));
       double hb = 0.0;
@@ -855,7 +860,8 @@ kf_status kf_solve(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t l
       cudaStreamSynchronize(s);
       double e = 0.0;
       int its = 0;
-      r = gmres_column(f, bcol, xcol, sqrt(hb), f->gmres_m, f->refine_max_iter, f->refine_tol, s, &e, &its);
+      r = gmres_column(f, bcol, xcol, sqrt(hb), f->gmres_m, f->refine_max_iter, f->refine_tol, transpose, s, &e,
+                       &its);
       worst = std::max(worst, e);
       iters = std::max(iters, its);
       KF_PHASE(KF_PH_MISC, s, k_put_col<<<grid_for(N, 256), 256, 0, s>>>(xcol, nrhs, col, W, N));
@@ -868,9 +874,29 @@ kf_status kf_solve(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t l
     c->dfree(nb, sizeof(double), s);
     return r;
   };
+  kf_status r = (refine && f->gmres_m > 0) ? gmres_path() : richardson();
+  if (eps_out) *eps_out = eps;
+  if (iters_out) *iters_out = iters;
+  return r;
+}
+
+// Whether solves with this factor are refined: the mixed path by default, the
+// FP64 path when the caller asked for it; refine_max_iter <= 0 turns it off.
+static bool refines(const kf_factor* f) {
+  return (f->prec == KF_PREC_MIXED || f->refine_user) && f->refine_max_iter > 0;
+}
+
+extern "C" {
+
+kf_status kf_solve(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t ld, int32_t dtype, int32_t transpose,
+                   void* stream, kf_solve_info* info) {
+  kf_status st = check_rhs(f, B, X, nrhs, ld, dtype);
+  if (st != KF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  int iters = 0;
+  double eps = -1.0;
   st = with_vectors(f, B, X, nrhs, ld, dtype, s, [&](double* W) -> kf_status {
-    if (refine && f->gmres_m > 0) return gmres_path(W);
-    return richardson(W);
+    return solve_refined(f, W, nrhs, transpose ? 1 : 0, refines(f), info != nullptr, s, &eps, &iters);
   });
   if (info) {
     info->eps_r = eps;
@@ -926,7 +952,9 @@ kf_status kf_grad(kf_factor* f, const void* x, const void* dLdx, void* dLdb, dou
   double hs[2] = {0, 0};
   if (r == KF_OK)
     r = with_vectors(f, dLdx, dLdb, nrhs, ld, KF_F64, s, [&](double* A) -> kf_status {
-      kf_status q = kf_solve_device(f, A, nrhs, 1, s);  // a = (lambda I + K~)^-T dL/dx
+      // a = (lambda I + K~)^-T dL/dx, refined like the forward solve (GMRES on the
+      // transpose system against A^T) where the factor's solves are refined
+      kf_status q = solve_refined(f, A, nrhs, 1, refines(f), false, s, nullptr, nullptr);
       if (q != KF_OK) return q;
       cudaMemsetAsync(sums, 0, sizeof(double) * 2, s);
       KF_PHASE(KF_PH_MISC, s, k_dot_all<<<grid_for(N * nrhs, 256, 304), 256, 0, s>>>(A, Xt, N * nrhs, sums));

@@ -289,3 +289,6 @@ kf_status kf_factorize_level_z(kf_factor* f, int l, double* Tm, cudaStream_t s);
 kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s);
 kf_status kf_solve_device(kf_factor* f, double* W, int64_t nrhs, int transpose, cudaStream_t s);
 kf_status kf_matvec_device(kf_factor* f, const double* Xin, double* Y, int64_t nrhs, int deriv, cudaStream_t s);
+// y = (lambda I + K~)^T x (tree order, N x nrhs FP64), with the same operator
+// data as kf_matvec_device (FP64-accurate on the mixed path when it is stored).
+kf_status kf_matvec_transpose_device(kf_factor* f, const double* Xin, double* Y, int64_t nrhs, cudaStream_t s);

@@ -15,6 +15,10 @@
 //   w_l -= K_{r~ l}^T t_bot; w_r -= K_{l~ r}^T t_top; then the leaves.
 // Operator: leaves (lambda I + K_aa) x; g[c] = K_{c~ sib} x_sib for every
 //   non-root c; pushed down g[children] += P_c g[parent]; y += P_{leaf} g.
+// Transposed operator: leaves as above (K_aa is symmetric); g[leaf] =
+//   P_{leaf}^T x; gathered up g[parent] += P_c^T [g[l]; g[r]]; then for every
+//   non-root c, y_c += K_{c sib~} g[sib] (the transpose of K~_{sib c} =
+//   P_{sib sib~} K_{sib~ c}).
 #include <algorithm>
 
 #include "kf_internal.cuh"
@@ -643,6 +647,63 @@ __global__ void k_push_down(const int32_t* __restrict__ rank, int node0, int s_m
   }
 }
 
+// Gather skeleton weights up (transposed operator): g[a] += P_c^T [g[l]; g[r]].
+__global__ void k_push_up(const int32_t* __restrict__ rank, int node0, int s_max, const double* __restrict__ Pc,
+                          double* __restrict__ G, int k) {
+  const int nl = blockIdx.x, node = node0 + nl;
+  const int l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], s = rank[node];
+  const double* P = Pc + (int64_t)node * 2 * s_max * s_max;
+  const double* gl = G + (int64_t)l * s_max * k;
+  const double* gr = G + (int64_t)r * s_max * k;
+  for (int e = threadIdx.x; e < s * k; e += blockDim.x) {
+    const int q = e / k, c = e % k;
+    double acc = 0.0;
+    for (int i = 0; i < sl; ++i) acc += P[(int64_t)i * s_max + q] * gl[(int64_t)i * k + c];
+    for (int i = 0; i < sr; ++i) acc += P[(int64_t)(sl + i) * s_max + q] * gr[(int64_t)i * k + c];
+    G[((int64_t)node * s_max + q) * k + c] += acc;
+  }
+}
+
+// V pass of the transposed FP64-accurate operator: w[i][r] += sum_q V[i][q]
+// g[sib][q][r] for the rows of every node of a level, V as double-float pairs
+// (row i of node c: K(x_i, sib~)), in double-float arithmetic on the FP32
+// pipes: one warp per row, lanes over q, the lanes' pairs combined with exact
+// two-sums; g[sib] split into pairs in shared memory.
+__global__ void __launch_bounds__(256) k_rowupd_df(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                   const int32_t* __restrict__ rank, int node0, int s_max,
+                                                   const float2* __restrict__ M, const double* __restrict__ G, int k,
+                                                   double* __restrict__ W) {
+  __shared__ float2 gs[KF_MAX_SMAX];
+  const int nl = blockIdx.y, node = node0 + nl, sib = node ^ 1;
+  const int b = lo[node], n = hi[node] - b;
+  const int cnt = rank[sib];
+  const int r0 = blockIdx.x * kRowUpdRows;
+  if (cnt == 0 || r0 >= n) return;
+  const int r1 = min(n, r0 + kRowUpdRows);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = 0; r < k; ++r) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) gs[q] = kf_split_df(G[((int64_t)sib * s_max + q) * k + r]);
+    __syncthreads();
+    for (int i = r0 + warp; i < r1; i += 8) {
+      const float2* Mi = M + (int64_t)(b + i) * s_max;
+      float sh = 0.f, sl = 0.f;
+      for (int q = lane; q < cnt; q += 32) {
+        const float2 m = Mi[q], v = gs[q];
+        kf_df_fma(m.x, m.y, v.x, v.y, sh, sl);
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, sh, off), ol = __shfl_xor_sync(0xffffffffu, sl, off);
+        float t, e;
+        kf_two_sum(sh, oh, t, e);
+        e = __fadd_rn(e, __fadd_rn(sl, ol));
+        kf_fast_two_sum(t, e, sh, sl);
+      }
+      if (lane == 0) W[(int64_t)(b + i) * k + r] += (double)sh + (double)sl;
+    }
+  }
+}
+
 template <typename TV>
 __global__ void k_axpy_cast(const double* __restrict__ a, TV* __restrict__ b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -708,15 +769,19 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
 }
 
 template <typename TM>
-kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deriv, double* G, cudaStream_t s) {
+kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deriv, int transpose, double* G,
+                   cudaStream_t s) {
   kf_tree* t = f->t;
   kf_ctx* c = f->ctx;
   const int D = t->D, s_max = f->s_max;
   const int64_t N = t->N;
-  const TM* VT = (const TM*)f->VT;
+  // stored V blocks are read only when src is SRC_STORED (never for dK~/dh,
+  // which the FP64 instantiation also serves on the mixed path)
+  const TM* VT = deriv ? nullptr : (const TM*)f->VT;
   const int leaf0 = 1 << D;
   const double inv_h3 = 1.0 / (f->h * f->h * f->h);
   const int src = deriv ? SRC_DKERNEL : (f->vstore == KF_V_STORED ? SRC_STORED : SRC_KERNEL);
+  auto vt_level = [&](int l) { return VT ? VT + (int64_t)(l - 1) * N * s_max : nullptr; };
   if (f->Kdf && !deriv) {
     dim3 gl((unsigned)std::max(1, std::min(64, (t->leaf_max * 32 + 255) / 256)), 1 << D);
     const size_t xsm = sizeof(float2) * t->leaf_max;
@@ -731,6 +796,30 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
   }
   if (D == 0) { KF_LAUNCH_CHECK(c); return KF_OK; }
   KF_CUDA(c, cudaMemsetAsync(G, 0, sizeof(double) * (size_t)(t->nnodes + 1) * s_max * k, s));
+  if (transpose) {
+    // g[leaf] = P_leaf^T x, then up the tree, then y_c += K_{c sib~} g[sib] on every level
+    const int64_t lrows = (N >> D) + 1;
+    dim3 gcl((unsigned)((lrows + kRowsPerChunk - 1) / kRowsPerChunk), 1 << D);
+    launch_colsum<double, double>(gcl, s, t->d_lo, t->d_hi, f->rank, f->skel, leaf0, s_max, 0, SRC_STORED, f->Pleaf,
+                                  t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G, KF_PH_MV_ROWUPD);
+    for (int l = D - 1; l >= 1; --l)
+      KF_PHASE(KF_PH_MV_PUSH, s, k_push_up<<<1 << l, 256, 0, s>>>(f->rank, 1 << l, s_max, f->Pc, G, (int)k));
+    for (int l = 1; l <= D; ++l) {
+      const int64_t rows = (N >> l) + 1;
+      if (f->VTdf) {
+        dim3 g((unsigned)((rows + kRowUpdRows - 1) / kRowUpdRows), 1 << l);
+        KF_PHASE(KF_PH_MV_COLSUM, s, k_rowupd_df<<<g, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, 1 << l, s_max,
+                                                                     f->VTdf + (int64_t)(l - 1) * N * s_max, G,
+                                                                     (int)k, y));
+      } else {
+        launch_rowupd<TM, double>(rows, 1 << l, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, s_max, 1, src,
+                                  vt_level(l), t->X64, t->X32, t->d, f->c_exp, inv_h3, G, 1.0, y, (int)k,
+                                  KF_PH_MV_COLSUM);
+      }
+    }
+    KF_LAUNCH_CHECK(c);
+    return KF_OK;
+  }
   for (int l = 1; l <= D; ++l) {
     const int64_t rows = (N >> l) + 1;
     dim3 gc((unsigned)((rows + kRowsPerChunk - 1) / kRowsPerChunk), 1 << l);
@@ -743,9 +832,8 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
         KF_PHASE(KF_PH_MV_COLSUM, s, k_colsum_df<4><<<gc, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, 1 << l, s_max, Vl, x,
                                                                         (int)k, G));
     } else
-      launch_colsum<TM, double>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, s_max, 1, src,
-                                VT + (int64_t)(l - 1) * N * s_max, t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G,
-                                KF_PH_MV_COLSUM);
+      launch_colsum<TM, double>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, s_max, 1, src, vt_level(l),
+                                t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G, KF_PH_MV_COLSUM);
   }
   for (int l = 1; l < D; ++l)
     KF_PHASE(KF_PH_MV_PUSH, s, k_push_down<<<1 << l, 256, 0, s>>>(f->rank, 1 << l, s_max, f->Pc, G, (int)k));
@@ -790,13 +878,25 @@ kf_status kf_solve_device(kf_factor* f, double* W, int64_t k, int transpose, cud
   return st;
 }
 
-kf_status kf_matvec_device(kf_factor* f, const double* x, double* y, int64_t k, int deriv, cudaStream_t s) {
+static kf_status matvec_any(kf_factor* f, const double* x, double* y, int64_t k, int deriv, int transpose,
+                            cudaStream_t s) {
   kf_ctx* c = f->ctx;
   const size_t gb = sizeof(double) * (size_t)(f->t->nnodes + 1) * f->s_max * k;
   double* G = (double*)c->dalloc(gb, s);
   if (!G) return kf_set_err(c, KF_ENOMEM, "matvec: allocation failed");
-  kf_status st = f->prec == KF_PREC_FP64 ? matvec_t<double>(f, x, y, k, deriv, G, s)
-                                         : matvec_t<float>(f, x, y, k, deriv, G, s);
+  // dK~/dh (deriv) is evaluated from the FP64 coordinates on both paths: the
+  // gradient's -a^T (dK~/dh) x cancels heavily (the sum of |terms| is often
+  // 10^3-10^4 times the result), so FP32 entries would leave it at ~1e-4
+  kf_status st = (f->prec == KF_PREC_FP64 || deriv) ? matvec_t<double>(f, x, y, k, deriv, transpose, G, s)
+                                                    : matvec_t<float>(f, x, y, k, deriv, transpose, G, s);
   c->dfree(G, gb, s);
   return st;
+}
+
+kf_status kf_matvec_device(kf_factor* f, const double* x, double* y, int64_t k, int deriv, cudaStream_t s) {
+  return matvec_any(f, x, y, k, deriv, 0, s);
+}
+
+kf_status kf_matvec_transpose_device(kf_factor* f, const double* x, double* y, int64_t k, cudaStream_t s) {
+  return matvec_any(f, x, y, k, 0, 1, s);
 }

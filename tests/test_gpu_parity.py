@@ -218,6 +218,46 @@ def test_matvec_transpose_and_grad_parity(c1):
     assert abs(dh - dho) <= 1e-9 * abs(dho)
 
 
+@pytest.mark.parametrize("prec,extra", [(MIXED, {"refine_tol": 1e-13}),
+                                         (FP64, {"refine_tol": 1e-13, "refine_max_iter": 20, "fp64_operator": True})])
+def test_refined_transpose_solve_and_gradient(c1, prec, extra):
+    """Transpose solves and the adjoint of kf_grad are refined like forward
+    solves: GMRES on the transpose system against the transposed operator
+    (double-float V and leaf blocks on the mixed path, FP64 on the FP64 path),
+    preconditioned by the transpose sweep; both reach the oracle's transpose
+    solve and gradient of the same K~.  dL/dh sums terms about 4,600 times
+    larger than itself here, so it gets 1e-7."""
+    p, o, tree = c1
+    ranks, skel, P = ids_from_oracle(o, p.s_max)
+    F = kf.factorize_with_ids(tree, p.h, p.lam, p.s_max, ranks, skel, P, precision=prec, **extra)
+    b = p.B[:, 0]
+    xt, info = F.solve(torch.from_numpy(b).cuda(), transpose=True, info=True)
+    assert info["eps_r"] <= extra["refine_tol"]
+    assert rel(xt.cpu().numpy(), o.solve(b, transpose=True)) <= 1e-10
+    xo = o.solve(b)
+    y = np.random.default_rng(5).standard_normal(p.N)
+    g = 2 * (xo - y)
+    db, dl, dh = F.grad(torch.from_numpy(xo).cuda(), torch.from_numpy(g).cuda())
+    dbo, dlo, dho = o.grad(xo, g)
+    assert rel(db.cpu().numpy(), dbo) <= 1e-10
+    assert abs(dl - dlo) <= 1e-10 * abs(dlo)
+    assert abs(dh - dho) <= 1e-7 * abs(dho)
+
+
+def test_transposed_operator_ragged_leaves():
+    """The transposed FP64-accurate operator on ragged leaves (N = 5000, 312
+    and 313 points): the refined transpose solve against the oracle's."""
+    X, b = problem(5000, 8, seed=11)
+    o = oracle.Oracle(X, 300)
+    o.skeletonize(0.5, 1e-6, 64)
+    o.factorize(1.0)
+    tree = kf.Tree(torch.from_numpy(X).cuda(), 300)
+    ranks, skel, P = ids_from_oracle(o, 64)
+    F = kf.factorize_with_ids(tree, 0.5, 1.0, 64, ranks, skel, P, precision=MIXED, refine_tol=1e-13)
+    xt = F.solve(torch.from_numpy(b).cuda(), transpose=True).cpu().numpy()
+    assert rel(xt, o.solve(b, transpose=True)) <= 1e-10
+
+
 def test_multiple_rhs_and_float32(c1):
     p, o, tree = c1
     F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=FP64)
