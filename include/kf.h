@@ -98,7 +98,13 @@ typedef struct {
   int32_t no_cluster_kernels; /* 1 = one CTA per node everywhere (no thread-block clusters for the
                              pivoted QR and reduced-system LU of the upper tree levels) */
   int32_t tc_tile_n;      /* mixed path: tile width of the tcgen05 products, 128 or 256 (0 = 256) */
-  int32_t reserved[3];
+  int32_t zinv_max_nodes; /* tree levels with at most this many nodes keep the explicit inverse of
+                             their reduced systems Z for the solve sweep (a product spread over many
+                             CTAs instead of a latency-bound LU solve per node), computed after each
+                             level's LU at 2 z^3 FP64 flops a node: 0 = default (64; none in
+                             kf_factorize_batched, whose concurrent problems hide that latency),
+                             -1 = none */
+  int32_t reserved[2];
 } kf_opts;
 
 /* Filled by kf_solve when non-NULL (synchronizes the stream). */

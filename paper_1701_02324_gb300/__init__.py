@@ -172,8 +172,9 @@ class Tree:
 
 def _opts(precision=KF_PREC_FP64, n_samp=0, seed=0, v_storage=KF_V_STORED, sync_errors=0, refine_tol=0.0,
           refine_max_iter=0, tensor_cores=True, fp64_operator=None, gmres_restart=0, cluster_kernels=True,
-          tc_tile_n=0):
+          tc_tile_n=0, zinv_max_nodes=0):
     o = kf_opts()
+    o.zinv_max_nodes = int(zinv_max_nodes)
     o.no_cluster_kernels = 0 if cluster_kernels else 1
     o.tc_tile_n = int(tc_tile_n)
     o.no_tensor_cores = 0 if tensor_cores else 1
@@ -192,11 +193,11 @@ class Factor:
                  n_samp: int = 0, seed: int = 0, v_storage=KF_V_STORED, refine_tol: float = 0.0,
                  refine_max_iter: int = 0, sync_errors: bool = True, tensor_cores: bool = True,
                  fp64_operator=None, gmres_restart: int = 0, cluster_kernels: bool = True, tc_tile_n: int = 0,
-                 _ids=None):
+                 zinv_max_nodes: int = 0, _ids=None):
         self.tree, self.ctx = tree, tree.ctx
         self.h_, self.lam, self.tau, self.s_max, self.precision = float(h), float(lam), float(tau), int(s_max), precision
         o = _opts(precision, n_samp, seed, v_storage, int(sync_errors), refine_tol, refine_max_iter, tensor_cores,
-                  fp64_operator, gmres_restart, cluster_kernels, tc_tile_n)
+                  fp64_operator, gmres_restart, cluster_kernels, tc_tile_n, zinv_max_nodes)
         h_out = ctypes.c_void_p()
         if _ids is None:
             st = self.ctx.lib.kf_factorize(tree.h, self.h_, self.lam, self.tau, self.s_max, ctypes.byref(o),
@@ -366,7 +367,8 @@ def factorize_batched(trees, hs, lams, taus, s_max: int, precision=KF_PREC_MIXED
     lam = np.ascontiguousarray(lams, dtype=np.float64)
     tau = np.ascontiguousarray(taus, dtype=np.float64)
     o = _opts(precision, n_samp, seed, KF_V_STORED, 0, 0.0, -1, tensor_cores=kw.get("tensor_cores", True),
-              cluster_kernels=kw.get("cluster_kernels", True), tc_tile_n=kw.get("tc_tile_n", 0))
+              cluster_kernels=kw.get("cluster_kernels", True), tc_tile_n=kw.get("tc_tile_n", 0),
+              zinv_max_nodes=kw.get("zinv_max_nodes", 0))
     out = (ctypes.c_void_p * n)()
     tarr = _ptr_array([t.h.value for t in trees])
     st = ctx.lib.kf_factorize_batched(tarr, n, h.ctypes.data_as(ctypes.c_void_p), lam.ctypes.data_as(ctypes.c_void_p),

@@ -34,7 +34,8 @@ class kf_opts(ctypes.Structure):
         ("gmres_restart", ctypes.c_int32),
         ("no_cluster_kernels", ctypes.c_int32),
         ("tc_tile_n", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("zinv_max_nodes", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 

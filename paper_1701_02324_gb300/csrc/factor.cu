@@ -765,7 +765,9 @@ __device__ void zlu_update(double* A, int ldz, int z, int kb, int nb, int part, 
   }
 }
 
-// X[:, q0:q1) = Z^-1 B[:, q0:q1) from the LU in A (columns >= s are zero)
+// X[:, q0:q1) = Z^-1 B[:, q0:q1) from the LU in A (columns >= s are zero;
+// B = nullptr stands for the identity, so that X is Z^-1); s_max is the row
+// stride of B and X
 template <int TC, bool L2>
 __device__ void z_solve_cols_impl(const double* A, int ldz, int z, const double* B, double* X, int s_max, int s,
                                   int q0, int q1, ZShared& sh);
@@ -793,7 +795,8 @@ __device__ void z_solve_cols_impl(const double* A, int ldz, int z, const double*
   const int* rm = sh.rm;
   for (int64_t e = tid; e < (int64_t)ldz * qw; e += blockDim.x) {
     int i = (int)(e / qw), q = q0 + (int)(e % qw);
-    X[(int64_t)i * s_max + q] = (i < z && q < s) ? B[(int64_t)rm[i] * s_max + q] : 0.0;
+    X[(int64_t)i * s_max + q] = (i < z && q < s) ? (B ? B[(int64_t)rm[i] * s_max + q] : (rm[i] == q ? 1.0 : 0.0))
+                                                 : 0.0;
   }
   __syncthreads();
   const int qe = min(q1, s);
@@ -890,6 +893,23 @@ __global__ void __launch_bounds__(256) k_z_factor(const int32_t* __restrict__ ra
   if (!solve_pc) return;
   z_solve_cols<kZTS, false>(A, ldz, z, Pc + (int64_t)node * ldz * s_max, T + (int64_t)nl * ldz * s_max,
                             T32 ? T32 + (int64_t)nl * ldz * s_max : nullptr, s_max, rank[node], 0, s_max, sh);
+}
+
+// Z^-1 of the nodes of a level from their LU (rows stored in pivot order,
+// row map piv): blockIdx.x = node, blockIdx.y = a block of qw columns of the
+// identity, solved with the tiled L and U sweeps of z_solve_cols.
+__global__ void __launch_bounds__(256) k_z_inverse(const int32_t* __restrict__ rank, int node0, int ldz,
+                                                   const double* __restrict__ ZLU, const int32_t* __restrict__ piv,
+                                                   double* __restrict__ Zinv, int qw) {
+  __shared__ ZShared sh;
+  const int node = node0 + blockIdx.x;
+  const int z = rank[2 * node] + rank[2 * node + 1];
+  const int q0 = blockIdx.y * qw;
+  if (q0 >= z) return;
+  for (int i = threadIdx.x; i < z; i += blockDim.x) sh.rm[i] = piv[(int64_t)node * ldz + i];
+  __syncthreads();
+  z_solve_cols_impl<16, false>(ZLU + (int64_t)node * ldz * ldz, ldz, z, nullptr, Zinv + (int64_t)node * ldz * ldz,
+                               ldz, z, q0, min(q0 + qw, ldz), sh);
 }
 
 // cluster size is set at launch (cudaLaunchAttributeClusterDimension)
@@ -1278,6 +1298,15 @@ kf_status kf_factorize_level(kf_factor* f, int l, double* Tm, cudaStream_t s) {
   return st == KF_OK ? kf_factorize_level_z(f, l, Tm, s) : st;
 }
 
+kf_status kf_z_inverse_level(kf_factor* f, int l, cudaStream_t s) {
+  if (l > f->zinv_top) return KF_OK;
+  const int ldz = 2 * f->s_max, qw = 16;
+  dim3 g(1u << l, (unsigned)((ldz + qw - 1) / qw));
+  KF_PHASE(KF_PH_ZLU, s, k_z_inverse<<<g, 256, 0, s>>>(f->rank, 1 << l, ldz, f->ZLU, f->Zpiv, f->Zinv, qw));
+  KF_LAUNCH_CHECK(f->ctx);
+  return KF_OK;
+}
+
 kf_status kf_factorize_device(kf_factor* f, cudaStream_t s) {
   kf_ctx* c = f->ctx;
   kf_status st = kf_factorize_leaves(f, s, true, 0);
@@ -1285,17 +1314,21 @@ kf_status kf_factorize_device(kf_factor* f, cudaStream_t s) {
   const size_t tb = kf_factor_tm_bytes(f);
   double* Tm = (double*)c->dalloc(tb, s);
   if (!Tm) return kf_set_err(c, KF_ENOMEM, "factorize: allocation failed");
-  for (int l = f->t->D - 1; l >= 0 && st == KF_OK; --l) st = kf_factorize_level(f, l, Tm, s);
+  for (int l = f->t->D - 1; l >= 0 && st == KF_OK; --l) {
+    st = kf_factorize_level(f, l, Tm, s);
+    if (st == KF_OK) st = kf_z_inverse_level(f, l, s);
+  }
   c->dfree(Tm, tb, s);
   return st;
 }
 
-// Skeletonization and factorization interleaved on four streams: level l of
+// Skeletonization and factorization interleaved on five streams: level l of
 // the factorization needs the skeletons of levels l + 1 and l only, so the
 // pivoted QRs of the upper levels run while the lower levels are factorized
 // (s1: skeletons; s4: the leaf blocks and their Cholesky factors, which need
 // no skeleton and start at once; s2: P^ of the leaves and the reduced
-// systems; s3: V blocks, then the FP64 operator's leaf blocks).  Events order
+// systems; s3: V blocks, then the FP64 operator's leaf blocks; s5: Z^-1 of the
+// upper levels, each after its level's LU).  Events order
 // the streams; the caller's stream waits for them at the end.
 kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
   kf_ctx* c = f->ctx;
@@ -1309,9 +1342,9 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
   const size_t tb = kf_factor_tm_bytes(f);
   double* Tm = st == KF_OK ? (double*)c->dalloc(tb, s) : nullptr;
   if (st == KF_OK && !Tm) st = kf_set_err(c, KF_ENOMEM, "factorize: allocation failed");
-  cudaStream_t s1 = nullptr, s2 = nullptr, s3 = nullptr, s4 = nullptr;
-  cudaEvent_t evl = nullptr;
-  std::vector<cudaEvent_t> ev(D + 4, nullptr), evv(D, nullptr);
+  cudaStream_t s1 = nullptr, s2 = nullptr, s3 = nullptr, s4 = nullptr, s5 = nullptr;
+  cudaEvent_t evl = nullptr, evi = nullptr;
+  std::vector<cudaEvent_t> ev(D + 4, nullptr), evv(D, nullptr), evz(D, nullptr);
   if (st == KF_OK) {
     // priorities (measured): the skeleton chain (s1) and the leaf blocks with
     // their Cholesky factors (s4, at the start beside the leaf sample blocks)
@@ -1324,9 +1357,13 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
     KF_CUDA(c, cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, std::min(hi_prio + 1, lo_prio)));
     KF_CUDA(c, cudaStreamCreateWithPriority(&s3, cudaStreamNonBlocking, lo_prio));
     KF_CUDA(c, cudaStreamCreateWithPriority(&s4, cudaStreamNonBlocking, hi_prio));
+    // s5: Z^-1 of the upper levels, after each level's LU, beside the chain
+    KF_CUDA(c, cudaStreamCreateWithPriority(&s5, cudaStreamNonBlocking, lo_prio));
     KF_CUDA(c, cudaEventCreateWithFlags(&evl, cudaEventDisableTiming));
+    KF_CUDA(c, cudaEventCreateWithFlags(&evi, cudaEventDisableTiming));
     for (auto& e : ev) KF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     for (auto& e : evv) KF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (auto& e : evz) KF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     // ev[l]: skeletons of level l done (on s1); ev[0]: allocations ready (on s);
     // ev[D+1]: factorization done (on s2); ev[D+2]: skeletons done (on s1);
     // ev[D+3]: V blocks done (on s3); evv[l]: V blocks of level l done (on s3)
@@ -1355,11 +1392,21 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
       } else {
         cudaStreamWaitEvent(s2, evv[l], 0);
         st = kf_factorize_level_z(f, l, Tm, s2);
+        if (st == KF_OK && l <= f->zinv_top) {
+          cudaEventRecord(evz[l], s2);
+          cudaStreamWaitEvent(s5, evz[l], 0);
+          st = kf_z_inverse_level(f, l, s5);
+        }
       }
     }
     if (st == KF_OK) {
       cudaStreamWaitEvent(s2, evv[0], 0);
       st = kf_factorize_level_z(f, 0, Tm, s2);
+      if (st == KF_OK) {
+        cudaEventRecord(evz[0], s2);
+        cudaStreamWaitEvent(s5, evz[0], 0);
+        st = kf_z_inverse_level(f, 0, s5);
+      }
     }
     // the FP64 operator's leaf blocks need the tree only, and only the solve
     // reads them: last on the V-block stream, where they fill the SMs that the
@@ -1372,6 +1419,8 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
     cudaStreamWaitEvent(s, ev[D + 1], 0);
     cudaStreamWaitEvent(s, ev[D + 2], 0);
     cudaStreamWaitEvent(s, ev[D + 3], 0);
+    cudaEventRecord(evi, s5);
+    cudaStreamWaitEvent(s, evi, 0);
   }
   if (Tm) c->dfree(Tm, tb, s);
   kf_skel_end(f, &sc, s);
@@ -1379,6 +1428,10 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
     if (e) cudaEventDestroy(e);
   for (auto& e : evv)
     if (e) cudaEventDestroy(e);
+  for (auto& e : evz)
+    if (e) cudaEventDestroy(e);
+  if (s5) cudaStreamDestroy(s5);
+  if (evi) cudaEventDestroy(evi);
   if (s1) cudaStreamDestroy(s1);
   if (s2) cudaStreamDestroy(s2);
   if (s3) cudaStreamDestroy(s3);

@@ -51,6 +51,11 @@ struct kf_tree {
   std::vector<std::pair<void*, size_t>> allocs;
 };
 
+// default: levels with at most this many nodes keep Z^-1 for the solve sweep
+// (measured at N = 2^20, s_max = 256: the direct sweep 18% faster on the mixed
+// path and 9% on the FP64 path, the factorization within 1.5%)
+constexpr int kZinvDefaultMaxNodes = 64;
+
 struct kf_factor {
   kf_tree* t = nullptr;
   kf_ctx* ctx = nullptr;
@@ -80,6 +85,12 @@ struct kf_factor {
   float* Pleaf32 = nullptr;
   double* ZLU = nullptr;
   int32_t* Zpiv = nullptr;
+  // explicit Z^-1 of the nodes of levels 0..zinv_top (ldz^2 each, by node):
+  // there the sweep's LU solves, one CTA per node, are latency bound, while a
+  // product with Z^-1 spreads over many CTAs
+  double* Zinv = nullptr;
+  int32_t zinv_top = -1;
+  int32_t zinv_max_nodes = kZinvDefaultMaxNodes;  // -1: none
   int32_t* status = nullptr;
   double* pivr = nullptr;  // per node: smallest / largest pivot of its leaf Cholesky or Z LU
   std::vector<std::pair<void*, size_t>> allocs;
@@ -289,6 +300,10 @@ kf_status kf_factorize_level_z(kf_factor* f, int l, double* Tm, cudaStream_t s);
 kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s);
 kf_status kf_solve_device(kf_factor* f, double* W, int64_t nrhs, int transpose, cudaStream_t s);
 kf_status kf_matvec_device(kf_factor* f, const double* Xin, double* Y, int64_t nrhs, int deriv, cudaStream_t s);
+// Z^-1 of the nodes of level l (l <= f->zinv_top) from their LU; stream order
+// after the level's LU.
+kf_status kf_z_inverse_level(kf_factor* f, int l, cudaStream_t s);
+
 // y = (lambda I + K~)^T x (tree order, N x nrhs FP64), with the same operator
 // data as kf_matvec_device (FP64-accurate on the mixed path when it is stored).
 kf_status kf_matvec_transpose_device(kf_factor* f, const double* Xin, double* Y, int64_t nrhs, cudaStream_t s);

@@ -531,6 +531,84 @@ __global__ void __launch_bounds__(256) k_zsolve(const int32_t* __restrict__ rank
 
 // ---- operator pieces ------------------------------------------------------------
 // Leaf blocks: y_i = lambda x_i + sum_j K(x_i, x_j) x_j (or dK/dh, no lambda).
+// ---- reduced systems by the explicit inverse (upper levels) -------------------
+// out[l], out[r] <- Z^-1 [in[l]; in[r]] (transpose = 0) or Z^-T [...] (1) for
+// the levels that keep Z^-1: the LU solve of such a node is a chain of 2 z/32
+// dependent blocks on one CTA, while this product spreads a node over z/32
+// CTAs.  blockIdx.x = node of the level, blockIdx.y = a block of 32 output
+// entries.  Z^-1: warp w forms entries w, w + 8, .. of the block, lanes over
+// the columns (a row is one coalesced segment), 16 loads in flight per lane,
+// shuffle reduction.  Z^-T: lane q forms entry q of the block (column q of
+// Z^-1: a row's 32 entries are one coalesced segment), the warps split the
+// rows and add their partial sums in shared memory.
+constexpr int kZinvChunk = 16;
+__global__ void __launch_bounds__(256) k_zinv_apply(const int32_t* __restrict__ rank, int node0, int ldz, int s_max,
+                                                    const double* __restrict__ Zinv, const double* __restrict__ in,
+                                                    double* __restrict__ out, int k, int transpose) {
+  __shared__ double u[2 * KF_MAX_SMAX];
+  __shared__ double part[8][33];
+  const int node = node0 + blockIdx.x, l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], z = sl + sr;
+  const int e0 = blockIdx.y * 32;
+  if (e0 >= z) return;
+  const double* A = Zinv + (int64_t)node * ldz * ldz;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  auto dst = [&](int i) -> int64_t { return i < sl ? (int64_t)l * s_max + i : (int64_t)r * s_max + (i - sl); };
+  for (int c = 0; c < k; ++c) {
+    __syncthreads();
+    for (int i = tid; i < z; i += blockDim.x) u[i] = in[dst(i) * k + c];
+    __syncthreads();
+    if (!transpose) {
+      for (int q = warp; q < 32; q += 8) {
+        const int i = e0 + q;
+        if (i >= z) break;  // warp-uniform
+        const double* Ai = A + (int64_t)i * ldz;
+        double acc = 0.0;
+        for (int j0 = 0; j0 < z; j0 += 32 * kZinvChunk) {
+          double v[kZinvChunk];
+#pragma unroll
+          for (int t = 0; t < kZinvChunk; ++t) {
+            const int j = j0 + 32 * t + lane;
+            v[t] = j < z ? Ai[j] : 0.0;
+          }
+#pragma unroll
+          for (int t = 0; t < kZinvChunk; ++t) {
+            const int j = j0 + 32 * t + lane;
+            if (j < z) acc = fma(v[t], u[j], acc);
+          }
+        }
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) out[dst(i) * k + c] = acc;
+      }
+    } else {
+      const int j = e0 + lane;
+      double acc = 0.0;
+      if (j < z) {
+        for (int i0 = warp; i0 < z; i0 += 8 * kZinvChunk) {
+          double v[kZinvChunk];
+#pragma unroll
+          for (int t = 0; t < kZinvChunk; ++t) {
+            const int i = i0 + 8 * t;
+            v[t] = i < z ? A[(int64_t)i * ldz + j] : 0.0;
+          }
+#pragma unroll
+          for (int t = 0; t < kZinvChunk; ++t) {
+            const int i = i0 + 8 * t;
+            if (i < z) acc = fma(v[t], u[i], acc);
+          }
+        }
+      }
+      part[warp][lane] = acc;
+      __syncthreads();
+      if (warp == 0 && j < z) {
+        double sum = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) sum += part[w][lane];
+        out[dst(j) * k + c] = sum;
+      }
+    }
+  }
+}
+
 template <typename TM>
 __global__ void __launch_bounds__(128) k_leaf_mv(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                  int leaf0, const double* __restrict__ X64,
@@ -735,6 +813,18 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
   const size_t zs_smem = sizeof(double) * (2 * (size_t)ldz + (ldz + 1) / 2 + 8 * 32 * 33);
   KF_CUDA(c, cudaFuncSetAttribute(k_leaf_solve<TM, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls_smem));
   KF_CUDA(c, cudaFuncSetAttribute(k_zsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs_smem));
+  // t = Z^-1 [u_l; u_r] (or Z^-T) for the nodes of level l: the explicit
+  // inverse where the factorization kept it, else the LU
+  auto zsolve = [&](int l, int tr) {
+    if (l <= f->zinv_top && f->Zinv) {
+      dim3 gz(1u << l, (unsigned)((ldz + 31) / 32));
+      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zinv_apply<<<gz, 256, 0, s>>>(f->rank, 1 << l, ldz, s_max, f->Zinv, U, Vb,
+                                                                   (int)k, tr));
+    } else {
+      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<1 << l, 256, zs_smem, s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv,
+                                                                         U, Vb, (int)k, tr));
+    }
+  };
   if (!transpose) {
     KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve<TM, TV><<<1 << D, 256, ls_smem, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
     for (int l = D - 1; l >= 0; --l) {
@@ -744,8 +834,7 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
       dim3 gc((unsigned)((rows + kRowsPerChunk - 1) / kRowsPerChunk), nc);
       launch_colsum<TM, TV>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 1, vsrc, lvl(VT, l + 1), t->X64,
                             t->X32, t->d, f->c_exp, inv_h3, W, (int)k, U);
-      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<1 << l, 256, zs_smem, s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv, U, Vb,
-                                                         (int)k, 0));
+      zsolve(l, 0);
       launch_rowupd<TM, TV>(rows, nc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 0, SRC_STORED,
                             lvl(Phat, l + 1), t->X64, t->X32, t->d, f->c_exp, inv_h3, Vb, -1.0, W, (int)k);
     }
@@ -757,8 +846,7 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
       dim3 gc((unsigned)((rows + kRowsPerChunk - 1) / kRowsPerChunk), nc);
       launch_colsum<TM, TV>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 0, SRC_STORED, lvl(Phat, l + 1),
                             t->X64, t->X32, t->d, f->c_exp, inv_h3, W, (int)k, U);
-      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<1 << l, 256, zs_smem, s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv, U, Vb,
-                                                         (int)k, 1));
+      zsolve(l, 1);
       launch_rowupd<TM, TV>(rows, nc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 1, vsrc, lvl(VT, l + 1),
                             t->X64, t->X32, t->d, f->c_exp, inv_h3, Vb, -1.0, W, (int)k);
     }

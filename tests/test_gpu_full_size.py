@@ -15,9 +15,10 @@ properties that hold at any size:
   independent operator implementation) and its distance from the FP64
   solution within the 1e-5 bar of the headline metric;
 * the gradient through the solve: the quadratic identity
-  L(b + v) - L(b - v) = 2 <dL/db, v> (exact for L = ||x - y||^2) and a
-  Richardson-extrapolated central difference in lambda (skeletons do not
-  depend on lambda);
+  L(b + v) - L(b - v) = 2 <dL/db, v> (exact for L = ||x - y||^2), the
+  identity dL/dlambda = -<g, A^-1 x>, dL/dh against a central difference of
+  the operator with the skeletons held fixed, and the refined mixed gradient
+  against the refined FP64 one;
 * the batched workload: every sampled problem's skeletons against a whole
   oracle run of that problem, and the residual of the batched FP64 solution
   against the oracle's operator.
@@ -183,63 +184,85 @@ def test_differentiation_tree_and_nodes(diffw):
         del F
 
 
-def test_differentiation_gradient_identities(diffw):
-    """FP64 path, loss L = ||x - y||^2 with x = (lambda I + K~)^-1 b.
+def ids_from_factor(F, o, s_max):
+    """The factor's own skeletons and P, in the layout kf_factorize_with_ids
+    takes (node ranges from the oracle's tree, which equals the CUDA tree)."""
+    nn = o.nnodes
+    r = F.ranks()
+    leaf_max = max(o.node_range(a)[1] - o.node_range(a)[0] for a in range(1 << o.D, 1 << (o.D + 1)))
+    cmax = max(leaf_max, 2 * s_max)
+    ranks = np.zeros(nn + 1, np.int32)
+    skel = np.zeros((nn + 1) * s_max, np.int64)
+    P = np.zeros((nn + 1) * s_max * cmax)
+    for a in range(2, nn + 1):
+        s = int(r[a])
+        ranks[a] = s
+        lo, hi = o.node_range(a)
+        c = hi - lo if o.is_leaf(a) else int(r[2 * a]) + int(r[2 * a + 1])
+        skel[a * s_max: a * s_max + s] = F.skeleton(a)
+        P[a * s_max * cmax: a * s_max * cmax + s * c] = F.P(a, c).ravel()
+    return ranks, skel, P
 
-    * dL/db: L is quadratic in b, so (L(b + v) - L(b - v)) / 2 = <dL/db, v>
-      exactly for any v; both sides are computed by the library (forward and
-      transpose sweeps), so they agree to the sweeps' rounding: 1e-5 relative.
-    * dL/dlambda: the skeletons do not depend on lambda, so refactorizing at
-      lambda +- delta moves only the factors; Richardson extrapolation of the
-      central differences at delta and delta/2 (error O(delta^4)) agrees with
-      the adjoint to 1e-3 relative (the bound allows for the rounding of the
-      ill-conditioned solves divided by delta = 1e-2 lambda).
-    * dL/dh holds the skeletons and P fixed; it is checked against the
-      oracle's adjoint at small sizes."""
+
+def test_differentiation_gradient_identities(diffw):
+    """FP64 path, loss L = ||x - y||^2 with x = (lambda I + K~)^-1 b = A^-1 b.
+
+    * dL/db = a = A^-T g (g = dL/dx): L is quadratic in b, so
+      (L(b + v) - L(b - v)) / 2 = <a, v> exactly for any v; both sides come
+      from the library (forward and transpose sweeps): 1e-5 relative.
+    * dL/dlambda = -<a, x> = -<g, A^-1 x>: the forward sweep applied to x gives
+      the same number, 1e-6 relative.  (A central difference in lambda is no
+      check here: lambda I + K~ of this workload has an eigenvalue close to
+      zero, and L(lambda) turns within a step of 1e-2.)
+    * dL/dh = -<a, (dK~/dh) x> with skeletons and P held fixed: against a
+      central difference of the operator, -<a, (A(h + d) - A(h - d)) x> / 2d,
+      with the factor's own skeletons and P imported at h +- d (d = 1e-4 h;
+      truncation about 1e-8, rounding about 1e-8 after the sum's cancellation):
+      1e-5 relative."""
     p, o, tree, _ = diffw
     b = torch.from_numpy(p.B[:, 0]).cuda()
     y = torch.from_numpy(p.extra["y"]).cuda()
-
-    def loss(lam, bb):
-        F = kf.Factor(tree, p.h, lam, p.tau, p.s_max, precision=FP64, refine_max_iter=-1)
-        x = F.solve(bb)
-        return F, x, float(((x - y) ** 2).sum())
-
-    F, x, L0 = loss(p.lam, b)
-    db, dl, dh = F.grad(x, 2 * (x - y))
+    F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=FP64, refine_max_iter=-1)
+    x = F.solve(b)
+    g = 2 * (x - y)
+    db, dl, dh = F.grad(x, g)
     v = torch.from_numpy(np.random.default_rng(7).standard_normal(p.N)).cuda()
     xp, xm = F.solve(b + v), F.solve(b - v)
     fd_b = (float(((xp - y) ** 2).sum()) - float(((xm - y) ** 2).sum())) / 2.0
     assert abs(fd_b - float((db * v).sum())) <= 1e-5 * abs(fd_b)
-    del F, xp, xm
-    d = 1e-2 * p.lam
-
-    def central(delta):
-        return (loss(p.lam + delta, b)[2] - loss(p.lam - delta, b)[2]) / (2 * delta)
-
-    fd_l = (4 * central(d / 2) - central(d)) / 3
-    assert abs(fd_l - dl) <= 1e-3 * abs(fd_l)
-    assert np.isfinite(dh)
+    del xp, xm
+    z = F.solve(x)
+    assert abs(dl + float((g * z).sum())) <= 1e-6 * abs(dl)
+    ranks, skel, P = ids_from_factor(F, o, p.s_max)
+    del F
+    d = 1e-4 * p.h
+    ys = []
+    for hh in (p.h + d, p.h - d):
+        Fh = kf.factorize_with_ids(tree, hh, p.lam, p.s_max, ranks, skel, P, precision=FP64, refine_max_iter=-1)
+        ys.append(Fh.matvec(x))
+        del Fh
+    fd_h = -float((db * (ys[0] - ys[1])).sum()) / (2 * d)
+    assert abs(fd_h - dh) <= 1e-5 * abs(dh)
 
 
 def test_differentiation_mixed_gradient_matches_refined_fp64(diffw):
     """The benchmark's differentiation run: the mixed path with its forward
     solve and adjoint refined by GMRES(50) to eps_r <= 1e-9 against the
     FP64-accurate operator and its transpose, dK~/dh from FP64 coordinates.
-    Reference: the FP64 factorization refined to eps_r <= 1e-11.  dL/db and
+    Reference: the FP64 factorization refined the same way.  x, dL/db and
     dL/dlambda within 1e-6; dL/dh, a sum with heavy cancellation, within 1e-4."""
     p, o, tree, _ = diffw
     b = torch.from_numpy(p.B[:, 0]).cuda()
     y = torch.from_numpy(p.extra["y"]).cuda()
     out = []
     for prec, kw in ((MIXED, {"refine_tol": 1e-9, "refine_max_iter": 400, "gmres_restart": 50}),
-                     (FP64, {"refine_tol": 1e-11, "refine_max_iter": 40, "gmres_restart": 20})):
+                     (FP64, {"refine_tol": 1e-9, "refine_max_iter": 400, "gmres_restart": 50})):
         F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=prec, fp64_operator=True, **kw)
         x = F.solve(b)
         out.append((x, *F.grad(x, 2 * (x - y))))
         del F
     (xm, dbm, dlm, dhm), (x64, db64, dl64, dh64) = out
-    assert rel(xm.cpu().numpy(), x64.cpu().numpy()) <= 1e-7
+    assert rel(xm.cpu().numpy(), x64.cpu().numpy()) <= 1e-6
     assert rel(dbm.cpu().numpy(), db64.cpu().numpy()) <= 1e-6
     assert abs(dlm - dl64) <= 1e-6 * abs(dl64)
     assert abs(dhm - dh64) <= 1e-4 * abs(dh64)

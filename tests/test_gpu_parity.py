@@ -258,6 +258,24 @@ def test_transposed_operator_ragged_leaves():
     assert rel(xt, o.solve(b, transpose=True)) <= 1e-10
 
 
+@pytest.mark.parametrize("zn", [-1, 1, 4, 64])
+def test_reduced_system_inverse_levels(c1, zn):
+    """The sweeps solve the reduced systems of the levels with at most
+    zinv_max_nodes nodes by their explicit inverse (formed after each level's
+    LU) and the others by the LU: every split gives the oracle's forward and
+    transpose solutions (direct sweeps; FP32 factors on the mixed path)."""
+    p, o, tree = c1
+    ranks, skel, P = ids_from_oracle(o, p.s_max)
+    b = p.B[:, 0]
+    bt = torch.from_numpy(b).cuda()
+    xo, xto = o.solve(b), o.solve(b, transpose=True)
+    for prec, tol in ((FP64, 1e-10), (MIXED, 1e-4)):
+        F = kf.factorize_with_ids(tree, p.h, p.lam, p.s_max, ranks, skel, P, precision=prec, refine_max_iter=-1,
+                                  zinv_max_nodes=zn)
+        assert rel(F.solve(bt).cpu().numpy(), xo) <= tol
+        assert rel(F.solve(bt, transpose=True).cpu().numpy(), xto) <= tol
+
+
 def test_multiple_rhs_and_float32(c1):
     p, o, tree = c1
     F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=FP64)
