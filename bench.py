@@ -146,12 +146,12 @@ def phase_work(p, D, lo, hi, ranks, n_samp):
     N, d, s_max = p.N, p.d, p.s_max
     r = ranks
     per_level = level_qr_flops(None, ranks, N, D, n_samp, s_max, lo, hi)
-    clus = [l for l in range(1, D) if (1 << l) <= 64]
+    clus = [l for l in range(1, D) if (1 << l) <= 8]   # levels whose QR runs on thread-block clusters
     w = {"qr_leaf": ("fp64", per_level[D], "step"),
          "qr": ("fp64", sum(per_level[l] for l in range(1, D) if l not in clus), "step"),
          "qr_cluster": ("fp64", sum(per_level[l] for l in clus), "step")}
     ent = ventries = 0.0
-    zoff = tel = zlu = 0.0
+    zoff = tel = zlu = zinv = 0.0
     chol = phat = 0.0
     b_leaf = b_cs = b_ru = b_z = 0.0
     m_leaf = m_cs = m_ru = 0.0
@@ -177,6 +177,8 @@ def phase_work(p, D, lo, hi, ranks, n_samp):
         z = r[cl] + r[cr]
         zoff += 3 * 2.0 * r[cl] * r[cr] * (nl + nr)
         zlu += 2.0 / 3.0 * z ** 3 + (2.0 * z * z * r[a] if a >= 2 else 0.0)
+        if a < 128:  # levels with at most 64 nodes keep Z^-1 (the library's default)
+            zinv += 2.0 * z ** 3
         if a >= 2:
             tel += 3 * 2.0 * (nl * r[cl] + nr * r[cr]) * r[a]
         b_z += 8.0 * z * z
@@ -184,6 +186,7 @@ def phase_work(p, D, lo, hi, ranks, n_samp):
               "leaf_cholesky": ("fp32", chol, "step"), "leaf_phat": ("fp32", phat, "step"),
               "eval_V": ("fp32i", ventries * (21.0 * d + 70.0), "step"),
               "zoff": ("tf32", zoff, "step"), "telescope": ("tf32", tel, "step"), "z_lu": ("fp64", zlu, "step"),
+              "z_inv": ("fp64", zinv, "step"),
               "solve_leaf": ("hbm", b_leaf, "sweep"), "solve_colsum": ("hbm", b_cs, "sweep"),
               "solve_rowupd": ("hbm", b_ru, "sweep"), "solve_zsolve": ("hbm", b_z, "sweep"),
               "matvec_leaf": ("hbm", m_leaf, "matvec"), "matvec_colsum": ("hbm", m_cs, "matvec"),

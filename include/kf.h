@@ -284,8 +284,9 @@ kf_status kf_profile_enable(int32_t on);
  * (the pivoted QR of the leaf level; "qr" holds the other one-CTA-per-node
  * levels), matvec_colsum and matvec_rowupd (the V-block passes of kf_matvec
  * and of the refinement's operator; solve_colsum and solve_rowupd are those of
- * the solve sweep). */
-#define KF_PHASE_COUNT 23
+ * the solve sweep), z_inv (the explicit Z^-1 of the upper levels, see
+ * kf_opts.zinv_max_nodes). */
+#define KF_PHASE_COUNT 24
 kf_status kf_profile_read(double* ms, int64_t* launches, int32_t nphase);
 /* Per-launch timeline of the launches recorded since the last kf_profile_read
  * (which it leaves in place): for launch q < *n, its start and end in ms

@@ -76,7 +76,7 @@ SIGNATURES = {
 
 PHASES = ["tree", "sample", "eval_A", "qr", "leaf_assemble", "leaf_cholesky", "leaf_phat", "eval_V", "zoff", "z_lu",
           "z_solve_pc", "telescope", "solve_leaf", "solve_colsum", "solve_zsolve", "solve_rowupd", "matvec_leaf",
-          "matvec_push", "misc", "qr_cluster", "qr_leaf", "matvec_colsum", "matvec_rowupd"]
+          "matvec_push", "misc", "qr_cluster", "qr_leaf", "matvec_colsum", "matvec_rowupd", "z_inv"]
 
 _lock = threading.Lock()
 _lib = None

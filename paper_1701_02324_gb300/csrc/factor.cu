@@ -1302,7 +1302,7 @@ kf_status kf_z_inverse_level(kf_factor* f, int l, cudaStream_t s) {
   if (l > f->zinv_top) return KF_OK;
   const int ldz = 2 * f->s_max, qw = 16;
   dim3 g(1u << l, (unsigned)((ldz + qw - 1) / qw));
-  KF_PHASE(KF_PH_ZLU, s, k_z_inverse<<<g, 256, 0, s>>>(f->rank, 1 << l, ldz, f->ZLU, f->Zpiv, f->Zinv, qw));
+  KF_PHASE(KF_PH_ZINV, s, k_z_inverse<<<g, 256, 0, s>>>(f->rank, 1 << l, ldz, f->ZLU, f->Zpiv, f->Zinv, qw));
   KF_LAUNCH_CHECK(f->ctx);
   return KF_OK;
 }

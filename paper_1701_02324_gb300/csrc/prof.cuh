@@ -32,6 +32,7 @@ enum kf_phase {
   KF_PH_QR_LEAF,
   KF_PH_MV_COLSUM,
   KF_PH_MV_ROWUPD,
+  KF_PH_ZINV,
   KF_PH_COUNT
 };
 

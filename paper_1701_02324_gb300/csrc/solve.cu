@@ -710,35 +710,62 @@ __global__ void __launch_bounds__(256) k_colsum_df(const int32_t* __restrict__ l
 }
 
 // Push skeleton coefficients down: g[l] += P_c[:s_l] g[a], g[r] += P_c[s_l:] g[a].
-__global__ void k_push_down(const int32_t* __restrict__ rank, int node0, int s_max, const double* __restrict__ Pc,
-                            double* __restrict__ G, int k) {
-  const int nl = blockIdx.x, node = node0 + nl;
-  const int l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], s = rank[node];
+// blockIdx.x = node of the level, blockIdx.y = a block of 32 rows of P_c:
+// warp w forms rows w, w + 8, .. of the block, lanes over the columns (a row
+// of P_c is contiguous), shuffle reduction; a node spreads over z/32 CTAs.
+__global__ void __launch_bounds__(256) k_push_down(const int32_t* __restrict__ rank, int node0, int s_max,
+                                                   const double* __restrict__ Pc, double* __restrict__ G, int k) {
+  const int node = node0 + blockIdx.x;
+  const int l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], s = rank[node], z = sl + sr;
+  const int i0 = blockIdx.y * 32;
+  if (i0 >= z || s == 0) return;
   const double* P = Pc + (int64_t)node * 2 * s_max * s_max;
   const double* ga = G + (int64_t)node * s_max * k;
-  for (int e = threadIdx.x; e < (sl + sr) * k; e += blockDim.x) {
-    int i = e / k, c = e % k;
-    double acc = 0.0;
-    for (int q = 0; q < s; ++q) acc += P[(int64_t)i * s_max + q] * ga[(int64_t)q * k + c];
-    double* dst = i < sl ? G + ((int64_t)l * s_max + i) * k + c : G + ((int64_t)r * s_max + (i - sl)) * k + c;
-    *dst += acc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int w = warp; w < 32; w += 8) {
+    const int i = i0 + w;
+    if (i >= z) break;  // warp-uniform
+    const double* Pi = P + (int64_t)i * s_max;
+    double* dst = i < sl ? G + ((int64_t)l * s_max + i) * k : G + ((int64_t)r * s_max + (i - sl)) * k;
+    for (int c = 0; c < k; ++c) {
+      double acc = 0.0;
+      for (int q = lane; q < s; q += 32) acc = fma(Pi[q], ga[(int64_t)q * k + c], acc);
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (lane == 0) dst[c] += acc;
+    }
   }
 }
 
 // Gather skeleton weights up (transposed operator): g[a] += P_c^T [g[l]; g[r]].
-__global__ void k_push_up(const int32_t* __restrict__ rank, int node0, int s_max, const double* __restrict__ Pc,
-                          double* __restrict__ G, int k) {
-  const int nl = blockIdx.x, node = node0 + nl;
-  const int l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], s = rank[node];
+// blockIdx.x = node of the level, blockIdx.y = a block of 32 columns of P_c:
+// lane q forms column q of the block (a row's 32 entries are one coalesced
+// segment), the warps split the rows and add their partial sums in shared
+// memory.
+__global__ void __launch_bounds__(256) k_push_up(const int32_t* __restrict__ rank, int node0, int s_max,
+                                                 const double* __restrict__ Pc, double* __restrict__ G, int k) {
+  __shared__ double part[8][33];
+  const int node = node0 + blockIdx.x;
+  const int l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], s = rank[node], z = sl + sr;
+  const int q0 = blockIdx.y * 32;
+  if (q0 >= s) return;
   const double* P = Pc + (int64_t)node * 2 * s_max * s_max;
-  const double* gl = G + (int64_t)l * s_max * k;
-  const double* gr = G + (int64_t)r * s_max * k;
-  for (int e = threadIdx.x; e < s * k; e += blockDim.x) {
-    const int q = e / k, c = e % k;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, q = q0 + lane;
+  for (int c = 0; c < k; ++c) {
     double acc = 0.0;
-    for (int i = 0; i < sl; ++i) acc += P[(int64_t)i * s_max + q] * gl[(int64_t)i * k + c];
-    for (int i = 0; i < sr; ++i) acc += P[(int64_t)(sl + i) * s_max + q] * gr[(int64_t)i * k + c];
-    G[((int64_t)node * s_max + q) * k + c] += acc;
+    if (q < s)
+      for (int i = warp; i < z; i += 8) {
+        const double gi = i < sl ? G[((int64_t)l * s_max + i) * k + c] : G[((int64_t)r * s_max + (i - sl)) * k + c];
+        acc = fma(P[(int64_t)i * s_max + q], gi, acc);
+      }
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && q < s) {
+      double sum = 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) sum += part[w][lane];
+      G[((int64_t)node * s_max + q) * k + c] += sum;
+    }
+    __syncthreads();
   }
 }
 
@@ -891,7 +918,8 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
     launch_colsum<double, double>(gcl, s, t->d_lo, t->d_hi, f->rank, f->skel, leaf0, s_max, 0, SRC_STORED, f->Pleaf,
                                   t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G, KF_PH_MV_ROWUPD);
     for (int l = D - 1; l >= 1; --l)
-      KF_PHASE(KF_PH_MV_PUSH, s, k_push_up<<<1 << l, 256, 0, s>>>(f->rank, 1 << l, s_max, f->Pc, G, (int)k));
+      KF_PHASE(KF_PH_MV_PUSH, s, k_push_up<<<dim3(1u << l, (unsigned)((s_max + 31) / 32)), 256, 0, s>>>(
+                                     f->rank, 1 << l, s_max, f->Pc, G, (int)k));
     for (int l = 1; l <= D; ++l) {
       const int64_t rows = (N >> l) + 1;
       if (f->VTdf) {
@@ -923,8 +951,10 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
       launch_colsum<TM, double>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, s_max, 1, src, vt_level(l),
                                 t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G, KF_PH_MV_COLSUM);
   }
+  const dim3 gpd(1, (unsigned)((2 * s_max + 31) / 32));
   for (int l = 1; l < D; ++l)
-    KF_PHASE(KF_PH_MV_PUSH, s, k_push_down<<<1 << l, 256, 0, s>>>(f->rank, 1 << l, s_max, f->Pc, G, (int)k));
+    KF_PHASE(KF_PH_MV_PUSH, s, k_push_down<<<dim3(1u << l, gpd.y), 256, 0, s>>>(f->rank, 1 << l, s_max, f->Pc, G,
+                                                                                (int)k));
   const int64_t rows = (N >> D) + 1;
   launch_rowupd<double, double>(rows, 1 << D, s, t->d_lo, t->d_hi, f->rank, f->skel, leaf0, s_max, 0, SRC_STORED,
                                 f->Pleaf, t->X64, t->X32, t->d, f->c_exp, inv_h3, G, 1.0, y, (int)k, KF_PH_MV_ROWUPD);

@@ -212,8 +212,10 @@ def test_differentiation_gradient_identities(diffw):
       from the library (forward and transpose sweeps): 1e-5 relative.
     * dL/dlambda = -<a, x> = -<g, A^-1 x>: the forward sweep applied to x gives
       the same number, 1e-6 relative.  (A central difference in lambda is no
-      check here: lambda I + K~ of this workload has an eigenvalue close to
-      zero, and L(lambda) turns within a step of 1e-2.)
+      check on this workload: Richardson-extrapolated from steps of 1e-2 and
+      5e-3 it gave -4.7e9 against the adjoint's +1.16e9, which this identity
+      and the refined FP64 path confirm to 1e-8; L(lambda) bends sharply within
+      such steps, as it does near a small eigenvalue of lambda I + K~.)
     * dL/dh = -<a, (dK~/dh) x> with skeletons and P held fixed: against a
       central difference of the operator, -<a, (A(h + d) - A(h - d)) x> / 2d,
       with the factor's own skeletons and P imported at h +- d (d = 1e-4 h;
