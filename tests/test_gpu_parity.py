@@ -276,6 +276,24 @@ def test_reduced_system_inverse_levels(c1, zn):
         assert rel(F.solve(bt, transpose=True).cpu().numpy(), xto) <= tol
 
 
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (MIXED, 1e-4)])
+def test_v_recompute_matches_oracle(c1, prec, tol):
+    """KF_V_RECOMPUTE: the solve sweeps and the operator evaluate the V blocks
+    K(x_i, sib~) on the fly (matrix-free, Sec. II-D) instead of reading the
+    stored ones: forward and transpose solutions (direct sweeps; FP32 factors
+    on the mixed path) and, on the FP64 path, the operator equal the oracle's."""
+    p, o, tree = c1
+    ranks, skel, P = ids_from_oracle(o, p.s_max)
+    F = kf.factorize_with_ids(tree, p.h, p.lam, p.s_max, ranks, skel, P, precision=prec, refine_max_iter=-1,
+                              v_storage=kf.KF_V_RECOMPUTE, fp64_operator=False)
+    b = p.B[:, 0]
+    bt = torch.from_numpy(b).cuda()
+    assert rel(F.solve(bt).cpu().numpy(), o.solve(b)) <= tol
+    assert rel(F.solve(bt, transpose=True).cpu().numpy(), o.solve(b, transpose=True)) <= tol
+    if prec == FP64:
+        assert rel(F.matvec(bt).cpu().numpy(), o.matvec(b)) <= 1e-12
+
+
 def test_multiple_rhs_and_float32(c1):
     p, o, tree = c1
     F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=FP64)
@@ -338,6 +356,55 @@ def test_ragged_sizes():
     ranks, skel, P = ids_from_oracle(o, 48)
     F = kf.factorize_with_ids(tree, 0.4, 0.5, 48, ranks, skel, P)
     assert rel(F.solve(torch.from_numpy(b).cuda()).cpu().numpy(), o.solve(b)) <= 1e-10
+
+
+def test_maximum_rank_s_max_512():
+    """The largest rank the library takes (s_max = 512, |S'| = 1024): N = 2048
+    points in [0,1]^8 with h = 0.3 keep every rank at its cap (full-rank leaves
+    of 512 points, z = 1024 reduced systems above), which drives the QR with 32
+    rows per lane, 1024 x 1024 reduced systems, their explicit inverse at the
+    root and 512-column tcgen05 products.  Skeletons equal the oracle's; FP64
+    direct solve and mixed solve refined to 1e-12 within 1e-10 of the oracle,
+    forward and transpose."""
+    X = np.random.default_rng(31).random((2048, 8))
+    b = np.random.default_rng(32).standard_normal(2048)
+    h, lam, tau, smax = 0.3, 0.5, 1e-12, 512
+    o = oracle.Oracle(X, 512)
+    o.skeletonize(h, tau, smax)
+    o.factorize(lam)
+    xo, xto = o.solve(b), o.solve(b, transpose=True)
+    tree = kf.Tree(torch.from_numpy(X).cuda(), 512)
+    bt = torch.from_numpy(b).cuda()
+    for prec, kw in ((FP64, {}), (MIXED, {"refine_tol": 1e-12})):
+        F = kf.Factor(tree, h, lam, tau, smax, precision=prec, **kw)
+        r = F.ranks()
+        assert all(int(r[a]) == o.rank(a) == 512 for a in range(2, o.nnodes + 1))
+        assert all(np.array_equal(F.skeleton(a), o.skel(a)) for a in range(2, o.nnodes + 1))
+        assert rel(F.solve(bt).cpu().numpy(), xo) <= 1e-10
+        assert rel(F.solve(bt, transpose=True).cpu().numpy(), xto) <= 1e-10
+
+
+def test_empty_inputs_rejected_and_duplicate_points():
+    """Empty inputs are rejected with KF_EINVAL (no points, no coordinates,
+    m = 0, no right-hand side); heavily duplicated points (9 distinct
+    positions among 1500: ties in every distance and projection, broken by the
+    original index) still give the oracle's tree bit for bit."""
+    dev = "cuda"
+    for X, m in ((torch.zeros((0, 3), dtype=torch.float64, device=dev), 8),
+                 (torch.zeros((10, 0), dtype=torch.float64, device=dev), 8),
+                 (torch.rand((10, 3), dtype=torch.float64, device=dev), 0)):
+        with pytest.raises(kf.KFError) as e:
+            kf.Tree(X, m)
+        assert e.value.status == kf._abi.KF_EINVAL
+    X = np.random.default_rng(41).integers(0, 3, size=(1500, 2)).astype(np.float64)
+    tree = kf.Tree(torch.from_numpy(X).cuda(), 64)
+    o = oracle.Oracle(X, 64)
+    assert np.array_equal(tree.perm().cpu().numpy(), o.perm())
+    F = kf.Factor(tree, 0.7, 1.0, 1e-8, 16)
+    b = torch.zeros(1500, dtype=torch.float64, device=dev)
+    x = torch.zeros_like(b)
+    lib = kf._abi.load()
+    assert lib.kf_solve(F.h, b.data_ptr(), x.data_ptr(), 0, 1500, kf.KF_F64, 0, None, None) == kf._abi.KF_EINVAL
 
 
 def test_small_h_limit_is_diagonal():
