@@ -85,11 +85,15 @@ __device__ __forceinline__ void warp_tile_rowupd(int r0, int r1, int kb, int nb,
   }
 }
 
+// 128 threads a CTA, 8 (FP32) or 4 (FP64) CTAs an SM: with 256 threads and
+// half as many CTAs, 1024 leaves took 1.7 rounds of the 608 slots (FP32) and
+// the second round ran two thirds full.
+constexpr int kLeafSolveThreads = 128;
 template <typename TM, typename TV>
-__global__ void __launch_bounds__(256, sizeof(TM) == 4 ? 4 : 2) k_leaf_solve(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+__global__ void __launch_bounds__(kLeafSolveThreads, sizeof(TM) == 4 ? 8 : 4) k_leaf_solve(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                     int leaf0, int ldL, const TM* __restrict__ Lall,
                                                     TV* __restrict__ W, int k) {
-  constexpr int NB = 32;
+  constexpr int NB = 32, NQ = NB * NB / kLeafSolveThreads;  // diagonal-block entries per thread
   __shared__ TV xb[NB];
   __shared__ TM db[NB][NB + 1];  // the staged diagonal block
   __shared__ TV dinv[NB];        // reciprocals of its diagonal (divisions in parallel)
@@ -102,18 +106,18 @@ __global__ void __launch_bounds__(256, sizeof(TM) == 4 ? 4 : 2) k_leaf_solve(con
   const int tid = threadIdx.x, lane = tid & 31;
   // diagonal blocks fetched into registers one block ahead, then committed
   // to shared memory; warp 0 forms the reciprocals of the diagonal
-  TM pre[4];
+  TM pre[NQ];
   auto fetch = [&](int kb, int nb) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = q * 256 + tid, i = e >> 5, j = e & 31;
+    for (int q = 0; q < NQ; ++q) {
+      const int e = q * kLeafSolveThreads + tid, i = e >> 5, j = e & 31;
       pre[q] = (i < nb && j <= i) ? L[(int64_t)(kb + i) * ldL + kb + j] : (TM)0;
     }
   };
   auto commit = [&](int nb) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = q * 256 + tid;
+    for (int q = 0; q < NQ; ++q) {
+      const int e = q * kLeafSolveThreads + tid;
       db[e >> 5][e & 31] = pre[q];
     }
     __syncthreads();
@@ -836,7 +840,7 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
   const double inv_h3 = 1.0 / (f->h * f->h * f->h);
   const int vsrc = f->vstore == KF_V_STORED ? SRC_STORED : SRC_KERNEL;
   // dynamic shared memory: the warps' 32 x 33 row tiles (plus the Z solve's vectors and row map)
-  const size_t ls_smem = sizeof(TM) * 8 * 32 * 33;
+  const size_t ls_smem = sizeof(TM) * (kLeafSolveThreads / 32) * 32 * 33;
   const size_t zs_smem = sizeof(double) * (2 * (size_t)ldz + (ldz + 1) / 2 + 8 * 32 * 33);
   KF_CUDA(c, cudaFuncSetAttribute(k_leaf_solve<TM, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls_smem));
   KF_CUDA(c, cudaFuncSetAttribute(k_zsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs_smem));
@@ -853,7 +857,7 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
     }
   };
   if (!transpose) {
-    KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve<TM, TV><<<1 << D, 256, ls_smem, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
+    KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve<TM, TV><<<1 << D, kLeafSolveThreads, ls_smem, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
     for (int l = D - 1; l >= 0; --l) {
       const int c0 = 1 << (l + 1), nc = 1 << (l + 1);
       const int64_t rows = (N >> (l + 1)) + 1;
@@ -877,7 +881,7 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
       launch_rowupd<TM, TV>(rows, nc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 1, vsrc, lvl(VT, l + 1),
                             t->X64, t->X32, t->d, f->c_exp, inv_h3, Vb, -1.0, W, (int)k);
     }
-    KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve<TM, TV><<<1 << D, 256, ls_smem, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
+    KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve<TM, TV><<<1 << D, kLeafSolveThreads, ls_smem, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
   }
   KF_LAUNCH_CHECK(c);
   return KF_OK;
