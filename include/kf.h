@@ -186,9 +186,10 @@ kf_status kf_grad(kf_factor* f, const void* x, const void* dLdx, void* dLdb, dou
  * N and ranks) with ONE CUDA-graph launch: the factors are allocated first,
  * then every problem's kernel sequence is captured into one graph whose
  * branches run concurrently on up to 16 streams, and the graph is launched
- * once on `stream` (the spec batched configuration; Algorithms 1-2 per
- * problem).  h, lambda, tau: host arrays of nprob values; s_max and opts are
- * shared.  out: host array of nprob factor handles (NULL on failure).
+ * once on `stream` (no counterpart in the paper, which solves one problem at
+ * a time; Algorithms 1-2 per problem).  h, lambda, tau: host arrays of nprob
+ * values; s_max and opts are shared (opts.zinv_max_nodes = 0 means no explicit
+ * Z^-1 here).  out: host array of nprob factor handles (NULL on failure).
  * Synchronizes `stream`; returns the worst per-problem status (KF_EILLCOND
  * leaves the factors in place).  Scratch memory inside the graph comes from
  * cudaMallocAsync even when the context has an allocator. */
