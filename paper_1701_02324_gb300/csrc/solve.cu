@@ -215,12 +215,33 @@ __global__ void __launch_bounds__(256) k_colsum(const int32_t* __restrict__ lo, 
       TV acc[kMaxK];
 #pragma unroll
       for (int r = 0; r < kMaxK; ++r) acc[r] = (TV)0;
-      for (int i = r0; i < r1; ++i) {
-        TV m;
-        if (src == SRC_STORED) m = (TV)M[(int64_t)(b + i) * s_max + q];
-        else m = (TV)eval_src<TM>(src, X64, X32, b + i, sk[q], d, c_exp, inv_h3);
+      if (src == SRC_STORED) {
+        // 8 rows' loads in flight before their products (the same order of sums)
+        const TM* Mq = M + (int64_t)(b + r0) * s_max + q;
+        const int nr = r1 - r0;
+        int i = 0;
+        for (; i + 8 <= nr; i += 8) {
+          TM mv[8];
 #pragma unroll
-        for (int r = 0; r < kMaxK; ++r) acc[r] += m * ws[i - r0][r];
+          for (int u = 0; u < 8; ++u) mv[u] = Mq[(int64_t)(i + u) * s_max];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const TV m = (TV)mv[u];
+#pragma unroll
+            for (int r = 0; r < kMaxK; ++r) acc[r] += m * ws[i + u][r];
+          }
+        }
+        for (; i < nr; ++i) {
+          const TV m = (TV)Mq[(int64_t)i * s_max];
+#pragma unroll
+          for (int r = 0; r < kMaxK; ++r) acc[r] += m * ws[i][r];
+        }
+      } else {
+        for (int i = r0; i < r1; ++i) {
+          const TV m = (TV)eval_src<TM>(src, X64, X32, b + i, sk[q], d, c_exp, inv_h3);
+#pragma unroll
+          for (int r = 0; r < kMaxK; ++r) acc[r] += m * ws[i - r0][r];
+        }
       }
       double* out = U + ((int64_t)dst * s_max + q) * k + kb;
       for (int r = 0; r < kk; ++r) atomicAdd(out + r, (double)acc[r]);
@@ -277,11 +298,32 @@ __global__ void __launch_bounds__(256) k_rowupd(const int32_t* __restrict__ lo, 
       TV acc[KB];
 #pragma unroll
       for (int r = 0; r < KB; ++r) acc[r] = (TV)0;
-      for (int q = lane; q < cnt; q += 32) {
-        const TV m = (src == SRC_STORED) ? (TV)M[(int64_t)(b + i) * s_max + q]
-                                         : (TV)eval_src<TM>(src, X64, X32, b + i, sk[q], d, c_exp, inv_h3);
+      if (src == SRC_STORED) {
+        // a row's 8 loads per lane in flight before their products (the same order of sums)
+        const TM* Mi = M + (int64_t)(b + i) * s_max;
+        int q = lane;
+        for (; q + 32 * 7 < cnt; q += 32 * 8) {
+          TM mv[8];
 #pragma unroll
-        for (int r = 0; r < KB; ++r) acc[r] += m * vs[q * KB + r];
+          for (int u = 0; u < 8; ++u) mv[u] = Mi[q + 32 * u];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const TV m = (TV)mv[u];
+#pragma unroll
+            for (int r = 0; r < KB; ++r) acc[r] += m * vs[(q + 32 * u) * KB + r];
+          }
+        }
+        for (; q < cnt; q += 32) {
+          const TV m = (TV)Mi[q];
+#pragma unroll
+          for (int r = 0; r < KB; ++r) acc[r] += m * vs[q * KB + r];
+        }
+      } else {
+        for (int q = lane; q < cnt; q += 32) {
+          const TV m = (TV)eval_src<TM>(src, X64, X32, b + i, sk[q], d, c_exp, inv_h3);
+#pragma unroll
+          for (int r = 0; r < KB; ++r) acc[r] += m * vs[q * KB + r];
+        }
       }
 #pragma unroll
       for (int r = 0; r < KB; ++r)
