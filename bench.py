@@ -83,13 +83,21 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = [r for r in self.rows if len(r) >= 9 and r[0] == str(gpu_index)]
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": reasons, "samples": len(rows)}
+        return summarize_clocks(self.rows, gpu_index)
+
+
+def summarize_clocks(rows, gpu_index=0):
+    """Median SM clock, maximum SM clock and the throttle reasons seen in
+    nvidia-smi samples (index, clocks.sm, clocks.max.sm, power.draw,
+    clocks_event_reasons.active, then hw_slowdown, hw_thermal_slowdown,
+    sw_thermal_slowdown, sw_power_cap as Active / Not Active) of one GPU."""
+    rows = [r for r in rows if len(r) >= 9 and r[0] == str(gpu_index)]
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+            "reasons": reasons, "samples": len(rows)}
 
 
 # ---------------------------------------------------------------- algorithmic work
