@@ -162,7 +162,7 @@ kf_status kf_factor_free(kf_factor* f);
  * transposed operator, M^-T being the transpose sweep.  The operator is
  * FP64-accurate when opts.fp64_operator is set (or on the FP64 path);
  * otherwise the mixed path evaluates it in FP32.  KF_ENOTCONV when the
- * refinement stops above refine_tol (X then holds the last iterate). */
+ * refinement stops above refine_tol (X is then left unwritten). */
 kf_status kf_solve(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t ld, int32_t dtype,
                    int32_t transpose, void* stream, kf_solve_info* info);
 /* Y = (lambda I + K~) X with the operator the factorization inverts
