@@ -74,6 +74,9 @@ def _load():
             "kfo_matvec": (I32, [P, P, P, I32]),
             "kfo_grad": (I32, [P, P, P, P, P, P]),
             "kfo_subtrees": (I32, [P, P, I32, D, D, I32, I32, U64, D]),
+            "kfo_hybrid": (I32, [P, I32, D, D, I32, I32, U64, D]),
+            "kfo_hybrid_solve": (I32, [P, P, P]),
+            "kfo_hybrid_matvec": (I32, [P, P, P]),
             "kfo_splitmix64": (U64, [U64]),
         }
         for name, (res, args) in sig.items():
@@ -187,6 +190,34 @@ class Oracle:
         if st not in (KFO_OK, KFO_EILLCOND):
             raise ValueError(f"oracle subtrees status {st}")
         return int(st)
+
+    # ---- hybrid level-restricted solver (Sec. II-C, Algorithms 6-8) ----------
+    def hybrid(self, L: int, h: float, tau: float, s_max: int, lam: float, n_samp: int | None = None,
+               seed: int = 0x1701) -> int:
+        """Frontier at level L: subtrees below it compressed and factorized,
+        the reduced system I + VW of the frontier skeletons factored."""
+        if n_samp is None:
+            n_samp = 2 * s_max
+        self.h, self.tau, self.s_max, self.lam = float(h), float(tau), int(s_max), float(lam)
+        st = self._lib.kfo_hybrid(self._h, int(L), float(h), float(tau), int(s_max), int(n_samp),
+                                  ctypes.c_uint64(seed), float(lam))
+        if st not in (KFO_OK, KFO_EILLCOND):
+            raise ValueError(f"oracle hybrid status {st}")
+        return int(st)
+
+    def hybrid_solve(self, b: np.ndarray) -> np.ndarray:
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.empty(self.N)
+        if self._lib.kfo_hybrid_solve(self._h, _ptr(b), _ptr(x)) != KFO_OK:
+            raise ValueError("oracle: hybrid_solve needs kfo_hybrid first")
+        return x
+
+    def hybrid_matvec(self, x: np.ndarray) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.empty(self.N)
+        if self._lib.kfo_hybrid_matvec(self._h, _ptr(x), _ptr(y)) != KFO_OK:
+            raise ValueError("oracle: hybrid_matvec needs kfo_hybrid first")
+        return y
 
     # ---- factorization ------------------------------------------------------
     def factorize(self, lam: float, variant: int = 0) -> int:

@@ -49,6 +49,12 @@ struct kfo {
   int64_t* hi;
   double h, c_exp, lambda;
   int32_t skeletonized, factorized, variant;
+  /* hybrid level-restricted solver (kfo_hybrid): frontier level, offsets of
+   * the frontier skeleton blocks, LU of the reduced system I + VW */
+  int32_t hyb_ready, hyb_L;
+  int64_t* hyb_off;
+  double* hyb_lu;
+  int64_t* hyb_piv;
   int32_t illcond;
   node_t* nd;     /* indexed by heap id */
 };
@@ -260,6 +266,7 @@ void kfo_free(kfo* o) {
   if (!o) return;
   free_factor(o);
   free_skel(o);
+  free(o->hyb_off); free(o->hyb_lu); free(o->hyb_piv);
   free(o->nd); free(o->X); free(o->perm); free(o->lo); free(o->hi);
   free(o);
 }
@@ -461,6 +468,7 @@ static void skeletonize_rec(kfo* o, int32_t a, double tau, int32_t s_max, int32_
 
 int32_t kfo_skeletonize(kfo* o, double h, double tau, int32_t s_max, int32_t n_samp, uint64_t seed) {
   if (!(h > 0.0) || !(tau >= 0.0) || s_max < 0 || n_samp < 0) return KFO_EINVAL;
+  o->hyb_ready = 0;
   free_factor(o);
   free_skel(o);
   o->h = h;
@@ -652,6 +660,7 @@ int32_t kfo_factorize(kfo* o, double lambda, int32_t variant) {
   if (!o->skeletonized) return KFO_EINVAL;
   if (!(lambda >= 0.0) || (variant != 0 && variant != 1)) return KFO_EINVAL;
   free_factor(o);
+  o->hyb_ready = 0;
   o->lambda = lambda;
   o->variant = variant;
   o->illcond = 0;
@@ -861,6 +870,7 @@ int32_t kfo_subtrees(kfo* o, const int32_t* roots, int32_t nroots, double h, dou
       if (i != j && (is_ancestor_or_self(roots[i], roots[j]) || is_ancestor_or_self(roots[j], roots[i])))
         return KFO_EINVAL;  /* subtrees must be disjoint */
   }
+  o->hyb_ready = 0;
   for (int32_t i = 0; i < nroots; ++i)
     for (int32_t lv = 0; ((int64_t)roots[i] << lv) <= o->nnodes; ++lv)
       for (int64_t b = (int64_t)roots[i] << lv; b < ((int64_t)roots[i] + 1) << lv; ++b) clear_node(&o->nd[b]);
@@ -876,4 +886,140 @@ int32_t kfo_subtrees(kfo* o, const int32_t* roots, int32_t nroots, double h, dou
   }
   if (nroots == 1 && roots[0] == 1) o->skeletonized = o->factorized = 1; /* the whole tree */
   return o->illcond ? KFO_EILLCOND : KFO_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hybrid level-restricted solver (Sec. II-C "Fast hybrid solver",
+ * Algorithms 6-8).  The frontier A is the set of the 2^L nodes of level L
+ * (1 <= L <= D): their subtrees are skeletonized and factorized by
+ * Algorithms 1-2, the frontier nodes' own IDs and P^ included; the nodes above
+ * A are neither compressed nor factorized.  The operator is
+ *   lambda I + K~ = D + U V,   D = blockdiag(lambda I + K~_aa),
+ *   U = blockdiag(P_{a a~}),   V[a~, b] = K_{a~ b} for frontier nodes b != a
+ *   (and 0 for b = a),
+ * so the block between two frontier subtrees is P_{a a~} K_{a~ b} (the second
+ * form of Eq. e:uv).  With W = D^-1 U = blockdiag(P^_a), Eq. (e:smw) gives
+ *   x = D^-1 u - W (I + V W)^-1 V D^-1 u          (Algorithm 6).
+ * The paper solves the reduced system I + VW (size sum_a s_a) by a Krylov
+ * method with the products of Algorithms 7 (MatVecW) and 8 (MatVecV); the
+ * oracle forms it, (VW)[a~, b~] = K_{a~ b} P^_b, and factors it with LU.
+ * READING: the last line of Algorithm 6 is printed w = u - MatVecW(root, w, A);
+ * the vector the correction is subtracted from is D^-1 u of its first line,
+ * as Eq. (e:smw) requires. */
+static int32_t frontier_s(const kfo* o, int32_t a) { return o->nd[a].s; }
+
+/* t[a~] = sum over frontier b != a of K_{a~ b} y_b (Algorithm 8 over A). */
+static void hyb_apply_v(const kfo* o, const double* y, double* t) {
+  int32_t nA = 1 << o->hyb_L;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int32_t ia = 0; ia < nA; ++ia) {
+    int32_t a = nA + ia;
+    const node_t* na = &o->nd[a];
+    for (int32_t q = 0; q < na->s; ++q) {
+      double acc = 0.0;
+      for (int32_t ib = 0; ib < nA; ++ib) {
+        int32_t b = nA + ib;
+        if (b == a) continue;
+        for (int64_t j = o->lo[b]; j < o->hi[b]; ++j) acc = acc + kern(o, na->skel[q], j) * y[j];
+      }
+      t[o->hyb_off[ia] + q] = acc;
+    }
+  }
+}
+
+int32_t kfo_hybrid(kfo* o, int32_t L, double h, double tau, int32_t s_max, int32_t n_samp, uint64_t seed,
+                   double lambda) {
+  if (!o || L < 1 || L > o->D) return KFO_EINVAL;
+  int32_t nA = 1 << L;
+  int32_t* roots = (int32_t*)malloc(sizeof(int32_t) * nA);
+  for (int32_t i = 0; i < nA; ++i) roots[i] = nA + i;
+  int32_t st = kfo_subtrees(o, roots, nA, h, tau, s_max, n_samp, seed, lambda);
+  free(roots);
+  if (st != KFO_OK && st != KFO_EILLCOND) return st;
+  free(o->hyb_off); free(o->hyb_lu); free(o->hyb_piv);
+  o->hyb_L = L;
+  o->hyb_off = (int64_t*)malloc(sizeof(int64_t) * (nA + 1));
+  o->hyb_off[0] = 0;
+  for (int32_t i = 0; i < nA; ++i) o->hyb_off[i + 1] = o->hyb_off[i] + frontier_s(o, nA + i);
+  int64_t S = o->hyb_off[nA];
+  o->hyb_lu = (double*)calloc((size_t)(S > 0 ? S * S : 1), sizeof(double));
+  o->hyb_piv = (int64_t*)malloc(sizeof(int64_t) * (S > 0 ? S : 1));
+  double* M = o->hyb_lu;
+  for (int64_t i = 0; i < S; ++i) M[i * S + i] = 1.0;
+  /* (VW)[a~, b~] = K_{a~ b} P^_b for frontier nodes a != b */
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int32_t ia = 0; ia < nA; ++ia) {
+    const node_t* na = &o->nd[nA + ia];
+    for (int32_t ib = 0; ib < nA; ++ib) {
+      if (ib == ia) continue;
+      int32_t b = nA + ib;
+      const node_t* nb = &o->nd[b];
+      int64_t n = nsz(o, b);
+      double* Kab = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (na->s > 0 ? na->s : 1));
+      for (int32_t q = 0; q < na->s; ++q)
+        for (int64_t j = 0; j < n; ++j) Kab[q * n + j] = kern(o, na->skel[q], o->lo[b] + j);
+      for (int32_t q = 0; q < na->s; ++q)
+        for (int32_t t = 0; t < nb->s; ++t) {
+          double acc = 0.0;
+          for (int64_t j = 0; j < n; ++j) acc = acc + Kab[q * n + j] * nb->Phat[j * nb->s + t];
+          M[(o->hyb_off[ia] + q) * S + o->hyb_off[ib] + t] += acc;
+        }
+      free(Kab);
+    }
+  }
+  double rel = S > 0 ? lu_factor(M, o->hyb_piv, S) : 1.0;
+  o->hyb_ready = 1;
+  return (st == KFO_EILLCOND || rel < 1e-14) ? KFO_EILLCOND : KFO_OK;
+}
+
+int32_t kfo_hybrid_solve(const kfo* o, const double* b, double* x) {
+  if (!o || !o->hyb_ready) return KFO_EINVAL;
+  int64_t N = o->N;
+  int32_t nA = 1 << o->hyb_L;
+  int64_t S = o->hyb_off[nA];
+  double* y = (double*)malloc(sizeof(double) * N);
+  double* t = (double*)calloc((size_t)(S > 0 ? S : 1), sizeof(double));
+  for (int64_t i = 0; i < N; ++i) y[i] = b[o->perm[i]];
+  /* y = D^-1 u: the direct solve of every frontier subtree (Algorithm 3) */
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int32_t ia = 0; ia < nA; ++ia) solve_rec(o, nA + ia, y + o->lo[nA + ia], 1, 1);
+  hyb_apply_v(o, y, t);                                   /* t = V y */
+  if (S > 0) lu_solve(o->hyb_lu, o->hyb_piv, S, t, 1, 0); /* z = (I + V W)^-1 t */
+  for (int32_t ia = 0; ia < nA; ++ia) {                   /* x = y - W z */
+    const node_t* na = &o->nd[nA + ia];
+    for (int64_t i = 0; i < nsz(o, nA + ia); ++i) {
+      double acc = 0.0;
+      for (int32_t q = 0; q < na->s; ++q) acc = acc + na->Phat[i * na->s + q] * t[o->hyb_off[ia] + q];
+      y[o->lo[nA + ia] + i] = y[o->lo[nA + ia] + i] - acc;
+    }
+  }
+  for (int64_t i = 0; i < N; ++i) x[o->perm[i]] = y[i];
+  free(y); free(t);
+  return KFO_OK;
+}
+
+int32_t kfo_hybrid_matvec(const kfo* o, const double* x, double* y) {
+  if (!o || !o->hyb_ready) return KFO_EINVAL;
+  int64_t N = o->N;
+  int32_t nA = 1 << o->hyb_L;
+  int64_t S = o->hyb_off[nA];
+  double* u = (double*)malloc(sizeof(double) * N);
+  double* v = (double*)malloc(sizeof(double) * N);
+  double* t = (double*)calloc((size_t)(S > 0 ? S : 1), sizeof(double));
+  for (int64_t i = 0; i < N; ++i) u[i] = x[o->perm[i]];
+  /* D u: the hierarchical operator of every frontier subtree */
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int32_t ia = 0; ia < nA; ++ia) matvec_rec(o, nA + ia, u + o->lo[nA + ia], v + o->lo[nA + ia], 0);
+  hyb_apply_v(o, u, t);                                   /* V u */
+  for (int32_t ia = 0; ia < nA; ++ia) {                   /* + U (V u) */
+    const node_t* na = &o->nd[nA + ia];
+    for (int64_t i = 0; i < nsz(o, nA + ia); ++i) {
+      double acc = 0.0;
+      for (int32_t q = 0; q < na->s; ++q) acc = acc + na->Pfull[i * na->s + q] * t[o->hyb_off[ia] + q];
+      v[o->lo[nA + ia] + i] = v[o->lo[nA + ia] + i] + acc;
+    }
+  }
+  for (int64_t i = 0; i < N; ++i) y[o->perm[i]] = v[i];
+  free(u); free(v); free(t);
+  return KFO_OK;
 }

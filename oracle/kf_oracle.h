@@ -81,6 +81,18 @@ int32_t kfo_grad(const kfo* o, const double* x, const double* g, double* dLdb, d
 int32_t kfo_subtrees(kfo* o, const int32_t* roots, int32_t nroots, double h, double tau, int32_t s_max,
                      int32_t n_samp, uint64_t seed, double lambda);
 
+/* Hybrid level-restricted solver (Sec. II-C, Algorithms 6-8): the subtrees
+ * of the 2^L frontier nodes of level L (1 <= L <= D) are skeletonized and
+ * factorized (the frontier nodes' IDs included); above them nothing is
+ * compressed, and the reduced system I + VW of the frontier skeletons is
+ * formed and factored with LU.  Replaces any earlier skeletons or factors of
+ * those subtrees.  KFO_EILLCOND when a pivot is tiny. */
+int32_t kfo_hybrid(kfo* o, int32_t L, double h, double tau, int32_t s_max, int32_t n_samp, uint64_t seed,
+                   double lambda);
+/* x = (D + U V)^-1 b (Algorithm 6) and y = (D + U V) x, ORIGINAL order. */
+int32_t kfo_hybrid_solve(const kfo* o, const double* b, double* x);
+int32_t kfo_hybrid_matvec(const kfo* o, const double* x, double* y);
+
 /* splitmix64 output function (used by the sampler); exposed for its pin. */
 uint64_t kfo_splitmix64(uint64_t x);
 

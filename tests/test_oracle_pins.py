@@ -433,3 +433,73 @@ def test_subtrees_equal_the_whole_run():
     np.testing.assert_array_equal(full.solve(b), whole.solve(b))
     with pytest.raises(ValueError):
         part.subtrees([4, 9], 0.4, 1e-6, 24, 0.6)     # 9 lies under 4
+
+
+# ---------------------------------------------------------------- hybrid level-restricted solver
+def test_hybrid_at_level_1_equals_the_direct_solver():
+    """With the frontier at level 1 the hybrid operator D + UV (Sec. II-C) is
+    the direct solver's operator (Eq. e:blocksmw at the root, same IDs below),
+    and its reduced system I + VW is the root's Z: same operator, same solution."""
+    X, rng = make(N=2048, d=3, m=64, seed=15)
+    direct, hyb = Oracle(X, 64), Oracle(X, 64)
+    direct.skeletonize(0.25, 1e-6, 40)
+    direct.factorize(0.7)
+    assert hyb.hybrid(1, 0.25, 1e-6, 40, 0.7) == KFO_OK
+    b = rng.standard_normal(2048)
+    np.testing.assert_allclose(hyb.hybrid_matvec(b), direct.matvec(b), rtol=0, atol=1e-13 * np.abs(b).sum())
+    x, xd = hyb.hybrid_solve(b), direct.solve(b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-12
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_hybrid_full_rank_equals_dense_cholesky(L):
+    """tau = 0, s_max >= N/2 and S' = the whole complement: every ID keeps all
+    columns, the hybrid operator is lambda I + K exactly at any frontier level,
+    and its solve equals scipy's dense Cholesky solve."""
+    X, rng = make(N=1024, d=4, m=128, seed=7)
+    o = Oracle(X, 128)
+    assert o.hybrid(L, 0.35, 0.0, 1024, 1.0, n_samp=1024) == KFO_OK
+    b = rng.standard_normal(1024)
+    A = gauss_K(X, X, 0.35) + np.eye(1024)
+    xd = sla.cho_solve(sla.cho_factor(A), b)
+    assert np.linalg.norm(o.hybrid_solve(b) - xd) / np.linalg.norm(xd) <= 1e-10
+
+
+def test_hybrid_operator_blocks_and_solve():
+    """Frontier at the leaves (L = D): D = blockdiag(lambda I + K_aa) exact,
+    the block between leaves a != b is P_{a a~} K_{a~ b} (second form of
+    Eq. e:uv).  The operator assembled column by column from the oracle equals
+    that block matrix built here from the kernel definition and the oracle's
+    skeletons and P; the hybrid solve (Algorithm 6) equals numpy's dense solve
+    of it, and it is a different (less compressed) operator than the direct
+    solver's."""
+    X, rng = make(N=512, d=3, m=64, seed=16)
+    o = Oracle(X, 64)
+    h, lam = 0.3, 0.5
+    assert o.hybrid(o.D, h, 1e-4, 24, lam) == KFO_OK
+    perm = o.perm()
+    Xt = X[perm]
+    nA = 1 << o.D
+    A = np.zeros((512, 512))
+    for a in range(nA, 2 * nA):
+        la, ha = o.node_range(a)
+        A[la:ha, la:ha] = gauss_K(Xt[la:ha], Xt[la:ha], h) + lam * np.eye(ha - la)
+        Pa, sk = o.P_full(a), o.skel(a)
+        for b in range(nA, 2 * nA):
+            if b == a:
+                continue
+            lb, hb = o.node_range(b)
+            A[la:ha, lb:hb] = Pa @ gauss_K(Xt[sk], Xt[lb:hb], h)
+    inv = np.argsort(perm)                      # tree position of each original index
+    Ao = A[np.ix_(inv, inv)]                    # the same operator in original order
+    I = np.eye(512)
+    Ah = np.stack([o.hybrid_matvec(I[:, j]) for j in range(512)], axis=1)
+    assert np.abs(Ah - Ao).max() <= 1e-13 * np.abs(Ao).max()
+    b = rng.standard_normal(512)
+    x = o.hybrid_solve(b)
+    xd = np.linalg.solve(Ao, b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-12
+    direct = Oracle(X, 64)
+    direct.skeletonize(h, 1e-4, 24)
+    direct.factorize(lam)
+    assert np.linalg.norm(direct.matvec(b) - Ao @ b) > 1e-8 * np.linalg.norm(Ao @ b)
