@@ -27,7 +27,8 @@
  *    B + j*ld (elements), ld >= N.
  *  - Sizes: N < 2^31, 1 <= d <= 1024, 1 <= m, 1 <= s_max <= 512.
  *  - Handles own the device memory they allocate, drawn through the
- *    allocator given to kf_create (cudaMalloc/cudaFree when NULL).  A factor
+ *    allocator given to kf_create (cudaMallocAsync/cudaFreeAsync on the call's
+ *    stream when NULL).  A factor
  *    keeps a pointer to its tree: free factors before their tree.  *_free(NULL)
  *    is a no-op.
  *  - Device-side errors (ill-conditioned pivots, bounded waits that ran out)
@@ -54,7 +55,7 @@ typedef enum {
                            (Sec. III "Stability": detectable instability) */
   KF_ENOTCONV = 5,      /* refinement did not reach the requested residual */
   KF_ETIMEOUT = 6,      /* a bounded device-side wait ran out */
-  KF_EUNSUPPORTED = 7   /* valid request this build does not support */
+  KF_EUNSUPPORTED = 7   /* valid request the library does not support */
 } kf_status;
 
 typedef enum { KF_F32 = 0, KF_F64 = 1 } kf_dtype;

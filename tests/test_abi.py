@@ -36,3 +36,27 @@ def test_library_loads_without_gpu():
     assert lib.kf_status_string(4) == b"KF_EILLCOND"
     assert lib.kf_status_string(0) == b"KF_OK"
 
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """include/kf.h compiles as strict C99 with warnings as errors, and a C
+    program that takes the address of every declared entry point links
+    against libkf.so (run needs no GPU: it is only linked)."""
+    lib = _build.build()
+    names = declared_symbols()
+    src = tmp_path / "use_kf.c"
+    src.write_text(
+        '#include "kf.h"\n'
+        "typedef void (*fp)(void);\n"
+        "fp kf_all[] = {\n" + "".join(f"  (fp){n},\n" for n in names) + "};\n"
+        "int main(void) {\n"
+        "  kf_opts o = {0};\n"
+        "  kf_solve_info info = {0};\n"
+        "  o.precision = KF_PREC_MIXED;\n"
+        "  return (int)(sizeof(kf_all) / sizeof(kf_all[0])) + o.precision + info.iters - 1 - "
+        f"{len(names)};\n"
+        "}\n")
+    obj = tmp_path / "use_kf.o"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    "-c", str(src), "-o", str(obj)], check=True)
+    subprocess.run(["gcc", str(obj), "-L", os.path.dirname(lib), "-lkf",
+                    "-Wl,--unresolved-symbols=ignore-in-shared-libs", "-o", str(tmp_path / "use_kf")], check=True)
