@@ -451,16 +451,17 @@ def test_hybrid_at_level_1_equals_the_direct_solver():
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-12
 
 
-@pytest.mark.parametrize("L", [1, 2, 3])
-def test_hybrid_full_rank_equals_dense_cholesky(L):
+@pytest.mark.parametrize("N,m,L", [(1024, 128, 1), (1024, 128, 2), (1024, 128, 3), (1000, 100, 2), (1000, 100, 4)])
+def test_hybrid_full_rank_equals_dense_cholesky(N, m, L):
     """tau = 0, s_max >= N/2 and S' = the whole complement: every ID keeps all
-    columns, the hybrid operator is lambda I + K exactly at any frontier level,
-    and its solve equals scipy's dense Cholesky solve."""
-    X, rng = make(N=1024, d=4, m=128, seed=7)
-    o = Oracle(X, 128)
+    columns, the hybrid operator is lambda I + K exactly at any frontier level
+    (also on ragged trees: N = 1000, leaves of 62 and 63 points), and its solve
+    equals scipy's dense Cholesky solve."""
+    X, rng = make(N=N, d=4, m=m, seed=7)
+    o = Oracle(X, m)
     assert o.hybrid(L, 0.35, 0.0, 1024, 1.0, n_samp=1024) == KFO_OK
-    b = rng.standard_normal(1024)
-    A = gauss_K(X, X, 0.35) + np.eye(1024)
+    b = rng.standard_normal(N)
+    A = gauss_K(X, X, 0.35) + np.eye(N)
     xd = sla.cho_solve(sla.cho_factor(A), b)
     assert np.linalg.norm(o.hybrid_solve(b) - xd) / np.linalg.norm(xd) <= 1e-10
 
