@@ -35,12 +35,14 @@ sys.path.insert(0, ROOT)
 METRIC = "factorize sec & solve RHS/s at N=1M, rel err≤1e-5; mixed vs FP64 GPU path"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 1.25          # recipe's nominal FP64 rate (152 SMs, 2.07 GHz)
-# DRAM bytes (read + write) of the leaf-level k_pivoted_qr launch at N = 2^20,
-# from the ncu capture summarised in profiles/k_pivoted_qr_leaf_level_N131072.md
-# (leaf level at N = 2^17, 128 leaves, scaled by the 8x leaf count); None while
-# the kernel differs from the captured one.
+# DRAM bytes (read + write) of the leaf-level k_pivoted_qr launch at N = 2^20:
+# ncu's dram__bytes_read.sum + dram__bytes_write.sum of that launch captured on
+# the same recipe at N = 2^17 (128 leaves, 176 GB), scaled by the 8x leaf count
+# (every leaf streams the same bytes); None while the kernel differs from the
+# captured one.
 QR_TRAFFIC_PER_LAUNCH = 1.41e12
-QR_TRAFFIC_SRC = "profiles/k_pivoted_qr_leaf_level_N131072.md"
+QR_TRAFFIC_SRC = ("ncu DRAM read+write bytes of the leaf-level k_pivoted_qr launch on the same recipe at "
+                  "N=2^17 (128 leaves), scaled x8 to the 1024 leaves of N=2^20")
 ORACLE_SAMPLE_N = 8192           # points per oracle sample step
 
 
@@ -102,19 +104,31 @@ def summarize_clocks(rows, gpu_index=0):
 
 # ---------------------------------------------------------------- algorithmic work
 def qr_flops(ns, c, s):
-    """FP64 flops of the truncated pivoted Householder QR + P of one node:
-    initial column norms, per step the reflector application (dot + update)
-    and the norms of the trailing columns, then T = R11^-1 R12."""
+    """FP64 flops the truncated pivoted Householder QR + P of one node
+    executes: the initial column norms; per step k the Householder vector
+    (2 (ns - k)), the reflector's dot products and update of the trailing
+    columns (4 (ns - k)(c - k - 1)) and one downdate per trailing norm
+    (2 (c - k - 1)); then T = R11^-1 R12 (s^2 (c - s)).  The kernel downdates
+    the norms and evaluates one again only after it has fallen 16x (a few
+    times per column over the whole QR), which this count leaves out."""
     f = 2.0 * ns * c
     for k in range(s):
         rows, cols = ns - k, c - k - 1
-        f += 4.0 * rows * cols + 2.0 * (rows - 1) * cols
+        f += 2.0 * rows + 4.0 * rows * cols + 2.0 * cols
     f += float(s) * s * (c - s)
     return f
 
 
-def level_qr_flops(sizes, ranks, N, D, n_samp, s_max, lo, hi):
-    """QR flops per tree level (dict level -> flops), from realized ranks."""
+def qr_flops_bound(ns, c, s):
+    """The coarser work bound 4 |S'| c s of one node's ID (every step charged
+    the full block)."""
+    return 4.0 * ns * c * s
+
+
+def level_qr_flops(sizes, ranks, N, D, n_samp, s_max, lo, hi, model=None):
+    """QR flops per tree level (dict level -> flops), from realized ranks,
+    with the executed-flop model (default) or another per-node model."""
+    model = model or qr_flops
     out = {}
     for l in range(1, D + 1):
         tot = 0.0
@@ -122,7 +136,7 @@ def level_qr_flops(sizes, ranks, N, D, n_samp, s_max, lo, hi):
             n = hi[a] - lo[a]
             ns = min(n_samp, N - n)
             c = n if l == D else ranks[2 * a] + ranks[2 * a + 1]
-            tot += qr_flops(ns, c, ranks[a])
+            tot += model(ns, c, ranks[a])
         out[l] = tot
     return out
 
@@ -294,8 +308,28 @@ def cpu_cores():
         return os.cpu_count()
 
 
+def oracle_scaling_check(sizes):
+    """Times the oracle (tree + skeletonize + factorize, as it stands) once
+    at each size of the scale recipe and compares the measured time ratios
+    with the work model N * (levels + 1) that extrapolates the CPU baseline
+    to N = 2^20."""
+    rows = []
+    for n in sizes:
+        tf, ts, D = run_oracle_sample(n)
+        rows.append({"N": n, "levels": D, "factorize_s": round(tf, 3), "solve_s": round(ts, 4)})
+    base = rows[0]
+    for r in rows:
+        r["model_ratio"] = round(oracle_scale(base["N"], r["N"]), 3)
+        r["measured_ratio"] = round(r["factorize_s"] / base["factorize_s"], 3)
+    return {"oracle_scaling": rows, "cores": int(os.environ.get("OMP_NUM_THREADS", cpu_cores())),
+            "model": "factorize time proportional to N * (levels + 1)"}
+
+
 def reference_main(args, rank, world):
     if rank != 0:
+        return
+    if args.oracle_sizes:
+        print(json.dumps(oracle_scaling_check([int(v) for v in args.oracle_sizes.split(",")])), flush=True)
         return
     scale = oracle_scale(ORACLE_SAMPLE_N)
     for _ in range(args.warmup):
@@ -636,16 +670,20 @@ def gpu_main(args, rank, world):
         # the leaf level's k_pivoted_qr launch (one CTA per leaf), the largest
         # single launch of the step; the other levels are phases qr and qr_cluster
         per_level = level_qr_flops(None, ranks, p.N, D, 2 * p.s_max, p.s_max, lo, hi)
-        flops = per_level[D] * args.steps
+        bound_level = level_qr_flops(None, ranks, p.N, D, 2 * p.s_max, p.s_max, lo, hi, model=qr_flops_bound)
         avg_ms = phase_ms["qr_leaf"] / phase_launches["qr_leaf"]
-        per_launch = flops / phase_launches["qr_leaf"]
+        per_launch = per_level[D] * args.steps / phase_launches["qr_leaf"]
         achieved = per_launch / (avg_ms * 1e-3) / 1e12
+        achieved_bound = bound_level[D] * args.steps / phase_launches["qr_leaf"] / (avg_ms * 1e-3) / 1e12
         roof = {"kernel": "k_pivoted_qr, leaf level (FP64 ID, one CTA per leaf)", "bound": "alu",
                 "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
                 "traffic": QR_TRAFFIC_PER_LAUNCH, "traffic_src": QR_TRAFFIC_SRC,
                 "peak_src": "recipe nominal FP64 rate (1.25 TFLOP/s; 1.20 measured by an FMA loop)",
-                "work_per_launch": per_launch, "avg_launch_ms": avg_ms}
+                "work_model": "executed Householder flops from the realized ranks (norms downdated, not recomputed)",
+                "work_per_launch": per_launch, "avg_launch_ms": round(avg_ms, 3),
+                "frac_of_bound_model": round(achieved_bound / FP64_PEAK_TFLOPS, 4),
+                "bound_model": "4 |S'| c s per node"}
     else:
         sb = solve_bytes(p.N, D, ranks, lo, hi, 4) * args.steps
         sweep_ms = sum(phase_ms[k] for k in ("solve_leaf", "solve_colsum", "solve_zsolve", "solve_rowupd"))
@@ -653,9 +691,9 @@ def gpu_main(args, rank, world):
         roof = {"kernel": f"dominant phase {dominant}", "bound": "hbm", "achieved": round(achieved, 1),
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
                 "traffic": None}
-    roof["phase_ms_per_step"] = {k: round(v / args.steps, 3) for k, v in phase_ms.items() if v > 0}
-    roof["phase_rooflines"] = phase_rooflines(phase_work(p, D, lo, hi, ranks, 2 * p.s_max), phase_ms,
-                                              phase_launches, args.steps, peaks)
+    phase_ms_per_step = {k: round(v / args.steps, 3) for k, v in phase_ms.items() if v > 0}
+    phase_roofs = phase_rooflines(phase_work(p, D, lo, hi, ranks, 2 * p.s_max), phase_ms, phase_launches,
+                                  args.steps, peaks)
 
     # ---- CPU baseline (oracle, bounded sample) ------------------------------------------
     cpu = None
@@ -675,24 +713,22 @@ def gpu_main(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "scale_N1048576_d28", "N": p.N, "d": p.d, "h": p.h, "lambda": p.lam, "m": p.m,
                        "s_max": p.s_max, "tau": p.tau, "n_samp": 2 * p.s_max, "nrhs": 1,
-                       "precision": "mixed (FP32 factors with tcgen05 3xTF32 products; FP64 ID, Z, T, operator, "
-                                    "GMRES)", "parallelism": f"replicas x{world}",
-                       "l2": "inputs and factors larger than L2 (no flush needed)"},
+                       "precision": "mixed (FP32 factors, tcgen05 3xTF32 products; FP64 ID, Z, T, operator, GMRES)",
+                       "parallelism": f"replicas x{world}", "l2": "inputs and factors larger than L2 (no flush)"},
+            # the metric's comparison, as top-level scalars
             "solve_rhs_per_s": round(1.0 / solve_s, 2),
-            "solve_note": f"mixed solve = direct sweep of the FP32 factors + GMRES({args.gmres_m}) against the FP64 operator "
-                          f"to eps_r <= {args.mixed_tol:g}",
+            "solve_note": f"mixed: FP32 sweep + GMRES({args.gmres_m}) vs the FP64 operator to eps_r <= {args.mixed_tol:g}",
             "gmres_iters": float(np.mean(gmres_iters[-args.steps:])) if gmres_iters else None,
-            "autotuned": {("mixed" if k == kf.KF_PREC_MIXED else "fp64"): {"chosen": v[0],
-                          "candidate_ms": [round(t, 2) for t in v[1]]} for k, v in tuned.items()} or None,
             "mixed_rel_err_vs_reference": mixed_rel if fp64 else None,
-            "fp64_path": fp64,
-            "mixed_unrefined": unref,
-            "solve_seed_study": seed_study,
-            "mixed_solve_at_metric_bar": at_bar,
-            "differentiation": diff,
-            "batched": batched,
-            "accuracy_reference": reference if fp64 else None,
-            "ranks": {"mean": float(np.mean(ranks[2:])), "max": int(np.max(ranks))},
+            "mixed_solve_rhs_per_s_at_1e-5": at_bar["solve_rhs_per_s"] if at_bar else None,
+            "mixed_rel_err_at_1e-5": at_bar["rel_err_vs_reference"] if at_bar else None,
+            "fp64_factorize_s": fp64["factorize_s"] if fp64 else None,
+            "fp64_solve_rhs_per_s": fp64["solve_rhs_per_s"] if fp64 else None,
+            "fp64_rel_err_vs_reference": fp64["rel_err_vs_reference"] if fp64 else None,
+            "mixed_unrefined_rel_err": unref["rel_err_vs_reference"] if unref else None,
+            "reference": "FP64 factorization + GMRES vs the FP64 operator (eps_r %.1e)" % reference["eps_r"]
+                         if fp64 else None,
+            "ranks": {"mean": round(float(np.mean(ranks[2:])), 1), "max": int(np.max(ranks))},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -700,7 +736,21 @@ def gpu_main(args, rank, world):
             "clocks": clk,
             "peaks_src": peaks["src"],
         }
+        detail = {
+            "detail_of": METRIC, "workload": "scale_N1048576_d28",
+            "phase_ms_per_step": phase_ms_per_step, "phase_rooflines": phase_roofs,
+            "autotuned": {("mixed" if k == kf.KF_PREC_MIXED else "fp64"): {"chosen": v[0],
+                          "candidate_ms": [round(t, 2) for t in v[1]]} for k, v in tuned.items()} or None,
+            "fp64_path": fp64, "mixed_unrefined": unref, "mixed_solve_at_metric_bar": at_bar,
+            "solve_seed_study": seed_study, "accuracy_reference": reference if fp64 else None,
+            "differentiation": diff, "batched": batched,
+        }
         print(json.dumps(line), flush=True)
+        # the per-phase and per-workload figures: one JSON line on stderr (and a file on request)
+        print(json.dumps(detail), file=sys.stderr, flush=True)
+        if args.detail_out:
+            with open(args.detail_out, "w") as fh:
+                json.dump(detail, fh, indent=1)
 
 
 def once(args):
@@ -752,6 +802,10 @@ def main():
     ap.add_argument("--mixed-tol", type=float, default=1e-9,
                     help="GMRES target eps_r of the mixed solve (the FP64 direct solve reaches about 1e-8)")
     ap.add_argument("--unrefined", action="store_true", help="--once: mixed factors without the FP64 operator or GMRES")
+    ap.add_argument("--oracle-sizes", default=None,
+                    help="--impl reference: time the oracle once at each of these comma-separated sizes of the "
+                         "scale recipe and compare with the extrapolation model")
+    ap.add_argument("--detail-out", default=None, help="also write the per-phase / per-workload details to this file")
     args = ap.parse_args()
     if args.once:
         once(args)

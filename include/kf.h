@@ -242,8 +242,11 @@ kf_status kf_factorize_with_ids(kf_tree* t, double h, double lambda, int32_t s_m
  * X:    device, N x d FP64 row-major, original order (read only).
  * Xt:   device output, N x d FP64, the points in tree order.
  * perm: device output, N int64, perm[i] = original index of tree position i.
- * Limits: 1 <= N <= 65536, 1 <= d, N * d <= 2^19, m >= 1; larger sizes are
- * rejected with KF_EINVAL and a message in kf_last_error(NULL).
+ * Limits: 1 <= N <= 65536, 1 <= d <= 1024 (as kf_tree_build), N * d <= 2^19,
+ * m >= 1; larger sizes are rejected with KF_EINVAL and a message in
+ * kf_last_error(NULL); a current device index above 63 gives KF_EUNSUPPORTED.
+ * X is checked for non-finite coordinates before anything is written: on
+ * that KF_EINVAL, Xt and perm are left untouched.
  * Scratch: one 12 MiB file-scope device array that every GPU loading the
  * library holds until the process exits.  Every call shares it and it keeps
  * the previous call's contents (the call initializes what it reads), so calls
@@ -270,6 +273,16 @@ kf_status kf_tree_perm_noalloc(const double* X, int64_t N, int32_t d, int32_t m,
 #define KF_AUTOTUNE_MAX 8
 kf_status kf_autotune(kf_tree* t, double h, double lambda, double tau, int32_t s_max, const kf_opts* base,
                       void* stream, kf_opts* best, float* ms, int32_t* ncand);
+
+/* Test hook of the device-side time-out path (no counterpart in the paper).
+ * polls > 0: every CTA of the tensor-core products of the mixed path (the Z
+ * off-diagonal blocks and the telescoping) first polls an mbarrier that
+ * nothing arrives at, at most `polls` times, and then takes the path of a
+ * bounded wait that ran out: it flags KF_ETIMEOUT in the factor's device
+ * status word, skips its product, frees its tensor memory and returns, so the
+ * context stays usable.  polls = 0 (the default) turns the probe off.
+ * Process-wide for the current device; synchronous.  KF_EINVAL for polls < 0. */
+kf_status kf_test_tc_wait_probe(int64_t polls);
 
 /* ---- diagnostics ------------------------------------------------------------- */
 /* Number of kernel launches this process has made through the library. */

@@ -414,6 +414,16 @@ def _autograd():
 
         @staticmethod
         def forward(ctx, b, lam, h, factor):
+            # The factorization fixes lambda and h; a solve with other values
+            # would be stale while backward reported gradients at the values
+            # passed in, so a mismatch is an error (refactorize instead).
+            for name, given, held in (("lambda", lam, factor.lam), ("h", h, factor.h_)):
+                v = float(given.detach().reshape(-1)[0]) if torch.is_tensor(given) else float(given)
+                if torch.is_tensor(given) and given.numel() != 1:
+                    raise ValueError(f"KernelSolve: {name} must be a scalar")
+                if v != held:
+                    raise ValueError(f"KernelSolve: {name}={v!r} differs from the factorization's {held!r}; "
+                                     "factorize again with the new value")
             x = factor.solve(b)
             ctx.factor = factor
             ctx.lam_dtype = lam.dtype if torch.is_tensor(lam) else torch.float64

@@ -68,6 +68,7 @@ SIGNATURES = {
     "kf_factorize_batched": (_I32, [_P, _I32, _P, _P, _P, _I32, _P, _P, _P]),
     "kf_solve_batched": (_I32, [_P, _I32, _P, _P, _P, _P, _I32, _P]),
     "kf_autotune": (_I32, [_P, _D, _D, _D, _I32, _P, _P, _P, _P, _P]),
+    "kf_test_tc_wait_probe": (_I32, [_I64]),
     "kf_launch_count": (_I64, []),
     "kf_profile_enable": (_I32, [_I32]),
     "kf_profile_read": (_I32, [_P, _P, _I32]),

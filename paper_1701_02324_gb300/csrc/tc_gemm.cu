@@ -27,6 +27,13 @@ constexpr int kBM = 128;  // rows per tile (tcgen05 M for cta_group::1)
 constexpr int kBK = 32;   // K elements staged per round (4 MMAs of K = 8)
 constexpr long long kSpinLimit = 1ll << 28;
 
+// Test hook of the time-out path (kf_test_tc_wait_probe): when positive, each
+// CTA of k_tc_gemm first polls an mbarrier that nothing arrives at, at most
+// this many times, and on giving up takes the path of a wait that ran out:
+// it flags KF_DEV_TIMEOUT, issues no MMA, stores nothing, frees its tensor
+// memory and returns.  Zero (no probe) in normal use.
+__device__ long long g_tc_probe_polls = 0;
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ float to_tf32(float x) {
@@ -209,8 +216,9 @@ template <int BN, class Problem>
 __global__ void __launch_bounds__(kThreads) k_tc_gemm(Problem prob, int32_t* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   constexpr int kStage = 2 * kBM * kBK + 2 * BN * kBK;  // floats per stage
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t mbar[3];  // two stages; [2] only for the time-out probe
   __shared__ uint32_t tmem_base;
+  __shared__ int probe_timed_out;
   const Tile t = prob.tile(blockIdx.x, blockIdx.y, blockIdx.z);
   if (t.skip) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -218,6 +226,17 @@ __global__ void __launch_bounds__(kThreads) k_tc_gemm(Problem prob, int32_t* __r
   if (tid == 0) {
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
+    mbar_init(&mbar[2], 1);
+    probe_timed_out = 0;
+    const long long polls = g_tc_probe_polls;
+    if (polls > 0) {
+      bool arrived = false;
+      for (long long i = 0; i < polls && !arrived; ++i) arrived = mbar_try_wait(&mbar[2], 0u);
+      if (!arrived) {
+        probe_timed_out = 1;
+        atomicOr(status, KF_DEV_TIMEOUT);
+      }
+    }
   }
   fence_before_sync();
   __syncthreads();
@@ -225,7 +244,7 @@ __global__ void __launch_bounds__(kThreads) k_tc_gemm(Problem prob, int32_t* __r
   const uint32_t tmem = tmem_base;
   constexpr uint32_t idesc = idesc_tf32(kBM, BN);
   uint32_t uses[2] = {0u, 0u};  // commits issued per stage
-  bool ok = true;
+  bool ok = probe_timed_out == 0;
   int c = 0;
   for (int kc = t.k0; kc < t.k1 && ok; kc += kBK, ++c) {
     const int st = c & 1;
@@ -419,4 +438,13 @@ kf_status kf_tc_telescope(const int32_t* lo, const int32_t* hi, const int32_t* r
   return tile_n == 128
              ? tc_telescope_bn<128>(lo, hi, rank, node0, nn, s_max, Pc_hat, Tm, ldz, Pa_hat, rows_per_child, status, s)
              : tc_telescope_bn<256>(lo, hi, rank, node0, nn, s_max, Pc_hat, Tm, ldz, Pa_hat, rows_per_child, status, s);
+}
+
+extern "C" kf_status kf_test_tc_wait_probe(int64_t polls) {
+  if (polls < 0) return kf_set_err(nullptr, KF_EINVAL, "kf_test_tc_wait_probe: polls must be >= 0");
+  long long v = (long long)polls;
+  cudaError_t e = cudaMemcpyToSymbol(g_tc_probe_polls, &v, sizeof(v));
+  if (e != cudaSuccess)
+    return kf_set_err(nullptr, KF_ECUDA, "kf_test_tc_wait_probe: %s", cudaGetErrorString(e));
+  return KF_OK;
 }

@@ -12,6 +12,7 @@
 // formulas.  Per-node reductions run over fixed chunks of the node; the
 // per-node sort is a bitonic network over segments padded to a power of two.
 #include <algorithm>
+#include <atomic>
 
 #include "kf_internal.cuh"
 #include "prof.cuh"
@@ -341,6 +342,7 @@ namespace {
 constexpr int64_t kNoAllocMaxN = 65536;
 constexpr int64_t kNoAllocMaxND = int64_t(1) << 19;
 constexpr size_t kNoAllocBytes = size_t(12) << 20;
+constexpr int kNoAllocMaxDevices = 64;
 
 __global__ void k_node_ranges(int64_t N, int D, int32_t* __restrict__ lo, int32_t* __restrict__ hi) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
@@ -368,21 +370,28 @@ extern "C" kf_status kf_tree_perm_noalloc(const double* X, int64_t N, int32_t d,
   if (N < 1 || N > kNoAllocMaxN)
     return kf_set_err(nullptr, KF_EINVAL, "kf_tree_perm_noalloc: N = %lld outside [1, %lld]", (long long)N,
                       (long long)kNoAllocMaxN);
-  if (d < 1 || (int64_t)N * d > kNoAllocMaxND)
-    return kf_set_err(nullptr, KF_EINVAL, "kf_tree_perm_noalloc: N * d = %lld exceeds %lld (or d < 1)",
-                      (long long)N * d, (long long)kNoAllocMaxND);
+  if (d < 1 || d > KF_MAX_D)
+    return kf_set_err(nullptr, KF_EINVAL, "kf_tree_perm_noalloc: d = %d outside [1, %d]", d, KF_MAX_D);
+  if ((int64_t)N * d > kNoAllocMaxND)
+    return kf_set_err(nullptr, KF_EINVAL, "kf_tree_perm_noalloc: N * d = %lld exceeds %lld", (long long)N * d,
+                      (long long)kNoAllocMaxND);
   if (m < 1) return kf_set_err(nullptr, KF_EINVAL, "kf_tree_perm_noalloc: m must be >= 1");
-  // device address of the scratch array, looked up once per device
-  static void* dev_ptr[64] = {nullptr};
+  // Device address of the scratch array, looked up once per device.  Each
+  // entry is atomic, so first calls from several host threads (on the same or
+  // different devices) at worst look the same address up twice.
+  static std::atomic<void*> dev_ptr[kNoAllocMaxDevices];
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0)
     return kf_set_err(nullptr, KF_ECUDA, "kf_tree_perm_noalloc: no current device");
-  if (!dev_ptr[dev]) {
+  if (dev >= kNoAllocMaxDevices)
+    return kf_set_err(nullptr, KF_EUNSUPPORTED, "kf_tree_perm_noalloc: device index %d, only devices 0..%d are "
+                      "supported", dev, kNoAllocMaxDevices - 1);
+  if (!dev_ptr[dev].load(std::memory_order_acquire)) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, kf_noalloc_tree_scratch);
     if (e != cudaSuccess)
       return kf_set_err(nullptr, KF_ECUDA, "kf_tree_perm_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-    dev_ptr[dev] = p;
+    dev_ptr[dev].store(p, std::memory_order_release);
   }
   int D = 0;
   while (((int64_t)m << D) < N) ++D;
@@ -393,7 +402,7 @@ extern "C" kf_status kf_tree_perm_noalloc(const double* X, int64_t N, int32_t d,
   const int maxnodes = D > 0 ? 1 << (D - 1) : 1;
   const int64_t part_cap = (N + kChunk - 1) / kChunk + 2 + 2 * (int64_t)maxnodes;
   // carve the scratch array
-  unsigned char* base = (unsigned char*)dev_ptr[dev];
+  unsigned char* base = (unsigned char*)dev_ptr[dev].load(std::memory_order_acquire);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     unsigned char* q = base + off;
@@ -413,18 +422,20 @@ extern "C" kf_status kf_tree_perm_noalloc(const double* X, int64_t N, int32_t d,
   if (off > kNoAllocBytes)
     return kf_set_err(nullptr, KF_EINVAL, "kf_tree_perm_noalloc: scratch of %zu bytes needed, %zu available", off,
                       kNoAllocBytes);
-  // inputs: copy X into the caller's output, check it, node ranges, identity order
-  if (cudaMemcpyAsync(Xt, X, sizeof(double) * N * d, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-      cudaMemsetAsync(bad, 0, sizeof(int32_t), s) != cudaSuccess)
+  // check X before any output is written (Xt and perm stay untouched when it
+  // holds a non-finite coordinate), then copy it, node ranges, identity order
+  if (cudaMemsetAsync(bad, 0, sizeof(int32_t), s) != cudaSuccess)
     return kf_set_err(nullptr, KF_ECUDA, "kf_tree_perm_noalloc: %s", cudaGetErrorString(cudaGetLastError()));
-  KF_PHASE(KF_PH_MISC, s, k_check_finite<<<grid_for(N * d, 256), 256, 0, s>>>(Xt, N * d, bad));
-  KF_PHASE(KF_PH_TREE, s, k_node_ranges<<<1, 1, 0, s>>>(N, D, lo, hi));
-  KF_PHASE(KF_PH_TREE, s, k_iota64<<<grid_for(N, 256), 256, 0, s>>>(perm, N));
+  KF_PHASE(KF_PH_MISC, s, k_check_finite<<<grid_for(N * d, 256), 256, 0, s>>>(X, N * d, bad));
   int32_t hbad = 0;
   if (cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return kf_set_err(nullptr, KF_ECUDA, "kf_tree_perm_noalloc: %s", cudaGetErrorString(cudaGetLastError()));
   if (hbad) return kf_set_err(nullptr, KF_EINVAL, "kf_tree_perm_noalloc: X has non-finite coordinates");
+  if (cudaMemcpyAsync(Xt, X, sizeof(double) * N * d, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return kf_set_err(nullptr, KF_ECUDA, "kf_tree_perm_noalloc: %s", cudaGetErrorString(cudaGetLastError()));
+  KF_PHASE(KF_PH_TREE, s, k_node_ranges<<<1, 1, 0, s>>>(N, D, lo, hi));
+  KF_PHASE(KF_PH_TREE, s, k_iota64<<<grid_for(N, 256), 256, 0, s>>>(perm, N));
   int32_t* ip = ia + maxnodes;
   int32_t* iq = ia + 2 * maxnodes;
   double* Xa = Xt;

@@ -94,3 +94,32 @@ def test_refinement_not_reaching_its_target_is_reported():
     G = kf.Factor(tree, 0.5, 1.0, 1e-6, 64, precision=kf.KF_PREC_MIXED, refine_tol=1e-10)
     x, info = G.solve(b, info=True)
     assert info["eps_r"] <= 1e-10
+
+
+def test_device_wait_that_runs_out_is_reported():
+    """KF_ETIMEOUT from a bounded device wait: with the probe on, every CTA of
+    the mixed path's tcgen05 products waits on an mbarrier that nothing
+    arrives at, gives up after a few polls, flags the time-out and returns
+    without its product.  The factor's status word reports KF_ETIMEOUT; with
+    the probe off the next factorization on the same context solves to the
+    usual accuracy."""
+    lib = _abi.load()
+    rng = np.random.default_rng(4)
+    X = torch.from_numpy(rng.random((4096, 8))).cuda()
+    b = torch.from_numpy(rng.standard_normal(4096)).cuda()
+    tree = kf.Tree(X, 256)
+    assert lib.kf_test_tc_wait_probe(-1) == _abi.KF_EINVAL
+    assert lib.kf_test_tc_wait_probe(64) == _abi.KF_OK
+    try:
+        F = kf.Factor(tree, 0.5, 1.0, 1e-6, 64, precision=kf.KF_PREC_MIXED, sync_errors=False, refine_max_iter=-1)
+        assert F.device_status() == _abi.KF_ETIMEOUT
+        del F
+    finally:
+        assert lib.kf_test_tc_wait_probe(0) == _abi.KF_OK
+    G = kf.Factor(tree, 0.5, 1.0, 1e-6, 64, precision=kf.KF_PREC_MIXED, refine_tol=1e-10)
+    assert G.device_status() == _abi.KF_OK
+    x, info = G.solve(b, info=True)
+    assert info["eps_r"] <= 1e-10
+    H = kf.Factor(tree, 0.5, 1.0, 1e-6, 64, precision=kf.KF_PREC_FP64)
+    xh = H.solve(b)
+    assert float(torch.linalg.norm(x - xh) / torch.linalg.norm(xh)) <= 1e-8

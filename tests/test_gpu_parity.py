@@ -498,6 +498,22 @@ def test_autograd_kernel_solve_matches_oracle_gradient():
     assert abs(ht.grad.item() - dho) <= 1e-8 * abs(dho)
 
 
+def test_autograd_kernel_solve_rejects_other_lambda_or_h():
+    """KernelSolve solves with the factorization's own lambda and h, so a
+    lambda or h that differs from them is an error rather than a stale solve
+    whose backward would report gradients at the values passed in."""
+    X, b = problem(1024, 3, seed=23)
+    tree = kf.Tree(torch.from_numpy(X).cuda(), 128)
+    F = kf.Factor(tree, 0.4, 0.9, 1e-7, 32, precision=FP64)
+    bt = torch.tensor(b, device="cuda", requires_grad=True)
+    f64 = dict(device="cuda", dtype=torch.float64)
+    x = kf.KernelSolve.apply(bt, torch.tensor(0.9, **f64), torch.tensor(0.4, **f64), F)
+    assert x.shape == bt.shape
+    for lam, h in ((0.91, 0.4), (0.9, 0.41)):
+        with pytest.raises(ValueError):
+            kf.KernelSolve.apply(bt, torch.tensor(lam, **f64), torch.tensor(h, **f64), F)
+
+
 # ---------------------------------------------------------------- profiler
 def test_profile_totals_and_timeline(c1):
     """kf_profile_read totals and kf_profile_timeline records of one
