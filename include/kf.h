@@ -105,7 +105,17 @@ typedef struct {
                              level's LU at 2 z^3 FP64 flops a node: 0 = default (64; none in
                              kf_factorize_batched, whose concurrent problems hide that latency),
                              -1 = none */
-  int32_t reserved[2];
+  int32_t hybrid_level;   /* 0 = the direct solver (Algorithm 2 up to the root).  L >= 1: the hybrid
+                             level-restricted solver of Sec. II-C (Algorithms 6-8) with its frontier
+                             at level L (1 <= L <= depth): the subtrees of the 2^L nodes of level L
+                             are skeletonized and factorized (the frontier nodes' own IDs included),
+                             nothing above them is compressed, and the reduced system I + VW of the
+                             frontier skeletons, (VW)[a~, b~] = K_{a~ b} P^_b for frontier nodes
+                             a != b, is formed in FP64 and LU-factored (2^L s_max <= 1024, else
+                             KF_EUNSUPPORTED).  kf_solve (transpose = 0) and kf_matvec then apply
+                             (D + UV)^-1 and D + UV, D = blockdiag(lambda I + K~_aa); transpose
+                             solves and kf_grad return KF_EUNSUPPORTED.  kf_factorize only. */
+  int32_t reserved[1];
 } kf_opts;
 
 /* Filled by kf_solve when non-NULL (synchronizes the stream). */
@@ -196,9 +206,18 @@ kf_status kf_grad(kf_factor* f, const void* x, const void* dLdx, void* dLdb, dou
  * cudaMallocAsync even when the context has an allocator. */
 kf_status kf_factorize_batched(kf_tree* const* trees, int32_t nprob, const double* h, const double* lambda,
                                const double* tau, int32_t s_max, const kf_opts* opts, void* stream, kf_factor** out);
-/* X_i = (lambda_i I + K~_i)^-1 B_i for nprob factors with one CUDA-graph launch
- * (Algorithm 3 per problem, no refinement).  B, X: host arrays of DEVICE
- * pointers; nrhs, ld: host arrays.  Synchronizes `stream`. */
+/* X_i = (lambda_i I + K~_i)^-1 B_i for nprob factors: the direct sweeps of
+ * every problem in one CUDA-graph launch (Algorithm 3 per problem).  When the
+ * factors refine (the mixed path by default, see kf_solve), the batch is then
+ * refined as a whole: each step is one graph launch for the residuals
+ * b - (lambda I + K~) x of every unconverged problem (FP64-accurate operator)
+ * and one for x += M^-1 r, with one host synchronization per step to read the
+ * residual norms; a problem leaves the batch once its relative residual
+ * (Eq. e:errors, max over its columns) is at most its refine_tol, and a problem
+ * whose residual falls by less than half in a step finishes with GMRES(m) per
+ * column, as kf_solve does.  B, X: host arrays of DEVICE pointers; nrhs, ld:
+ * host arrays.  Synchronizes `stream`.  KF_ENOTCONV when a problem ends above
+ * its refine_tol (X is written all the same). */
 kf_status kf_solve_batched(kf_factor* const* f, int32_t nprob, const void* const* B, void* const* X,
                            const int64_t* nrhs, const int64_t* ld, int32_t dtype, void* stream);
 
@@ -300,8 +319,9 @@ kf_status kf_profile_enable(int32_t on);
  * levels), matvec_colsum and matvec_rowupd (the V-block passes of kf_matvec
  * and of the refinement's operator; solve_colsum and solve_rowupd are those of
  * the solve sweep), z_inv (the explicit Z^-1 of the upper levels, see
- * kf_opts.zinv_max_nodes). */
-#define KF_PHASE_COUNT 24
+ * kf_opts.zinv_max_nodes), hybrid (the reduced system of the hybrid solver:
+ * its coupling blocks, LU and products, kf_opts.hybrid_level). */
+#define KF_PHASE_COUNT 25
 kf_status kf_profile_read(double* ms, int64_t* launches, int32_t nphase);
 /* Per-launch timeline of the launches recorded since the last kf_profile_read
  * (which it leaves in place): for launch q < *n, its start and end in ms

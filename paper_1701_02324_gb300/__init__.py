@@ -172,8 +172,9 @@ class Tree:
 
 def _opts(precision=KF_PREC_FP64, n_samp=0, seed=0, v_storage=KF_V_STORED, sync_errors=0, refine_tol=0.0,
           refine_max_iter=0, tensor_cores=True, fp64_operator=None, gmres_restart=0, cluster_kernels=True,
-          tc_tile_n=0, zinv_max_nodes=0):
+          tc_tile_n=0, zinv_max_nodes=0, hybrid_level=0):
     o = kf_opts()
+    o.hybrid_level = int(hybrid_level)
     o.zinv_max_nodes = int(zinv_max_nodes)
     o.no_cluster_kernels = 0 if cluster_kernels else 1
     o.tc_tile_n = int(tc_tile_n)
@@ -193,11 +194,15 @@ class Factor:
                  n_samp: int = 0, seed: int = 0, v_storage=KF_V_STORED, refine_tol: float = 0.0,
                  refine_max_iter: int = 0, sync_errors: bool = True, tensor_cores: bool = True,
                  fp64_operator=None, gmres_restart: int = 0, cluster_kernels: bool = True, tc_tile_n: int = 0,
-                 zinv_max_nodes: int = 0, _ids=None):
+                 zinv_max_nodes: int = 0, hybrid_level: int = 0, _ids=None):
+        """hybrid_level = L >= 1: the hybrid level-restricted solver of
+        Sec. II-C (Algorithms 6-8) with its frontier at tree level L; 0: the
+        direct solver (Algorithms 2-3)."""
         self.tree, self.ctx = tree, tree.ctx
         self.h_, self.lam, self.tau, self.s_max, self.precision = float(h), float(lam), float(tau), int(s_max), precision
+        self.hybrid_level = int(hybrid_level)
         o = _opts(precision, n_samp, seed, v_storage, int(sync_errors), refine_tol, refine_max_iter, tensor_cores,
-                  fp64_operator, gmres_restart, cluster_kernels, tc_tile_n, zinv_max_nodes)
+                  fp64_operator, gmres_restart, cluster_kernels, tc_tile_n, zinv_max_nodes, hybrid_level)
         h_out = ctypes.c_void_p()
         if _ids is None:
             st = self.ctx.lib.kf_factorize(tree.h, self.h_, self.lam, self.tau, self.s_max, ctypes.byref(o),
@@ -357,18 +362,21 @@ def autotune(tree: Tree, h: float, lam: float, tau: float, s_max: int, precision
 
 
 def factorize_batched(trees, hs, lams, taus, s_max: int, precision=KF_PREC_MIXED, n_samp: int = 0, seed: int = 0,
-                      **kw):
+                      refine_tol: float = 0.0, refine_max_iter: int = 0, **kw):
     """Factorize many independent problems with one CUDA-graph launch
-    (kf_factorize_batched).  Returns a list of Factor objects."""
+    (kf_factorize_batched).  Returns a list of Factor objects.  Their solves
+    (solve_batched) are refined like kf_solve's: by default on the mixed path
+    (refine_max_iter = 0), never with refine_max_iter = -1."""
     import numpy as np
     n = len(trees)
     ctx = trees[0].ctx
     h = np.ascontiguousarray(hs, dtype=np.float64)
     lam = np.ascontiguousarray(lams, dtype=np.float64)
     tau = np.ascontiguousarray(taus, dtype=np.float64)
-    o = _opts(precision, n_samp, seed, KF_V_STORED, 0, 0.0, -1, tensor_cores=kw.get("tensor_cores", True),
-              cluster_kernels=kw.get("cluster_kernels", True), tc_tile_n=kw.get("tc_tile_n", 0),
-              zinv_max_nodes=kw.get("zinv_max_nodes", 0))
+    o = _opts(precision, n_samp, seed, KF_V_STORED, 0, refine_tol, refine_max_iter,
+              tensor_cores=kw.get("tensor_cores", True), fp64_operator=kw.get("fp64_operator"),
+              gmres_restart=kw.get("gmres_restart", 0), cluster_kernels=kw.get("cluster_kernels", True),
+              tc_tile_n=kw.get("tc_tile_n", 0), zinv_max_nodes=kw.get("zinv_max_nodes", 0))
     out = (ctypes.c_void_p * n)()
     tarr = _ptr_array([t.h.value for t in trees])
     st = ctx.lib.kf_factorize_batched(tarr, n, h.ctypes.data_as(ctypes.c_void_p), lam.ctypes.data_as(ctypes.c_void_p),

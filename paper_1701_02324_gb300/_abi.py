@@ -35,7 +35,8 @@ class kf_opts(ctypes.Structure):
         ("no_cluster_kernels", ctypes.c_int32),
         ("tc_tile_n", ctypes.c_int32),
         ("zinv_max_nodes", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("hybrid_level", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 1),
     ]
 
 
@@ -77,7 +78,7 @@ SIGNATURES = {
 
 PHASES = ["tree", "sample", "eval_A", "qr", "leaf_assemble", "leaf_cholesky", "leaf_phat", "eval_V", "zoff", "z_lu",
           "z_solve_pc", "telescope", "solve_leaf", "solve_colsum", "solve_zsolve", "solve_rowupd", "matvec_leaf",
-          "matvec_push", "misc", "qr_cluster", "qr_leaf", "matvec_colsum", "matvec_rowupd", "z_inv"]
+          "matvec_push", "misc", "qr_cluster", "qr_leaf", "matvec_colsum", "matvec_rowupd", "z_inv", "hybrid"]
 
 _lock = threading.Lock()
 _lib = None

@@ -1377,13 +1377,16 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
     if (st == KF_OK) st = kf_factorize_leaves(f, s4, false, 1);
     cudaEventRecord(evl, s4);
     cudaStreamWaitEvent(s2, evl, 0);
-    for (int l = D; l >= 1 && st == KF_OK; --l) {
+    // the hybrid solver (frontier level Lh >= 1) skeletonizes and factorizes
+    // the levels from the leaves up to its frontier only
+    const int Lh = f->hyb_L;
+    for (int l = D; l >= std::max(1, Lh) && st == KF_OK; --l) {
       st = kf_skel_level(f, l, &sc, s1);
       cudaEventRecord(ev[l], s1);
       if (st != KF_OK) break;
       // V blocks of level l - 1 (rows of level l) need the skeletons of level l
       cudaStreamWaitEvent(s3, ev[l], 0);
-      st = kf_factorize_level_v(f, l - 1, s3);
+      if (l - 1 >= Lh) st = kf_factorize_level_v(f, l - 1, s3);
       cudaEventRecord(evv[l - 1], s3);
       if (st != KF_OK) break;
       cudaStreamWaitEvent(s2, ev[l], 0);
@@ -1399,7 +1402,7 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
         }
       }
     }
-    if (st == KF_OK) {
+    if (st == KF_OK && Lh == 0) {
       cudaStreamWaitEvent(s2, evv[0], 0);
       st = kf_factorize_level_z(f, 0, Tm, s2);
       if (st == KF_OK) {
@@ -1408,6 +1411,9 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
         st = kf_z_inverse_level(f, 0, s5);
       }
     }
+    // hybrid: the reduced system I + VW of the frontier (needs the frontier
+    // skeletons and P^ of level Lh, both ordered before this point on s2)
+    if (st == KF_OK && Lh > 0) st = kf_hybrid_reduced_system(f, s2);
     // the FP64 operator's leaf blocks need the tree only, and only the solve
     // reads them: last on the V-block stream, where they fill the SMs that the
     // latency-bound upper levels leave idle (ahead of the V blocks they held
@@ -1438,4 +1444,15 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
   if (s4) cudaStreamDestroy(s4);
   if (evl) cudaEventDestroy(evl);
   return st;
+}
+
+// LU of one reduced system stored as node 1 of a two-node array (row stride
+// ldz <= 2 KF_MAX_SMAX): the hybrid solver's I + VW, whose rank array gives
+// node 1 a first child of rank S and a second of rank 0.
+kf_status kf_z_factor_one_launch(const int32_t* rank, int ldz, double* Z, int32_t* piv, int32_t* status,
+                                 double* pivr, cudaStream_t s) {
+  if (ldz < 1 || ldz > 2 * KF_MAX_SMAX) return KF_EINVAL;
+  KF_PHASE(KF_PH_HYBRID, s, k_z_factor<<<1, 256, 0, s>>>(rank, 1, ldz, 1, Z, piv, nullptr, nullptr, nullptr, 0, status,
+                                                         pivr));
+  return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
 }

@@ -255,6 +255,7 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
     if (opts->gmres_restart != 0) f->gmres_m = opts->gmres_restart > 0 ? std::min(opts->gmres_restart, 64) : 0;
     if (opts->no_cluster_kernels) f->use_cluster_qr = f->use_cluster_lu = 0;
     if (opts->zinv_max_nodes != 0) f->zinv_max_nodes = opts->zinv_max_nodes > 0 ? opts->zinv_max_nodes : -1;
+    f->hyb_L = opts->hybrid_level;
     if (opts->tc_tile_n == 128) f->tc_bn = 128;
     else if (opts->tc_tile_n != 0 && opts->tc_tile_n != 256) {
       delete f;
@@ -272,6 +273,17 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
   if (f->n_samp > 1024) {
     delete f;
     return kf_set_err(c, KF_EINVAL, "n_samp must be <= 1024");
+  }
+  if (f->hyb_L < 0 || f->hyb_L > t->D) {
+    const int Lbad = f->hyb_L;
+    delete f;
+    return kf_set_err(c, KF_EINVAL, "hybrid_level %d outside [0, %d] (the tree depth)", Lbad, t->D);
+  }
+  if (f->hyb_L > 0 && ((int64_t)s_max << f->hyb_L) > 2 * KF_MAX_SMAX) {
+    const int Lbad = f->hyb_L;
+    delete f;
+    return kf_set_err(c, KF_EUNSUPPORTED, "hybrid reduced system of up to 2^%d * s_max = %lld rows; at most %d "
+                      "are supported", Lbad, (long long)s_max << Lbad, 2 * KF_MAX_SMAX);
   }
   const int64_t N = t->N;
   const int D = t->D;
@@ -302,6 +314,21 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
     if (!f->Kdf || (D > 0 && f->prec != KF_PREC_FP64 && !f->VTdf)) {
       kf_factor_free(f);
       return kf_set_err(c, KF_ENOMEM, "factorize: device allocation of the FP64 operator failed");
+    }
+  }
+  if (f->hyb_L > 0) {
+    const int nA = 1 << f->hyb_L;
+    f->hyb_scap = s_max << f->hyb_L;
+    const size_t sc = (size_t)f->hyb_scap;
+    f->Vh = falloc<double>(f, (size_t)nA * s_max * N, s);
+    f->HM = falloc<double>(f, 2 * sc * sc, s);
+    f->Hpiv = falloc<int32_t>(f, 2 * sc, s);
+    f->Hrank = falloc<int32_t>(f, 4, s);
+    f->Hoff = falloc<int32_t>(f, (size_t)nA + 1, s);
+    f->Hpivr = falloc<double>(f, 2, s);
+    if (!f->Vh || !f->HM || !f->Hpiv || !f->Hrank || !f->Hoff || !f->Hpivr) {
+      kf_factor_free(f);
+      return kf_set_err(c, KF_ENOMEM, "factorize: device allocation of the hybrid reduced system failed");
     }
   }
   bool ok = f->rank && f->skel && f->status && f->pivr && f->Pleaf && f->L &&
@@ -514,6 +541,7 @@ kf_status kf_autotune(kf_tree* t, double h, double lambda, double tau, int32_t s
   kf_ctx* c = t->ctx;
   kf_opts b0 = {};
   if (base) b0 = *base;
+  if (b0.hybrid_level != 0) return kf_set_err(c, KF_EUNSUPPORTED, "kf_autotune: the direct solver only");
   b0.sync_errors = 0;
   std::vector<kf_opts> cand;
   for (int cl = 0; cl < 2; ++cl) {
@@ -572,6 +600,8 @@ kf_status kf_factorize_with_ids(kf_tree* t, double h, double lambda, int32_t s_m
                                 kf_factor** out) {
   if (!t || !out || !ranks || !skel || !P) return KF_EINVAL;
   *out = nullptr;
+  if (opts && opts->hybrid_level != 0)
+    return kf_set_err(t->ctx, KF_EUNSUPPORTED, "kf_factorize_with_ids: the hybrid solver is kf_factorize only");
   cudaStream_t s = (cudaStream_t)stream;
   kf_factor* f = nullptr;
   kf_status st = alloc_factor(t, h, lambda, 0.0, s_max, opts, s, &f);
@@ -937,6 +967,7 @@ kf_status kf_grad(kf_factor* f, const void* x, const void* dLdx, void* dLdb, dou
   kf_status st = check_rhs(f, x, dLdx, nrhs, ld, KF_F64);
   if (st != KF_OK) return st;
   if (!dLdb || !dLdlambda || !dLdh) return kf_set_err(f->ctx, KF_EINVAL, "NULL gradient output");
+  if (f->hyb_L > 0) return kf_set_err(f->ctx, KF_EUNSUPPORTED, "kf_grad: not available for the hybrid solver");
   cudaStream_t s = (cudaStream_t)stream;
   kf_ctx* c = f->ctx;
   const int64_t N = f->t->N;
@@ -1110,6 +1141,155 @@ kf_status run_batched_graph(kf_ctx* c, int32_t nprob, cudaStream_t s, Enq enq) {
   return st;
 }
 
+// Many problems solved and refined together: the direct sweeps of all
+// problems in one graph launch, then refinement steps x += M^-1 (b - A x) for
+// the whole batch, each step two graph launches (the residuals of every
+// unconverged problem against its operator, then the sweeps of those
+// residuals), with one host synchronization per step to read the residual
+// norms.  A problem leaves the batch once its relative residual (Eq. e:errors,
+// max over its columns) is at most its refine_tol; a problem whose residual
+// falls by less than half in a step (or that reaches refine_max_iter steps)
+// finishes column by column with GMRES(m) from where it stands, like kf_solve.
+// Problems whose factors do not refine get the direct sweep only.
+kf_status solve_batched_refined(kf_factor* const* f, int32_t nprob, const void* const* B, void* const* X,
+                                const int64_t* nrhs, const int64_t* ld, int32_t dtype, cudaStream_t s) {
+  kf_ctx* c = f[0]->ctx;
+  struct Prob {
+    double *Bt = nullptr, *Wt = nullptr, *R = nullptr, *Y = nullptr;
+    size_t vb = 0;
+    double eps = INFINITY;
+    int steps = 0;
+    int state = 0;  // 0 refining, 1 converged, 2 to GMRES, 3 direct only
+    std::vector<double> bn2;  // squared column norms of b
+  };
+  std::vector<Prob> P(nprob);
+  int64_t ktot = 0;
+  std::vector<int64_t> koff(nprob + 1, 0);
+  for (int32_t i = 0; i < nprob; ++i) koff[i + 1] = koff[i] + nrhs[i];
+  ktot = koff[nprob];
+  double* nrm = (double*)c->dalloc(sizeof(double) * 2 * ktot, s);
+  kf_status st = nrm ? KF_OK : kf_set_err(c, KF_ENOMEM, "batched solve: allocation failed");
+  for (int32_t i = 0; i < nprob && st == KF_OK; ++i) {
+    Prob& q = P[i];
+    q.vb = sizeof(double) * (size_t)f[i]->t->N * nrhs[i];
+    q.Bt = (double*)c->dalloc(q.vb, s);
+    q.Wt = (double*)c->dalloc(q.vb, s);
+    q.R = (double*)c->dalloc(q.vb, s);
+    q.Y = (double*)c->dalloc(q.vb, s);
+    if (!q.Bt || !q.Wt || !q.R || !q.Y) st = kf_set_err(c, KF_ENOMEM, "batched solve: allocation failed");
+    q.state = refines(f[i]) ? 0 : 3;
+  }
+  std::vector<int32_t> act;
+  auto run_on = [&](const std::vector<int32_t>& ids, auto enq) -> kf_status {
+    if (ids.empty()) return KF_OK;
+    return run_batched_graph(c, (int32_t)ids.size(), s,
+                             [&](int32_t j, cudaStream_t si) -> kf_status { return enq(ids[j], si); });
+  };
+  std::vector<int32_t> all(nprob);
+  for (int32_t i = 0; i < nprob; ++i) all[i] = i;
+  // b in tree order, x = M^-1 b
+  if (st == KF_OK)
+    st = run_on(all, [&](int32_t i, cudaStream_t si) -> kf_status {
+      const int64_t N = f[i]->t->N, k = nrhs[i];
+      KF_PHASE(KF_PH_MISC, si, k_gather_in<<<grid_for(N * k, 256), 256, 0, si>>>(B[i], dtype, ld[i], f[i]->t->perm,
+                                                                                  N, k, P[i].Bt));
+      KF_CUDA(c, cudaMemcpyAsync(P[i].Wt, P[i].Bt, P[i].vb, cudaMemcpyDeviceToDevice, si));
+      return kf_solve_device(f[i], P[i].Wt, k, 0, si);
+    });
+  for (int32_t i = 0; i < nprob; ++i)
+    if (P[i].state == 0) act.push_back(i);
+  std::vector<double> hn(2 * ktot);
+  while (st == KF_OK && !act.empty()) {
+    // r = b - A x and the column norms of r and b
+    KF_CUDA(c, cudaMemsetAsync(nrm, 0, sizeof(double) * 2 * ktot, s));
+    KF_CUDA(c, cudaStreamSynchronize(s));
+    st = run_on(act, [&](int32_t i, cudaStream_t si) -> kf_status {
+      const int64_t N = f[i]->t->N, k = nrhs[i];
+      kf_status r = apply_op(f[i], P[i].Wt, P[i].Y, k, 0, si);
+      if (r != KF_OK) return r;
+      KF_PHASE(KF_PH_MISC, si, k_sub<<<grid_for(N * k, 256), 256, 0, si>>>(P[i].Bt, P[i].Y, P[i].R, N * k));
+      KF_PHASE(KF_PH_MISC, si, k_colnorm2<<<grid_for(N, 256, 304), 256, 0, si>>>(P[i].R, N, k, nrm + 2 * koff[i]));
+      KF_PHASE(KF_PH_MISC, si, k_colnorm2<<<grid_for(N, 256, 304), 256, 0, si>>>(P[i].Bt, N, k,
+                                                                                 nrm + 2 * koff[i] + k));
+      return KF_OK;
+    });
+    if (st != KF_OK) break;
+    KF_CUDA(c, cudaMemcpy(hn.data(), nrm, sizeof(double) * 2 * ktot, cudaMemcpyDeviceToHost));
+    std::vector<int32_t> next;
+    for (int32_t i : act) {
+      const int64_t k = nrhs[i];
+      double e = 0.0;
+      for (int64_t j = 0; j < k; ++j) {
+        const double rr = hn[2 * koff[i] + j], bb = hn[2 * koff[i] + k + j];
+        e = std::max(e, bb > 0 ? sqrt(rr / bb) : sqrt(rr));
+      }
+      Prob& q = P[i];
+      q.bn2.assign(hn.begin() + 2 * koff[i] + k, hn.begin() + 2 * koff[i] + 2 * k);
+      const double prev = q.eps;
+      q.eps = e;
+      if (e <= f[i]->refine_tol) q.state = 1;
+      else if (q.steps >= f[i]->refine_max_iter || !(e <= 0.5 * prev)) q.state = 2;
+      else next.push_back(i);
+    }
+    act.swap(next);
+    if (act.empty()) break;
+    // x += M^-1 r
+    st = run_on(act, [&](int32_t i, cudaStream_t si) -> kf_status {
+      const int64_t N = f[i]->t->N, k = nrhs[i];
+      kf_status r = kf_solve_device(f[i], P[i].R, k, 0, si);
+      if (r != KF_OK) return r;
+      KF_PHASE(KF_PH_MISC, si, k_add<<<grid_for(N * k, 256), 256, 0, si>>>(P[i].Wt, P[i].R, N * k));
+      ++P[i].steps;
+      return KF_OK;
+    });
+  }
+  // the problems the steps did not settle: GMRES(m) per column from the current x
+  kf_status worst = KF_OK;
+  for (int32_t i = 0; i < nprob && st == KF_OK; ++i) {
+    if (P[i].state != 2) continue;
+    kf_factor* fi = f[i];
+    const int64_t N = fi->t->N, k = nrhs[i];
+    const size_t cb = sizeof(double) * N;
+    double* bcol = (double*)c->dalloc(cb, s);
+    double* xcol = (double*)c->dalloc(cb, s);
+    if (!bcol || !xcol) st = kf_set_err(c, KF_ENOMEM, "batched solve: allocation failed");
+    double pe = 0.0;
+    for (int64_t col = 0; col < k && st == KF_OK; ++col) {
+      KF_PHASE(KF_PH_MISC, s, k_get_col<<<grid_for(N, 256), 256, 0, s>>>(P[i].Bt, k, col, bcol, N));
+      KF_PHASE(KF_PH_MISC, s, k_get_col<<<grid_for(N, 256), 256, 0, s>>>(P[i].Wt, k, col, xcol, N));
+      const double bn = sqrt(P[i].bn2[col]);
+      double e = 0.0;
+      int its = 0;
+      st = gmres_column(fi, bcol, xcol, bn, fi->gmres_m > 0 ? fi->gmres_m : 50, fi->refine_max_iter, fi->refine_tol, 0,
+                        s, &e, &its);
+      pe = std::max(pe, e);
+      KF_PHASE(KF_PH_MISC, s, k_put_col<<<grid_for(N, 256), 256, 0, s>>>(xcol, k, col, P[i].Wt, N));
+    }
+    if (bcol) c->dfree(bcol, cb, s);
+    if (xcol) c->dfree(xcol, cb, s);
+    P[i].eps = pe;
+    if (st == KF_OK && pe > fi->refine_tol && worst == KF_OK)
+      worst = kf_set_err(c, KF_ENOTCONV, "batched solve: problem %d stopped at eps_r = %.3e", i, pe);
+  }
+  // x back to the caller's order and type
+  if (st == KF_OK)
+    st = run_on(all, [&](int32_t i, cudaStream_t si) -> kf_status {
+      const int64_t N = f[i]->t->N, k = nrhs[i];
+      KF_PHASE(KF_PH_MISC, si, k_scatter_out<<<grid_for(N * k, 256), 256, 0, si>>>(P[i].Wt, f[i]->t->perm, N, k, X[i],
+                                                                                   dtype, ld[i]));
+      return KF_OK;
+    });
+  if (st == KF_OK) KF_CUDA(c, cudaStreamSynchronize(s));
+  for (auto& q : P) {
+    if (q.Bt) c->dfree(q.Bt, q.vb, s);
+    if (q.Wt) c->dfree(q.Wt, q.vb, s);
+    if (q.R) c->dfree(q.R, q.vb, s);
+    if (q.Y) c->dfree(q.Y, q.vb, s);
+  }
+  if (nrm) c->dfree(nrm, sizeof(double) * 2 * ktot, s);
+  return st == KF_OK ? worst : st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1123,6 +1303,8 @@ kf_status kf_factorize_batched(kf_tree* const* trees, int32_t nprob, const doubl
     if (trees[i]->ctx != trees[0]->ctx) return kf_set_err(nullptr, KF_EINVAL, "batched: trees of different contexts");
   }
   kf_ctx* c = trees[0]->ctx;
+  if (opts && opts->hybrid_level != 0)
+    return kf_set_err(c, KF_EUNSUPPORTED, "batched: the hybrid solver is kf_factorize only");
   cudaStream_t s = (cudaStream_t)stream;
   // the batch's concurrent graph branches hide the latency of the per-node LU
   // solves, so by default no Z^-1 is formed here (measured on 256 problems of
@@ -1165,6 +1347,9 @@ kf_status kf_solve_batched(kf_factor* const* f, int32_t nprob, const void* const
       return kf_set_err(f[i]->ctx, KF_EINVAL, "batched solve: B and X must be device pointers");
   }
   kf_ctx* c = f[0]->ctx;
+  bool any_refined = false;
+  for (int32_t i = 0; i < nprob; ++i) any_refined = any_refined || refines(f[i]);
+  if (any_refined) return solve_batched_refined(f, nprob, B, X, nrhs, ld, dtype, (cudaStream_t)stream);
   return run_batched_graph(c, nprob, (cudaStream_t)stream, [&](int32_t i, cudaStream_t si) -> kf_status {
     return with_vectors(f[i], B[i], X[i], nrhs[i], ld[i], dtype, si,
                         [&](double* W) { return kf_solve_device(f[i], W, nrhs[i], 0, si); });

@@ -91,6 +91,22 @@ struct kf_factor {
   double* Zinv = nullptr;
   int32_t zinv_top = -1;
   int32_t zinv_max_nodes = kZinvDefaultMaxNodes;  // -1: none
+  // hybrid level-restricted solver (Sec. II-C): frontier level hyb_L >= 1, or
+  // 0 for the direct solver.  Vh: per frontier node a, s_max rows of N FP64
+  // entries K(x_{a~q}, x_j) (zero for j in a and for q >= s_a).  The reduced
+  // system I + VW is stored as node 1 of a two-node Z array (HM: 2 hyb_scap^2,
+  // node 1 at offset hyb_scap^2; Hpiv: 2 hyb_scap), with Hrank = {0, 0, S, 0}
+  // so that the reduced-system LU and solve kernels see one node whose first
+  // child has rank S = sum of the frontier ranks; Hoff: prefix sums of the
+  // frontier ranks (2^L + 1 entries).
+  int32_t hyb_L = 0;
+  int32_t hyb_scap = 0;
+  double* Vh = nullptr;
+  double* HM = nullptr;
+  int32_t* Hpiv = nullptr;
+  int32_t* Hrank = nullptr;
+  int32_t* Hoff = nullptr;
+  double* Hpivr = nullptr;
   int32_t* status = nullptr;
   double* pivr = nullptr;  // per node: smallest / largest pivot of its leaf Cholesky or Z LU
   std::vector<std::pair<void*, size_t>> allocs;
@@ -307,3 +323,22 @@ kf_status kf_z_inverse_level(kf_factor* f, int l, cudaStream_t s);
 // y = (lambda I + K~)^T x (tree order, N x nrhs FP64), with the same operator
 // data as kf_matvec_device (FP64-accurate on the mixed path when it is stored).
 kf_status kf_matvec_transpose_device(kf_factor* f, const double* Xin, double* Y, int64_t nrhs, cudaStream_t s);
+
+// ---- hybrid level-restricted solver (hybrid.cu) ------------------------------------
+// After the frontier subtrees are factorized: offsets of the frontier ranks,
+// the coupling rows Vh, the reduced system I + VW and its LU (stream order).
+kf_status kf_hybrid_reduced_system(kf_factor* f, cudaStream_t s);
+// W (tree order, N x k FP64, point-major) <- W - W_L (I + VW)^-1 V W: the
+// top of Algorithm 6, applied after the frontier subtrees' direct solves.
+kf_status kf_hybrid_top_solve(kf_factor* f, double* W, int64_t k, cudaStream_t s);
+// G (per node, (node * s_max + q) * k + c) of the frontier nodes <- V x: the
+// coupling between frontier subtrees in the operator D + UV (Algorithm 8).
+kf_status kf_hybrid_top_apply(kf_factor* f, const double* x, double* G, int64_t k, cudaStream_t s);
+// launchers of kernels that live with the direct solver's reduced systems
+// (factor.cu, solve.cu), for the one synthetic node of the hybrid system
+kf_status kf_z_factor_one_launch(const int32_t* rank, int ldz, double* Z, int32_t* piv, int32_t* status,
+                                 double* pivr, cudaStream_t s);
+kf_status kf_zsolve_one_launch(const int32_t* rank, int ldz, const double* ZLU, const int32_t* piv, const double* in,
+                               double* out, int k, cudaStream_t s);
+// W -= rows of P^ (level l, type of the factor) times the per-node vector V
+kf_status kf_rowupd_level_launch(kf_factor* f, int l, const double* V, double* W, int64_t k, cudaStream_t s);

@@ -33,6 +33,7 @@ enum kf_phase {
   KF_PH_MV_COLSUM,
   KF_PH_MV_ROWUPD,
   KF_PH_ZINV,
+  KF_PH_HYBRID,
   KF_PH_COUNT
 };
 

@@ -900,7 +900,9 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
   };
   if (!transpose) {
     KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve<TM, TV><<<1 << D, kLeafSolveThreads, ls_smem, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
-    for (int l = D - 1; l >= 0; --l) {
+    // the hybrid solver stops at its frontier level (the reduced system above
+    // it is applied by kf_hybrid_top_solve); the direct solver goes to the root
+    for (int l = D - 1; l >= f->hyb_L; --l) {
       const int c0 = 1 << (l + 1), nc = 1 << (l + 1);
       const int64_t rows = (N >> (l + 1)) + 1;
       KF_CUDA(c, cudaMemsetAsync(U, 0, ubytes, s));
@@ -982,7 +984,9 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
     KF_LAUNCH_CHECK(c);
     return KF_OK;
   }
-  for (int l = 1; l <= D; ++l) {
+  // sibling couplings inside the frontier subtrees of the hybrid solver
+  // (levels below its frontier), or at every level of the direct solver
+  for (int l = f->hyb_L + 1; l <= D; ++l) {
     const int64_t rows = (N >> l) + 1;
     dim3 gc((unsigned)((rows + kRowsPerChunk - 1) / kRowsPerChunk), 1 << l);
     if (f->VTdf && !deriv) {  // FP64-accurate operator of the mixed path
@@ -997,8 +1001,14 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
       launch_colsum<TM, double>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, s_max, 1, src, vt_level(l),
                                 t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G, KF_PH_MV_COLSUM);
   }
+  // the hybrid solver's frontier nodes couple with every other frontier node
+  // (V of Algorithm 8), pushed down from the frontier like a sibling coupling
+  if (f->hyb_L > 0) {
+    kf_status hs = kf_hybrid_top_apply(f, x, G, k, s);
+    if (hs != KF_OK) return hs;
+  }
   const dim3 gpd(1, (unsigned)((2 * s_max + 31) / 32));
-  for (int l = 1; l < D; ++l)
+  for (int l = std::max(1, f->hyb_L); l < D; ++l)
     KF_PHASE(KF_PH_MV_PUSH, s, k_push_down<<<dim3(1u << l, gpd.y), 256, 0, s>>>(f->rank, 1 << l, s_max, f->Pc, G,
                                                                                 (int)k));
   const int64_t rows = (N >> D) + 1;
@@ -1024,6 +1034,11 @@ kf_status kf_solve_device(kf_factor* f, double* W, int64_t k, int transpose, cud
     return kf_set_err(c, KF_ENOMEM, "solve: allocation failed");
   }
   kf_status st;
+  if (f->hyb_L > 0 && transpose) {
+    c->dfree(U, ub, s);
+    c->dfree(Vb, ub, s);
+    return kf_set_err(c, KF_EUNSUPPORTED, "transpose solves of the hybrid solver are not supported");
+  }
   if (f->prec == KF_PREC_FP64) {
     st = solve_t<double, double>(f, W, k, transpose, U, Vb, s);
   } else {
@@ -1039,12 +1054,16 @@ kf_status kf_solve_device(kf_factor* f, double* W, int64_t k, int transpose, cud
   }
   c->dfree(U, ub, s);
   c->dfree(Vb, ub, s);
+  // Algorithm 6 above the frontier: w = D^-1 u - W (I + V W)^-1 V D^-1 u
+  if (st == KF_OK && f->hyb_L > 0) st = kf_hybrid_top_solve(f, W, k, s);
   return st;
 }
 
 static kf_status matvec_any(kf_factor* f, const double* x, double* y, int64_t k, int deriv, int transpose,
                             cudaStream_t s) {
   kf_ctx* c = f->ctx;
+  if (f->hyb_L > 0 && (deriv || transpose))
+    return kf_set_err(c, KF_EUNSUPPORTED, "the hybrid solver's operator has no transpose or h-derivative here");
   const size_t gb = sizeof(double) * (size_t)(f->t->nnodes + 1) * f->s_max * k;
   double* G = (double*)c->dalloc(gb, s);
   if (!G) return kf_set_err(c, KF_ENOMEM, "matvec: allocation failed");
@@ -1063,4 +1082,35 @@ kf_status kf_matvec_device(kf_factor* f, const double* x, double* y, int64_t k, 
 
 kf_status kf_matvec_transpose_device(kf_factor* f, const double* x, double* y, int64_t k, cudaStream_t s) {
   return matvec_any(f, x, y, k, 0, 1, s);
+}
+
+// Solve with one reduced system stored as node 1 of a two-node array (see
+// kf_z_factor_one_launch): in/out hold its S entries contiguously at
+// (2 ldz + i) * k + c, the layout k_zsolve reads for a node whose first
+// child has rank S at a row stride of ldz.
+kf_status kf_zsolve_one_launch(const int32_t* rank, int ldz, const double* ZLU, const int32_t* piv, const double* in,
+                               double* out, int k, cudaStream_t s) {
+  if (ldz < 1 || ldz > 2 * KF_MAX_SMAX) return KF_EINVAL;
+  const size_t zs_smem = sizeof(double) * (2 * (size_t)ldz + (ldz + 1) / 2 + 8 * 32 * 33);
+  if (cudaFuncSetAttribute(k_zsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs_smem) != cudaSuccess)
+    return KF_ECUDA;
+  KF_PHASE(KF_PH_HYBRID, s, k_zsolve<<<1, 256, zs_smem, s>>>(rank, 1, ldz, ldz, ZLU, piv, in, out, k, 0));
+  return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
+}
+
+kf_status kf_rowupd_level_launch(kf_factor* f, int l, const double* V, double* W, int64_t k, cudaStream_t s) {
+  kf_tree* t = f->t;
+  const int64_t N = t->N;
+  const int64_t rows = (N >> l) + 1;
+  const double inv_h3 = 1.0 / (f->h * f->h * f->h);
+  const int64_t off = (int64_t)(l - 1) * N * f->s_max;
+  if (f->prec == KF_PREC_FP64)
+    launch_rowupd<double, double>(rows, 1 << l, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, f->s_max, 0,
+                                  SRC_STORED, (const double*)f->Phat + off, t->X64, t->X32, t->d, f->c_exp, inv_h3, V,
+                                  -1.0, W, (int)k, KF_PH_HYBRID);
+  else
+    launch_rowupd<float, double>(rows, 1 << l, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, f->s_max, 0,
+                                 SRC_STORED, (const float*)f->Phat + off, t->X64, t->X32, t->d, f->c_exp, inv_h3, V,
+                                 -1.0, W, (int)k, KF_PH_HYBRID);
+  return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
 }

@@ -346,3 +346,40 @@ def test_batched_workload_full_size():
         eg = max(o.residual(B[:, j], x[:, j]) for j in range(4))
         assert eg <= max(100 * eo, 1e-12), (i, eg, eo)
     assert full_match >= 2
+
+
+def test_batched_workload_mixed_refined_full_size():
+    """The 256-problem batch on the mixed path, its solves refined as a batch
+    (x += M^-1 r steps, GMRES for the problems those leave short) to eps_r <=
+    1e-9 against each problem's FP64-accurate operator (GMRES stagnates near
+    2e-10 on the worst-conditioned problems): every problem's 64
+    solutions within 1e-5 of the FP64 path's batched direct solution (the
+    C4 bar), and the median, smallest and largest problems within 1e-5 of
+    the oracle's direct solve where every skeleton matches."""
+    probs = inputs.batched(256, 64)
+    trees = [kf.Tree(torch.from_numpy(q.X).cuda(), q.m) for q in probs]
+    hs, lams, taus = [q.h for q in probs], [q.lam for q in probs], [q.tau for q in probs]
+    Bs = [torch.from_numpy(q.B).cuda() for q in probs]
+    f64 = kf.factorize_batched(trees, hs, lams, taus, probs[0].s_max, precision=FP64, cluster_kernels=False)
+    x64 = kf.solve_batched(f64, Bs)
+    del f64
+    fm = kf.factorize_batched(trees, hs, lams, taus, probs[0].s_max, precision=MIXED, cluster_kernels=False,
+                              refine_tol=1e-9)
+    xm = kf.solve_batched(fm, Bs)
+    errs = [rel(a.cpu().numpy(), b.cpu().numpy()) for a, b in zip(xm, x64)]
+    assert max(errs) <= 1e-5, (int(np.argmax(errs)), max(errs))
+    Ns = np.array([q.N for q in probs])
+    order = np.argsort(Ns, kind="stable")
+    matched = 0
+    for i in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+        q = probs[i]
+        o = oracle.Oracle(q.X, q.m)
+        o.skeletonize(q.h, q.tau, q.s_max, n_samp=q.n_samp, seed=q.seed)
+        o.factorize(q.lam)
+        nodes = range(2, o.nnodes + 1)
+        if not all(np.array_equal(fm[i].skeleton(a), o.skel(a)) for a in nodes):
+            continue
+        matched += 1
+        xo = o.solve(q.B[:, :4])
+        assert rel(xm[i][:, :4].cpu().numpy(), xo) <= 1e-5, i
+    assert matched >= 2

@@ -459,18 +459,21 @@ def test_batched_matches_single_and_oracle():
     Xs = [rng.random((n, 8)) for n in Ns]
     Bs = [rng.standard_normal((n, 3)) for n in Ns]
     trees = [kf.Tree(torch.from_numpy(X).cuda(), 256, ctx=ctx) for X in Xs]
-    for prec, tol in ((FP64, 1e-10), (MIXED, 1e-5)):
-        facs = kf.factorize_batched(trees, hs, [0.5] * len(Ns), [1e-5] * len(Ns), 64, precision=prec)
+    o = oracle.Oracle(Xs[1], 256)
+    o.skeletonize(hs[1], 1e-5, 64)
+    o.factorize(0.5)
+    # FP64 direct sweeps; mixed sweeps without refinement (refine_max_iter = -1)
+    # and with the batch refined as a whole (the mixed path's default)
+    for prec, rmi, tol_single, tol_oracle in ((FP64, 0, 1e-10, 1e-10), (MIXED, -1, 1e-5, 1e-4),
+                                              (MIXED, 0, 1e-8, 1e-8)):
+        facs = kf.factorize_batched(trees, hs, [0.5] * len(Ns), [1e-5] * len(Ns), 64, precision=prec,
+                                    refine_max_iter=rmi)
         xs = kf.solve_batched(facs, [torch.from_numpy(B).cuda() for B in Bs])
         for i in (0, 4):
-            single = kf.Factor(trees[i], hs[i], 0.5, 1e-5, 64, precision=prec, refine_max_iter=-1)
+            single = kf.Factor(trees[i], hs[i], 0.5, 1e-5, 64, precision=prec, refine_max_iter=rmi)
             xi = single.solve(torch.from_numpy(Bs[i]).cuda()).cpu().numpy()
-            assert rel(xs[i].cpu().numpy(), xi) <= (1e-10 if prec == FP64 else 1e-5)
-        o = oracle.Oracle(Xs[1], 256)
-        o.skeletonize(hs[1], 1e-5, 64)
-        o.factorize(0.5)
-        # the batched solve is the direct sweep without refinement: 3xTF32 factors on the mixed path
-        assert rel(xs[1].cpu().numpy(), o.solve(Bs[1])) <= (tol if prec == FP64 else 1e-4)
+            assert rel(xs[i].cpu().numpy(), xi) <= tol_single
+        assert rel(xs[1].cpu().numpy(), o.solve(Bs[1])) <= tol_oracle
 
 
 def test_autograd_kernel_solve_matches_oracle_gradient():
