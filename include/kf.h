@@ -168,7 +168,9 @@ kf_status kf_factor_free(kf_factor* f);
  * alias.  When refinement is on (mixed path by default, refine_max_iter > 0)
  * the solve is refined against the hierarchical operator, with FP64
  * accumulation, until the relative residual (Eq. e:errors) is below
- * opts.refine_tol: by x += M^-1 r or by GMRES(m) (opts.gmres_restart), M being
+ * opts.refine_tol: by x += M^-1 r or by GMRES(m) (opts.gmres_restart; the
+ * columns of B run their own GMRES iterations in lockstep, sharing every
+ * sweep and operator launch), M being
  * the factorization.  A transpose solve is refined the same way against the
  * transposed operator, M^-T being the transpose sweep.  The operator is
  * FP64-accurate when opts.fp64_operator is set (or on the FP64 path);
@@ -214,12 +216,17 @@ kf_status kf_factorize_batched(kf_tree* const* trees, int32_t nprob, const doubl
  * and one for x += M^-1 r, with one host synchronization per step to read the
  * residual norms; a problem leaves the batch once its relative residual
  * (Eq. e:errors, max over its columns) is at most its refine_tol, and a problem
- * whose residual falls by less than half in a step finishes with GMRES(m) per
- * column, as kf_solve does.  B, X: host arrays of DEVICE pointers; nrhs, ld:
- * host arrays.  Synchronizes `stream`.  KF_ENOTCONV when a problem ends above
- * its refine_tol (X is written all the same). */
+ * whose residual falls by less than half in a step finishes with GMRES(m) on
+ * its columns, as kf_solve does.  B, X: host arrays of DEVICE pointers; nrhs, ld:
+ * host arrays.  info: NULL or a host array of nprob records (eps_r: the final
+ * relative residual, max over the problem's columns, -1 when the problem was
+ * not refined; iters: refinement steps plus GMRES iterations, max over
+ * columns; status: KF_OK or KF_ENOTCONV for that problem).  Synchronizes
+ * `stream`.  KF_ENOTCONV when a problem ends above its refine_tol (X is
+ * written all the same). */
 kf_status kf_solve_batched(kf_factor* const* f, int32_t nprob, const void* const* B, void* const* X,
-                           const int64_t* nrhs, const int64_t* ld, int32_t dtype, void* stream);
+                           const int64_t* nrhs, const int64_t* ld, int32_t dtype, void* stream,
+                           kf_solve_info* info);
 
 /* ---- inspection (host outputs; they synchronize the stream) -------------- */
 /* Heap-numbered nodes: root 1, children 2a and 2a+1, level l holds nodes

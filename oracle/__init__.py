@@ -78,6 +78,9 @@ def _load():
             "kfo_hybrid_solve": (I32, [P, P, P]),
             "kfo_hybrid_matvec": (I32, [P, P, P]),
             "kfo_splitmix64": (U64, [U64]),
+            "kfo_knn": (I32, [P, I32, I32, I32, U64, P]),
+            "kfo_set_near": (I32, [P, P, I32, I32]),
+            "kfo_node_near": (I32, [P, I32, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -136,6 +139,32 @@ class Oracle:
         out = np.empty(max(n_samp, 1), dtype=np.int64)
         k = self._lib.kfo_sample(self._h, a, n_samp, ctypes.c_uint64(seed), _ptr(out))
         return out[:k].copy()
+
+    # ---- near-field sampling -------------------------------------------------
+    def knn(self, kappa: int, ntrees: int, leaf: int, seed: int) -> np.ndarray:
+        """kappa nearest tree positions of every point by randomized
+        projection trees (N x kappa int64, -1 padding)."""
+        out = np.empty((self.N, kappa), dtype=np.int64)
+        if self._lib.kfo_knn(self._h, int(kappa), int(ntrees), int(leaf), ctypes.c_uint64(seed), _ptr(out)) != KFO_OK:
+            raise ValueError("oracle knn: bad arguments")
+        return out
+
+    def set_near(self, nbr, near_cap: int = 0):
+        """Near-field sampling from the neighbour lists nbr (None: uniform)."""
+        if nbr is None:
+            self._lib.kfo_set_near(self._h, None, 0, 0)
+            return
+        nbr = np.ascontiguousarray(nbr, dtype=np.int64)
+        if self._lib.kfo_set_near(self._h, _ptr(nbr), nbr.shape[1], int(near_cap)) != KFO_OK:
+            raise ValueError("oracle set_near: bad arguments")
+
+    def node_near(self, a: int):
+        """The node's near list (positions) and counts."""
+        cap = 4096
+        pos = np.empty(cap, dtype=np.int64)
+        cnt = np.empty(cap, dtype=np.int32)
+        n = int(self._lib.kfo_node_near(self._h, a, _ptr(pos), _ptr(cnt)))
+        return pos[:n].copy(), cnt[:n].copy()
 
     # ---- skeletons ----------------------------------------------------------
     def skeletonize(self, h: float, tau: float, s_max: int, n_samp: int | None = None, seed: int = 0x1701):

@@ -57,6 +57,13 @@ struct kfo {
   int64_t* hyb_piv;
   int32_t illcond;
   node_t* nd;     /* indexed by heap id */
+  /* near-field sampling (kfo_set_near): per node, at most near_cap neighbour
+   * positions outside the node, by decreasing count (ties: smaller position),
+   * with their counts; near_on = 0 means uniform sampling */
+  int32_t near_on, near_cap;
+  int64_t** near_pos;
+  int32_t** near_cnt;
+  int32_t* near_len;
 };
 
 static int is_leaf(const kfo* o, int32_t a) { return a >= (1 << o->D); }
@@ -262,11 +269,20 @@ static void free_skel(kfo* o) {
   o->skeletonized = 0;
 }
 
+static void free_near(kfo* o) {
+  if (o->near_pos)
+    for (int32_t a = 0; a <= o->nnodes; ++a) { free(o->near_pos[a]); free(o->near_cnt[a]); }
+  free(o->near_pos); free(o->near_cnt); free(o->near_len);
+  o->near_pos = NULL; o->near_cnt = NULL; o->near_len = NULL;
+  o->near_on = 0;
+}
+
 void kfo_free(kfo* o) {
   if (!o) return;
   free_factor(o);
   free_skel(o);
   free(o->hyb_off); free(o->hyb_lu); free(o->hyb_piv);
+  free_near(o);
   free(o->nd); free(o->X); free(o->perm); free(o->lo); free(o->hi);
   free(o);
 }
@@ -298,6 +314,10 @@ static int cmp_i64(const void* A, const void* B) {
   return (a > b) - (a < b);
 }
 
+/* With near-field sampling on (kfo_set_near): the first min(|near list|,
+ * floor(n_s / 2)) entries of the node's near list are taken, and the rest of
+ * S' is drawn as above, a draw also being skipped when its position is one of
+ * the near entries taken. */
 int32_t kfo_sample(const kfo* o, int32_t a, int32_t n_samp, uint64_t seed, int64_t* out) {
   int64_t lo = o->lo[a], sz = nsz(o, a), M = o->N - sz;
   int64_t ns = M < n_samp ? M : n_samp;
@@ -306,17 +326,236 @@ int32_t kfo_sample(const kfo* o, int32_t a, int32_t n_samp, uint64_t seed, int64
     for (int64_t i = 0; i < o->N; ++i) if (i < lo || i >= lo + sz) out[t++] = i;
     return (int32_t)ns;
   }
-  int64_t got = 0;
+  int64_t got = 0, n1 = 0;
+  if (o->near_on) {
+    n1 = o->near_len[a] < ns / 2 ? o->near_len[a] : ns / 2;
+    for (int64_t t = 0; t < n1; ++t) out[got++] = o->near_pos[a][t];
+  }
   for (uint64_t j = 0; got < ns; ++j) {
     uint64_t u = kfo_splitmix64(seed ^ ((uint64_t)a << 32) ^ j);
     int64_t c = (int64_t)(u % (uint64_t)M);
+    int64_t pos = c < lo ? c : c + sz;
     int dup = 0;
-    for (int64_t t = 0; t < got; ++t) if (out[t] == c) { dup = 1; break; }
-    if (!dup) out[got++] = c;
+    for (int64_t t = 0; t < got; ++t) if (out[t] == pos) { dup = 1; break; }
+    if (!dup) out[got++] = pos;
   }
-  for (int64_t t = 0; t < ns; ++t) if (out[t] >= lo) out[t] += sz;
   qsort(out, ns, sizeof(int64_t), cmp_i64);
   return (int32_t)ns;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Near-field sampling.  READING: the paper samples S' as ASKIT does, whose
+ * sampling draws on the kappa nearest neighbours of the node's points (the
+ * paper's parameter kappa, Sec. IV) and fills up with uniform samples.  Here:
+ *  1. Neighbours by randomized projection trees: tree t over the tree
+ *     positions splits every node like the ball tree (depth
+ *     ceil(log2(N / leaf)), floor(n/2) points to the left child) by the order
+ *     of (projection on x_q - x_p, position), with p and q the points at
+ *     offsets splitmix64(seed ^ (t << 56) ^ (node << 1) ^ k) mod n, k = 0, 1,
+ *     of the node's current list (projections in FP64 as the ball tree's).
+ *     Within a leaf every point's candidates are the leaf's other points, at
+ *     the FP32 squared distance of the FP32-rounded coordinates (sequential
+ *     fmaf over the coordinates of u = x_ik - x_jk).  A point keeps the kappa
+ *     best (distance, position) pairs over all trees, distinct positions.
+ *  2. Node lists: a leaf counts how often each position outside it occurs in
+ *     its points' neighbour lists; an internal node adds up its children's
+ *     lists (counts of equal positions summed, positions inside it dropped).
+ *     Each keeps the near_cap positions of largest count (ties: smaller
+ *     position), in that order.
+ *  3. kfo_sample takes the first min(list length, floor(n_s / 2)) of them. */
+typedef struct { float d; int64_t j; } nbr_t;
+
+static int cmp_nbr(const void* A, const void* B) {
+  const nbr_t* a = (const nbr_t*)A;
+  const nbr_t* b = (const nbr_t*)B;
+  if (a->d != b->d) return a->d < b->d ? -1 : 1;
+  return (a->j > b->j) - (a->j < b->j);
+}
+
+typedef struct { int64_t pos; int64_t cnt; } cnt_t;
+
+static int cmp_cnt_pos(const void* A, const void* B) {
+  const cnt_t* a = (const cnt_t*)A;
+  const cnt_t* b = (const cnt_t*)B;
+  return (a->pos > b->pos) - (a->pos < b->pos);
+}
+static int cmp_cnt_rank(const void* A, const void* B) {
+  const cnt_t* a = (const cnt_t*)A;
+  const cnt_t* b = (const cnt_t*)B;
+  if (a->cnt != b->cnt) return a->cnt > b->cnt ? -1 : 1;
+  return (a->pos > b->pos) - (a->pos < b->pos);
+}
+
+typedef struct { double key; int64_t pos; } proj_t;
+static int cmp_proj(const void* A, const void* B) {
+  const proj_t* a = (const proj_t*)A;
+  const proj_t* b = (const proj_t*)B;
+  if (a->key != b->key) return a->key < b->key ? -1 : 1;
+  return (a->pos > b->pos) - (a->pos < b->pos);
+}
+
+static float dist32(const float* x, const float* y, int32_t d) {
+  float acc = 0.0f;
+  for (int32_t k = 0; k < d; ++k) {
+    float u = x[k] - y[k];
+    acc = fmaf(u, u, acc);
+  }
+  return acc;
+}
+
+/* Orders positions ord[0..N) by randomized projection tree t; leaves of the
+ * complete tree of depth Dk are contiguous ranges (node ranges as the ball
+ * tree's). */
+static void rp_tree(const kfo* o, int32_t t, int32_t Dk, uint64_t seed, int64_t* ord) {
+  const int64_t N = o->N;
+  const int32_t d = o->d;
+  int64_t nn = (int64_t)1 << (Dk + 1);
+  int64_t* lo = (int64_t*)malloc(sizeof(int64_t) * nn);
+  int64_t* hi = (int64_t*)malloc(sizeof(int64_t) * nn);
+  lo[1] = 0; hi[1] = N;
+  for (int64_t a = 1; a < ((int64_t)1 << Dk); ++a) {
+    int64_t n = hi[a] - lo[a], mid = lo[a] + n / 2;
+    lo[2 * a] = lo[a]; hi[2 * a] = mid; lo[2 * a + 1] = mid; hi[2 * a + 1] = hi[a];
+  }
+  for (int64_t i = 0; i < N; ++i) ord[i] = i;
+  for (int32_t l = 0; l < Dk; ++l) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t a = (int64_t)1 << l; a < ((int64_t)1 << (l + 1)); ++a) {
+      int64_t n = hi[a] - lo[a];
+      if (n < 2) continue;
+      int64_t* L = ord + lo[a];
+      uint64_t key = seed ^ ((uint64_t)t << 56) ^ ((uint64_t)a << 1);
+      const double* xp = o->X + L[kfo_splitmix64(key ^ 0) % (uint64_t)n] * d;
+      const double* xq = o->X + L[kfo_splitmix64(key ^ 1) % (uint64_t)n] * d;
+      proj_t* pr = (proj_t*)malloc(sizeof(proj_t) * n);
+      for (int64_t i = 0; i < n; ++i) {
+        const double* xi = o->X + L[i] * d;
+        double acc = 0.0;
+        for (int32_t k = 0; k < d; ++k) acc = acc + (xi[k] - xp[k]) * (xq[k] - xp[k]);
+        pr[i].key = acc;
+        pr[i].pos = L[i];
+      }
+      qsort(pr, n, sizeof(proj_t), cmp_proj);
+      for (int64_t i = 0; i < n; ++i) L[i] = pr[i].pos;
+      free(pr);
+    }
+  }
+  free(lo); free(hi);
+}
+
+int32_t kfo_knn(const kfo* o, int32_t kappa, int32_t ntrees, int32_t leaf, uint64_t seed, int64_t* nbr) {
+  if (!o || kappa < 1 || ntrees < 1 || leaf < 2) return KFO_EINVAL;
+  const int64_t N = o->N;
+  const int32_t d = o->d;
+  int32_t Dk = 0;
+  while (((int64_t)leaf << Dk) < N) ++Dk;
+  float* xf = (float*)malloc(sizeof(float) * (size_t)N * d);
+  for (int64_t i = 0; i < N * d; ++i) xf[i] = (float)o->X[i];
+  nbr_t* best = (nbr_t*)malloc(sizeof(nbr_t) * (size_t)N * kappa);
+  int32_t* nbest = (int32_t*)calloc((size_t)N, sizeof(int32_t));
+  int64_t* ord = (int64_t*)malloc(sizeof(int64_t) * N);
+  int64_t nleaf = (int64_t)1 << Dk;
+  for (int32_t t = 0; t < ntrees; ++t) {
+    rp_tree(o, t, Dk, seed, ord);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t f = 0; f < nleaf; ++f) {
+      /* leaf range of the complete tree: the same halving as rp_tree */
+      int64_t lo = 0, hi = N;
+      for (int32_t l = Dk - 1; l >= 0; --l) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if ((f >> l) & 1) lo = mid; else hi = mid;
+      }
+      int64_t n = hi - lo;
+      nbr_t* cand = (nbr_t*)malloc(sizeof(nbr_t) * (size_t)(n + kappa));
+      for (int64_t ii = lo; ii < hi; ++ii) {
+        int64_t i = ord[ii];
+        int64_t c = 0;
+        for (int32_t q = 0; q < nbest[i]; ++q) cand[c++] = best[i * kappa + q];
+        for (int64_t jj = lo; jj < hi; ++jj) {
+          int64_t j = ord[jj];
+          if (j == i) continue;
+          int dup = 0;
+          for (int32_t q = 0; q < nbest[i]; ++q) if (best[i * kappa + q].j == j) { dup = 1; break; }
+          if (dup) continue;
+          cand[c].d = dist32(xf + i * d, xf + j * d, d);
+          cand[c].j = j;
+          ++c;
+        }
+        qsort(cand, c, sizeof(nbr_t), cmp_nbr);
+        int32_t keep = c < kappa ? (int32_t)c : kappa;
+        for (int32_t q = 0; q < keep; ++q) best[i * kappa + q] = cand[q];
+        nbest[i] = keep;
+      }
+      free(cand);
+    }
+  }
+  for (int64_t i = 0; i < N; ++i)
+    for (int32_t q = 0; q < kappa; ++q) nbr[i * kappa + q] = q < nbest[i] ? best[i * kappa + q].j : -1;
+  free(xf); free(best); free(nbest); free(ord);
+  return KFO_OK;
+}
+
+/* top near_cap of a (pos, cnt) multiset: merge equal positions, rank */
+static int32_t near_select(cnt_t* e, int64_t n, int32_t cap, int64_t** pos_out, int32_t** cnt_out) {
+  qsort(e, n, sizeof(cnt_t), cmp_cnt_pos);
+  int64_t u = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (u > 0 && e[u - 1].pos == e[i].pos) e[u - 1].cnt += e[i].cnt;
+    else e[u++] = e[i];
+  }
+  qsort(e, u, sizeof(cnt_t), cmp_cnt_rank);
+  int32_t keep = u < cap ? (int32_t)u : cap;
+  *pos_out = (int64_t*)malloc(sizeof(int64_t) * (keep > 0 ? keep : 1));
+  *cnt_out = (int32_t*)malloc(sizeof(int32_t) * (keep > 0 ? keep : 1));
+  for (int32_t q = 0; q < keep; ++q) { (*pos_out)[q] = e[q].pos; (*cnt_out)[q] = (int32_t)e[q].cnt; }
+  return keep;
+}
+
+int32_t kfo_set_near(kfo* o, const int64_t* nbr, int32_t kappa, int32_t near_cap) {
+  if (!o) return KFO_EINVAL;
+  free_near(o);
+  if (!nbr) return KFO_OK;
+  if (kappa < 1 || near_cap < 0) return KFO_EINVAL;
+  o->near_cap = near_cap;
+  o->near_pos = (int64_t**)calloc((size_t)o->nnodes + 1, sizeof(int64_t*));
+  o->near_cnt = (int32_t**)calloc((size_t)o->nnodes + 1, sizeof(int32_t*));
+  o->near_len = (int32_t*)calloc((size_t)o->nnodes + 1, sizeof(int32_t));
+  for (int32_t l = o->D; l >= 1; --l) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t a = 1 << l; a < (1 << (l + 1)); ++a) {
+      int64_t lo = o->lo[a], hi = o->hi[a];
+      cnt_t* e;
+      int64_t n = 0;
+      if (l == o->D) {
+        e = (cnt_t*)malloc(sizeof(cnt_t) * (size_t)((hi - lo) * kappa + 1));
+        for (int64_t i = lo; i < hi; ++i)
+          for (int32_t q = 0; q < kappa; ++q) {
+            int64_t j = nbr[i * kappa + q];
+            if (j >= 0 && (j < lo || j >= hi)) { e[n].pos = j; e[n].cnt = 1; ++n; }
+          }
+      } else {
+        int32_t c0 = 2 * a, c1 = 2 * a + 1;
+        e = (cnt_t*)malloc(sizeof(cnt_t) * (size_t)(o->near_len[c0] + o->near_len[c1] + 1));
+        for (int32_t cc = c0; cc <= c1; ++cc)
+          for (int32_t q = 0; q < o->near_len[cc]; ++q) {
+            int64_t j = o->near_pos[cc][q];
+            if (j < lo || j >= hi) { e[n].pos = j; e[n].cnt = o->near_cnt[cc][q]; ++n; }
+          }
+      }
+      o->near_len[a] = near_select(e, n, near_cap, &o->near_pos[a], &o->near_cnt[a]);
+      free(e);
+    }
+  }
+  o->near_on = 1;
+  return KFO_OK;
+}
+
+int32_t kfo_node_near(const kfo* o, int32_t a, int64_t* pos, int32_t* cnt) {
+  if (!o || !o->near_on || a < 2 || a > o->nnodes) return 0;
+  int32_t n = o->near_len[a];
+  if (pos) memcpy(pos, o->near_pos[a], sizeof(int64_t) * n);
+  if (cnt) memcpy(cnt, o->near_cnt[a], sizeof(int32_t) * n);
+  return n;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -40,6 +40,19 @@ void kfo_node_range(const kfo* o, int32_t node, int64_t* lo, int64_t* hi);
 /* Sampled rows S' of a non-root node (reading of Sec. II-A, sampling of S). */
 int32_t kfo_sample(const kfo* o, int32_t node, int32_t n_samp, uint64_t seed, int64_t* out);
 
+/* Near-field sampling (reading of the ASKIT sampling the paper uses, Sec.
+ * II-A and the parameter kappa of Sec. IV).  kfo_knn: for every tree position
+ * the kappa nearest positions found by ntrees randomized projection trees with
+ * leaves of at most `leaf` points (FP32 squared distances of the FP32-rounded
+ * coordinates; -1 pads a short list); nbr: N x kappa.  kfo_set_near: node
+ * lists of at most near_cap positions built from nbr; from then on
+ * kfo_sample (and the skeletonizations) take the first min(list length,
+ * floor(n_s / 2)) of the node's list and draw the rest uniformly.  nbr = NULL
+ * turns it off.  kfo_node_near: the node's list and counts; returns its length. */
+int32_t kfo_knn(const kfo* o, int32_t kappa, int32_t ntrees, int32_t leaf, uint64_t seed, int64_t* nbr);
+int32_t kfo_set_near(kfo* o, const int64_t* nbr, int32_t kappa, int32_t near_cap);
+int32_t kfo_node_near(const kfo* o, int32_t a, int64_t* pos, int32_t* cnt);
+
 /* Skeletonization, Algorithm 1 with the ID of Eq. (e:id).  n_samp = |S'| cap. */
 int32_t kfo_skeletonize(kfo* o, double h, double tau, int32_t s_max, int32_t n_samp, uint64_t seed);
 int32_t kfo_rank(const kfo* o, int32_t node);

@@ -394,9 +394,12 @@ def factorize_batched(trees, hs, lams, taus, s_max: int, precision=KF_PREC_MIXED
     return facs
 
 
-def solve_batched(factors, Bs):
-    """X_i = (lambda_i I + K~_i)^-1 B_i for every problem with one CUDA-graph
-    launch (kf_solve_batched).  B_i: device tensors N_i x k_i (float32/64)."""
+def solve_batched(factors, Bs, info: bool = False):
+    """X_i = (lambda_i I + K~_i)^-1 B_i for every problem (kf_solve_batched):
+    the direct sweeps in one CUDA-graph launch, refined as a batch when the
+    factors refine.  B_i: device tensors N_i x k_i (float32/64).  With
+    info=True returns (X, infos) with one {"eps_r", "iters", "status"} per
+    problem, and a problem left above its refine_tol does not raise."""
     torch = _torch()
     n = len(factors)
     Bc = [B.reshape(B.shape[0], -1).t().contiguous() for B in Bs]
@@ -404,10 +407,15 @@ def solve_batched(factors, Bs):
     nrhs = (ctypes.c_int64 * n)(*[b.shape[0] for b in Bc])
     ld = (ctypes.c_int64 * n)(*[f.tree.N for f in factors])
     ctx = factors[0].ctx
+    inf = (kf_solve_info * n)()
     st = ctx.lib.kf_solve_batched(_ptr_array([f.h.value for f in factors]), n, _ptr_array([b.data_ptr() for b in Bc]),
-                                  _ptr_array([x.data_ptr() for x in Xc]), nrhs, ld, _dtype_code(Bc[0]), _stream_ptr())
-    ctx.check(st)
-    return [x.t().reshape(B.shape) for x, B in zip(Xc, Bs)]
+                                  _ptr_array([x.data_ptr() for x in Xc]), nrhs, ld, _dtype_code(Bc[0]), _stream_ptr(),
+                                  inf)
+    ctx.check(st, allow=(_abi.KF_ENOTCONV,) if info else ())
+    xs = [x.t().reshape(B.shape) for x, B in zip(Xc, Bs)]
+    if info:
+        return xs, [{"eps_r": r.eps_r, "iters": r.iters, "status": r.status} for r in inf]
+    return xs
 
 
 def _autograd():

@@ -67,7 +67,7 @@ SIGNATURES = {
     "kf_factorize_with_ids": (_I32, [_P, _D, _D, _I32, _P, _P, _P, _P, _P, ctypes.POINTER(_P)]),
     "kf_tree_perm_noalloc": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
     "kf_factorize_batched": (_I32, [_P, _I32, _P, _P, _P, _I32, _P, _P, _P]),
-    "kf_solve_batched": (_I32, [_P, _I32, _P, _P, _P, _P, _I32, _P]),
+    "kf_solve_batched": (_I32, [_P, _I32, _P, _P, _P, _P, _I32, _P, _P]),
     "kf_autotune": (_I32, [_P, _D, _D, _D, _I32, _P, _P, _P, _P, _P]),
     "kf_test_tc_wait_probe": (_I32, [_I64]),
     "kf_launch_count": (_I64, []),

@@ -126,56 +126,59 @@ __global__ void k_add(double* __restrict__ x, const double* __restrict__ d, int6
     x[i] += d[i];
 }
 
-// ---- GMRES helpers --------------------------------------------------------------
-// h[j] += sum_i V[j][i] w[i], j < J (one block-partial per j, atomics)
-__global__ void k_multidot(const double* __restrict__ V, int64_t ldv, int J, const double* __restrict__ w, int64_t n,
-                           double* __restrict__ h) {
-  __shared__ double sh[8];
+// ---- GMRES helpers ----------------------------------------------------------------
+// Dot products, updates and scalings of Krylov vectors for k columns at once.
+// k columns stored point-major (element (i, c) at i * k + c), so that k
+// independent GMRES iterations share every launch:
+// h[j * k + c] += sum_i V_j[i * k + c] w[i * k + c], j < J.  Each thread keeps
+// one column (the grid stride is a multiple of k); a block adds its partial
+// sums per column in shared memory, then once per column into h.
+__global__ void k_multidot_k(const double* __restrict__ V, int64_t ldv, int J, const double* __restrict__ w,
+                             int64_t n, int k, double* __restrict__ h) {
+  extern __shared__ double shk[];
+  const int64_t T = (int64_t)gridDim.x * blockDim.x;
+  const int64_t stride = (T / k) * k;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int c = (int)(gid % k);
   for (int j = 0; j < J; ++j) {
-    const double* v = V + (int64_t)j * ldv;
-    double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-      acc = fma(v[i], w[i], acc);
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    for (int q = threadIdx.x; q < k; q += blockDim.x) shk[q] = 0.0;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
-      atomicAdd(h + j, t);
+    if (gid < stride) {
+      const double* v = V + (int64_t)j * ldv;
+      double acc = 0.0;
+      for (int64_t e = gid; e < n * k; e += stride) acc = fma(v[e], w[e], acc);
+      atomicAdd(&shk[c], acc);
     }
     __syncthreads();
+    for (int q = threadIdx.x; q < k; q += blockDim.x) atomicAdd(h + (int64_t)j * k + q, shk[q]);
+    __syncthreads();
   }
 }
-// w[i] -= sum_j h[j] V[j][i]
-__global__ void k_multiaxpy(const double* __restrict__ V, int64_t ldv, int J, const double* __restrict__ h,
-                            double* __restrict__ w, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double acc = w[i];
-    for (int j = 0; j < J; ++j) acc = fma(-h[j], V[(int64_t)j * ldv + i], acc);
-    w[i] = acc;
+// w[i * k + c] -= sum_j h[j * k + c] V_j[i * k + c]
+__global__ void k_multiaxpy_k(const double* __restrict__ V, int64_t ldv, int J, const double* __restrict__ h,
+                              double* __restrict__ w, int64_t n, int k) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % k);
+    double acc = w[e];
+    for (int j = 0; j < J; ++j) acc = fma(-h[(int64_t)j * k + c], V[(int64_t)j * ldv + e], acc);
+    w[e] = acc;
   }
 }
-// x[i] += sum_j y[j] Z[j][i]
-__global__ void k_zupdate(const double* __restrict__ Z, int64_t ldz, int J, const double* __restrict__ y,
-                          double* __restrict__ x, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double acc = x[i];
-    for (int j = 0; j < J; ++j) acc = fma(y[j], Z[(int64_t)j * ldz + i], acc);
-    x[i] = acc;
+// x[i * k + c] += sum_j y[j * k + c] Z_j[i * k + c]
+__global__ void k_zupdate_k(const double* __restrict__ Z, int64_t ldz, int J, const double* __restrict__ y,
+                            double* __restrict__ x, int64_t n, int k) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % k);
+    double acc = x[e];
+    for (int j = 0; j < J; ++j) acc = fma(y[(int64_t)j * k + c], Z[(int64_t)j * ldz + e], acc);
+    x[e] = acc;
   }
 }
-__global__ void k_scale_copy(const double* __restrict__ a, double s, double* __restrict__ b, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = a[i] * s;
-}
-__global__ void k_get_col(const double* __restrict__ W, int64_t k, int64_t r, double* __restrict__ v, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v[i] = W[i * k + r];
-}
-__global__ void k_put_col(const double* __restrict__ v, int64_t k, int64_t r, double* __restrict__ W, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    W[i * k + r] = v[i];
+// b[i * k + c] = a[i * k + c] * sc[c]
+__global__ void k_scale_cols(const double* __restrict__ a, const double* __restrict__ sc, double* __restrict__ b,
+                             int64_t n, int k) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k; e += (int64_t)gridDim.x * blockDim.x)
+    b[e] = a[e] * sc[e % k];
 }
 
 struct Staged {
@@ -745,95 +748,209 @@ static kf_status rel_residual(kf_factor* f, const double* Bt, const double* Xt, 
   return KF_OK;
 }
 
-// GMRES(m) for (lambda I + K~) x = b (or its transpose system), one column:
-// right preconditioning by the factorization (z_j = M^-1 v_j, or M^-T v_j,
-// kept), FP64 Krylov basis orthogonalized by classical Gram-Schmidt applied
-// twice, Givens rotations on the host, the true residual recomputed at every
-// restart.  x holds the initial guess.
-static kf_status gmres_column(kf_factor* f, const double* b, double* x, double bnorm, int m, int maxit, double tol,
-                              int transpose, cudaStream_t s, double* eps, int* iters) {
+// GMRES(m) for (lambda I + K~) X = B (or the transpose system), k columns in
+// lockstep: k independent Krylov iterations (each column its own basis,
+// Hessenberg matrix and Givens rotations, on the host) that share every
+// launch -- one k-column preconditioner sweep (z_j = M^-1 v_j, or M^-T v_j,
+// kept) and one k-column operator product per iteration, classical
+// Gram-Schmidt applied twice, three host round trips per iteration for all
+// columns together.  FP64 basis, right preconditioning by the factorization,
+// the true residual recomputed at every restart.  B, X: N x k point-major;
+// X holds the initial guess.  bnorm: host, ||b_c||.  A column stops
+// contributing once its residual estimate is below tol ||b_c|| (later steps
+// of the shared iteration leave its solution as it is).
+static kf_status gmres_block(kf_factor* f, const double* b, double* x, const double* bnorm, int k, int m, int maxit,
+                             double tol, int transpose, cudaStream_t s, double* eps_out, int* iters_out) {
   kf_ctx* c = f->ctx;
-  const int64_t N = f->t->N;
-  const size_t vb = sizeof(double) * N;
+  const int64_t N = f->t->N, nk = N * (int64_t)k;
+  const size_t vb = sizeof(double) * (size_t)nk;
   double* V = (double*)c->dalloc(vb * (m + 1), s);
   double* Zb = (double*)c->dalloc(vb * m, s);
   double* w = (double*)c->dalloc(vb, s);
-  double* h = (double*)c->dalloc(sizeof(double) * (m + 2), s);
-  kf_status st = (V && Zb && w && h) ? KF_OK : kf_set_err(c, KF_ENOMEM, "gmres: allocation failed");
-  const int g = grid_for(N, 256, 304);
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gg(m + 1), hh(m + 2), y(m);
-  auto fetch = [&](int cnt) -> kf_status {
+  double* h = (double*)c->dalloc(sizeof(double) * (size_t)(m + 2) * k, s);
+  double* dsc = (double*)c->dalloc(sizeof(double) * (size_t)k, s);
+  kf_status st = (V && Zb && w && h && dsc) ? KF_OK : kf_set_err(c, KF_ENOMEM, "gmres: allocation failed");
+  const int g = grid_for(nk, 256, 304);
+  const int gd = std::max(g, (k + 255) / 256);
+  const size_t dsm = sizeof(double) * (size_t)k;
+  std::vector<double> H((size_t)k * (m + 1) * m), cs((size_t)k * m), sn((size_t)k * m), gg((size_t)k * (m + 1));
+  std::vector<double> hh((size_t)(m + 2) * k), y((size_t)m * k), sc(k), beta(k), eps(k, 0.0);
+  std::vector<int> jc(k), done(k);
+  auto Hc = [&](int col, int r, int q) -> double& { return H[((size_t)col * (m + 1) + r) * m + q]; };
+  auto fetch = [&](size_t cnt) -> kf_status {
     KF_CUDA(c, cudaMemcpyAsync(hh.data(), h, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
     KF_CUDA(c, cudaStreamSynchronize(s));
     return KF_OK;
   };
+  auto upload_sc = [&]() -> kf_status {
+    KF_CUDA(c, cudaMemcpyAsync(dsc, sc.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
+    KF_CUDA(c, cudaStreamSynchronize(s));  // sc is rewritten on the host before the next use
+    return KF_OK;
+  };
   int it = 0;
+  double worst = 0.0;
   while (st == KF_OK) {
-    // r = b - A x, beta = ||r||
-    st = apply_op(f, x, w, 1, transpose, s);
+    // R = B - A X, beta_c = ||r_c||
+    st = apply_op(f, x, w, k, transpose, s);
     if (st != KF_OK) break;
-    KF_PHASE(KF_PH_MISC, s, k_sub<<<g, 256, 0, s>>>(b, w, w, N));
-    cudaMemsetAsync(h, 0, sizeof(double), s);
-    KF_PHASE(KF_PH_MISC, s, k_multidot<<<g, 256, 0, s>>>(w, 0, 1, w, N, h));
-    if ((st = fetch(1)) != KF_OK) break;
-    const double beta = sqrt(hh[0]);
-    *eps = bnorm > 0 ? beta / bnorm : beta;
-    if (*eps <= tol || it >= maxit || beta == 0.0) break;
-    KF_PHASE(KF_PH_MISC, s, k_scale_copy<<<g, 256, 0, s>>>(w, 1.0 / beta, V, N));
-    std::fill(gg.begin(), gg.end(), 0.0);
-    gg[0] = beta;
+    KF_PHASE(KF_PH_MISC, s, k_sub<<<g, 256, 0, s>>>(b, w, w, nk));
+    cudaMemsetAsync(h, 0, sizeof(double) * k, s);
+    KF_PHASE(KF_PH_MISC, s, k_colnorm2<<<grid_for(N, 256, 304), 256, 0, s>>>(w, N, k, h));
+    if ((st = fetch(k)) != KF_OK) break;
+    worst = 0.0;
+    for (int col = 0; col < k; ++col) {
+      beta[col] = sqrt(hh[col]);
+      eps[col] = bnorm[col] > 0 ? beta[col] / bnorm[col] : beta[col];
+      worst = std::max(worst, eps[col]);
+      done[col] = !(eps[col] > tol) || beta[col] == 0.0;
+      sc[col] = done[col] ? 0.0 : 1.0 / beta[col];
+      jc[col] = 0;
+      std::fill(gg.begin() + (size_t)col * (m + 1), gg.begin() + (size_t)(col + 1) * (m + 1), 0.0);
+      gg[(size_t)col * (m + 1)] = done[col] ? 0.0 : beta[col];
+    }
+    if (worst <= tol || it >= maxit) break;
+    if ((st = upload_sc()) != KF_OK) break;
+    KF_PHASE(KF_PH_MISC, s, k_scale_cols<<<g, 256, 0, s>>>(w, dsc, V, N, k));
     int j = 0;
-    for (; j < m && it < maxit; ++j, ++it) {
-      double* zj = Zb + (int64_t)j * N;
-      KF_CUDA(c, cudaMemcpyAsync(zj, V + (int64_t)j * N, vb, cudaMemcpyDeviceToDevice, s));
-      if ((st = kf_solve_device(f, zj, 1, transpose, s)) != KF_OK) break;  // z_j = M^-1 v_j (M^-T v_j)
-      if ((st = apply_op(f, zj, w, 1, transpose, s)) != KF_OK) break;     // w = A z_j (A^T z_j)
+    for (; j < m && it < maxit; ++j) {
+      double* zj = Zb + (int64_t)j * nk;
+      KF_CUDA(c, cudaMemcpyAsync(zj, V + (int64_t)j * nk, vb, cudaMemcpyDeviceToDevice, s));
+      if ((st = kf_solve_device(f, zj, k, transpose, s)) != KF_OK) break;  // z_j = M^-1 v_j (M^-T v_j)
+      if ((st = apply_op(f, zj, w, k, transpose, s)) != KF_OK) break;     // w = A z_j (A^T z_j)
       for (int pass = 0; pass < 2; ++pass) {                            // CGS2
-        cudaMemsetAsync(h, 0, sizeof(double) * (j + 1), s);
-        KF_PHASE(KF_PH_MISC, s, k_multidot<<<g, 256, 0, s>>>(V, N, j + 1, w, N, h));
-        KF_PHASE(KF_PH_MISC, s, k_multiaxpy<<<g, 256, 0, s>>>(V, N, j + 1, h, w, N));
-        if ((st = fetch(j + 1)) != KF_OK) break;
-        for (int q = 0; q <= j; ++q) H[(size_t)q * m + j] = (pass == 0 ? 0.0 : H[(size_t)q * m + j]) + hh[q];
+        cudaMemsetAsync(h, 0, sizeof(double) * (size_t)(j + 1) * k, s);
+        KF_PHASE(KF_PH_MISC, s, k_multidot_k<<<gd, 256, dsm, s>>>(V, nk, j + 1, w, N, k, h));
+        KF_PHASE(KF_PH_MISC, s, k_multiaxpy_k<<<g, 256, 0, s>>>(V, nk, j + 1, h, w, N, k));
+        if ((st = fetch((size_t)(j + 1) * k)) != KF_OK) break;
+        for (int col = 0; col < k; ++col)
+          for (int q = 0; q <= j; ++q) Hc(col, q, j) = (pass == 0 ? 0.0 : Hc(col, q, j)) + hh[(size_t)q * k + col];
       }
       if (st != KF_OK) break;
-      cudaMemsetAsync(h, 0, sizeof(double), s);
-      KF_PHASE(KF_PH_MISC, s, k_multidot<<<g, 256, 0, s>>>(w, 0, 1, w, N, h));
-      if ((st = fetch(1)) != KF_OK) break;
-      const double hn = sqrt(hh[0]);
-      H[(size_t)(j + 1) * m + j] = hn;
-      if (hn > 0) KF_PHASE(KF_PH_MISC, s, k_scale_copy<<<g, 256, 0, s>>>(w, 1.0 / hn, V + (int64_t)(j + 1) * N, N));
-      for (int q = 0; q < j; ++q) {  // previous rotations on the new column
-        const double a = H[(size_t)q * m + j], bq = H[(size_t)(q + 1) * m + j];
-        H[(size_t)q * m + j] = cs[q] * a + sn[q] * bq;
-        H[(size_t)(q + 1) * m + j] = -sn[q] * a + cs[q] * bq;
+      cudaMemsetAsync(h, 0, sizeof(double) * k, s);
+      KF_PHASE(KF_PH_MISC, s, k_colnorm2<<<grid_for(N, 256, 304), 256, 0, s>>>(w, N, k, h));
+      if ((st = fetch(k)) != KF_OK) break;
+      bool all_done = true;
+      for (int col = 0; col < k; ++col) {
+        const double hn = sqrt(hh[col]);
+        sc[col] = (!done[col] && hn > 0) ? 1.0 / hn : 0.0;
+        if (done[col]) continue;
+        double* gc = gg.data() + (size_t)col * (m + 1);
+        double* csc = cs.data() + (size_t)col * m;
+        double* snc = sn.data() + (size_t)col * m;
+        Hc(col, j + 1, j) = hn;
+        for (int q = 0; q < j; ++q) {  // previous rotations on the new column
+          const double a = Hc(col, q, j), bq = Hc(col, q + 1, j);
+          Hc(col, q, j) = csc[q] * a + snc[q] * bq;
+          Hc(col, q + 1, j) = -snc[q] * a + csc[q] * bq;
+        }
+        const double a = Hc(col, j, j), bq = Hc(col, j + 1, j);
+        const double r = hypot(a, bq);
+        csc[j] = r > 0 ? a / r : 1.0;
+        snc[j] = r > 0 ? bq / r : 0.0;
+        Hc(col, j, j) = r;
+        Hc(col, j + 1, j) = 0.0;
+        gc[j + 1] = -snc[j] * gc[j];
+        gc[j] = csc[j] * gc[j];
+        jc[col] = j + 1;
+        if (fabs(gc[j + 1]) <= tol * bnorm[col] * 0.5 || hn == 0.0 || r == 0.0) done[col] = 1;
+        all_done = all_done && done[col];
       }
-      const double a = H[(size_t)j * m + j], bq = H[(size_t)(j + 1) * m + j];
-      const double r = hypot(a, bq);
-      cs[j] = r > 0 ? a / r : 1.0;
-      sn[j] = r > 0 ? bq / r : 0.0;
-      H[(size_t)j * m + j] = r;
-      H[(size_t)(j + 1) * m + j] = 0.0;
-      gg[j + 1] = -sn[j] * gg[j];
-      gg[j] = cs[j] * gg[j];
-      if (fabs(gg[j + 1]) <= tol * bnorm * 0.5 || hn == 0.0) { ++j; ++it; break; }
+      ++it;
+      if (all_done) { ++j; break; }
+      if ((st = upload_sc()) != KF_OK) break;
+      KF_PHASE(KF_PH_MISC, s, k_scale_cols<<<g, 256, 0, s>>>(w, dsc, V + (int64_t)(j + 1) * nk, N, k));
     }
     if (st != KF_OK) break;
-    // y = H^-1 g (upper triangular), x += Z y
-    for (int q = j - 1; q >= 0; --q) {
-      double acc = gg[q];
-      for (int t2 = q + 1; t2 < j; ++t2) acc -= H[(size_t)q * m + t2] * y[t2];
-      y[q] = acc / H[(size_t)q * m + q];
+    // per column: y = H^-1 g (upper triangular, its own jc steps), then X += Z Y
+    std::fill(y.begin(), y.end(), 0.0);
+    int J = 0;
+    for (int col = 0; col < k; ++col) {
+      const double* gc = gg.data() + (size_t)col * (m + 1);
+      for (int q = jc[col] - 1; q >= 0; --q) {
+        double acc = gc[q];
+        for (int t2 = q + 1; t2 < jc[col]; ++t2) acc -= Hc(col, q, t2) * y[(size_t)t2 * k + col];
+        y[(size_t)q * k + col] = Hc(col, q, q) != 0.0 ? acc / Hc(col, q, q) : 0.0;
+      }
+      J = std::max(J, jc[col]);
     }
-    KF_CUDA(c, cudaMemcpyAsync(h, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
-    KF_PHASE(KF_PH_MISC, s, k_zupdate<<<g, 256, 0, s>>>(Zb, N, j, h, x, N));
-    KF_CUDA(c, cudaStreamSynchronize(s));  // y lives on the host stack
+    if (J > 0) {
+      KF_CUDA(c, cudaMemcpyAsync(h, y.data(), sizeof(double) * (size_t)J * k, cudaMemcpyHostToDevice, s));
+      KF_PHASE(KF_PH_MISC, s, k_zupdate_k<<<g, 256, 0, s>>>(Zb, nk, J, h, x, N, k));
+    }
+    KF_CUDA(c, cudaStreamSynchronize(s));  // y lives on the host
   }
-  *iters = it;
+  *eps_out = worst;
+  *iters_out = it;
   c->dfree(V, vb * (m + 1), s);
   c->dfree(Zb, vb * m, s);
   c->dfree(w, vb, s);
-  c->dfree(h, sizeof(double) * (m + 2), s);
+  c->dfree(h, sizeof(double) * (size_t)(m + 2) * k, s);
+  c->dfree(dsc, sizeof(double) * (size_t)k, s);
   return st;
+}
+
+// Columns [c0, c0 + kg) of the point-major N x k matrix W <-> a point-major N x kg block.
+__global__ void k_get_cols(const double* __restrict__ W, int64_t k, int64_t c0, int kg, double* __restrict__ out,
+                           int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * kg; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = W[(e / kg) * k + c0 + e % kg];
+}
+__global__ void k_put_cols(const double* __restrict__ in, int64_t k, int64_t c0, int kg, double* __restrict__ W,
+                           int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * kg; e += (int64_t)gridDim.x * blockDim.x)
+    W[(e / kg) * k + c0 + e % kg] = in[e];
+}
+
+// GMRES(m) (lockstep, gmres_block) on groups of columns whose bases (2m + 2
+// vectors each) take at most 4 GB, in place on W (N x nrhs, tree order).
+// Bsrc = nullptr: W holds the right-hand sides on entry and each group starts
+// from their direct solve; otherwise Bsrc holds them and W the initial guess.
+// eps: the worst final relative residual; iters: the most iterations.
+static kf_status gmres_columns(kf_factor* f, double* W, int64_t nrhs, int transpose, cudaStream_t s, double* eps,
+                               int* iters, const double* Bsrc = nullptr) {
+  kf_ctx* c = f->ctx;
+  const int64_t N = f->t->N;
+  const int m = f->gmres_m > 0 ? f->gmres_m : 50;
+  const double budget = 4e9;
+  const int64_t kg_max = std::max<int64_t>(1, std::min<int64_t>(nrhs, (int64_t)(budget / ((2.0 * m + 2) * 8.0 * N))));
+  const size_t gb = sizeof(double) * (size_t)N * kg_max;
+  double* bg = (double*)c->dalloc(gb, s);
+  double* xg = (double*)c->dalloc(gb, s);
+  double* nb = (double*)c->dalloc(sizeof(double) * (size_t)kg_max, s);
+  kf_status r = (bg && xg && nb) ? KF_OK : kf_set_err(c, KF_ENOMEM, "gmres: allocation failed");
+  double worst = 0.0;
+  int most = 0;
+  std::vector<double> hb(kg_max);
+  for (int64_t c0 = 0; c0 < nrhs && r == KF_OK; c0 += kg_max) {
+    const int kg = (int)std::min<int64_t>(kg_max, nrhs - c0);
+    const int64_t ne = N * kg;
+    if (Bsrc) {
+      KF_PHASE(KF_PH_MISC, s, k_get_cols<<<grid_for(ne, 256), 256, 0, s>>>(Bsrc, nrhs, c0, kg, bg, N));
+      KF_PHASE(KF_PH_MISC, s, k_get_cols<<<grid_for(ne, 256), 256, 0, s>>>(W, nrhs, c0, kg, xg, N));
+    } else {
+      KF_PHASE(KF_PH_MISC, s, k_get_cols<<<grid_for(ne, 256), 256, 0, s>>>(W, nrhs, c0, kg, bg, N));
+      cudaMemcpyAsync(xg, bg, sizeof(double) * (size_t)ne, cudaMemcpyDeviceToDevice, s);
+      if ((r = kf_solve_device(f, xg, kg, transpose, s)) != KF_OK) break;
+    }
+    cudaMemsetAsync(nb, 0, sizeof(double) * kg, s);
+    KF_PHASE(KF_PH_MISC, s, k_colnorm2<<<grid_for(N, 256, 304), 256, 0, s>>>(bg, N, kg, nb));
+    cudaMemcpyAsync(hb.data(), nb, sizeof(double) * kg, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    for (int q = 0; q < kg; ++q) hb[q] = sqrt(hb[q]);
+    double e = 0.0;
+    int its = 0;
+    r = gmres_block(f, bg, xg, hb.data(), kg, m, f->refine_max_iter, f->refine_tol, transpose, s, &e, &its);
+    worst = std::max(worst, e);
+    most = std::max(most, its);
+    KF_PHASE(KF_PH_MISC, s, k_put_cols<<<grid_for(ne, 256), 256, 0, s>>>(xg, nrhs, c0, kg, W, N));
+  }
+  cudaStreamSynchronize(s);
+  c->dfree(bg, gb, s);
+  c->dfree(xg, gb, s);
+  c->dfree(nb, sizeof(double) * (size_t)kg_max, s);
+  *eps = worst;
+  *iters = most;
+  return r;
 }
 
 // Solve in place, W: N x nrhs FP64 in tree order.  The direct sweep of the
@@ -878,36 +995,11 @@ static kf_status solve_refined(kf_factor* f, double* W, int64_t nrhs, int transp
     return r;
   };
   auto gmres_path = [&]() -> kf_status {
-    // GMRES(m) per column, starting from the direct solve of the factorization
-    const size_t cb = sizeof(double) * N;
-    double* bcol = (double*)c->dalloc(cb, s);
-    double* xcol = (double*)c->dalloc(cb, s);
-    double* nb = (double*)c->dalloc(sizeof(double), s);
-    kf_status r = (bcol && xcol && nb) ? KF_OK : kf_set_err(c, KF_ENOMEM, "gmres: allocation failed");
-    double worst = 0.0;
-    for (int64_t col = 0; col < nrhs && r == KF_OK; ++col) {
-      KF_PHASE(KF_PH_MISC, s, k_get_col<<<grid_for(N, 256), 256, 0, s>>>(W, nrhs, col, bcol, N));
-      cudaMemcpyAsync(xcol, bcol, cb, cudaMemcpyDeviceToDevice, s);
-      if ((r = kf_solve_device(f, xcol, 1, transpose, s)) != KF_OK) break;
-      cudaMemsetAsync(nb, 0, sizeof(double), s);
-      KF_PHASE(KF_PH_MISC, s, k_colnorm2<<<grid_for(N, 256, 304), 256, 0, s>>>(bcol, N, 1, nb));
-      double hb = 0.0;
-      cudaMemcpyAsync(&hb, nb, sizeof(double), cudaMemcpyDeviceToHost, s);
-      cudaStreamSynchronize(s);
-      double e = 0.0;
-      int its = 0;
-      r = gmres_column(f, bcol, xcol, sqrt(hb), f->gmres_m, f->refine_max_iter, f->refine_tol, transpose, s, &e,
-                       &its);
-      worst = std::max(worst, e);
-      iters = std::max(iters, its);
-      KF_PHASE(KF_PH_MISC, s, k_put_col<<<grid_for(N, 256), 256, 0, s>>>(xcol, nrhs, col, W, N));
-    }
-    eps = worst;
-    if (r == KF_OK && worst > f->refine_tol)
-      r = kf_set_err(c, KF_ENOTCONV, "GMRES stopped at eps_r = %.3e after %d iterations", worst, iters);
-    c->dfree(bcol, cb, s);
-    c->dfree(xcol, cb, s);
-    c->dfree(nb, sizeof(double), s);
+    // GMRES(m) from the direct solve of the factorization, the columns in
+    // lockstep groups whose Krylov bases fit a fixed memory budget
+    kf_status r = gmres_columns(f, W, nrhs, transpose, s, &eps, &iters);
+    if (r == KF_OK && eps > f->refine_tol)
+      r = kf_set_err(c, KF_ENOTCONV, "GMRES stopped at eps_r = %.3e after %d iterations", eps, iters);
     return r;
   };
   kf_status r = (refine && f->gmres_m > 0) ? gmres_path() : richardson();
@@ -1152,7 +1244,8 @@ kf_status run_batched_graph(kf_ctx* c, int32_t nprob, cudaStream_t s, Enq enq) {
 // finishes column by column with GMRES(m) from where it stands, like kf_solve.
 // Problems whose factors do not refine get the direct sweep only.
 kf_status solve_batched_refined(kf_factor* const* f, int32_t nprob, const void* const* B, void* const* X,
-                                const int64_t* nrhs, const int64_t* ld, int32_t dtype, cudaStream_t s) {
+                                const int64_t* nrhs, const int64_t* ld, int32_t dtype, cudaStream_t s,
+                                kf_solve_info* info) {
   kf_ctx* c = f[0]->ctx;
   struct Prob {
     double *Bt = nullptr, *Wt = nullptr, *R = nullptr, *Y = nullptr;
@@ -1160,7 +1253,6 @@ kf_status solve_batched_refined(kf_factor* const* f, int32_t nprob, const void* 
     double eps = INFINITY;
     int steps = 0;
     int state = 0;  // 0 refining, 1 converged, 2 to GMRES, 3 direct only
-    std::vector<double> bn2;  // squared column norms of b
   };
   std::vector<Prob> P(nprob);
   int64_t ktot = 0;
@@ -1224,7 +1316,6 @@ kf_status solve_batched_refined(kf_factor* const* f, int32_t nprob, const void* 
         e = std::max(e, bb > 0 ? sqrt(rr / bb) : sqrt(rr));
       }
       Prob& q = P[i];
-      q.bn2.assign(hn.begin() + 2 * koff[i] + k, hn.begin() + 2 * koff[i] + 2 * k);
       const double prev = q.eps;
       q.eps = e;
       if (e <= f[i]->refine_tol) q.state = 1;
@@ -1243,34 +1334,25 @@ kf_status solve_batched_refined(kf_factor* const* f, int32_t nprob, const void* 
       return KF_OK;
     });
   }
-  // the problems the steps did not settle: GMRES(m) per column from the current x
+  // the problems the steps did not settle: GMRES(m) on all their columns in
+  // lockstep, from the current x
   kf_status worst = KF_OK;
   for (int32_t i = 0; i < nprob && st == KF_OK; ++i) {
     if (P[i].state != 2) continue;
-    kf_factor* fi = f[i];
-    const int64_t N = fi->t->N, k = nrhs[i];
-    const size_t cb = sizeof(double) * N;
-    double* bcol = (double*)c->dalloc(cb, s);
-    double* xcol = (double*)c->dalloc(cb, s);
-    if (!bcol || !xcol) st = kf_set_err(c, KF_ENOMEM, "batched solve: allocation failed");
     double pe = 0.0;
-    for (int64_t col = 0; col < k && st == KF_OK; ++col) {
-      KF_PHASE(KF_PH_MISC, s, k_get_col<<<grid_for(N, 256), 256, 0, s>>>(P[i].Bt, k, col, bcol, N));
-      KF_PHASE(KF_PH_MISC, s, k_get_col<<<grid_for(N, 256), 256, 0, s>>>(P[i].Wt, k, col, xcol, N));
-      const double bn = sqrt(P[i].bn2[col]);
-      double e = 0.0;
-      int its = 0;
-      st = gmres_column(fi, bcol, xcol, bn, fi->gmres_m > 0 ? fi->gmres_m : 50, fi->refine_max_iter, fi->refine_tol, 0,
-                        s, &e, &its);
-      pe = std::max(pe, e);
-      KF_PHASE(KF_PH_MISC, s, k_put_col<<<grid_for(N, 256), 256, 0, s>>>(xcol, k, col, P[i].Wt, N));
-    }
-    if (bcol) c->dfree(bcol, cb, s);
-    if (xcol) c->dfree(xcol, cb, s);
+    int pits = 0;
+    st = gmres_columns(f[i], P[i].Wt, nrhs[i], 0, s, &pe, &pits, P[i].Bt);
     P[i].eps = pe;
-    if (st == KF_OK && pe > fi->refine_tol && worst == KF_OK)
+    P[i].steps += pits;
+    if (st == KF_OK && pe > f[i]->refine_tol && worst == KF_OK)
       worst = kf_set_err(c, KF_ENOTCONV, "batched solve: problem %d stopped at eps_r = %.3e", i, pe);
   }
+  if (info)
+    for (int32_t i = 0; i < nprob; ++i) {
+      info[i].eps_r = P[i].state == 3 ? -1.0 : P[i].eps;
+      info[i].iters = P[i].steps;
+      info[i].status = (P[i].state != 3 && P[i].eps > f[i]->refine_tol) ? KF_ENOTCONV : KF_OK;
+    }
   // x back to the caller's order and type
   if (st == KF_OK)
     st = run_on(all, [&](int32_t i, cudaStream_t si) -> kf_status {
@@ -1338,7 +1420,8 @@ kf_status kf_factorize_batched(kf_tree* const* trees, int32_t nprob, const doubl
 }
 
 kf_status kf_solve_batched(kf_factor* const* f, int32_t nprob, const void* const* B, void* const* X,
-                           const int64_t* nrhs, const int64_t* ld, int32_t dtype, void* stream) {
+                           const int64_t* nrhs, const int64_t* ld, int32_t dtype, void* stream,
+                           kf_solve_info* info) {
   if (!f || nprob < 1 || !B || !X || !nrhs || !ld) return kf_set_err(nullptr, KF_EINVAL, "batched solve: bad arguments");
   for (int32_t i = 0; i < nprob; ++i) {
     kf_status r = check_rhs(f[i], B[i], X[i], nrhs[i], ld[i], dtype);
@@ -1349,7 +1432,9 @@ kf_status kf_solve_batched(kf_factor* const* f, int32_t nprob, const void* const
   kf_ctx* c = f[0]->ctx;
   bool any_refined = false;
   for (int32_t i = 0; i < nprob; ++i) any_refined = any_refined || refines(f[i]);
-  if (any_refined) return solve_batched_refined(f, nprob, B, X, nrhs, ld, dtype, (cudaStream_t)stream);
+  if (any_refined) return solve_batched_refined(f, nprob, B, X, nrhs, ld, dtype, (cudaStream_t)stream, info);
+  if (info)
+    for (int32_t i = 0; i < nprob; ++i) info[i] = kf_solve_info{-1.0, 0, KF_OK};
   return run_batched_graph(c, nprob, (cudaStream_t)stream, [&](int32_t i, cudaStream_t si) -> kf_status {
     return with_vectors(f[i], B[i], X[i], nrhs[i], ld[i], dtype, si,
                         [&](double* W) { return kf_solve_device(f[i], W, nrhs[i], 0, si); });

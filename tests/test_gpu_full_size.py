@@ -365,9 +365,13 @@ def test_batched_workload_mixed_refined_full_size():
     del f64
     fm = kf.factorize_batched(trees, hs, lams, taus, probs[0].s_max, precision=MIXED, cluster_kernels=False,
                               refine_tol=1e-9)
-    xm = kf.solve_batched(fm, Bs)
+    xm, infos = kf.solve_batched(fm, Bs, info=True)
     errs = [rel(a.cpu().numpy(), b.cpu().numpy()) for a, b in zip(xm, x64)]
-    assert max(errs) <= 1e-5, (int(np.argmax(errs)), max(errs))
+    worst = int(np.argmax(errs))
+    assert max(errs) <= 1e-5, (worst, max(errs), infos[worst])
+    # a problem whose GMRES stagnated above 1e-9 (measured: at most 2 of 256, near 1.3e-7) still ends
+    # with a residual two orders below what the 1e-5 bar on the error needs at these conditionings
+    assert max(i["eps_r"] for i in infos) <= 1e-6
     Ns = np.array([q.N for q in probs])
     order = np.argsort(Ns, kind="stable")
     matched = 0
@@ -383,3 +387,51 @@ def test_batched_workload_mixed_refined_full_size():
         xo = o.solve(q.B[:, :4])
         assert rel(xm[i][:, :4].cpu().numpy(), xo) <= 1e-5, i
     assert matched >= 2
+
+
+def test_mixed_workload_solves_against_whole_oracle():
+    """The mixed workload (N = 65,536, d = 8, lambda = 0.1, 16 RHS) against a
+    whole oracle run (Algorithms 1-3 over the full tree).  lambda = 0.1 leaves
+    lambda I + K~ ill-conditioned here (||x|| / ||b|| ~ 250, reduced-system
+    pivots down to 4e-5 of the largest): the oracle's own FP64 direct solve
+    reaches eps_r ~ 6e-7 and is accurate to ~1e-7 only, so element-wise
+    agreement is held to what both direct solves can give, and the refined
+    solutions are held to the oracle's operator:
+    * GPU FP64 direct sweep vs the oracle's direct solve, both FP64
+      renderings of Algorithm 3 on the same K~: within 1e-5;
+    * GPU FP64 path refined by GMRES to eps_r <= 1e-10: the oracle's operator
+      (Eq. e:uv, second form) gives it eps_r <= 1e-9;
+    * mixed path (FP32 factors, all 16 RHS refined together by lockstep
+      GMRES(50) against the FP64-accurate operator to eps_r <= 1e-6, the
+      bar's setting): within 1e-5 of the refined FP64 solution and of the
+      oracle's direct solve, eps_r <= 2e-6 under the oracle's operator.
+    The FP32 factorization alone is no solver here (error O(1)); skeletons
+    must match the oracle's at every node for K~ to be the same."""
+    p = inputs.mixed()
+    o = oracle.Oracle(p.X, p.m)
+    o.skeletonize(p.h, p.tau, p.s_max, n_samp=p.n_samp, seed=p.seed)
+    o.factorize(p.lam)
+    tree = kf.Tree(torch.from_numpy(p.X).cuda(), p.m)
+    B = p.B[:, :2]
+    Bt = torch.from_numpy(p.B).cuda()
+    F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=FP64, fp64_operator=True, refine_max_iter=-1)
+    nodes = range(2, o.nnodes + 1)
+    assert all(np.array_equal(F.skeleton(a), o.skel(a)) for a in nodes)
+    xo = o.solve(B)
+    assert rel(F.solve(Bt[:, :2]).cpu().numpy(), xo) <= 1e-5
+    del F
+    Fr = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=FP64, fp64_operator=True, refine_tol=1e-10,
+                   refine_max_iter=200, gmres_restart=50)
+    xr = Fr.solve(Bt[:, :2]).cpu().numpy()
+    del Fr
+    for j in range(2):
+        assert o.residual(B[:, j], xr[:, j]) <= 1e-9
+    Fm = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=MIXED, refine_tol=1e-6, refine_max_iter=400,
+                   gmres_restart=50)
+    xm, info = Fm.solve(Bt, info=True)
+    assert info["eps_r"] <= 1e-6
+    xm = xm.cpu().numpy()
+    assert rel(xm[:, :2], xr) <= 1e-5
+    assert rel(xm[:, :2], xo) <= 1e-5
+    for j in range(2):
+        assert o.residual(B[:, j], xm[:, j]) <= 2e-6
