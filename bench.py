@@ -520,6 +520,60 @@ def gpu_main(args, rank, world):
                   "solve_rhs_per_s": round(1e3 / e0.elapsed_time(e1), 2), "rel_err_vs_reference": relf(xb_)}
         del Fb, tree, xb_
 
+    # ---- near-field sampling of S' (knn_kappa = 16): the same workload and metric ------
+    # (factorization including the neighbour search; the mixed solve to the metric's
+    # bar and to the timed solve's eps_r; the FP64 direct solve; errors against the
+    # FP64 factorization of the same K~ refined by GMRES)
+    near = None
+    if not args.no_near:
+        tree = kf.Tree(X, p.m)
+        kn = dict(knn_kappa=args.knn_kappa)
+        def fact_time(prec, **kw):
+            ts = []
+            for _ in range(2):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=prec, sync_errors=False, **kn, **kw)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return F, min(ts) / 1e3
+        def solve_time(F):
+            F.solve(b)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            x, inf = F.solve(b, info=True)
+            e1.record()
+            torch.cuda.synchronize()
+            return x, inf, e0.elapsed_time(e1) / 1e3
+        Fr = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=kf.KF_PREC_FP64, fp64_operator=True,
+                       refine_max_iter=30, refine_tol=1e-12, gmres_restart=30, sync_errors=False, **kn)
+        xr, ir = Fr.solve(b, info=True)
+        del Fr
+        relr = lambda a: float(torch.linalg.norm(a - xr) / torch.linalg.norm(xr))
+        F64, f64_s = fact_time(kf.KF_PREC_FP64, fp64_operator=False, refine_max_iter=-1, **opt(kf.KF_PREC_FP64))
+        x64, _, s64 = solve_time(F64)
+        ranks_n = F64.ranks()
+        del F64
+        Fm, fm_s = fact_time(kf.KF_PREC_MIXED, fp64_operator=True, refine_tol=1e-6, refine_max_iter=400,
+                             gmres_restart=args.gmres_m, **opt(kf.KF_PREC_MIXED))
+        xm, im, sm = solve_time(Fm)
+        del Fm
+        Fu, _ = fact_time(kf.KF_PREC_MIXED, fp64_operator=False, refine_max_iter=-1, **opt(kf.KF_PREC_MIXED))
+        xu, _, su = solve_time(Fu)
+        del Fu, tree
+        near = {"knn_kappa": args.knn_kappa, "knn_trees": 4, "knn_leaf": 512,
+                "reference_eps_r": ir["eps_r"], "ranks_mean": float(np.mean(ranks_n[2:])),
+                "fp64": {"factorize_s": round(f64_s, 4), "solve_rhs_per_s": round(1 / s64, 2),
+                         "rel_err_vs_reference": relr(x64)},
+                "mixed_at_1e-5": {"factorize_s": round(fm_s, 4), "solve_rhs_per_s": round(1 / sm, 2),
+                                  "gmres_iters": im["iters"], "eps_r": im["eps_r"], "rel_err_vs_reference": relr(xm)},
+                "mixed_unrefined": {"solve_rhs_per_s": round(1 / su, 2), "rel_err_vs_reference": relr(xu)},
+                "note": "S' half from the nodes' near-field lists (kappa nearest neighbours by randomized "
+                        "projection trees), half uniform; factorization times include the neighbour search"}
+
     # ---- GMRES iterations of the mixed solve at other sampler seeds ------------------
     # (the default seed's K~ is the most ill-conditioned of those tried: its
     # iteration count moves with rounding-level changes of the FP32 factors)
@@ -737,6 +791,11 @@ def gpu_main(args, rank, world):
             "mixed_unrefined_rel_err": unref["rel_err_vs_reference"] if unref else None,
             "reference": "FP64 factorization + GMRES vs the FP64 operator (eps_r %.1e)" % reference["eps_r"]
                          if fp64 else None,
+            "near_field_mixed_solve_rhs_per_s_at_1e-5": near["mixed_at_1e-5"]["solve_rhs_per_s"] if near else None,
+            "near_field_mixed_rel_err_at_1e-5": near["mixed_at_1e-5"]["rel_err_vs_reference"] if near else None,
+            "near_field_mixed_factorize_s": near["mixed_at_1e-5"]["factorize_s"] if near else None,
+            "near_field_fp64_solve_rhs_per_s": near["fp64"]["solve_rhs_per_s"] if near else None,
+            "near_field_mixed_unrefined_rel_err": near["mixed_unrefined"]["rel_err_vs_reference"] if near else None,
             "batched_mixed_max_rel_err_vs_fp64": batched["mixed"]["rel_err_vs_fp64"]["max"] if batched else None,
             "batched_mixed_solve_rhs_per_s": batched["mixed"]["rhs_per_s"] if batched else None,
             "batched_fp64_solve_rhs_per_s": batched["fp64"]["rhs_per_s"] if batched else None,
@@ -755,6 +814,7 @@ def gpu_main(args, rank, world):
                           "candidate_ms": [round(t, 2) for t in v[1]]} for k, v in tuned.items()} or None,
             "fp64_path": fp64, "mixed_unrefined": unref, "mixed_solve_at_metric_bar": at_bar,
             "solve_seed_study": seed_study, "accuracy_reference": reference if fp64 else None,
+            "near_field_sampling": near,
             "differentiation": diff, "batched": batched,
         }
         print(json.dumps(line), flush=True)
@@ -804,6 +864,8 @@ def main():
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-seed-study", action="store_true", help="skip the mixed solve at other sampler seeds")
+    ap.add_argument("--no-near", action="store_true", help="skip the near-field sampling variant of the workload")
+    ap.add_argument("--knn-kappa", type=int, default=16, help="neighbours per point of the near-field variant")
     ap.add_argument("--no-autotune", action="store_true", help="default kernel variants instead of kf_autotune's")
     ap.add_argument("--batched-n", type=int, default=256, help="problems of the batched workload")
     ap.add_argument("--once", action="store_true",

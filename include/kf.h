@@ -102,9 +102,9 @@ typedef struct {
   int32_t zinv_max_nodes; /* tree levels with at most this many nodes keep the explicit inverse of
                              their reduced systems Z for the solve sweep (a product spread over many
                              CTAs instead of a latency-bound LU solve per node), computed after each
-                             level's LU at 2 z^3 FP64 flops a node: 0 = default (64; none in
-                             kf_factorize_batched, whose concurrent problems hide that latency),
-                             -1 = none */
+                             level's LU at 2 z^3 FP64 flops a node: 0 = default (64; in
+                             kf_factorize_batched none for factors whose solves are not refined,
+                             whose single sweep the concurrent problems hide), -1 = none */
   int32_t hybrid_level;   /* 0 = the direct solver (Algorithm 2 up to the root).  L >= 1: the hybrid
                              level-restricted solver of Sec. II-C (Algorithms 6-8) with its frontier
                              at level L (1 <= L <= depth): the subtrees of the 2^L nodes of level L
@@ -115,7 +115,19 @@ typedef struct {
                              KF_EUNSUPPORTED).  kf_solve (transpose = 0) and kf_matvec then apply
                              (D + UV)^-1 and D + UV, D = blockdiag(lambda I + K~_aa); transpose
                              solves and kf_grad return KF_EUNSUPPORTED.  kf_factorize only. */
-  int32_t reserved[1];
+  int32_t knn_kappa;      /* near-field sampling of S' (the ASKIT sampling the paper uses, Sec. II-A,
+                             with kappa neighbours, Sec. IV): 0 = uniform sampling (default); kappa in
+                             1..32: every point's kappa nearest points are found by knn_trees
+                             randomized projection trees with leaves of at most knn_leaf points
+                             (FP32 squared distances of the FP32 coordinates, sequential fused
+                             multiply-adds, ties to the smaller tree position); every node lists the
+                             positions outside it that its points' lists name most often (a parent
+                             adds its children's lists), keeps n_samp / 2 of them, and S' takes the
+                             first min(list length, floor(n_s / 2)) of those and draws the rest
+                             uniformly.  Needs leaf size x kappa <= 16384 (else KF_EUNSUPPORTED). */
+  int32_t knn_trees;      /* projection trees of the neighbour search (0 = 4) */
+  int32_t knn_leaf;       /* their leaf size, 2..1024 (0 = 512) */
+  int32_t reserved[3];
 } kf_opts;
 
 /* Filled by kf_solve when non-NULL (synchronizes the stream). */
@@ -202,7 +214,7 @@ kf_status kf_grad(kf_factor* f, const void* x, const void* dLdx, void* dLdb, dou
  * once on `stream` (no counterpart in the paper, which solves one problem at
  * a time; Algorithms 1-2 per problem).  h, lambda, tau: host arrays of nprob
  * values; s_max and opts are shared (opts.zinv_max_nodes = 0 means no explicit
- * Z^-1 here).  out: host array of nprob factor handles (NULL on failure).
+ * Z^-1 here unless the factors' solves are refined).  out: host array of nprob factor handles (NULL on failure).
  * Synchronizes `stream`; returns the worst per-problem status (KF_EILLCOND
  * leaves the factors in place).  Scratch memory inside the graph comes from
  * cudaMallocAsync even when the context has an allocator. */
@@ -245,6 +257,14 @@ kf_status kf_factor_skeleton(const kf_factor* f, int32_t node, int64_t* skel, vo
 kf_status kf_factor_P(const kf_factor* f, int32_t node, double* P, void* stream);
 /* P^_node = K~_node^-1 P_{node node~}, |node| x s row-major FP64. */
 kf_status kf_factor_Phat(const kf_factor* f, int32_t node, double* Phat, void* stream);
+
+/* Near-field sampling (kf_opts.knn_kappa > 0): every point's neighbour list,
+ * nbr: host, N x kappa int32 tree positions (-1 pads a short list); and the
+ * list of a non-root node: pos and cnt host arrays of n_samp / 2 entries, the
+ * first *len of them used, positions by decreasing count.  KF_EINVAL when
+ * near-field sampling is off. */
+kf_status kf_factor_knn(const kf_factor* f, int32_t* nbr, void* stream);
+kf_status kf_factor_near(const kf_factor* f, int32_t node, int32_t* pos, int32_t* cnt, int32_t* len, void* stream);
 
 /* Test hook: factorize with skeletons and interpolation matrices supplied by
  * the caller instead of computing them, so that the factorization can be
@@ -327,8 +347,9 @@ kf_status kf_profile_enable(int32_t on);
  * and of the refinement's operator; solve_colsum and solve_rowupd are those of
  * the solve sweep), z_inv (the explicit Z^-1 of the upper levels, see
  * kf_opts.zinv_max_nodes), hybrid (the reduced system of the hybrid solver:
- * its coupling blocks, LU and products, kf_opts.hybrid_level). */
-#define KF_PHASE_COUNT 25
+ * its coupling blocks, LU and products, kf_opts.hybrid_level), near (the
+ * neighbour lists of near-field sampling, kf_opts.knn_kappa). */
+#define KF_PHASE_COUNT 26
 kf_status kf_profile_read(double* ms, int64_t* launches, int32_t nphase);
 /* Per-launch timeline of the launches recorded since the last kf_profile_read
  * (which it leaves in place): for launch q < *n, its start and end in ms

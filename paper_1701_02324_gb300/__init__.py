@@ -172,9 +172,10 @@ class Tree:
 
 def _opts(precision=KF_PREC_FP64, n_samp=0, seed=0, v_storage=KF_V_STORED, sync_errors=0, refine_tol=0.0,
           refine_max_iter=0, tensor_cores=True, fp64_operator=None, gmres_restart=0, cluster_kernels=True,
-          tc_tile_n=0, zinv_max_nodes=0, hybrid_level=0):
+          tc_tile_n=0, zinv_max_nodes=0, hybrid_level=0, knn_kappa=0, knn_trees=0, knn_leaf=0):
     o = kf_opts()
     o.hybrid_level = int(hybrid_level)
+    o.knn_kappa, o.knn_trees, o.knn_leaf = int(knn_kappa), int(knn_trees), int(knn_leaf)
     o.zinv_max_nodes = int(zinv_max_nodes)
     o.no_cluster_kernels = 0 if cluster_kernels else 1
     o.tc_tile_n = int(tc_tile_n)
@@ -194,15 +195,20 @@ class Factor:
                  n_samp: int = 0, seed: int = 0, v_storage=KF_V_STORED, refine_tol: float = 0.0,
                  refine_max_iter: int = 0, sync_errors: bool = True, tensor_cores: bool = True,
                  fp64_operator=None, gmres_restart: int = 0, cluster_kernels: bool = True, tc_tile_n: int = 0,
-                 zinv_max_nodes: int = 0, hybrid_level: int = 0, _ids=None):
+                 zinv_max_nodes: int = 0, hybrid_level: int = 0, knn_kappa: int = 0, knn_trees: int = 0,
+                 knn_leaf: int = 0, _ids=None):
         """hybrid_level = L >= 1: the hybrid level-restricted solver of
         Sec. II-C (Algorithms 6-8) with its frontier at tree level L; 0: the
-        direct solver (Algorithms 2-3)."""
+        direct solver (Algorithms 2-3).  knn_kappa > 0: near-field sampling
+        of S' from every point's knn_kappa nearest neighbours (knn_trees
+        projection trees with leaves of knn_leaf points)."""
         self.tree, self.ctx = tree, tree.ctx
         self.h_, self.lam, self.tau, self.s_max, self.precision = float(h), float(lam), float(tau), int(s_max), precision
         self.hybrid_level = int(hybrid_level)
+        self._knn_kappa, self._n_samp = int(knn_kappa), int(n_samp)
         o = _opts(precision, n_samp, seed, v_storage, int(sync_errors), refine_tol, refine_max_iter, tensor_cores,
-                  fp64_operator, gmres_restart, cluster_kernels, tc_tile_n, zinv_max_nodes, hybrid_level)
+                  fp64_operator, gmres_restart, cluster_kernels, tc_tile_n, zinv_max_nodes, hybrid_level, knn_kappa,
+                  knn_trees, knn_leaf)
         h_out = ctypes.c_void_p()
         if _ids is None:
             st = self.ctx.lib.kf_factorize(tree.h, self.h_, self.lam, self.tau, self.s_max, ctypes.byref(o),
@@ -287,6 +293,29 @@ class Factor:
         out = np.zeros(max(s * nrows, 1))
         self.ctx.check(self.ctx.lib.kf_factor_Phat(self.h, node, out.ctypes.data_as(ctypes.c_void_p), _stream_ptr()))
         return out[: s * nrows].reshape(nrows, s)
+
+    def knn(self):
+        """Every point's neighbour list of near-field sampling (N x kappa tree positions, -1 padding)."""
+        import numpy as np
+        kappa = self._kappa()
+        out = np.zeros((self.tree.N, kappa), dtype=np.int32)
+        self.ctx.check(self.ctx.lib.kf_factor_knn(self.h, out.ctypes.data_as(ctypes.c_void_p), _stream_ptr()))
+        return out
+
+    def near(self, node: int):
+        """A node's near-field list: positions and counts."""
+        import numpy as np
+        cap = max(1, (self._n_samp or 2 * self.s_max) // 2)
+        pos = np.zeros(cap, dtype=np.int32)
+        cnt = np.zeros(cap, dtype=np.int32)
+        n = ctypes.c_int32()
+        self.ctx.check(self.ctx.lib.kf_factor_near(self.h, int(node), pos.ctypes.data_as(ctypes.c_void_p),
+                                                   cnt.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n),
+                                                   _stream_ptr()))
+        return pos[:n.value].copy(), cnt[:n.value].copy()
+
+    def _kappa(self):
+        return self._knn_kappa
 
     def pivot_ratios(self):
         """Smallest/largest pivot of every node's leaf Cholesky or Z LU."""

@@ -36,7 +36,10 @@ class kf_opts(ctypes.Structure):
         ("tc_tile_n", ctypes.c_int32),
         ("zinv_max_nodes", ctypes.c_int32),
         ("hybrid_level", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 1),
+        ("knn_kappa", ctypes.c_int32),
+        ("knn_trees", ctypes.c_int32),
+        ("knn_leaf", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -64,6 +67,8 @@ SIGNATURES = {
     "kf_factor_P": (_I32, [_P, _I32, _P, _P]),
     "kf_factor_Phat": (_I32, [_P, _I32, _P, _P]),
     "kf_factor_pivot_ratios": (_I32, [_P, _P, _P]),
+    "kf_factor_knn": (_I32, [_P, _P, _P]),
+    "kf_factor_near": (_I32, [_P, _I32, _P, _P, _P, _P]),
     "kf_factorize_with_ids": (_I32, [_P, _D, _D, _I32, _P, _P, _P, _P, _P, ctypes.POINTER(_P)]),
     "kf_tree_perm_noalloc": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
     "kf_factorize_batched": (_I32, [_P, _I32, _P, _P, _P, _I32, _P, _P, _P]),
@@ -78,7 +83,7 @@ SIGNATURES = {
 
 PHASES = ["tree", "sample", "eval_A", "qr", "leaf_assemble", "leaf_cholesky", "leaf_phat", "eval_V", "zoff", "z_lu",
           "z_solve_pc", "telescope", "solve_leaf", "solve_colsum", "solve_zsolve", "solve_rowupd", "matvec_leaf",
-          "matvec_push", "misc", "qr_cluster", "qr_leaf", "matvec_colsum", "matvec_rowupd", "z_inv", "hybrid"]
+          "matvec_push", "misc", "qr_cluster", "qr_leaf", "matvec_colsum", "matvec_rowupd", "z_inv", "hybrid", "near"]
 
 _lock = threading.Lock()
 _lib = None

@@ -259,6 +259,9 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
     if (opts->no_cluster_kernels) f->use_cluster_qr = f->use_cluster_lu = 0;
     if (opts->zinv_max_nodes != 0) f->zinv_max_nodes = opts->zinv_max_nodes > 0 ? opts->zinv_max_nodes : -1;
     f->hyb_L = opts->hybrid_level;
+    f->knn_kappa = opts->knn_kappa;
+    if (opts->knn_trees > 0) f->knn_trees = opts->knn_trees;
+    if (opts->knn_leaf > 0) f->knn_leaf = opts->knn_leaf;
     if (opts->tc_tile_n == 128) f->tc_bn = 128;
     else if (opts->tc_tile_n != 0 && opts->tc_tile_n != 256) {
       delete f;
@@ -276,6 +279,17 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
   if (f->n_samp > 1024) {
     delete f;
     return kf_set_err(c, KF_EINVAL, "n_samp must be <= 1024");
+  }
+  if (f->knn_kappa < 0 || f->knn_kappa > 32 || f->knn_trees < 1 || f->knn_trees > 64 || f->knn_leaf < 2 ||
+      f->knn_leaf > 1024) {
+    delete f;
+    return kf_set_err(c, KF_EINVAL, "near-field sampling: knn_kappa in 0..32, knn_trees in 1..64, knn_leaf in "
+                      "2..1024");
+  }
+  if (f->knn_kappa > 0 && (int64_t)t->leaf_max * f->knn_kappa > 16384) {
+    delete f;
+    return kf_set_err(c, KF_EUNSUPPORTED, "near-field sampling: leaf size x knn_kappa = %lld exceeds 16384",
+                      (long long)t->leaf_max * f->knn_kappa);
   }
   if (f->hyb_L < 0 || f->hyb_L > t->D) {
     const int Lbad = f->hyb_L;
@@ -317,6 +331,17 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
     if (!f->Kdf || (D > 0 && f->prec != KF_PREC_FP64 && !f->VTdf)) {
       kf_factor_free(f);
       return kf_set_err(c, KF_ENOMEM, "factorize: device allocation of the FP64 operator failed");
+    }
+  }
+  if (f->knn_kappa > 0) {
+    f->near_cap = f->n_samp / 2;
+    f->nbr = falloc<int32_t>(f, (size_t)N * f->knn_kappa, s);
+    f->near_pos = falloc<int32_t>(f, nn * (size_t)std::max(1, f->near_cap), s);
+    f->near_cnt = falloc<int32_t>(f, nn * (size_t)std::max(1, f->near_cap), s);
+    f->near_len = falloc<int32_t>(f, nn, s);
+    if (!f->nbr || !f->near_pos || !f->near_cnt || !f->near_len) {
+      kf_factor_free(f);
+      return kf_set_err(c, KF_ENOMEM, "factorize: device allocation of the near-field lists failed");
     }
   }
   if (f->hyb_L > 0) {
@@ -1121,6 +1146,30 @@ static kf_status node_ok(const kf_factor* f, int32_t node) {
   return KF_OK;
 }
 
+kf_status kf_factor_knn(const kf_factor* f, int32_t* nbr, void* stream) {
+  if (!f || !nbr) return KF_EINVAL;
+  if (f->knn_kappa <= 0) return kf_set_err(f->ctx, KF_EINVAL, "kf_factor_knn: near-field sampling is off");
+  cudaStream_t s = (cudaStream_t)stream;
+  KF_CUDA(f->ctx, cudaMemcpyAsync(nbr, f->nbr, sizeof(int32_t) * (size_t)f->t->N * f->knn_kappa,
+                                  cudaMemcpyDeviceToHost, s));
+  KF_CUDA(f->ctx, cudaStreamSynchronize(s));
+  return KF_OK;
+}
+
+kf_status kf_factor_near(const kf_factor* f, int32_t node, int32_t* pos, int32_t* cnt, int32_t* len, void* stream) {
+  if (!f || !pos || !cnt || !len) return KF_EINVAL;
+  if (f->knn_kappa <= 0) return kf_set_err(f->ctx, KF_EINVAL, "kf_factor_near: near-field sampling is off");
+  kf_status st = node_ok(f, node);
+  if (st != KF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t cap = (size_t)f->near_cap;
+  KF_CUDA(f->ctx, cudaMemcpyAsync(len, f->near_len + node, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  KF_CUDA(f->ctx, cudaMemcpyAsync(pos, f->near_pos + node * cap, sizeof(int32_t) * cap, cudaMemcpyDeviceToHost, s));
+  KF_CUDA(f->ctx, cudaMemcpyAsync(cnt, f->near_cnt + node * cap, sizeof(int32_t) * cap, cudaMemcpyDeviceToHost, s));
+  KF_CUDA(f->ctx, cudaStreamSynchronize(s));
+  return KF_OK;
+}
+
 kf_status kf_factor_skeleton(const kf_factor* f, int32_t node, int64_t* skel, void* stream) {
   if (!f || !skel) return KF_EINVAL;
   kf_status st = node_ok(f, node);
@@ -1388,12 +1437,17 @@ kf_status kf_factorize_batched(kf_tree* const* trees, int32_t nprob, const doubl
   if (opts && opts->hybrid_level != 0)
     return kf_set_err(c, KF_EUNSUPPORTED, "batched: the hybrid solver is kf_factorize only");
   cudaStream_t s = (cudaStream_t)stream;
-  // the batch's concurrent graph branches hide the latency of the per-node LU
-  // solves, so by default no Z^-1 is formed here (measured on 256 problems of
-  // 2,048-32,768 points: Z^-1 on levels of <= 64 nodes cost 37% more
-  // factorization time for 33% less solve time)
+  // A single direct sweep of the batch hides the latency of the per-node LU
+  // solves in its concurrent graph branches, so factors that are not refined
+  // form no Z^-1 by default (measured on 256 problems of 2,048-32,768 points:
+  // Z^-1 on levels of <= 64 nodes cost 37% more factorization time for 33%
+  // less time of one solve).  Refined factors (the mixed path by default) run
+  // several sweeps of all right-hand sides per solve, and there the LU solves,
+  // one column after another on one CTA per node, dominated (11 of 23 s of
+  // refined 64-RHS solves of that batch); they keep the default of kf_factorize.
   kf_opts ob = opts ? *opts : kf_opts{};
-  if (ob.zinv_max_nodes == 0) ob.zinv_max_nodes = -1;
+  const bool refined = ob.refine_max_iter > 0 || (ob.precision == KF_PREC_MIXED && ob.refine_max_iter == 0);
+  if (ob.zinv_max_nodes == 0 && !refined) ob.zinv_max_nodes = -1;
   kf_status st = KF_OK;
   for (int32_t i = 0; i < nprob && st == KF_OK; ++i) st = alloc_factor(trees[i], h[i], lambda[i], tau[i], s_max, &ob, s, &out[i]);
   if (st == KF_OK) KF_CUDA(c, cudaStreamSynchronize(s));  // buffers zeroed before the graph runs

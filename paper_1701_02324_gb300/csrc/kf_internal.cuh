@@ -107,6 +107,14 @@ struct kf_factor {
   int32_t* Hrank = nullptr;
   int32_t* Hoff = nullptr;
   double* Hpivr = nullptr;
+  // near-field sampling (knn_kappa > 0): every point's kappa neighbours (tree
+  // positions, N x kappa, -1 padding) and every node's list of at most
+  // near_cap = n_samp / 2 positions (node * near_cap + i), counts, lengths
+  int32_t knn_kappa = 0, knn_trees = 4, knn_leaf = 512, near_cap = 0;
+  int32_t* nbr = nullptr;
+  int32_t* near_pos = nullptr;
+  int32_t* near_cnt = nullptr;
+  int32_t* near_len = nullptr;
   int32_t* status = nullptr;
   double* pivr = nullptr;  // per node: smallest / largest pivot of its leaf Cholesky or Z LU
   std::vector<std::pair<void*, size_t>> allocs;
@@ -342,3 +350,9 @@ kf_status kf_zsolve_one_launch(const int32_t* rank, int ldz, const double* ZLU, 
                                double* out, int k, cudaStream_t s);
 // W -= rows of P^ (level l, type of the factor) times the per-node vector V
 kf_status kf_rowupd_level_launch(kf_factor* f, int l, const double* V, double* W, int64_t k, cudaStream_t s);
+
+// ---- near-field sampling (tree.cu, knn.cu) ------------------------------------------
+// order of the tree positions under randomized projection tree tidx of depth Dk
+kf_status kf_rp_order(kf_tree* t, int tidx, int Dk, uint64_t seed, int64_t* ord, cudaStream_t s);
+// f->nbr and the node lists f->near_* from the tree (stream order)
+kf_status kf_near_field_lists(kf_factor* f, cudaStream_t s);

@@ -34,6 +34,7 @@ enum kf_phase {
   KF_PH_MV_ROWUPD,
   KF_PH_ZINV,
   KF_PH_HYBRID,
+  KF_PH_NEAR,
   KF_PH_COUNT
 };
 

@@ -23,9 +23,13 @@
 namespace {
 
 // ---- 1. sampling: one warp per node ------------------------------------------
+// With near-field sampling (near_pos != nullptr) the first min(list length,
+// floor(n_s / 2)) entries of the node's near list are accepted before the
+// draws, which then also skip them (knn.cu).
 __global__ void k_sample(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi, int64_t N, int node0,
-                         int nn, int n_samp, uint64_t seed, int32_t* __restrict__ samp, int32_t* __restrict__ ns_out,
-                         int32_t* __restrict__ status) {
+                         int nn, int n_samp, uint64_t seed, const int32_t* __restrict__ near_pos,
+                         const int32_t* __restrict__ near_len, int near_cap, int32_t* __restrict__ samp,
+                         int32_t* __restrict__ ns_out, int32_t* __restrict__ status) {
   extern __shared__ int32_t acc[];  // n_samp accepted candidates
   int nl = blockIdx.x;
   if (nl >= nn) return;
@@ -40,6 +44,15 @@ __global__ void k_sample(const int32_t* __restrict__ lo, const int32_t* __restri
     return;
   }
   int got = 0;
+  if (near_pos) {  // near entries first, as complement indices (the draws' space)
+    const int n1 = (int)((int64_t)near_len[node] < ns / 2 ? (int64_t)near_len[node] : ns / 2);
+    for (int t = lane; t < n1; t += 32) {
+      const int32_t p = near_pos[(int64_t)node * near_cap + t];
+      acc[t] = (int32_t)(p < b ? p : p - sz);
+    }
+    got = n1;
+    __syncwarp();
+  }
   // bounded: with n_s < N - |a| distinct values exist; the cap only guards
   // against a generator defect and flags it instead of spinning
   for (uint64_t j0 = 0; got < ns; j0 += 32) {
@@ -676,9 +689,14 @@ kf_status kf_skel_begin(kf_factor* f, kf_skel_scratch* sc, cudaStream_t s) {
   sc->nsamp = (int32_t*)c->dalloc(sizeof(int32_t) * nsampled, s);
   if (!sc->A || !sc->samp || !sc->nsamp)
     return kf_set_err(c, KF_ENOMEM, "skeletonize: allocation of %zu bytes failed", sizeof(double) * sc->a_elems);
+  if (f->knn_kappa > 0) {
+    kf_status st = kf_near_field_lists(f, s);
+    if (st != KF_OK) return st;
+  }
   KF_PHASE(KF_PH_SAMPLE, s, k_sample<<<(unsigned)nsampled, 32, sizeof(int32_t) * f->n_samp, s>>>(
-                                t->d_lo, t->d_hi, t->N, 2, (int)nsampled, f->n_samp, f->seed, sc->samp, sc->nsamp,
-                                f->status));
+                                t->d_lo, t->d_hi, t->N, 2, (int)nsampled, f->n_samp, f->seed,
+                                f->knn_kappa > 0 ? f->near_pos : nullptr, f->near_len, f->near_cap, sc->samp,
+                                sc->nsamp, f->status));
   KF_LAUNCH_CHECK(c);
   return KF_OK;
 }

@@ -575,6 +575,66 @@ __global__ void __launch_bounds__(256) k_zsolve(const int32_t* __restrict__ rank
   }
 }
 
+// The same product for several right-hand sides at once: a 32 x 64 tile of
+// out (32 entries of the node's vector x 64 columns) per CTA, the reduction
+// over the node's z entries in chunks of 32 with the Z^-1 block (or its
+// transpose) and the input block staged in shared memory, so that Z^-1 is
+// read once per 64 columns instead of once per column.  Thread (ty, tx)
+// forms rows ty*4..+3 of columns tx and tx + 32.
+__global__ void __launch_bounds__(256) k_zinv_apply_multi(const int32_t* __restrict__ rank, int node0, int ldz,
+                                                          int s_max, const double* __restrict__ Zinv,
+                                                          const double* __restrict__ in, double* __restrict__ out,
+                                                          int k, int transpose) {
+  __shared__ double sa[32][33];
+  __shared__ double su[32][65];
+  const int node = node0 + blockIdx.x, l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], z = sl + sr;
+  const int e0 = blockIdx.y * 32, c0 = blockIdx.z * 64;
+  if (e0 >= z || c0 >= k) return;
+  const double* A = Zinv + (int64_t)node * ldz * ldz;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  auto dst = [&](int i) -> int64_t { return i < sl ? (int64_t)l * s_max + i : (int64_t)r * s_max + (i - sl); };
+  double acc[4][2] = {};
+  for (int j0 = 0; j0 < z; j0 += 32) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int ii = ty * 4 + q, i = e0 + ii, j = j0 + tx;
+      // row i of Z^-1 (or column i, for Z^-T), entries j0..j0+31
+      sa[ii][tx] = (i < z && j < z) ? (transpose ? A[(int64_t)j * ldz + i] : A[(int64_t)i * ldz + j]) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int jj = ty * 4 + q, j = j0 + jj;
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const int c = c0 + tx + 32 * h2;
+        su[jj][tx + 32 * h2] = (j < z && c < k) ? in[dst(j) * k + c] : 0.0;
+      }
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int jj = 0; jj < 32; ++jj) {
+      const double u0 = su[jj][tx], u1 = su[jj][tx + 32];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const double a = sa[ty * 4 + q][jj];
+        acc[q][0] = fma(a, u0, acc[q][0]);
+        acc[q][1] = fma(a, u1, acc[q][1]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = e0 + ty * 4 + q;
+    if (i >= z) continue;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+      const int c = c0 + tx + 32 * h2;
+      if (c < k) out[dst(i) * k + c] = acc[q][h2];
+    }
+  }
+}
+
 // ---- operator pieces ------------------------------------------------------------
 // Leaf blocks: y_i = lambda x_i + sum_j K(x_i, x_j) x_j (or dK/dh, no lambda).
 // ---- reduced systems by the explicit inverse (upper levels) -------------------
@@ -676,31 +736,50 @@ __global__ void __launch_bounds__(128) k_leaf_mv(const int32_t* __restrict__ lo,
 // y_i = lambda x_i + sum_j K[i][j] x_j, the products and sums in double-float
 // arithmetic on the FP32 pipes.  The leaf's x is split into pairs once per
 // CTA in shared memory; one warp per row, lanes over j.
+// RB right-hand sides r0 .. r0 + RB - 1 (those below k) per launch: each row of
+// Kdf is read once for all of them; per right-hand side the arithmetic and its
+// order are those of RB = 1.
+template <int RB>
 __global__ void __launch_bounds__(256) k_leaf_mv_df(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                     int leaf0, int ldL, const float2* __restrict__ Kdf,
                                                     double lambda, const double* __restrict__ x,
-                                                    double* __restrict__ y, int k, int r) {
-  extern __shared__ float2 xs[];  // n
+                                                    double* __restrict__ y, int k, int r0) {
+  extern __shared__ float2 xs[];  // n x RB
   const int lf = blockIdx.y, node = leaf0 + lf;
   const int b = lo[node], n = hi[node] - b;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) xs[j] = kf_split_df(x[(int64_t)(b + j) * k + r]);
+  const int nr = min(RB, k - r0);
+  for (int e = threadIdx.x; e < n * RB; e += blockDim.x) {
+    const int j = e / RB, q = e % RB;
+    xs[e] = q < nr ? kf_split_df(x[(int64_t)(b + j) * k + r0 + q]) : make_float2(0.f, 0.f);
+  }
   __syncthreads();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   for (int i = warp; i < n; i += (gridDim.x * blockDim.x) >> 5) {
     const float2* Ki = Kdf + ((int64_t)lf * ldL + i) * ldL;
-    float sh = 0.f, sl = 0.f;
+    float sh[RB], sl[RB];
+#pragma unroll
+    for (int q = 0; q < RB; ++q) sh[q] = sl[q] = 0.f;
     for (int j = lane; j < n; j += 32) {
-      const float2 m = Ki[j], v = xs[j];
-      kf_df_fma(m.x, m.y, v.x, v.y, sh, sl);
+      const float2 m = Ki[j];
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        const float2 v = xs[j * RB + q];
+        kf_df_fma(m.x, m.y, v.x, v.y, sh[q], sl[q]);
+      }
     }
-    for (int off = 16; off > 0; off >>= 1) {
-      const float oh = __shfl_xor_sync(0xffffffffu, sh, off), ol = __shfl_xor_sync(0xffffffffu, sl, off);
-      float t, e;
-      kf_two_sum(sh, oh, t, e);
-      e = __fadd_rn(e, __fadd_rn(sl, ol));
-      kf_fast_two_sum(t, e, sh, sl);
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      for (int off = 16; off > 0; off >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, sh[q], off), ol = __shfl_xor_sync(0xffffffffu, sl[q], off);
+        float t, e;
+        kf_two_sum(sh[q], oh, t, e);
+        e = __fadd_rn(e, __fadd_rn(sl[q], ol));
+        kf_fast_two_sum(t, e, sh[q], sl[q]);
+      }
+      if (lane == 0 && q < nr)
+        y[(int64_t)(b + i) * k + r0 + q] =
+            lambda * x[(int64_t)(b + i) * k + r0 + q] + ((double)sh[q] + (double)sl[q]);
     }
-    if (lane == 0) y[(int64_t)(b + i) * k + r] = lambda * x[(int64_t)(b + i) * k + r] + ((double)sh + (double)sl);
   }
 }
 
@@ -891,8 +970,14 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
   auto zsolve = [&](int l, int tr) {
     if (l <= f->zinv_top && f->Zinv) {
       dim3 gz(1u << l, (unsigned)((ldz + 31) / 32));
-      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zinv_apply<<<gz, 256, 0, s>>>(f->rank, 1 << l, ldz, s_max, f->Zinv, U, Vb,
+      if (k >= 4) {
+        dim3 gm(1u << l, (unsigned)((ldz + 31) / 32), (unsigned)((k + 63) / 64));
+        KF_PHASE(KF_PH_S_ZSOLVE, s, k_zinv_apply_multi<<<gm, 256, 0, s>>>(f->rank, 1 << l, ldz, s_max, f->Zinv, U, Vb,
+                                                                          (int)k, tr));
+      } else {
+        KF_PHASE(KF_PH_S_ZSOLVE, s, k_zinv_apply<<<gz, 256, 0, s>>>(f->rank, 1 << l, ldz, s_max, f->Zinv, U, Vb,
                                                                    (int)k, tr));
+      }
     } else {
       KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<1 << l, 256, zs_smem, s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv,
                                                                          U, Vb, (int)k, tr));
@@ -947,11 +1032,18 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
   auto vt_level = [&](int l) { return VT ? VT + (int64_t)(l - 1) * N * s_max : nullptr; };
   if (f->Kdf && !deriv) {
     dim3 gl((unsigned)std::max(1, std::min(64, (t->leaf_max * 32 + 255) / 256)), 1 << D);
-    const size_t xsm = sizeof(float2) * t->leaf_max;
-    KF_CUDA(c, cudaFuncSetAttribute(k_leaf_mv_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
-    for (int r = 0; r < k; ++r)
-      KF_PHASE(KF_PH_MV_LEAF, s, k_leaf_mv_df<<<gl, 256, xsm, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, f->Kdf,
-                                                                  f->lambda, x, y, (int)k, r));
+    if (k == 1) {
+      const size_t xsm = sizeof(float2) * t->leaf_max;
+      KF_CUDA(c, cudaFuncSetAttribute(k_leaf_mv_df<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
+      KF_PHASE(KF_PH_MV_LEAF, s, k_leaf_mv_df<1><<<gl, 256, xsm, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, f->Kdf,
+                                                                     f->lambda, x, y, (int)k, 0));
+    } else {  // eight right-hand sides per pass over the leaf blocks
+      const size_t xsm = sizeof(float2) * t->leaf_max * 8;
+      KF_CUDA(c, cudaFuncSetAttribute(k_leaf_mv_df<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
+      for (int r = 0; r < k; r += 8)
+        KF_PHASE(KF_PH_MV_LEAF, s, k_leaf_mv_df<8><<<gl, 256, xsm, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, f->Kdf,
+                                                                       f->lambda, x, y, (int)k, r));
+    }
   } else {
     dim3 gl((t->leaf_max + 127) / 128, 1 << D);
     KF_PHASE(KF_PH_MV_LEAF, s, k_leaf_mv<TM><<<gl, 128, 0, s>>>(t->d_lo, t->d_hi, leaf0, t->X64, t->X32, t->d, f->c_exp, inv_h3,

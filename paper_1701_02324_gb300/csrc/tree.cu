@@ -13,6 +13,7 @@
 // per-node sort is a bitonic network over segments padded to a power of two.
 #include <algorithm>
 #include <atomic>
+#include <vector>
 
 #include "kf_internal.cuh"
 #include "prof.cuh"
@@ -213,6 +214,35 @@ __global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (float)in[i];
 }
+// node ranges of the complete tree of depth D over N points (floor(n/2) to
+// the left child), heap numbered
+__global__ void k_node_ranges(int64_t N, int D, int32_t* __restrict__ lo, int32_t* __restrict__ hi) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  lo[1] = 0;
+  hi[1] = (int32_t)N;
+  for (int a = 1; a < (1 << D); ++a) {
+    int32_t n = hi[a] - lo[a], mid = lo[a] + n / 2;
+    lo[2 * a] = lo[a];
+    hi[2 * a] = mid;
+    lo[2 * a + 1] = mid;
+    hi[2 * a + 1] = hi[a];
+  }
+}
+
+// Randomized projection tree `tidx` (near-field sampling): the split points p
+// and q of every node of a level, at offsets splitmix64(seed ^ (tidx << 56) ^
+// (node << 1) ^ k) mod n (k = 0, 1) of the node's current list.
+__global__ void k_rp_pairs(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi, int node0, int nn,
+                           uint64_t seed, int tidx, int32_t* __restrict__ ip, int32_t* __restrict__ iq) {
+  for (int nl = blockIdx.x * blockDim.x + threadIdx.x; nl < nn; nl += gridDim.x * blockDim.x) {
+    const int a = node0 + nl;
+    const int64_t n = hi[a] - lo[a];
+    const uint64_t key = seed ^ ((uint64_t)tidx << 56) ^ ((uint64_t)a << 1);
+    ip[nl] = lo[a] + (n > 0 ? (int32_t)(kf_splitmix64(key ^ 0) % (uint64_t)n) : 0);
+    iq[nl] = lo[a] + (n > 0 ? (int32_t)(kf_splitmix64(key ^ 1) % (uint64_t)n) : 0);
+  }
+}
+
 __global__ void k_iota64(int64_t* p, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = i;
 }
@@ -332,6 +362,91 @@ kf_status kf_tree_build_device(kf_tree* t, cudaStream_t s) {
 
 // ---- allocation-free variant of the tree build ------------------------------------
 //
+// Near-field sampling: the order of the tree positions under randomized
+// projection tree `tidx` of depth Dk (every node split like the ball tree's,
+// by the order of (projection on x_q - x_p, position), p and q from
+// k_rp_pairs); the leaves are the contiguous ranges of the complete tree of
+// depth Dk.  ord: device, N int64.  The same projection, sort and gather
+// kernels as the ball tree; coordinates from the tree's FP64 copy.
+kf_status kf_rp_order(kf_tree* t, int tidx, int Dk, uint64_t seed, int64_t* ord, cudaStream_t s) {
+  kf_ctx* c = t->ctx;
+  const int64_t N = t->N;
+  const int d = t->d;
+  KF_PHASE(KF_PH_NEAR, s, k_iota64<<<grid_for(N, 256), 256, 0, s>>>(ord, N));
+  KF_LAUNCH_CHECK(c);
+  if (Dk == 0) return KF_OK;
+  int64_t segmax = 1;
+  while (segmax < N) segmax <<= 1;
+  const int64_t vcap = 2 * segmax;
+  const int maxnodes = 1 << (Dk - 1);
+  const int nn_all = 2 << Dk;
+  std::vector<int32_t> hlo(nn_all, 0), hhi(nn_all, 0);
+  hlo[1] = 0;
+  hhi[1] = (int32_t)N;
+  for (int a = 1; a < (1 << Dk); ++a) {
+    int32_t n = hhi[a] - hlo[a], mid = hlo[a] + n / 2;
+    hlo[2 * a] = hlo[a]; hhi[2 * a] = mid; hlo[2 * a + 1] = mid; hhi[2 * a + 1] = hhi[a];
+  }
+  size_t bytes_X = sizeof(double) * N * d, bytes_p = sizeof(int64_t) * N;
+  double* Xa = (double*)c->dalloc(bytes_X, s);
+  double* Xb = (double*)c->dalloc(bytes_X, s);
+  int64_t* pb = (int64_t*)c->dalloc(bytes_p, s);
+  double* key = (double*)c->dalloc(sizeof(double) * vcap, s);
+  int64_t* orig = (int64_t*)c->dalloc(sizeof(int64_t) * vcap, s);
+  int32_t* pos = (int32_t*)c->dalloc(sizeof(int32_t) * vcap, s);
+  int32_t* ia = (int32_t*)c->dalloc(sizeof(int32_t) * 2 * maxnodes, s);
+  int32_t* rlo = (int32_t*)c->dalloc(sizeof(int32_t) * nn_all, s);
+  int32_t* rhi = (int32_t*)c->dalloc(sizeof(int32_t) * nn_all, s);
+  kf_status st = KF_OK;
+  if (!Xa || !Xb || !pb || !key || !orig || !pos || !ia || !rlo || !rhi) {
+    st = kf_set_err(c, KF_ENOMEM, "near-field sampling: allocation failed");
+  } else {
+    cudaMemcpyAsync(Xa, t->X64, bytes_X, cudaMemcpyDeviceToDevice, s);
+    KF_PHASE(KF_PH_NEAR, s, k_node_ranges<<<1, 1, 0, s>>>(N, Dk, rlo, rhi));
+    int32_t* ip = ia;
+    int32_t* iq = ia + maxnodes;
+    int64_t* pa = ord;
+    for (int l = 0; l < Dk && st == KF_OK; ++l) {
+      const int node0 = 1 << l, nn = 1 << l;
+      int64_t nmax = 0;
+      for (int a = node0; a < 2 * node0; ++a) nmax = std::max<int64_t>(nmax, hhi[a] - hlo[a]);
+      KF_PHASE(KF_PH_NEAR, s, k_rp_pairs<<<(nn + 127) / 128, 128, 0, s>>>(rlo, rhi, node0, nn, seed, tidx, ip, iq));
+      int64_t seg = 1;
+      while (seg < nmax) seg <<= 1;
+      if (seg < 2) seg = 2;
+      const int64_t total = seg * nn;
+      dim3 gk((unsigned)std::min<int64_t>((seg + 255) / 256, 4096), nn);
+      KF_PHASE(KF_PH_NEAR, s, k_proj_keys<<<gk, 256, 0, s>>>(Xa, pa, d, rlo, rhi, node0, seg, ip, iq, key, orig, pos));
+      const int tiles = (int)((total + kSortTile - 1) / kSortTile);
+      const int64_t ktile = std::min<int64_t>(seg, kSortTile);
+      KF_PHASE(KF_PH_NEAR, s, k_bitonic_shared<<<tiles, 512, 0, s>>>(key, orig, pos, total, seg, 2, ktile, 1));
+      for (int64_t k = 2 * kSortTile; k <= seg; k <<= 1) {
+        for (int64_t j = k >> 1; j >= kSortTile; j >>= 1)
+          KF_PHASE(KF_PH_NEAR, s, k_bitonic_global<<<grid_for(total, 256), 256, 0, s>>>(key, orig, pos, total, seg, k, j));
+        KF_PHASE(KF_PH_NEAR, s, k_bitonic_shared<<<tiles, 512, 0, s>>>(key, orig, pos, total, seg, k, k, kSortTile / 2));
+      }
+      KF_PHASE(KF_PH_NEAR, s, k_gather_rows<<<gk, 256, 0, s>>>(Xa, pa, d, rlo, rhi, node0, seg, pos, Xb, pb));
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) st = kf_set_err(c, KF_ECUDA, "projection tree level %d: %s", l, cudaGetErrorString(e));
+      std::swap(Xa, Xb);
+      std::swap(pa, pb);
+    }
+    if (st == KF_OK && pa != ord) cudaMemcpyAsync(ord, pa, bytes_p, cudaMemcpyDeviceToDevice, s);
+    // the ping-pong may have swapped the caller's buffer into pb: free the other one
+    if (pb == ord) pb = pa;
+  }
+  c->dfree(Xa, bytes_X, s);
+  c->dfree(Xb, bytes_X, s);
+  c->dfree(pb, bytes_p, s);
+  c->dfree(key, sizeof(double) * vcap, s);
+  c->dfree(orig, sizeof(int64_t) * vcap, s);
+  c->dfree(pos, sizeof(int32_t) * vcap, s);
+  c->dfree(ia, sizeof(int32_t) * 2 * maxnodes, s);
+  c->dfree(rlo, sizeof(int32_t) * nn_all, s);
+  c->dfree(rhi, sizeof(int32_t) * nn_all, s);
+  return st;
+}
+
 // kf_tree_perm_noalloc runs the same kernels as kf_tree_build_device but takes
 // every scratch buffer from one file-scope device array instead of the
 // allocator, and uses the caller's outputs as the other half of each
@@ -343,19 +458,6 @@ constexpr int64_t kNoAllocMaxN = 65536;
 constexpr int64_t kNoAllocMaxND = int64_t(1) << 19;
 constexpr size_t kNoAllocBytes = size_t(12) << 20;
 constexpr int kNoAllocMaxDevices = 64;
-
-__global__ void k_node_ranges(int64_t N, int D, int32_t* __restrict__ lo, int32_t* __restrict__ hi) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  lo[1] = 0;
-  hi[1] = (int32_t)N;
-  for (int a = 1; a < (1 << D); ++a) {
-    int32_t n = hi[a] - lo[a], mid = lo[a] + n / 2;
-    lo[2 * a] = lo[a];
-    hi[2 * a] = mid;
-    lo[2 * a + 1] = mid;
-    hi[2 * a + 1] = hi[a];
-  }
-}
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
