@@ -540,13 +540,15 @@ def gpu_main(args, rank, world):
                 ts.append(e0.elapsed_time(e1))
             return F, min(ts) / 1e3
         def solve_time(F):
+            # timed without the info record (which adds a residual evaluation); info from a second solve
             F.solve(b)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            x, inf = F.solve(b, info=True)
+            x = F.solve(b)
             e1.record()
             torch.cuda.synchronize()
+            _, inf = F.solve(b, info=True)
             return x, inf, e0.elapsed_time(e1) / 1e3
         Fr = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=kf.KF_PREC_FP64, fp64_operator=True,
                        refine_max_iter=30, refine_tol=1e-12, gmres_restart=30, sync_errors=False, **kn)
@@ -561,6 +563,11 @@ def gpu_main(args, rank, world):
                              gmres_restart=args.gmres_m, **opt(kf.KF_PREC_MIXED))
         xm, im, sm = solve_time(Fm)
         del Fm
+        # x += M^-1 r steps against the FP64-accurate operator until the residual is at the bar
+        Fs, _ = fact_time(kf.KF_PREC_MIXED, fp64_operator=True, refine_tol=args.near_rich_tol, refine_max_iter=20,
+                          gmres_restart=-1, **opt(kf.KF_PREC_MIXED))
+        xs_, is_, ss = solve_time(Fs)
+        del Fs
         Fu, _ = fact_time(kf.KF_PREC_MIXED, fp64_operator=False, refine_max_iter=-1, **opt(kf.KF_PREC_MIXED))
         xu, _, su = solve_time(Fu)
         del Fu, tree
@@ -570,6 +577,8 @@ def gpu_main(args, rank, world):
                          "rel_err_vs_reference": relr(x64)},
                 "mixed_at_1e-5": {"factorize_s": round(fm_s, 4), "solve_rhs_per_s": round(1 / sm, 2),
                                   "gmres_iters": im["iters"], "eps_r": im["eps_r"], "rel_err_vs_reference": relr(xm)},
+                "mixed_richardson": {"refine_tol": args.near_rich_tol, "solve_rhs_per_s": round(1 / ss, 2),
+                                     "steps": is_["iters"], "eps_r": is_["eps_r"], "rel_err_vs_reference": relr(xs_)},
                 "mixed_unrefined": {"solve_rhs_per_s": round(1 / su, 2), "rel_err_vs_reference": relr(xu)},
                 "note": "S' half from the nodes' near-field lists (kappa nearest neighbours by randomized "
                         "projection trees), half uniform; factorization times include the neighbour search"}
@@ -794,6 +803,9 @@ def gpu_main(args, rank, world):
             "near_field_mixed_solve_rhs_per_s_at_1e-5": near["mixed_at_1e-5"]["solve_rhs_per_s"] if near else None,
             "near_field_mixed_rel_err_at_1e-5": near["mixed_at_1e-5"]["rel_err_vs_reference"] if near else None,
             "near_field_mixed_factorize_s": near["mixed_at_1e-5"]["factorize_s"] if near else None,
+            "near_field_fp64_factorize_s": near["fp64"]["factorize_s"] if near else None,
+            "near_field_mixed_richardson_rhs_per_s": near["mixed_richardson"]["solve_rhs_per_s"] if near else None,
+            "near_field_mixed_richardson_rel_err": near["mixed_richardson"]["rel_err_vs_reference"] if near else None,
             "near_field_fp64_solve_rhs_per_s": near["fp64"]["solve_rhs_per_s"] if near else None,
             "near_field_mixed_unrefined_rel_err": near["mixed_unrefined"]["rel_err_vs_reference"] if near else None,
             "batched_mixed_max_rel_err_vs_fp64": batched["mixed"]["rel_err_vs_fp64"]["max"] if batched else None,
@@ -866,6 +878,8 @@ def main():
     ap.add_argument("--no-seed-study", action="store_true", help="skip the mixed solve at other sampler seeds")
     ap.add_argument("--no-near", action="store_true", help="skip the near-field sampling variant of the workload")
     ap.add_argument("--knn-kappa", type=int, default=16, help="neighbours per point of the near-field variant")
+    ap.add_argument("--near-rich-tol", type=float, default=2e-6,
+                    help="residual target of the near-field variant's x += M^-1 r solve")
     ap.add_argument("--no-autotune", action="store_true", help="default kernel variants instead of kf_autotune's")
     ap.add_argument("--batched-n", type=int, default=256, help="problems of the batched workload")
     ap.add_argument("--once", action="store_true",

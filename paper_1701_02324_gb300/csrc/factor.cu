@@ -24,6 +24,10 @@ kf_status kf_tc_zoff(const int32_t* lo, const int32_t* hi, const int32_t* rank, 
 kf_status kf_tc_telescope(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
                           const float* Pc_hat, const float* Tm, int ldz, float* Pa_hat, int64_t rows_per_child,
                           int32_t* status, cudaStream_t s, int tile_n);
+kf_status kf_tc_leaf_panel(const int32_t* lo, const int32_t* hi, int leaf0, int nleaf, int ldL, int kb, float* L,
+                           const float* Dinv, int32_t* status, cudaStream_t s);
+kf_status kf_tc_leaf_phat(const int32_t* lo, const int32_t* hi, const int32_t* rank, int leaf0, int nleaf, int ldL,
+                          float* L, const float* Dinv, int s_max, float* Y, int32_t* status, cudaStream_t s);
 
 namespace {
 
@@ -178,6 +182,106 @@ __global__ void __launch_bounds__(256) k_leaf_cholesky(const int32_t* __restrict
   }
   if (bad) atomicOr(status, KF_DEV_ILLCOND);
   if (tid == 0) pivr[node] = (n == 0 || amax == 0.0) ? 1.0 : fmax(minpiv, 0.0) / amax;
+}
+
+// ---- leaves on the tensor cores (mixed path) ---------------------------------------
+// Panel kb (128 columns) of every leaf's Cholesky factorization, one CTA per
+// leaf: the diagonal block L11 by an unblocked right-looking Cholesky in
+// shared memory, written back in place, and its inverse Linv = L11^-1 (lower;
+// column j by forward substitution) into the leaf's panel slot of Dinv, for
+// the tcgen05 products that form the panel rows below and the trailing update
+// (kf_tc_leaf_panel) and P^ (kf_tc_leaf_phat).  Pivots as k_leaf_cholesky: a
+// pivot at most 1e-14 times the largest diagonal entry flags KF_DEV_ILLCOND;
+// track[2 lf] keeps that entry, track[2 lf + 1] the smallest pivot so far.
+constexpr int kPanel = 128;
+__global__ void __launch_bounds__(256) k_chol_panel(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                    int leaf0, int ldL, float* __restrict__ Lall, int kb, int npan,
+                                                    float* __restrict__ Dinv, double* __restrict__ track,
+                                                    int32_t* __restrict__ status, double* __restrict__ pivr) {
+  extern __shared__ float pan[];
+  float(*Dm)[kPanel + 1] = (float(*)[kPanel + 1])pan;                         // L11
+  float(*Im)[kPanel + 1] = (float(*)[kPanel + 1])(pan + kPanel * (kPanel + 1));  // L11^-1
+  __shared__ float red[8];
+  __shared__ float lkk_sh;
+  __shared__ double amax_sh, minpiv_sh;
+  __shared__ int bad_sh;
+  const int lf = blockIdx.x, node = leaf0 + lf, tid = threadIdx.x;
+  const int n = hi[node] - lo[node], nb = min(kPanel, n - kb);
+  if (nb <= 0) return;
+  float* L = Lall + (int64_t)lf * ldL * ldL;
+  if (kb == 0) {  // max |diagonal| of A (FP32 compare; only a scale for the pivot test)
+    float mx = 0.f;
+    for (int i = tid; i < n; i += blockDim.x) mx = fmaxf(mx, fabsf(L[(int64_t)i * ldL + i]));
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      float m2 = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmaxf(m2, red[w]);
+      amax_sh = (double)m2;
+      minpiv_sh = INFINITY;
+    }
+  } else if (tid == 0) {
+    amax_sh = track[2 * lf];
+    minpiv_sh = track[2 * lf + 1];
+  }
+  if (tid == 0) bad_sh = 0;
+  for (int e = tid; e < kPanel * kPanel; e += blockDim.x) {
+    const int i = e / kPanel, j = e % kPanel;
+    Dm[i][j] = (i < nb && j <= i) ? L[(int64_t)(kb + i) * ldL + kb + j] : 0.f;
+    Im[i][j] = 0.f;
+  }
+  __syncthreads();
+  const double amax = amax_sh;
+  for (int k = 0; k < nb; ++k) {
+    if (tid == 0) {
+      float dkk = Dm[k][k];
+      minpiv_sh = fmin(minpiv_sh, (double)dkk);
+      if (!((double)dkk > 1e-14 * amax)) {
+        bad_sh = 1;
+        dkk = (float)(1e-14 * amax + 1e-30);
+      }
+      lkk_sh = sqrtf(dkk);
+      Dm[k][k] = lkk_sh;
+    }
+    __syncthreads();
+    const float lkk = lkk_sh;
+    for (int i = k + 1 + tid; i < nb; i += blockDim.x) Dm[i][k] = Dm[i][k] / lkk;
+    __syncthreads();
+    const int w = nb - k - 1;
+    for (int e = tid; e < w * w; e += blockDim.x) {
+      const int i = k + 1 + e / w, j = k + 1 + e % w;
+      if (j <= i) Dm[i][j] -= Dm[i][k] * Dm[j][k];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    if (j <= i) L[(int64_t)(kb + i) * ldL + kb + j] = Dm[i][j];
+  }
+  if (tid < nb) {  // column tid of L11^-1
+    const int j = tid;
+    Im[j][j] = 1.f / Dm[j][j];
+    for (int i = j + 1; i < nb; ++i) {
+      float acc = 0.f;
+      for (int t = j; t < i; ++t) acc = fmaf(Dm[i][t], Im[t][j], acc);
+      Im[i][j] = -acc / Dm[i][i];
+    }
+  }
+  __syncthreads();
+  float* Di = Dinv + ((int64_t)lf * npan + kb / kPanel) * kPanel * kPanel;
+  for (int e = tid; e < kPanel * kPanel; e += blockDim.x) Di[e] = Im[e / kPanel][e % kPanel];
+  if (tid == 0) {
+    if (bad_sh) atomicOr(status, KF_DEV_ILLCOND);
+    track[2 * lf] = amax;
+    track[2 * lf + 1] = minpiv_sh;
+    if (kb + nb >= n) pivr[node] = (n == 0 || amax == 0.0) ? 1.0 : fmax(minpiv_sh, 0.0) / amax;
+  }
+}
+
+__global__ void k_to_f32_rows(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
 }
 
 // P^ = L^-T L^-1 P for one leaf per CTA; rhs = Pleaf rows of the leaf (FP64,
@@ -1113,11 +1217,35 @@ kf_status leaves_t(kf_factor* f, cudaStream_t s, bool with_k64, int part) {
       kf_status r = kf_leaf_k64_launch(f, s);
       if (r != KF_OK) return r;
     }
-    KF_PHASE(KF_PH_LEAF_CHOL, s, k_leaf_cholesky<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, ldL, L, f->status, f->pivr));
+    if (sizeof(T) == 4 && f->Dinv) {  // mixed path on the tensor cores: 128-column panels
+      const size_t psm = sizeof(float) * 2 * kPanel * (kPanel + 1);
+      KF_CUDA(c, cudaFuncSetAttribute(k_chol_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+      const int npan = (ldL + kPanel - 1) / kPanel;
+      for (int kb = 0; kb < ldL; kb += kPanel) {
+        KF_PHASE(KF_PH_LEAF_CHOL, s, k_chol_panel<<<nleaf, 256, psm, s>>>(t->d_lo, t->d_hi, leaf0, ldL, (float*)L,
+                                                                        kb, npan, f->Dinv, f->ltrack, f->status,
+                                                                        f->pivr));
+        KF_LAUNCH_CHECK(c);
+        if (kf_tc_leaf_panel(t->d_lo, t->d_hi, leaf0, nleaf, ldL, kb, (float*)L, f->Dinv, f->status, s) != KF_OK)
+          return kf_set_err(c, KF_ECUDA, "leaf panel products: %s", cudaGetErrorString(cudaGetLastError()));
+      }
+    } else {
+      KF_PHASE(KF_PH_LEAF_CHOL, s, k_leaf_cholesky<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, leaf0, ldL, L, f->status, f->pivr));
+    }
   }
-  if (D > 0 && part != 1)
-    KF_PHASE(KF_PH_LEAF_PHAT, s, k_leaf_phat<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, leaf0, ldL, L, f->Pleaf, s_max,
-                                                                  Phat + (int64_t)(D - 1) * N * s_max));
+  if (D > 0 && part != 1) {
+    T* PhD = Phat + (int64_t)(D - 1) * N * s_max;
+    if (sizeof(T) == 4 && f->Dinv) {
+      KF_PHASE(KF_PH_LEAF_PHAT, s, k_to_f32_rows<<<grid_for(N * s_max, 256), 256, 0, s>>>(f->Pleaf, (float*)PhD,
+                                                                                        N * s_max));
+      if (kf_tc_leaf_phat(t->d_lo, t->d_hi, f->rank, leaf0, nleaf, ldL, (float*)L, f->Dinv, s_max, (float*)PhD,
+                          f->status, s) != KF_OK)
+        return kf_set_err(c, KF_ECUDA, "leaf P^ products: %s", cudaGetErrorString(cudaGetLastError()));
+    } else {
+      KF_PHASE(KF_PH_LEAF_PHAT, s, k_leaf_phat<T><<<nleaf, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, leaf0, ldL, L,
+                                                                        f->Pleaf, s_max, PhD));
+    }
+  }
   KF_LAUNCH_CHECK(c);
   return KF_OK;
 }

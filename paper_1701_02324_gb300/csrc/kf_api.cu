@@ -333,6 +333,15 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
       return kf_set_err(c, KF_ENOMEM, "factorize: device allocation of the FP64 operator failed");
     }
   }
+  if (f->prec == KF_PREC_MIXED && f->use_tc) {  // leaf factorization on the tensor cores
+    const size_t npan = ((size_t)t->leaf_max + 127) / 128;
+    f->Dinv = falloc<float>(f, ((size_t)1 << D) * npan * 128 * 128, s);
+    f->ltrack = falloc<double>(f, ((size_t)1 << D) * 2, s);
+    if (!f->Dinv || !f->ltrack) {
+      kf_factor_free(f);
+      return kf_set_err(c, KF_ENOMEM, "factorize: device allocation of the leaf panels failed");
+    }
+  }
   if (f->knn_kappa > 0) {
     f->near_cap = f->n_samp / 2;
     f->nbr = falloc<int32_t>(f, (size_t)N * f->knn_kappa, s);

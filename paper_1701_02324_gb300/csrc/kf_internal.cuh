@@ -115,6 +115,10 @@ struct kf_factor {
   int32_t* near_pos = nullptr;
   int32_t* near_cnt = nullptr;
   int32_t* near_len = nullptr;
+  // mixed path with tcgen05 products: inverses of the leaves' 128 x 128
+  // diagonal Cholesky blocks (leaf, panel) and per-leaf pivot tracking
+  float* Dinv = nullptr;
+  double* ltrack = nullptr;
   int32_t* status = nullptr;
   double* pivr = nullptr;  // per node: smallest / largest pivot of its leaf Cholesky or Z LU
   std::vector<std::pair<void*, size_t>> allocs;

@@ -9,8 +9,10 @@
 //     16 bytes per core matrix; LBO = 128 B between core matrices along K,
 //     SBO = 1024 B between 8-row groups), split into tf32 hi and lo parts;
 //   * one thread issues tcgen05.mma kind::tf32 for A_hi B_hi + A_hi B_lo +
-//     A_lo B_hi (3xTF32: about FP32 accuracy) into an FP32 accumulator in
-//     tensor memory, and tcgen05.commit arrives on an mbarrier;
+//     A_lo B_hi (3xTF32, about 2^-22 relative) into an FP32 accumulator in
+//     tensor memory -- or, for problems with three operand pieces, the six
+//     products that reach the FP32 rounding level -- and tcgen05.commit
+//     arrives on an mbarrier;
 //   * the epilogue reads the accumulator with tcgen05.ld (warp w reads lane
 //     quadrant w mod 4, rows 32(w mod 4)..+31, and a quarter of the columns)
 //     and hands each value to the problem's store.
@@ -159,9 +161,15 @@ __device__ __forceinline__ void tile_coord(int e, int rows, int& r, int& k) {
   k = (g / rg) * 4 + kl;
 }
 
+// Operand pieces: Problem::kPieces = 2 splits every value into tf32 hi + lo
+// (3 MMAs per product: hi hi + hi lo + lo hi, about 2^-22 relative); 3 splits
+// it into hi + mid + lo (6 MMAs: hi hi + hi mid + mid hi + hi lo + lo hi +
+// mid mid, the FP32 rounding level) for the products whose errors the
+// factorization amplifies most (the leaves).  A stage holds the pieces of A
+// then those of B, each kBM x kBK (A) or BN x kBK (B) floats.
 template <class Problem, int BN>
-__device__ __forceinline__ void stage_chunk(const Problem& prob, const Tile& t, int kc, float* Ahi, float* Alo,
-                                            float* Bhi, float* Blo) {
+__device__ __forceinline__ void stage_chunk(const Problem& prob, const Tile& t, int kc, float* As, float* Bs) {
+  constexpr int P = Problem::kPieces;
   const int tid = threadIdx.x;
   const int kn = min(kBK, t.k1 - kc);
   // all global loads of the chunk first (in flight together), then the split
@@ -183,39 +191,61 @@ __device__ __forceinline__ void stage_chunk(const Problem& prob, const Tile& t, 
   for (int q = 0; q < NA; ++q) {
     int m, k;
     tile_coord<Problem::a_m_fastest>(tid + q * kThreads, kBM, m, k);
-    const float hi = to_tf32(va[q]);
     const int o = core_off(m, k);
-    Ahi[o] = hi;
-    Alo[o] = to_tf32(va[q] - hi);
+    const float hi = to_tf32(va[q]), r1 = va[q] - hi;  // r1 exact
+    if (P == 2) {
+      As[o] = hi;
+      As[kBM * kBK + o] = to_tf32(r1);
+    } else {
+      const float mid = to_tf32(r1);
+      As[o] = hi;
+      As[kBM * kBK + o] = mid;
+      As[2 * kBM * kBK + o] = to_tf32(r1 - mid);
+    }
   }
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     int n, k;
     tile_coord<Problem::b_n_fastest>(tid + q * kThreads, BN, n, k);
-    const float hi = to_tf32(vb[q]);
     const int o = core_off(n, k);
-    Bhi[o] = hi;
-    Blo[o] = to_tf32(vb[q] - hi);
+    const float hi = to_tf32(vb[q]), r1 = vb[q] - hi;
+    if (P == 2) {
+      Bs[o] = hi;
+      Bs[BN * kBK + o] = to_tf32(r1);
+    } else {
+      const float mid = to_tf32(r1);
+      Bs[o] = hi;
+      Bs[BN * kBK + o] = mid;
+      Bs[2 * BN * kBK + o] = to_tf32(r1 - mid);
+    }
   }
 }
 
-__device__ __forceinline__ void issue_chunk(uint32_t tmem, uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl,
-                                            uint32_t idesc, bool first) {
+template <int P, int BN>
+__device__ __forceinline__ void issue_chunk(uint32_t tmem, uint32_t as, uint32_t bs, uint32_t idesc, bool first) {
+  constexpr uint32_t sa = kBM * kBK * 4, sb = BN * kBK * 4;  // bytes between pieces
 #pragma unroll
   for (int kk = 0; kk < kBK / 8; ++kk) {
     const uint32_t off = kk * 256;  // two core matrices along K per MMA (K = 8 tf32)
-    const uint64_t dah = smem_desc(ah + off, 128, 1024), dal = smem_desc(al + off, 128, 1024);
-    const uint64_t dbh = smem_desc(bh + off, 128, 1024), dbl = smem_desc(bl + off, 128, 1024);
-    mma_tf32(tmem, dah, dbh, idesc, (first && kk == 0) ? 0u : 1u);
-    mma_tf32(tmem, dah, dbl, idesc, 1u);
-    mma_tf32(tmem, dal, dbh, idesc, 1u);
+    const uint64_t a0 = smem_desc(as + off, 128, 1024), a1 = smem_desc(as + sa + off, 128, 1024);
+    const uint64_t b0 = smem_desc(bs + off, 128, 1024), b1 = smem_desc(bs + sb + off, 128, 1024);
+    mma_tf32(tmem, a0, b0, idesc, (first && kk == 0) ? 0u : 1u);
+    mma_tf32(tmem, a0, b1, idesc, 1u);
+    mma_tf32(tmem, a1, b0, idesc, 1u);
+    if (P == 3) {
+      const uint64_t a2 = smem_desc(as + 2 * sa + off, 128, 1024), b2 = smem_desc(bs + 2 * sb + off, 128, 1024);
+      mma_tf32(tmem, a0, b2, idesc, 1u);
+      mma_tf32(tmem, a2, b0, idesc, 1u);
+      mma_tf32(tmem, a1, b1, idesc, 1u);
+    }
   }
 }
 
 template <int BN, class Problem>
 __global__ void __launch_bounds__(kThreads) k_tc_gemm(Problem prob, int32_t* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  constexpr int kStage = 2 * kBM * kBK + 2 * BN * kBK;  // floats per stage
+  constexpr int P = Problem::kPieces;
+  constexpr int kStage = P * kBM * kBK + P * BN * kBK;  // floats per stage
   __shared__ __align__(8) uint64_t mbar[3];  // two stages; [2] only for the time-out probe
   __shared__ uint32_t tmem_base;
   __shared__ int probe_timed_out;
@@ -248,10 +278,8 @@ __global__ void __launch_bounds__(kThreads) k_tc_gemm(Problem prob, int32_t* __r
   int c = 0;
   for (int kc = t.k0; kc < t.k1 && ok; kc += kBK, ++c) {
     const int st = c & 1;
-    float* Ahi = (float*)smem_raw + st * kStage;
-    float* Alo = Ahi + kBM * kBK;
-    float* Bhi = Alo + kBM * kBK;
-    float* Blo = Bhi + BN * kBK;
+    float* As = (float*)smem_raw + st * kStage;
+    float* Bs = As + P * kBM * kBK;
     if (uses[st] > 0) {  // the MMAs that read this stage two chunks ago must be done
       if (!mbar_wait(&mbar[st], (uses[st] - 1) & 1u)) {
         ok = false;
@@ -259,12 +287,12 @@ __global__ void __launch_bounds__(kThreads) k_tc_gemm(Problem prob, int32_t* __r
         break;
       }
     }
-    stage_chunk<Problem, BN>(prob, t, kc, Ahi, Alo, Bhi, Blo);
+    stage_chunk<Problem, BN>(prob, t, kc, As, Bs);
     fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
       fence_after_sync();
-      issue_chunk(tmem, smem_u32(Ahi), smem_u32(Alo), smem_u32(Bhi), smem_u32(Blo), idesc, kc == t.k0);
+      issue_chunk<P, BN>(tmem, smem_u32(As), smem_u32(Bs), idesc, kc == t.k0);
       mma_commit(&mbar[st]);
     }
     ++uses[st];
@@ -311,6 +339,7 @@ __global__ void __launch_bounds__(kThreads) k_tc_gemm(Problem prob, int32_t* __r
 // The long reduction over the child's rows is split over blockIdx.y; partial
 // tiles are added into the FP64 Z with atomics.
 struct ZoffProblem {
+  static constexpr int kPieces = 2;
   static constexpr bool a_m_fastest = true;   // VT rows are contiguous in m
   static constexpr bool b_n_fastest = true;   // P^ rows are contiguous in n
   const int32_t* lo;
@@ -348,6 +377,7 @@ struct ZoffProblem {
 
 // ---- telescoping: P^_a[rows of c, :s_a] = P^_c[:, :s_c] T[c block, :s_a] ---------
 struct TelescopeProblem {
+  static constexpr int kPieces = 2;
   static constexpr bool a_m_fastest = false;  // P^_c rows are contiguous in k
   static constexpr bool b_n_fastest = true;   // T rows are contiguous in n
   const int32_t* lo;
@@ -380,10 +410,151 @@ struct TelescopeProblem {
   __device__ void store(const Tile&, int m, int n, float v) const { Pa_hat[(int64_t)m * s_max + n] = v; }
 };
 
+// ---- leaf factorization on the tensor cores (mixed path) --------------------------
+// The leaf blocks A = lambda I + K_aa are factorized A = L L^T by 128-column
+// panels kb: the panel's diagonal block L11 and its inverse Linv are formed on
+// CUDA cores (k_chol_panel, factor.cu); these products do the rest.  Leaf lf's
+// matrix is L + lf * ldL^2 (row-major, lower triangle); its panels' inverses
+// are Dinv + (lf * npan + kb / 128) * 128^2 (row-major, 128 x 128).
+struct LeafPanel {
+  static constexpr int kPieces = 3;  // FP32-level products: the leaves' errors are the most amplified
+  const int32_t* lo;
+  const int32_t* hi;
+  int leaf0, ldL, kb, npan;
+  float* L;
+  const float* Dinv;
+  __device__ int size(int lf) const { return hi[leaf0 + lf] - lo[leaf0 + lf]; }
+  __device__ float* Lm(int lf) const { return L + (int64_t)lf * ldL * ldL; }
+  __device__ const float* Di(int lf) const { return Dinv + ((int64_t)lf * npan + kb / kBM) * kBM * kBM; }
+};
+
+// L21 = A21 Linv^T: rows kb + nb .. n - 1 of the panel columns, in place
+struct LeafTrsmProblem : LeafPanel {
+  static constexpr bool a_m_fastest = false;
+  static constexpr bool b_n_fastest = false;
+  __device__ Tile tile(int bx, int, int bz) const {
+    Tile t;
+    t.node = bz;
+    const int n = size(bz), nb = min(kBM, n - kb);
+    t.base = nb;
+    t.M = n - kb - nb;
+    t.N = nb;
+    t.m0 = bx * kBM;
+    t.n0 = 0;
+    t.k0 = 0;
+    t.k1 = nb;
+    t.skip = nb <= 0 || t.M <= 0 || t.m0 >= t.M;
+    return t;
+  }
+  __device__ float loadA(const Tile& t, int m, int k) const {
+    return Lm(t.node)[(int64_t)(kb + t.base + m) * ldL + kb + k];
+  }
+  __device__ float loadB(const Tile& t, int k, int n) const { return Di(t.node)[n * kBM + k]; }
+  __device__ void store(const Tile& t, int m, int n, float v) const {
+    Lm(t.node)[(int64_t)(kb + t.base + m) * ldL + kb + n] = v;
+  }
+};
+
+// A22 -= L21 L21^T on the lower triangle (tiles wholly above the diagonal skipped)
+struct LeafSyrkProblem : LeafPanel {
+  static constexpr bool a_m_fastest = false;
+  static constexpr bool b_n_fastest = false;
+  int tile_n;
+  __device__ Tile tile(int bx, int by, int bz) const {
+    Tile t;
+    t.node = bz;
+    const int n = size(bz), nb = min(kBM, n - kb);
+    t.base = nb;
+    t.M = t.N = n - kb - nb;
+    t.m0 = bx * kBM;
+    t.n0 = by * tile_n;
+    t.k0 = 0;
+    t.k1 = nb;
+    t.skip = nb <= 0 || t.M <= 0 || t.m0 >= t.M || t.n0 >= t.N || t.n0 > t.m0 + kBM - 1;
+    return t;
+  }
+  __device__ float loadA(const Tile& t, int m, int k) const {
+    return Lm(t.node)[(int64_t)(kb + t.base + m) * ldL + kb + k];
+  }
+  __device__ float loadB(const Tile& t, int k, int n) const {
+    return Lm(t.node)[(int64_t)(kb + t.base + n) * ldL + kb + k];
+  }
+  __device__ void store(const Tile& t, int m, int n, float v) const {
+    if (n <= m) Lm(t.node)[(int64_t)(kb + t.base + m) * ldL + kb + t.base + n] -= v;
+  }
+};
+
+// P^ = L^-T L^-1 P on Y = the leaf rows of P^ (stride s_max, rank s columns):
+// Y_i = Linv_i Y_i (TRANS: Linv_i^T Y_i), in place on the panel's rows
+template <bool TRANS>
+struct PhatDinvProblem : LeafPanel {
+  static constexpr bool a_m_fastest = TRANS;
+  static constexpr bool b_n_fastest = true;
+  const int32_t* rank;
+  int s_max, tile_n;
+  float* Y;
+  __device__ Tile tile(int, int by, int bz) const {
+    Tile t;
+    t.node = bz;
+    const int n = size(bz), nb = min(kBM, n - kb);
+    t.base = lo[leaf0 + bz];
+    t.M = nb;
+    t.N = rank[leaf0 + bz];
+    t.m0 = 0;
+    t.n0 = by * tile_n;
+    t.k0 = 0;
+    t.k1 = nb;
+    t.skip = nb <= 0 || t.N <= 0 || t.n0 >= t.N;
+    return t;
+  }
+  __device__ float loadA(const Tile& t, int m, int k) const {
+    return TRANS ? Di(t.node)[k * kBM + m] : Di(t.node)[m * kBM + k];
+  }
+  __device__ float loadB(const Tile& t, int k, int n) const { return Y[(int64_t)(t.base + kb + k) * s_max + n]; }
+  __device__ void store(const Tile& t, int m, int n, float v) const { Y[(int64_t)(t.base + kb + m) * s_max + n] = v; }
+};
+
+// ABOVE = false: Y[kb+nb+m] -= L[kb+nb+m][kb..kb+nb) Y_i (forward substitution);
+// ABOVE = true:  Y[m] -= L[kb..kb+nb)[m]^T Y_i for m < kb (backward)
+template <bool ABOVE>
+struct PhatUpdateProblem : LeafPanel {
+  static constexpr bool a_m_fastest = ABOVE;
+  static constexpr bool b_n_fastest = true;
+  const int32_t* rank;
+  int s_max, tile_n;
+  float* Y;
+  __device__ Tile tile(int bx, int by, int bz) const {
+    Tile t;
+    t.node = bz;
+    const int n = size(bz), nb = min(kBM, n - kb);
+    t.base = lo[leaf0 + bz];
+    t.M = ABOVE ? kb : n - kb - nb;
+    t.N = rank[leaf0 + bz];
+    t.m0 = bx * kBM;
+    t.n0 = by * tile_n;
+    t.k0 = 0;
+    t.k1 = nb;
+    t.skip = nb <= 0 || t.M <= 0 || t.N <= 0 || t.m0 >= t.M || t.n0 >= t.N;
+    return t;
+  }
+  __device__ float loadA(const Tile& t, int m, int k) const {
+    const int nb = min(kBM, size(t.node) - kb);
+    return ABOVE ? Lm(t.node)[(int64_t)(kb + k) * ldL + m] : Lm(t.node)[(int64_t)(kb + nb + m) * ldL + kb + k];
+  }
+  __device__ float loadB(const Tile& t, int k, int n) const { return Y[(int64_t)(t.base + kb + k) * s_max + n]; }
+  __device__ void store(const Tile& t, int m, int n, float v) const {
+    const int nb = min(kBM, size(t.node) - kb);
+    const int row = ABOVE ? m : kb + nb + m;
+    Y[(int64_t)(t.base + row) * s_max + n] -= v;
+  }
+};
+
 }  // namespace
 
 // ---- launchers ---------------------------------------------------------------------
-static size_t tc_smem_bytes(int BN) { return 2 * sizeof(float) * (size_t)(2 * kBM * kBK + 2 * BN * kBK); }
+static size_t tc_smem_bytes(int BN, int pieces = 2) {
+  return 2 * sizeof(float) * (size_t)pieces * (kBM * kBK + BN * kBK);
+}
 
 template <int BN>
 static kf_status tc_zoff_bn(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
@@ -438,6 +609,74 @@ kf_status kf_tc_telescope(const int32_t* lo, const int32_t* hi, const int32_t* r
   return tile_n == 128
              ? tc_telescope_bn<128>(lo, hi, rank, node0, nn, s_max, Pc_hat, Tm, ldz, Pa_hat, rows_per_child, status, s)
              : tc_telescope_bn<256>(lo, hi, rank, node0, nn, s_max, Pc_hat, Tm, ldz, Pa_hat, rows_per_child, status, s);
+}
+
+template <int BN, class Problem>
+static kf_status tc_launch(const Problem& p, dim3 g, int phase, int32_t* status, cudaStream_t s) {
+  const size_t smem = tc_smem_bytes(BN, Problem::kPieces);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN, Problem>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return KF_ECUDA;
+  KF_PHASE(phase, s, k_tc_gemm<BN, Problem><<<g, kThreads, smem, s>>>(p, status));
+  return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
+}
+
+// Panel kb of the leaves' Cholesky factorization after k_chol_panel: the
+// panel rows below the diagonal block (L21 = A21 Linv^T), then the trailing
+// update A22 -= L21 L21^T.  nleaf leaves of at most ldL rows.
+kf_status kf_tc_leaf_panel(const int32_t* lo, const int32_t* hi, int leaf0, int nleaf, int ldL, int kb, float* L,
+                           const float* Dinv, int32_t* status, cudaStream_t s) {
+  const int npan = (ldL + kBM - 1) / kBM;
+  const int rows = ldL - kb - kBM;  // the most rows below the panel
+  if (rows <= 0) return KF_OK;
+  const unsigned mt = (unsigned)((rows + kBM - 1) / kBM);
+  LeafTrsmProblem pt;
+  pt.lo = lo; pt.hi = hi; pt.leaf0 = leaf0; pt.ldL = ldL; pt.kb = kb; pt.npan = npan; pt.L = L; pt.Dinv = Dinv;
+  kf_status st = tc_launch<128>(pt, dim3(mt, 1, (unsigned)nleaf), KF_PH_LEAF_CHOL, status, s);
+  if (st != KF_OK) return st;
+  LeafSyrkProblem py;
+  static_cast<LeafPanel&>(py) = pt;
+  py.tile_n = 128;
+  return tc_launch<128>(py, dim3(mt, mt, (unsigned)nleaf), KF_PH_LEAF_CHOL, status, s);
+}
+
+// P^ = L^-T L^-1 P for the leaves on the tensor cores: Y (the leaf rows of P^
+// of the leaf level, FP32, holding P on entry) is solved in place panel by
+// panel, forward then backward.
+kf_status kf_tc_leaf_phat(const int32_t* lo, const int32_t* hi, const int32_t* rank, int leaf0, int nleaf, int ldL,
+                          float* L, const float* Dinv, int s_max, float* Y, int32_t* status, cudaStream_t s) {
+  const int npan = (ldL + kBM - 1) / kBM;
+  const int BN = 128;
+  const unsigned nt = (unsigned)((s_max + BN - 1) / BN);
+  LeafPanel base;
+  base.lo = lo; base.hi = hi; base.leaf0 = leaf0; base.ldL = ldL; base.npan = npan; base.L = L; base.Dinv = Dinv;
+  kf_status st = KF_OK;
+  for (int pi = 0; pi < npan && st == KF_OK; ++pi) {  // forward: L Y = P
+    base.kb = pi * kBM;
+    PhatDinvProblem<false> pd;
+    static_cast<LeafPanel&>(pd) = base;
+    pd.rank = rank; pd.s_max = s_max; pd.tile_n = BN; pd.Y = Y;
+    st = tc_launch<128>(pd, dim3(1, nt, (unsigned)nleaf), KF_PH_LEAF_PHAT, status, s);
+    const int rows = ldL - base.kb - kBM;
+    if (st != KF_OK || rows <= 0) continue;
+    PhatUpdateProblem<false> pu;
+    static_cast<LeafPanel&>(pu) = base;
+    pu.rank = rank; pu.s_max = s_max; pu.tile_n = BN; pu.Y = Y;
+    st = tc_launch<128>(pu, dim3((unsigned)((rows + kBM - 1) / kBM), nt, (unsigned)nleaf), KF_PH_LEAF_PHAT, status, s);
+  }
+  for (int pi = npan - 1; pi >= 0 && st == KF_OK; --pi) {  // backward: L^T X = Y
+    base.kb = pi * kBM;
+    PhatDinvProblem<true> pd;
+    static_cast<LeafPanel&>(pd) = base;
+    pd.rank = rank; pd.s_max = s_max; pd.tile_n = BN; pd.Y = Y;
+    st = tc_launch<128>(pd, dim3(1, nt, (unsigned)nleaf), KF_PH_LEAF_PHAT, status, s);
+    if (st != KF_OK || base.kb == 0) continue;
+    PhatUpdateProblem<true> pu;
+    static_cast<LeafPanel&>(pu) = base;
+    pu.rank = rank; pu.s_max = s_max; pu.tile_n = BN; pu.Y = Y;
+    st = tc_launch<128>(pu, dim3((unsigned)((base.kb + kBM - 1) / kBM), nt, (unsigned)nleaf), KF_PH_LEAF_PHAT,
+                        status, s);
+  }
+  return st;
 }
 
 extern "C" kf_status kf_test_tc_wait_probe(int64_t polls) {

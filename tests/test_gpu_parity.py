@@ -560,3 +560,39 @@ def test_profile_totals_and_timeline(c1):
         assert lib.kf_profile_timeline(None, None, None, None, 0, ctypes.byref(bad)) == _abi.KF_EINVAL
     finally:
         lib.kf_profile_enable(0)
+
+
+@pytest.mark.parametrize("N,d,m,smax", [(3001, 5, 300, 48), (4096, 8, 1024, 64), (2200, 3, 140, 32)])
+def test_leaf_factorization_on_tensor_cores(N, d, m, smax):
+    """Row a4 on the mixed path: the leaves' Cholesky factors by 128-column
+    panels (diagonal block and its inverse on CUDA cores, panel rows and
+    trailing updates as tcgen05 3xTF32 products) and P^ = A^-1 P by panel
+    products with those inverses, against the oracle's FP64 P^ of every leaf
+    (LU of lambda I + K_aa) at FP32 accuracy scaled by cond(A): ragged leaves of
+    1, 2 and 8 panels.  The pivot ratios agree with the CUDA-core kernels'."""
+    rng = np.random.default_rng(N)
+    X = rng.random((N, d))
+    h, lam, tau = 0.4, 0.5, 1e-6
+    o = oracle.Oracle(X, m)
+    o.skeletonize(h, tau, smax)
+    o.factorize(lam)
+    tree = kf.Tree(torch.from_numpy(X).cuda(), m)
+    Ft = kf.Factor(tree, h, lam, tau, smax, precision=MIXED, refine_max_iter=-1)
+    Fc = kf.Factor(tree, h, lam, tau, smax, precision=MIXED, refine_max_iter=-1, tensor_cores=False)
+    Xt = X[o.perm()]
+    for a in range(1 << o.D, 1 << (o.D + 1)):
+        lo, hi = o.node_range(a)
+        Y = Xt[lo:hi]
+        A = lam * np.eye(hi - lo) + np.exp(-0.5 * ((Y[:, None, :] - Y[None, :, :]) ** 2).sum(-1) / h**2)
+        cond = np.linalg.cond(A)
+        ref = o.Phat(a)
+        if ref.size == 0:
+            continue
+        assert rel(Ft.Phat(a, hi - lo), ref) <= 2e-7 * cond, a
+        assert rel(Fc.Phat(a, hi - lo), ref) <= 2e-7 * cond, a
+    pt, pc = Ft.pivot_ratios(), Fc.pivot_ratios()
+    leaves = slice(1 << o.D, 1 << (o.D + 1))
+    assert np.allclose(pt[leaves], pc[leaves], rtol=1e-3)
+    b = rng.standard_normal(N)
+    G = kf.Factor(tree, h, lam, tau, smax, precision=MIXED, refine_tol=1e-11)
+    assert rel(G.solve(torch.from_numpy(b).cuda()).cpu().numpy(), o.solve(b)) <= 1e-8
