@@ -127,7 +127,13 @@ typedef struct {
                              uniformly.  Needs leaf size x kappa <= 16384 (else KF_EUNSUPPORTED). */
   int32_t knn_trees;      /* projection trees of the neighbour search (0 = 4) */
   int32_t knn_leaf;       /* their leaf size, 2..1024 (0 = 512) */
-  int32_t reserved[3];
+  int32_t zoff_fused;     /* mixed path with tcgen05 products: 0 = the Z off-diagonal blocks K_{l~ r} P^_r
+                             read the stored V blocks (default); 1 = they evaluate their kernel entries
+                             inside the product (kernel summation fused with the weights, Sec. II-D):
+                             FP32 squared distances of the FP32 coordinates and a fast exponential,
+                             so the entries carry ~1e-6 relative error instead of FP32 rounding, and
+                             the reduced systems no longer wait for the V blocks */
+  int32_t reserved[2];
 } kf_opts;
 
 /* Filled by kf_solve when non-NULL (synchronizes the stream). */

@@ -39,7 +39,8 @@ class kf_opts(ctypes.Structure):
         ("knn_kappa", ctypes.c_int32),
         ("knn_trees", ctypes.c_int32),
         ("knn_leaf", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("zoff_fused", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 

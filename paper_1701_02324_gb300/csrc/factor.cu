@@ -24,6 +24,9 @@ kf_status kf_tc_zoff(const int32_t* lo, const int32_t* hi, const int32_t* rank, 
 kf_status kf_tc_telescope(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
                           const float* Pc_hat, const float* Tm, int ldz, float* Pa_hat, int64_t rows_per_child,
                           int32_t* status, cudaStream_t s, int tile_n);
+kf_status kf_tc_zoff_fused(const int32_t* lo, const int32_t* hi, const int32_t* rank, const int32_t* skel,
+                           const float* X32, int d, float c_exp, int node0, int nn, int s_max, const float* Ph,
+                           int ldz, double* Z, int64_t rows_per_child, int32_t* status, cudaStream_t s, int tile_n);
 kf_status kf_tc_leaf_panel(const int32_t* lo, const int32_t* hi, int leaf0, int nleaf, int ldL, int kb, float* L,
                            const float* Dinv, int32_t* status, cudaStream_t s);
 kf_status kf_tc_leaf_phat(const int32_t* lo, const int32_t* hi, const int32_t* rank, int leaf0, int nleaf, int ldL,
@@ -1307,7 +1310,11 @@ kf_status level_reduce(kf_factor* f, int l, double* Tm, cudaStream_t s) {
   const int tiles = ((s_max + 63) / 64) * ((s_max + 63) / 64);
   const int64_t rows = N >> (l + 1);
   int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(rows / 512, (152 * 8) / std::max(1, 2 * nn * tiles) + 1));
-  if (sizeof(T) == 4 && f->use_tc) {
+  if (sizeof(T) == 4 && f->use_tc && f->fused_zoff) {  // kernel entries evaluated inside the product
+    kf_status r = kf_tc_zoff_fused(t->d_lo, t->d_hi, f->rank, f->skel, t->X32, t->d, f->c_exp_hi, node0, nn, s_max,
+                                   (const float*)lvl(Phat, l + 1), ldz, f->ZLU, rows, f->status, s, f->tc_bn);
+    if (r != KF_OK) return kf_set_err(c, r, "tensor-core Z blocks failed at level %d", l);
+  } else if (sizeof(T) == 4 && f->use_tc) {
     kf_status r = kf_tc_zoff(t->d_lo, t->d_hi, f->rank, node0, nn, s_max, (const float*)lvl(VT, l + 1),
                              (const float*)lvl(Phat, l + 1), ldz, f->ZLU, rows, f->status, s, f->tc_bn);
     if (r != KF_OK) return kf_set_err(c, r, "tensor-core Z blocks failed at level %d", l);
@@ -1521,7 +1528,8 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
       if (l == D) {
         st = kf_factorize_leaves(f, s2, false, 2);
       } else {
-        cudaStreamWaitEvent(s2, evv[l], 0);
+        // the stored V blocks feed the Z blocks unless the product evaluates them itself
+        if (!kf_zoff_fused(f)) cudaStreamWaitEvent(s2, evv[l], 0);
         st = kf_factorize_level_z(f, l, Tm, s2);
         if (st == KF_OK && l <= f->zinv_top) {
           cudaEventRecord(evz[l], s2);
@@ -1531,7 +1539,7 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
       }
     }
     if (st == KF_OK && Lh == 0) {
-      cudaStreamWaitEvent(s2, evv[0], 0);
+      if (!kf_zoff_fused(f)) cudaStreamWaitEvent(s2, evv[0], 0);
       st = kf_factorize_level_z(f, 0, Tm, s2);
       if (st == KF_OK) {
         cudaEventRecord(evz[0], s2);

@@ -260,6 +260,7 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
     if (opts->zinv_max_nodes != 0) f->zinv_max_nodes = opts->zinv_max_nodes > 0 ? opts->zinv_max_nodes : -1;
     f->hyb_L = opts->hybrid_level;
     f->knn_kappa = opts->knn_kappa;
+    f->fused_zoff = opts->zoff_fused ? 1 : 0;
     if (opts->knn_trees > 0) f->knn_trees = opts->knn_trees;
     if (opts->knn_leaf > 0) f->knn_leaf = opts->knn_leaf;
     if (opts->tc_tile_n == 128) f->tc_bn = 128;

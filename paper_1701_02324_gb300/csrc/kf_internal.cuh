@@ -63,6 +63,7 @@ struct kf_factor {
   float c_exp_hi = 0, c_exp_lo = 0;  // c_exp as a double-float pair
   int32_t s_max = 0, n_samp = 0, cmax = 0, prec = 0, vstore = 0, sync_errors = 0;
   int32_t use_tc = 1;  // mixed path: tcgen05 products (0: CUDA-core FP32)
+  int32_t fused_zoff = 0;  // mixed path with tcgen05: 1 = Z blocks evaluate their kernel entries (no V read)
   int32_t tc_bn = 256; // tile width of the tcgen05 products: 128 or 256 columns
   int32_t use_cluster_qr = 1;  // upper tree levels: cluster QR in distributed shared memory
   int32_t use_cluster_lu = 1;  // upper tree levels: reduced-system LU and T on a CTA cluster per node
@@ -360,3 +361,7 @@ kf_status kf_rowupd_level_launch(kf_factor* f, int l, const double* V, double* W
 kf_status kf_rp_order(kf_tree* t, int tidx, int Dk, uint64_t seed, int64_t* ord, cudaStream_t s);
 // f->nbr and the node lists f->near_* from the tree (stream order)
 kf_status kf_near_field_lists(kf_factor* f, cudaStream_t s);
+
+// whether the Z off-diagonal blocks evaluate their kernel entries inside the
+// tcgen05 product (mixed path) instead of reading the stored V blocks
+inline bool kf_zoff_fused(const kf_factor* f) { return f->prec == KF_PREC_MIXED && f->use_tc && f->fused_zoff; }

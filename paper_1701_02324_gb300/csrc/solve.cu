@@ -20,6 +20,7 @@
 //   non-root c, y_c += K_{c sib~} g[sib] (the transpose of K~_{sib c} =
 //   P_{sib sib~} K_{sib~ c}).
 #include <algorithm>
+#include <cstring>
 
 #include "kf_internal.cuh"
 #include "prof.cuh"
@@ -180,28 +181,169 @@ __global__ void __launch_bounds__(kLeafSolveThreads, sizeof(TM) == 4 ? 8 : 4) k_
   }
 }
 
+// Several right-hand sides per pass (k >= 2): the leaf's KC columns of the
+// right-hand side stay in shared memory for the whole forward and backward
+// sweep, so that L is streamed once per KC columns instead of once per column
+// and every loaded entry of L serves KC products.  Per 32-row block the
+// diagonal block is staged in shared memory and each warp solves KC / 8 of its
+// columns with shuffles; then every thread updates one row of the rest of the
+// leaf for all KC columns (forward: row i of L, entries kb..kb+31; backward:
+// column i of L, a coalesced read across the threads).  Per column the
+// operations and their order are those of k_leaf_solve.  Shared-memory rows
+// are KC + 16 / sizeof(TV) values long (a 16-byte multiple that makes the
+// threads' 16-byte row accesses conflict-free); rows n .. n rounded up to 32
+// are zero.  grid = (leaves, column chunks of KC).
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+
+template <typename TV, int KC>
+constexpr int leaf_multi_stride() { return KC + 16 / (int)sizeof(TV); }
+
+// y_i -= sum_{j < 32} l_j x_{kb+j} for all KC columns of row i of a block of
+// right-hand sides held in shared memory (row r at ys[r * RS], RS a multiple
+// of 16 bytes): the l_j in registers, the rows kb.. read as 16-byte
+// broadcasts (one address in every lane), the sums formed in j order.
+template <typename TM, typename TV, int KC, int RS>
+__device__ __forceinline__ void block_row_update(TV* ys, int i, int kb, const TM (&lv)[32]) {
+  constexpr int VW = 16 / (int)sizeof(TV);
+  using V16 = typename Vec16<TV>::type;
+  TV acc[KC];
+#pragma unroll
+  for (int c = 0; c < KC; ++c) acc[c] = (TV)0;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const TV l = (TV)lv[j];
+    const V16* xj = (const V16*)(ys + (kb + j) * RS);
+#pragma unroll
+    for (int q = 0; q < KC / VW; ++q) {
+      TV x[VW];
+      const V16 v = xj[q];
+      memcpy(x, &v, 16);
+#pragma unroll
+      for (int u = 0; u < VW; ++u) acc[q * VW + u] += l * x[u];
+    }
+  }
+  V16* yr = (V16*)(ys + i * RS);
+#pragma unroll
+  for (int q = 0; q < KC / VW; ++q) {
+    TV y[VW];
+    V16 v = yr[q];
+    memcpy(y, &v, 16);
+#pragma unroll
+    for (int u = 0; u < VW; ++u) y[u] -= acc[q * VW + u];
+    memcpy(&v, y, 16);
+    yr[q] = v;
+  }
+}
+
+template <typename TM, typename TV, int KC>
+__global__ void __launch_bounds__(256) k_leaf_solve_multi(const int32_t* __restrict__ lo,
+                                                          const int32_t* __restrict__ hi, int leaf0, int ldL,
+                                                          const TM* __restrict__ Lall, TV* __restrict__ W, int k) {
+  static_assert(KC % 8 == 0, "KC: a multiple of 8");
+  constexpr int NB = 32, RS = leaf_multi_stride<TV, KC>();
+  extern __shared__ __align__(16) unsigned char lsm[];
+  TV* ys = (TV*)lsm;  // ((n + 31) / 32 * 32) x RS
+  __shared__ TM db[NB][NB + 1];
+  __shared__ TV dinv[NB];
+  const int lf = blockIdx.x, node = leaf0 + lf;
+  const int b = lo[node], n = hi[node] - b;
+  const int c0 = blockIdx.y * KC;
+  if (c0 >= k || n <= 0) return;
+  const int kc = min(KC, k - c0), npad = (n + NB - 1) / NB * NB;
+  const TM* L = Lall + (int64_t)lf * ldL * ldL;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < npad * RS; e += blockDim.x) {
+    const int i = e / RS, c = e % RS;
+    ys[e] = (i < n && c < kc) ? W[(int64_t)(b + i) * k + c0 + c] : (TV)0;
+  }
+  auto stage = [&](int kb, int nb) {
+    __syncthreads();
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+      const int i = e >> 5, j = e & 31;
+      db[i][j] = (i < nb && j <= i) ? L[(int64_t)(kb + i) * ldL + kb + j] : (TM)0;
+    }
+    __syncthreads();
+    if (tid < NB) dinv[lane] = lane < nb ? (TV)1 / (TV)db[lane][lane] : (TV)0;
+    __syncthreads();
+  };
+  auto update = [&](int i, int kb, const TM (&lv)[NB]) { block_row_update<TM, TV, KC, RS>(ys, i, kb, lv); };
+  // forward: L y = b
+  for (int kb = 0; kb < n; kb += NB) {
+    const int nb = min(NB, n - kb);
+    stage(kb, nb);
+    for (int c = warp; c < KC; c += 8) {
+      TV yi = lane < nb ? ys[(kb + lane) * RS + c] : (TV)0;
+      for (int j = 0; j < nb; ++j) {
+        if (lane == j) yi *= dinv[j];
+        const TV yj = __shfl_sync(0xffffffffu, yi, j);
+        if (lane > j && lane < nb) yi -= (TV)db[lane][j] * yj;
+      }
+      if (lane < nb) ys[(kb + lane) * RS + c] = yi;
+    }
+    __syncthreads();
+    for (int i = kb + nb + tid; i < n; i += blockDim.x) {
+      const TM* Li = L + (int64_t)i * ldL + kb;
+      TM lv[NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) lv[j] = j < nb ? Li[j] : (TM)0;
+      update(i, kb, lv);
+    }
+  }
+  // backward: L^T x = y
+  for (int kb = (n - 1) / NB * NB; kb >= 0; kb -= NB) {
+    const int nb = min(NB, n - kb);
+    stage(kb, nb);
+    for (int c = warp; c < KC; c += 8) {
+      TV xi = lane < nb ? ys[(kb + lane) * RS + c] : (TV)0;
+      for (int j = nb - 1; j >= 0; --j) {
+        if (lane == j) xi *= dinv[j];
+        const TV xj = __shfl_sync(0xffffffffu, xi, j);
+        if (lane < j) xi -= (TV)db[j][lane] * xj;
+      }
+      if (lane < nb) ys[(kb + lane) * RS + c] = xi;
+    }
+    __syncthreads();
+    for (int i = tid; i < kb; i += blockDim.x) {
+      TM lv[NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) lv[j] = j < nb ? L[(int64_t)(kb + j) * ldL + i] : (TM)0;
+      update(i, kb, lv);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < n * RS; e += blockDim.x) {
+    const int i = e / RS, c = e % RS;
+    if (c < kc) W[(int64_t)(b + i) * k + c0 + c] = ys[e];
+  }
+}
+
 // ---- segmented column sums -------------------------------------------------------
 // For every node b of a level (grid.y) and a chunk of its rows (grid.x):
 // u[dst(b)][q][r] += sum_i M[i][q] w[i][r], q < cnt(b).  Sibling mode: the
 // columns are the sibling's skeleton (cnt = rank[sib], dst = sib); own mode:
 // cnt = rank[b], dst = b.  u is FP64 [node][s_max][k].
+// ROWS rows per CTA (128; 512 for several right-hand sides, so that the
+// FP64 atomic adds of the partial sums, kMaxK per column and CTA, stay few
+// beside the products).
 constexpr int kRowsPerChunk = 128;
 
-template <typename TM, typename TV, int kMaxK>
+template <typename TM, typename TV, int kMaxK, int ROWS = kRowsPerChunk>
 __global__ void __launch_bounds__(256) k_colsum(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                 const int32_t* __restrict__ rank, const int32_t* __restrict__ skel,
                                                 int node0, int s_max, int sibling_mode, int src,
                                                 const TM* __restrict__ M, const double* __restrict__ X64,
                                                 const float* __restrict__ X32, int d, double c_exp, double inv_h3,
                                                 const TV* __restrict__ W, int k, double* __restrict__ U) {
-  __shared__ TV ws[kRowsPerChunk][kMaxK];
+  __shared__ TV ws[ROWS][kMaxK];
   const int nl = blockIdx.y, node = node0 + nl, sib = node ^ 1;
   const int b = lo[node], n = hi[node] - b;
   const int cnt = sibling_mode ? rank[sib] : rank[node];
   const int dst = sibling_mode ? sib : node;
-  const int r0 = blockIdx.x * kRowsPerChunk;
+  const int r0 = blockIdx.x * ROWS;
   if (r0 >= n || cnt == 0) return;
-  const int r1 = min(n, r0 + kRowsPerChunk);
+  const int r1 = min(n, r0 + ROWS);
   const int32_t* sk = skel + (int64_t)sib * s_max;
   for (int kb = 0; kb < k; kb += kMaxK) {
     const int kk = min(kMaxK, k - kb);
@@ -257,9 +399,21 @@ void launch_colsum(dim3 g, cudaStream_t s, const int32_t* lo, const int32_t* hi,
   if (k == 1)
     KF_PHASE(phase, s, k_colsum<TM, TV, 1><<<g, 256, 0, s>>>(lo, hi, rank, skel, node0, s_max, sib, src, M, X64, X32, d, c_exp, inv_h3,
                                           W, k, U));
-  else
-    KF_PHASE(phase, s, k_colsum<TM, TV, 8><<<g, 256, 0, s>>>(lo, hi, rank, skel, node0, s_max, sib, src, M, X64, X32, d, c_exp, inv_h3,
-                                          W, k, U));
+  else {
+    // g.x counts 128-row chunks; several right-hand sides take 512 rows a CTA
+    const dim3 g4((g.x + 3) / 4, g.y);
+    bool done = false;
+    if constexpr (sizeof(TV) == 4) {
+      if (k > 8) {  // 16 columns a pass: each loaded entry of M serves 16 products
+        KF_PHASE(phase, s, k_colsum<TM, TV, 16, 512><<<g4, 256, 0, s>>>(lo, hi, rank, skel, node0, s_max, sib, src, M,
+                                                                        X64, X32, d, c_exp, inv_h3, W, k, U));
+        done = true;
+      }
+    }
+    if (!done)
+      KF_PHASE(phase, s, k_colsum<TM, TV, 8, 512><<<g4, 256, 0, s>>>(lo, hi, rank, skel, node0, s_max, sib, src, M, X64,
+                                                                     X32, d, c_exp, inv_h3, W, k, U));
+  }
 }
 
 // ---- row updates: w[i][r] += sign * sum_q M[i][q] v[src(b)][q][r] ------------------
@@ -384,6 +538,83 @@ __global__ void __launch_bounds__(256) k_rowupd_tile(const int32_t* __restrict__
   }
 }
 
+// Several right-hand sides, stored M: a warp takes 32 rows and walks the
+// node's columns in 32-wide tiles, each loaded row by row (coalesced) into the
+// warp's shared-memory tile; lane q then forms row q's products with all KB
+// staged columns of v (16-byte broadcast reads), so that every FMA is a useful
+// one and no cross-lane reduction is needed.  v is staged in the vector
+// precision, cnt rounded up to 32 rows of KB values, zero past cnt and k.
+template <typename TM, typename TV, int KB>
+__global__ void __launch_bounds__(256) k_rowupd_multi(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                      const int32_t* __restrict__ rank, int node0, int s_max,
+                                                      int sibling_mode, const TM* __restrict__ M,
+                                                      const double* __restrict__ V, double sign,
+                                                      TV* __restrict__ W, int k) {
+  constexpr int VW = 16 / (int)sizeof(TV);
+  static_assert(KB % VW == 0, "KB: a multiple of the 16-byte vector");
+  using V16 = typename Vec16<TV>::type;
+  extern __shared__ __align__(16) unsigned char rm_smem[];
+  TV* vs = (TV*)rm_smem;  // KF_MAX_SMAX x KB
+  TM(*tile)[32][33] = (TM(*)[32][33])(rm_smem + sizeof(TV) * KF_MAX_SMAX * KB);  // 8 warps x 32 x 33
+  const int nl = blockIdx.y, node = node0 + nl, sib = node ^ 1;
+  const int b = lo[node], n = hi[node] - b;
+  const int cnt = sibling_mode ? rank[sib] : rank[node];
+  const int from = sibling_mode ? sib : node;
+  const int r0 = blockIdx.x * kRowUpdRows;
+  if (cnt == 0 || r0 >= n) return;
+  const int r1 = min(n, r0 + kRowUpdRows);
+  const double* v = V + (int64_t)from * s_max * k;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cpad = (cnt + 31) & ~31;
+  TM(*t)[33] = tile[warp];
+  for (int kb = 0; kb < k; kb += KB) {
+    const int kk = min(KB, k - kb);
+    __syncthreads();
+    for (int e = threadIdx.x; e < cpad * KB; e += blockDim.x) {
+      const int q = e / KB, r = e % KB;
+      vs[e] = (q < cnt && r < kk) ? (TV)v[(int64_t)q * k + kb + r] : (TV)0;
+    }
+    __syncthreads();
+    for (int i0 = r0 + warp * 32; i0 < r1; i0 += 8 * 32) {
+      TV acc[KB];
+#pragma unroll
+      for (int r = 0; r < KB; ++r) acc[r] = (TV)0;
+      for (int q0 = 0; q0 < cnt; q0 += 32) {
+        TM x[32];
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr)
+          x[rr] = (i0 + rr < r1 && q0 + lane < cnt) ? M[(int64_t)(b + i0 + rr) * s_max + q0 + lane] : (TM)0;
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr) t[rr][lane] = x[rr];
+        __syncwarp();
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+          const TV m = (TV)t[lane][j];
+          const V16* vj = (const V16*)(vs + (q0 + j) * KB);
+#pragma unroll
+          for (int qq = 0; qq < KB / VW; ++qq) {
+            TV y[VW];
+            const V16 w = vj[qq];
+            memcpy(y, &w, 16);
+#pragma unroll
+            for (int u = 0; u < VW; ++u) acc[qq * VW + u] += m * y[u];
+          }
+        }
+        __syncwarp();
+      }
+      if (i0 + lane < r1) {
+        TV* wr = W + (int64_t)(b + i0 + lane) * k + kb;
+#pragma unroll
+        for (int r = 0; r < KB; ++r)
+          if (r < kk) wr[r] += (TV)sign * acc[r];
+      }
+    }
+  }
+}
+
+template <typename TM, typename TV, int KB>
+constexpr size_t rowupd_multi_smem() { return sizeof(TV) * KF_MAX_SMAX * KB + sizeof(TM) * 8 * 32 * 33; }
+
 template <typename TM, typename TV>
 void launch_rowupd(int64_t rows, int nnodes, cudaStream_t s, const int32_t* lo, const int32_t* hi, const int32_t* rank,
                    const int32_t* skel, int node0, int s_max, int sib, int src, const TM* M, const double* X64,
@@ -403,6 +634,27 @@ void launch_rowupd(int64_t rows, int nnodes, cudaStream_t s, const int32_t* lo, 
       KF_PHASE(phase, s, k_rowupd_tile<TM, TV><<<g, 256, smem, s>>>(lo, hi, rank, node0, s_max, sib, M, V, sign, W));
       return;
     }
+  }
+  if (k >= 2 && src == SRC_STORED) {
+    // several right-hand sides: the tiled form, 16 FP32 (8 FP64) columns a pass
+    constexpr int KB = sizeof(TV) == 4 ? 16 : 8;
+    const bool wide = k > 8;
+    const size_t smem = wide ? rowupd_multi_smem<TM, TV, KB>() : rowupd_multi_smem<TM, TV, 8>();
+    static bool attr_multi = false;  // per instantiation; setting it twice is harmless
+    if (!attr_multi) {
+      cudaFuncSetAttribute(k_rowupd_multi<TM, TV, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)rowupd_multi_smem<TM, TV, KB>());
+      cudaFuncSetAttribute(k_rowupd_multi<TM, TV, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)rowupd_multi_smem<TM, TV, 8>());
+      attr_multi = true;
+    }
+    if (wide)
+      KF_PHASE(phase, s, k_rowupd_multi<TM, TV, KB><<<g, 256, smem, s>>>(lo, hi, rank, node0, s_max, sib, M, V, sign,
+                                                                        W, k));
+    else
+      KF_PHASE(phase, s, k_rowupd_multi<TM, TV, 8><<<g, 256, smem, s>>>(lo, hi, rank, node0, s_max, sib, M, V, sign,
+                                                                       W, k));
+    return;
   }
   if (k == 1)
     KF_PHASE(phase, s, k_rowupd<TM, TV, 1><<<g, 256, 0, s>>>(lo, hi, rank, skel, node0, nnodes, s_max, sib, src, M,
@@ -475,7 +727,9 @@ __global__ void __launch_bounds__(256) k_zsolve(const int32_t* __restrict__ rank
     }
   };
   const int top = z > 0 ? ((z - 1) / 32) * 32 : 0;
-  for (int c = 0; c < k; ++c) {
+  // right-hand sides c = blockIdx.y, blockIdx.y + gridDim.y, ...: several CTAs
+  // of one node solve different columns at once
+  for (int c = blockIdx.y; c < k; c += gridDim.y) {
     for (int i = tid; i < z; i += blockDim.x)
       u[i] = i < sl ? in[((int64_t)l * s_max + i) * k + c] : in[((int64_t)r * s_max + (i - sl)) * k + c];
     __syncthreads();
@@ -573,6 +827,154 @@ __global__ void __launch_bounds__(256) k_zsolve(const int32_t* __restrict__ rank
     }
     __syncthreads();
   }
+}
+
+// The reduced systems for several right-hand sides (k >= 2): KC columns of
+// [in_l; in_r] per CTA held in shared memory (row i at ts[i * RS]) through
+// all four triangular sweeps, so that the LU is read once per KC columns
+// instead of once per column.  Per 32-row block the diagonal block is staged
+// in shared memory and each warp solves KC / 8 columns with shuffles; then
+// every thread updates one row of the rest for all KC columns: from row pm[i]
+// of the LU (L and U sweeps, entries kb..kb+31) or from column i of rows
+// pm[kb..kb+31] (the transposed sweeps, coalesced across the threads).
+// grid = (nodes of the level, column chunks of KC).
+template <int KC>
+__global__ void __launch_bounds__(256) k_zsolve_multi(const int32_t* __restrict__ rank, int node0, int ldz,
+                                                      int s_max, const double* __restrict__ ZLU,
+                                                      const int32_t* __restrict__ piv, const double* __restrict__ in,
+                                                      double* __restrict__ out, int k, int transpose) {
+  constexpr int RS = leaf_multi_stride<double, KC>();
+  extern __shared__ __align__(16) unsigned char zm_smem[];
+  const int nl = blockIdx.x, node = node0 + nl;
+  const int l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], z = sl + sr;
+  const int c0 = blockIdx.y * KC;
+  if (c0 >= k || z == 0) return;
+  const int kc = min(KC, k - c0), zpad = (z + 31) / 32 * 32;
+  double* ts = (double*)zm_smem;       // zpad x RS
+  int* pm = (int*)(ts + (size_t)zpad * RS);  // z
+  __shared__ double db[32][33];
+  __shared__ double dinv[32];
+  const double* A = ZLU + (int64_t)node * ldz * ldz;
+  const int32_t* pv = piv + (int64_t)node * ldz;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  auto dst = [&](int i) -> int64_t { return i < sl ? (int64_t)l * s_max + i : (int64_t)r * s_max + (i - sl); };
+  for (int i = tid; i < z; i += blockDim.x) pm[i] = pv[i];
+  __syncthreads();
+  // the right-hand sides, permuted by P for the L U sweeps
+  for (int e = tid; e < zpad * RS; e += blockDim.x) {
+    const int i = e / RS, c = e % RS;
+    ts[e] = (i < z && c < kc) ? in[dst(transpose ? i : pm[i]) * k + c0 + c] : 0.0;
+  }
+  auto stage = [&](int kb, int nb, bool recip) {
+    __syncthreads();
+    for (int e = tid; e < 32 * 32; e += blockDim.x) {
+      const int i = e >> 5, j = e & 31;
+      db[i][j] = (i < nb && j < nb) ? A[(int64_t)pm[kb + i] * ldz + kb + j] : 0.0;
+    }
+    __syncthreads();
+    if (recip && tid < 32) dinv[lane] = lane < nb ? 1.0 / db[lane][lane] : 0.0;
+    __syncthreads();
+  };
+  auto update = [&](int i, int kb, const double (&lv)[32]) { block_row_update<double, double, KC, RS>(ts, i, kb, lv); };
+  const int top = (z - 1) / 32 * 32;
+  if (!transpose) {
+    // L (unit lower): forward
+    for (int kb = 0; kb < z; kb += 32) {
+      const int nb = min(32, z - kb);
+      stage(kb, nb, false);
+      for (int c = warp; c < KC; c += 8) {
+        double yi = lane < nb ? ts[(kb + lane) * RS + c] : 0.0;
+        for (int j = 0; j < nb; ++j) {
+          const double yj = __shfl_sync(0xffffffffu, yi, j);
+          if (lane > j && lane < nb) yi = fma(-db[lane][j], yj, yi);
+        }
+        if (lane < nb) ts[(kb + lane) * RS + c] = yi;
+      }
+      __syncthreads();
+      for (int i = kb + nb + tid; i < z; i += blockDim.x) {
+        const double* Ai = A + (int64_t)pm[i] * ldz + kb;
+        double lv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) lv[j] = j < nb ? Ai[j] : 0.0;
+        update(i, kb, lv);
+      }
+    }
+    // U: backward
+    for (int kb = top; kb >= 0; kb -= 32) {
+      const int nb = min(32, z - kb);
+      stage(kb, nb, true);
+      for (int c = warp; c < KC; c += 8) {
+        double xi = lane < nb ? ts[(kb + lane) * RS + c] : 0.0;
+        for (int j = nb - 1; j >= 0; --j) {
+          if (lane == j) xi *= dinv[j];
+          const double xj = __shfl_sync(0xffffffffu, xi, j);
+          if (lane < j) xi = fma(-db[lane][j], xj, xi);
+        }
+        if (lane < nb) ts[(kb + lane) * RS + c] = xi;
+      }
+      __syncthreads();
+      for (int i = tid; i < kb; i += blockDim.x) {
+        const double* Ai = A + (int64_t)pm[i] * ldz + kb;
+        double lv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) lv[j] = j < nb ? Ai[j] : 0.0;
+        update(i, kb, lv);
+      }
+    }
+  } else {
+    // U^T: forward
+    for (int kb = 0; kb < z; kb += 32) {
+      const int nb = min(32, z - kb);
+      stage(kb, nb, true);
+      for (int c = warp; c < KC; c += 8) {
+        double yi = lane < nb ? ts[(kb + lane) * RS + c] : 0.0;
+        for (int j = 0; j < nb; ++j) {
+          if (lane == j) yi *= dinv[j];
+          const double yj = __shfl_sync(0xffffffffu, yi, j);
+          if (lane > j && lane < nb) yi = fma(-db[j][lane], yj, yi);
+        }
+        if (lane < nb) ts[(kb + lane) * RS + c] = yi;
+      }
+      __syncthreads();
+      for (int i = kb + nb + tid; i < z; i += blockDim.x) {
+        double lv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) lv[j] = j < nb ? A[(int64_t)pm[kb + j] * ldz + i] : 0.0;
+        update(i, kb, lv);
+      }
+    }
+    // L^T (unit): backward
+    for (int kb = top; kb >= 0; kb -= 32) {
+      const int nb = min(32, z - kb);
+      stage(kb, nb, false);
+      for (int c = warp; c < KC; c += 8) {
+        double xi = lane < nb ? ts[(kb + lane) * RS + c] : 0.0;
+        for (int j = nb - 1; j >= 0; --j) {
+          const double xj = __shfl_sync(0xffffffffu, xi, j);
+          if (lane < j) xi = fma(-db[j][lane], xj, xi);
+        }
+        if (lane < nb) ts[(kb + lane) * RS + c] = xi;
+      }
+      __syncthreads();
+      for (int i = tid; i < kb; i += blockDim.x) {
+        double lv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) lv[j] = j < nb ? A[(int64_t)pm[kb + j] * ldz + i] : 0.0;
+        update(i, kb, lv);
+      }
+    }
+  }
+  __syncthreads();
+  // x = P^T w for the transposed solve: x[pm[i]] = w[i]
+  for (int e = tid; e < z * RS; e += blockDim.x) {
+    const int i = e / RS, c = e % RS;
+    if (c < kc) out[dst(transpose ? pm[i] : i) * k + c0 + c] = ts[e];
+  }
+}
+
+inline size_t zsolve_multi_smem(int ldz) {
+  const int zpad = (ldz + 31) / 32 * 32;
+  return sizeof(double) * (size_t)zpad * leaf_multi_stride<double, 8>() + sizeof(int) * (size_t)ldz;
 }
 
 // The same product for several right-hand sides at once: a 32 x 64 tile of
@@ -744,13 +1146,13 @@ __global__ void __launch_bounds__(256) k_leaf_mv_df(const int32_t* __restrict__ 
                                                     int leaf0, int ldL, const float2* __restrict__ Kdf,
                                                     double lambda, const double* __restrict__ x,
                                                     double* __restrict__ y, int k, int r0) {
-  extern __shared__ float2 xs[];  // n x RB
+  extern __shared__ float2 xs[];  // RB x n: the lanes' consecutive j are consecutive words
   const int lf = blockIdx.y, node = leaf0 + lf;
   const int b = lo[node], n = hi[node] - b;
   const int nr = min(RB, k - r0);
   for (int e = threadIdx.x; e < n * RB; e += blockDim.x) {
     const int j = e / RB, q = e % RB;
-    xs[e] = q < nr ? kf_split_df(x[(int64_t)(b + j) * k + r0 + q]) : make_float2(0.f, 0.f);
+    xs[q * n + j] = q < nr ? kf_split_df(x[(int64_t)(b + j) * k + r0 + q]) : make_float2(0.f, 0.f);
   }
   __syncthreads();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -763,7 +1165,7 @@ __global__ void __launch_bounds__(256) k_leaf_mv_df(const int32_t* __restrict__ 
       const float2 m = Ki[j];
 #pragma unroll
       for (int q = 0; q < RB; ++q) {
-        const float2 v = xs[j * RB + q];
+        const float2 v = xs[q * n + j];
         kf_df_fma(m.x, m.y, v.x, v.y, sh[q], sl[q]);
       }
     }
@@ -788,18 +1190,18 @@ __global__ void __launch_bounds__(256) k_leaf_mv_df(const int32_t* __restrict__ 
 // double-float arithmetic on the FP32 pipes (the same partition as k_colsum,
 // one thread per skeleton column, the chunk's w split into pairs in shared
 // memory, 8 rows' loads in flight).
-template <int KB>
+template <int KB, int ROWS = kRowsPerChunk>
 __global__ void __launch_bounds__(256) k_colsum_df(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                    const int32_t* __restrict__ rank, int node0, int s_max,
                                                    const float2* __restrict__ M, const double* __restrict__ W, int k,
                                                    double* __restrict__ U) {
-  __shared__ float2 ws[kRowsPerChunk][KB];
+  __shared__ float2 ws[ROWS][KB];
   const int nl = blockIdx.y, node = node0 + nl, sib = node ^ 1;
   const int b = lo[node], n = hi[node] - b;
   const int cnt = rank[sib];
-  const int r0 = blockIdx.x * kRowsPerChunk;
+  const int r0 = blockIdx.x * ROWS;
   if (r0 >= n || cnt == 0) return;
-  const int r1 = min(n, r0 + kRowsPerChunk), nr = r1 - r0;
+  const int r1 = min(n, r0 + ROWS), nr = r1 - r0;
   for (int kb = 0; kb < k; kb += KB) {
     const int kk = min(KB, k - kb);
     __syncthreads();
@@ -860,6 +1262,148 @@ __global__ void __launch_bounds__(256) k_push_down(const int32_t* __restrict__ r
     }
   }
 }
+
+// The same push for several right-hand sides: a 32 x 64 tile of the
+// children's rows (32 rows of P_c x 64 columns) per CTA, the reduction over
+// the parent's s entries in chunks of 32 with the P_c block and g[a] staged in
+// shared memory (P_c read once per 64 columns).  Thread (ty, tx) forms rows
+// ty*4..+3 of columns tx and tx + 32.  grid = (nodes, z / 32, k / 64).
+__global__ void __launch_bounds__(256) k_push_down_multi(const int32_t* __restrict__ rank, int node0, int s_max,
+                                                         const double* __restrict__ Pc, double* __restrict__ G,
+                                                         int k) {
+  __shared__ double sa[32][33];
+  __shared__ double su[32][65];
+  const int node = node0 + blockIdx.x;
+  const int l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], s = rank[node], z = sl + sr;
+  const int e0 = blockIdx.y * 32, c0 = blockIdx.z * 64;
+  if (e0 >= z || c0 >= k || s == 0) return;
+  const double* P = Pc + (int64_t)node * 2 * s_max * s_max;
+  const double* ga = G + (int64_t)node * s_max * k;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  double acc[4][2] = {};
+  for (int j0 = 0; j0 < s; j0 += 32) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int ii = ty * 4 + q, i = e0 + ii, j = j0 + tx;
+      sa[ii][tx] = (i < z && j < s) ? P[(int64_t)i * s_max + j] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int jj = ty * 4 + q, j = j0 + jj;
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const int c = c0 + tx + 32 * h2;
+        su[jj][tx + 32 * h2] = (j < s && c < k) ? ga[(int64_t)j * k + c] : 0.0;
+      }
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int jj = 0; jj < 32; ++jj) {
+      const double u0 = su[jj][tx], u1 = su[jj][tx + 32];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const double a = sa[ty * 4 + q][jj];
+        acc[q][0] = fma(a, u0, acc[q][0]);
+        acc[q][1] = fma(a, u1, acc[q][1]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = e0 + ty * 4 + q;
+    if (i >= z) continue;
+    double* dst = i < sl ? G + ((int64_t)l * s_max + i) * k : G + ((int64_t)r * s_max + (i - sl)) * k;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+      const int c = c0 + tx + 32 * h2;
+      if (c < k) dst[c] += acc[q][h2];
+    }
+  }
+}
+
+// Several right-hand sides on the mixed path's FP64-accurate operator:
+// out[i][c] += sum_q M[i][q] v[q][c] for the rows of a stored FP64 matrix, in
+// double-float arithmetic on the FP32 pipes (the FP64 pipe would bound these
+// passes at 2 k FP64 flops per entry).  PUSH: the rows of P_c of a node of the
+// level (grid.y), pushed into its children's skeleton weights g[l], g[r] from
+// v = g[node]; else the rows of the leaf interpolation P of a leaf (grid.y)
+// into y from v = g[leaf].  A warp takes 32 rows and walks the columns in
+// 32-wide tiles, each entry split into a pair once as its tile is staged; lane
+// q forms row q's KB sums.  v is split into pairs once per CTA (dynamic shared
+// memory: KF_MAX_SMAX x KB pairs, then the warps' tiles).
+template <int KB, bool PUSH>
+__global__ void __launch_bounds__(256) k_rows_df(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                 const int32_t* __restrict__ rank, int node0, int s_max,
+                                                 const double* __restrict__ M, const double* __restrict__ V,
+                                                 double* __restrict__ out, int k) {
+  extern __shared__ __align__(16) unsigned char rd_smem[];
+  float2* vs = (float2*)rd_smem;                                                   // KF_MAX_SMAX x KB
+  float2(*tile)[32][33] = (float2(*)[32][33])(rd_smem + sizeof(float2) * KF_MAX_SMAX * KB);  // 8 warps
+  const int node = node0 + blockIdx.y;
+  int nrows, cnt, sl = 0;
+  const double* Mb;
+  if (PUSH) {
+    sl = rank[2 * node];
+    nrows = sl + rank[2 * node + 1];
+    cnt = rank[node];
+    Mb = M + (int64_t)node * 2 * s_max * s_max;
+  } else {
+    nrows = hi[node] - lo[node];
+    cnt = rank[node];
+    Mb = M + (int64_t)lo[node] * s_max;
+  }
+  const int r0 = blockIdx.x * kRowUpdRows;
+  if (cnt == 0 || r0 >= nrows) return;
+  const int r1 = min(nrows, r0 + kRowUpdRows);
+  const double* v = V + (int64_t)node * s_max * k;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cpad = (cnt + 31) & ~31;
+  float2(*t)[33] = tile[warp];
+  auto dst = [&](int i) -> double* {
+    if (PUSH) return out + ((int64_t)(i < sl ? 2 * node : 2 * node + 1) * s_max + (i < sl ? i : i - sl)) * k;
+    return out + (int64_t)(lo[node] + i) * k;
+  };
+  for (int kb = 0; kb < k; kb += KB) {
+    const int kk = min(KB, k - kb);
+    __syncthreads();
+    for (int e = threadIdx.x; e < cpad * KB; e += blockDim.x) {
+      const int q = e / KB, r = e % KB;
+      vs[e] = (q < cnt && r < kk) ? kf_split_df(v[(int64_t)q * k + kb + r]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int i0 = r0 + warp * 32; i0 < r1; i0 += 8 * 32) {
+      float sh[KB], sl2[KB];
+#pragma unroll
+      for (int r = 0; r < KB; ++r) sh[r] = sl2[r] = 0.f;
+      for (int q0 = 0; q0 < cnt; q0 += 32) {
+        double x[32];
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr)
+          x[rr] = (i0 + rr < r1 && q0 + lane < cnt) ? Mb[(int64_t)(i0 + rr) * s_max + q0 + lane] : 0.0;
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr) t[rr][lane] = kf_split_df(x[rr]);
+        __syncwarp();
+        for (int j = 0; j < 32; ++j) {
+          const float2 m = t[lane][j];
+          const float2* vj = vs + (q0 + j) * KB;  // one address in every lane: a broadcast
+#pragma unroll
+          for (int r = 0; r < KB; ++r) kf_df_fma(m.x, m.y, vj[r].x, vj[r].y, sh[r], sl2[r]);
+        }
+        __syncwarp();
+      }
+      if (i0 + lane < r1) {
+        double* o = dst(i0 + lane) + kb;
+#pragma unroll
+        for (int r = 0; r < KB; ++r)
+          if (r < kk) o[r] += (double)sh[r] + (double)sl2[r];
+      }
+    }
+  }
+}
+
+template <int KB>
+constexpr size_t rows_df_smem() { return sizeof(float2) * (KF_MAX_SMAX * KB + 8 * 32 * 33); }
 
 // Gather skeleton weights up (transposed operator): g[a] += P_c^T [g[l]; g[r]].
 // blockIdx.x = node of the level, blockIdx.y = a block of 32 columns of P_c:
@@ -965,6 +1509,9 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
   const size_t zs_smem = sizeof(double) * (2 * (size_t)ldz + (ldz + 1) / 2 + 8 * 32 * 33);
   KF_CUDA(c, cudaFuncSetAttribute(k_leaf_solve<TM, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls_smem));
   KF_CUDA(c, cudaFuncSetAttribute(k_zsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs_smem));
+  const size_t zm_smem = zsolve_multi_smem(ldz);
+  if (k >= 2)
+    KF_CUDA(c, cudaFuncSetAttribute(k_zsolve_multi<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zm_smem));
   // t = Z^-1 [u_l; u_r] (or Z^-T) for the nodes of level l: the explicit
   // inverse where the factorization kept it, else the LU
   auto zsolve = [&](int l, int tr) {
@@ -978,13 +1525,47 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
         KF_PHASE(KF_PH_S_ZSOLVE, s, k_zinv_apply<<<gz, 256, 0, s>>>(f->rank, 1 << l, ldz, s_max, f->Zinv, U, Vb,
                                                                    (int)k, tr));
       }
+    } else if (k >= 2) {
+      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve_multi<8><<<dim3(1u << l, (unsigned)((k + 7) / 8)), 256, zm_smem, s>>>(
+                                      f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv, U, Vb, (int)k, tr));
     } else {
-      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<1 << l, 256, zs_smem, s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv,
-                                                                         U, Vb, (int)k, tr));
+      KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve<<<dim3(1u << l, 1u), 256, zs_smem, s>>>(f->rank, 1 << l, ldz, s_max,
+                                                                                  f->ZLU, f->Zpiv, U, Vb, (int)k, tr));
+    }
+  };
+  // leaf blocks: one column per pass (k = 1), else KC columns per pass with
+  // the columns in shared memory (16 FP32 or 8 FP64 columns; 8 FP32 columns
+  // for k <= 8), when the leaf's columns fit
+  const int npad = (t->leaf_max + 31) / 32 * 32;
+  constexpr int KCm = sizeof(TV) == 4 ? 16 : 8;
+  const bool wide = sizeof(TV) == 4 && k > 8;
+  const size_t lm_smem = sizeof(TV) * (size_t)npad *
+                         (wide ? leaf_multi_stride<TV, KCm>() : leaf_multi_stride<TV, 8>());
+  const bool leaf_multi = k >= 2 && lm_smem <= 200 * 1024;
+  if (leaf_multi) {
+    if (wide)
+      KF_CUDA(c, cudaFuncSetAttribute(k_leaf_solve_multi<TM, TV, KCm>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)lm_smem));
+    else
+      KF_CUDA(c, cudaFuncSetAttribute(k_leaf_solve_multi<TM, TV, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)lm_smem));
+  }
+  auto leaf_solve = [&]() {
+    if (!leaf_multi) {
+      KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve<TM, TV><<<1 << D, kLeafSolveThreads, ls_smem, s>>>(
+                                    t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
+    } else if (wide) {
+      const dim3 g(1u << D, (unsigned)((k + KCm - 1) / KCm));
+      KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve_multi<TM, TV, KCm><<<g, 256, lm_smem, s>>>(
+                                    t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
+    } else {
+      const dim3 g(1u << D, (unsigned)((k + 7) / 8));
+      KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve_multi<TM, TV, 8><<<g, 256, lm_smem, s>>>(
+                                    t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
     }
   };
   if (!transpose) {
-    KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve<TM, TV><<<1 << D, kLeafSolveThreads, ls_smem, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
+    leaf_solve();
     // the hybrid solver stops at its frontier level (the reduced system above
     // it is applied by kf_hybrid_top_solve); the direct solver goes to the root
     for (int l = D - 1; l >= f->hyb_L; --l) {
@@ -1010,7 +1591,7 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
       launch_rowupd<TM, TV>(rows, nc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 1, vsrc, lvl(VT, l + 1),
                             t->X64, t->X32, t->d, f->c_exp, inv_h3, Vb, -1.0, W, (int)k);
     }
-    KF_PHASE(KF_PH_S_LEAF, s, k_leaf_solve<TM, TV><<<1 << D, kLeafSolveThreads, ls_smem, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
+    leaf_solve();
   }
   KF_LAUNCH_CHECK(c);
   return KF_OK;
@@ -1086,9 +1667,15 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
       if (k == 1)
         KF_PHASE(KF_PH_MV_COLSUM, s, k_colsum_df<1><<<gc, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, 1 << l, s_max, Vl, x,
                                                                         (int)k, G));
-      else
+      else if (k <= 4)
         KF_PHASE(KF_PH_MV_COLSUM, s, k_colsum_df<4><<<gc, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, 1 << l, s_max, Vl, x,
                                                                         (int)k, G));
+      else if (k <= 8)
+        KF_PHASE(KF_PH_MV_COLSUM, s, k_colsum_df<8><<<gc, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, 1 << l, s_max, Vl, x,
+                                                                        (int)k, G));
+      else  // 16 columns a pass over 256 rows: each pair of V serves 16 double-float products
+        KF_PHASE(KF_PH_MV_COLSUM, s, k_colsum_df<16, 256><<<dim3((gc.x + 1) / 2, gc.y), 256, 0, s>>>(
+                                         t->d_lo, t->d_hi, f->rank, 1 << l, s_max, Vl, x, (int)k, G));
     } else
       launch_colsum<TM, double>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, s_max, 1, src, vt_level(l),
                                 t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G, KF_PH_MV_COLSUM);
@@ -1100,12 +1687,35 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
     if (hs != KF_OK) return hs;
   }
   const dim3 gpd(1, (unsigned)((2 * s_max + 31) / 32));
-  for (int l = std::max(1, f->hyb_L); l < D; ++l)
-    KF_PHASE(KF_PH_MV_PUSH, s, k_push_down<<<dim3(1u << l, gpd.y), 256, 0, s>>>(f->rank, 1 << l, s_max, f->Pc, G,
-                                                                                (int)k));
+  // several right-hand sides on the FP64-accurate operator: double-float passes over P_c and P
+  const bool rows_df = f->VTdf && !deriv && k >= 2;
+  if (rows_df) {
+    KF_CUDA(c, cudaFuncSetAttribute(k_rows_df<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)rows_df_smem<8>()));
+    KF_CUDA(c, cudaFuncSetAttribute(k_rows_df<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)rows_df_smem<8>()));
+  }
+  for (int l = std::max(1, f->hyb_L); l < D; ++l) {
+    if (rows_df)
+      KF_PHASE(KF_PH_MV_PUSH, s, k_rows_df<8, true><<<dim3((unsigned)((2 * s_max + kRowUpdRows - 1) / kRowUpdRows),
+                                                          1u << l), 256, rows_df_smem<8>(), s>>>(
+                                     t->d_lo, t->d_hi, f->rank, 1 << l, s_max, f->Pc, G, G, (int)k));
+    else if (k >= 2)
+      KF_PHASE(KF_PH_MV_PUSH, s, k_push_down_multi<<<dim3(1u << l, gpd.y, (unsigned)((k + 63) / 64)), 256, 0, s>>>(
+                                     f->rank, 1 << l, s_max, f->Pc, G, (int)k));
+    else
+      KF_PHASE(KF_PH_MV_PUSH, s, k_push_down<<<dim3(1u << l, gpd.y), 256, 0, s>>>(f->rank, 1 << l, s_max, f->Pc, G,
+                                                                                  (int)k));
+  }
   const int64_t rows = (N >> D) + 1;
-  launch_rowupd<double, double>(rows, 1 << D, s, t->d_lo, t->d_hi, f->rank, f->skel, leaf0, s_max, 0, SRC_STORED,
-                                f->Pleaf, t->X64, t->X32, t->d, f->c_exp, inv_h3, G, 1.0, y, (int)k, KF_PH_MV_ROWUPD);
+  if (rows_df)
+    KF_PHASE(KF_PH_MV_ROWUPD, s, k_rows_df<8, false><<<dim3((unsigned)((rows + kRowUpdRows - 1) / kRowUpdRows),
+                                                           1u << D), 256, rows_df_smem<8>(), s>>>(
+                                     t->d_lo, t->d_hi, f->rank, leaf0, s_max, f->Pleaf, G, y, (int)k));
+  else
+    launch_rowupd<double, double>(rows, 1 << D, s, t->d_lo, t->d_hi, f->rank, f->skel, leaf0, s_max, 0, SRC_STORED,
+                                  f->Pleaf, t->X64, t->X32, t->d, f->c_exp, inv_h3, G, 1.0, y, (int)k,
+                                  KF_PH_MV_ROWUPD);
   KF_LAUNCH_CHECK(c);
   return KF_OK;
 }
@@ -1186,7 +1796,8 @@ kf_status kf_zsolve_one_launch(const int32_t* rank, int ldz, const double* ZLU, 
   const size_t zs_smem = sizeof(double) * (2 * (size_t)ldz + (ldz + 1) / 2 + 8 * 32 * 33);
   if (cudaFuncSetAttribute(k_zsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs_smem) != cudaSuccess)
     return KF_ECUDA;
-  KF_PHASE(KF_PH_HYBRID, s, k_zsolve<<<1, 256, zs_smem, s>>>(rank, 1, ldz, ldz, ZLU, piv, in, out, k, 0));
+  KF_PHASE(KF_PH_HYBRID, s, k_zsolve<<<dim3(1, (unsigned)std::min(k, 16)), 256, zs_smem, s>>>(rank, 1, ldz, ldz, ZLU,
+                                                                                              piv, in, out, k, 0));
   return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
 }
 

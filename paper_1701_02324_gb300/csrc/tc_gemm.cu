@@ -375,6 +375,31 @@ struct ZoffProblem {
   }
 };
 
+// ---- Z off-diagonal blocks with the kernel entries evaluated in the product ----------
+// The same blocks as ZoffProblem, K_{l~ r} P^_r and K_{r~ l} P^_l, but the A
+// operand K(x_{sib~ m}, x_k) is evaluated while the operand is staged (FP32
+// squared distance of the FP32 coordinates, sequential fused multiply-adds,
+// then exp), as kernel summation fuses the kernel evaluation into the product
+// with the weights (Sec. II-D): the V blocks are neither read nor needed
+// before the reduced systems.
+struct ZoffFusedProblem : ZoffProblem {
+  const float* X32;
+  const int32_t* skel;
+  int d;
+  float c_exp;
+  __device__ float loadA(const Tile& t, int m, int k) const {
+    const int sib = t.side == 0 ? 2 * t.node : 2 * t.node + 1;  // the skeleton's node
+    const float* xs = X32 + (int64_t)skel[(int64_t)sib * s_max + m] * d;
+    const float* xk = X32 + (int64_t)k * d;
+    float acc = 0.f;
+    for (int q = 0; q < d; ++q) {
+      const float u = __fsub_rn(xs[q], xk[q]);
+      acc = __fmaf_rn(u, u, acc);
+    }
+    return __expf(acc * c_exp);
+  }
+};
+
 // ---- telescoping: P^_a[rows of c, :s_a] = P^_c[:, :s_c] T[c block, :s_a] ---------
 struct TelescopeProblem {
   static constexpr int kPieces = 2;
@@ -556,6 +581,15 @@ static size_t tc_smem_bytes(int BN, int pieces = 2) {
   return 2 * sizeof(float) * (size_t)pieces * (kBM * kBK + BN * kBK);
 }
 
+template <int BN, class Problem>
+static kf_status tc_launch(const Problem& p, dim3 g, int phase, int32_t* status, cudaStream_t s) {
+  const size_t smem = tc_smem_bytes(BN, Problem::kPieces);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN, Problem>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return KF_ECUDA;
+  KF_PHASE(phase, s, k_tc_gemm<BN, Problem><<<g, kThreads, smem, s>>>(p, status));
+  return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
+}
+
 template <int BN>
 static kf_status tc_zoff_bn(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
                             const float* VT, const float* Ph, int ldz, double* Z, int64_t rows_per_child,
@@ -595,6 +629,32 @@ static kf_status tc_telescope_bn(const int32_t* lo, const int32_t* hi, const int
   return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
 }
 
+template <int BN>
+static kf_status tc_zoff_fused_bn(const int32_t* lo, const int32_t* hi, const int32_t* rank, const int32_t* skel,
+                                  const float* X32, int d, float c_exp, int node0, int nn, int s_max, const float* Ph,
+                                  int ldz, double* Z, int64_t rows_per_child, int32_t* status, cudaStream_t s) {
+  ZoffFusedProblem p;
+  p.lo = lo; p.hi = hi; p.rank = rank; p.node0 = node0; p.s_max = s_max; p.ldz = ldz;
+  p.ntile_n = (s_max + BN - 1) / BN;
+  p.tile_n = BN;
+  p.VT = nullptr; p.Ph = Ph; p.Z = Z;
+  p.X32 = X32; p.skel = skel; p.d = d; p.c_exp = c_exp;
+  const int mt = (s_max + kBM - 1) / kBM;
+  const int64_t tiles = (int64_t)mt * p.ntile_n * 2 * nn;
+  p.ksplit = (int)std::max<int64_t>(1, std::min<int64_t>((rows_per_child + 1023) / 1024, (2 * 152 + tiles - 1) / tiles));
+  return tc_launch<BN>(p, dim3(mt * p.ntile_n, p.ksplit, 2 * nn), KF_PH_ZOFF, status, s);
+}
+
+// tile_n: the tile width BN of the products, 128 or 256 columns
+kf_status kf_tc_zoff_fused(const int32_t* lo, const int32_t* hi, const int32_t* rank, const int32_t* skel,
+                           const float* X32, int d, float c_exp, int node0, int nn, int s_max, const float* Ph,
+                           int ldz, double* Z, int64_t rows_per_child, int32_t* status, cudaStream_t s, int tile_n) {
+  return tile_n == 128 ? tc_zoff_fused_bn<128>(lo, hi, rank, skel, X32, d, c_exp, node0, nn, s_max, Ph, ldz, Z,
+                                               rows_per_child, status, s)
+                       : tc_zoff_fused_bn<256>(lo, hi, rank, skel, X32, d, c_exp, node0, nn, s_max, Ph, ldz, Z,
+                                               rows_per_child, status, s);
+}
+
 // tile_n: the tile width BN of the products, 128 or 256 columns
 kf_status kf_tc_zoff(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
                      const float* VT, const float* Ph, int ldz, double* Z, int64_t rows_per_child, int32_t* status,
@@ -611,14 +671,6 @@ kf_status kf_tc_telescope(const int32_t* lo, const int32_t* hi, const int32_t* r
              : tc_telescope_bn<256>(lo, hi, rank, node0, nn, s_max, Pc_hat, Tm, ldz, Pa_hat, rows_per_child, status, s);
 }
 
-template <int BN, class Problem>
-static kf_status tc_launch(const Problem& p, dim3 g, int phase, int32_t* status, cudaStream_t s) {
-  const size_t smem = tc_smem_bytes(BN, Problem::kPieces);
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN, Problem>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return KF_ECUDA;
-  KF_PHASE(phase, s, k_tc_gemm<BN, Problem><<<g, kThreads, smem, s>>>(p, status));
-  return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
-}
 
 // Panel kb of the leaves' Cholesky factorization after k_chol_panel: the
 // panel rows below the diagonal block (L21 = A21 Linv^T), then the trailing

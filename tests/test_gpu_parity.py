@@ -596,3 +596,30 @@ def test_leaf_factorization_on_tensor_cores(N, d, m, smax):
     b = rng.standard_normal(N)
     G = kf.Factor(tree, h, lam, tau, smax, precision=MIXED, refine_tol=1e-11)
     assert rel(G.solve(torch.from_numpy(b).cuda()).cpu().numpy(), o.solve(b)) <= 1e-8
+
+
+@pytest.mark.parametrize("N,d,m,smax,h", [(4096, 8, 256, 64, 0.5), (3001, 5, 100, 32, 0.35)])
+def test_fused_z_blocks_match_stored_v(N, d, m, smax, h):
+    """Row a5 on the mixed path, kf_opts.zoff_fused = 1: the reduced systems'
+    off-diagonal blocks K_{l~ r} P^_r with the kernel entries evaluated inside
+    the tcgen05 product against the default product that reads the stored V
+    blocks: P^ of every internal node within 1e-4 (the fused entries carry
+    ~1e-6 relative error: FP32 squared distances of the FP32 coordinates); the
+    fused factors refined by GMRES solve within 1e-8 of the oracle."""
+    rng = np.random.default_rng(N + 5)
+    X, b = rng.random((N, d)), rng.standard_normal(N)
+    lam, tau = 0.7, 1e-6
+    o = oracle.Oracle(X, m)
+    o.skeletonize(h, tau, smax)
+    o.factorize(lam)
+    tree = kf.Tree(torch.from_numpy(X).cuda(), m)
+    Ff = kf.Factor(tree, h, lam, tau, smax, precision=MIXED, refine_max_iter=-1, zoff_fused=True)
+    Fv = kf.Factor(tree, h, lam, tau, smax, precision=MIXED, refine_max_iter=-1)
+    for a in range(2, 1 << o.D):
+        lo, hi = o.node_range(a)
+        pf, pv = Ff.Phat(a, hi - lo), Fv.Phat(a, hi - lo)
+        if pv.size == 0:
+            continue
+        assert rel(pf, pv) <= 1e-4, a
+    G = kf.Factor(tree, h, lam, tau, smax, precision=MIXED, refine_tol=1e-11, zoff_fused=True)
+    assert rel(G.solve(torch.from_numpy(b).cuda()).cpu().numpy(), o.solve(b)) <= 1e-8
