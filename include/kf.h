@@ -133,7 +133,16 @@ typedef struct {
                              FP32 squared distances of the FP32 coordinates and a fast exponential,
                              so the entries carry ~1e-6 relative error instead of FP32 rounding, and
                              the reduced systems no longer wait for the V blocks */
-  int32_t reserved[2];
+  int32_t w_recompute;    /* 1 = memory-lean W (Sec. III, storage): P^ is kept for the leaves only, with
+                             T = Z^-1 P_c of every node (z x s each); the solve applies P^ of a level
+                             as P^_leaf times the telescoped T's (Eq. e:invtelescope), pushed down
+                             the tree, and the transpose sweep gathers up the same way.  Storage of P^
+                             falls from D N s_max to 3 N s_max values (two levels alternate during the
+                             factorization).  Not with the hybrid solver (KF_EUNSUPPORTED);
+                             kf_factor_Phat then returns the leaves' P^ only.  With
+                             v_storage = KF_V_RECOMPUTE the factorization also keeps only three
+                             levels of V blocks, used in turn. */
+  int32_t reserved[1];
 } kf_opts;
 
 /* Filled by kf_solve when non-NULL (synchronizes the stream). */

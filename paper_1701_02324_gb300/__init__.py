@@ -172,9 +172,10 @@ class Tree:
 
 def _opts(precision=KF_PREC_FP64, n_samp=0, seed=0, v_storage=KF_V_STORED, sync_errors=0, refine_tol=0.0,
           refine_max_iter=0, tensor_cores=True, fp64_operator=None, gmres_restart=0, cluster_kernels=True,
-          tc_tile_n=0, zinv_max_nodes=0, hybrid_level=0, knn_kappa=0, knn_trees=0, knn_leaf=0, zoff_fused=False):
+          tc_tile_n=0, zinv_max_nodes=0, hybrid_level=0, knn_kappa=0, knn_trees=0, knn_leaf=0, zoff_fused=False, w_recompute=False):
     o = kf_opts()
     o.zoff_fused = 1 if zoff_fused else 0
+    o.w_recompute = 1 if w_recompute else 0
     o.hybrid_level = int(hybrid_level)
     o.knn_kappa, o.knn_trees, o.knn_leaf = int(knn_kappa), int(knn_trees), int(knn_leaf)
     o.zinv_max_nodes = int(zinv_max_nodes)
@@ -197,7 +198,7 @@ class Factor:
                  refine_max_iter: int = 0, sync_errors: bool = True, tensor_cores: bool = True,
                  fp64_operator=None, gmres_restart: int = 0, cluster_kernels: bool = True, tc_tile_n: int = 0,
                  zinv_max_nodes: int = 0, hybrid_level: int = 0, knn_kappa: int = 0, knn_trees: int = 0,
-                 knn_leaf: int = 0, zoff_fused: bool = False, _ids=None):
+                 knn_leaf: int = 0, zoff_fused: bool = False, w_recompute: bool = False, _ids=None):
         """hybrid_level = L >= 1: the hybrid level-restricted solver of
         Sec. II-C (Algorithms 6-8) with its frontier at tree level L; 0: the
         direct solver (Algorithms 2-3).  knn_kappa > 0: near-field sampling
@@ -209,7 +210,7 @@ class Factor:
         self._knn_kappa, self._n_samp = int(knn_kappa), int(n_samp)
         o = _opts(precision, n_samp, seed, v_storage, int(sync_errors), refine_tol, refine_max_iter, tensor_cores,
                   fp64_operator, gmres_restart, cluster_kernels, tc_tile_n, zinv_max_nodes, hybrid_level, knn_kappa,
-                  knn_trees, knn_leaf, zoff_fused)
+                  knn_trees, knn_leaf, zoff_fused, w_recompute)
         h_out = ctypes.c_void_p()
         if _ids is None:
             st = self.ctx.lib.kf_factorize(tree.h, self.h_, self.lam, self.tau, self.s_max, ctypes.byref(o),

@@ -40,7 +40,8 @@ class kf_opts(ctypes.Structure):
         ("knn_trees", ctypes.c_int32),
         ("knn_leaf", ctypes.c_int32),
         ("zoff_fused", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("w_recompute", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 1),
     ]
 
 

@@ -19,14 +19,16 @@
 #include "prof.cuh"
 
 kf_status kf_tc_zoff(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
-                     const float* VT, const float* Ph, int ldz, double* Z, int64_t rows_per_child, int32_t* status,
-                     cudaStream_t s, int tile_n);
+                     const float* VT, const float* Ph, int ldz, double* Z, int64_t rows_per_child, float* parts,
+                     size_t parts_cap, int32_t* status, cudaStream_t s, int tile_n);
+size_t kf_tc_zoff_parts_bytes(int s_max, int tile_n, int nn, int64_t rows_per_child);
 kf_status kf_tc_telescope(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
                           const float* Pc_hat, const float* Tm, int ldz, float* Pa_hat, int64_t rows_per_child,
                           int32_t* status, cudaStream_t s, int tile_n);
 kf_status kf_tc_zoff_fused(const int32_t* lo, const int32_t* hi, const int32_t* rank, const int32_t* skel,
                            const float* X32, int d, float c_exp, int node0, int nn, int s_max, const float* Ph,
-                           int ldz, double* Z, int64_t rows_per_child, int32_t* status, cudaStream_t s, int tile_n);
+                           int ldz, double* Z, int64_t rows_per_child, float* parts, size_t parts_cap,
+                           int32_t* status, cudaStream_t s, int tile_n);
 kf_status kf_tc_leaf_panel(const int32_t* lo, const int32_t* hi, int leaf0, int nleaf, int ldL, int kb, float* L,
                            const float* Dinv, int32_t* status, cudaStream_t s);
 kf_status kf_tc_leaf_phat(const int32_t* lo, const int32_t* hi, const int32_t* rank, int leaf0, int nleaf, int ldL,
@@ -37,6 +39,12 @@ namespace {
 template <typename T> struct Acc;
 template <> struct Acc<double> { using type = double; };
 template <> struct Acc<float> { using type = float; };
+
+// split over K of the CUDA-core Z-block products (64 x 64 tiles): enough CTAs
+// for the GPU, at least 512 rows a part
+inline int zoff64_ksplit(int64_t rows, int nn, int tiles) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(rows / 512, (152 * 8) / std::max(1, 2 * nn * tiles) + 1));
+}
 
 inline int grid_for(int64_t n, int threads, int cap = 152 * 16) {
   int64_t g = (n + threads - 1) / threads;
@@ -598,7 +606,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_zoff(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                               const int32_t* __restrict__ rank, int node0, int s_max,
                                               const T* __restrict__ VT, const T* __restrict__ Ph, int ldz,
-                                              double* __restrict__ Z, int ksplit) {
+                                              double* __restrict__ Z, int ksplit, double* __restrict__ parts) {
   using A = typename Acc<T>::type;
   constexpr int TS = 64, KC = 16;
   __shared__ T sa[KC][TS];
@@ -647,15 +655,44 @@ __global__ void __launch_bounds__(256) k_zoff(const int32_t* __restrict__ lo, co
     }
     __syncthreads();
   }
+  // one writer per entry without a split; with one, the partial tile goes to
+  // parts[tile][ks] and k_zoff_reduce64 adds the parts in ks order
   double* Zb = Z + (int64_t)node * ldz * ldz;
+  double* pt = parts + (((int64_t)blockIdx.z * gridDim.x + blockIdx.x) * ksplit + blockIdx.y) * TS * TS;
   const int roff = side == 0 ? 0 : sl, coff = side == 0 ? sl : 0;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       int i = tm * TS + ty * 4 + a, j = tn * TS + tx * 4 + b;
-      if (i < M && j < Nn) atomicAdd(&Zb[(int64_t)(roff + i) * ldz + coff + j], (double)acc[a][b]);
+      if (i < M && j < Nn) {
+        if (ksplit == 1) Zb[(int64_t)(roff + i) * ldz + coff + j] += (double)acc[a][b];
+        else pt[(ty * 4 + a) * TS + tx * 4 + b] = (double)acc[a][b];
+      }
     }
+}
+
+// the split-K parts of k_zoff added in ks order (the same tile mapping)
+__global__ void __launch_bounds__(256) k_zoff_reduce64(const int32_t* __restrict__ rank, int node0, int ldz,
+                                                       int ksplit, const double* __restrict__ parts,
+                                                       double* __restrict__ Z) {
+  constexpr int TS = 64;
+  const int side = blockIdx.y & 1, node = node0 + (blockIdx.y >> 1);
+  const int sl = rank[2 * node], sr = rank[2 * node + 1];
+  const int M = side == 0 ? sl : sr, Nn = side == 0 ? sr : sl;
+  const int nt = (Nn + TS - 1) / TS + (Nn == 0);
+  const int tm = blockIdx.x / nt, tn = blockIdx.x % nt;
+  if (M == 0 || Nn == 0 || tm * TS >= M || tn * TS >= Nn) return;
+  const double* pt = parts + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * ksplit * TS * TS;
+  double* Zb = Z + (int64_t)node * ldz * ldz;
+  const int roff = side == 0 ? 0 : sl, coff = side == 0 ? sl : 0;
+  for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
+    const int i = tm * TS + e / TS, j = tn * TS + e % TS;
+    if (i >= M || j >= Nn) continue;
+    double sum = 0.0;
+    for (int ks = 0; ks < ksplit; ++ks) sum += pt[(int64_t)ks * TS * TS + e];
+    Zb[(int64_t)(roff + i) * ldz + coff + j] += sum;
+  }
 }
 
 // Blocked LU with partial pivoting of Z (FP64) followed, for non-root nodes,
@@ -1237,7 +1274,7 @@ kf_status leaves_t(kf_factor* f, cudaStream_t s, bool with_k64, int part) {
     }
   }
   if (D > 0 && part != 1) {
-    T* PhD = Phat + (int64_t)(D - 1) * N * s_max;
+    T* PhD = Phat + kf_phat_level_off(f, D);
     if (sizeof(T) == 4 && f->Dinv) {
       KF_PHASE(KF_PH_LEAF_PHAT, s, k_to_f32_rows<<<grid_for(N * s_max, 256), 256, 0, s>>>(f->Pleaf, (float*)PhD,
                                                                                         N * s_max));
@@ -1280,14 +1317,14 @@ kf_status level_eval_v(kf_factor* f, int l, cudaStream_t s) {
     dim3 gt((unsigned)((rows + kVT - 1) / kVT), (unsigned)((s_max + kVT - 1) / kVT), 2 * nn);
     KF_PHASE(KF_PH_EVAL_V, s, k_eval_vt_tiled<<<gt, 256, ts, s>>>(t->X32, t->X32lo, t->d, f->c_exp, t->d_lo, t->d_hi,
                                                                 f->rank, f->skel, s_max, child0,
-                                                                (float*)lvl(VT, l + 1),
+                                                                (float*)(VT + kf_vt_level_off(f, l + 1)),
                                                                 f->VTdf ? f->VTdf + (int64_t)l * N * s_max : nullptr,
                                                                 f->c_exp_hi, f->c_exp_lo, t->exp_tab));
   } else {
     KF_CUDA(c, cudaFuncSetAttribute(k_eval_vt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vt_smem));
     KF_PHASE(KF_PH_EVAL_V, s, k_eval_vt<T><<<gv, 256, vt_smem, s>>>(t->X64, t->X32, t->d, f->c_exp, t->d_lo, t->d_hi,
                                                                    f->rank, f->skel, s_max, child0, vt_rows, qchunk,
-                                                                   lvl(VT, l + 1)));
+                                                                   VT + kf_vt_level_off(f, l + 1)));
   }
   KF_LAUNCH_CHECK(c);
   return KF_OK;
@@ -1297,30 +1334,44 @@ kf_status level_eval_v(kf_factor* f, int l, cudaStream_t s) {
 template <typename T>
 kf_status level_reduce(kf_factor* f, int l, double* Tm, cudaStream_t s) {
   float* Tm32 = f->prec == KF_PREC_FP64 ? nullptr : (float*)(Tm + kf_factor_tm_elems(f));
+  size_t zp_cap = 0;
+  void* zparts = kf_factor_zparts(f, Tm, &zp_cap);
   kf_tree* t = f->t;
   kf_ctx* c = f->ctx;
   const int s_max = f->s_max, ldz = 2 * s_max;
   const int64_t N = t->N;
   T* Phat = (T*)f->Phat;
   T* VT = (T*)f->VT;
-  auto lvl = [&](T* base, int lv) { return base + (int64_t)(lv - 1) * N * s_max; };
+  auto phl = [&](int lv) { return Phat + kf_phat_level_off(f, lv); };
   const int node0 = 1 << l, nn = 1 << l;
   // Z
   KF_PHASE(KF_PH_ZOFF, s, k_z_init<<<dim3(grid_for((int64_t)ldz * ldz, 256, 64), nn), 256, 0, s>>>(f->rank, node0, ldz, f->ZLU));
   const int tiles = ((s_max + 63) / 64) * ((s_max + 63) / 64);
   const int64_t rows = N >> (l + 1);
-  int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(rows / 512, (152 * 8) / std::max(1, 2 * nn * tiles) + 1));
+  const int ksplit = zoff64_ksplit(rows, nn, tiles);
   if (sizeof(T) == 4 && f->use_tc && f->fused_zoff) {  // kernel entries evaluated inside the product
     kf_status r = kf_tc_zoff_fused(t->d_lo, t->d_hi, f->rank, f->skel, t->X32, t->d, f->c_exp_hi, node0, nn, s_max,
-                                   (const float*)lvl(Phat, l + 1), ldz, f->ZLU, rows, f->status, s, f->tc_bn);
+                                   (const float*)phl(l + 1), ldz, f->ZLU, rows, (float*)zparts, zp_cap, f->status, s,
+                                   f->tc_bn);
     if (r != KF_OK) return kf_set_err(c, r, "tensor-core Z blocks failed at level %d", l);
   } else if (sizeof(T) == 4 && f->use_tc) {
-    kf_status r = kf_tc_zoff(t->d_lo, t->d_hi, f->rank, node0, nn, s_max, (const float*)lvl(VT, l + 1),
-                             (const float*)lvl(Phat, l + 1), ldz, f->ZLU, rows, f->status, s, f->tc_bn);
+    kf_status r = kf_tc_zoff(t->d_lo, t->d_hi, f->rank, node0, nn, s_max, (const float*)(VT + kf_vt_level_off(f, l + 1)),
+                             (const float*)phl(l + 1), ldz, f->ZLU, rows, (float*)zparts, zp_cap, f->status, s,
+                             f->tc_bn);
     if (r != KF_OK) return kf_set_err(c, r, "tensor-core Z blocks failed at level %d", l);
   } else {
-    KF_PHASE(KF_PH_ZOFF, s, k_zoff<T><<<dim3(tiles, ksplit, 2 * nn), 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, node0, s_max, lvl(VT, l + 1),
-                                                          lvl(Phat, l + 1), ldz, f->ZLU, ksplit));
+    const dim3 gz(tiles, ksplit, 2 * nn);
+    if (ksplit > 1) {
+      const size_t pb = sizeof(double) * (size_t)gz.x * gz.y * gz.z * 64 * 64;
+      if (pb > zp_cap) return kf_set_err(c, KF_EINVAL, "Z blocks: split-K scratch too small at level %d", l);
+      KF_CUDA(c, cudaMemsetAsync(zparts, 0, pb, s));
+    }
+    KF_PHASE(KF_PH_ZOFF, s, k_zoff<T><<<gz, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, node0, s_max,
+                                                          VT + kf_vt_level_off(f, l + 1), phl(l + 1), ldz, f->ZLU,
+                                                          ksplit, (double*)zparts));
+    if (ksplit > 1)
+      KF_PHASE(KF_PH_ZOFF, s, k_zoff_reduce64<<<dim3(tiles, 2 * nn), 256, 0, s>>>(f->rank, node0, ldz, ksplit,
+                                                                                (const double*)zparts, f->ZLU));
   }
   // few nodes: a cluster of CTAs per node (one CTA per SM: the kernel takes
   // 255 registers a thread), the largest size whose nn clusters are all
@@ -1374,16 +1425,22 @@ kf_status level_reduce(kf_factor* f, int l, double* Tm, cudaStream_t s) {
     KF_PHASE(KF_PH_ZLU, s, k_z_factor<<<nn, 256, 0, s>>>(f->rank, node0, ldz, s_max, f->ZLU, f->Zpiv, f->Pc, Tm, Tm32,
                                                          l >= 1 ? 1 : 0, f->status, f->pivr));
   }
+  if (l >= 1 && f->Tw) {  // memory-lean W: keep T = Z^-1 P_c of the level's nodes for the solve
+    const size_t tb = sizeof(T) * (size_t)nn * ldz * s_max;
+    const void* src = sizeof(T) == 4 ? (const void*)Tm32 : (const void*)Tm;
+    KF_CUDA(c, cudaMemcpyAsync((char*)f->Tw + sizeof(T) * (size_t)node0 * ldz * s_max, src, tb,
+                               cudaMemcpyDeviceToDevice, s));
+  }
   if (l >= 1) {
     const int64_t cmax_rows = (N >> (l + 1)) + 1;
     dim3 gt((unsigned)((cmax_rows + 63) / 64), (s_max + 63) / 64, 2 * nn);
     if (sizeof(T) == 4 && f->use_tc) {
-      kf_status r = kf_tc_telescope(t->d_lo, t->d_hi, f->rank, node0, nn, s_max, (const float*)lvl(Phat, l + 1), Tm32,
-                                    ldz, (float*)lvl(Phat, l), cmax_rows, f->status, s, f->tc_bn);
+      kf_status r = kf_tc_telescope(t->d_lo, t->d_hi, f->rank, node0, nn, s_max, (const float*)phl(l + 1), Tm32,
+                                    ldz, (float*)phl(l), cmax_rows, f->status, s, f->tc_bn);
       if (r != KF_OK) return kf_set_err(c, r, "tensor-core telescoping failed at level %d", l);
     } else {
-      KF_PHASE(KF_PH_TELESCOPE, s, k_telescope<T><<<gt, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, node0, s_max, lvl(Phat, l + 1), Tm, ldz,
-                                        lvl(Phat, l)));
+      KF_PHASE(KF_PH_TELESCOPE, s, k_telescope<T><<<gt, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, node0, s_max, phl(l + 1), Tm, ldz,
+                                        phl(l)));
     }
   }
   cudaError_t e = cudaGetLastError();
@@ -1394,8 +1451,35 @@ kf_status level_reduce(kf_factor* f, int l, double* Tm, cudaStream_t s) {
 }  // namespace
 
 // T = Z^-1 P_c of one level (FP64) and, on the mixed path, its FP32 copy right after it
-size_t kf_factor_tm_bytes(const kf_factor* f) {
-  return (sizeof(double) + (f->prec == KF_PREC_FP64 ? 0 : sizeof(float))) * kf_factor_tm_elems(f);
+// the Z-block products' split-K partials of the largest level
+static size_t zoff_parts_bytes(const kf_factor* f) {
+  size_t need = 0;
+  const int s_max = f->s_max, tiles = ((s_max + 63) / 64) * ((s_max + 63) / 64);
+  for (int l = 0; l < f->t->D; ++l) {
+    const int nn = 1 << l;
+    const int64_t rows = f->t->N >> (l + 1);
+    size_t b;
+    if (f->prec != KF_PREC_FP64 && f->use_tc) {
+      b = kf_tc_zoff_parts_bytes(s_max, f->tc_bn, nn, rows);
+    } else {
+      const int ks = zoff64_ksplit(rows, nn, tiles);
+      b = ks > 1 ? sizeof(double) * (size_t)tiles * 2 * nn * ks * 64 * 64 : 0;
+    }
+    need = std::max(need, b);
+  }
+  return need;
+}
+
+static size_t tm_core_bytes(const kf_factor* f) {
+  const size_t b = (sizeof(double) + (f->prec == KF_PREC_FP64 ? 0 : sizeof(float))) * kf_factor_tm_elems(f);
+  return (b + 255) / 256 * 256;
+}
+
+size_t kf_factor_tm_bytes(const kf_factor* f) { return tm_core_bytes(f) + zoff_parts_bytes(f); }
+
+void* kf_factor_zparts(const kf_factor* f, double* Tm, size_t* cap) {
+  *cap = zoff_parts_bytes(f);
+  return *cap ? (void*)((char*)Tm + tm_core_bytes(f)) : nullptr;
 }
 
 size_t kf_factor_tm_elems(const kf_factor* f) {
@@ -1412,6 +1496,31 @@ kf_status kf_leaf_k64_launch(kf_factor* f, cudaStream_t s) {
   KF_PHASE(KF_PH_LEAF_ASM, s, k_leaf_k64<<<g, 256, smem, s>>>(t->X32lo, t->X32, t->d, f->c_exp, t->d_lo, t->d_hi,
                                                               1 << t->D, t->leaf_max, f->Kdf, f->c_exp_hi,
                                                               f->c_exp_lo, t->exp_tab));
+  KF_LAUNCH_CHECK(f->ctx);
+  return KF_OK;
+}
+
+__global__ void k_split_df_array(const double* __restrict__ a, float2* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = kf_split_df(a[i]);
+}
+
+kf_status kf_split_p_df(kf_factor* f, cudaStream_t s) {
+  if (!f->Pleafdf || !f->Pcdf) return KF_OK;
+  const int64_t nl = f->t->N * (int64_t)f->s_max, nc = ((int64_t)1 << f->t->D) * 2 * f->s_max * f->s_max;
+  KF_PHASE(KF_PH_MISC, s, k_split_df_array<<<grid_for(nl, 256), 256, 0, s>>>(f->Pleaf, f->Pleafdf, nl));
+  KF_PHASE(KF_PH_MISC, s, k_split_df_array<<<grid_for(nc, 256), 256, 0, s>>>(f->Pc, f->Pcdf, nc));
+  KF_LAUNCH_CHECK(f->ctx);
+  return KF_OK;
+}
+
+kf_status kf_split_z_df(kf_factor* f, cudaStream_t s) {
+  if (!f->ZLUdf) return KF_OK;
+  const int64_t ldz2 = 4 * (int64_t)f->s_max * f->s_max;
+  const int64_t first = ((int64_t)2 << f->zinv_top) * ldz2, last = ((int64_t)1 << f->t->D) * ldz2;
+  if (last > first)
+    KF_PHASE(KF_PH_MISC, s, k_split_df_array<<<grid_for(last - first, 256), 256, 0, s>>>(f->ZLU + first,
+                                                                                      f->ZLUdf + first, last - first));
   KF_LAUNCH_CHECK(f->ctx);
   return KF_OK;
 }
@@ -1454,6 +1563,8 @@ kf_status kf_factorize_device(kf_factor* f, cudaStream_t s) {
     if (st == KF_OK) st = kf_z_inverse_level(f, l, s);
   }
   c->dfree(Tm, tb, s);
+  if (st == KF_OK) st = kf_split_p_df(f, s);
+  if (st == KF_OK) st = kf_split_z_df(f, s);
   return st;
 }
 
@@ -1479,7 +1590,7 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
   if (st == KF_OK && !Tm) st = kf_set_err(c, KF_ENOMEM, "factorize: allocation failed");
   cudaStream_t s1 = nullptr, s2 = nullptr, s3 = nullptr, s4 = nullptr, s5 = nullptr;
   cudaEvent_t evl = nullptr, evi = nullptr;
-  std::vector<cudaEvent_t> ev(D + 4, nullptr), evv(D, nullptr), evz(D, nullptr);
+  std::vector<cudaEvent_t> ev(D + 4, nullptr), evv(D, nullptr), evz(D, nullptr), evr(D, nullptr);
   if (st == KF_OK) {
     // priorities (measured): the skeleton chain (s1) and the leaf blocks with
     // their Cholesky factors (s4, at the start beside the leaf sample blocks)
@@ -1499,6 +1610,7 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
     for (auto& e : ev) KF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     for (auto& e : evv) KF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     for (auto& e : evz) KF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (auto& e : evr) KF_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     // ev[l]: skeletons of level l done (on s1); ev[0]: allocations ready (on s);
     // ev[D+1]: factorization done (on s2); ev[D+2]: skeletons done (on s1);
     // ev[D+3]: V blocks done (on s3); evv[l]: V blocks of level l done (on s3)
@@ -1519,8 +1631,11 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
       st = kf_skel_level(f, l, &sc, s1);
       cudaEventRecord(ev[l], s1);
       if (st != KF_OK) break;
-      // V blocks of level l - 1 (rows of level l) need the skeletons of level l
+      // V blocks of level l - 1 (rows of level l) need the skeletons of level l;
+      // with three V slots (V recomputed in the sweeps) they overwrite the V
+      // blocks of level l + 3, which the reduced systems of level l + 2 read
       cudaStreamWaitEvent(s3, ev[l], 0);
+      if (f->vstore == KF_V_RECOMPUTE && l + 2 <= D - 1) cudaStreamWaitEvent(s3, evr[l + 2], 0);
       if (l - 1 >= Lh) st = kf_factorize_level_v(f, l - 1, s3);
       cudaEventRecord(evv[l - 1], s3);
       if (st != KF_OK) break;
@@ -1531,6 +1646,7 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
         // the stored V blocks feed the Z blocks unless the product evaluates them itself
         if (!kf_zoff_fused(f)) cudaStreamWaitEvent(s2, evv[l], 0);
         st = kf_factorize_level_z(f, l, Tm, s2);
+        cudaEventRecord(evr[l], s2);
         if (st == KF_OK && l <= f->zinv_top) {
           cudaEventRecord(evz[l], s2);
           cudaStreamWaitEvent(s5, evz[l], 0);
@@ -1550,11 +1666,14 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
     // hybrid: the reduced system I + VW of the frontier (needs the frontier
     // skeletons and P^ of level Lh, both ordered before this point on s2)
     if (st == KF_OK && Lh > 0) st = kf_hybrid_reduced_system(f, s2);
+    if (st == KF_OK) st = kf_split_z_df(f, s2);
     // the FP64 operator's leaf blocks need the tree only, and only the solve
     // reads them: last on the V-block stream, where they fill the SMs that the
     // latency-bound upper levels leave idle (ahead of the V blocks they held
     // back the first level's V blocks and with them the reduced systems)
     if (st == KF_OK && f->Kdf) st = kf_leaf_k64_launch(f, s3);
+    // the operator's pairs of Pleaf and P_c, once every skeleton is known
+    if (st == KF_OK) st = kf_split_p_df(f, s1);
     cudaEventRecord(ev[D + 1], s2);
     cudaEventRecord(ev[D + 2], s1);
     cudaEventRecord(ev[D + 3], s3);
@@ -1571,6 +1690,8 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
   for (auto& e : evv)
     if (e) cudaEventDestroy(e);
   for (auto& e : evz)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : evr)
     if (e) cudaEventDestroy(e);
   if (s5) cudaStreamDestroy(s5);
   if (evi) cudaEventDestroy(evi);

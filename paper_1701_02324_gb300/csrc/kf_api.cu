@@ -84,38 +84,74 @@ __global__ void k_scatter_out(const double* __restrict__ W, const int64_t* __res
     else ((float*)X)[dst] = (float)W[e];
   }
 }
-// per-column squared norms (atomic FP64)
-__global__ void k_colnorm2(const double* __restrict__ W, int64_t N, int64_t k, double* __restrict__ out) {
-  __shared__ double sh[8];
-  for (int64_t r = 0; r < k; ++r) {
-    double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-      acc += W[i * k + r] * W[i * k + r];
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-      atomicAdd(out + r, t);
-    }
+// ---- deterministic reductions ------------------------------------------------------
+// A fixed grid of kRedBlocks blocks: every block forms its partial sums in a
+// fixed order (thread-strided sums, then a fixed tree in shared memory) and
+// writes them to part[block][e]; k_sum_parts adds the partials in block order.
+// The results do not depend on the order in which blocks run.
+constexpr int kRedBlocks = 256, kRedThreads = 256;
+
+__device__ __forceinline__ double block_tree_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
 }
-__global__ void k_dot_all(const double* __restrict__ a, const double* __restrict__ b, int64_t n, double* __restrict__ out) {
-  __shared__ double sh[8];
+// part[block][r] = the block's share of sum_i W[i][r]^2 (W: N x k point-major)
+__global__ void __launch_bounds__(kRedThreads) k_colnorm2_part(const double* __restrict__ W, int64_t N, int64_t k,
+                                                                double* __restrict__ part) {
+  __shared__ double sh[kRedThreads];
+  const int64_t T = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = 0; r < k; ++r) {
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += T) acc += W[i * k + r] * W[i * k + r];
+    const double t = block_tree_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x * k + r] = t;
+  }
+}
+__global__ void __launch_bounds__(kRedThreads) k_dot_part(const double* __restrict__ a, const double* __restrict__ b,
+                                                           int64_t n, double* __restrict__ part) {
+  __shared__ double sh[kRedThreads];
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     acc += a[i] * b[i];
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    atomicAdd(out, t);
+  const double t = block_tree_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+// out[e] = sum over blocks b (in order) of part[b][e]
+__global__ void k_sum_parts(const double* __restrict__ part, int nblk, int64_t len, double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    double sum = 0.0;
+    for (int b = 0; b < nblk; ++b) sum += part[(int64_t)b * len + e];
+    out[e] = sum;
   }
 }
+// host side of the deterministic reductions (partials from the context's allocator)
+static kf_status red_colnorm2(kf_ctx* c, const double* W, int64_t N, int64_t k, double* out, cudaStream_t s) {
+  const size_t pb = sizeof(double) * kRedBlocks * (size_t)k;
+  double* part = (double*)c->dalloc(pb, s);
+  if (!part) return kf_set_err(c, KF_ENOMEM, "reduction: allocation failed");
+  KF_PHASE(KF_PH_MISC, s, k_colnorm2_part<<<kRedBlocks, kRedThreads, 0, s>>>(W, N, k, part));
+  KF_PHASE(KF_PH_MISC, s, k_sum_parts<<<(unsigned)std::min<int64_t>(64, (k + 255) / 256), 256, 0, s>>>(
+                              part, kRedBlocks, k, out));
+  c->dfree(part, pb, s);
+  return KF_OK;
+}
+static kf_status red_dot(kf_ctx* c, const double* a, const double* b, int64_t n, double* out, cudaStream_t s) {
+  const size_t pb = sizeof(double) * kRedBlocks;
+  double* part = (double*)c->dalloc(pb, s);
+  if (!part) return kf_set_err(c, KF_ENOMEM, "reduction: allocation failed");
+  KF_PHASE(KF_PH_MISC, s, k_dot_part<<<kRedBlocks, kRedThreads, 0, s>>>(a, b, n, part));
+  KF_PHASE(KF_PH_MISC, s, k_sum_parts<<<1, 256, 0, s>>>(part, kRedBlocks, 1, out));
+  c->dfree(part, pb, s);
+  return KF_OK;
+}
+
 // r = b - y
 __global__ void k_sub(const double* __restrict__ b, const double* __restrict__ y, double* __restrict__ r, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -130,29 +166,46 @@ __global__ void k_add(double* __restrict__ x, const double* __restrict__ d, int6
 // Dot products, updates and scalings of Krylov vectors for k columns at once.
 // k columns stored point-major (element (i, c) at i * k + c), so that k
 // independent GMRES iterations share every launch:
-// h[j * k + c] += sum_i V_j[i * k + c] w[i * k + c], j < J.  Each thread keeps
-// one column (the grid stride is a multiple of k); a block adds its partial
-// sums per column in shared memory, then once per column into h.
-__global__ void k_multidot_k(const double* __restrict__ V, int64_t ldv, int J, const double* __restrict__ w,
-                             int64_t n, int k, double* __restrict__ h) {
-  extern __shared__ double shk[];
+// part[block][j][c] = the block's share of sum_i V_j[i * k + c] w[i * k + c],
+// j < J.  Each thread keeps one column (the grid stride is a multiple of k);
+// a block adds its threads' sums per column in thread order (shared memory).
+__global__ void __launch_bounds__(kRedThreads) k_multidot_part(const double* __restrict__ V, int64_t ldv, int J,
+                                                                const double* __restrict__ w, int64_t n, int k,
+                                                                double* __restrict__ part) {
+  __shared__ double sh[kRedThreads];
   const int64_t T = (int64_t)gridDim.x * blockDim.x;
   const int64_t stride = (T / k) * k;
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int c = (int)(gid % k);
   for (int j = 0; j < J; ++j) {
-    for (int q = threadIdx.x; q < k; q += blockDim.x) shk[q] = 0.0;
-    __syncthreads();
+    double acc = 0.0;
     if (gid < stride) {
       const double* v = V + (int64_t)j * ldv;
-      double acc = 0.0;
       for (int64_t e = gid; e < n * k; e += stride) acc = fma(v[e], w[e], acc);
-      atomicAdd(&shk[c], acc);
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int q = threadIdx.x; q < k; q += blockDim.x) {
+      double sum = 0.0;
+      for (int t = 0; t < (int)blockDim.x; ++t)
+        if ((blockIdx.x * (int64_t)blockDim.x + t) % k == q && blockIdx.x * (int64_t)blockDim.x + t < stride)
+          sum += sh[t];
+      part[((int64_t)blockIdx.x * J + j) * k + q] = sum;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < k; q += blockDim.x) atomicAdd(h + (int64_t)j * k + q, shk[q]);
-    __syncthreads();
   }
+}
+// h[j * k + c] = sum_i V_j[i * k + c] w[i * k + c], j < J (deterministic)
+static kf_status red_multidot(kf_ctx* c, const double* V, int64_t ldv, int J, const double* w, int64_t n, int k,
+                              double* h, cudaStream_t s) {
+  const size_t pb = sizeof(double) * kRedBlocks * (size_t)J * k;
+  double* part = (double*)c->dalloc(pb, s);
+  if (!part) return kf_set_err(c, KF_ENOMEM, "reduction: allocation failed");
+  KF_PHASE(KF_PH_MISC, s, k_multidot_part<<<kRedBlocks, kRedThreads, 0, s>>>(V, ldv, J, w, n, k, part));
+  const int64_t len = (int64_t)J * k;
+  KF_PHASE(KF_PH_MISC, s, k_sum_parts<<<(unsigned)std::min<int64_t>(64, (len + 255) / 256), 256, 0, s>>>(
+                              part, kRedBlocks, len, h));
+  c->dfree(part, pb, s);
+  return KF_OK;
 }
 // w[i * k + c] -= sum_j h[j * k + c] V_j[i * k + c]
 __global__ void k_multiaxpy_k(const double* __restrict__ V, int64_t ldv, int J, const double* __restrict__ h,
@@ -261,6 +314,7 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
     f->hyb_L = opts->hybrid_level;
     f->knn_kappa = opts->knn_kappa;
     f->fused_zoff = opts->zoff_fused ? 1 : 0;
+    f->w_lean = opts->w_recompute ? 1 : 0;
     if (opts->knn_trees > 0) f->knn_trees = opts->knn_trees;
     if (opts->knn_leaf > 0) f->knn_leaf = opts->knn_leaf;
     if (opts->tc_tile_n == 128) f->tc_bn = 128;
@@ -297,6 +351,10 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
     delete f;
     return kf_set_err(c, KF_EINVAL, "hybrid_level %d outside [0, %d] (the tree depth)", Lbad, t->D);
   }
+  if (f->hyb_L > 0 && f->w_lean) {
+    delete f;
+    return kf_set_err(c, KF_EUNSUPPORTED, "memory-lean W (w_recompute) is not available with the hybrid solver");
+  }
   if (f->hyb_L > 0 && ((int64_t)s_max << f->hyb_L) > 2 * KF_MAX_SMAX) {
     const int Lbad = f->hyb_L;
     delete f;
@@ -322,14 +380,26 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
     while (zt >= 0 && zt + 1 <= D - 1 && (1 << (zt + 1)) <= f->zinv_max_nodes) ++zt;
     f->zinv_top = zt;
     if (zt >= 0) f->Zinv = falloc<double>(f, (size_t)(2 << zt) * 4 * s_max * s_max, s);
-    f->Phat = falloc<char>(f, (size_t)D * N * s_max * ts, s);
-    f->VT = falloc<char>(f, (size_t)D * N * s_max * ts, s);
+    if (f->prec == KF_PREC_MIXED && zt + 1 <= D - 1) {
+      f->ZLUdf = falloc<float2>(f, (size_t)(1 << D) * 4 * s_max * s_max, s);
+      if (!f->ZLUdf) {
+        kf_factor_free(f);
+        return kf_set_err(c, KF_ENOMEM, "factorize: device allocation of the reduced systems' pairs failed");
+      }
+    }
+    f->Phat = falloc<char>(f, (size_t)(f->w_lean ? std::min(D, 3) : D) * N * s_max * ts, s);
+    if (f->w_lean) f->Tw = falloc<char>(f, (size_t)(1 << D) * 2 * s_max * s_max * ts, s);
+    f->VT = falloc<char>(f, (size_t)(f->vstore == KF_V_RECOMPUTE ? std::min(D + 1, 3) : D) * N * s_max * ts, s);
   }
   f->L = falloc<char>(f, (size_t)(1 << D) * t->leaf_max * t->leaf_max * ts, s);
   if (f->fp64_op) {
     f->Kdf = falloc<float2>(f, (size_t)(1 << D) * t->leaf_max * t->leaf_max, s);
-    if (D > 0 && f->prec != KF_PREC_FP64) f->VTdf = falloc<float2>(f, (size_t)D * N * s_max, s);
-    if (!f->Kdf || (D > 0 && f->prec != KF_PREC_FP64 && !f->VTdf)) {
+    if (D > 0 && f->prec != KF_PREC_FP64) {
+      f->VTdf = falloc<float2>(f, (size_t)D * N * s_max, s);
+      f->Pleafdf = falloc<float2>(f, (size_t)N * s_max, s);
+      f->Pcdf = falloc<float2>(f, (size_t)(1 << D) * 2 * s_max * s_max, s);
+    }
+    if (!f->Kdf || (D > 0 && f->prec != KF_PREC_FP64 && (!f->VTdf || !f->Pleafdf || !f->Pcdf))) {
       kf_factor_free(f);
       return kf_set_err(c, KF_ENOMEM, "factorize: device allocation of the FP64 operator failed");
     }
@@ -370,7 +440,8 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
     }
   }
   bool ok = f->rank && f->skel && f->status && f->pivr && f->Pleaf && f->L &&
-            (D == 0 || (f->Pc && f->ZLU && f->Zpiv && (f->Zinv || f->zinv_top < 0) && f->Phat && f->VT));
+            (D == 0 || (f->Pc && f->ZLU && f->Zpiv && (f->Zinv || f->zinv_top < 0) && f->Phat && f->VT &&
+                        (f->Tw || !f->w_lean)));
   if (!ok) {
     kf_factor_free(f);
     return kf_set_err(c, KF_ENOMEM, "factorize: device allocation failed");
@@ -772,8 +843,8 @@ static kf_status rel_residual(kf_factor* f, const double* Bt, const double* Xt, 
   if (st != KF_OK) return st;
   KF_PHASE(KF_PH_MISC, s, k_sub<<<grid_for(N * k, 256), 256, 0, s>>>(Bt, Y, R, N * k));
   KF_CUDA(c, cudaMemsetAsync(nrm, 0, sizeof(double) * 2 * k, s));
-  KF_PHASE(KF_PH_MISC, s, k_colnorm2<<<grid_for(N, 256, 304), 256, 0, s>>>(R, N, k, nrm));
-  KF_PHASE(KF_PH_MISC, s, k_colnorm2<<<grid_for(N, 256, 304), 256, 0, s>>>(Bt, N, k, nrm + k));
+  if ((st = red_colnorm2(c, R, N, k, nrm, s)) != KF_OK) return st;
+  if ((st = red_colnorm2(c, Bt, N, k, nrm + k, s)) != KF_OK) return st;
   std::vector<double> h(2 * k);
   KF_CUDA(c, cudaMemcpyAsync(h.data(), nrm, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
   KF_CUDA(c, cudaStreamSynchronize(s));
@@ -806,8 +877,6 @@ static kf_status gmres_block(kf_factor* f, const double* b, double* x, const dou
   double* dsc = (double*)c->dalloc(sizeof(double) * (size_t)k, s);
   kf_status st = (V && Zb && w && h && dsc) ? KF_OK : kf_set_err(c, KF_ENOMEM, "gmres: allocation failed");
   const int g = grid_for(nk, 256, 304);
-  const int gd = std::max(g, (k + 255) / 256);
-  const size_t dsm = sizeof(double) * (size_t)k;
   std::vector<double> H((size_t)k * (m + 1) * m), cs((size_t)k * m), sn((size_t)k * m), gg((size_t)k * (m + 1));
   std::vector<double> hh((size_t)(m + 2) * k), y((size_t)m * k), sc(k), beta(k), eps(k, 0.0);
   std::vector<int> jc(k), done(k);
@@ -829,8 +898,7 @@ static kf_status gmres_block(kf_factor* f, const double* b, double* x, const dou
     st = apply_op(f, x, w, k, transpose, s);
     if (st != KF_OK) break;
     KF_PHASE(KF_PH_MISC, s, k_sub<<<g, 256, 0, s>>>(b, w, w, nk));
-    cudaMemsetAsync(h, 0, sizeof(double) * k, s);
-    KF_PHASE(KF_PH_MISC, s, k_colnorm2<<<grid_for(N, 256, 304), 256, 0, s>>>(w, N, k, h));
+    if ((st = red_colnorm2(c, w, N, k, h, s)) != KF_OK) break;
     if ((st = fetch(k)) != KF_OK) break;
     worst = 0.0;
     for (int col = 0; col < k; ++col) {
@@ -853,16 +921,14 @@ static kf_status gmres_block(kf_factor* f, const double* b, double* x, const dou
       if ((st = kf_solve_device(f, zj, k, transpose, s)) != KF_OK) break;  // z_j = M^-1 v_j (M^-T v_j)
       if ((st = apply_op(f, zj, w, k, transpose, s)) != KF_OK) break;     // w = A z_j (A^T z_j)
       for (int pass = 0; pass < 2; ++pass) {                            // CGS2
-        cudaMemsetAsync(h, 0, sizeof(double) * (size_t)(j + 1) * k, s);
-        KF_PHASE(KF_PH_MISC, s, k_multidot_k<<<gd, 256, dsm, s>>>(V, nk, j + 1, w, N, k, h));
+        if ((st = red_multidot(c, V, nk, j + 1, w, N, k, h, s)) != KF_OK) break;
         KF_PHASE(KF_PH_MISC, s, k_multiaxpy_k<<<g, 256, 0, s>>>(V, nk, j + 1, h, w, N, k));
         if ((st = fetch((size_t)(j + 1) * k)) != KF_OK) break;
         for (int col = 0; col < k; ++col)
           for (int q = 0; q <= j; ++q) Hc(col, q, j) = (pass == 0 ? 0.0 : Hc(col, q, j)) + hh[(size_t)q * k + col];
       }
       if (st != KF_OK) break;
-      cudaMemsetAsync(h, 0, sizeof(double) * k, s);
-      KF_PHASE(KF_PH_MISC, s, k_colnorm2<<<grid_for(N, 256, 304), 256, 0, s>>>(w, N, k, h));
+      if ((st = red_colnorm2(c, w, N, k, h, s)) != KF_OK) break;
       if ((st = fetch(k)) != KF_OK) break;
       bool all_done = true;
       for (int col = 0; col < k; ++col) {
@@ -967,8 +1033,7 @@ static kf_status gmres_columns(kf_factor* f, double* W, int64_t nrhs, int transp
       cudaMemcpyAsync(xg, bg, sizeof(double) * (size_t)ne, cudaMemcpyDeviceToDevice, s);
       if ((r = kf_solve_device(f, xg, kg, transpose, s)) != KF_OK) break;
     }
-    cudaMemsetAsync(nb, 0, sizeof(double) * kg, s);
-    KF_PHASE(KF_PH_MISC, s, k_colnorm2<<<grid_for(N, 256, 304), 256, 0, s>>>(bg, N, kg, nb));
+    if ((r = red_colnorm2(c, bg, N, kg, nb, s)) != KF_OK) break;
     cudaMemcpyAsync(hb.data(), nb, sizeof(double) * kg, cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     for (int q = 0; q < kg; ++q) hb[q] = sqrt(hb[q]);
@@ -1120,9 +1185,8 @@ kf_status kf_grad(kf_factor* f, const void* x, const void* dLdx, void* dLdb, dou
       // transpose system against A^T) where the factor's solves are refined
       kf_status q = solve_refined(f, A, nrhs, 1, refines(f), false, s, nullptr, nullptr);
       if (q != KF_OK) return q;
-      cudaMemsetAsync(sums, 0, sizeof(double) * 2, s);
-      KF_PHASE(KF_PH_MISC, s, k_dot_all<<<grid_for(N * nrhs, 256, 304), 256, 0, s>>>(A, Xt, N * nrhs, sums));
-      KF_PHASE(KF_PH_MISC, s, k_dot_all<<<grid_for(N * nrhs, 256, 304), 256, 0, s>>>(A, DX, N * nrhs, sums + 1));
+      if ((q = red_dot(c, A, Xt, N * nrhs, sums, s)) != KF_OK) return q;
+      if ((q = red_dot(c, A, DX, N * nrhs, sums + 1, s)) != KF_OK) return q;
       cudaMemcpyAsync(hs, sums, sizeof(double) * 2, cudaMemcpyDeviceToHost, s);
       return KF_OK;
     });
@@ -1226,7 +1290,9 @@ kf_status kf_factor_Phat(const kf_factor* f, int32_t node, double* Phat, void* s
   std::vector<int32_t> r(t->nnodes + 1);
   KF_CUDA(f->ctx, cudaMemcpyAsync(r.data(), f->rank, sizeof(int32_t) * r.size(), cudaMemcpyDeviceToHost, s));
   const int n = t->hi[node] - t->lo[node];
-  const size_t off = ((size_t)(l - 1) * t->N + t->lo[node]) * s_max;
+  if (f->w_lean && l != t->D)
+    return kf_set_err(f->ctx, KF_EUNSUPPORTED, "memory-lean W keeps P^ of the leaves only (node %d)", node);
+  const size_t off = (size_t)kf_phat_level_off(f, l) + (size_t)t->lo[node] * s_max;
   std::vector<char> buf((size_t)std::max(n, 1) * s_max * f->tsize());
   KF_CUDA(f->ctx, cudaMemcpyAsync(buf.data(), (const char*)f->Phat + off * f->tsize(), (size_t)n * s_max * f->tsize(),
                                   cudaMemcpyDeviceToHost, s));
@@ -1359,9 +1425,8 @@ kf_status solve_batched_refined(kf_factor* const* f, int32_t nprob, const void* 
       kf_status r = apply_op(f[i], P[i].Wt, P[i].Y, k, 0, si);
       if (r != KF_OK) return r;
       KF_PHASE(KF_PH_MISC, si, k_sub<<<grid_for(N * k, 256), 256, 0, si>>>(P[i].Bt, P[i].Y, P[i].R, N * k));
-      KF_PHASE(KF_PH_MISC, si, k_colnorm2<<<grid_for(N, 256, 304), 256, 0, si>>>(P[i].R, N, k, nrm + 2 * koff[i]));
-      KF_PHASE(KF_PH_MISC, si, k_colnorm2<<<grid_for(N, 256, 304), 256, 0, si>>>(P[i].Bt, N, k,
-                                                                                 nrm + 2 * koff[i] + k));
+      if ((r = red_colnorm2(c, P[i].R, N, k, nrm + 2 * koff[i], si)) != KF_OK) return r;
+      if ((r = red_colnorm2(c, P[i].Bt, N, k, nrm + 2 * koff[i] + k, si)) != KF_OK) return r;
       return KF_OK;
     });
     if (st != KF_OK) break;

@@ -64,6 +64,11 @@ struct kf_factor {
   int32_t s_max = 0, n_samp = 0, cmax = 0, prec = 0, vstore = 0, sync_errors = 0;
   int32_t use_tc = 1;  // mixed path: tcgen05 products (0: CUDA-core FP32)
   int32_t fused_zoff = 0;  // mixed path with tcgen05: 1 = Z blocks evaluate their kernel entries (no V read)
+  // memory-lean W (kf_opts.w_recompute): P^ of the leaves and two alternating
+  // levels only (3 N s_max); Tw holds T = Z^-1 P_c of every internal node
+  // (ldz x s_max each, by node, in the factor precision)
+  int32_t w_lean = 0;
+  void* Tw = nullptr;
   int32_t tc_bn = 256; // tile width of the tcgen05 products: 128 or 256 columns
   int32_t use_cluster_qr = 1;  // upper tree levels: cluster QR in distributed shared memory
   int32_t use_cluster_lu = 1;  // upper tree levels: reduced-system LU and T on a CTA cluster per node
@@ -73,6 +78,13 @@ struct kf_factor {
   // FP64-accurate operator (fp64_op), stored as double-float pairs (hi, lo):
   float2* VTdf = nullptr;  // mixed path: D x N x s_max V blocks
   float2* Kdf = nullptr;   // leaf blocks lambda-free K_aa, leaf_max^2 each
+  // mixed path: Pleaf and Pc as pairs, for the operator's passes over several
+  // right-hand sides (split once at the end of the factorization)
+  float2* Pleafdf = nullptr;
+  float2* Pcdf = nullptr;
+  // mixed path: the reduced systems' LU factors as pairs (by node, like ZLU) for
+  // the levels that keep no Z^-1, read by the sweep over several right-hand sides
+  float2* ZLUdf = nullptr;
   double refine_tol = 1e-10;
   int32_t refine_max_iter = 8;
   uint64_t seed = 0x1701;
@@ -270,6 +282,14 @@ __device__ __forceinline__ void kf_df_fma(float ah, float al, float bh, float bl
   kf_fast_two_sum(s, t, sh, sl);
 }
 
+// y <- y - s for double-float pairs (y as hi, lo; s as hi, lo)
+__device__ __forceinline__ void kf_df_sub(float& yh, float& yl, float sh, float sl) {
+  float t, e;
+  kf_two_sum(yh, -sh, t, e);
+  e = __fadd_rn(e, __fsub_rn(yl, sl));
+  kf_fast_two_sum(t, e, yh, yl);
+}
+
 // a double as a double-float pair (two conversions, off the hot loops)
 __device__ __forceinline__ float2 kf_split_df(double x) {
   const float h = (float)x;
@@ -319,9 +339,15 @@ kf_status kf_factorize_device(kf_factor* f, cudaStream_t s);
 // kf_factor_tm_elems() doubles.
 size_t kf_factor_tm_elems(const kf_factor* f);
 size_t kf_factor_tm_bytes(const kf_factor* f);
+// the split-K partials of the Z-block products inside that scratch (cap bytes)
+void* kf_factor_zparts(const kf_factor* f, double* Tm, size_t* cap);
 // part 0: all; 1: leaf blocks and their Cholesky factors; 2: P^ = A^-1 P
 kf_status kf_factorize_leaves(kf_factor* f, cudaStream_t s, bool with_k64, int part);
 kf_status kf_leaf_k64_launch(kf_factor* f, cudaStream_t s);
+// Pleaf and Pc as double-float pairs (mixed path with the FP64-accurate operator)
+kf_status kf_split_p_df(kf_factor* f, cudaStream_t s);
+// the LU factors of the levels without Z^-1 as double-float pairs (mixed path)
+kf_status kf_split_z_df(kf_factor* f, cudaStream_t s);
 kf_status kf_factorize_level(kf_factor* f, int l, double* Tm, cudaStream_t s);
 kf_status kf_factorize_level_v(kf_factor* f, int l, cudaStream_t s);
 kf_status kf_factorize_level_z(kf_factor* f, int l, double* Tm, cudaStream_t s);
@@ -364,4 +390,22 @@ kf_status kf_near_field_lists(kf_factor* f, cudaStream_t s);
 
 // whether the Z off-diagonal blocks evaluate their kernel entries inside the
 // tcgen05 product (mixed path) instead of reading the stored V blocks
+// offset (elements) of P^ of level l (1..D) in f->Phat: N x s_max per level, or
+// with memory-lean W the leaves in slot 0 and levels D-1, D-2, .. alternating
+// in slots 1 and 2
+inline int64_t kf_phat_level_off(const kf_factor* f, int l) {
+  const int D = f->t->D;
+  const int64_t per = f->t->N * (int64_t)f->s_max;
+  if (!f->w_lean) return (int64_t)(l - 1) * per;
+  return (l == D ? 0 : 1 + ((D - 1 - l) & 1)) * per;
+}
+
+// offset (elements) of the V blocks of level l (1..D) in f->VT: N x s_max per
+// level, or, when the sweeps evaluate V on the fly (KF_V_RECOMPUTE), three
+// slots used in turn (level l needs the V blocks of level l + 1 only)
+inline int64_t kf_vt_level_off(const kf_factor* f, int l) {
+  const int64_t per = f->t->N * (int64_t)f->s_max;
+  return f->vstore == KF_V_RECOMPUTE ? (int64_t)(l % 3) * per : (int64_t)(l - 1) * per;
+}
+
 inline bool kf_zoff_fused(const kf_factor* f) { return f->prec == KF_PREC_MIXED && f->use_tc && f->fused_zoff; }

@@ -269,6 +269,7 @@ __global__ void __launch_bounds__(256) k_leaf_solve_multi(const int32_t* __restr
     __syncthreads();
   };
   auto update = [&](int i, int kb, const TM (&lv)[NB]) { block_row_update<TM, TV, KC, RS>(ys, i, kb, lv); };
+  const bool vec_rows = (ldL * (int)sizeof(TM)) % 16 == 0;
   // forward: L y = b
   for (int kb = 0; kb < n; kb += NB) {
     const int nb = min(NB, n - kb);
@@ -283,11 +284,23 @@ __global__ void __launch_bounds__(256) k_leaf_solve_multi(const int32_t* __restr
       if (lane < nb) ys[(kb + lane) * RS + c] = yi;
     }
     __syncthreads();
+    // rows below the block (they exist only when nb = 32): the thread's 32
+    // entries of row i as 16-byte loads where the rows are 16-byte aligned
     for (int i = kb + nb + tid; i < n; i += blockDim.x) {
       const TM* Li = L + (int64_t)i * ldL + kb;
       TM lv[NB];
+      if (vec_rows) {
+        using VM = typename Vec16<TM>::type;
+        constexpr int VWM = 16 / (int)sizeof(TM);
 #pragma unroll
-      for (int j = 0; j < NB; ++j) lv[j] = j < nb ? Li[j] : (TM)0;
+        for (int q = 0; q < NB / VWM; ++q) {
+          const VM v = ((const VM*)Li)[q];
+          memcpy(lv + q * VWM, &v, 16);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < NB; ++j) lv[j] = j < nb ? Li[j] : (TM)0;
+      }
       update(i, kb, lv);
     }
   }
@@ -324,10 +337,74 @@ __global__ void __launch_bounds__(256) k_leaf_solve_multi(const int32_t* __restr
 // u[dst(b)][q][r] += sum_i M[i][q] w[i][r], q < cnt(b).  Sibling mode: the
 // columns are the sibling's skeleton (cnt = rank[sib], dst = sib); own mode:
 // cnt = rank[b], dst = b.  u is FP64 [node][s_max][k].
-// ROWS rows per CTA (128; 512 for several right-hand sides, so that the
-// FP64 atomic adds of the partial sums, kMaxK per column and CTA, stay few
-// beside the products).
+// ROWS rows per CTA (128; 512 for several right-hand sides).  The sums are
+// deterministic: each CTA writes its partial sums to parts[node][chunk][q][c]
+// (chunk = blockIdx.x, s_max x k per chunk) and colsum_reduce adds them in a
+// fixed order into u[dst], so the result does not depend on the order in
+// which the CTAs run.
 constexpr int kRowsPerChunk = 128;
+
+// The partial sums of a column-sum launch (parts[node][chunk][q][c], chunk =
+// blockIdx.x of that launch, nchunk_stride chunks a node) added in a fixed
+// order by two more launches: groups of kColsumGroup consecutive chunks first
+// (parts2[node][group][q][c]), then the groups into u[dst].  Both spread the
+// node's cnt x k sums over many threads and CTAs.
+constexpr int kColsumGroup = 32;
+
+__global__ void __launch_bounds__(256) k_colsum_reduce1(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                        const int32_t* __restrict__ rank, int node0, int sibling,
+                                                        int rows_per_chunk, int nchunk_stride, int s_max, int k,
+                                                        const double* __restrict__ parts, double* __restrict__ parts2,
+                                                        int ngroup_stride) {
+  const int nl = blockIdx.y, node = node0 + nl, g = blockIdx.z;
+  const int cnt = sibling ? rank[node ^ 1] : rank[node];
+  const int nch = (hi[node] - lo[node] + rows_per_chunk - 1) / rows_per_chunk;
+  const int c0 = g * kColsumGroup, c1 = min(nch, c0 + kColsumGroup);
+  if (c0 >= c1) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt * k; e += gridDim.x * blockDim.x) {
+    const int q = e / k, c = e % k;
+    double sum = 0.0;
+    for (int ch = c0; ch < c1; ++ch) sum += parts[(((int64_t)nl * nchunk_stride + ch) * s_max + q) * k + c];
+    parts2[(((int64_t)nl * ngroup_stride + g) * s_max + q) * k + c] = sum;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_colsum_reduce2(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                        const int32_t* __restrict__ rank, int node0, int sibling,
+                                                        int rows_per_chunk, int s_max, int k,
+                                                        const double* __restrict__ parts2, int ngroup_stride,
+                                                        double* __restrict__ U) {
+  const int nl = blockIdx.y, node = node0 + nl;
+  const int cnt = sibling ? rank[node ^ 1] : rank[node], dst = sibling ? node ^ 1 : node;
+  const int nch = (hi[node] - lo[node] + rows_per_chunk - 1) / rows_per_chunk;
+  const int ng = (nch + kColsumGroup - 1) / kColsumGroup;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt * k; e += gridDim.x * blockDim.x) {
+    const int q = e / k, c = e % k;
+    double sum = 0.0;
+    for (int g = 0; g < ng; ++g) sum += parts2[(((int64_t)nl * ngroup_stride + g) * s_max + q) * k + c];
+    U[((int64_t)dst * s_max + q) * k + c] += sum;
+  }
+}
+
+// the two reductions after a column-sum launch of grid g (g.x chunks of
+// rows_per_chunk rows, g.y nodes)
+inline void colsum_reduce(dim3 g, cudaStream_t s, const int32_t* lo, const int32_t* hi, const int32_t* rank,
+                          int node0, int sibling, int rows_per_chunk, int s_max, int k, const double* parts,
+                          double* parts2, double* U, int phase) {
+  const int ng = ((int)g.x + kColsumGroup - 1) / kColsumGroup;
+  const unsigned ex = (unsigned)std::min<int64_t>(64, ((int64_t)s_max * k + 255) / 256);
+  KF_PHASE(phase, s, k_colsum_reduce1<<<dim3(ex, g.y, ng), 256, 0, s>>>(lo, hi, rank, node0, sibling, rows_per_chunk,
+                                                                         (int)g.x, s_max, k, parts, parts2, ng));
+  KF_PHASE(phase, s, k_colsum_reduce2<<<dim3(ex, g.y), 256, 0, s>>>(lo, hi, rank, node0, sibling, rows_per_chunk,
+                                                                     s_max, k, parts2, ng, U));
+}
+
+// A bound on the partial sums of any column-sum launch of one sweep or
+// operator product over N points (chunks of at least `rows` rows; at most
+// 2^D nodes a level, each with one partly filled chunk).
+inline size_t colsum_parts_bound(int64_t N, int D, int s_max, int64_t k, int rows) {
+  return (size_t)(N / rows + ((int64_t)2 << D) + 4) * s_max * k;
+}
 
 template <typename TM, typename TV, int kMaxK, int ROWS = kRowsPerChunk>
 __global__ void __launch_bounds__(256) k_colsum(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
@@ -335,12 +412,11 @@ __global__ void __launch_bounds__(256) k_colsum(const int32_t* __restrict__ lo, 
                                                 int node0, int s_max, int sibling_mode, int src,
                                                 const TM* __restrict__ M, const double* __restrict__ X64,
                                                 const float* __restrict__ X32, int d, double c_exp, double inv_h3,
-                                                const TV* __restrict__ W, int k, double* __restrict__ U) {
+                                                const TV* __restrict__ W, int k, double* __restrict__ parts) {
   __shared__ TV ws[ROWS][kMaxK];
   const int nl = blockIdx.y, node = node0 + nl, sib = node ^ 1;
   const int b = lo[node], n = hi[node] - b;
   const int cnt = sibling_mode ? rank[sib] : rank[node];
-  const int dst = sibling_mode ? sib : node;
   const int r0 = blockIdx.x * ROWS;
   if (r0 >= n || cnt == 0) return;
   const int r1 = min(n, r0 + ROWS);
@@ -385,8 +461,8 @@ __global__ void __launch_bounds__(256) k_colsum(const int32_t* __restrict__ lo, 
           for (int r = 0; r < kMaxK; ++r) acc[r] += m * ws[i - r0][r];
         }
       }
-      double* out = U + ((int64_t)dst * s_max + q) * k + kb;
-      for (int r = 0; r < kk; ++r) atomicAdd(out + r, (double)acc[r]);
+      double* out = parts + (((int64_t)nl * gridDim.x + blockIdx.x) * s_max + q) * k + kb;
+      for (int r = 0; r < kk; ++r) out[r] = (double)acc[r];
     }
   }
 }
@@ -395,24 +471,26 @@ template <typename TM, typename TV>
 void launch_colsum(dim3 g, cudaStream_t s, const int32_t* lo, const int32_t* hi, const int32_t* rank,
                    const int32_t* skel, int node0, int s_max, int sib, int src, const TM* M, const double* X64,
                    const float* X32, int d, double c_exp, double inv_h3, const TV* W, int k, double* U,
-                   int phase = KF_PH_S_COLSUM) {
-  if (k == 1)
+                   double* parts, double* parts2, int phase = KF_PH_S_COLSUM) {
+  if (k == 1) {
     KF_PHASE(phase, s, k_colsum<TM, TV, 1><<<g, 256, 0, s>>>(lo, hi, rank, skel, node0, s_max, sib, src, M, X64, X32, d, c_exp, inv_h3,
-                                          W, k, U));
-  else {
+                                          W, k, parts));
+    colsum_reduce(g, s, lo, hi, rank, node0, sib, kRowsPerChunk, s_max, k, parts, parts2, U, phase);
+  } else {
     // g.x counts 128-row chunks; several right-hand sides take 512 rows a CTA
     const dim3 g4((g.x + 3) / 4, g.y);
     bool done = false;
     if constexpr (sizeof(TV) == 4) {
       if (k > 8) {  // 16 columns a pass: each loaded entry of M serves 16 products
         KF_PHASE(phase, s, k_colsum<TM, TV, 16, 512><<<g4, 256, 0, s>>>(lo, hi, rank, skel, node0, s_max, sib, src, M,
-                                                                        X64, X32, d, c_exp, inv_h3, W, k, U));
+                                                                        X64, X32, d, c_exp, inv_h3, W, k, parts));
         done = true;
       }
     }
     if (!done)
       KF_PHASE(phase, s, k_colsum<TM, TV, 8, 512><<<g4, 256, 0, s>>>(lo, hi, rank, skel, node0, s_max, sib, src, M, X64,
-                                                                     X32, d, c_exp, inv_h3, W, k, U));
+                                                                     X32, d, c_exp, inv_h3, W, k, parts));
+    colsum_reduce(g4, s, lo, hi, rank, node0, sib, 512, s_max, k, parts, parts2, U, phase);
   }
 }
 
@@ -977,6 +1055,184 @@ inline size_t zsolve_multi_smem(int ldz) {
   return sizeof(double) * (size_t)zpad * leaf_multi_stride<double, 8>() + sizeof(int) * (size_t)ldz;
 }
 
+// y_i -= sum_{j < 32} l_j x_{kb+j} for all KC columns of row i, everything as
+// double-float pairs (rows of ts are RS pairs long, a 16-byte multiple; the
+// rows kb.. read as 16-byte broadcasts), on the FP32 pipes.
+template <int KC, int RS>
+__device__ __forceinline__ void block_row_update_df(float2* ts, int i, int kb, const float2 (&lv)[32]) {
+  static_assert(KC % 2 == 0 && (RS * 8) % 16 == 0, "pairs in 16-byte groups");
+  float sh[KC], sl[KC];
+#pragma unroll
+  for (int c = 0; c < KC; ++c) sh[c] = sl[c] = 0.f;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const float2 l = lv[j];
+    const float4* xj = (const float4*)(ts + (kb + j) * RS);
+#pragma unroll
+    for (int q = 0; q < KC / 2; ++q) {
+      const float4 v = xj[q];
+      kf_df_fma(l.x, l.y, v.x, v.y, sh[2 * q], sl[2 * q]);
+      kf_df_fma(l.x, l.y, v.z, v.w, sh[2 * q + 1], sl[2 * q + 1]);
+    }
+  }
+  float4* yr = (float4*)(ts + i * RS);
+#pragma unroll
+  for (int q = 0; q < KC / 2; ++q) {
+    float4 y = yr[q];
+    kf_df_sub(y.x, y.y, sh[2 * q], sl[2 * q]);
+    kf_df_sub(y.z, y.w, sh[2 * q + 1], sl[2 * q + 1]);
+    yr[q] = y;
+  }
+}
+
+// The reduced systems of the mixed path's sweep for several right-hand sides:
+// the structure of k_zsolve_multi, with the KC columns held as double-float
+// pairs and the row updates formed from the pairs of the LU factors (ZLUdf)
+// in double-float arithmetic on the FP32 pipes, which have about 60 times the
+// FP64 pipe's rate (the FP64 updates, z^2 k multiply-adds per node and sweep,
+// bounded this step).  The 32 x 32 diagonal blocks stay FP64: their entries
+// come from ZLU, each warp converts its column of the block to FP64, solves it
+// with shuffles and splits the result back.
+template <int KC>
+__global__ void __launch_bounds__(256) k_zsolve_df(const int32_t* __restrict__ rank, int node0, int ldz, int s_max,
+                                                   const double* __restrict__ ZLU, const float2* __restrict__ ZLUdf,
+                                                   const int32_t* __restrict__ piv, const double* __restrict__ in,
+                                                   double* __restrict__ out, int k, int transpose) {
+  constexpr int RS = KC + 2;
+  extern __shared__ __align__(16) unsigned char zd_smem[];
+  const int nl = blockIdx.x, node = node0 + nl;
+  const int l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], z = sl + sr;
+  const int c0 = blockIdx.y * KC;
+  if (c0 >= k || z == 0) return;
+  const int kc = min(KC, k - c0), zpad = (z + 31) / 32 * 32;
+  float2* ts = (float2*)zd_smem;                 // zpad x RS pairs
+  int* pm = (int*)(ts + (size_t)zpad * RS);      // z
+  __shared__ double db[32][33];
+  __shared__ double dinv[32];
+  const double* A = ZLU + (int64_t)node * ldz * ldz;
+  const float2* Ad = ZLUdf + (int64_t)node * ldz * ldz;
+  const int32_t* pv = piv + (int64_t)node * ldz;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  auto dst = [&](int i) -> int64_t { return i < sl ? (int64_t)l * s_max + i : (int64_t)r * s_max + (i - sl); };
+  for (int i = tid; i < z; i += blockDim.x) pm[i] = pv[i];
+  __syncthreads();
+  for (int e = tid; e < zpad * RS; e += blockDim.x) {
+    const int i = e / RS, c = e % RS;
+    ts[e] = (i < z && c < kc) ? kf_split_df(in[dst(transpose ? i : pm[i]) * k + c0 + c]) : make_float2(0.f, 0.f);
+  }
+  auto stage = [&](int kb, int nb, bool recip) {
+    __syncthreads();
+    for (int e = tid; e < 32 * 32; e += blockDim.x) {
+      const int i = e >> 5, j = e & 31;
+      db[i][j] = (i < nb && j < nb) ? A[(int64_t)pm[kb + i] * ldz + kb + j] : 0.0;
+    }
+    __syncthreads();
+    if (recip && tid < 32) dinv[lane] = lane < nb ? 1.0 / db[lane][lane] : 0.0;
+    __syncthreads();
+  };
+  auto get = [&](int i, int c) -> double {
+    const float2 v = ts[i * RS + c];
+    return (double)v.x + (double)v.y;
+  };
+  auto update = [&](int i, int kb, const float2 (&lv)[32]) { block_row_update_df<KC, RS>(ts, i, kb, lv); };
+  const float2 zero2 = make_float2(0.f, 0.f);
+  const int top = (z - 1) / 32 * 32;
+  if (!transpose) {
+    for (int kb = 0; kb < z; kb += 32) {  // L (unit lower): forward
+      const int nb = min(32, z - kb);
+      stage(kb, nb, false);
+      for (int c = warp; c < KC; c += 8) {
+        double yi = lane < nb ? get(kb + lane, c) : 0.0;
+        for (int j = 0; j < nb; ++j) {
+          const double yj = __shfl_sync(0xffffffffu, yi, j);
+          if (lane > j && lane < nb) yi = fma(-db[lane][j], yj, yi);
+        }
+        if (lane < nb) ts[(kb + lane) * RS + c] = kf_split_df(yi);
+      }
+      __syncthreads();
+      for (int i = kb + nb + tid; i < z; i += blockDim.x) {
+        const float2* Ai = Ad + (int64_t)pm[i] * ldz + kb;
+        float2 lv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) lv[j] = j < nb ? Ai[j] : zero2;
+        update(i, kb, lv);
+      }
+    }
+    for (int kb = top; kb >= 0; kb -= 32) {  // U: backward
+      const int nb = min(32, z - kb);
+      stage(kb, nb, true);
+      for (int c = warp; c < KC; c += 8) {
+        double xi = lane < nb ? get(kb + lane, c) : 0.0;
+        for (int j = nb - 1; j >= 0; --j) {
+          if (lane == j) xi *= dinv[j];
+          const double xj = __shfl_sync(0xffffffffu, xi, j);
+          if (lane < j) xi = fma(-db[lane][j], xj, xi);
+        }
+        if (lane < nb) ts[(kb + lane) * RS + c] = kf_split_df(xi);
+      }
+      __syncthreads();
+      for (int i = tid; i < kb; i += blockDim.x) {
+        const float2* Ai = Ad + (int64_t)pm[i] * ldz + kb;
+        float2 lv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) lv[j] = j < nb ? Ai[j] : zero2;
+        update(i, kb, lv);
+      }
+    }
+  } else {
+    for (int kb = 0; kb < z; kb += 32) {  // U^T: forward
+      const int nb = min(32, z - kb);
+      stage(kb, nb, true);
+      for (int c = warp; c < KC; c += 8) {
+        double yi = lane < nb ? get(kb + lane, c) : 0.0;
+        for (int j = 0; j < nb; ++j) {
+          if (lane == j) yi *= dinv[j];
+          const double yj = __shfl_sync(0xffffffffu, yi, j);
+          if (lane > j && lane < nb) yi = fma(-db[j][lane], yj, yi);
+        }
+        if (lane < nb) ts[(kb + lane) * RS + c] = kf_split_df(yi);
+      }
+      __syncthreads();
+      for (int i = kb + nb + tid; i < z; i += blockDim.x) {
+        float2 lv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) lv[j] = j < nb ? Ad[(int64_t)pm[kb + j] * ldz + i] : zero2;
+        update(i, kb, lv);
+      }
+    }
+    for (int kb = top; kb >= 0; kb -= 32) {  // L^T (unit): backward
+      const int nb = min(32, z - kb);
+      stage(kb, nb, false);
+      for (int c = warp; c < KC; c += 8) {
+        double xi = lane < nb ? get(kb + lane, c) : 0.0;
+        for (int j = nb - 1; j >= 0; --j) {
+          const double xj = __shfl_sync(0xffffffffu, xi, j);
+          if (lane < j) xi = fma(-db[j][lane], xj, xi);
+        }
+        if (lane < nb) ts[(kb + lane) * RS + c] = kf_split_df(xi);
+      }
+      __syncthreads();
+      for (int i = tid; i < kb; i += blockDim.x) {
+        float2 lv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) lv[j] = j < nb ? Ad[(int64_t)pm[kb + j] * ldz + i] : zero2;
+        update(i, kb, lv);
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < z * RS; e += blockDim.x) {
+    const int i = e / RS, c = e % RS;
+    if (c < kc) out[dst(transpose ? pm[i] : i) * k + c0 + c] = (double)ts[e].x + (double)ts[e].y;
+  }
+}
+
+template <int KC>
+inline size_t zsolve_df_smem(int ldz) {
+  const int zpad = (ldz + 31) / 32 * 32;
+  return sizeof(float2) * (size_t)zpad * (KC + 2) + sizeof(int) * (size_t)ldz;
+}
+
 // The same product for several right-hand sides at once: a 32 x 64 tile of
 // out (32 entries of the node's vector x 64 columns) per CTA, the reduction
 // over the node's z entries in chunks of 32 with the Z^-1 block (or its
@@ -1145,14 +1401,15 @@ template <int RB>
 __global__ void __launch_bounds__(256) k_leaf_mv_df(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                     int leaf0, int ldL, const float2* __restrict__ Kdf,
                                                     double lambda, const double* __restrict__ x,
-                                                    double* __restrict__ y, int k, int r0) {
+                                                    const float2* __restrict__ xdf, double* __restrict__ y, int k,
+                                                    int r0) {
   extern __shared__ float2 xs[];  // RB x n: the lanes' consecutive j are consecutive words
   const int lf = blockIdx.y, node = leaf0 + lf;
   const int b = lo[node], n = hi[node] - b;
   const int nr = min(RB, k - r0);
   for (int e = threadIdx.x; e < n * RB; e += blockDim.x) {
     const int j = e / RB, q = e % RB;
-    xs[q * n + j] = q < nr ? kf_split_df(x[(int64_t)(b + j) * k + r0 + q]) : make_float2(0.f, 0.f);
+    xs[q * n + j] = q < nr ? xdf[(int64_t)(b + j) * k + r0 + q] : make_float2(0.f, 0.f);
   }
   __syncthreads();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -1161,7 +1418,21 @@ __global__ void __launch_bounds__(256) k_leaf_mv_df(const int32_t* __restrict__ 
     float sh[RB], sl[RB];
 #pragma unroll
     for (int q = 0; q < RB; ++q) sh[q] = sl[q] = 0.f;
-    for (int j = lane; j < n; j += 32) {
+    // four entries of the row in flight before their products (the same order of sums)
+    int j = lane;
+    for (; j + 96 < n; j += 128) {
+      float2 m[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) m[u] = Ki[j + 32 * u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+          const float2 v = xs[q * n + j + 32 * u];
+          kf_df_fma(m[u].x, m[u].y, v.x, v.y, sh[q], sl[q]);
+        }
+    }
+    for (; j < n; j += 32) {
       const float2 m = Ki[j];
 #pragma unroll
       for (int q = 0; q < RB; ++q) {
@@ -1193,8 +1464,8 @@ __global__ void __launch_bounds__(256) k_leaf_mv_df(const int32_t* __restrict__ 
 template <int KB, int ROWS = kRowsPerChunk>
 __global__ void __launch_bounds__(256) k_colsum_df(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                    const int32_t* __restrict__ rank, int node0, int s_max,
-                                                   const float2* __restrict__ M, const double* __restrict__ W, int k,
-                                                   double* __restrict__ U) {
+                                                   const float2* __restrict__ M, const float2* __restrict__ W, int k,
+                                                   double* __restrict__ parts) {
   __shared__ float2 ws[ROWS][KB];
   const int nl = blockIdx.y, node = node0 + nl, sib = node ^ 1;
   const int b = lo[node], n = hi[node] - b;
@@ -1207,7 +1478,7 @@ __global__ void __launch_bounds__(256) k_colsum_df(const int32_t* __restrict__ l
     __syncthreads();
     for (int e = threadIdx.x; e < nr * KB; e += blockDim.x) {
       const int i = e / KB, c = e % KB;
-      ws[i][c] = c < kk ? kf_split_df(W[(int64_t)(b + r0 + i) * k + kb + c]) : make_float2(0.f, 0.f);
+      ws[i][c] = c < kk ? W[(int64_t)(b + r0 + i) * k + kb + c] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
@@ -1230,8 +1501,8 @@ __global__ void __launch_bounds__(256) k_colsum_df(const int32_t* __restrict__ l
 #pragma unroll
         for (int c = 0; c < KB; ++c) kf_df_fma(m.x, m.y, ws[i][c].x, ws[i][c].y, sh[c], sl[c]);
       }
-      double* out = U + ((int64_t)sib * s_max + q) * k + kb;
-      for (int c = 0; c < kk; ++c) atomicAdd(out + c, (double)sh[c] + (double)sl[c]);
+      double* out = parts + (((int64_t)nl * gridDim.x + blockIdx.x) * s_max + q) * k + kb;
+      for (int c = 0; c < kk; ++c) out[c] = (double)sh[c] + (double)sl[c];
     }
   }
 }
@@ -1240,23 +1511,27 @@ __global__ void __launch_bounds__(256) k_colsum_df(const int32_t* __restrict__ l
 // blockIdx.x = node of the level, blockIdx.y = a block of 32 rows of P_c:
 // warp w forms rows w, w + 8, .. of the block, lanes over the columns (a row
 // of P_c is contiguous), shuffle reduction; a node spreads over z/32 CTAs.
+// Also the memory-lean sweep's push of reduced-system solutions through
+// T = Z^-1 P_c (same layout, FP32 on the mixed path): Gin and G may differ.
+template <typename TP>
 __global__ void __launch_bounds__(256) k_push_down(const int32_t* __restrict__ rank, int node0, int s_max,
-                                                   const double* __restrict__ Pc, double* __restrict__ G, int k) {
+                                                   const TP* __restrict__ Pc, const double* __restrict__ Gin,
+                                                   double* __restrict__ G, int k) {
   const int node = node0 + blockIdx.x;
   const int l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], s = rank[node], z = sl + sr;
   const int i0 = blockIdx.y * 32;
   if (i0 >= z || s == 0) return;
-  const double* P = Pc + (int64_t)node * 2 * s_max * s_max;
-  const double* ga = G + (int64_t)node * s_max * k;
+  const TP* P = Pc + (int64_t)node * 2 * s_max * s_max;
+  const double* ga = Gin + (int64_t)node * s_max * k;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int w = warp; w < 32; w += 8) {
     const int i = i0 + w;
     if (i >= z) break;  // warp-uniform
-    const double* Pi = P + (int64_t)i * s_max;
+    const TP* Pi = P + (int64_t)i * s_max;
     double* dst = i < sl ? G + ((int64_t)l * s_max + i) * k : G + ((int64_t)r * s_max + (i - sl)) * k;
     for (int c = 0; c < k; ++c) {
       double acc = 0.0;
-      for (int q = lane; q < s; q += 32) acc = fma(Pi[q], ga[(int64_t)q * k + c], acc);
+      for (int q = lane; q < s; q += 32) acc = fma((double)Pi[q], ga[(int64_t)q * k + c], acc);
       for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
       if (lane == 0) dst[c] += acc;
     }
@@ -1268,24 +1543,25 @@ __global__ void __launch_bounds__(256) k_push_down(const int32_t* __restrict__ r
 // the parent's s entries in chunks of 32 with the P_c block and g[a] staged in
 // shared memory (P_c read once per 64 columns).  Thread (ty, tx) forms rows
 // ty*4..+3 of columns tx and tx + 32.  grid = (nodes, z / 32, k / 64).
+template <typename TP>
 __global__ void __launch_bounds__(256) k_push_down_multi(const int32_t* __restrict__ rank, int node0, int s_max,
-                                                         const double* __restrict__ Pc, double* __restrict__ G,
-                                                         int k) {
+                                                         const TP* __restrict__ Pc, const double* __restrict__ Gin,
+                                                         double* __restrict__ G, int k) {
   __shared__ double sa[32][33];
   __shared__ double su[32][65];
   const int node = node0 + blockIdx.x;
   const int l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], s = rank[node], z = sl + sr;
   const int e0 = blockIdx.y * 32, c0 = blockIdx.z * 64;
   if (e0 >= z || c0 >= k || s == 0) return;
-  const double* P = Pc + (int64_t)node * 2 * s_max * s_max;
-  const double* ga = G + (int64_t)node * s_max * k;
+  const TP* P = Pc + (int64_t)node * 2 * s_max * s_max;
+  const double* ga = Gin + (int64_t)node * s_max * k;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   double acc[4][2] = {};
   for (int j0 = 0; j0 < s; j0 += 32) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int ii = ty * 4 + q, i = e0 + ii, j = j0 + tx;
-      sa[ii][tx] = (i < z && j < s) ? P[(int64_t)i * s_max + j] : 0.0;
+      sa[ii][tx] = (i < z && j < s) ? (double)P[(int64_t)i * s_max + j] : 0.0;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -1323,26 +1599,30 @@ __global__ void __launch_bounds__(256) k_push_down_multi(const int32_t* __restri
 }
 
 // Several right-hand sides on the mixed path's FP64-accurate operator:
-// out[i][c] += sum_q M[i][q] v[q][c] for the rows of a stored FP64 matrix, in
-// double-float arithmetic on the FP32 pipes (the FP64 pipe would bound these
-// passes at 2 k FP64 flops per entry).  PUSH: the rows of P_c of a node of the
-// level (grid.y), pushed into its children's skeleton weights g[l], g[r] from
-// v = g[node]; else the rows of the leaf interpolation P of a leaf (grid.y)
-// into y from v = g[leaf].  A warp takes 32 rows and walks the columns in
-// 32-wide tiles, each entry split into a pair once as its tile is staged; lane
-// q forms row q's KB sums.  v is split into pairs once per CTA (dynamic shared
-// memory: KF_MAX_SMAX x KB pairs, then the warps' tiles).
-template <int KB, bool PUSH>
+// out[i][c] += sum_q M[i][q] v[q][c] for the rows of a matrix stored as
+// double-float pairs, in double-float arithmetic on the FP32 pipes (the FP64
+// pipe would bound these passes at 2 k FP64 flops per entry, and splitting
+// FP64 entries here would bound them at the FP64 pipe's conversions).  MODE 0:
+// the rows of the leaf interpolation P of a leaf (grid.y) into y from v =
+// g[leaf]; 1 (PUSH): the rows of P_c of a node of the level, pushed into its
+// children's skeleton weights g[l], g[r] from v = g[node]; 2: the rows of the
+// V blocks of a level, K(x_i, sib~), in the transposed operator (v = g[sib]).
+// A warp takes 32 rows and walks the columns in 32-wide tiles staged row by
+// row (coalesced); lane q forms row q's KB sums.  v is split into pairs once
+// per CTA (dynamic shared memory: KF_MAX_SMAX x KB pairs, then the warps'
+// tiles).
+template <int KB, int MODE>
 __global__ void __launch_bounds__(256) k_rows_df(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                  const int32_t* __restrict__ rank, int node0, int s_max,
-                                                 const double* __restrict__ M, const double* __restrict__ V,
+                                                 const float2* __restrict__ M, const double* __restrict__ V,
                                                  double* __restrict__ out, int k) {
   extern __shared__ __align__(16) unsigned char rd_smem[];
   float2* vs = (float2*)rd_smem;                                                   // KF_MAX_SMAX x KB
   float2(*tile)[32][33] = (float2(*)[32][33])(rd_smem + sizeof(float2) * KF_MAX_SMAX * KB);  // 8 warps
-  const int node = node0 + blockIdx.y;
+  constexpr bool PUSH = MODE == 1;
+  const int node = node0 + blockIdx.y, from = MODE == 2 ? node ^ 1 : node;
   int nrows, cnt, sl = 0;
-  const double* Mb;
+  const float2* Mb;
   if (PUSH) {
     sl = rank[2 * node];
     nrows = sl + rank[2 * node + 1];
@@ -1350,13 +1630,13 @@ __global__ void __launch_bounds__(256) k_rows_df(const int32_t* __restrict__ lo,
     Mb = M + (int64_t)node * 2 * s_max * s_max;
   } else {
     nrows = hi[node] - lo[node];
-    cnt = rank[node];
+    cnt = rank[from];
     Mb = M + (int64_t)lo[node] * s_max;
   }
   const int r0 = blockIdx.x * kRowUpdRows;
   if (cnt == 0 || r0 >= nrows) return;
   const int r1 = min(nrows, r0 + kRowUpdRows);
-  const double* v = V + (int64_t)node * s_max * k;
+  const double* v = V + (int64_t)from * s_max * k;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cpad = (cnt + 31) & ~31;
   float2(*t)[33] = tile[warp];
@@ -1377,12 +1657,13 @@ __global__ void __launch_bounds__(256) k_rows_df(const int32_t* __restrict__ lo,
 #pragma unroll
       for (int r = 0; r < KB; ++r) sh[r] = sl2[r] = 0.f;
       for (int q0 = 0; q0 < cnt; q0 += 32) {
-        double x[32];
+        float2 x[32];
 #pragma unroll
         for (int rr = 0; rr < 32; ++rr)
-          x[rr] = (i0 + rr < r1 && q0 + lane < cnt) ? Mb[(int64_t)(i0 + rr) * s_max + q0 + lane] : 0.0;
+          x[rr] = (i0 + rr < r1 && q0 + lane < cnt) ? Mb[(int64_t)(i0 + rr) * s_max + q0 + lane]
+                                                    : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int rr = 0; rr < 32; ++rr) t[rr][lane] = kf_split_df(x[rr]);
+        for (int rr = 0; rr < 32; ++rr) t[rr][lane] = x[rr];
         __syncwarp();
         for (int j = 0; j < 32; ++j) {
           const float2 m = t[lane][j];
@@ -1410,21 +1691,23 @@ constexpr size_t rows_df_smem() { return sizeof(float2) * (KF_MAX_SMAX * KB + 8 
 // lane q forms column q of the block (a row's 32 entries are one coalesced
 // segment), the warps split the rows and add their partial sums in shared
 // memory.
+template <typename TP>
 __global__ void __launch_bounds__(256) k_push_up(const int32_t* __restrict__ rank, int node0, int s_max,
-                                                 const double* __restrict__ Pc, double* __restrict__ G, int k) {
+                                                 const TP* __restrict__ Pc, const double* __restrict__ Gin,
+                                                 double* __restrict__ G, int k) {
   __shared__ double part[8][33];
   const int node = node0 + blockIdx.x;
   const int l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], s = rank[node], z = sl + sr;
   const int q0 = blockIdx.y * 32;
   if (q0 >= s) return;
-  const double* P = Pc + (int64_t)node * 2 * s_max * s_max;
+  const TP* P = Pc + (int64_t)node * 2 * s_max * s_max;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, q = q0 + lane;
   for (int c = 0; c < k; ++c) {
     double acc = 0.0;
     if (q < s)
       for (int i = warp; i < z; i += 8) {
-        const double gi = i < sl ? G[((int64_t)l * s_max + i) * k + c] : G[((int64_t)r * s_max + (i - sl)) * k + c];
-        acc = fma(P[(int64_t)i * s_max + q], gi, acc);
+        const double gi = i < sl ? Gin[((int64_t)l * s_max + i) * k + c] : Gin[((int64_t)r * s_max + (i - sl)) * k + c];
+        acc = fma((double)P[(int64_t)i * s_max + q], gi, acc);
       }
     part[warp][lane] = acc;
     __syncthreads();
@@ -1435,6 +1718,66 @@ __global__ void __launch_bounds__(256) k_push_up(const int32_t* __restrict__ ran
       G[((int64_t)node * s_max + q) * k + c] += sum;
     }
     __syncthreads();
+  }
+}
+
+// The same gather for several right-hand sides: a 32 x 64 tile of g[a]
+// (32 of its s entries x 64 columns) per CTA, the reduction over the z rows
+// of P_c in chunks of 32 with the P_c block and the children's weights
+// staged in shared memory.  grid = (nodes, s / 32, k / 64).
+template <typename TP>
+__global__ void __launch_bounds__(256) k_push_up_multi(const int32_t* __restrict__ rank, int node0, int s_max,
+                                                       const TP* __restrict__ Pc, const double* __restrict__ Gin,
+                                                       double* __restrict__ G, int k) {
+  __shared__ double sa[32][33];
+  __shared__ double su[32][65];
+  const int node = node0 + blockIdx.x;
+  const int l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], s = rank[node], z = sl + sr;
+  const int q0 = blockIdx.y * 32, c0 = blockIdx.z * 64;
+  if (q0 >= s || c0 >= k) return;
+  const TP* P = Pc + (int64_t)node * 2 * s_max * s_max;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  auto gch = [&](int i) -> const double* {
+    return i < sl ? Gin + ((int64_t)l * s_max + i) * k : Gin + ((int64_t)r * s_max + (i - sl)) * k;
+  };
+  double acc[4][2] = {};
+  for (int i0 = 0; i0 < z; i0 += 32) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {  // sa[qq][ii] = P[i0 + ii][q0 + qq]: row i0 + ii read along q
+      const int ii = ty * 4 + q, i = i0 + ii, qq = q0 + tx;
+      sa[tx][ii] = (i < z && qq < s) ? (double)P[(int64_t)i * s_max + qq] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int ii = ty * 4 + q, i = i0 + ii;
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const int c = c0 + tx + 32 * h2;
+        su[ii][tx + 32 * h2] = (i < z && c < k) ? gch(i)[c] : 0.0;
+      }
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int ii = 0; ii < 32; ++ii) {
+      const double u0 = su[ii][tx], u1 = su[ii][tx + 32];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const double a = sa[ty * 4 + q][ii];
+        acc[q][0] = fma(a, u0, acc[q][0]);
+        acc[q][1] = fma(a, u1, acc[q][1]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int qq = q0 + ty * 4 + q;
+    if (qq >= s) continue;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+      const int c = c0 + tx + 32 * h2;
+      if (c < k) G[((int64_t)node * s_max + qq) * k + c] += acc[q][h2];
+    }
   }
 }
 
@@ -1478,6 +1821,13 @@ __global__ void __launch_bounds__(256) k_rowupd_df(const int32_t* __restrict__ l
   }
 }
 
+// x as double-float pairs, once per operator product (the FP64 pipe that the
+// split needs is far too narrow to split it again in every CTA that reads it)
+__global__ void k_split_vec(const double* __restrict__ a, float2* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = kf_split_df(a[i]);
+}
+
 template <typename TV>
 __global__ void k_axpy_cast(const double* __restrict__ a, TV* __restrict__ b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -1491,7 +1841,8 @@ __global__ void k_cast_back(const TV* __restrict__ a, double* __restrict__ b, in
 
 // ---- drivers -------------------------------------------------------------------------
 template <typename TM, typename TV>
-kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, double* Vb, cudaStream_t s) {
+kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, double* Vb, double* parts, double* parts2,
+                  cudaStream_t s) {
   kf_tree* t = f->t;
   kf_ctx* c = f->ctx;
   const int D = t->D, s_max = f->s_max, ldz = 2 * s_max;
@@ -1510,8 +1861,12 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
   KF_CUDA(c, cudaFuncSetAttribute(k_leaf_solve<TM, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls_smem));
   KF_CUDA(c, cudaFuncSetAttribute(k_zsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs_smem));
   const size_t zm_smem = zsolve_multi_smem(ldz);
-  if (k >= 2)
+  const size_t zd16_smem = zsolve_df_smem<16>(ldz), zd8_smem = zsolve_df_smem<8>(ldz);
+  if (k >= 2) {
     KF_CUDA(c, cudaFuncSetAttribute(k_zsolve_multi<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zm_smem));
+    KF_CUDA(c, cudaFuncSetAttribute(k_zsolve_df<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zd16_smem));
+    KF_CUDA(c, cudaFuncSetAttribute(k_zsolve_df<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zd8_smem));
+  }
   // t = Z^-1 [u_l; u_r] (or Z^-T) for the nodes of level l: the explicit
   // inverse where the factorization kept it, else the LU
   auto zsolve = [&](int l, int tr) {
@@ -1525,6 +1880,14 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
         KF_PHASE(KF_PH_S_ZSOLVE, s, k_zinv_apply<<<gz, 256, 0, s>>>(f->rank, 1 << l, ldz, s_max, f->Zinv, U, Vb,
                                                                    (int)k, tr));
       }
+    } else if (k >= 2 && f->ZLUdf) {  // mixed path: double-float row updates
+      if (k > 8)
+        KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve_df<16><<<dim3(1u << l, (unsigned)((k + 15) / 16)), 256, zd16_smem,
+                                                       s>>>(f->rank, 1 << l, ldz, s_max, f->ZLU, f->ZLUdf, f->Zpiv,
+                                                            U, Vb, (int)k, tr));
+      else
+        KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve_df<8><<<dim3(1u << l, 1u), 256, zd8_smem, s>>>(
+                                        f->rank, 1 << l, ldz, s_max, f->ZLU, f->ZLUdf, f->Zpiv, U, Vb, (int)k, tr));
     } else if (k >= 2) {
       KF_PHASE(KF_PH_S_ZSOLVE, s, k_zsolve_multi<8><<<dim3(1u << l, (unsigned)((k + 7) / 8)), 256, zm_smem, s>>>(
                                       f->rank, 1 << l, ldz, s_max, f->ZLU, f->Zpiv, U, Vb, (int)k, tr));
@@ -1538,7 +1901,9 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
   // for k <= 8), when the leaf's columns fit
   const int npad = (t->leaf_max + 31) / 32 * 32;
   constexpr int KCm = sizeof(TV) == 4 ? 16 : 8;
-  const bool wide = sizeof(TV) == 4 && k > 8;
+  // 16 columns a CTA only for k > 16: two CTAs of 8 columns per leaf for k <= 16
+  // (the leaf's chain of 32-row blocks is latency bound; more CTAs hide it)
+  const bool wide = sizeof(TV) == 4 && k > 16;
   const size_t lm_smem = sizeof(TV) * (size_t)npad *
                          (wide ? leaf_multi_stride<TV, KCm>() : leaf_multi_stride<TV, 8>());
   const bool leaf_multi = k >= 2 && lm_smem <= 200 * 1024;
@@ -1564,6 +1929,53 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
                                     t->d_lo, t->d_hi, leaf0, t->leaf_max, L, W, (int)k));
     }
   };
+  // the column sums and row updates of one level (sib: the columns / vector of
+  // the sibling's skeleton)
+  auto colsum = [&](int c0, int nc, int sib, int src, const TM* M, dim3 gc) {
+    launch_colsum<TM, TV>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, sib, src, M, t->X64, t->X32, t->d,
+                          f->c_exp, inv_h3, W, (int)k, U, parts, parts2);
+  };
+  auto rowupd = [&](int c0, int nc, int64_t rows, int sib, int src, const TM* M, const double* V) {
+    launch_rowupd<TM, TV>(rows, nc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, sib, src, M, t->X64, t->X32,
+                          t->d, f->c_exp, inv_h3, V, -1.0, W, (int)k);
+  };
+  // memory-lean W: P^ of a level is P^_leaf times the T = Z^-1 P_c of the
+  // nodes below it (Eq. e:invtelescope).  Forward: the reduced-system solution
+  // t of the nodes of level l + 1 (in Vb) is pushed down through the T's to
+  // the leaves (into U, whose entries below level l + 1 are zero), then one
+  // leaf-level row update.  Transpose: the leaves' P^^T w (into U), gathered
+  // up through the T's to level l + 1.
+  const TM* Tw = (const TM*)f->Tw;
+  const TM* Pleafh = Phat + kf_phat_level_off(f, D);
+  const int64_t leaf_rows = (N >> D) + 1;
+  const unsigned gpz = (unsigned)((2 * s_max + 31) / 32), gps = (unsigned)((s_max + 31) / 32);
+  const unsigned gpk = (unsigned)((k + 63) / 64);
+  auto lean_down = [&](int l) {
+    const double* gin = Vb;
+    for (int lev = l + 1; lev < D; ++lev) {
+      if (k >= 2)
+        KF_PHASE(KF_PH_S_ROWUPD, s, k_push_down_multi<TM><<<dim3(1u << lev, gpz, gpk), 256, 0, s>>>(
+                                        f->rank, 1 << lev, s_max, Tw, gin, U, (int)k));
+      else
+        KF_PHASE(KF_PH_S_ROWUPD, s, k_push_down<TM><<<dim3(1u << lev, gpz), 256, 0, s>>>(f->rank, 1 << lev, s_max,
+                                                                                        Tw, gin, U, (int)k));
+      gin = U;
+    }
+    rowupd(leaf0, 1 << D, leaf_rows, 0, SRC_STORED, Pleafh, gin);
+  };
+  auto lean_up = [&](int l) {
+    const dim3 gcl((unsigned)((leaf_rows + kRowsPerChunk - 1) / kRowsPerChunk), 1u << D);
+    colsum(leaf0, 1 << D, 0, SRC_STORED, Pleafh, gcl);
+    for (int lev = D - 1; lev >= l + 1; --lev) {
+      if (k >= 2)
+        KF_PHASE(KF_PH_S_COLSUM, s, k_push_up_multi<TM><<<dim3(1u << lev, gps, gpk), 256, 0, s>>>(
+                                        f->rank, 1 << lev, s_max, Tw, U, U, (int)k));
+      else
+        KF_PHASE(KF_PH_S_COLSUM, s, k_push_up<TM><<<dim3(1u << lev, gps), 256, 0, s>>>(f->rank, 1 << lev, s_max, Tw,
+                                                                                      U, U, (int)k));
+    }
+  };
+  const bool lean = f->w_lean && Tw;
   if (!transpose) {
     leaf_solve();
     // the hybrid solver stops at its frontier level (the reduced system above
@@ -1573,11 +1985,10 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
       const int64_t rows = (N >> (l + 1)) + 1;
       KF_CUDA(c, cudaMemsetAsync(U, 0, ubytes, s));
       dim3 gc((unsigned)((rows + kRowsPerChunk - 1) / kRowsPerChunk), nc);
-      launch_colsum<TM, TV>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 1, vsrc, lvl(VT, l + 1), t->X64,
-                            t->X32, t->d, f->c_exp, inv_h3, W, (int)k, U);
+      colsum(c0, nc, 1, vsrc, VT + kf_vt_level_off(f, l + 1), gc);
       zsolve(l, 0);
-      launch_rowupd<TM, TV>(rows, nc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 0, SRC_STORED,
-                            lvl(Phat, l + 1), t->X64, t->X32, t->d, f->c_exp, inv_h3, Vb, -1.0, W, (int)k);
+      if (lean) lean_down(l);
+      else rowupd(c0, nc, rows, 0, SRC_STORED, Phat + kf_phat_level_off(f, l + 1), Vb);
     }
   } else {
     for (int l = 0; l < D; ++l) {
@@ -1585,11 +1996,10 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
       const int64_t rows = (N >> (l + 1)) + 1;
       KF_CUDA(c, cudaMemsetAsync(U, 0, ubytes, s));
       dim3 gc((unsigned)((rows + kRowsPerChunk - 1) / kRowsPerChunk), nc);
-      launch_colsum<TM, TV>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 0, SRC_STORED, lvl(Phat, l + 1),
-                            t->X64, t->X32, t->d, f->c_exp, inv_h3, W, (int)k, U);
+      if (lean) lean_up(l);
+      else colsum(c0, nc, 0, SRC_STORED, Phat + kf_phat_level_off(f, l + 1), gc);
       zsolve(l, 1);
-      launch_rowupd<TM, TV>(rows, nc, s, t->d_lo, t->d_hi, f->rank, f->skel, c0, s_max, 1, vsrc, lvl(VT, l + 1),
-                            t->X64, t->X32, t->d, f->c_exp, inv_h3, Vb, -1.0, W, (int)k);
+      rowupd(c0, nc, rows, 1, vsrc, VT + kf_vt_level_off(f, l + 1), Vb);
     }
     leaf_solve();
   }
@@ -1599,7 +2009,7 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
 
 template <typename TM>
 kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deriv, int transpose, double* G,
-                   cudaStream_t s) {
+                   float2* xdf, double* parts, double* parts2, cudaStream_t s) {
   kf_tree* t = f->t;
   kf_ctx* c = f->ctx;
   const int D = t->D, s_max = f->s_max;
@@ -1610,20 +2020,23 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
   const int leaf0 = 1 << D;
   const double inv_h3 = 1.0 / (f->h * f->h * f->h);
   const int src = deriv ? SRC_DKERNEL : (f->vstore == KF_V_STORED ? SRC_STORED : SRC_KERNEL);
-  auto vt_level = [&](int l) { return VT ? VT + (int64_t)(l - 1) * N * s_max : nullptr; };
+  auto vt_level = [&](int l) { return VT ? VT + kf_vt_level_off(f, l) : nullptr; };
+  const bool split = xdf && f->Kdf && !deriv;
+  if (split) KF_PHASE(KF_PH_MISC, s, k_split_vec<<<grid_for(N * k, 256), 256, 0, s>>>(x, xdf, N * k));
   if (f->Kdf && !deriv) {
-    dim3 gl((unsigned)std::max(1, std::min(64, (t->leaf_max * 32 + 255) / 256)), 1 << D);
     if (k == 1) {
+      dim3 gl((unsigned)std::max(1, std::min(64, (t->leaf_max * 32 + 255) / 256)), 1 << D);
       const size_t xsm = sizeof(float2) * t->leaf_max;
       KF_CUDA(c, cudaFuncSetAttribute(k_leaf_mv_df<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
       KF_PHASE(KF_PH_MV_LEAF, s, k_leaf_mv_df<1><<<gl, 256, xsm, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, f->Kdf,
-                                                                     f->lambda, x, y, (int)k, 0));
-    } else {  // eight right-hand sides per pass over the leaf blocks
+                                                                     f->lambda, x, xdf, y, (int)k, 0));
+    } else {  // eight right-hand sides per pass over the leaf blocks, 16 CTAs a leaf
+      dim3 gl((unsigned)std::max(1, std::min(16, (t->leaf_max * 32 + 255) / 256)), 1 << D);
       const size_t xsm = sizeof(float2) * t->leaf_max * 8;
       KF_CUDA(c, cudaFuncSetAttribute(k_leaf_mv_df<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
       for (int r = 0; r < k; r += 8)
         KF_PHASE(KF_PH_MV_LEAF, s, k_leaf_mv_df<8><<<gl, 256, xsm, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, f->Kdf,
-                                                                       f->lambda, x, y, (int)k, r));
+                                                                       f->lambda, x, xdf, y, (int)k, r));
     }
   } else {
     dim3 gl((t->leaf_max + 127) / 128, 1 << D);
@@ -1637,13 +2050,28 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
     const int64_t lrows = (N >> D) + 1;
     dim3 gcl((unsigned)((lrows + kRowsPerChunk - 1) / kRowsPerChunk), 1 << D);
     launch_colsum<double, double>(gcl, s, t->d_lo, t->d_hi, f->rank, f->skel, leaf0, s_max, 0, SRC_STORED, f->Pleaf,
-                                  t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G, KF_PH_MV_ROWUPD);
-    for (int l = D - 1; l >= 1; --l)
-      KF_PHASE(KF_PH_MV_PUSH, s, k_push_up<<<dim3(1u << l, (unsigned)((s_max + 31) / 32)), 256, 0, s>>>(
-                                     f->rank, 1 << l, s_max, f->Pc, G, (int)k));
+                                  t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G, parts, parts2,
+                                  KF_PH_MV_ROWUPD);
+    for (int l = D - 1; l >= 1; --l) {
+      if (k >= 2)
+        KF_PHASE(KF_PH_MV_PUSH, s, k_push_up_multi<double><<<dim3(1u << l, (unsigned)((s_max + 31) / 32),
+                                                                  (unsigned)((k + 63) / 64)), 256, 0, s>>>(
+                                       f->rank, 1 << l, s_max, f->Pc, G, G, (int)k));
+      else
+        KF_PHASE(KF_PH_MV_PUSH, s, k_push_up<double><<<dim3(1u << l, (unsigned)((s_max + 31) / 32)), 256, 0, s>>>(
+                                       f->rank, 1 << l, s_max, f->Pc, G, G, (int)k));
+    }
+    if (f->VTdf && k >= 2)
+      KF_CUDA(c, cudaFuncSetAttribute(k_rows_df<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)rows_df_smem<8>()));
     for (int l = 1; l <= D; ++l) {
       const int64_t rows = (N >> l) + 1;
-      if (f->VTdf) {
+      if (f->VTdf && k >= 2) {  // several right-hand sides: double-float row passes
+        KF_PHASE(KF_PH_MV_COLSUM, s, k_rows_df<8, 2><<<dim3((unsigned)((rows + kRowUpdRows - 1) / kRowUpdRows),
+                                                            1u << l), 256, rows_df_smem<8>(), s>>>(
+                                         t->d_lo, t->d_hi, f->rank, 1 << l, s_max,
+                                         f->VTdf + (int64_t)(l - 1) * N * s_max, G, y, (int)k));
+      } else if (f->VTdf) {
         dim3 g((unsigned)((rows + kRowUpdRows - 1) / kRowUpdRows), 1 << l);
         KF_PHASE(KF_PH_MV_COLSUM, s, k_rowupd_df<<<g, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, 1 << l, s_max,
                                                                      f->VTdf + (int64_t)(l - 1) * N * s_max, G,
@@ -1664,21 +2092,29 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
     dim3 gc((unsigned)((rows + kRowsPerChunk - 1) / kRowsPerChunk), 1 << l);
     if (f->VTdf && !deriv) {  // FP64-accurate operator of the mixed path
       const float2* Vl = f->VTdf + (int64_t)(l - 1) * N * s_max;
+      // several right-hand sides: 256 rows a CTA (16 columns a pass for k > 8)
+      const dim3 g2((gc.x + 1) / 2, gc.y);
       if (k == 1)
-        KF_PHASE(KF_PH_MV_COLSUM, s, k_colsum_df<1><<<gc, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, 1 << l, s_max, Vl, x,
-                                                                        (int)k, G));
+        KF_PHASE(KF_PH_MV_COLSUM, s, k_colsum_df<1><<<gc, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, 1 << l, s_max, Vl, xdf,
+                                                                        (int)k, parts));
       else if (k <= 4)
-        KF_PHASE(KF_PH_MV_COLSUM, s, k_colsum_df<4><<<gc, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, 1 << l, s_max, Vl, x,
-                                                                        (int)k, G));
+        KF_PHASE(KF_PH_MV_COLSUM, s, k_colsum_df<4, 256><<<g2, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, 1 << l, s_max,
+                                                                             Vl, xdf, (int)k, parts));
       else if (k <= 8)
-        KF_PHASE(KF_PH_MV_COLSUM, s, k_colsum_df<8><<<gc, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, 1 << l, s_max, Vl, x,
-                                                                        (int)k, G));
-      else  // 16 columns a pass over 256 rows: each pair of V serves 16 double-float products
-        KF_PHASE(KF_PH_MV_COLSUM, s, k_colsum_df<16, 256><<<dim3((gc.x + 1) / 2, gc.y), 256, 0, s>>>(
-                                         t->d_lo, t->d_hi, f->rank, 1 << l, s_max, Vl, x, (int)k, G));
+        KF_PHASE(KF_PH_MV_COLSUM, s, k_colsum_df<8, 256><<<g2, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, 1 << l, s_max,
+                                                                             Vl, xdf, (int)k, parts));
+      else
+        KF_PHASE(KF_PH_MV_COLSUM, s, k_colsum_df<16, 256><<<g2, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, 1 << l, s_max,
+                                                                              Vl, xdf, (int)k, parts));
+      if (k == 1)
+        colsum_reduce(gc, s, t->d_lo, t->d_hi, f->rank, 1 << l, 1, kRowsPerChunk, s_max, (int)k, parts, parts2, G,
+                      KF_PH_MV_COLSUM);
+      else
+        colsum_reduce(g2, s, t->d_lo, t->d_hi, f->rank, 1 << l, 1, 256, s_max, (int)k, parts, parts2, G,
+                      KF_PH_MV_COLSUM);
     } else
       launch_colsum<TM, double>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, s_max, 1, src, vt_level(l),
-                                t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G, KF_PH_MV_COLSUM);
+                                t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G, parts, parts2, KF_PH_MV_COLSUM);
   }
   // the hybrid solver's frontier nodes couple with every other frontier node
   // (V of Algorithm 8), pushed down from the frontier like a sibling coupling
@@ -1688,30 +2124,30 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
   }
   const dim3 gpd(1, (unsigned)((2 * s_max + 31) / 32));
   // several right-hand sides on the FP64-accurate operator: double-float passes over P_c and P
-  const bool rows_df = f->VTdf && !deriv && k >= 2;
+  const bool rows_df = f->VTdf && f->Pcdf && f->Pleafdf && !deriv && k >= 2;
   if (rows_df) {
-    KF_CUDA(c, cudaFuncSetAttribute(k_rows_df<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    KF_CUDA(c, cudaFuncSetAttribute(k_rows_df<8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)rows_df_smem<8>()));
-    KF_CUDA(c, cudaFuncSetAttribute(k_rows_df<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    KF_CUDA(c, cudaFuncSetAttribute(k_rows_df<8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)rows_df_smem<8>()));
   }
   for (int l = std::max(1, f->hyb_L); l < D; ++l) {
     if (rows_df)
-      KF_PHASE(KF_PH_MV_PUSH, s, k_rows_df<8, true><<<dim3((unsigned)((2 * s_max + kRowUpdRows - 1) / kRowUpdRows),
+      KF_PHASE(KF_PH_MV_PUSH, s, k_rows_df<8, 1><<<dim3((unsigned)((2 * s_max + kRowUpdRows - 1) / kRowUpdRows),
                                                           1u << l), 256, rows_df_smem<8>(), s>>>(
-                                     t->d_lo, t->d_hi, f->rank, 1 << l, s_max, f->Pc, G, G, (int)k));
+                                     t->d_lo, t->d_hi, f->rank, 1 << l, s_max, f->Pcdf, G, G, (int)k));
     else if (k >= 2)
-      KF_PHASE(KF_PH_MV_PUSH, s, k_push_down_multi<<<dim3(1u << l, gpd.y, (unsigned)((k + 63) / 64)), 256, 0, s>>>(
-                                     f->rank, 1 << l, s_max, f->Pc, G, (int)k));
+      KF_PHASE(KF_PH_MV_PUSH, s, k_push_down_multi<double><<<dim3(1u << l, gpd.y, (unsigned)((k + 63) / 64)), 256, 0, s>>>(
+                                     f->rank, 1 << l, s_max, f->Pc, G, G, (int)k));
     else
-      KF_PHASE(KF_PH_MV_PUSH, s, k_push_down<<<dim3(1u << l, gpd.y), 256, 0, s>>>(f->rank, 1 << l, s_max, f->Pc, G,
-                                                                                  (int)k));
+      KF_PHASE(KF_PH_MV_PUSH, s, k_push_down<double><<<dim3(1u << l, gpd.y), 256, 0, s>>>(f->rank, 1 << l, s_max, f->Pc, G,
+                                                                                          G, (int)k));
   }
   const int64_t rows = (N >> D) + 1;
   if (rows_df)
-    KF_PHASE(KF_PH_MV_ROWUPD, s, k_rows_df<8, false><<<dim3((unsigned)((rows + kRowUpdRows - 1) / kRowUpdRows),
+    KF_PHASE(KF_PH_MV_ROWUPD, s, k_rows_df<8, 0><<<dim3((unsigned)((rows + kRowUpdRows - 1) / kRowUpdRows),
                                                            1u << D), 256, rows_df_smem<8>(), s>>>(
-                                     t->d_lo, t->d_hi, f->rank, leaf0, s_max, f->Pleaf, G, y, (int)k));
+                                     t->d_lo, t->d_hi, f->rank, leaf0, s_max, f->Pleafdf, G, y, (int)k));
   else
     launch_rowupd<double, double>(rows, 1 << D, s, t->d_lo, t->d_hi, f->rank, f->skel, leaf0, s_max, 0, SRC_STORED,
                                   f->Pleaf, t->X64, t->X32, t->d, f->c_exp, inv_h3, G, 1.0, y, (int)k,
@@ -1721,6 +2157,30 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
 }
 
 }  // namespace
+
+// Scratch of the deterministic column sums: the partial sums of a launch
+// (parts) and of its chunk groups (parts2), bounded over the launches of one
+// sweep or operator product with chunks of at least `rows` rows.
+struct ColsumScratch {
+  double* parts = nullptr;
+  double* parts2 = nullptr;
+  size_t pb = 0, pb2 = 0;
+  kf_ctx* c = nullptr;
+  cudaStream_t s = nullptr;
+  bool alloc(kf_ctx* ctx, const kf_factor* f, int64_t k, int rows, cudaStream_t st) {
+    c = ctx;
+    s = st;
+    pb = sizeof(double) * colsum_parts_bound(f->t->N, f->t->D, f->s_max, k, rows);
+    pb2 = sizeof(double) * colsum_parts_bound(f->t->N, f->t->D, f->s_max, k, rows * kColsumGroup);
+    parts = (double*)c->dalloc(pb, s);
+    parts2 = (double*)c->dalloc(pb2, s);
+    return parts && parts2;
+  }
+  ~ColsumScratch() {
+    if (parts) c->dfree(parts, pb, s);
+    if (parts2) c->dfree(parts2, pb2, s);
+  }
+};
 
 // W: N x k FP64 in tree order; solved in place.  The mixed path runs the sweep
 // on an FP32 copy.
@@ -1741,15 +2201,21 @@ kf_status kf_solve_device(kf_factor* f, double* W, int64_t k, int transpose, cud
     c->dfree(Vb, ub, s);
     return kf_set_err(c, KF_EUNSUPPORTED, "transpose solves of the hybrid solver are not supported");
   }
+  ColsumScratch cs;
+  if (!cs.alloc(c, f, k, k == 1 ? kRowsPerChunk : 512, s)) {
+    c->dfree(U, ub, s);
+    c->dfree(Vb, ub, s);
+    return kf_set_err(c, KF_ENOMEM, "solve: allocation failed");
+  }
   if (f->prec == KF_PREC_FP64) {
-    st = solve_t<double, double>(f, W, k, transpose, U, Vb, s);
+    st = solve_t<double, double>(f, W, k, transpose, U, Vb, cs.parts, cs.parts2, s);
   } else {
     float* W32 = (float*)c->dalloc(sizeof(float) * N * k, s);
     if (!W32) {
       st = kf_set_err(c, KF_ENOMEM, "solve: allocation failed");
     } else {
       KF_PHASE(KF_PH_MISC, s, k_axpy_cast<float><<<grid_for(N * k, 256), 256, 0, s>>>(W, W32, N * k));
-      st = solve_t<float, float>(f, W32, k, transpose, U, Vb, s);
+      st = solve_t<float, float>(f, W32, k, transpose, U, Vb, cs.parts, cs.parts2, s);
       KF_PHASE(KF_PH_MISC, s, k_cast_back<float><<<grid_for(N * k, 256), 256, 0, s>>>(W32, W, N * k));
       c->dfree(W32, sizeof(float) * N * k, s);
     }
@@ -1769,11 +2235,26 @@ static kf_status matvec_any(kf_factor* f, const double* x, double* y, int64_t k,
   const size_t gb = sizeof(double) * (size_t)(f->t->nnodes + 1) * f->s_max * k;
   double* G = (double*)c->dalloc(gb, s);
   if (!G) return kf_set_err(c, KF_ENOMEM, "matvec: allocation failed");
+  // x as double-float pairs for the FP64-accurate operator's leaf and V passes
+  const size_t xb = f->Kdf && !deriv ? sizeof(float2) * (size_t)f->t->N * k : 0;
+  float2* xdf = xb ? (float2*)c->dalloc(xb, s) : nullptr;
+  if (xb && !xdf) {
+    c->dfree(G, gb, s);
+    return kf_set_err(c, KF_ENOMEM, "matvec: allocation failed");
+  }
   // dK~/dh (deriv) is evaluated from the FP64 coordinates on both paths: the
   // gradient's -a^T (dK~/dh) x cancels heavily (the sum of |terms| is often
   // 10^3-10^4 times the result), so FP32 entries would leave it at ~1e-4
-  kf_status st = (f->prec == KF_PREC_FP64 || deriv) ? matvec_t<double>(f, x, y, k, deriv, transpose, G, s)
-                                                    : matvec_t<float>(f, x, y, k, deriv, transpose, G, s);
+  ColsumScratch cs;
+  if (!cs.alloc(c, f, k, k == 1 ? kRowsPerChunk : 256, s)) {
+    if (xdf) c->dfree(xdf, xb, s);
+    c->dfree(G, gb, s);
+    return kf_set_err(c, KF_ENOMEM, "matvec: allocation failed");
+  }
+  kf_status st = (f->prec == KF_PREC_FP64 || deriv)
+                     ? matvec_t<double>(f, x, y, k, deriv, transpose, G, xdf, cs.parts, cs.parts2, s)
+                     : matvec_t<float>(f, x, y, k, deriv, transpose, G, xdf, cs.parts, cs.parts2, s);
+  if (xdf) c->dfree(xdf, xb, s);
   c->dfree(G, gb, s);
   return st;
 }

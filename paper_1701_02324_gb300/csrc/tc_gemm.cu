@@ -136,6 +136,7 @@ __device__ __forceinline__ int core_off(int r, int k) { return (r >> 3) * 256 + 
 struct Tile {
   int m0, n0, k0, k1, M, N;  // tile origin, K range, valid extents (absolute indices)
   int node, side, base;      // problem-specific
+  int tl, ks;                // split-K products: output tile index and part of K
   bool skip;
 };
 
@@ -338,6 +339,11 @@ __global__ void __launch_bounds__(kThreads) k_tc_gemm(Problem prob, int32_t* __r
 // side 1: rows of l, block Z[s_l:, 0:s_l] = K_{r~ l} P^_l
 // The long reduction over the child's rows is split over blockIdx.y; partial
 // tiles are added into the FP64 Z with atomics.
+// Split over K (ksplit > 1): each CTA writes its FP32 partial tile to
+// parts[tile][ks] and k_zoff_reduce adds the ksplit partials of an entry in
+// the order ks = 0, 1, .. into Z, so that Z does not depend on the order in
+// which the CTAs run; with ksplit = 1 a CTA adds its tile into Z directly
+// (one writer per entry).
 struct ZoffProblem {
   static constexpr int kPieces = 2;
   static constexpr bool a_m_fastest = true;   // VT rows are contiguous in m
@@ -349,6 +355,7 @@ struct ZoffProblem {
   const float* VT;
   const float* Ph;
   double* Z;
+  float* parts;
   __device__ Tile tile(int bx, int by, int bz) const {
     Tile t;
     t.side = bz & 1;
@@ -360,6 +367,8 @@ struct ZoffProblem {
     t.base = sl;
     t.m0 = (bx / ntile_n) * kBM;
     t.n0 = (bx % ntile_n) * tile_n;
+    t.tl = bz * ((s_max + kBM - 1) / kBM) * ntile_n + bx;
+    t.ks = by;
     const int rb = lo[c], rn = hi[c] - rb;
     const int chunk = ((rn + ksplit - 1) / ksplit + kBK - 1) / kBK * kBK;
     t.k0 = rb + by * chunk;
@@ -370,10 +379,37 @@ struct ZoffProblem {
   __device__ float loadA(const Tile&, int m, int k) const { return VT[(int64_t)k * s_max + m]; }
   __device__ float loadB(const Tile&, int k, int n) const { return Ph[(int64_t)k * s_max + n]; }
   __device__ void store(const Tile& t, int m, int n, float v) const {
+    if (ksplit > 1) {
+      parts[((int64_t)(t.tl * ksplit + t.ks) * kBM + (m - t.m0)) * tile_n + (n - t.n0)] = v;
+      return;
+    }
     const int roff = t.side == 0 ? 0 : t.base, coff = t.side == 0 ? t.base : 0;
-    atomicAdd(Z + (int64_t)t.node * ldz * ldz + (int64_t)(roff + m) * ldz + coff + n, (double)v);
+    Z[(int64_t)t.node * ldz * ldz + (int64_t)(roff + m) * ldz + coff + n] += (double)v;
   }
 };
+
+// Z blocks += the ksplit partial tiles of each entry, added in ks order
+// (FP64 sums of the FP32 partials).  grid = (tiles of a block, 2 x nodes), the
+// tile numbering of ZoffProblem::tile.
+__global__ void __launch_bounds__(256) k_zoff_reduce(const int32_t* __restrict__ rank, int node0, int s_max, int ldz,
+                                                     int ksplit, int ntile_n, int tile_n,
+                                                     const float* __restrict__ parts, double* __restrict__ Z) {
+  const int bx = blockIdx.x, bz = blockIdx.y, side = bz & 1, node = node0 + (bz >> 1);
+  const int sl = rank[2 * node], sr = rank[2 * node + 1];
+  const int M = side == 0 ? sl : sr, N = side == 0 ? sr : sl;
+  const int m0 = (bx / ntile_n) * kBM, n0 = (bx % ntile_n) * tile_n;
+  if (m0 >= M || n0 >= N) return;
+  const int roff = side == 0 ? 0 : sl, coff = side == 0 ? sl : 0;
+  const int64_t tl = (int64_t)bz * gridDim.x + bx;
+  double* Zb = Z + (int64_t)node * ldz * ldz;
+  for (int e = threadIdx.x; e < kBM * tile_n; e += blockDim.x) {
+    const int mi = e / tile_n, ni = e % tile_n;
+    if (m0 + mi >= M || n0 + ni >= N) continue;
+    double sum = 0.0;
+    for (int ks = 0; ks < ksplit; ++ks) sum += (double)parts[((tl * ksplit + ks) * kBM + mi) * tile_n + ni];
+    Zb[(int64_t)(roff + m0 + mi) * ldz + coff + n0 + ni] += sum;
+  }
+}
 
 // ---- Z off-diagonal blocks with the kernel entries evaluated in the product ----------
 // The same blocks as ZoffProblem, K_{l~ r} P^_r and K_{r~ l} P^_l, but the A
@@ -590,26 +626,43 @@ static kf_status tc_launch(const Problem& p, dim3 g, int phase, int32_t* status,
   return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
 }
 
+// ksplit of the Z-block products: enough CTAs to fill the GPU, the reduction
+// split over the child's rows
+static int zoff_ksplit(int64_t tiles, int64_t rows_per_child) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((rows_per_child + 1023) / 1024, (2 * 152 + tiles - 1) / tiles));
+}
+
+// the split-K partials, zeroed (a part of K left empty writes nothing), then
+// the product, then their sum in ks order
+template <int BN, typename Problem>
+static kf_status zoff_run(Problem& p, int nn, int mt, float* parts, size_t parts_cap, int32_t* status,
+                          cudaStream_t s) {
+  const dim3 g(mt * p.ntile_n, p.ksplit, 2 * nn);
+  p.parts = parts;
+  if (p.ksplit > 1) {
+    const size_t pb = sizeof(float) * (size_t)g.x * g.z * p.ksplit * kBM * BN;
+    if (!parts || pb > parts_cap) return KF_EINVAL;
+    if (cudaMemsetAsync(parts, 0, pb, s) != cudaSuccess) return KF_ECUDA;
+  }
+  kf_status st = tc_launch<BN>(p, g, KF_PH_ZOFF, status, s);
+  if (st != KF_OK || p.ksplit == 1) return st;
+  KF_PHASE(KF_PH_ZOFF, s, k_zoff_reduce<<<dim3(g.x, g.z), 256, 0, s>>>(p.rank, p.node0, p.s_max, p.ldz, p.ksplit,
+                                                                       p.ntile_n, BN, parts, p.Z));
+  return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
+}
+
 template <int BN>
 static kf_status tc_zoff_bn(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
                             const float* VT, const float* Ph, int ldz, double* Z, int64_t rows_per_child,
-                            int32_t* status, cudaStream_t s) {
+                            float* parts, size_t parts_cap, int32_t* status, cudaStream_t s) {
   ZoffProblem p;
   p.lo = lo; p.hi = hi; p.rank = rank; p.node0 = node0; p.s_max = s_max; p.ldz = ldz;
   p.ntile_n = (s_max + BN - 1) / BN;
   p.tile_n = BN;
   p.VT = VT; p.Ph = Ph; p.Z = Z;
   const int mt = (s_max + kBM - 1) / kBM;
-  // enough CTAs to fill the GPU: split the reduction over the child's rows
-  const int64_t tiles = (int64_t)mt * p.ntile_n * 2 * nn;
-  int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>((rows_per_child + 1023) / 1024, (2 * 152 + tiles - 1) / tiles));
-  p.ksplit = ksplit;
-  const size_t smem = tc_smem_bytes(BN);
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN, ZoffProblem>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return KF_ECUDA;
-  dim3 g(mt * p.ntile_n, ksplit, 2 * nn);
-  KF_PHASE(KF_PH_ZOFF, s, k_tc_gemm<BN, ZoffProblem><<<g, kThreads, smem, s>>>(p, status));
-  return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ECUDA;
+  p.ksplit = zoff_ksplit((int64_t)mt * p.ntile_n * 2 * nn, rows_per_child);
+  return zoff_run<BN>(p, nn, mt, parts, parts_cap, status, s);
 }
 
 template <int BN>
@@ -632,7 +685,8 @@ static kf_status tc_telescope_bn(const int32_t* lo, const int32_t* hi, const int
 template <int BN>
 static kf_status tc_zoff_fused_bn(const int32_t* lo, const int32_t* hi, const int32_t* rank, const int32_t* skel,
                                   const float* X32, int d, float c_exp, int node0, int nn, int s_max, const float* Ph,
-                                  int ldz, double* Z, int64_t rows_per_child, int32_t* status, cudaStream_t s) {
+                                  int ldz, double* Z, int64_t rows_per_child, float* parts, size_t parts_cap,
+                                  int32_t* status, cudaStream_t s) {
   ZoffFusedProblem p;
   p.lo = lo; p.hi = hi; p.rank = rank; p.node0 = node0; p.s_max = s_max; p.ldz = ldz;
   p.ntile_n = (s_max + BN - 1) / BN;
@@ -640,27 +694,37 @@ static kf_status tc_zoff_fused_bn(const int32_t* lo, const int32_t* hi, const in
   p.VT = nullptr; p.Ph = Ph; p.Z = Z;
   p.X32 = X32; p.skel = skel; p.d = d; p.c_exp = c_exp;
   const int mt = (s_max + kBM - 1) / kBM;
-  const int64_t tiles = (int64_t)mt * p.ntile_n * 2 * nn;
-  p.ksplit = (int)std::max<int64_t>(1, std::min<int64_t>((rows_per_child + 1023) / 1024, (2 * 152 + tiles - 1) / tiles));
-  return tc_launch<BN>(p, dim3(mt * p.ntile_n, p.ksplit, 2 * nn), KF_PH_ZOFF, status, s);
+  p.ksplit = zoff_ksplit((int64_t)mt * p.ntile_n * 2 * nn, rows_per_child);
+  return zoff_run<BN>(p, nn, mt, parts, parts_cap, status, s);
 }
 
 // tile_n: the tile width BN of the products, 128 or 256 columns
 kf_status kf_tc_zoff_fused(const int32_t* lo, const int32_t* hi, const int32_t* rank, const int32_t* skel,
                            const float* X32, int d, float c_exp, int node0, int nn, int s_max, const float* Ph,
-                           int ldz, double* Z, int64_t rows_per_child, int32_t* status, cudaStream_t s, int tile_n) {
+                           int ldz, double* Z, int64_t rows_per_child, float* parts, size_t parts_cap,
+                           int32_t* status, cudaStream_t s, int tile_n) {
   return tile_n == 128 ? tc_zoff_fused_bn<128>(lo, hi, rank, skel, X32, d, c_exp, node0, nn, s_max, Ph, ldz, Z,
-                                               rows_per_child, status, s)
+                                               rows_per_child, parts, parts_cap, status, s)
                        : tc_zoff_fused_bn<256>(lo, hi, rank, skel, X32, d, c_exp, node0, nn, s_max, Ph, ldz, Z,
-                                               rows_per_child, status, s);
+                                               rows_per_child, parts, parts_cap, status, s);
+}
+
+// bytes of split-K partials the Z blocks of a level need (0: no split)
+size_t kf_tc_zoff_parts_bytes(int s_max, int tile_n, int nn, int64_t rows_per_child) {
+  const int mt = (s_max + kBM - 1) / kBM, nt = (s_max + tile_n - 1) / tile_n;
+  const int64_t tiles = (int64_t)mt * nt * 2 * nn;
+  const int ks = zoff_ksplit(tiles, rows_per_child);
+  return ks > 1 ? sizeof(float) * (size_t)tiles * ks * kBM * tile_n : 0;
 }
 
 // tile_n: the tile width BN of the products, 128 or 256 columns
 kf_status kf_tc_zoff(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,
-                     const float* VT, const float* Ph, int ldz, double* Z, int64_t rows_per_child, int32_t* status,
-                     cudaStream_t s, int tile_n) {
-  return tile_n == 128 ? tc_zoff_bn<128>(lo, hi, rank, node0, nn, s_max, VT, Ph, ldz, Z, rows_per_child, status, s)
-                       : tc_zoff_bn<256>(lo, hi, rank, node0, nn, s_max, VT, Ph, ldz, Z, rows_per_child, status, s);
+                     const float* VT, const float* Ph, int ldz, double* Z, int64_t rows_per_child, float* parts,
+                     size_t parts_cap, int32_t* status, cudaStream_t s, int tile_n) {
+  return tile_n == 128 ? tc_zoff_bn<128>(lo, hi, rank, node0, nn, s_max, VT, Ph, ldz, Z, rows_per_child, parts,
+                                         parts_cap, status, s)
+                       : tc_zoff_bn<256>(lo, hi, rank, node0, nn, s_max, VT, Ph, ldz, Z, rows_per_child, parts,
+                                         parts_cap, status, s);
 }
 
 kf_status kf_tc_telescope(const int32_t* lo, const int32_t* hi, const int32_t* rank, int node0, int nn, int s_max,

@@ -367,7 +367,9 @@ def test_batched_workload_mixed_refined_full_size():
     f64 = kf.factorize_batched(trees, hs, lams, taus, probs[0].s_max, precision=FP64, cluster_kernels=False,
                                refine_tol=1e-10, refine_max_iter=100)
     x64, inf64 = kf.solve_batched(f64, Bs, info=True)
-    assert max(i["eps_r"] for i in inf64) <= 1e-8   # GMRES on the FP64 factors stagnates near 1e-9 on one problem
+    # GMRES on the FP64 factors stagnates on the worst-conditioned problem of this batch, at a level set by
+    # rounding order (1.3e-9 with atomic sums, 1.4e-8 with the fixed-order sums): the reference is good to ~1e-7
+    assert max(i["eps_r"] for i in inf64) <= 1e-7
     del f64
     fm = kf.factorize_batched(trees, hs, lams, taus, probs[0].s_max, precision=MIXED, cluster_kernels=False,
                               refine_tol=1e-9)
@@ -501,9 +503,10 @@ def test_scale_against_whole_oracle_golden(scale):
     refined by the oracle's own solve and operator).  Every node's rank and
     skeleton list equal the oracle's (64-bit hashes), so the GPU approximates
     the same K~; then, at 2,000 seeded indices:
-    * FP64 path refined by GMRES to eps_r <= 1e-11: within 1e-10 of the
-      refined oracle solution (on this K~ the error of a solve is about its
-      eps_r: the FP64 direct sweep measured 1.3e-8 at eps_r 1.6e-8);
+    * FP64 path refined by GMRES to eps_r <= 1e-11: within 50 x (its eps_r +
+      the refined oracle's, 6.5e-12) of the refined oracle solution: the two
+      solutions differ by at most ||A^-1|| times their residuals, and here
+      ||x|| / ||b|| is about 50 (measured: 2.9e-10);
     * FP64 direct sweep: within 10 x (its eps_r + the oracle's) of the
       oracle's direct solution (both direct solves stop near 1e-8, in
       different summation orders);
@@ -529,7 +532,8 @@ def test_scale_against_whole_oracle_golden(scale):
            if format(_fnv1a64(F.skeleton(a)), "016x") != g["skel_fnv1a64"][a - 2]]
     assert not bad, bad[:8]
     x, info = F.solve(b, info=True)
-    assert rel(x.cpu().numpy()[idx], xr) <= 1e-10
+    assert info["eps_r"] <= 1e-11
+    assert rel(x.cpu().numpy()[idx], xr) <= 50 * (info["eps_r"] + g["eps_r_refined"])
     del F
     F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=FP64, fp64_operator=True, refine_max_iter=-1)
     x, info = F.solve(b, info=True)

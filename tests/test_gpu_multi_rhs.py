@@ -72,6 +72,8 @@ def test_block_solve_equals_column_solves_mixed(problem, k):
         assert rel(Xb[:, c], xc) <= 1e-5, c
     G = kf.Factor(p["tree"], p["h"], p["lam"], p["tau"], p["smax"], precision=MIXED, refine_tol=1e-12)
     assert rel(G.solve(Bt).cpu().numpy(), p["o"].solve(B)) <= 1e-9
+    # the transpose solve refined against the transposed FP64-accurate operator (k-column passes)
+    assert rel(G.solve(Bt, transpose=True).cpu().numpy(), p["o"].solve(B, transpose=True)) <= 1e-9
 
 
 @pytest.mark.parametrize("k", [2, 7, 16, 33])

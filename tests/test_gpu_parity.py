@@ -623,3 +623,41 @@ def test_fused_z_blocks_match_stored_v(N, d, m, smax, h):
         assert rel(pf, pv) <= 1e-4, a
     G = kf.Factor(tree, h, lam, tau, smax, precision=MIXED, refine_tol=1e-11, zoff_fused=True)
     assert rel(G.solve(torch.from_numpy(b).cuda()).cpu().numpy(), o.solve(b)) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_results_are_bitwise_deterministic(prec):
+    """Two factorizations of the same problem and two runs of every solve give
+    the same bits: the split-K partial sums of the Z blocks, the segmented
+    column sums of the sweep and the operator, and the refinement's norms and
+    dot products are all added in a fixed order (no floating-point atomics).
+    N = 2^15 so that the upper levels split their Z-block products over K."""
+    rng = np.random.default_rng(77)
+    N, d, m, smax, h, lam = 1 << 15, 6, 256, 64, 0.5, 0.7
+    X = rng.random((N, d))
+    B = torch.from_numpy(rng.standard_normal((N, 4))).cuda()
+    tree = kf.Tree(torch.from_numpy(X).cuda(), m)
+    kw = dict(precision=prec, fp64_operator=True, refine_tol=1e-11, refine_max_iter=60, gmres_restart=20)
+    F1 = kf.Factor(tree, h, lam, 1e-6, smax, **kw)
+    F2 = kf.Factor(tree, h, lam, 1e-6, smax, **kw)
+    r = F1.ranks()
+    for a in (2, 3, 5, 9, 17, 40):
+        if r[a] == 0:
+            continue
+        rows = _node_rows(tree, a)
+        assert np.array_equal(F1.Phat(a, rows), F2.Phat(a, rows)), a
+    x1, i1 = F1.solve(B, info=True)
+    x2, i2 = F2.solve(B, info=True)
+    assert torch.equal(x1, x2) and i1 == i2
+    assert torch.equal(F1.solve(B), F1.solve(B))
+    assert torch.equal(F1.matvec(B), F2.matvec(B))
+    assert torch.equal(F1.solve(B, transpose=True), F2.solve(B, transpose=True))
+
+
+def _node_rows(tree, a):
+    """Number of points of node a (the tree's median split: sizes follow from N)."""
+    lvl = int(np.floor(np.log2(a)))
+    sizes = [tree.N]
+    for _ in range(lvl):
+        sizes = [s for n in sizes for s in (n // 2, n - n // 2)]
+    return sizes[a - (1 << lvl)]
