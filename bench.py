@@ -469,7 +469,7 @@ def gpu_main(args, rank, world):
     fact_s, solve_s, ms_per_step = max_over_ranks([fact_s, solve_s, ms_per_step], dev)
 
     # ---- FP64 comparison leg (same workload, same skeletons) ---------------------
-    fp64, unref, at_bar = None, None, None
+    fp64, unref, at_bar, vs_oracle = None, None, None, None
     if not args.no_fp64:
         def timed(prec, refined, nsteps):
             ff, fs, x = [], [], None
@@ -503,6 +503,19 @@ def gpu_main(args, rank, world):
                  "rel_err_vs_reference": relf(xun),
                  "note": "mixed factors without the FP64 operator and without refinement"}
         mixed_rel = relf(x_mixed)
+        # errors against the whole oracle run of this workload (a golden written by the oracle alone:
+        # its refined solution at 2,000 seeded indices)
+        gpath = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "scale_oracle.json")
+        if os.path.exists(gpath):
+            gold = json.load(open(gpath))
+            if gold["N"] == p.N and gold["seed"] == p.seed and gold["s_max"] == p.s_max:
+                gidx = torch.tensor(gold["index"], device=dev)
+                gx = torch.tensor([float(v) for v in gold["x_refined"]], dtype=torch.float64, device=dev)
+                relo = lambda a: float(torch.linalg.norm(a[gidx] - gx) / torch.linalg.norm(gx))
+                vs_oracle = {"fp64_direct": relo(x64), "mixed_timed_solve": relo(x_mixed),
+                             "fp64_refined_reference": relo(xref),
+                             "what": "relative error at the 2,000 indices of the whole oracle run's refined "
+                                     "solution (eps_r %.1e)" % gold["eps_r_refined"]}
         reference = {"what": "FP64 factorization + GMRES against the FP64 operator", "eps_r": iref["eps_r"],
                      "iters": iref["iters"]}
         # the mixed solve stopped at the metric's own bar instead (relative error <= 1e-5 against the
@@ -520,6 +533,8 @@ def gpu_main(args, rank, world):
         torch.cuda.synchronize()
         at_bar = {"refine_tol": 1e-6, "gmres_iters": ib["iters"], "eps_r": ib["eps_r"],
                   "solve_rhs_per_s": round(1e3 / e0.elapsed_time(e1), 2), "rel_err_vs_reference": relf(xb_)}
+        if vs_oracle is not None:
+            vs_oracle["mixed_at_1e-5"] = relo(xb_)
         del Fb, tree, xb_
 
     # ---- near-field sampling of S' (knn_kappa = 16): the same workload and metric ------
@@ -847,13 +862,15 @@ def gpu_main(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "scale_N1048576_d28", "N": p.N, "d": p.d, "h": p.h, "lambda": p.lam, "m": p.m,
                        "s_max": p.s_max, "tau": p.tau, "n_samp": 2 * p.s_max, "nrhs": 1,
-                       "precision": "mixed (FP32 factors, tcgen05 3xTF32 products; FP64 ID, Z, T, operator, GMRES)",
+                       "precision": "mixed (FP32 factors, tcgen05 products of 3xTF32 or three tf32 pieces; FP64 ID, Z, T, operator, GMRES)",
                        "parallelism": f"replicas x{world}", "l2": "inputs and factors larger than L2 (no flush)"},
             # the metric's comparison, as top-level scalars
             "solve_rhs_per_s": round(1.0 / solve_s, 2),
             "solve_note": f"mixed: FP32 sweep + GMRES({args.gmres_m}) vs the FP64 operator to eps_r <= {args.mixed_tol:g}",
             "gmres_iters": float(np.mean(gmres_iters[-args.steps:])) if gmres_iters else None,
             "mixed_rel_err_vs_reference": mixed_rel if fp64 else None,
+            "mixed_rel_err_vs_oracle": vs_oracle["mixed_timed_solve"] if vs_oracle else None,
+            "fp64_rel_err_vs_oracle": vs_oracle["fp64_direct"] if vs_oracle else None,
             "mixed_solve_rhs_per_s_at_1e-5": at_bar["solve_rhs_per_s"] if at_bar else None,
             "mixed_rel_err_at_1e-5": at_bar["rel_err_vs_reference"] if at_bar else None,
             "fp64_factorize_s": fp64["factorize_s"] if fp64 else None,
@@ -894,6 +911,7 @@ def gpu_main(args, rank, world):
                           "candidate_ms": [round(t, 2) for t in v[1]]} for k, v in tuned.items()} or None,
             "fp64_path": fp64, "mixed_unrefined": unref, "mixed_solve_at_metric_bar": at_bar,
             "solve_seed_study": seed_study, "accuracy_reference": reference if fp64 else None,
+            "vs_whole_oracle": vs_oracle,
             "near_field_sampling": near,
             "memory_lean_w": lean,
             "differentiation": diff, "batched": batched,

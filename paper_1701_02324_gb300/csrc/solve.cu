@@ -1398,7 +1398,7 @@ __global__ void __launch_bounds__(128) k_leaf_mv(const int32_t* __restrict__ lo,
 // Kdf is read once for all of them; per right-hand side the arithmetic and its
 // order are those of RB = 1.
 template <int RB>
-__global__ void __launch_bounds__(256) k_leaf_mv_df(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+__global__ void __launch_bounds__(512) k_leaf_mv_df(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
                                                     int leaf0, int ldL, const float2* __restrict__ Kdf,
                                                     double lambda, const double* __restrict__ x,
                                                     const float2* __restrict__ xdf, double* __restrict__ y, int k,
@@ -1686,6 +1686,35 @@ __global__ void __launch_bounds__(256) k_rows_df(const int32_t* __restrict__ lo,
 template <int KB>
 constexpr size_t rows_df_smem() { return sizeof(float2) * (KF_MAX_SMAX * KB + 8 * 32 * 33); }
 
+// The memory-lean sweep's push of reduced-system solutions, one right-hand
+// side: g[l], g[r] += T g[a] with T = Z^-1 P_c, in the factor's precision (the
+// sweep's: FP32 on the mixed path, where FP64 products would bound this push
+// at the FP64 pipe's rate), g[a] staged in shared memory once per CTA;
+// blockIdx.x = node, blockIdx.y = a block of 32 rows of T, a warp per row.
+template <typename TP>
+__global__ void __launch_bounds__(256) k_push_down_lean(const int32_t* __restrict__ rank, int node0, int s_max,
+                                                        const TP* __restrict__ Tw, const double* __restrict__ Gin,
+                                                        double* __restrict__ G) {
+  __shared__ TP gs[KF_MAX_SMAX];
+  const int node = node0 + blockIdx.x;
+  const int l = 2 * node, r = l + 1, sl = rank[l], sr = rank[r], s = rank[node], z = sl + sr;
+  const int i0 = blockIdx.y * 32;
+  if (i0 >= z || s == 0) return;
+  const TP* P = Tw + (int64_t)node * 2 * s_max * s_max;
+  for (int q = threadIdx.x; q < s; q += blockDim.x) gs[q] = (TP)Gin[(int64_t)node * s_max + q];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int w = warp; w < 32; w += 8) {
+    const int i = i0 + w;
+    if (i >= z) break;  // warp-uniform
+    const TP* Pi = P + (int64_t)i * s_max;
+    TP acc = (TP)0;
+    for (int q = lane; q < s; q += 32) acc += Pi[q] * gs[q];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) (i < sl ? G[(int64_t)l * s_max + i] : G[(int64_t)r * s_max + (i - sl)]) += (double)acc;
+  }
+}
+
 // Gather skeleton weights up (transposed operator): g[a] += P_c^T [g[l]; g[r]].
 // blockIdx.x = node of the level, blockIdx.y = a block of 32 columns of P_c:
 // lane q forms column q of the block (a row's 32 entries are one coalesced
@@ -1957,8 +1986,8 @@ kf_status solve_t(kf_factor* f, TV* W, int64_t k, int transpose, double* U, doub
         KF_PHASE(KF_PH_S_ROWUPD, s, k_push_down_multi<TM><<<dim3(1u << lev, gpz, gpk), 256, 0, s>>>(
                                         f->rank, 1 << lev, s_max, Tw, gin, U, (int)k));
       else
-        KF_PHASE(KF_PH_S_ROWUPD, s, k_push_down<TM><<<dim3(1u << lev, gpz), 256, 0, s>>>(f->rank, 1 << lev, s_max,
-                                                                                        Tw, gin, U, (int)k));
+        KF_PHASE(KF_PH_S_ROWUPD, s, k_push_down_lean<TM><<<dim3(1u << lev, gpz), 256, 0, s>>>(f->rank, 1 << lev,
+                                                                                             s_max, Tw, gin, U));
       gin = U;
     }
     rowupd(leaf0, 1 << D, leaf_rows, 0, SRC_STORED, Pleafh, gin);
@@ -2030,12 +2059,12 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
       KF_CUDA(c, cudaFuncSetAttribute(k_leaf_mv_df<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
       KF_PHASE(KF_PH_MV_LEAF, s, k_leaf_mv_df<1><<<gl, 256, xsm, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, f->Kdf,
                                                                      f->lambda, x, xdf, y, (int)k, 0));
-    } else {  // eight right-hand sides per pass over the leaf blocks, 16 CTAs a leaf
-      dim3 gl((unsigned)std::max(1, std::min(16, (t->leaf_max * 32 + 255) / 256)), 1 << D);
+    } else {  // eight right-hand sides per pass over the leaf blocks, 8 CTAs of 16 warps a leaf
+      dim3 gl((unsigned)std::max(1, std::min(8, (t->leaf_max * 32 + 511) / 512)), 1 << D);
       const size_t xsm = sizeof(float2) * t->leaf_max * 8;
       KF_CUDA(c, cudaFuncSetAttribute(k_leaf_mv_df<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
       for (int r = 0; r < k; r += 8)
-        KF_PHASE(KF_PH_MV_LEAF, s, k_leaf_mv_df<8><<<gl, 256, xsm, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, f->Kdf,
+        KF_PHASE(KF_PH_MV_LEAF, s, k_leaf_mv_df<8><<<gl, 512, xsm, s>>>(t->d_lo, t->d_hi, leaf0, t->leaf_max, f->Kdf,
                                                                        f->lambda, x, xdf, y, (int)k, r));
     }
   } else {
