@@ -916,6 +916,9 @@ def gpu_main(args, rank, world):
             "memory_lean_w": lean,
             "differentiation": diff, "batched": batched,
         }
+        for k, v in line.items():  # errors to three significant figures in the one-line summary
+            if isinstance(v, float) and "rel_err" in k:
+                line[k] = float(f"{v:.3g}")
         print(json.dumps(line), flush=True)
         # the per-phase and per-workload figures: one JSON line on stderr (and a file on request)
         print(json.dumps(detail), file=sys.stderr, flush=True)
