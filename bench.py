@@ -952,19 +952,21 @@ def ctypes_p():
     return ctypes.c_void_p
 
 
-def multi_rhs_case():
+def multi_rhs_case(tc_operator=False):
     """The scale recipe at N = 2^17 with near-field sampling, mixed factors with
     the FP64 operator copy and Z^-1 on the levels of at most 8 nodes (so that
     levels 4-6 solve their reduced systems by LU): one operator product and one
     direct sweep of 16 right-hand sides, twice (the case the profiles of the
-    several-right-hand-side kernels are taken on)."""
+    several-right-hand-side kernels are taken on).  tc_operator: the factors
+    also keep the BF16 digits of V, and the product's V pass runs on the
+    tensor cores."""
     import torch
     import paper_1701_02324_gb300 as kf
     from paper_1701_02324_gb300 import inputs
     p = inputs.scale(1 << 17)
     tree = kf.Tree(torch.from_numpy(p.X).cuda(), p.m)
     F = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=kf.KF_PREC_MIXED, fp64_operator=True,
-                  refine_max_iter=-1, knn_kappa=16, sync_errors=False, zinv_max_nodes=8)
+                  refine_max_iter=-1, knn_kappa=16, sync_errors=False, zinv_max_nodes=8, tc_operator=tc_operator)
     B = torch.from_numpy(inputs.rhs(p.N, 16, 5)).cuda()
     for _ in range(2):
         Y = F.matvec(B)
@@ -1008,12 +1010,14 @@ def main():
     ap.add_argument("--detail-out", default=None, help="also write the per-phase / per-workload details to this file")
     ap.add_argument("--multi-rhs-case", action="store_true",
                     help="run the small case the several-right-hand-side kernels are profiled on and exit")
+    ap.add_argument("--tc-operator", action="store_true",
+                    help="--multi-rhs-case: factors with the BF16 digits of V (tensor-core V pass)")
     args = ap.parse_args()
     if args.once:
         once(args)
         return
     if args.multi_rhs_case:
-        multi_rhs_case()
+        multi_rhs_case(args.tc_operator)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -142,7 +142,12 @@ typedef struct {
                              kf_factor_Phat then returns the leaves' P^ only.  With
                              v_storage = KF_V_RECOMPUTE the factorization also keeps only three
                              levels of V blocks, used in turn. */
-  int32_t reserved[1];
+  int32_t tc_operator;    /* mixed path with fp64_operator: 1 = also keep the V blocks as exact BF16
+                             integer digits (7 per entry, 14 bytes, Ozaki splitting), so that the
+                             FP64-accurate operator's V pass (Eq. e:blocksmw) over 16 or more
+                             right-hand sides runs as tcgen05 products with exact FP32 accumulation
+                             (about 2^-49 max|x_r| per product, against the double-float kernels'
+                             2^-46 |V x|); 0 = double-float CUDA-core passes only (default) */
 } kf_opts;
 
 /* Filled by kf_solve when non-NULL (synchronizes the stream). */

@@ -172,9 +172,11 @@ class Tree:
 
 def _opts(precision=KF_PREC_FP64, n_samp=0, seed=0, v_storage=KF_V_STORED, sync_errors=0, refine_tol=0.0,
           refine_max_iter=0, tensor_cores=True, fp64_operator=None, gmres_restart=0, cluster_kernels=True,
-          tc_tile_n=0, zinv_max_nodes=0, hybrid_level=0, knn_kappa=0, knn_trees=0, knn_leaf=0, zoff_fused=False, w_recompute=False):
+          tc_tile_n=0, zinv_max_nodes=0, hybrid_level=0, knn_kappa=0, knn_trees=0, knn_leaf=0, zoff_fused=False, w_recompute=False,
+          tc_operator=False):
     o = kf_opts()
     o.zoff_fused = 1 if zoff_fused else 0
+    o.tc_operator = 1 if tc_operator else 0
     o.w_recompute = 1 if w_recompute else 0
     o.hybrid_level = int(hybrid_level)
     o.knn_kappa, o.knn_trees, o.knn_leaf = int(knn_kappa), int(knn_trees), int(knn_leaf)
@@ -198,19 +200,22 @@ class Factor:
                  refine_max_iter: int = 0, sync_errors: bool = True, tensor_cores: bool = True,
                  fp64_operator=None, gmres_restart: int = 0, cluster_kernels: bool = True, tc_tile_n: int = 0,
                  zinv_max_nodes: int = 0, hybrid_level: int = 0, knn_kappa: int = 0, knn_trees: int = 0,
-                 knn_leaf: int = 0, zoff_fused: bool = False, w_recompute: bool = False, _ids=None):
+                 knn_leaf: int = 0, zoff_fused: bool = False, w_recompute: bool = False, tc_operator: bool = False,
+                 _ids=None):
         """hybrid_level = L >= 1: the hybrid level-restricted solver of
         Sec. II-C (Algorithms 6-8) with its frontier at tree level L; 0: the
         direct solver (Algorithms 2-3).  knn_kappa > 0: near-field sampling
         of S' from every point's knn_kappa nearest neighbours (knn_trees
-        projection trees with leaves of knn_leaf points)."""
+        projection trees with leaves of knn_leaf points).  tc_operator: the
+        mixed path's FP64-accurate operator keeps its V blocks as exact BF16
+        digits as well, for tensor-core V passes over 16 or more columns."""
         self.tree, self.ctx = tree, tree.ctx
         self.h_, self.lam, self.tau, self.s_max, self.precision = float(h), float(lam), float(tau), int(s_max), precision
         self.hybrid_level = int(hybrid_level)
         self._knn_kappa, self._n_samp = int(knn_kappa), int(n_samp)
         o = _opts(precision, n_samp, seed, v_storage, int(sync_errors), refine_tol, refine_max_iter, tensor_cores,
                   fp64_operator, gmres_restart, cluster_kernels, tc_tile_n, zinv_max_nodes, hybrid_level, knn_kappa,
-                  knn_trees, knn_leaf, zoff_fused, w_recompute)
+                  knn_trees, knn_leaf, zoff_fused, w_recompute, tc_operator)
         h_out = ctypes.c_void_p()
         if _ids is None:
             st = self.ctx.lib.kf_factorize(tree.h, self.h_, self.lam, self.tau, self.s_max, ctypes.byref(o),
@@ -407,7 +412,8 @@ def factorize_batched(trees, hs, lams, taus, s_max: int, precision=KF_PREC_MIXED
     o = _opts(precision, n_samp, seed, KF_V_STORED, 0, refine_tol, refine_max_iter,
               tensor_cores=kw.get("tensor_cores", True), fp64_operator=kw.get("fp64_operator"),
               gmres_restart=kw.get("gmres_restart", 0), cluster_kernels=kw.get("cluster_kernels", True),
-              tc_tile_n=kw.get("tc_tile_n", 0), zinv_max_nodes=kw.get("zinv_max_nodes", 0))
+              tc_tile_n=kw.get("tc_tile_n", 0), zinv_max_nodes=kw.get("zinv_max_nodes", 0),
+              tc_operator=kw.get("tc_operator", False))
     out = (ctypes.c_void_p * n)()
     tarr = _ptr_array([t.h.value for t in trees])
     st = ctx.lib.kf_factorize_batched(tarr, n, h.ctypes.data_as(ctypes.c_void_p), lam.ctypes.data_as(ctypes.c_void_p),

@@ -41,7 +41,7 @@ class kf_opts(ctypes.Structure):
         ("knn_leaf", ctypes.c_int32),
         ("zoff_fused", ctypes.c_int32),
         ("w_recompute", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 1),
+        ("tc_operator", ctypes.c_int32),
     ]
 
 

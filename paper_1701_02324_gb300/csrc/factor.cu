@@ -1320,6 +1320,10 @@ kf_status level_eval_v(kf_factor* f, int l, cudaStream_t s) {
                                                                 (float*)(VT + kf_vt_level_off(f, l + 1)),
                                                                 f->VTdf ? f->VTdf + (int64_t)l * N * s_max : nullptr,
                                                                 f->c_exp_hi, f->c_exp_lo, t->exp_tab));
+    if (f->VTsl) {
+      kf_status zs = kf_oz_slice_v(f, l + 1, s);
+      if (zs != KF_OK) return zs;
+    }
   } else {
     KF_CUDA(c, cudaFuncSetAttribute(k_eval_vt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vt_smem));
     KF_PHASE(KF_PH_EVAL_V, s, k_eval_vt<T><<<gv, 256, vt_smem, s>>>(t->X64, t->X32, t->d, f->c_exp, t->d_lo, t->d_hi,
@@ -1497,7 +1501,7 @@ kf_status kf_leaf_k64_launch(kf_factor* f, cudaStream_t s) {
                                                               1 << t->D, t->leaf_max, f->Kdf, f->c_exp_hi,
                                                               f->c_exp_lo, t->exp_tab));
   KF_LAUNCH_CHECK(f->ctx);
-  return KF_OK;
+  return kf_oz_slice_leaf(f, s);  // their BF16 digits, when the factors keep them (tc_operator)
 }
 
 __global__ void k_split_df_array(const double* __restrict__ a, float2* __restrict__ b, int64_t n) {

@@ -315,6 +315,7 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
     f->knn_kappa = opts->knn_kappa;
     f->fused_zoff = opts->zoff_fused ? 1 : 0;
     f->w_lean = opts->w_recompute ? 1 : 0;
+    f->use_oz = opts->tc_operator > 0 ? 1 : 0;
     if (opts->knn_trees > 0) f->knn_trees = opts->knn_trees;
     if (opts->knn_leaf > 0) f->knn_leaf = opts->knn_leaf;
     if (opts->tc_tile_n == 128) f->tc_bn = 128;
@@ -402,6 +403,13 @@ kf_status alloc_factor(kf_tree* t, double h, double lambda, double tau, int32_t 
     if (!f->Kdf || (D > 0 && f->prec != KF_PREC_FP64 && (!f->VTdf || !f->Pleafdf || !f->Pcdf))) {
       kf_factor_free(f);
       return kf_set_err(c, KF_ENOMEM, "factorize: device allocation of the FP64 operator failed");
+    }
+    if (f->use_oz && f->use_tc && f->VTdf) {  // BF16 digits of the V blocks (tc_operator)
+      kf_status zs = kf_oz_alloc(f, s);
+      if (zs != KF_OK) {
+        kf_factor_free(f);
+        return zs;
+      }
     }
   }
   if (f->prec == KF_PREC_MIXED && f->use_tc) {  // leaf factorization on the tensor cores

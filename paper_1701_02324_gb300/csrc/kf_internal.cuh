@@ -133,10 +133,42 @@ struct kf_factor {
   float* Dinv = nullptr;
   double* ltrack = nullptr;
   int32_t* status = nullptr;
-  double* pivr = nullptr;  // per node: smallest / largest pivot of its leaf Cholesky or Z LU
+  double* pivr = nullptr;
+  // mixed path, FP64-accurate operator with tc_operator: the V blocks as exact
+  // BF16 integer digits for the tensor-core V pass of blocks of right-hand
+  // sides (oz_op.cu): tiles of 128 rows x 128 skeleton columns x 7 digits, by
+  // level (element offsets oz_off[l]) and 128-row window (oz_wbase: first
+  // window of each node within its level, heap indexed)
+  int32_t use_oz = 0;
+  uint16_t* VTsl = nullptr;
+  uint16_t* Ksl = nullptr;  // the leaf blocks' digits: (leaf, row tile, column window) tiles
+  int32_t* oz_wbase = nullptr;
+  std::vector<int64_t> oz_off;
+  std::vector<int32_t> oz_wbase_h;  // per node: smallest / largest pivot of its leaf Cholesky or Z LU
   std::vector<std::pair<void*, size_t>> allocs;
   size_t tsize() const { return prec == KF_PREC_FP64 ? 8 : 4; }
 };
+
+// tensor-core V pass of the FP64-accurate operator (oz_op.cu)
+constexpr int kOzTileElems = 128 * 128;  // one BF16 digit tile: 128 skeleton columns x 128 rows
+constexpr int kOzChunkRows = 1024;       // rows of one partial sum
+struct kf_oz_x {                         // the digits of one operator input
+  uint16_t* xsl = nullptr;               // 7 x kpad x ldx BF16 digits
+  unsigned long long* xmax = nullptr;
+  int32_t* xexp = nullptr;               // tau_r = 2^xexp[r]
+  int64_t ldx = 0, k = 0;
+  int kpad = 0, nc = 0;
+  size_t bytes = 0;
+};
+kf_status kf_oz_alloc(kf_factor* f, cudaStream_t s);
+kf_status kf_oz_slice_v(kf_factor* f, int lv, cudaStream_t s);
+kf_status kf_oz_slice_leaf(kf_factor* f, cudaStream_t s);
+kf_status kf_oz_leaf(kf_factor* f, const kf_oz_x& oz, int64_t k, double lambda, const double* x, double* y,
+                     cudaStream_t s);
+kf_status kf_oz_prepare_x(kf_factor* f, const double* x, int64_t k, kf_oz_x* oz, cudaStream_t s);
+void kf_oz_release_x(kf_factor* f, kf_oz_x* oz, cudaStream_t s);
+kf_status kf_oz_colsum_level(kf_factor* f, int l, const kf_oz_x& oz, int64_t k, double* parts, int* nchunk,
+                             cudaStream_t s);
 
 // device status bits
 #define KF_DEV_ILLCOND 1

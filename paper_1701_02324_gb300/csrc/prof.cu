@@ -29,6 +29,17 @@ cudaEvent_t get_event() {
   cudaEventCreate(&e);
   return e;
 }
+
+// Inside a stream capture a plain event record only expresses a dependency;
+// an external record becomes a node of the graph, so launches in the batched
+// graphs are timed too.
+void record(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, s);
+}
 }  // namespace
 
 void kf_prof_begin(int, cudaStream_t s) {
@@ -36,14 +47,14 @@ void kf_prof_begin(int, cudaStream_t s) {
   if (!g_on.load(std::memory_order_relaxed)) return;
   std::lock_guard<std::mutex> lk(g_mu);
   t_open = get_event();
-  cudaEventRecord(t_open, s);
+  record(t_open, s);
 }
 
 void kf_prof_end(int phase, cudaStream_t s) {
   if (!g_on.load(std::memory_order_relaxed) || !t_open) return;
   std::lock_guard<std::mutex> lk(g_mu);
   cudaEvent_t b = get_event();
-  cudaEventRecord(b, s);
+  record(b, s);
   g_recs.push_back({phase, t_open, b, s});
   t_open = nullptr;
 }

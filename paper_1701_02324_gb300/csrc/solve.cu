@@ -2052,7 +2052,21 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
   auto vt_level = [&](int l) { return VT ? VT + kf_vt_level_off(f, l) : nullptr; };
   const bool split = xdf && f->Kdf && !deriv;
   if (split) KF_PHASE(KF_PH_MISC, s, k_split_vec<<<grid_for(N * k, 256), 256, 0, s>>>(x, xdf, N * k));
-  if (f->Kdf && !deriv) {
+  // 16 or more right-hand sides on factors with BF16 digits (tc_operator): the
+  // leaf blocks and the V pass on the tensor cores (oz_op.cu), from the digits
+  // of x formed once here
+  kf_oz_x oz;
+  if ((f->Ksl || (f->VTsl && !transpose && D > f->hyb_L)) && !deriv && k >= 16 && k <= 4096) {
+    kf_status zs = kf_oz_prepare_x(f, x, k, &oz, s);
+    if (zs != KF_OK) return zs;
+  }
+  if (oz.xsl && f->Ksl) {
+    kf_status zs = kf_oz_leaf(f, oz, k, f->lambda, x, y, s);
+    if (zs != KF_OK) {
+      kf_oz_release_x(f, &oz, s);
+      return zs;
+    }
+  } else if (f->Kdf && !deriv) {
     if (k == 1) {
       dim3 gl((unsigned)std::max(1, std::min(64, (t->leaf_max * 32 + 255) / 256)), 1 << D);
       const size_t xsm = sizeof(float2) * t->leaf_max;
@@ -2072,6 +2086,7 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
     KF_PHASE(KF_PH_MV_LEAF, s, k_leaf_mv<TM><<<gl, 128, 0, s>>>(t->d_lo, t->d_hi, leaf0, t->X64, t->X32, t->d, f->c_exp, inv_h3,
                                      deriv ? SRC_DKERNEL : SRC_KERNEL, f->lambda, x, y, (int)k));
   }
+  if (oz.xsl && (D == 0 || transpose || !f->VTsl)) kf_oz_release_x(f, &oz, s);  // only the leaf pass used them
   if (D == 0) { KF_LAUNCH_CHECK(c); return KF_OK; }
   KF_CUDA(c, cudaMemsetAsync(G, 0, sizeof(double) * (size_t)(t->nnodes + 1) * s_max * k, s));
   if (transpose) {
@@ -2119,7 +2134,16 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
   for (int l = f->hyb_L + 1; l <= D; ++l) {
     const int64_t rows = (N >> l) + 1;
     dim3 gc((unsigned)((rows + kRowsPerChunk - 1) / kRowsPerChunk), 1 << l);
-    if (f->VTdf && !deriv) {  // FP64-accurate operator of the mixed path
+    if (oz.xsl && f->VTsl) {
+      int nch = 0;
+      kf_status zs = kf_oz_colsum_level(f, l, oz, k, parts, &nch, s);
+      if (zs != KF_OK) {
+        kf_oz_release_x(f, &oz, s);
+        return zs;
+      }
+      colsum_reduce(dim3((unsigned)nch, 1u << l), s, t->d_lo, t->d_hi, f->rank, 1 << l, 1, kOzChunkRows, s_max,
+                    (int)k, parts, parts2, G, KF_PH_MV_COLSUM);
+    } else if (f->VTdf && !deriv) {  // FP64-accurate operator of the mixed path
       const float2* Vl = f->VTdf + (int64_t)(l - 1) * N * s_max;
       // several right-hand sides: 256 rows a CTA (16 columns a pass for k > 8)
       const dim3 g2((gc.x + 1) / 2, gc.y);
@@ -2145,6 +2169,7 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
       launch_colsum<TM, double>(gc, s, t->d_lo, t->d_hi, f->rank, f->skel, 1 << l, s_max, 1, src, vt_level(l),
                                 t->X64, t->X32, t->d, f->c_exp, inv_h3, x, (int)k, G, parts, parts2, KF_PH_MV_COLSUM);
   }
+  if (oz.xsl) kf_oz_release_x(f, &oz, s);
   // the hybrid solver's frontier nodes couple with every other frontier node
   // (V of Algorithm 8), pushed down from the frontier like a sibling coupling
   if (f->hyb_L > 0) {

@@ -5,7 +5,8 @@ shared memory, tiled row updates, 16-column sums, tiled pushes), which read
 each factor entry once per 8 or 16 columns.  Every column of a block solve
 is compared with the same column solved alone (k = 1 kernels) and, on the
 FP64 path, with the oracle; the transposed sweep and the FP64-accurate
-operator likewise.  Shapes: ragged leaves, block widths that leave a partial
+operator likewise, the latter also with its V pass on the tensor cores
+(tc_operator: exact BF16 digit products).  Shapes: ragged leaves, block widths that leave a partial
 chunk (5, 19), and the levels with and without the explicit Z^-1.
 """
 import numpy as np
@@ -92,3 +93,45 @@ def test_block_operator_equals_column_operator(problem, k):
             yc = F.matvec(Bt[:, c].contiguous()).cpu().numpy()
             assert rel(Yb[:, c], yc) <= 1e-13, (prec, c)
         assert rel(Yb, ref) <= (1e-12 if prec == FP64 else 1e-12), prec
+
+
+@pytest.mark.parametrize("k", [16, 33, 64])
+def test_tensor_core_v_pass_equals_double_float(problem, k):
+    """The FP64-accurate operator with its V pass as exact BF16 digit products
+    on the tensor cores (16 or more columns) against the double-float
+    CUDA-core pass (tc_operator off), single columns and the oracle's matvec;
+    node starts here are not multiples of 8 and nodes span several 1024-row
+    chunks and ragged 128-row windows."""
+    p = problem
+    B = p["rng"].standard_normal((p["N"], k)) * np.exp(p["rng"].uniform(-3, 3, k))  # columns of unequal scale
+    Bt = torch.from_numpy(B).cuda()
+    ref = p["o"].matvec(B)
+    F = kf.Factor(p["tree"], p["h"], p["lam"], p["tau"], p["smax"], precision=MIXED, fp64_operator=True,
+                  tc_operator=True)
+    G = kf.Factor(p["tree"], p["h"], p["lam"], p["tau"], p["smax"], precision=MIXED, fp64_operator=True)
+    Yt = F.matvec(Bt).cpu().numpy()
+    Yd = G.matvec(Bt).cpu().numpy()
+    for c in range(k):
+        assert rel(Yt[:, c], Yd[:, c]) <= 1e-13, c
+    assert rel(Yt, ref) <= 1e-12
+    # refined block solve on those factors: the residuals come from the tensor-core pass
+    H = kf.Factor(p["tree"], p["h"], p["lam"], p["tau"], p["smax"], precision=MIXED, fp64_operator=True,
+                  tc_operator=True, refine_tol=1e-12)
+    assert rel(H.solve(Bt).cpu().numpy(), p["o"].solve(B)) <= 1e-9
+
+
+def test_tensor_core_v_pass_two_skeleton_tiles():
+    """Ranks above 128 (two 128-column skeleton tiles per node) and a column
+    count that leaves a partial group of 32: the tensor-core V pass against
+    the double-float pass."""
+    rng = np.random.default_rng(0x0253)
+    N, d, m, smax = 20000, 5, 512, 160
+    X = torch.from_numpy(rng.random((N, d))).cuda()
+    tree = kf.Tree(X, m)
+    F = kf.Factor(tree, 0.25, 1.0, 1e-9, smax, precision=MIXED, fp64_operator=True, tc_operator=True)
+    G = kf.Factor(tree, 0.25, 1.0, 1e-9, smax, precision=MIXED, fp64_operator=True)
+    assert int(F.ranks().max()) > 128
+    B = torch.from_numpy(rng.standard_normal((N, 40))).cuda()
+    Yt, Yd = F.matvec(B).cpu().numpy(), G.matvec(B).cpu().numpy()
+    for c in range(40):
+        assert rel(Yt[:, c], Yd[:, c]) <= 1e-13, c
