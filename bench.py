@@ -576,15 +576,18 @@ def gpu_main(args, rank, world):
         # sweep is bound by its FP64 arithmetic, which grows with the block
         B16 = torch.from_numpy(inputs.rhs(p.N, 16, 1701003 + 33)).to(dev)
 
-        def block_time(F):
-            F.solve(B16)
+        def block_time(F, B=B16):
+            F.solve(B)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            X16 = F.solve(B16)
+            XB = F.solve(B)
             e1.record()
             torch.cuda.synchronize()
-            return X16, e0.elapsed_time(e1) / 1e3
+            return XB, e0.elapsed_time(e1) / 1e3
+        # a block of 64: the FP64 direct sweep against the Richardson solve on factors whose
+        # FP64-accurate operator runs on the tensor cores (tc_operator)
+        B64 = torch.from_numpy(inputs.rhs(p.N, 64, 1701003 + 65)).to(dev)
         Fr16 = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=kf.KF_PREC_FP64, fp64_operator=True,
                          refine_max_iter=30, refine_tol=1e-12, gmres_restart=30, sync_errors=False, **kn)
         Xr16 = Fr16.solve(B16)
@@ -593,6 +596,7 @@ def gpu_main(args, rank, world):
         F64, f64_s = fact_time(kf.KF_PREC_FP64, fp64_operator=False, refine_max_iter=-1, **opt(kf.KF_PREC_FP64))
         x64, _, s64 = solve_time(F64)
         X64_16, s64_16 = block_time(F64)
+        X64_64, s64_64 = block_time(F64, B64)
         ranks_n = F64.ranks()
         del F64
         Fm, fm_s = fact_time(kf.KF_PREC_MIXED, fp64_operator=True, refine_tol=1e-6, refine_max_iter=400,
@@ -605,6 +609,21 @@ def gpu_main(args, rank, world):
         xs_, is_, ss = solve_time(Fs)
         Xs16, ss16 = block_time(Fs)
         del Fs
+        # the factors keep the BF16 digits of V and of the leaf blocks as well (one factorization:
+        # two of these at once would hold some 260 GB)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        Ft = kf.Factor(tree, p.h, p.lam, p.tau, p.s_max, precision=kf.KF_PREC_MIXED, sync_errors=False,
+                       fp64_operator=True, refine_tol=args.near_rich_tol, refine_max_iter=20, gmres_restart=-1,
+                       tc_operator=True, **kn, **opt(kf.KF_PREC_MIXED))
+        e1.record()
+        torch.cuda.synchronize()
+        ft_s = e0.elapsed_time(e1) / 1e3
+        Xt16, st16 = block_time(Ft)
+        Xt64, st64 = block_time(Ft, B64)
+        del Ft
         Fu, _ = fact_time(kf.KF_PREC_MIXED, fp64_operator=False, refine_max_iter=-1, **opt(kf.KF_PREC_MIXED))
         xu, _, su = solve_time(Fu)
         del Fu, tree
@@ -621,7 +640,16 @@ def gpu_main(args, rank, world):
                                             rel16(X64_16)},
                             "mixed_richardson": {"solve_rhs_per_s": round(16 / ss16, 2), "rel_err_vs_reference":
                                                  rel16(Xs16)},
+                            "mixed_richardson_tc_operator": {"solve_rhs_per_s": round(16 / st16, 2),
+                                                             "rel_err_vs_reference": rel16(Xt16)},
                             "note": "16 seeded right-hand sides solved together"},
+                "block64": {"fp64_direct": {"solve_rhs_per_s": round(64 / s64_64, 2)},
+                            "mixed_richardson_tc_operator": {
+                                "factorize_s": round(ft_s, 4), "solve_rhs_per_s": round(64 / st64, 2),
+                                "rel_err_vs_fp64_direct": float(torch.linalg.norm(Xt64 - X64_64) /
+                                                                torch.linalg.norm(X64_64))},
+                            "note": "64 seeded right-hand sides; the FP64 direct solution is within ~1e-15 of "
+                                    "the reference at this sampling"},
                 "note": "S' half from the nodes' near-field lists (kappa nearest neighbours by randomized "
                         "projection trees), half uniform; factorization times include the neighbour search"}
 
@@ -726,6 +754,7 @@ def gpu_main(args, rank, world):
                 # mixed: solves refined as a batch to eps_r <= 1e-9 (the C4 bar is 1e-5 on the error)
                 facs = kf.factorize_batched(trees_b, hs, lams, taus, probs[0].s_max, precision=prec,
                                             refine_tol=1e-9 if prec == kf.KF_PREC_MIXED else 0.0,
+                                            tc_operator=prec == kf.KF_PREC_MIXED,
                                             **(tuned_b if prec == kf.KF_PREC_MIXED else tuned_b64))
                 e1.record()
                 xs, binf = kf.solve_batched(facs, Bb, info=True)
@@ -759,8 +788,8 @@ def gpu_main(args, rank, world):
                                                "per node x the same"},
                    "note": "factorize_batched (one CUDA-graph launch) and solve_batched: FP64 direct sweeps (one "
                            "graph launch); mixed sweeps refined as a batch to eps_r <= 1e-9 (two graph launches per "
-                           "step, GMRES for problems that stall); the mixed error is per problem against the FP64 "
-                           "path's solution"}
+                           "step, GMRES for problems that stall) against the FP64-accurate operator on the tensor "
+                           "cores (tc_operator); the mixed error is per problem against the FP64 path's solution"}
         del xs, xs64, trees_b, Bb
 
     # ---- differentiation workload (N=2^18, d=54): factorize, solve, gradient ----------
@@ -890,6 +919,13 @@ def gpu_main(args, rank, world):
             "near_field_block16_mixed_rhs_per_s": near["block16"]["mixed_richardson"]["solve_rhs_per_s"] if near else None,
             "near_field_block16_mixed_rel_err": near["block16"]["mixed_richardson"]["rel_err_vs_reference"]
                                                 if near else None,
+            "near_field_block16_mixed_tc_rhs_per_s":
+                near["block16"]["mixed_richardson_tc_operator"]["solve_rhs_per_s"] if near else None,
+            "near_field_block64_fp64_rhs_per_s": near["block64"]["fp64_direct"]["solve_rhs_per_s"] if near else None,
+            "near_field_block64_mixed_tc_rhs_per_s":
+                near["block64"]["mixed_richardson_tc_operator"]["solve_rhs_per_s"] if near else None,
+            "near_field_block64_mixed_tc_rel_err":
+                near["block64"]["mixed_richardson_tc_operator"]["rel_err_vs_fp64_direct"] if near else None,
             "near_field_mixed_unrefined_rel_err": near["mixed_unrefined"]["rel_err_vs_reference"] if near else None,
             "lean_factor_gb": [lean["standard"]["factor_gb"], lean["w_recompute"]["factor_gb"]] if lean else None,
             "lean_mixed_solve_rhs_per_s": lean["w_recompute"]["solve_rhs_per_s"] if lean else None,
