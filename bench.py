@@ -751,7 +751,7 @@ def gpu_main(args, rank, world):
                 e1 = torch.cuda.Event(enable_timing=True)
                 e2 = torch.cuda.Event(enable_timing=True)
                 e0.record()
-                # mixed: solves refined as a batch to eps_r <= 1e-9 (the C4 bar is 1e-5 on the error)
+                # mixed: solves refined as a batch to eps_r <= 1e-9 (the batched workload's bar is 1e-5 on the error)
                 facs = kf.factorize_batched(trees_b, hs, lams, taus, probs[0].s_max, precision=prec,
                                             refine_tol=1e-9 if prec == kf.KF_PREC_MIXED else 0.0,
                                             tc_operator=prec == kf.KF_PREC_MIXED,

@@ -355,7 +355,7 @@ def test_batched_workload_mixed_refined_full_size():
     2e-10 on the worst-conditioned problems): every problem's 64
     solutions within 1e-5 of the FP64 path's batched solution refined to
     eps_r <= 1e-10 (1.3e-9 on the worst problem, where GMRES stagnates even
-    on the FP64 factors) (the C4 bar), and the median, smallest and largest
+    on the FP64 factors) (the batched workload's bar), and the median, smallest and largest
     problems within 1e-5 of the oracle's direct solve where every skeleton
     matches."""
     probs = inputs.batched(256, 64)
