@@ -1569,6 +1569,7 @@ kf_status kf_factorize_device(kf_factor* f, cudaStream_t s) {
   c->dfree(Tm, tb, s);
   if (st == KF_OK) st = kf_split_p_df(f, s);
   if (st == KF_OK) st = kf_split_z_df(f, s);
+  if (st == KF_OK) st = kf_oz_slice_rows(f, s);  // digits of P^ and P (tc_operator)
   return st;
 }
 
@@ -1704,6 +1705,7 @@ kf_status kf_skel_factorize_pipelined(kf_factor* f, cudaStream_t s) {
   if (s3) cudaStreamDestroy(s3);
   if (s4) cudaStreamDestroy(s4);
   if (evl) cudaEventDestroy(evl);
+  if (st == KF_OK) st = kf_oz_slice_rows(f, s);  // digits of P^ and P (tc_operator), after every level
   return st;
 }
 

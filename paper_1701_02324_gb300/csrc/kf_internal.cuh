@@ -142,6 +142,10 @@ struct kf_factor {
   int32_t use_oz = 0;
   uint16_t* VTsl = nullptr;
   uint16_t* Ksl = nullptr;  // the leaf blocks' digits: (leaf, row tile, column window) tiles
+  // the leaves' P as row-scaled 7-digit tiles (row windows x skeleton
+  // windows) for the operator's row update (row exponents PLrexp)
+  uint16_t* PLsl = nullptr;
+  int32_t* PLrexp = nullptr;
   int32_t* oz_wbase = nullptr;
   std::vector<int64_t> oz_off;
   std::vector<int32_t> oz_wbase_h;  // per node: smallest / largest pivot of its leaf Cholesky or Z LU
@@ -152,11 +156,11 @@ struct kf_factor {
 // tensor-core V pass of the FP64-accurate operator (oz_op.cu)
 constexpr int kOzTileElems = 128 * 128;  // one BF16 digit tile: 128 skeleton columns x 128 rows
 constexpr int kOzChunkRows = 1024;       // rows of one partial sum
-struct kf_oz_x {                         // the digits of one operator input
-  uint16_t* xsl = nullptr;               // 7 x kpad x ldx BF16 digits
+struct kf_oz_x {                         // the digits of one B operand
+  uint16_t* xsl = nullptr;               // nd x kpad x ldx BF16 digits
   unsigned long long* xmax = nullptr;
-  int32_t* xexp = nullptr;               // tau_r = 2^xexp[r]
-  int64_t ldx = 0, k = 0;
+  int32_t* xexp = nullptr;               // scales 2^xexp (per column, or per node and column)
+  int64_t ldx = 0, k = 0, nexp = 0;
   int kpad = 0, nc = 0;
   size_t bytes = 0;
 };
@@ -166,6 +170,9 @@ kf_status kf_oz_slice_leaf(kf_factor* f, cudaStream_t s);
 kf_status kf_oz_leaf(kf_factor* f, const kf_oz_x& oz, int64_t k, double lambda, const double* x, double* y,
                      cudaStream_t s);
 kf_status kf_oz_prepare_x(kf_factor* f, const double* x, int64_t k, kf_oz_x* oz, cudaStream_t s);
+kf_status kf_oz_prepare_t(kf_factor* f, int lv, const double* Vt, int64_t k, kf_oz_x* oz, cudaStream_t s);
+kf_status kf_oz_slice_rows(kf_factor* f, cudaStream_t s);
+kf_status kf_oz_rowupd(kf_factor* f, const kf_oz_x& td, int64_t k, double* y, double sign, cudaStream_t s);
 void kf_oz_release_x(kf_factor* f, kf_oz_x* oz, cudaStream_t s);
 kf_status kf_oz_colsum_level(kf_factor* f, int l, const kf_oz_x& oz, int64_t k, double* parts, int* nchunk,
                              cudaStream_t s);

@@ -1,6 +1,7 @@
-// oz_op.cu -- the V pass of the mixed path's FP64-accurate operator for
-// blocks of right-hand sides on the tensor cores, exact in integer
-// arithmetic.  The pass forms, for every node of a level, the column sums of
+// oz_op.cu -- the mixed path's FP64-accurate operator for blocks of
+// right-hand sides on the tensor cores, exact in integer arithmetic: the
+// leaf blocks K_aa x_a, the leaves' row update P g of the skeleton weights,
+// and the V pass, which forms for every node of a level the column sums of
 // its sibling coupling (Eq. e:blocksmw, the K_{sib~ node} x_node of the
 // hierarchical matvec)
 //
@@ -53,7 +54,6 @@ namespace {
 using namespace kf_tc;
 
 constexpr int kOzSlices = 7;                      // digits per operand
-constexpr int kOzGroups = 8;                      // digit pairs p + q = 0 .. 7
 constexpr int kOzWin = 128;                       // rows per window (exact accumulation)
 constexpr int kOzWinPerChunk = kOzChunkRows / kOzWin;
 constexpr int kOzQ = 128;                         // skeleton columns per CTA (MMA M)
@@ -182,8 +182,13 @@ __global__ void __launch_bounds__(256) k_oz_slice_leaf(const int32_t* __restrict
 }
 
 // ---- operator call: x digits ----------------------------------------------------
-// column maxima of |x| as FP64 bit patterns (non-negative doubles order like
-// their bit patterns, so integer maxima are exact and order-independent)
+// Order-preserving key of |x| (non-negative doubles order like their bit
+// patterns, so integer maxima are exact and order-independent)
+__device__ __forceinline__ unsigned long long oz_key(double x) {
+  return (unsigned long long)__double_as_longlong(fabs(x));
+}
+
+// column maxima of |x| (N x k point-major) as keys
 __global__ void __launch_bounds__(256) k_oz_colmax(const double* __restrict__ x, int64_t N, int k,
                                                    unsigned long long* __restrict__ mx) {
   extern __shared__ unsigned long long smx[];
@@ -191,24 +196,38 @@ __global__ void __launch_bounds__(256) k_oz_colmax(const double* __restrict__ x,
   __syncthreads();
   const int64_t nk = N * k;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x)
-    atomicMax(&smx[e % k], (unsigned long long)__double_as_longlong(fabs(x[e])));
+    atomicMax(&smx[e % k], oz_key(x[e]));
   __syncthreads();
   for (int r = threadIdx.x; r < k; r += blockDim.x)
     if (smx[r]) atomicMax(&mx[r], smx[r]);
 }
 
-// e_r with 2^e_r > max |x_r| (0 for a zero column; a non-finite column gets
-// kOzBadExp, which makes its sums NaN)
+// e with 2^e > the key's value (0 for zero; a non-finite value gets
+// kOzBadExp, which makes the sums NaN)
 constexpr int kOzBadExp = -100000;
+__device__ __forceinline__ int oz_exp_of(unsigned long long key) {
+  const int ef = (int)((key >> 52) & 0x7FFu);
+  return ef == 0x7FF ? kOzBadExp : (key == 0ull ? 0 : ef - 1023 + 1);
+}
 __global__ void k_oz_exponents(const unsigned long long* __restrict__ mx, int k, int32_t* __restrict__ xexp) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < k; r += gridDim.x * blockDim.x) {
-    const int ef = (int)((mx[r] >> 52) & 0x7FFu);
-    xexp[r] = ef == 0x7FF ? kOzBadExp : (mx[r] == 0ull ? 0 : ef - 1023 + 1);
-  }
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < k; r += gridDim.x * blockDim.x) xexp[r] = oz_exp_of(mx[r]);
 }
 
-// xsl[(p kpad + r) ldx + i]: digit p of round(x_ir 2^(49 - e_r)), balanced
-// (each of d_6 .. d_1 in [-64, 63], d_0 the rest, |d_0| <= 128)
+// the ND balanced digits of v (|v| <= 2^(7 ND)): each of d_(ND-1) .. d_1 in
+// [-64, 63], d_0 the rest (|d_0| <= 128), as BF16 bit patterns
+template <int ND>
+__device__ __forceinline__ void oz_digits(int64_t v, uint16_t (&dg)[ND]) {
+#pragma unroll
+  for (int p = ND - 1; p >= 1; --p) {
+    const int64_t d = ((v + 64) & 127) - 64;
+    dg[p] = (uint16_t)oz_bf16((int)d);
+    v = (v - d) >> 7;
+  }
+  dg[0] = (uint16_t)oz_bf16((int)v);
+}
+
+// xsl[(p kpad + r) ldx + i]: digit p of round(x_ir 2^(7 ND - e_r))
+template <int ND>
 __global__ void __launch_bounds__(256) k_oz_slice_x(const double* __restrict__ x, int64_t N, int k, int kpad,
                                                     int64_t ldx, const int32_t* __restrict__ xexp,
                                                     uint16_t* __restrict__ xsl) {
@@ -217,56 +236,146 @@ __global__ void __launch_bounds__(256) k_oz_slice_x(const double* __restrict__ x
     const int r = (int)(e / N);
     const int64_t i = e % N;  // consecutive threads: consecutive rows of one column (coalesced digit stores)
     const int ex = xexp[r];
-    int64_t v = ex == kOzBadExp ? 0 : oz_fixed_d(x[i * k + r], 49 - ex);
-    int dg[kOzSlices];
+    uint16_t dg[ND];
+    oz_digits<ND>(ex == kOzBadExp ? 0 : oz_fixed_d(x[i * k + r], 7 * ND - ex), dg);
 #pragma unroll
-    for (int p = kOzSlices - 1; p >= 1; --p) {
-      const int64_t d = ((v + 64) & 127) - 64;
-      dg[p] = (int)d;
-      v = (v - d) >> 7;
-    }
-    dg[0] = (int)v;
-#pragma unroll
-    for (int p = 0; p < kOzSlices; ++p) xsl[((int64_t)p * kpad + r) * ldx + i] = (uint16_t)oz_bf16(dg[p]);
+    for (int p = 0; p < ND; ++p) xsl[((int64_t)p * kpad + r) * ldx + i] = dg[p];
   }
 }
 
-// ---- the V pass -----------------------------------------------------------------
+// The skeleton vectors t_a of the nodes of a level (Vt[(node s_max + q) k + r],
+// q < rank[node]) as digits for the row updates: per node and column a scale
+// 2^e (xexp[nl k + r]) and xsl[(p kpad + r) ldx + nl s_pad + q].  One CTA a
+// node; smem: k keys.
+template <int ND>
+__global__ void __launch_bounds__(256) k_oz_slice_t(const int32_t* __restrict__ rank, int node0, int s_max,
+                                                    int s_pad, const double* __restrict__ Vt, int k, int kpad,
+                                                    int64_t ldx, int32_t* __restrict__ xexp,
+                                                    uint16_t* __restrict__ xsl) {
+  extern __shared__ unsigned long long tmx[];
+  const int nl = blockIdx.x, node = node0 + nl, sa = rank[node];
+  for (int r = threadIdx.x; r < k; r += blockDim.x) tmx[r] = 0ull;
+  __syncthreads();
+  const double* T = Vt + (int64_t)node * s_max * k;
+  for (int e = threadIdx.x; e < sa * k; e += blockDim.x) atomicMax(&tmx[e % k], oz_key(T[e]));
+  __syncthreads();
+  for (int r = threadIdx.x; r < k; r += blockDim.x) xexp[(int64_t)nl * k + r] = oz_exp_of(tmx[r]);
+  __syncthreads();
+  for (int e = threadIdx.x; e < sa * k; e += blockDim.x) {
+    const int q = e / k, r = e % k;
+    const int ex = xexp[(int64_t)nl * k + r];
+    uint16_t dg[ND];
+    oz_digits<ND>(ex == kOzBadExp ? 0 : oz_fixed_d(T[e], 7 * ND - ex), dg);
+#pragma unroll
+    for (int p = 0; p < ND; ++p) xsl[((int64_t)p * kpad + r) * ldx + (int64_t)nl * s_pad + q] = dg[p];
+  }
+}
+
+// ---- factorization: row-scaled digit tiles of the leaves' P (operator) ----------
+// rexp[i] = e with 2^e > max_{q < rank[node]} |M[i][q]| for the rows of the
+// nodes of a level; one warp a row
+__global__ void __launch_bounds__(256) k_oz_row_exp(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                    const int32_t* __restrict__ rank, int node0, int s_max,
+                                                    const double* __restrict__ M, int32_t* __restrict__ rexp) {
+  const int node = node0 + blockIdx.y, b = lo[node], n = hi[node] - b, sa = rank[node];
+  const int lane = threadIdx.x & 31;
+  for (int i = blockIdx.x * 8 + (threadIdx.x >> 5); i < n; i += gridDim.x * 8) {
+    unsigned long long m = 0ull;
+    for (int q = lane; q < sa; q += 32) m = max(m, oz_key(M[(int64_t)(b + i) * s_max + q]));
+    for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (lane == 0) rexp[b + i] = oz_exp_of(m);
+  }
+}
+
+// tiles (window of the level's rows, skeleton window, digit): element (m =
+// row in the window, k = skeleton in the window), K-major as the V tiles;
+// grid = (windows of the largest node, nodes, skeleton windows)
+template <int ND>
+__global__ void __launch_bounds__(256) k_oz_slice_rows(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                       const int32_t* __restrict__ rank, int node0, int s_max,
+                                                       int qw, const double* __restrict__ M,
+                                                       const int32_t* __restrict__ rexp,
+                                                       const int32_t* __restrict__ wbase, uint16_t* __restrict__ tiles) {
+  const int nl = blockIdx.y, node = node0 + nl, w = blockIdx.x, t = blockIdx.z;
+  const int b = lo[node], n = hi[node] - b, sa = rank[node];
+  if (w * kOzWin >= n) return;
+  uint16_t* base = tiles + ((int64_t)(wbase[nl] + w) * qw + t) * ND * kOzTileElems;
+  for (int item = threadIdx.x; item < kOzWin * (kOzQ / 8); item += blockDim.x) {
+    const int kg = item % (kOzQ / 8), m = item / (kOzQ / 8);
+    const int i = w * kOzWin + m;
+    const int ex = i < n ? rexp[b + i] : 0;
+    uint32_t pk[ND][4];
+#pragma unroll
+    for (int p = 0; p < ND; ++p) pk[p][0] = pk[p][1] = pk[p][2] = pk[p][3] = 0u;
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const int q = t * kOzQ + kg * 8 + jj;
+      int64_t v = 0;
+      if (i < n && q < sa && ex != kOzBadExp) v = oz_fixed_d(M[(int64_t)(b + i) * s_max + q], 7 * ND - ex);
+      uint16_t dg[ND];
+      oz_digits<ND>(v, dg);
+#pragma unroll
+      for (int p = 0; p < ND; ++p) pk[p][jj >> 1] |= (uint32_t)dg[p] << (16 * (jj & 1));
+    }
+    const int off = ((m >> 3) * 16 + kg) * 64 + (m & 7) * 8;
+#pragma unroll
+    for (int p = 0; p < ND; ++p)
+      *(uint4*)(base + (int64_t)p * kOzTileElems + off) = make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
+  }
+}
+
+// ---- the tensor-core passes ----------------------------------------------------
+// 7 digits per operand: the digit pairs p + q <= 7 in 8 groups (a zero tile
+// after the x digit d_6 clears group 7, which has no pair with p = 0)
+constexpr int kOzGroups = 8;
+
 template <int NC>
 struct OzCfg {
-  static constexpr int kStages = NC == 16 ? 4 : 3;              // V digit tiles in flight
-  static constexpr int kBBytes = (kOzSlices + 1) * NC * kOzWin * 2;  // x digits of one window + a zero tile
+  static_assert(NC == 16 || NC == 32, "column group");
+  static constexpr int kGroups = kOzGroups;
+  static constexpr int kStages = NC == 16 ? 4 : 3;             // A digit tiles in flight
+  static constexpr int kBBytes = kGroups * NC * kOzWin * 2;    // x digits of one window (+ zero tiles)
   static constexpr int kSmem = kStages * kOzTileBytes + 2 * kBBytes;
-  static constexpr int kAccCols = kOzGroups * NC;               // one buffer of group sums
+  static constexpr int kAccCols = kGroups * NC;                // one buffer of group sums
   static constexpr uint32_t kTmemCols = 2 * kAccCols <= 256 ? 256u : 512u;
 };
 
-// V pass (LEAF = false): grid = (1024-row chunks of the largest node, nodes,
-// skeleton tiles x column groups); CTA (ch, node, t) sums rows 1024 ch ..
-// of the node against skeleton columns 128 t .. of its sibling into parts.
-// Leaf blocks (LEAF = true, leaves of at most 1024 points): grid = (1,
-// leaves, row tiles x column groups); CTA (0, leaf, t) forms rows 128 t ..
-// of y = lambda x + K_aa x over all of the leaf's columns, in place of the
-// skeleton columns: the same products with A = the leaf block's digits.
-template <int NC, bool LEAF>
+enum { kOzColsum = 0, kOzLeaf = 1, kOzRowupd = 2 };
+
+// MODE kOzColsum (V passes): grid = (1024-row chunks of the largest node,
+// nodes, skeleton tiles x column groups); CTA (ch, node, t) sums rows
+// 1024 ch .. of the node against skeleton columns 128 t .. of its sibling:
+// partial sums into parts.
+// MODE kOzLeaf (leaves of at most 1024 points): grid = (1, leaves, row
+// tiles x column groups); CTA (0, leaf, t) forms rows 128 t .. of
+// y = lambda x + K_aa x over all of the leaf's columns.
+// MODE kOzRowupd (the row update y_i += sign P_i g_a of the leaves, P's rows
+// scaled by 2^rexp[i]): grid = (1, leaves, row windows x column groups); CTA
+// (0, leaf, t) updates rows 128 t .. of the leaf from its skeleton weights
+// g_a (digits per leaf and column, scales 2^xexp[leaf k + r]); its skeleton
+// windows of 128 are read out like the V pass's row windows.
+template <int NC, int MODE, typename TY>
 __global__ void __launch_bounds__(kOzThreads, 1)
-    k_colsum_oz(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi, const int32_t* __restrict__ rank,
-                int node0, int s_max, int qt, const uint16_t* __restrict__ Asl, const int32_t* __restrict__ wbase,
-                const uint16_t* __restrict__ xsl, int64_t ldx, int kpad, const int32_t* __restrict__ xexp, int k,
-                int nchunk, double* __restrict__ parts, double lambda, const double* __restrict__ x,
-                double* __restrict__ y, int32_t* __restrict__ status) {
+    k_oz(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi, const int32_t* __restrict__ rank,
+         int node0, int s_max, int qt, const uint16_t* __restrict__ Asl, const int32_t* __restrict__ wbase,
+         const uint16_t* __restrict__ xsl, int64_t ldx, int kpad, const int32_t* __restrict__ xexp, int k,
+         int nchunk, double* __restrict__ parts, double lambda, const double* __restrict__ x, TY* __restrict__ y,
+         const int32_t* __restrict__ rexp, double sign, int32_t* __restrict__ status) {
   using C = OzCfg<NC>;
-  constexpr int ST = C::kStages;
+  constexpr int ST = C::kStages, G = C::kGroups, ND = kOzSlices;
   extern __shared__ __align__(1024) unsigned char oz_smem[];
   __shared__ __align__(8) uint64_t a_full[ST], a_empty[ST], b_full[2], b_empty[2], acc_full[2], acc_empty[2], done;
   __shared__ uint32_t tmem_base;
   const int nl = blockIdx.y, node = node0 + nl, sib = node ^ 1;
   const int b = lo[node], n = hi[node] - b;
-  const int cnt = LEAF ? n : rank[sib];  // rows of the product (M)
+  const int cnt = MODE == kOzColsum ? rank[sib] : n;  // rows of the product (M)
   const int t = blockIdx.z % qt, c0 = (blockIdx.z / qt) * NC;
   const int ch = blockIdx.x, w0 = ch * kOzWinPerChunk;
-  const int nw = min(kOzWinPerChunk, (n + kOzWin - 1) / kOzWin - w0);
+  const int s_a = MODE == kOzRowupd ? rank[node] : 0;
+  const int nw = MODE == kOzRowupd ? (s_a + kOzWin - 1) / kOzWin
+                                   : min(kOzWinPerChunk, (n + kOzWin - 1) / kOzWin - w0);
   if (nw <= 0 || cnt <= t * kOzQ || c0 >= k) return;  // uniform over the CTA
+  const int s_pad = (s_max + kOzWin - 1) / kOzWin * kOzWin;
   uint16_t* As = (uint16_t*)oz_smem;
   uint16_t* Bs = (uint16_t*)(oz_smem + ST * kOzTileBytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -289,14 +398,24 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = tmem_base;
-  const int nunits = nw * kOzSlices;  // (window, V digit) pairs, in order
+  const int nunits = nw * ND;  // (window, A digit) pairs, in order
   if (warp == 0) {
-    // bulk copies of the V digit tiles
+    // bulk copies of the A digit tiles.  V: (window of the level, skeleton
+    // tile); leaf blocks: (leaf, row tile, window); row updates: (row window
+    // of the level, skeleton window); 7 digit tiles each
     if (lane == 0) {
-      // V: tiles by (window of the level, skeleton tile); leaf: by (leaf, row tile, window)
-      const uint16_t* tiles = LEAF ? Asl + ((int64_t)nl * qt + t) * qt * kOzSlices * kOzTileElems
-                                   : Asl + ((int64_t)(wbase[nl] + w0) * qt + t) * kOzSlices * kOzTileElems;
-      const int64_t wstride = (int64_t)(LEAF ? 1 : qt) * kOzSlices * kOzTileElems;  // elements between windows
+      const uint16_t* tiles;
+      int64_t wstride;
+      if (MODE == kOzColsum) {
+        tiles = Asl + ((int64_t)(wbase[nl] + w0) * qt + t) * kOzSlices * kOzTileElems;
+        wstride = (int64_t)qt * kOzSlices * kOzTileElems;
+      } else if (MODE == kOzLeaf) {
+        tiles = Asl + ((int64_t)nl * qt + t) * qt * kOzSlices * kOzTileElems;
+        wstride = (int64_t)kOzSlices * kOzTileElems;
+      } else {
+        tiles = Asl + (int64_t)(wbase[nl] + t) * (s_pad / kOzWin) * ND * kOzTileElems;
+        wstride = (int64_t)ND * kOzTileElems;
+      }
       for (int u = 0; u < nunits; ++u) {
         const int st = u % ST;
         if (u >= ST && !mbar_wait(&a_empty[st], (uint32_t)((u / ST) - 1) & 1u)) {
@@ -304,13 +423,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           break;
         }
         mbar_arrive_expect_tx(&a_full[st], kOzTileBytes);
-        bulk_g2s(As + st * kOzTileElems, tiles + (u / kOzSlices) * wstride + (int64_t)(u % kOzSlices) * kOzTileElems,
-                 kOzTileBytes, &a_full[st]);
+        bulk_g2s(As + st * kOzTileElems, tiles + (u / ND) * wstride + (int64_t)(u % ND) * kOzTileElems, kOzTileBytes,
+                 &a_full[st]);
       }
     }
     __syncwarp();
   } else if (warp == 1) {
-    // MMAs: window w, V digit p against x digits q <= 7 - p into group p + q
+    // MMAs: per window and A digit p one chain with B = x digits d_0 .. into
+    // the accumulator columns from group p on (pair (p, q) -> group p + q)
     if (lane == 0) {
       bool ok = true;
       int issued = 0;
@@ -321,14 +441,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         if (!ok) break;
         fence_after_sync();
         const uint32_t bs0 = smem_u32(Bs + buf * (C::kBBytes / 2));
-        for (int p = 0; p < kOzSlices; ++p) {
-          const int u = w * kOzSlices + p, st = u % ST;
+        for (int p = 0; p < ND; ++p) {
+          const int u = w * ND + p, st = u % ST;
           if (!(ok = mbar_wait(&a_full[st], (uint32_t)(u / ST) & 1u))) break;
           fence_after_sync();
           const uint32_t as = smem_u32(As + st * kOzTileElems);
-          // p = 0: d_0 .. d_6 and the zero tile (groups 0-7, overwritten);
-          // p >= 1: d_0 .. d_min(6, 7-p) (groups p .. 7, accumulated)
-          const int nq = p == 0 ? kOzSlices + 1 : min(kOzSlices, kOzGroups - p);
+          // p = 0: every group (overwritten; the zero tile for group 7);
+          // p >= 1: groups p .. 7 (accumulated)
+          const int nq = p == 0 ? G : min(ND, G - p);
           const uint32_t idesc = idesc_bf16(kOzQ, nq * NC);
           const uint32_t dt = tmem + (uint32_t)(buf * C::kAccCols + p * NC);
 #pragma unroll
@@ -355,17 +475,26 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const int sid = tid - 64;
     for (int e = sid; e < NC * kOzWin / 8; e += 64)  // the zero tile after d_6, in both buffers
       for (int bb = 0; bb < 2; ++bb)
-        *(uint4*)(Bs + bb * (C::kBBytes / 2) + kOzSlices * NC * kOzWin + e * 8) = make_uint4(0u, 0u, 0u, 0u);
+        *(uint4*)(Bs + bb * (C::kBBytes / 2) + ND * NC * kOzWin + e * 8) = make_uint4(0u, 0u, 0u, 0u);
     for (int w = 0; w < nw; ++w) {
       const int buf = w & 1;
       if (w >= 2 && !mbar_wait(&b_empty[buf], (uint32_t)((w >> 1) - 1) & 1u)) {
         atomicOr(status, KF_DEV_TIMEOUT);
         break;
       }
-      const int ib = (w0 + w) * kOzWin, nr = min(kOzWin, n - ib);
-      const int64_t i0 = (int64_t)b + ib;
+      // rows of x (V, leaf: the node's rows of the window) or of t_a (row updates: skeletons)
+      int64_t i0;
+      int nr;
+      if (MODE == kOzRowupd) {
+        i0 = (int64_t)nl * s_pad + w * kOzWin;
+        nr = min(kOzWin, s_a - w * kOzWin);
+      } else {
+        const int ib = (w0 + w) * kOzWin;
+        i0 = (int64_t)b + ib;
+        nr = min(kOzWin, n - ib);
+      }
       uint16_t* B = Bs + buf * (C::kBBytes / 2);
-      for (int e = sid; e < kOzSlices * NC * (kOzWin / 8); e += 64) {
+      for (int e = sid; e < ND * NC * (kOzWin / 8); e += 64) {
         const int ig = e % (kOzWin / 8), r = (e / (kOzWin / 8)) % NC, q = e / (NC * (kOzWin / 8));
         const uint16_t* src = xsl + ((int64_t)q * kpad + c0 + r) * ldx + i0 + ig * 8;
         uint16_t* dst = B + q * NC * kOzWin + ((r >> 3) * 16 + ig) * 64 + (r & 7) * 8;
@@ -383,7 +512,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       mbar_arrive(&b_full[buf]);
     }
   } else {
-    // read-out: thread = accumulator row (skeleton column) t*128 + 32 (warp % 4) + lane
+    // read-out: thread = accumulator row t*128 + 32 (warp % 4) + lane
     const int quad = warp & 3;
     int64_t hi64[NC], lo64[NC];
 #pragma unroll
@@ -398,7 +527,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       }
       fence_after_sync();
 #pragma unroll 1
-      for (int g = 0; g < kOzGroups; ++g) {
+      for (int g = 0; g < G; ++g) {
         const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * C::kAccCols + g * NC);
         float v[NC];
         if constexpr (NC == 16) {
@@ -417,18 +546,24 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       fence_before_sync();
       mbar_arrive(&acc_empty[buf]);
     }
+    // value = 2^e (2^-35 hi + 2^-63 lo): e = the x column's exponent (plus the row's)
     const int q = t * kOzQ + quad * 32 + lane;
     if (ok && q < cnt) {
-      double* out = LEAF ? y + ((int64_t)b + q) * k : parts + (((int64_t)nl * nchunk + ch) * s_max + q) * k;
+      const int64_t row = (int64_t)b + q;
+      const int rx = MODE == kOzRowupd ? rexp[row] : 0;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int col = c0 + c;
         if (col >= k) break;
-        const int ex = xexp[col];
+        const int ex = MODE == kOzRowupd ? xexp[(int64_t)nl * k + col] : xexp[col];
         const double v = ex == kOzBadExp ? __longlong_as_double(0x7FF8000000000000ll)
-                                         : ldexp((double)hi64[c], ex - 35) + ldexp((double)lo64[c], ex - 63);
-        if (LEAF) out[col] = lambda * x[((int64_t)b + q) * k + col] + v;
-        else out[col] = v;
+                                         : ldexp((double)hi64[c], ex + rx - 35) + ldexp((double)lo64[c], ex + rx - 63);
+        if (MODE == kOzColsum)
+          parts[(((int64_t)nl * nchunk + ch) * s_max + q) * k + col] = v;
+        else if (MODE == kOzLeaf)
+          y[row * k + col] = (TY)(lambda * x[row * k + col] + v);
+        else
+          y[row * k + col] = (TY)((double)y[row * k + col] + sign * v);
       }
     }
   }
@@ -485,6 +620,44 @@ kf_status kf_oz_alloc(kf_factor* f, cudaStream_t s) {
       cudaGetLastError();
     }
   }
+  // row-scaled digits of the leaves' P (7 digits)
+  const int qw = (f->s_max + kOzWin - 1) / kOzWin;
+  auto grab = [&](size_t bytes) -> void* {
+    void* m = f->ctx->dalloc(bytes, s);
+    if (m) f->allocs.push_back({m, bytes});
+    else cudaGetLastError();
+    return m;
+  };
+  int64_t wD = 0;
+  for (int a = 1 << D; a < (2 << D); ++a) wD += (t->hi[a] - t->lo[a] + kOzWin - 1) / kOzWin;
+  f->PLsl = (uint16_t*)grab(sizeof(uint16_t) * (size_t)wD * qw * 7 * kOzTileElems);
+  f->PLrexp = f->PLsl ? (int32_t*)grab(sizeof(int32_t) * (size_t)t->N) : nullptr;
+  if (!f->PLrexp) f->PLsl = nullptr;
+  return KF_OK;
+}
+
+// row exponents and digit tiles of one matrix M (point-major N x s_max) over
+// the rows of the nodes of level lv
+void oz_rows_level(kf_factor* f, int lv, const double* M, int32_t* rexp, uint16_t* tiles, cudaStream_t s) {
+  kf_tree* t = f->t;
+  const int qw = (f->s_max + kOzWin - 1) / kOzWin;
+  int maxn = 0;
+  for (int a = 1 << lv; a < (2 << lv); ++a) maxn = std::max(maxn, t->hi[a] - t->lo[a]);
+  if (maxn == 0) return;
+  dim3 ge((unsigned)std::min(64, (maxn + 7) / 8), 1u << lv);
+  KF_PHASE(KF_PH_MISC, s, k_oz_row_exp<<<ge, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, 1 << lv, f->s_max, M, rexp));
+  dim3 g((unsigned)((maxn + kOzWin - 1) / kOzWin), 1u << lv, (unsigned)qw);
+  KF_PHASE(KF_PH_MISC, s, k_oz_slice_rows<kOzSlices><<<g, 256, 0, s>>>(t->d_lo, t->d_hi, f->rank, 1 << lv, f->s_max, qw,
+                                                                    M, rexp, f->oz_wbase + (1 << lv), tiles));
+}
+
+// the row-scaled digits of the leaves' P, once the factorization is complete
+kf_status kf_oz_slice_rows(kf_factor* f, cudaStream_t s) {
+  kf_tree* t = f->t;
+  const int D = t->D;
+  if (D == 0 || !f->oz_wbase || !f->PLsl) return KF_OK;
+  oz_rows_level(f, D, f->Pleaf, f->PLrexp, f->PLsl, s);
+  KF_LAUNCH_CHECK(f->ctx);
   return KF_OK;
 }
 
@@ -516,7 +689,7 @@ kf_status kf_oz_slice_v(kf_factor* f, int lv, cudaStream_t s) {
   return KF_OK;
 }
 
-// x of one operator call as digits (k >= 2 right-hand sides, N x k point-major)
+// x of one operator call (N x k point-major) as 7 digits a column
 kf_status kf_oz_prepare_x(kf_factor* f, const double* x, int64_t k, kf_oz_x* oz, cudaStream_t s) {
   kf_ctx* c = f->ctx;
   const int64_t N = f->t->N;
@@ -525,6 +698,7 @@ kf_status kf_oz_prepare_x(kf_factor* f, const double* x, int64_t k, kf_oz_x* oz,
   oz->kpad = (int)((k + oz->nc - 1) / oz->nc) * oz->nc;
   oz->ldx = (N + 7) / 8 * 8;
   oz->bytes = sizeof(uint16_t) * (size_t)kOzSlices * oz->kpad * oz->ldx;
+  oz->nexp = k;
   oz->xsl = (uint16_t*)c->dalloc(oz->bytes, s);
   oz->xmax = (unsigned long long*)c->dalloc(sizeof(unsigned long long) * (size_t)k, s);
   oz->xexp = (int32_t*)c->dalloc(sizeof(int32_t) * (size_t)k, s);
@@ -537,8 +711,33 @@ kf_status kf_oz_prepare_x(kf_factor* f, const double* x, int64_t k, kf_oz_x* oz,
   const int smx = (int)(sizeof(unsigned long long) * (size_t)k);
   KF_PHASE(KF_PH_MV_COLSUM, s, k_oz_colmax<<<grid_for(N * k, 256, 1024), 256, smx, s>>>(x, N, (int)k, oz->xmax));
   KF_PHASE(KF_PH_MV_COLSUM, s, k_oz_exponents<<<grid_for(k, 256), 256, 0, s>>>(oz->xmax, (int)k, oz->xexp));
-  KF_PHASE(KF_PH_MV_COLSUM, s, k_oz_slice_x<<<grid_for(N * k, 256), 256, 0, s>>>(x, N, (int)k, oz->kpad, oz->ldx,
-                                                                                oz->xexp, oz->xsl));
+  KF_PHASE(KF_PH_MV_COLSUM, s, k_oz_slice_x<kOzSlices><<<grid_for(N * k, 256), 256, 0, s>>>(
+                                   x, N, (int)k, oz->kpad, oz->ldx, oz->xexp, oz->xsl));
+  KF_LAUNCH_CHECK(c);
+  return KF_OK;
+}
+
+// the skeleton weights of the nodes of level lv (Vt, by node) as 7 digits for
+// a row update
+kf_status kf_oz_prepare_t(kf_factor* f, int lv, const double* Vt, int64_t k, kf_oz_x* oz, cudaStream_t s) {
+  kf_ctx* c = f->ctx;
+  const int nodes = 1 << lv, s_pad = (f->s_max + kOzWin - 1) / kOzWin * kOzWin;
+  oz->k = k;
+  oz->nc = k > 16 ? 32 : 16;
+  oz->kpad = (int)((k + oz->nc - 1) / oz->nc) * oz->nc;
+  oz->ldx = (int64_t)nodes * s_pad;
+  oz->bytes = sizeof(uint16_t) * (size_t)kOzSlices * oz->kpad * oz->ldx;
+  oz->nexp = (int64_t)nodes * k;
+  oz->xsl = (uint16_t*)c->dalloc(oz->bytes, s);
+  oz->xexp = (int32_t*)c->dalloc(sizeof(int32_t) * (size_t)oz->nexp, s);
+  if (!oz->xsl || !oz->xexp) {
+    kf_oz_release_x(f, oz, s);
+    return kf_set_err(c, KF_ENOMEM, "matvec: allocation of the skeleton-weight digits failed");
+  }
+  KF_CUDA(c, cudaMemsetAsync(oz->xsl, 0, oz->bytes, s));
+  const int smx = (int)(sizeof(unsigned long long) * (size_t)k);
+  KF_PHASE(KF_PH_MV_ROWUPD, s, k_oz_slice_t<kOzSlices><<<nodes, 256, smx, s>>>(
+                                   f->rank, nodes, f->s_max, s_pad, Vt, (int)k, oz->kpad, oz->ldx, oz->xexp, oz->xsl));
   KF_LAUNCH_CHECK(c);
   return KF_OK;
 }
@@ -547,12 +746,28 @@ void kf_oz_release_x(kf_factor* f, kf_oz_x* oz, cudaStream_t s) {
   kf_ctx* c = f->ctx;
   if (oz->xsl) c->dfree(oz->xsl, oz->bytes, s);
   if (oz->xmax) c->dfree(oz->xmax, sizeof(unsigned long long) * (size_t)oz->k, s);
-  if (oz->xexp) c->dfree(oz->xexp, sizeof(int32_t) * (size_t)oz->k, s);
+  if (oz->xexp) c->dfree(oz->xexp, sizeof(int32_t) * (size_t)oz->nexp, s);
   *oz = kf_oz_x{};
+}
+
+template <int NC, int MODE, typename TY>
+kf_status oz_launch(kf_factor* f, dim3 g, int phase, cudaStream_t s, int node0, int qt, const uint16_t* Asl,
+                    const int32_t* wb, const uint16_t* xsl, int64_t ldx, int kpad, const int32_t* xexp, int k,
+                    int nchunk, double* parts, double lambda, const double* x, TY* y, const int32_t* rexp,
+                    double sign) {
+  kf_tree* t = f->t;
+  using C = OzCfg<NC>;
+  KF_CUDA(f->ctx, cudaFuncSetAttribute(k_oz<NC, MODE, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
+  KF_PHASE(phase, s, k_oz<NC, MODE, TY><<<g, kOzThreads, C::kSmem, s>>>(
+                         t->d_lo, t->d_hi, f->rank, node0, f->s_max, qt, Asl, wb, xsl, ldx, kpad, xexp, k, nchunk,
+                         parts, lambda, x, y, rexp, sign, f->status));
+  KF_LAUNCH_CHECK(f->ctx);
+  return KF_OK;
 }
 
 // The V pass of level l: FP64 partial sums of 1024-row chunks into parts
 // (the layout of k_colsum's, nchunk chunks a node); the caller reduces them.
+// oz.nd = 7: the FP64-accurate operator; 4: the FP32 sweep.
 kf_status kf_oz_colsum_level(kf_factor* f, int l, const kf_oz_x& oz, int64_t k, double* parts, int* nchunk,
                              cudaStream_t s) {
   kf_tree* t = f->t;
@@ -564,21 +779,11 @@ kf_status kf_oz_colsum_level(kf_factor* f, int l, const kf_oz_x& oz, int64_t k, 
   dim3 g((unsigned)nch, 1u << l, (unsigned)(qt * (oz.kpad / oz.nc)));
   const uint16_t* Asl = f->VTsl + f->oz_off[l];
   const int32_t* wb = f->oz_wbase + (1 << l);
-  if (oz.nc == 16) {
-    KF_CUDA(f->ctx, cudaFuncSetAttribute(k_colsum_oz<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         OzCfg<16>::kSmem));
-    KF_PHASE(KF_PH_MV_COLSUM, s, k_colsum_oz<16, false><<<g, kOzThreads, OzCfg<16>::kSmem, s>>>(
-                                     t->d_lo, t->d_hi, f->rank, 1 << l, f->s_max, qt, Asl, wb, oz.xsl, oz.ldx,
-                                     oz.kpad, oz.xexp, (int)k, nch, parts, 0.0, nullptr, nullptr, f->status));
-  } else {
-    KF_CUDA(f->ctx, cudaFuncSetAttribute(k_colsum_oz<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         OzCfg<32>::kSmem));
-    KF_PHASE(KF_PH_MV_COLSUM, s, k_colsum_oz<32, false><<<g, kOzThreads, OzCfg<32>::kSmem, s>>>(
-                                     t->d_lo, t->d_hi, f->rank, 1 << l, f->s_max, qt, Asl, wb, oz.xsl, oz.ldx,
-                                     oz.kpad, oz.xexp, (int)k, nch, parts, 0.0, nullptr, nullptr, f->status));
-  }
-  KF_LAUNCH_CHECK(f->ctx);
-  return KF_OK;
+#define OZ_ARGS g, KF_PH_MV_COLSUM, s, 1 << l, qt, Asl, wb, oz.xsl, oz.ldx, oz.kpad, oz.xexp, (int)k, nch, parts, 0.0, \
+                nullptr, (double*)nullptr, nullptr, 0.0
+  if (oz.nc == 16) return oz_launch<16, kOzColsum, double>(f, OZ_ARGS);
+  return oz_launch<32, kOzColsum, double>(f, OZ_ARGS);
+#undef OZ_ARGS
 }
 
 // Leaf blocks: y = lambda x + K_aa x for every leaf (x, y: N x k, tree order)
@@ -587,19 +792,26 @@ kf_status kf_oz_leaf(kf_factor* f, const kf_oz_x& oz, int64_t k, double lambda, 
   kf_tree* t = f->t;
   const int tpl = (t->leaf_max + kOzQ - 1) / kOzQ;
   dim3 g(1u, 1u << t->D, (unsigned)(tpl * (oz.kpad / oz.nc)));
-  if (oz.nc == 16) {
-    KF_CUDA(f->ctx, cudaFuncSetAttribute(k_colsum_oz<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         OzCfg<16>::kSmem));
-    KF_PHASE(KF_PH_MV_LEAF, s, k_colsum_oz<16, true><<<g, kOzThreads, OzCfg<16>::kSmem, s>>>(
-                                   t->d_lo, t->d_hi, f->rank, 1 << t->D, f->s_max, tpl, f->Ksl, nullptr, oz.xsl,
-                                   oz.ldx, oz.kpad, oz.xexp, (int)k, 1, nullptr, lambda, x, y, f->status));
-  } else {
-    KF_CUDA(f->ctx, cudaFuncSetAttribute(k_colsum_oz<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         OzCfg<32>::kSmem));
-    KF_PHASE(KF_PH_MV_LEAF, s, k_colsum_oz<32, true><<<g, kOzThreads, OzCfg<32>::kSmem, s>>>(
-                                   t->d_lo, t->d_hi, f->rank, 1 << t->D, f->s_max, tpl, f->Ksl, nullptr, oz.xsl,
-                                   oz.ldx, oz.kpad, oz.xexp, (int)k, 1, nullptr, lambda, x, y, f->status));
-  }
-  KF_LAUNCH_CHECK(f->ctx);
-  return KF_OK;
+#define OZ_ARGS g, KF_PH_MV_LEAF, s, 1 << t->D, tpl, f->Ksl, nullptr, oz.xsl, oz.ldx, oz.kpad, oz.xexp, (int)k, 1, \
+                nullptr, lambda, x, y, nullptr, 0.0
+  if (oz.nc == 16) return oz_launch<16, kOzLeaf, double>(f, OZ_ARGS);
+  return oz_launch<32, kOzLeaf, double>(f, OZ_ARGS);
+#undef OZ_ARGS
+}
+
+// The operator's row update of the leaves from their skeleton weights (digits
+// in td): y += sign P g (7 digits of the leaves' P)
+kf_status kf_oz_rowupd(kf_factor* f, const kf_oz_x& td, int64_t k, double* y, double sign, cudaStream_t s) {
+  kf_tree* t = f->t;
+  const int lv = t->D;
+  int maxn = 0;
+  for (int a = 1 << lv; a < (2 << lv); ++a) maxn = std::max(maxn, t->hi[a] - t->lo[a]);
+  const int nwin = std::max(1, (maxn + kOzWin - 1) / kOzWin);
+  dim3 g(1u, 1u << lv, (unsigned)(nwin * (td.kpad / td.nc)));
+  const int32_t* wb = f->oz_wbase + (1 << lv);
+#define OZ_ARGS g, KF_PH_MV_ROWUPD, s, 1 << lv, nwin, f->PLsl, wb, td.xsl, td.ldx, td.kpad, td.xexp, (int)k, 1, \
+                nullptr, 0.0, nullptr, y, f->PLrexp, sign
+  if (td.nc == 16) return oz_launch<16, kOzRowupd, double>(f, OZ_ARGS);
+  return oz_launch<32, kOzRowupd, double>(f, OZ_ARGS);
+#undef OZ_ARGS
 }

@@ -2198,7 +2198,13 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
                                                                                           G, (int)k));
   }
   const int64_t rows = (N >> D) + 1;
-  if (rows_df)
+  if (f->PLsl && f->VTsl && !deriv && k >= 16 && k <= 4096) {  // y += P g of the leaves on the tensor cores
+    kf_oz_x td;
+    kf_status zs = kf_oz_prepare_t(f, D, G, k, &td, s);
+    if (zs == KF_OK) zs = kf_oz_rowupd(f, td, k, y, 1.0, s);
+    kf_oz_release_x(f, &td, s);
+    if (zs != KF_OK) return zs;
+  } else if (rows_df)
     KF_PHASE(KF_PH_MV_ROWUPD, s, k_rows_df<8, 0><<<dim3((unsigned)((rows + kRowUpdRows - 1) / kRowUpdRows),
                                                            1u << D), 256, rows_df_smem<8>(), s>>>(
                                      t->d_lo, t->d_hi, f->rank, leaf0, s_max, f->Pleafdf, G, y, (int)k));

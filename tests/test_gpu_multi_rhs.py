@@ -135,3 +135,4 @@ def test_tensor_core_v_pass_two_skeleton_tiles():
     Yt, Yd = F.matvec(B).cpu().numpy(), G.matvec(B).cpu().numpy()
     for c in range(40):
         assert rel(Yt[:, c], Yd[:, c]) <= 1e-13, c
+
