@@ -462,7 +462,9 @@ __global__ void __launch_bounds__(256) k_colsum(const int32_t* __restrict__ lo, 
         }
       }
       double* out = parts + (((int64_t)nl * gridDim.x + blockIdx.x) * s_max + q) * k + kb;
-      for (int r = 0; r < kk; ++r) out[r] = (double)acc[r];
+#pragma unroll
+      for (int r = 0; r < kMaxK; ++r)  // static indices keep acc in registers
+        if (r < kk) out[r] = (double)acc[r];
     }
   }
 }
@@ -478,6 +480,9 @@ void launch_colsum(dim3 g, cudaStream_t s, const int32_t* lo, const int32_t* hi,
     colsum_reduce(g, s, lo, hi, rank, node0, sib, kRowsPerChunk, s_max, k, parts, parts2, U, phase);
   } else {
     // g.x counts 128-row chunks; several right-hand sides take 512 rows a CTA
+    // (64 columns a pass over 128-row chunks measured slower: 24.1 against
+    // 17.9 ms per sweep of 64 columns at N = 2^20, the partial sums of four
+    // times as many chunks written and reduced)
     const dim3 g4((g.x + 3) / 4, g.y);
     bool done = false;
     if constexpr (sizeof(TV) == 4) {
@@ -632,8 +637,9 @@ __global__ void __launch_bounds__(256) k_rowupd_multi(const int32_t* __restrict_
   static_assert(KB % VW == 0, "KB: a multiple of the 16-byte vector");
   using V16 = typename Vec16<TV>::type;
   extern __shared__ __align__(16) unsigned char rm_smem[];
-  TV* vs = (TV*)rm_smem;  // KF_MAX_SMAX x KB
-  TM(*tile)[32][33] = (TM(*)[32][33])(rm_smem + sizeof(TV) * KF_MAX_SMAX * KB);  // 8 warps x 32 x 33
+  const int vrows = (s_max + 31) & ~31;
+  TV* vs = (TV*)rm_smem;  // vrows x KB
+  TM(*tile)[32][33] = (TM(*)[32][33])(rm_smem + sizeof(TV) * vrows * KB);  // 8 warps x 32 x 33
   const int nl = blockIdx.y, node = node0 + nl, sib = node ^ 1;
   const int b = lo[node], n = hi[node] - b;
   const int cnt = sibling_mode ? rank[sib] : rank[node];
@@ -691,7 +697,9 @@ __global__ void __launch_bounds__(256) k_rowupd_multi(const int32_t* __restrict_
 }
 
 template <typename TM, typename TV, int KB>
-constexpr size_t rowupd_multi_smem() { return sizeof(TV) * KF_MAX_SMAX * KB + sizeof(TM) * 8 * 32 * 33; }
+size_t rowupd_multi_smem(int s_max) {
+  return sizeof(TV) * (size_t)((s_max + 31) & ~31) * KB + sizeof(TM) * 8 * 32 * 33;
+}
 
 template <typename TM, typename TV>
 void launch_rowupd(int64_t rows, int nnodes, cudaStream_t s, const int32_t* lo, const int32_t* hi, const int32_t* rank,
@@ -714,24 +722,26 @@ void launch_rowupd(int64_t rows, int nnodes, cudaStream_t s, const int32_t* lo, 
     }
   }
   if (k >= 2 && src == SRC_STORED) {
-    // several right-hand sides: the tiled form, 16 FP32 (8 FP64) columns a pass
+    // several right-hand sides: the tiled form, 16 FP32 (8 FP64) columns a
+    // pass, or 64 FP32 columns for k > 32 (M read once per 64 columns)
     constexpr int KB = sizeof(TV) == 4 ? 16 : 8;
-    const bool wide = k > 8;
-    const size_t smem = wide ? rowupd_multi_smem<TM, TV, KB>() : rowupd_multi_smem<TM, TV, 8>();
-    static bool attr_multi = false;  // per instantiation; setting it twice is harmless
-    if (!attr_multi) {
-      cudaFuncSetAttribute(k_rowupd_multi<TM, TV, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)rowupd_multi_smem<TM, TV, KB>());
-      cudaFuncSetAttribute(k_rowupd_multi<TM, TV, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)rowupd_multi_smem<TM, TV, 8>());
-      attr_multi = true;
-    }
-    if (wide)
+    constexpr int KW = sizeof(TV) == 4 ? 64 : 8;
+    const int mode = (sizeof(TV) == 4 && k > 32) ? 2 : (k > 8 ? 1 : 0);
+    const size_t smem = mode == 2 ? rowupd_multi_smem<TM, TV, KW>(s_max)
+                                  : (mode == 1 ? rowupd_multi_smem<TM, TV, KB>(s_max) : rowupd_multi_smem<TM, TV, 8>(s_max));
+    if (mode == 2) {
+      cudaFuncSetAttribute(k_rowupd_multi<TM, TV, KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      KF_PHASE(phase, s, k_rowupd_multi<TM, TV, KW><<<g, 256, smem, s>>>(lo, hi, rank, node0, s_max, sib, M, V, sign,
+                                                                        W, k));
+    } else if (mode == 1) {
+      cudaFuncSetAttribute(k_rowupd_multi<TM, TV, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       KF_PHASE(phase, s, k_rowupd_multi<TM, TV, KB><<<g, 256, smem, s>>>(lo, hi, rank, node0, s_max, sib, M, V, sign,
                                                                         W, k));
-    else
+    } else {
+      cudaFuncSetAttribute(k_rowupd_multi<TM, TV, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       KF_PHASE(phase, s, k_rowupd_multi<TM, TV, 8><<<g, 256, smem, s>>>(lo, hi, rank, node0, s_max, sib, M, V, sign,
                                                                        W, k));
+    }
     return;
   }
   if (k == 1)
