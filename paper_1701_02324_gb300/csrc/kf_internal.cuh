@@ -146,6 +146,10 @@ struct kf_factor {
   // windows) for the operator's row update (row exponents PLrexp)
   uint16_t* PLsl = nullptr;
   int32_t* PLrexp = nullptr;
+  // P_c of the internal nodes the same way (node, row window, skeleton window),
+  // row exponents PCrexp[node 2 s_max + i], for the operator's pushes
+  uint16_t* PCsl = nullptr;
+  int32_t* PCrexp = nullptr;
   int32_t* oz_wbase = nullptr;
   std::vector<int64_t> oz_off;
   std::vector<int32_t> oz_wbase_h;  // per node: smallest / largest pivot of its leaf Cholesky or Z LU
@@ -173,6 +177,7 @@ kf_status kf_oz_prepare_x(kf_factor* f, const double* x, int64_t k, kf_oz_x* oz,
 kf_status kf_oz_prepare_t(kf_factor* f, int lv, const double* Vt, int64_t k, kf_oz_x* oz, cudaStream_t s);
 kf_status kf_oz_slice_rows(kf_factor* f, cudaStream_t s);
 kf_status kf_oz_rowupd(kf_factor* f, const kf_oz_x& td, int64_t k, double* y, double sign, cudaStream_t s);
+kf_status kf_oz_push(kf_factor* f, int lv, const kf_oz_x& td, int64_t k, double* G, cudaStream_t s);
 void kf_oz_release_x(kf_factor* f, kf_oz_x* oz, cudaStream_t s);
 kf_status kf_oz_colsum_level(kf_factor* f, int l, const kf_oz_x& oz, int64_t k, double* parts, int* nchunk,
                              cudaStream_t s);

@@ -324,6 +324,58 @@ __global__ void __launch_bounds__(256) k_oz_slice_rows(const int32_t* __restrict
   }
 }
 
+// P_c of every internal node a (FP64, rows i < s_l + s_r of (2 s_max) x s_max
+// blocks, columns q < s_a) as row-scaled digit tiles: rexp[a 2 s_max + i] and
+// tiles (node, row window, skeleton window, digit); grid = (row windows,
+// internal nodes 1 .. 2^D - 1, skeleton windows)
+template <int ND>
+__global__ void __launch_bounds__(256) k_oz_slice_pc(const int32_t* __restrict__ rank, int s_max, int rw, int qw,
+                                                     const double* __restrict__ Pc, int32_t* __restrict__ rexp,
+                                                     uint16_t* __restrict__ tiles) {
+  const int node = 1 + blockIdx.y, w = blockIdx.x, t = blockIdx.z;
+  const int z = rank[2 * node] + rank[2 * node + 1], sa = rank[node];
+  if (w * kOzWin >= z || t * kOzQ >= sa) return;
+  const double* M = Pc + (int64_t)node * 2 * s_max * s_max;
+  // every CTA of a row window forms its rows' exponents (cheap; no order between CTAs needed)
+  __shared__ int ex_s[kOzWin];
+  const int lane = threadIdx.x & 31;
+  for (int m = threadIdx.x >> 5; m < kOzWin; m += blockDim.x >> 5) {
+    const int i = w * kOzWin + m;
+    unsigned long long key = 0ull;
+    if (i < z)
+      for (int q = lane; q < sa; q += 32) key = max(key, oz_key(M[(int64_t)i * s_max + q]));
+    for (int off = 16; off > 0; off >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, off));
+    if (lane == 0) {
+      ex_s[m] = oz_exp_of(key);
+      if (t == 0 && i < z) rexp[(int64_t)node * 2 * s_max + i] = ex_s[m];
+    }
+  }
+  __syncthreads();
+  uint16_t* base = tiles + (((int64_t)node * rw + w) * qw + t) * ND * kOzTileElems;
+  for (int item = threadIdx.x; item < kOzWin * (kOzQ / 8); item += blockDim.x) {
+    const int kg = item % (kOzQ / 8), m = item / (kOzQ / 8);
+    const int i = w * kOzWin + m;
+    const int ex = ex_s[m];
+    uint32_t pk[ND][4];
+#pragma unroll
+    for (int p = 0; p < ND; ++p) pk[p][0] = pk[p][1] = pk[p][2] = pk[p][3] = 0u;
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const int q = t * kOzQ + kg * 8 + jj;
+      int64_t v = 0;
+      if (i < z && q < sa && ex != kOzBadExp) v = oz_fixed_d(M[(int64_t)i * s_max + q], 7 * ND - ex);
+      uint16_t dg[ND];
+      oz_digits<ND>(v, dg);
+#pragma unroll
+      for (int p = 0; p < ND; ++p) pk[p][jj >> 1] |= (uint32_t)dg[p] << (16 * (jj & 1));
+    }
+    const int off = ((m >> 3) * 16 + kg) * 64 + (m & 7) * 8;
+#pragma unroll
+    for (int p = 0; p < ND; ++p)
+      *(uint4*)(base + (int64_t)p * kOzTileElems + off) = make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
+  }
+}
+
 // ---- the tensor-core passes ----------------------------------------------------
 // 7 digits per operand: the digit pairs p + q <= 7 in 8 groups (a zero tile
 // after the x digit d_6 clears group 7, which has no pair with p = 0)
@@ -340,7 +392,7 @@ struct OzCfg {
   static constexpr uint32_t kTmemCols = 2 * kAccCols <= 256 ? 256u : 512u;
 };
 
-enum { kOzColsum = 0, kOzLeaf = 1, kOzRowupd = 2 };
+enum { kOzColsum = 0, kOzLeaf = 1, kOzRowupd = 2, kOzPush = 3 };
 
 // MODE kOzColsum (V passes): grid = (1024-row chunks of the largest node,
 // nodes, skeleton tiles x column groups); CTA (ch, node, t) sums rows
@@ -354,6 +406,11 @@ enum { kOzColsum = 0, kOzLeaf = 1, kOzRowupd = 2 };
 // (0, leaf, t) updates rows 128 t .. of the leaf from its skeleton weights
 // g_a (digits per leaf and column, scales 2^xexp[leaf k + r]); its skeleton
 // windows of 128 are read out like the V pass's row windows.
+// MODE kOzPush (the operator's push through P_c: g_children += P_c g_a for
+// the nodes a of a level, P_c's rows scaled by 2^rexp[a 2 s_max + i]): grid =
+// (1, nodes, row windows of P_c x column groups); CTA (0, a, t) forms rows
+// 128 t .. of P_c g_a, row i landing in slot i of the left child (i < s_l)
+// or slot i - s_l of the right one.
 template <int NC, int MODE, typename TY>
 __global__ void __launch_bounds__(kOzThreads, 1)
     k_oz(const int32_t* __restrict__ lo, const int32_t* __restrict__ hi, const int32_t* __restrict__ rank,
@@ -368,12 +425,13 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   __shared__ uint32_t tmem_base;
   const int nl = blockIdx.y, node = node0 + nl, sib = node ^ 1;
   const int b = lo[node], n = hi[node] - b;
-  const int cnt = MODE == kOzColsum ? rank[sib] : n;  // rows of the product (M)
+  // rows of the product (M): skeletons of the sibling, points, or P_c's rows
+  const int cnt = MODE == kOzColsum ? rank[sib] : (MODE == kOzPush ? rank[2 * node] + rank[2 * node + 1] : n);
   const int t = blockIdx.z % qt, c0 = (blockIdx.z / qt) * NC;
   const int ch = blockIdx.x, w0 = ch * kOzWinPerChunk;
-  const int s_a = MODE == kOzRowupd ? rank[node] : 0;
-  const int nw = MODE == kOzRowupd ? (s_a + kOzWin - 1) / kOzWin
-                                   : min(kOzWinPerChunk, (n + kOzWin - 1) / kOzWin - w0);
+  constexpr bool kSkel = MODE == kOzRowupd || MODE == kOzPush;  // contraction over the node's skeletons
+  const int s_a = kSkel ? rank[node] : 0;
+  const int nw = kSkel ? (s_a + kOzWin - 1) / kOzWin : min(kOzWinPerChunk, (n + kOzWin - 1) / kOzWin - w0);
   if (nw <= 0 || cnt <= t * kOzQ || c0 >= k) return;  // uniform over the CTA
   const int s_pad = (s_max + kOzWin - 1) / kOzWin * kOzWin;
   uint16_t* As = (uint16_t*)oz_smem;
@@ -412,8 +470,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       } else if (MODE == kOzLeaf) {
         tiles = Asl + ((int64_t)nl * qt + t) * qt * kOzSlices * kOzTileElems;
         wstride = (int64_t)kOzSlices * kOzTileElems;
-      } else {
+      } else if (MODE == kOzRowupd) {
         tiles = Asl + (int64_t)(wbase[nl] + t) * (s_pad / kOzWin) * ND * kOzTileElems;
+        wstride = (int64_t)ND * kOzTileElems;
+      } else {  // P_c of node a: (node, row window, skeleton window) tiles, qt row windows a node
+        tiles = Asl + ((int64_t)node * qt + t) * (s_pad / kOzWin) * ND * kOzTileElems;
         wstride = (int64_t)ND * kOzTileElems;
       }
       for (int u = 0; u < nunits; ++u) {
@@ -485,7 +546,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       // rows of x (V, leaf: the node's rows of the window) or of t_a (row updates: skeletons)
       int64_t i0;
       int nr;
-      if (MODE == kOzRowupd) {
+      if (kSkel) {
         i0 = (int64_t)nl * s_pad + w * kOzWin;
         nr = min(kOzWin, s_a - w * kOzWin);
       } else {
@@ -549,13 +610,17 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     // value = 2^e (2^-35 hi + 2^-63 lo): e = the x column's exponent (plus the row's)
     const int q = t * kOzQ + quad * 32 + lane;
     if (ok && q < cnt) {
-      const int64_t row = (int64_t)b + q;
-      const int rx = MODE == kOzRowupd ? rexp[row] : 0;
+      int64_t row = (int64_t)b + q;
+      if (MODE == kOzPush) {  // P_c's row q: a slot of the left or the right child
+        const int sl = rank[2 * node];
+        row = q < sl ? (int64_t)(2 * node) * s_max + q : (int64_t)(2 * node + 1) * s_max + (q - sl);
+      }
+      const int rx = MODE == kOzRowupd ? rexp[(int64_t)b + q] : (MODE == kOzPush ? rexp[(int64_t)node * 2 * s_max + q] : 0);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int col = c0 + c;
         if (col >= k) break;
-        const int ex = MODE == kOzRowupd ? xexp[(int64_t)nl * k + col] : xexp[col];
+        const int ex = kSkel ? xexp[(int64_t)nl * k + col] : xexp[col];
         const double v = ex == kOzBadExp ? __longlong_as_double(0x7FF8000000000000ll)
                                          : ldexp((double)hi64[c], ex + rx - 35) + ldexp((double)lo64[c], ex + rx - 63);
         if (MODE == kOzColsum)
@@ -633,6 +698,13 @@ kf_status kf_oz_alloc(kf_factor* f, cudaStream_t s) {
   f->PLsl = (uint16_t*)grab(sizeof(uint16_t) * (size_t)wD * qw * 7 * kOzTileElems);
   f->PLrexp = f->PLsl ? (int32_t*)grab(sizeof(int32_t) * (size_t)t->N) : nullptr;
   if (!f->PLrexp) f->PLsl = nullptr;
+  // P_c of the internal nodes (7 digits, rows scaled), for the operator's pushes
+  if (D >= 2) {
+    const int rw = (2 * f->s_max + kOzWin - 1) / kOzWin;
+    f->PCsl = (uint16_t*)grab(sizeof(uint16_t) * ((size_t)1 << D) * rw * qw * 7 * kOzTileElems);
+    f->PCrexp = f->PCsl ? (int32_t*)grab(sizeof(int32_t) * ((size_t)1 << D) * 2 * f->s_max) : nullptr;
+    if (!f->PCrexp) f->PCsl = nullptr;
+  }
   return KF_OK;
 }
 
@@ -655,8 +727,14 @@ void oz_rows_level(kf_factor* f, int lv, const double* M, int32_t* rexp, uint16_
 kf_status kf_oz_slice_rows(kf_factor* f, cudaStream_t s) {
   kf_tree* t = f->t;
   const int D = t->D;
-  if (D == 0 || !f->oz_wbase || !f->PLsl) return KF_OK;
-  oz_rows_level(f, D, f->Pleaf, f->PLrexp, f->PLsl, s);
+  if (D == 0 || !f->oz_wbase) return KF_OK;
+  if (f->PLsl) oz_rows_level(f, D, f->Pleaf, f->PLrexp, f->PLsl, s);
+  if (f->PCsl) {  // and P_c of the internal nodes that push (levels 1 .. D-1; node 1 is sliced too)
+    const int rw = (2 * f->s_max + kOzWin - 1) / kOzWin, qw = (f->s_max + kOzWin - 1) / kOzWin;
+    dim3 g((unsigned)rw, (unsigned)((1 << D) - 1), (unsigned)qw);
+    KF_PHASE(KF_PH_MISC, s, k_oz_slice_pc<kOzSlices><<<g, 256, 0, s>>>(f->rank, f->s_max, rw, qw, f->Pc, f->PCrexp,
+                                                                        f->PCsl));
+  }
   KF_LAUNCH_CHECK(f->ctx);
   return KF_OK;
 }
@@ -813,5 +891,17 @@ kf_status kf_oz_rowupd(kf_factor* f, const kf_oz_x& td, int64_t k, double* y, do
                 nullptr, 0.0, nullptr, y, f->PLrexp, sign
   if (td.nc == 16) return oz_launch<16, kOzRowupd, double>(f, OZ_ARGS);
   return oz_launch<32, kOzRowupd, double>(f, OZ_ARGS);
+#undef OZ_ARGS
+}
+
+// The operator's push of level lv: g_children += P_c g_a for the nodes a of
+// level lv (skeleton weights of the nodes by node in G; digits of g_a in td)
+kf_status kf_oz_push(kf_factor* f, int lv, const kf_oz_x& td, int64_t k, double* G, cudaStream_t s) {
+  const int rw = (2 * f->s_max + kOzWin - 1) / kOzWin;
+  dim3 g(1u, 1u << lv, (unsigned)(rw * (td.kpad / td.nc)));
+#define OZ_ARGS g, KF_PH_MV_PUSH, s, 1 << lv, rw, f->PCsl, nullptr, td.xsl, td.ldx, td.kpad, td.xexp, (int)k, 1, \
+                nullptr, 0.0, nullptr, G, f->PCrexp, 1.0
+  if (td.nc == 16) return oz_launch<16, kOzPush, double>(f, OZ_ARGS);
+  return oz_launch<32, kOzPush, double>(f, OZ_ARGS);
 #undef OZ_ARGS
 }

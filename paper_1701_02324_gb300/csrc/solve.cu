@@ -2195,8 +2195,15 @@ kf_status matvec_t(kf_factor* f, const double* x, double* y, int64_t k, int deri
     KF_CUDA(c, cudaFuncSetAttribute(k_rows_df<8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)rows_df_smem<8>()));
   }
+  const bool oz_push = f->PCsl && f->VTsl && !deriv && k >= 16 && k <= 4096;
   for (int l = std::max(1, f->hyb_L); l < D; ++l) {
-    if (rows_df)
+    if (oz_push) {  // g_children += P_c g_a on the tensor cores (digits of g_a formed per level)
+      kf_oz_x td;
+      kf_status zs = kf_oz_prepare_t(f, l, G, k, &td, s);
+      if (zs == KF_OK) zs = kf_oz_push(f, l, td, k, G, s);
+      kf_oz_release_x(f, &td, s);
+      if (zs != KF_OK) return zs;
+    } else if (rows_df)
       KF_PHASE(KF_PH_MV_PUSH, s, k_rows_df<8, 1><<<dim3((unsigned)((2 * s_max + kRowUpdRows - 1) / kRowUpdRows),
                                                           1u << l), 256, rows_df_smem<8>(), s>>>(
                                      t->d_lo, t->d_hi, f->rank, 1 << l, s_max, f->Pcdf, G, G, (int)k));
