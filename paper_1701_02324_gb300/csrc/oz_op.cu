@@ -1,7 +1,8 @@
 // oz_op.cu -- the mixed path's FP64-accurate operator for blocks of
 // right-hand sides on the tensor cores, exact in integer arithmetic: the
-// leaf blocks K_aa x_a, the leaves' row update P g of the skeleton weights,
-// and the V pass, which forms for every node of a level the column sums of
+// leaf blocks K_aa x_a, the pushes of the skeleton weights through P_c, the
+// leaves' row update P g, and the V pass, which forms for every node of a
+// level the column sums of
 // its sibling coupling (Eq. e:blocksmw, the K_{sib~ node} x_node of the
 // hierarchical matvec)
 //
