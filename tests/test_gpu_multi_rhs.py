@@ -136,3 +136,16 @@ def test_tensor_core_v_pass_two_skeleton_tiles():
     for c in range(40):
         assert rel(Yt[:, c], Yd[:, c]) <= 1e-13, c
 
+
+
+def test_tensor_core_operator_is_bitwise_deterministic(problem):
+    """The tensor-core operator passes sum exact integers per window and
+    reduce the chunks in a fixed order: two products give the same bits."""
+    p = problem
+    B = torch.from_numpy(p["rng"].standard_normal((p["N"], 33))).cuda()
+    F = kf.Factor(p["tree"], p["h"], p["lam"], p["tau"], p["smax"], precision=MIXED, fp64_operator=True,
+                  tc_operator=True)
+    Y1, Y2 = F.matvec(B), F.matvec(B)
+    assert torch.equal(Y1, Y2)
+    X1, X2 = F.solve(B), F.solve(B)  # refined against that operator
+    assert torch.equal(X1, X2)
