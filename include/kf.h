@@ -142,12 +142,15 @@ typedef struct {
                              kf_factor_Phat then returns the leaves' P^ only.  With
                              v_storage = KF_V_RECOMPUTE the factorization also keeps only three
                              levels of V blocks, used in turn. */
-  int32_t tc_operator;    /* mixed path with fp64_operator: 1 = also keep the V blocks as exact BF16
-                             integer digits (7 per entry, 14 bytes, Ozaki splitting), so that the
-                             FP64-accurate operator's V pass (Eq. e:blocksmw) over 16 or more
-                             right-hand sides runs as tcgen05 products with exact FP32 accumulation
-                             (about 2^-49 max|x_r| per product, against the double-float kernels'
-                             2^-46 |V x|); 0 = double-float CUDA-core passes only (default) */
+  int32_t tc_operator;    /* mixed path with fp64_operator: 1 = also keep the V blocks, the leaf blocks,
+                             the leaves' P and every P_c as exact BF16 integer digits (7 per entry,
+                             14 bytes; Ozaki splitting; P and P_c with rows scaled by powers of two),
+                             so that the FP64-accurate operator over 16 to 4096 right-hand sides
+                             (its leaf blocks, V pass of Eq. e:blocksmw, pushes through P_c and the
+                             leaves' P update) runs as tcgen05 products with exact FP32 accumulation
+                             (about 2^-49 of the column's scale per product, against the
+                             double-float kernels' 2^-46 of each product); refined solves of such
+                             blocks use it.  0 = double-float CUDA-core passes only (default) */
 } kf_opts;
 
 /* Filled by kf_solve when non-NULL (synchronizes the stream). */
