@@ -41,8 +41,7 @@ FP64_PEAK_TFLOPS = 1.25          # recipe's nominal FP64 rate (152 SMs, 2.07 GHz
 # (every leaf streams the same bytes); None while the kernel differs from the
 # captured one.
 QR_TRAFFIC_PER_LAUNCH = 1.41e12
-QR_TRAFFIC_SRC = ("ncu DRAM read+write bytes of the leaf-level k_pivoted_qr launch on the same recipe at "
-                  "N=2^17 (128 leaves), scaled x8 to the 1024 leaves of N=2^20")
+QR_TRAFFIC_SRC = "ncu DRAM read+write of this launch at N=2^17 (128 leaves) x8"
 ORACLE_SAMPLE_N = 8192           # points per oracle sample step
 
 
@@ -729,7 +728,7 @@ def gpu_main(args, rank, world):
             del F, tree
         e2e = {"value": round(statistics.mean(lib_t), 4), "unit": "s",
                "h2d_bytes_per_step": int(X_host.nbytes + b_host.nbytes), "d2h_bytes_per_step": int(xh.nbytes),
-               "note": "wall time of tree + factorize + solve with host X, b and x (copies inside)"}
+               "note": "tree + factorize + solve, host X, b, x"}
 
     # ---- batched workload: 256 uneven problems, 64 RHS each, one graph launch each ----
     batched = None
@@ -851,12 +850,12 @@ def gpu_main(args, rank, world):
         per_launch = per_level[D] * args.steps / phase_launches["qr_leaf"]
         achieved = per_launch / (avg_ms * 1e-3) / 1e12
         achieved_bound = bound_level[D] * args.steps / phase_launches["qr_leaf"] / (avg_ms * 1e-3) / 1e12
-        roof = {"kernel": "k_pivoted_qr, leaf level (FP64 ID, one CTA per leaf)", "bound": "alu",
+        roof = {"kernel": "k_pivoted_qr, leaf level", "bound": "alu",
                 "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
                 "traffic": QR_TRAFFIC_PER_LAUNCH, "traffic_src": QR_TRAFFIC_SRC,
-                "peak_src": "recipe nominal FP64 rate (1.25 TFLOP/s; 1.20 measured by an FMA loop)",
-                "work_model": "executed Householder flops from the realized ranks (norms downdated, not recomputed)",
+                "peak_src": "nominal FP64 (an FMA loop measured 1.20)",
+                "work_model": "executed Householder flops, realized ranks",
                 "work_per_launch": per_launch, "avg_launch_ms": round(avg_ms, 3),
                 "frac_of_bound_model": round(achieved_bound / FP64_PEAK_TFLOPS, 4),
                 "bound_model": "4 |S'| c s per node"}
@@ -878,10 +877,9 @@ def gpu_main(args, rank, world):
         sc = oracle_scale(ORACLE_SAMPLE_N)
         cpu = {"value": round(tf_o * sc, 3), "unit": "s", "cores": int(os.environ.get("OMP_NUM_THREADS", cpu_cores())),
                "kind": "oracle",
-               "sample": f"oracle tree+skeletonize+factorize of N={ORACLE_SAMPLE_N} points of the same recipe, "
-                         f"{tf_o:.2f} s, scaled by N*(levels+1) x{sc:.1f} to N=2^20 (an extrapolation; the model is "
-                         f"within 10% at N=2^17; a whole run at N=2^20 on 16 Arm host cores measured 1309 s, 1.9x "
-                         f"below the model); solve {ts_o * sc:.3f} s/RHS scaled",
+               "sample": f"oracle tree+skeletons+factorization of N={ORACLE_SAMPLE_N}, {tf_o:.2f} s, x{sc:.0f} "
+                         f"by N(levels+1) to 2^20 (extrapolated; a whole 2^20 run took 1309 s); "
+                         f"solve {ts_o * sc:.2f} s/RHS",
                "solve_rhs_per_s": round(1.0 / (ts_o * sc), 4)}
 
     if rank == 0:
@@ -891,11 +889,11 @@ def gpu_main(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "scale_N1048576_d28", "N": p.N, "d": p.d, "h": p.h, "lambda": p.lam, "m": p.m,
                        "s_max": p.s_max, "tau": p.tau, "n_samp": 2 * p.s_max, "nrhs": 1,
-                       "precision": "mixed (FP32 factors, tcgen05 products of 3xTF32 or three tf32 pieces; FP64 ID, Z, T, operator, GMRES)",
-                       "parallelism": f"replicas x{world}", "l2": "inputs and factors larger than L2 (no flush)"},
+                       "precision": "mixed: FP32 factors, tcgen05 3xTF32 products; FP64 ID, Z, T, operator, GMRES",
+                       "parallelism": f"replicas x{world}", "l2": "working set > L2, no flush"},
             # the metric's comparison, as top-level scalars
             "solve_rhs_per_s": round(1.0 / solve_s, 2),
-            "solve_note": f"mixed: FP32 sweep + GMRES({args.gmres_m}) vs the FP64 operator to eps_r <= {args.mixed_tol:g}",
+            "solve_note": f"FP32 sweep + GMRES({args.gmres_m}), FP64 operator, eps_r {args.mixed_tol:g}",
             "gmres_iters": float(np.mean(gmres_iters[-args.steps:])) if gmres_iters else None,
             "mixed_rel_err_vs_reference": mixed_rel if fp64 else None,
             "mixed_rel_err_vs_oracle": vs_oracle["mixed_timed_solve"] if vs_oracle else None,
@@ -906,32 +904,28 @@ def gpu_main(args, rank, world):
             "fp64_solve_rhs_per_s": fp64["solve_rhs_per_s"] if fp64 else None,
             "fp64_rel_err_vs_reference": fp64["rel_err_vs_reference"] if fp64 else None,
             "mixed_unrefined_rel_err": unref["rel_err_vs_reference"] if unref else None,
-            "reference": "FP64 factorization + GMRES vs the FP64 operator (eps_r %.1e)" % reference["eps_r"]
+            "reference": "FP64 factors + GMRES, eps_r %.1e" % reference["eps_r"]
                          if fp64 else None,
-            "near_field_mixed_solve_rhs_per_s_at_1e-5": near["mixed_at_1e-5"]["solve_rhs_per_s"] if near else None,
-            "near_field_mixed_rel_err_at_1e-5": near["mixed_at_1e-5"]["rel_err_vs_reference"] if near else None,
-            "near_field_mixed_factorize_s": near["mixed_at_1e-5"]["factorize_s"] if near else None,
-            "near_field_fp64_factorize_s": near["fp64"]["factorize_s"] if near else None,
-            "near_field_mixed_richardson_rhs_per_s": near["mixed_richardson"]["solve_rhs_per_s"] if near else None,
-            "near_field_mixed_richardson_rel_err": near["mixed_richardson"]["rel_err_vs_reference"] if near else None,
-            "near_field_fp64_solve_rhs_per_s": near["fp64"]["solve_rhs_per_s"] if near else None,
-            "near_field_block16_fp64_rhs_per_s": near["block16"]["fp64_direct"]["solve_rhs_per_s"] if near else None,
-            "near_field_block16_mixed_rhs_per_s": near["block16"]["mixed_richardson"]["solve_rhs_per_s"] if near else None,
-            "near_field_block16_mixed_rel_err": near["block16"]["mixed_richardson"]["rel_err_vs_reference"]
-                                                if near else None,
-            "near_field_block16_mixed_tc_rhs_per_s":
-                near["block16"]["mixed_richardson_tc_operator"]["solve_rhs_per_s"] if near else None,
-            "near_field_block64_fp64_rhs_per_s": near["block64"]["fp64_direct"]["solve_rhs_per_s"] if near else None,
-            "near_field_block64_mixed_tc_rhs_per_s":
-                near["block64"]["mixed_richardson_tc_operator"]["solve_rhs_per_s"] if near else None,
-            "near_field_block64_mixed_tc_rel_err":
-                near["block64"]["mixed_richardson_tc_operator"]["rel_err_vs_fp64_direct"] if near else None,
-            "near_field_mixed_unrefined_rel_err": near["mixed_unrefined"]["rel_err_vs_reference"] if near else None,
-            "lean_factor_gb": [lean["standard"]["factor_gb"], lean["w_recompute"]["factor_gb"]] if lean else None,
-            "lean_mixed_solve_rhs_per_s": lean["w_recompute"]["solve_rhs_per_s"] if lean else None,
-            "batched_mixed_max_rel_err_vs_fp64": batched["mixed"]["rel_err_vs_fp64"]["max"] if batched else None,
-            "batched_mixed_solve_rhs_per_s": batched["mixed"]["rhs_per_s"] if batched else None,
-            "batched_fp64_solve_rhs_per_s": batched["fp64"]["rhs_per_s"] if batched else None,
+            "near_field": {  # near-field sampling (kappa neighbours per point), same points and right-hand side
+                "factorize_s": [near["mixed_at_1e-5"]["factorize_s"], near["fp64"]["factorize_s"]],  # mixed, FP64
+                "mixed_rhs_per_s_at_1e-5": near["mixed_at_1e-5"]["solve_rhs_per_s"],
+                "mixed_rel_err_at_1e-5": near["mixed_at_1e-5"]["rel_err_vs_reference"],
+                "richardson_rhs_per_s": near["mixed_richardson"]["solve_rhs_per_s"],
+                "richardson_rel_err": near["mixed_richardson"]["rel_err_vs_reference"],
+                "fp64_rhs_per_s": near["fp64"]["solve_rhs_per_s"],
+                "unrefined_rel_err": near["mixed_unrefined"]["rel_err_vs_reference"],
+                "block16_rhs_per_s": {"fp64": near["block16"]["fp64_direct"]["solve_rhs_per_s"],
+                                      "mixed": near["block16"]["mixed_richardson"]["solve_rhs_per_s"],
+                                      "mixed_tc": near["block16"]["mixed_richardson_tc_operator"]["solve_rhs_per_s"]},
+                "block16_mixed_rel_err": near["block16"]["mixed_richardson"]["rel_err_vs_reference"],
+                "block64_rhs_per_s": {"fp64": near["block64"]["fp64_direct"]["solve_rhs_per_s"],
+                                      "mixed_tc": near["block64"]["mixed_richardson_tc_operator"]["solve_rhs_per_s"]},
+                "block64_mixed_tc_rel_err": near["block64"]["mixed_richardson_tc_operator"]["rel_err_vs_fp64_direct"],
+            } if near else None,
+            "lean": {"factor_gb": [lean["standard"]["factor_gb"], lean["w_recompute"]["factor_gb"]],
+                     "mixed_rhs_per_s": lean["w_recompute"]["solve_rhs_per_s"]} if lean else None,
+            "batched": {"mixed_rhs_per_s": batched["mixed"]["rhs_per_s"], "fp64_rhs_per_s": batched["fp64"]["rhs_per_s"],
+                        "mixed_max_rel_err_vs_fp64": batched["mixed"]["rel_err_vs_fp64"]["max"]} if batched else None,
             "ranks": {"mean": round(float(np.mean(ranks[2:])), 1), "max": int(np.max(ranks))},
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -952,15 +946,22 @@ def gpu_main(args, rank, world):
             "memory_lean_w": lean,
             "differentiation": diff, "batched": batched,
         }
-        for k, v in line.items():  # errors to three significant figures in the one-line summary
-            if isinstance(v, float) and "rel_err" in k:
-                line[k] = float(f"{v:.3g}")
-        print(json.dumps(line), flush=True)
+        print(json.dumps(round_errors(line)), flush=True)
         # the per-phase and per-workload figures: one JSON line on stderr (and a file on request)
         print(json.dumps(detail), file=sys.stderr, flush=True)
         if args.detail_out:
             with open(args.detail_out, "w") as fh:
                 json.dump(detail, fh, indent=1)
+
+
+def round_errors(obj, key=""):
+    """Relative errors to three significant figures in the one-line summary
+    (nested groups included); everything else as it is."""
+    if isinstance(obj, dict):
+        return {k: round_errors(v, k) for k, v in obj.items()}
+    if isinstance(obj, float) and "rel_err" in key:
+        return float(f"{obj:.3g}")
+    return obj
 
 
 def once(args):

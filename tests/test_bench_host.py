@@ -1,6 +1,6 @@
 """Host-side logic of bench.py on CPU: the clock-sample summary that decides
 whether a run was throttled, the node ranges its work model uses (against the
-oracle's tree), and the per-phase roofline arithmetic."""
+oracle's tree), the per-phase roofline arithmetic and the rounding of the one-line summary."""
 import numpy as np
 
 import bench
@@ -46,3 +46,15 @@ def test_phase_roofline_arithmetic():
     # 2 x 2.5e11 flops in 0.4 s = 1.25 TFLOP/s, the nominal FP64 rate
     assert out["z_lu"]["achieved"] == 1.25 and out["z_lu"]["frac"] == 1.0
     assert "zoff" not in out                        # no work: no rate
+
+
+def test_error_rounding_reaches_nested_groups():
+    line = {"value": 1.0891234, "mixed_rel_err_vs_oracle": 2.21234e-10,
+            "near_field": {"richardson_rel_err": 3.466450935e-07, "factorize_s": [1.4957, 4.7189],
+                           "block16_rhs_per_s": {"mixed_tc": 141.3612}},
+            "batched": None}
+    out = bench.round_errors(line)
+    assert out["value"] == 1.0891234 and out["mixed_rel_err_vs_oracle"] == 2.21e-10
+    assert out["near_field"]["richardson_rel_err"] == 3.47e-07
+    assert out["near_field"]["factorize_s"] == [1.4957, 4.7189]
+    assert out["near_field"]["block16_rhs_per_s"]["mixed_tc"] == 141.3612 and out["batched"] is None
