@@ -6,10 +6,13 @@ tau >= max |x|, into 7 balanced digits; digit products summed over a
 128-row window in the tensor core's FP32 accumulator must be exact, and the
 8 groups p + q <= 7 must carry the product to about 2^-49 tau per entry.
 These checks restate the scheme in integer arithmetic (Ozaki, Ogita, Oishi
-and Rump, Numer. Algorithms 59, 2012) and pin its two bounds: the window
-sums stay below 2^24 for the largest digits the cuts can produce, and the
-truncated sum agrees with exact rational arithmetic to the stated error.
+and Rump, Numer. Algorithms 59, 2012) and pin its bounds: the window
+sums stay below 2^24 for the largest digits the cuts can produce, the
+truncated sum agrees with exact rational arithmetic to the stated error, and
+the read-out's two int64 sums convert to FP64 exactly and carry the groups'
+weights.
 """
+import math
 from fractions import Fraction
 
 import numpy as np
@@ -82,3 +85,48 @@ def test_truncated_sum_matches_exact_arithmetic():
     exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(v, x))
     bound = Fraction(2) ** e / 2 ** 48 * sum(Fraction(float(a)) for a in v)
     assert abs(approx - exact) <= bound
+
+
+def _readout(A, Dg, e, rows):
+    """The kernels' read-out: per 128-row window the 8 exact group sums; over
+    the windows two int64 sums, hi = sum_{g<=3} acc_g 2^(7(3-g)) and
+    lo = sum_{g>=4} acc_g 2^(7(7-g)); the value 2^(e-35) hi + 2^(e-63) lo in
+    FP64 (two exact conversions, two exact scalings, one rounded addition)."""
+    hi = lo = 0
+    weighted = Fraction(0)  # the same group sums at their weights 2^(-7(g+2)), exactly
+    for w0 in range(0, rows, WIN):
+        for g in range(8):
+            acc = sum(A[i][p] * Dg[i][g - p] for i in range(w0, min(rows, w0 + WIN))
+                      for p in range(ND) if 0 <= g - p < ND)
+            weighted += Fraction(acc, 2 ** (7 * (g + 2)))
+            if g <= 3:
+                hi += acc << (7 * (3 - g))
+            else:
+                lo += acc << (7 * (7 - g))
+    return hi, lo, math.ldexp(float(hi), e - 35) + math.ldexp(float(lo), e - 63), weighted * Fraction(2) ** e
+
+
+def test_readout_int64_sums_convert_exactly():
+    """Eight windows (a 1024-row chunk or leaf, the most one read-out sums) of
+    the largest digits: |hi| and |lo| stay below 2^53, so both convert to
+    FP64 without rounding and the read-out rounds once, in its addition."""
+    amax = [128] + [127] * (ND - 1)
+    dmax = [128] + [64] * (ND - 1)
+    A, Dg = [amax] * (8 * WIN), [dmax] * (8 * WIN)
+    hi, lo, _, _ = _readout(A, Dg, 0, 8 * WIN)
+    assert 0 < hi < 2 ** 53 and 0 < lo < 2 ** 53
+
+
+def test_readout_matches_exact_group_sum():
+    """The read-out's shifts (7(3-g) with 2^-35, 7(7-g) with 2^-63) against
+    the group weights 2^(-7(g+2)) summed exactly: equal up to the one
+    rounding of the final addition."""
+    rng = np.random.default_rng(13)
+    n = 1000  # eight windows, the last one ragged
+    v = rng.random(n)
+    x = rng.standard_normal(n) * 3.0
+    e = int(np.frexp(np.abs(x).max())[1])
+    A = [v_digits(t) for t in v]
+    Dg = [x_digits(t, e) for t in x]
+    _, _, val, exact = _readout(A, Dg, e, n)
+    assert abs(Fraction(val) - exact) <= abs(exact) * Fraction(1, 2 ** 53)
