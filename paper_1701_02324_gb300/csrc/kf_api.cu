@@ -867,8 +867,9 @@ static kf_status rel_residual(kf_factor* f, const double* Bt, const double* Xt, 
 // Hessenberg matrix and Givens rotations, on the host) that share every
 // launch -- one k-column preconditioner sweep (z_j = M^-1 v_j, or M^-T v_j,
 // kept) and one k-column operator product per iteration, classical
-// Gram-Schmidt applied twice, three host round trips per iteration for all
-// columns together.  FP64 basis, right preconditioning by the factorization,
+// Gram-Schmidt applied twice, four host synchronizations per iteration for
+// all columns together (the two Gram-Schmidt passes' coefficients and the new
+// vector's norm come to the host, the column scales go back).  FP64 basis, right preconditioning by the factorization,
 // the true residual recomputed at every restart.  B, X: N x k point-major;
 // X holds the initial guess.  bnorm: host, ||b_c||.  A column stops
 // contributing once its residual estimate is below tol ||b_c|| (later steps
