@@ -215,7 +215,10 @@ kf_status kf_solve(kf_factor* f, const void* B, void* X, int64_t nrhs, int64_t l
                    int32_t transpose, void* stream, kf_solve_info* info);
 /* Y = (lambda I + K~) X with the operator the factorization inverts
  * (second form of Eq. e:uv): leaf blocks lambda I + K_aa, off-diagonal blocks
- * P_{l l~} K_{l~ r} and P_{r r~} K_{r~ l}.  Layout as kf_solve. */
+ * P_{l l~} K_{l~ r} and P_{r r~} K_{r~ l}.  Layout as kf_solve.  With
+ * opts.tc_operator and 16 <= nrhs <= 4096 the call holds the BF16 digits of X
+ * (14 bytes per entry) for its duration; KF_ENOMEM when they do not fit
+ * (Y then unspecified; a smaller block of columns fits). */
 kf_status kf_matvec(kf_factor* f, const void* X, void* Y, int64_t nrhs, int64_t ld, int32_t dtype, void* stream);
 /* Gradient of a loss L through x = (lambda I + K~)^-1 b given x and dL/dx:
  * a = (lambda I + K~)^-T dL/dx; dL/db = a; dL/dlambda = -sum a.x;
